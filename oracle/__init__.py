@@ -1,0 +1,241 @@
+"""FP64 CPU oracle of the TRT-LBM-VP method (arXiv:1901.08766) — TEST INFRASTRUCTURE.
+
+Only the tests, the package smoke check and the benchmark's CPU-baseline / reference
+arm may import this module. The CUDA library never calls it and shares no code
+with it. The arithmetic lives in ``lbm_oracle.c`` (plain C, FP64, one node at a
+time, in the paper's notation); this file builds it with gcc, marshals numpy
+arrays through ctypes and adds the host-side diagnostics (force coefficients and
+the Strouhal number, Sec. 3).
+
+Every function here is pinned by the ``-m "not gpu"`` tests against closed forms,
+invariants, reductions and brute force (see tests/test_oracle_pins.py).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_DEFAULT_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB = _DEFAULT_LIB
+_lock = threading.Lock()
+_lib = None
+
+EDGE = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
+SHAPE = {"circle": 0, "annulus_outside": 1, "naca4": 2}
+
+# D2Q9 constants of the oracle, Eq. (D2Q9) and the weights under Eq. (feq).
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+class _Params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nu", C.c_double),
+                ("magic_lambda", C.c_double), ("eta", C.c_double), ("rho0", C.c_double),
+                ("u_in_x", C.c_double), ("u_in_y", C.c_double), ("west", C.c_int32),
+                ("east", C.c_int32), ("south", C.c_int32), ("north", C.c_int32)]
+
+
+class _Body(C.Structure):
+    _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("vx", C.c_double),
+                ("vy", C.c_double), ("omega", C.c_double)]
+
+
+class _Shape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("body", C.c_int32), ("cx", C.c_double),
+                ("cy", C.c_double), ("radius", C.c_double), ("chord", C.c_double),
+                ("thickness", C.c_double), ("aoa_rad", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile lbm_oracle.c into _build/liboracle.so (gcc, -O2, no FP contraction)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and (
+                _LIB != _DEFAULT_LIB or os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-std=c11", "-fopenmp", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        u8p = C.POINTER(C.c_uint8)
+        L.ora_tau_s.restype = C.c_double
+        L.ora_tau_s.argtypes = [C.POINTER(_Params)]
+        L.ora_tau_a.restype = C.c_double
+        L.ora_tau_a.argtypes = [C.POINTER(_Params)]
+        L.ora_equilibrium.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+        L.ora_guo.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp]
+        L.ora_naca_half_thickness.restype = C.c_double
+        L.ora_naca_half_thickness.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.ora_rasterize.argtypes = [C.c_int32, C.c_int32, C.POINTER(_Shape), C.c_int32, u8p]
+        for fn in (L.ora_step_trt, L.ora_step_srt):
+            fn.argtypes = [C.POINTER(_Params), u8p, C.POINTER(_Body), C.c_int32, dp, dp, dp]
+        L.ora_run.restype = C.c_int
+        L.ora_run.argtypes = [C.POINTER(_Params), u8p, C.POINTER(_Body), C.c_int32, dp,
+                              C.c_int64, dp, C.c_int32]
+        L.ora_init.argtypes = [C.POINTER(_Params), C.c_double, C.c_double, dp]
+        L.ora_stream.argtypes = [C.POINTER(_Params), dp, dp]
+        L.ora_moments.argtypes = [C.POINTER(_Params), u8p, C.POINTER(_Body), dp, dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def params_of(spec) -> _Params:
+    e = spec["edges"]
+    return _Params(spec["nx"], spec["ny"], spec["nu"], spec["magic_lambda"], spec["eta"],
+                   spec["rho0"], spec["u_in"][0], spec["u_in"][1], EDGE[e["west"]],
+                   EDGE[e["east"]], EDGE[e["south"]], EDGE[e["north"]])
+
+
+def _shapes_of(spec):
+    shp = spec["shapes"]
+    arr = (_Shape * max(1, len(shp)))()
+    for k, s in enumerate(shp):
+        arr[k] = _Shape(SHAPE[s["kind"]], s["body"], s["cx"], s["cy"], s.get("radius", 0.0),
+                        s.get("chord", 0.0), s.get("thickness", 0.0), s.get("aoa_rad", 0.0))
+    return arr, len(shp)
+
+
+def _bodies_of(spec):
+    bs = spec["bodies"]
+    arr = (_Body * max(1, len(bs)))()
+    for k, b in enumerate(bs):
+        arr[k] = _Body(b["cx"], b["cy"], b["vx"], b["vy"], b["omega"])
+    return arr, len(bs)
+
+
+def tau_s(spec) -> float:
+    return lib().ora_tau_s(C.byref(params_of(spec)))
+
+
+def tau_a(spec) -> float:
+    return lib().ora_tau_a(C.byref(params_of(spec)))
+
+
+def equilibrium(rho, ux, uy) -> np.ndarray:
+    out = np.zeros(9)
+    lib().ora_equilibrium(rho, ux, uy, _dp(out))
+    return out
+
+
+def guo(ux, uy, fx, fy) -> np.ndarray:
+    out = np.zeros(9)
+    lib().ora_guo(ux, uy, fx, fy, _dp(out))
+    return out
+
+
+def naca_half_thickness(xc, t=0.12, chord=1.0) -> float:
+    return lib().ora_naca_half_thickness(xc, t, chord)
+
+
+def stream(spec, g) -> np.ndarray:
+    """Step (3) alone: the streamed populations f [9, ny, nx] of a state g."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    f = np.zeros_like(g)
+    lib().ora_stream(C.byref(params_of(spec)), _dp(g), _dp(f))
+    return f
+
+
+def rasterize(spec) -> np.ndarray:
+    """Body-id mask uint8 [ny, nx] (0 = fluid) from the spec's shapes."""
+    nx, ny = spec["nx"], spec["ny"]
+    mask = np.zeros((ny, nx), dtype=np.uint8)
+    arr, n = _shapes_of(spec)
+    lib().ora_rasterize(nx, ny, arr, n, mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return mask
+
+
+class Domain:
+    """One simulation: post-collision populations g [9, ny, nx] in FP64."""
+
+    def __init__(self, spec, mask=None, g=None):
+        self.spec = spec
+        self.p = params_of(spec)
+        self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask,
+                                         dtype=np.uint8)
+        self.bodies, self.nb = _bodies_of(spec)
+        nx, ny = spec["nx"], spec["ny"]
+        if g is None:
+            self.g = np.zeros((9, ny, nx))
+            lib().ora_init(C.byref(self.p), spec["u0"][0], spec["u0"][1], _dp(self.g))
+        else:
+            self.g = np.ascontiguousarray(g, dtype=np.float64).copy()
+        self.steps_done = 0
+
+    def run(self, n: int, srt: bool = False, want_forces: bool = True) -> np.ndarray:
+        """Advance n steps; returns the force on each body per step, [n, nbodies, 2]."""
+        forces = np.zeros((n, max(self.nb, 1), 2)) if want_forces else None
+        rc = lib().ora_run(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)),
+                           self.bodies, self.nb, _dp(self.g), n,
+                           _dp(forces) if want_forces else None, 1 if srt else 0)
+        if rc != 0:
+            raise MemoryError("oracle run failed to allocate")
+        self.steps_done += n
+        return forces[:, : self.nb] if want_forces else None
+
+    def step_once(self, srt: bool = False):
+        """One step returning (new g, forces [nbodies, 2]) without the run wrapper."""
+        out = np.zeros_like(self.g)
+        fb = np.zeros((max(self.nb, 1), 2))
+        fn = lib().ora_step_srt if srt else lib().ora_step_trt
+        fn(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)), self.bodies,
+           self.nb, _dp(self.g), _dp(out), _dp(fb))
+        self.g = out
+        self.steps_done += 1
+        return out, fb[: self.nb]
+
+    def moments(self):
+        nx, ny = self.spec["nx"], self.spec["ny"]
+        rho, ux, uy = (np.zeros((ny, nx)) for _ in range(3))
+        lib().ora_moments(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)),
+                          self.bodies, _dp(self.g), _dp(rho), _dp(ux), _dp(uy))
+        return rho, ux, uy
+
+
+# ---- diagnostics (Sec. 3: Re, C_d, C_l, St) ---------------------------------------------
+
+def coefficients(forces, U, ref_length, rho0=1.0):
+    """C_d = 2 F_x / (rho U^2 D), C_l = 2 F_y / (rho U^2 D) for a [n, 2] force series."""
+    f = np.asarray(forces, dtype=np.float64)
+    s = 2.0 / (rho0 * U * U * ref_length)
+    return f[:, 0] * s, f[:, 1] * s
+
+
+def strouhal(signal, ref_length, U, dt=1.0):
+    """St = f_q D / U from the upward zero crossings of (signal - mean), linearly
+    interpolated, over whole periods between the first and last crossing."""
+    x = np.asarray(signal, dtype=np.float64)
+    x = x - x.mean()
+    t_cross = []
+    for n in range(len(x) - 1):
+        if x[n] < 0.0 <= x[n + 1]:
+            t_cross.append((n + (-x[n]) / (x[n + 1] - x[n])) * dt)
+    if len(t_cross) < 2:
+        return 0.0
+    periods = len(t_cross) - 1
+    f = periods / (t_cross[-1] - t_cross[0])
+    return f * ref_length / U
+
+
+def rms(signal):
+    x = np.asarray(signal, dtype=np.float64)
+    return float(np.sqrt(np.mean((x - x.mean()) ** 2)))

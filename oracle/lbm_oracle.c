@@ -1,0 +1,345 @@
+/*
+ * Plain FP64 CPU oracle of the TRT-LBM-VP method (Cui, Wang, Yao, Liu, Yu,
+ * "A coupled two-relaxation-time lattice Boltzmann-volume penalization method for
+ * flows past obstacles", arXiv:1901.08766). TEST INFRASTRUCTURE ONLY: it is used by
+ * the tests, by the package's smoke check and by the benchmark's CPU baseline,
+ * never by the library's compute path. It shares no source with the CUDA library.
+ *
+ * Written for a reader checking it against the paper by eye: one cell at a time,
+ * the paper's notation (tau_s, tau_a, f^s, f^a, F^s, F^a, u*, du, F_VP), no fusion
+ * beyond what the equations state. Compiled with -O2 -ffp-contract=off.
+ *
+ * Readings of points the paper leaves open (each is listed in the design notes):
+ *  - tau_s = nu / c_s^2 + 1/2 (the printed relation omits the +1/2, Sec. 2.1);
+ *  - the Guo term is used without the extra (1 - 1/(2 lambda)) prefactor of its
+ *    definition, since the modified collision already relaxes F^s and F^a once each;
+ *  - f^eq and the Guo term use the corrected velocity u = u* + du, F_VP uses u*;
+ *  - the state is the post-collision population g; a step pulls g from the
+ *    neighbours (streaming), forms rho and u*, penalizes, then collides;
+ *  - edges: equilibrium inlet ghost, zero-gradient outflow, specular free-slip, or
+ *    periodic; the x rule is applied before the y rule;
+ *  - the reported force on body k is the force ON the body, -sum F_VP over its cells.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+
+/* D2Q9 velocities, Eq. (D2Q9): alpha = 0 rest, 1..4 at angles (alpha-1) pi/2,
+ * 5..8 at angles (2 alpha - 9) pi/4 with length sqrt(2). */
+static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* opposite direction -alpha (Sec. 2.1: f_{-1} = f_3, f_{-0} = f_0) */
+static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+/* reflection across a horizontal wall (e_y -> -e_y), used by free-slip edges */
+static const int REFLECT_Y[Q] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+/* weights below Eq. (feq) */
+static const double WGT[Q] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0; /* c_s^2, c_s = 1/sqrt(3) */
+
+/* edge kinds */
+enum { ORA_PERIODIC = 0, ORA_INLET = 1, ORA_OUTFLOW = 2, ORA_FREE_SLIP = 3 };
+/* shape kinds */
+enum { ORA_CIRCLE = 0, ORA_ANNULUS_OUTSIDE = 1, ORA_NACA4 = 2 };
+
+typedef struct {
+  int32_t nx, ny;
+  double nu, magic_lambda, eta, rho0;
+  double u_in_x, u_in_y;
+  int32_t west, east, south, north;
+} ora_params;
+
+typedef struct {
+  double cx, cy, vx, vy, omega;
+} ora_body;
+
+typedef struct {
+  int32_t kind, body;
+  double cx, cy, radius;
+  double chord, thickness, aoa_rad;
+} ora_shape;
+
+/* ---- relaxation times (Sec. 2.1) ------------------------------------------------ */
+
+double ora_tau_s(const ora_params *p) { return p->nu / CS2 + 0.5; }
+
+/* magic parameter Lambda = (tau_s - 1/2)(tau_a - 1/2) solved for tau_a */
+double ora_tau_a(const ora_params *p) {
+  return 0.5 + p->magic_lambda / (ora_tau_s(p) - 0.5);
+}
+
+/* ---- equilibrium, Eq. (feq) -------------------------------------------------------- */
+
+void ora_equilibrium(double rho, double ux, double uy, double *feq) {
+  double usq = ux * ux + uy * uy;
+  for (int a = 0; a < Q; a++) {
+    double eu = EX[a] * ux + EY[a] * uy;
+    feq[a] = rho * WGT[a] * (1.0 + eu / CS2 + (eu * eu - CS2 * usq) / (2.0 * CS2 * CS2));
+  }
+}
+
+/* Guo forcing term of Eq. (external-force-term) without its leading prefactor:
+ * F_alpha = w_alpha [ (e_alpha - u)/c_s^2 + (e_alpha . u) e_alpha / c_s^4 ] . F */
+void ora_guo(double ux, double uy, double fx, double fy, double *F) {
+  for (int a = 0; a < Q; a++) {
+    double eu = EX[a] * ux + EY[a] * uy;
+    double cx = (EX[a] - ux) / CS2 + eu * EX[a] / (CS2 * CS2);
+    double cy = (EY[a] - uy) / CS2 + eu * EY[a] / (CS2 * CS2);
+    F[a] = WGT[a] * (cx * fx + cy * fy);
+  }
+}
+
+/* ---- geometry -> mask chi (Eq. mask function) -------------------------------------- */
+
+/* NACA 4-digit symmetric half thickness at x = x'/c (open trailing edge), times c. */
+double ora_naca_half_thickness(double xc, double t, double chord) {
+  double s = sqrt(xc);
+  double p = (((-0.1015 * xc + 0.2843) * xc - 0.3516) * xc - 0.1260) * xc;
+  return 5.0 * t * chord * (0.2969 * s + p);
+}
+
+static int inside_shape(const ora_shape *s, double x, double y) {
+  if (s->kind == ORA_CIRCLE || s->kind == ORA_ANNULUS_OUTSIDE) {
+    double dx = x - s->cx, dy = y - s->cy;
+    double d2 = dx * dx + dy * dy;
+    double r2 = s->radius * s->radius;
+    return s->kind == ORA_CIRCLE ? (d2 < r2) : (d2 > r2);
+  }
+  if (s->kind == ORA_NACA4) {
+    /* quarter chord at (cx, cy); nose-up angle of attack positive */
+    double ca = cos(s->aoa_rad), sa = sin(s->aoa_rad);
+    double qc = 0.25 * s->chord;
+    double lex = s->cx - qc * ca, ley = s->cy + qc * sa; /* leading edge */
+    double dx = x - lex, dy = y - ley;
+    double xp = dx * ca - dy * sa; /* along the chord */
+    double yp = dx * sa + dy * ca; /* normal to the chord */
+    if (!(xp >= 0.0 && xp <= s->chord)) return 0;
+    double yt = ora_naca_half_thickness(xp / s->chord, s->thickness, s->chord);
+    return fabs(yp) <= yt;
+  }
+  return 0;
+}
+
+/* Body id per node (0 = fluid); later shapes overwrite earlier ones. */
+void ora_rasterize(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
+                   uint8_t *mask) {
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      uint8_t b = 0;
+      for (int k = 0; k < nshapes; k++)
+        if (inside_shape(&shapes[k], (double)i, (double)j)) b = (uint8_t)shapes[k].body;
+      mask[(size_t)j * nx + i] = b;
+    }
+}
+
+/* ---- streaming with the domain-edge rules (Eq. streaming) ---------------------------- */
+
+static inline double G(const double *g, const ora_params *p, int a, int j, int i) {
+  return g[((size_t)a * p->ny + j) * p->nx + i];
+}
+
+/* f_alpha(i, j) = g_alpha(i - e_x, j - e_y) at the previous time level. */
+static double pull(const ora_params *p, const double *g, const double *feq_inlet, int a,
+                   int i, int j) {
+  int sx = i - EX[a], sy = j - EY[a], src = a;
+  if (sx < 0) {
+    if (p->west == ORA_INLET) return feq_inlet[a];
+    sx += p->nx;
+  } else if (sx > p->nx - 1) {
+    if (p->east == ORA_OUTFLOW) sx = p->nx - 1;
+    else sx -= p->nx;
+  }
+  if (sy < 0) {
+    if (p->south == ORA_FREE_SLIP) { sy = 0; src = REFLECT_Y[a]; }
+    else sy += p->ny;
+  } else if (sy > p->ny - 1) {
+    if (p->north == ORA_FREE_SLIP) { sy = p->ny - 1; src = REFLECT_Y[a]; }
+    else sy -= p->ny;
+  }
+  return G(g, p, src, sy, sx);
+}
+
+/* Step (3) alone: f(x) = g(x - e_alpha) for every node and direction, with the edge
+ * rules of pull(). Used to pin the streaming and edge rules on their own. */
+void ora_stream(const ora_params *p, const double *g, double *f) {
+  double feq_inlet[Q];
+  ora_equilibrium(p->rho0, p->u_in_x, p->u_in_y, feq_inlet);
+  for (int a = 0; a < Q; a++)
+    for (int j = 0; j < p->ny; j++)
+      for (int i = 0; i < p->nx; i++)
+        f[((size_t)a * p->ny + j) * p->nx + i] = pull(p, g, feq_inlet, a, i, j);
+}
+
+/* Obstacle velocity U_O at node (i, j) of body k: V_k + Omega_k z x (x - c_k). */
+static void body_velocity(const ora_body *b, int i, int j, double *uox, double *uoy) {
+  *uox = b->vx - b->omega * ((double)j - b->cy);
+  *uoy = b->vy + b->omega * ((double)i - b->cx);
+}
+
+/* Per-node macroscopic step shared by the TRT and SRT updates: steps (3)-(5) of the
+ * algorithm of Sec. 2.2. Outputs rho, the corrected velocity u and F_VP. */
+static void node_moments(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
+                         const double *f, int i, int j, double *rho, double *ux,
+                         double *uy, double *fvx, double *fvy) {
+  /* Eq. (rho), Eq. (rho*velocity-star) */
+  double r = 0.0, jx = 0.0, jy = 0.0;
+  for (int a = 0; a < Q; a++) {
+    r += f[a];
+    jx += EX[a] * f[a];
+    jy += EY[a] * f[a];
+  }
+  double usx = jx / r, usy = jy / r;
+  int b = mask[(size_t)j * p->nx + i];
+  double chi = b ? 1.0 : 0.0;
+  double uox = 0.0, uoy = 0.0;
+  if (b) body_velocity(&bodies[b - 1], i, j, &uox, &uoy);
+  const double dt = 1.0;
+  /* Eq. (d-V) and Eq. (force-density) */
+  double dux = chi * (uox - usx) / (2.0 * p->eta / dt + chi);
+  double duy = chi * (uoy - usy) / (2.0 * p->eta / dt + chi);
+  *fvx = 2.0 * r * chi * (uox - usx) / (2.0 * p->eta + chi * dt);
+  *fvy = 2.0 * r * chi * (uoy - usy) / (2.0 * p->eta + chi * dt);
+  /* Eq. (velocity-r) */
+  *ux = usx + dux;
+  *uy = usy + duy;
+  *rho = r;
+}
+
+/* Force on body k = -sum of F_VP over its nodes (Eq. hydrodynamic force with the
+ * sign read as the force on the body), summed serially in row-major order. */
+static void sum_body_forces(const ora_params *p, const uint8_t *mask, const double *fv,
+                            int32_t nbodies, double *force) {
+  for (int k = 0; k < 2 * nbodies; k++) force[k] = 0.0;
+  for (int j = 0; j < p->ny; j++)
+    for (int i = 0; i < p->nx; i++) {
+      size_t c = (size_t)j * p->nx + i;
+      int b = mask[c];
+      if (b && b <= nbodies) {
+        force[2 * (b - 1) + 0] -= fv[2 * c];
+        force[2 * (b - 1) + 1] -= fv[2 * c + 1];
+      }
+    }
+}
+
+/*
+ * One TRT-LBM-VP time step (algorithm of Sec. 2.2, steps (2)-(6)):
+ * g_out(x) = collide(pull(g_in)) with Eq. (TRT-collision) and Eq. (collision-modified).
+ * force[2*(k-1) + {0,1}] receives the force on body k (row-major sum over its nodes).
+ */
+void ora_step_trt(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
+                  int32_t nbodies, const double *g_in, double *g_out, double *force) {
+  const double tau_s = ora_tau_s(p), tau_a = ora_tau_a(p);
+  double feq_inlet[Q];
+  ora_equilibrium(p->rho0, p->u_in_x, p->u_in_y, feq_inlet);
+  size_t cells = (size_t)p->nx * p->ny;
+  double *fv = (double *)malloc(sizeof(double) * 2 * cells);
+  if (!fv) abort();
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < p->ny; j++)
+    for (int i = 0; i < p->nx; i++) {
+      double f[Q], feq[Q], F[Q];
+      for (int a = 0; a < Q; a++) f[a] = pull(p, g_in, feq_inlet, a, i, j);
+      double rho, ux, uy, fvx, fvy;
+      node_moments(p, mask, bodies, f, i, j, &rho, &ux, &uy, &fvx, &fvy);
+      ora_equilibrium(rho, ux, uy, feq);
+      ora_guo(ux, uy, fvx, fvy, F);
+      for (int a = 0; a < Q; a++) {
+        int o = OPP[a];
+        double fs = 0.5 * (f[a] + f[o]), fa = 0.5 * (f[a] - f[o]);
+        double feqs = 0.5 * (feq[a] + feq[o]), feqa = 0.5 * (feq[a] - feq[o]);
+        double Fs = 0.5 * (F[a] + F[o]), Fa = 0.5 * (F[a] - F[o]);
+        double omega = -(fs - feqs) / tau_s - (fa - feqa) / tau_a;
+        g_out[((size_t)a * p->ny + j) * p->nx + i] =
+            f[a] + omega + (1.0 - 1.0 / (2.0 * tau_s)) * Fs + (1.0 - 1.0 / (2.0 * tau_a)) * Fa;
+      }
+      size_t c = (size_t)j * p->nx + i;
+      fv[2 * c] = fvx;
+      fv[2 * c + 1] = fvy;
+    }
+  sum_body_forces(p, mask, fv, nbodies, force);
+  free(fv);
+}
+
+/*
+ * The single-relaxation-time LBM-VP step the paper compares against (Sec. 3.1):
+ * g = f - (f - f^eq)/tau + (1 - 1/(2 tau)) F_alpha with tau = tau_s, the full
+ * (unsplit) Guo term and the same penalization.
+ */
+void ora_step_srt(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
+                  int32_t nbodies, const double *g_in, double *g_out, double *force) {
+  const double tau = ora_tau_s(p);
+  double feq_inlet[Q];
+  ora_equilibrium(p->rho0, p->u_in_x, p->u_in_y, feq_inlet);
+  size_t cells = (size_t)p->nx * p->ny;
+  double *fv = (double *)malloc(sizeof(double) * 2 * cells);
+  if (!fv) abort();
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < p->ny; j++)
+    for (int i = 0; i < p->nx; i++) {
+      double f[Q], feq[Q], F[Q];
+      for (int a = 0; a < Q; a++) f[a] = pull(p, g_in, feq_inlet, a, i, j);
+      double rho, ux, uy, fvx, fvy;
+      node_moments(p, mask, bodies, f, i, j, &rho, &ux, &uy, &fvx, &fvy);
+      ora_equilibrium(rho, ux, uy, feq);
+      ora_guo(ux, uy, fvx, fvy, F);
+      for (int a = 0; a < Q; a++)
+        g_out[((size_t)a * p->ny + j) * p->nx + i] =
+            f[a] - (f[a] - feq[a]) / tau + (1.0 - 1.0 / (2.0 * tau)) * F[a];
+      size_t c = (size_t)j * p->nx + i;
+      fv[2 * c] = fvx;
+      fv[2 * c + 1] = fvy;
+    }
+  sum_body_forces(p, mask, fv, nbodies, force);
+  free(fv);
+}
+
+/* Run n steps, ping-ponging between g and a scratch lattice; the result ends in g.
+ * forces: [n][nbodies][2] (may be NULL). srt != 0 selects the SRT update. */
+int ora_run(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
+            int32_t nbodies, double *g, int64_t n, double *forces, int32_t srt) {
+  size_t cells = (size_t)p->nx * p->ny;
+  double *tmp = (double *)malloc(sizeof(double) * Q * cells);
+  double *fb = (double *)malloc(sizeof(double) * 2 * (nbodies > 0 ? nbodies : 1));
+  if (!tmp || !fb) { free(tmp); free(fb); return -1; }
+  double *a = g, *b = tmp;
+  for (int64_t s = 0; s < n; s++) {
+    if (srt) ora_step_srt(p, mask, bodies, nbodies, a, b, fb);
+    else ora_step_trt(p, mask, bodies, nbodies, a, b, fb);
+    if (forces) memcpy(forces + (size_t)s * 2 * nbodies, fb, sizeof(double) * 2 * nbodies);
+    double *t = a; a = b; b = t;
+  }
+  if (a != g) memcpy(g, a, sizeof(double) * Q * cells);
+  free(tmp);
+  free(fb);
+  return 0;
+}
+
+/* Step (1): every node starts at f^eq(rho0, u0). */
+void ora_init(const ora_params *p, double u0x, double u0y, double *g) {
+  double feq[Q];
+  ora_equilibrium(p->rho0, u0x, u0y, feq);
+  size_t cells = (size_t)p->nx * p->ny;
+  for (int a = 0; a < Q; a++)
+    for (size_t c = 0; c < cells; c++) g[a * cells + c] = feq[a];
+}
+
+/* Macroscopic fields of the current state: rho and u = u* + du of the streamed
+ * populations (Eq. rho, Eq. rho*velocity-star, Eq. d-V, Eq. velocity-r). */
+void ora_moments(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
+                 const double *g, double *rho, double *ux, double *uy) {
+  double feq_inlet[Q];
+  ora_equilibrium(p->rho0, p->u_in_x, p->u_in_y, feq_inlet);
+  for (int j = 0; j < p->ny; j++)
+    for (int i = 0; i < p->nx; i++) {
+      double f[Q], r, vx, vy, fvx, fvy;
+      for (int a = 0; a < Q; a++) f[a] = pull(p, g, feq_inlet, a, i, j);
+      node_moments(p, mask, bodies, f, i, j, &r, &vx, &vy, &fvx, &fvy);
+      size_t c = (size_t)j * p->nx + i;
+      rho[c] = r;
+      ux[c] = vx;
+      uy[c] = vy;
+    }
+}

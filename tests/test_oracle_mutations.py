@@ -1,0 +1,98 @@
+"""The oracle's pins are sensitive: each plausible mistake planted in a copy of the
+oracle source (a dropped term, a wrong sign, index or table entry) makes at least one
+pin of tests/test_oracle_pins.py fail. Runs on the CPU only; the committed oracle is
+never modified."""
+import os
+import subprocess
+import warnings
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+import synth
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lbm_oracle.c")
+
+# (name, original text, planted mistake)
+MUTATIONS = [
+    ("reflect_table", "REFLECT_Y[Q] = {0, 1, 4, 3, 2, 8, 7, 6, 5}", "REFLECT_Y[Q] = {0, 1, 4, 3, 2, 7, 8, 5, 6}"),
+    ("opposite_table", "OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6}", "OPP[Q] = {0, 3, 4, 1, 2, 8, 7, 6, 5}"),
+    ("weight_diag", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0}", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 30.0}"),
+    ("feq_quadratic", "(2.0 * CS2 * CS2)", "(CS2 * CS2)"),
+    ("guo_drop_u", "double cx = (EX[a] - ux) / CS2", "double cx = (EX[a]) / CS2"),
+    ("guo_drop_quadratic", "double cy = (EY[a] - uy) / CS2 + eu * EY[a] / (CS2 * CS2);", "double cy = (EY[a] - uy) / CS2;"),
+    ("tau_s_no_half", "return p->nu / CS2 + 0.5;", "return p->nu / CS2 + 0.6;"),
+    ("tau_a_no_half", "return 0.5 + p->magic_lambda", "return 0.45 + p->magic_lambda"),
+    ("du_sign", "double dux = chi * (uox - usx)", "double dux = chi * (usx - uox)"),
+    ("fvp_factor", "*fvy = 2.0 * r * chi", "*fvy = 1.0 * r * chi"),
+    ("force_sign", "force[2 * (b - 1) + 0] -= fv[2 * c];", "force[2 * (b - 1) + 0] += fv[2 * c];"),
+    ("pull_direction", "int sx = i - EX[a], sy = j - EY[a], src = a;", "int sx = i + EX[a], sy = j - EY[a], src = a;"),
+    ("rotation_sign", "*uox = b->vx - b->omega", "*uox = b->vx + b->omega"),
+    ("antisym_factor", "(1.0 - 1.0 / (2.0 * tau_a)) * Fa", "(1.0 - 1.0 / (2.0 * tau_s)) * Fa"),
+    ("corrected_velocity", "*ux = usx + dux;", "*ux = usx;"),
+    ("outflow_rule", "if (p->east == ORA_OUTFLOW) sx = p->nx - 1;", "if (p->east == ORA_OUTFLOW) sx = p->nx - 2;"),
+    ("inlet_ghost", "if (p->west == ORA_INLET) return feq_inlet[a];", "if (p->west == ORA_INLET) return feq_inlet[OPP[a]];"),
+    ("naca_coefficient", "- 0.3516) * xc", "- 0.3561) * xc"),
+    ("naca_aoa_sign", "ley = s->cy + qc * sa;", "ley = s->cy - qc * sa;"),
+    ("circle_strict", "(d2 < r2) : (d2 > r2)", "(d2 <= r2) : (d2 > r2)"),
+]
+
+# Pins in order of cost; each mutation stops at the first one that fails.
+PINS = [
+    lambda: pins.test_equilibrium_moments(0.97, 0.05, -0.03),
+    lambda: pins.test_guo_term_moments(0.04, -0.02, -3e-4, 7e-4),
+    pins.test_gauss_circle_counts,
+    pins.test_rasterize_brute_force_small,
+    pins.test_naca0012_ordinates_published,
+    pins.test_naca_mask_area_and_attitude,
+    pins.test_stream_periodic_is_a_roll,
+    pins.test_stream_edge_rules,
+    lambda: [pins.test_rest_state_exactly_invariant(e) for e in pins.EDGE_SETS],
+    lambda: pins.test_uniform_flow_invariant(synth._edges(), (0.05, -0.03)),
+    lambda: pins.test_uniform_flow_invariant(
+        synth._edges("periodic", "periodic", "free_slip", "free_slip"), (0.06, 0.0)),
+    lambda: pins.test_uniform_flow_invariant(
+        synth._edges("inlet", "outflow", "free_slip", "free_slip"), (0.07, 0.0)),
+    pins.test_free_slip_channel_conserves_mass_and_axial_momentum,
+    pins.test_mass_conserved_periodic_with_moving_bodies,
+    pins.test_momentum_balance_equals_body_forces,
+    pins.test_fully_penalized_box_closed_form,
+    lambda: pins.test_shear_wave_decay_rate(0.1, 3 / 16),
+    pins.test_srt_reduction,
+    pins.test_couette_closed_form_and_trt_properties,
+]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(name, old, new, workdir):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mutated = src.replace(old, new, 1)
+    c_path = os.path.join(workdir, f"{name}.c")
+    so_path = os.path.join(workdir, f"{name}.so")
+    open(c_path, "w").write(mutated)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                           "-fopenmp", "-o", so_path, c_path, "-lm"])
+    saved_lib, saved_path = oracle._lib, oracle._LIB
+    try:
+        oracle._lib = None
+        oracle._LIB = so_path
+        caught = None
+        for k, pin in enumerate(PINS):
+            try:
+                with warnings.catch_warnings():
+                    warnings.simplefilter("ignore")
+                    pin()
+            except (AssertionError, FloatingPointError, ValueError, ZeroDivisionError,
+                    OverflowError):
+                caught = k
+                break
+        assert caught is not None, f"planted mistake {name} passed every pin"
+    finally:
+        oracle._lib, oracle._LIB = saved_lib, saved_path
