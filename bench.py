@@ -1,0 +1,362 @@
+"""Benchmark of the TRT-LBM-VP time step on GB300.
+
+Workload: the batched uneven-domain set (64 seeded domains, tandem and side-by-side
+cylinder pairs, widths 400..2000, height = width/2, Re 40..200, D = 40, U = 0.05),
+FP16-shifted storage, body forces every step, autotuned tile shape. One "step" is one
+time step of every domain: one force-reduction launch plus one fused sweep launch,
+replayed from CUDA graphs. The metric is GLUPS (10^9 node updates per second, every
+node counted, solid nodes included).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun (N > 1) every rank runs its own copy of the
+domain set (weak scaling, no data-path collective), timing is max over ranks.
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"f64": 145, "f32": 73, "f16s": 37, "bf16s": 37}
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "D2Q9 TRT-VP GLUPS, % HBM roofline; served-batch vs plain; p50/p99 latency"
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _traffic_record(storage):
+    """Per-node DRAM traffic of the sweep from a committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for name in ("lbm_sweep.cuh", "lbm_cell.cuh", f"lbm_sweep_{storage}.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1901_08766_gb300", "csrc", name), "rb").read())
+    entry = rec.get(storage)
+    if not entry or entry.get("source_sha256") != h.hexdigest():
+        return None
+    return entry
+
+
+def cpu_baseline(specs, seconds=12.0, min_steps=20):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample: the first
+    domain of the set, stepped until about `seconds` of CPU work."""
+    import oracle
+    spec = specs[0]
+    dom = oracle.Domain(spec)
+    cells = spec["nx"] * spec["ny"]
+    dom.run(2, want_forces=True)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        dom.run(10, want_forces=True)
+        steps += 10
+        el = time.perf_counter() - t0
+        if el >= seconds and steps >= min_steps:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": cells * steps / el / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"domain 0 of the set ({spec['nx']}x{spec['ny']}), {steps} steps, FP64, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    import oracle
+    specs = synth.batched_domains(64)
+    spec = specs[0]
+    cells = spec["nx"] * spec["ny"]
+    dom = oracle.Domain(spec)
+    dom.run(max(args.warmup, 0))
+    # each step of the reference arm: one oracle time step of the sample domain
+    t0 = time.perf_counter()
+    dom.run(args.steps)
+    el = time.perf_counter() - t0
+    value = cells * args.steps / el / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args, specs, "oracle sample: domain 0 of the set"),
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"domain 0 ({spec['nx']}x{spec['ny']}) for {args.steps} "
+                                       f"steps per run, FP64 oracle"},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, specs, extra=None):
+    cells = sum(s["nx"] * s["ny"] for s in specs)
+    c = {"workload": "batched uneven domains: 64 seeded tandem/side-by-side cylinder pairs, "
+                     "W 400..2000, H = W/2, Re 40..200, D = 40, U = 0.05",
+         "domains": len(specs), "cells": cells, "storage": args.storage,
+         "forces": "every step, FP64 per body", "graph_steps": args.graph_steps,
+         "l2": "inputs larger than L2 (working set %.2f GB per step)" %
+               (cells * BYTES_PER_CELL[args.storage] / 1e9),
+         "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    if extra:
+        c["note"] = extra
+    return c
+
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_1901_08766_gb300 as lbm
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    lbm.load()
+    specs = synth.batched_domains(64)
+    cells = sum(s["nx"] * s["ny"] for s in specs)
+    stream = torch.cuda.Stream()
+    nsteps_total = args.warmup + args.steps + args.profile_steps + 10
+
+    with torch.cuda.stream(stream):
+        batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_steps, stream=stream)
+        slots = [batch.admit(s, nsteps=nsteps_total, force_capacity=nsteps_total + 8) for s in specs]
+        tune_us = batch.autotune(reps=5) if not args.no_autotune else None
+        tile = batch.get_tile()
+        args.tile = tile
+        batch.run(args.warmup)
+        for k in slots:
+            batch.poll(k)
+        stream.synchronize()
+        launches0 = batch.info()["kernel_launches"]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ran = batch.run(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        clocks = sampler.stop()
+        launches = batch.info()["kernel_launches"] - launches0
+        assert ran == args.steps
+        # per-kernel durations of real steps, events on the batch stream
+        sweep_us, force_us, _ = batch.profile(args.profile_steps)
+        for k in slots:
+            _, _ = batch.poll(k)
+        batch.close()
+
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    value = cells * ws * args.steps / (ms / 1000.0) / 1e9
+    peak, peak_kind = _peak_hbm()
+    bpc = BYTES_PER_CELL[args.storage]
+    achieved = cells * bpc / (sweep_us * 1e-6) / 1e9
+    traffic = _traffic_record(args.storage)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "kernel": "sweep_kernel (fused stream + moments + VP + TRT collide)",
+                "bytes_per_cell": bpc, "cells_per_launch": cells,
+                "sweep_us": sweep_us, "force_us": force_us,
+                "traffic": (traffic["dram_bytes_per_cell"] * cells) if traffic else None}
+
+    e2e = None
+    plain = None
+    cpu = None
+    if rank == 0 and not args.quick:
+        e2e = measure_e2e(lbm, torch, specs, args)
+        plain = measure_plain_f32(lbm, torch, specs, args)
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(specs)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16s storage, f32 compute"
+            if args.storage == "f16s" else args.storage, "data": "synthetic",
+            "config": dict(_config(args, specs), tile={"vec": tile[0], "warps": tile[1], "rows": tile[2]},
+                           autotune_best_us=tune_us),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "plain_f32_per_domain": plain}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_e2e(lbm, torch, specs, args):
+    """The same metric through the public API with host inputs and outputs: admit every
+    domain from its host-side geometry, run the steps, read every force series back."""
+    import numpy as np
+    steps = args.steps
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_steps, stream=stream)
+        slots = [batch.admit(s, nsteps=steps, force_capacity=steps + 8) for s in specs]
+        if getattr(args, "tile", None):
+            batch.set_tile(*args.tile)
+        batch.run(steps)
+        nbytes_out = 0
+        for k in slots:
+            f, done = batch.poll(k)
+            nbytes_out += f.nbytes
+        stream.synchronize()
+        el = time.perf_counter() - t0
+        batch.close()
+    cells = sum(s["nx"] * s["ny"] for s in specs)
+    # host -> device per domain: parameters, shapes and bodies (the mask is rasterised
+    # on the device); device -> host: the force series
+    h2d = sum(120 + 56 * len(s["shapes"]) + 48 * len(s["bodies"]) for s in specs)
+    return {"value": cells * steps / el / 1e9, "unit": "GLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": nbytes_out / steps,
+            "includes": "batch creation, admission (rasterise + init), steps, force readback"}
+
+
+def measure_plain_f32(lbm, torch, specs, args, steps=30):
+    """The plain per-domain FP32 baseline: the same domains run one at a time in FP32,
+    one launch per kernel (no graphs, no batching); aggregate GLUPS of the sweeps."""
+    stream = torch.cuda.Stream()
+    total_cells_steps = 0
+    total_s = 0.0
+    with torch.cuda.stream(stream):
+        for s in specs[:: max(1, len(specs) // 16)]:
+            b = lbm.Batch("f32", max_domains=1, graph_steps=0, stream=stream)
+            k = b.admit(s, nsteps=steps + 5, force_capacity=steps + 8)
+            b.set_tile(4, 8, 2)
+            b.run(5)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(steps)
+            e1.record(stream)
+            e1.synchronize()
+            total_s += e0.elapsed_time(e1) / 1000.0
+            total_cells_steps += s["nx"] * s["ny"] * steps
+            b.close()
+    return {"value": total_cells_steps / total_s / 1e9, "unit": "GLUPS",
+            "sample": "16 of the 64 domains, one at a time, FP32 storage, no graphs, "
+                      f"{steps} steps each"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f16s", "bf16s", "f32", "f64"], default="f16s")
+    ap.add_argument("--graph-steps", type=int, default=32)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip e2e, plain and CPU legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,245 @@
+/*
+ * lbm.h — C ABI of the GB300 TRT-LBM-VP library (libpaper_1901_08766_gb300.so).
+ *
+ * The library advances 2D D2Q9 flows past obstacles with the coupled two-relaxation-
+ * time lattice Boltzmann / volume-penalization method of Cui, Wang, Yao, Liu and Yu
+ * (arXiv:1901.08766). One time step is one fused CUDA sweep per domain: pull-stream
+ * the populations (Eq. streaming), form rho and u* (Eq. rho, Eq. rho*velocity-star),
+ * penalize solid nodes (Eq. d-V, Eq. force-density, Eq. velocity-r), and collide with
+ * the TRT operator plus the split Guo forcing term (Eq. TRT-collision, Eq.
+ * collision-modified). The force on each body (Sec. 3, drag and lift sums) is
+ * reduced in FP64 every step into a device ring.
+ *
+ * Conventions for every call:
+ *  - Every function returns lbm_status; nothing aborts, throws or traps across the
+ *    ABI. lbm_last_error() gives a thread-local description of the last failure.
+ *  - Lattice units: dx = dy = dt = 1, c_s^2 = 1/3. Node (i, j) sits at (i, j),
+ *    i in [0, nx) along the flow, j in [0, ny) upward.
+ *  - Populations are ordered alpha = 0..8 as in Eq. (D2Q9): rest, (1,0), (0,1),
+ *    (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
+ *  - The library owns all device memory it allocates (populations, mask, force
+ *    ring); it allocates through the caller's lbm_alloc_fn (e.g. PyTorch's caching
+ *    allocator), or through cudaMallocAsync when none is given. The caller owns every
+ *    host buffer and every pointer it passes in; inputs are copied at the call.
+ *  - Work is enqueued on the cudaStream_t given at creation and is asynchronous,
+ *    except the calls documented as synchronising (they return host results).
+ *  - A domain or batch is used from one host thread at a time.
+ */
+#ifndef PAPER_1901_08766_GB300_LBM_H
+#define PAPER_1901_08766_GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* invalid argument or parameter combination */
+  LBM_ENOMEM = 2,    /* device or host allocation failed */
+  LBM_ECUDA = 3,     /* a CUDA runtime call failed (text in lbm_last_error) */
+  LBM_EUNSTABLE = 4, /* a domain diverged: rho <= 0.01, rho >= 100 or not finite (sticky) */
+  LBM_ETIMEOUT = 5,  /* reserved: a bounded wait ran out */
+  LBM_EBUSY = 6,     /* no free slot / over the memory budget / force ring full */
+  LBM_ENOTFOUND = 7  /* unknown slot */
+} lbm_status;
+
+/* Population storage. Collision and penalization run in FP64 for LBM_F64 and in FP32
+ * otherwise. LBM_F16S / LBM_BF16S store f_alpha - w_alpha rho0 rounded to nearest
+ * even (shifted by the rest weights, so that storage keeps the small deviations). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
+
+/* Domain-edge rules. x edges: west PERIODIC or INLET_EQ (ghost populations at
+ * f^eq(rho0, u_in)); east PERIODIC or OUTFLOW_ZG (zero gradient: the missing
+ * populations are read from the last column). y edges: PERIODIC or FREE_SLIP
+ * (specular reflection, walls half a cell outside the first and last rows). Both
+ * edges of an axis are periodic or neither is. The x rule is applied first. */
+typedef enum { LBM_PERIODIC = 0, LBM_INLET_EQ = 1, LBM_OUTFLOW_ZG = 2, LBM_FREE_SLIP = 3 } lbm_edge;
+
+/* Rigid body k (1-based id in the mask): obstacle velocity
+ * U_O(x) = (vx, vy) + omega * z x (x - (cx, cy))  (Eq. boundary-condition, Sec. 2.2).
+ * ref_length (D or chord) is carried for force coefficients only. */
+typedef struct {
+  double cx, cy, vx, vy, omega, ref_length;
+} lbm_body;
+
+typedef enum {
+  LBM_SHAPE_CIRCLE = 0,          /* chi = 1 where |x - c|^2 <  r^2 */
+  LBM_SHAPE_ANNULUS_OUTSIDE = 1, /* chi = 1 where |x - c|^2 >  r^2 (Couette outer wall) */
+  LBM_SHAPE_NACA4 = 2            /* NACA 00tt, quarter chord at c, nose-up aoa > 0 */
+} lbm_shape_kind;
+
+/* One obstacle shape of the mask function chi (Eq. mask function); tested at node
+ * positions in FP64. body is the id written where chi = 1 (1..255); later shapes
+ * overwrite earlier ones. NACA half thickness: 5 t c (0.2969 sqrt(x) - 0.1260 x -
+ * 0.3516 x^2 + 0.2843 x^3 - 0.1015 x^4), x = x'/c, inside when 0 <= x' <= c and
+ * |y'| <= y_t. */
+typedef struct {
+  int32_t kind, body;
+  double cx, cy, radius;
+  double chord, thickness, aoa_rad;
+} lbm_shape;
+
+typedef struct {
+  const lbm_shape *shapes; /* host array */
+  int32_t nshapes;
+} lbm_geometry;
+
+/* Problem parameters (Sec. 2: grid, nu or tau, Lambda, eta, U_in, initial state). */
+typedef struct {
+  int32_t nx, ny;         /* grid size, each >= 3 */
+  double nu;              /* > 0: tau_plus = nu / c_s^2 + 1/2; else tau_plus is used */
+  double tau_plus;        /* symmetric relaxation time tau_s, > 1/2 */
+  double magic_lambda;    /* Lambda = (tau_s - 1/2)(tau_a - 1/2) > 0 */
+  double eta;             /* penalization parameter, > 0 */
+  double rho0;            /* reference density (> 0) */
+  double u_in_x, u_in_y;  /* inlet velocity of an INLET_EQ west edge */
+  double u0_x, u0_y;      /* uniform initial velocity: g = f^eq(rho0, u0) everywhere */
+  int32_t west, east, south, north; /* lbm_edge */
+  int32_t storage;        /* lbm_storage */
+  int32_t force_every;    /* record body forces every k-th step (0: never) */
+  int32_t force_capacity; /* force-ring entries kept on the device (0: 8192) */
+} lbm_params;
+
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+
+typedef struct lbm_domain lbm_domain;
+typedef struct lbm_batch lbm_batch;
+
+/* Fill p with defaults: 64x64, nu = 0.1, Lambda = 3/16, eta = 1e-4, rho0 = 1, periodic,
+ * FP32 storage, forces every step, 8192-entry ring. */
+LBM_API void lbm_params_default(lbm_params *p);
+
+LBM_API const char *lbm_status_string(lbm_status s);
+LBM_API const char *lbm_last_error(void);
+
+/* Device bytes one domain with these parameters occupies (populations x2, mask,
+ * solid-node list bound, force ring). Used for admission by memory budget. */
+LBM_API size_t lbm_domain_bytes(const lbm_params *p, int32_t nbodies);
+
+/* ---- single domain ---------------------------------------------------------------- */
+
+/* Create a domain on the current CUDA device.
+ *  body_mask_host: nx*ny bytes, row-major [ny][nx], 0 = fluid, k = body k; or NULL to
+ *                  rasterise `geom` on the device (Eq. mask function).
+ *  bodies:         host array of nbodies rigid bodies (nbodies <= 255; every mask id
+ *                  must be <= nbodies).
+ *  cuda_stream:    cudaStream_t all work is ordered on (NULL: legacy default stream).
+ *  alloc/free/ctx: device allocator (both NULL: cudaMallocAsync/cudaFreeAsync).
+ * Initial state: g = f^eq(rho0, u0) at every node (step (1) of the algorithm).
+ * Synchronises once (the solid-node count sizes the force reducer's list). */
+LBM_API lbm_status lbm_domain_create(const lbm_params *p, const uint8_t *body_mask_host,
+                             const lbm_geometry *geom, const lbm_body *bodies,
+                             int32_t nbodies, void *cuda_stream, lbm_alloc_fn alloc,
+                             lbm_free_fn free_fn, void *alloc_ctx, lbm_domain **out);
+
+/* Advance nsteps time steps (steps (2)-(6), repeated). Asynchronous: divergence is
+ * reported by the next synchronising call (lbm_forces, lbm_moments). Returns
+ * LBM_EBUSY, doing nothing, if the undrained force entries would exceed the ring. */
+LBM_API lbm_status lbm_step(lbm_domain *d, int64_t nsteps);
+
+/* Drain recorded body forces into host `out` as [entries][nbodies][2] doubles (force
+ * ON body k: -sum of F_VP over its nodes, Sec. 3 drag/lift sums with the sign read
+ * as the force on the body). Copies min(available, max_entries) oldest entries and
+ * sets *written. Synchronises the stream. Returns LBM_EUNSTABLE if diverged. */
+LBM_API lbm_status lbm_forces(lbm_domain *d, double *out, int64_t max_entries, int64_t *written);
+
+/* Macroscopic fields of the current state, [ny][nx] FP64 each: rho and u = u* + du of
+ * the streamed populations (Eq. rho, Eq. velocity-r). Host or device pointers; any
+ * may be NULL. Synchronises the stream. */
+LBM_API lbm_status lbm_moments(lbm_domain *d, double *rho, double *ux, double *uy);
+
+/* Raw current populations in the storage type, [9][ny][nx] (element size 8, 4, 2, 2
+ * for F64, F32, F16S, BF16S; F16S/BF16S hold f - w rho0). bytes must equal
+ * 9*nx*ny*element size. Host or device pointers. Synchronise the stream. */
+LBM_API lbm_status lbm_get_populations(lbm_domain *d, void *out, size_t bytes);
+LBM_API lbm_status lbm_set_populations(lbm_domain *d, const void *in, size_t bytes);
+
+/* The body-id mask chi of Eq. (mask function) as used by the sweep, [ny][nx] bytes,
+ * 0 = fluid, k = body k. Host or device pointer. Synchronises the stream. */
+LBM_API lbm_status lbm_get_mask(lbm_domain *d, uint8_t *out);
+
+/* Steps done so far. */
+LBM_API lbm_status lbm_steps_done(lbm_domain *d, int64_t *steps);
+
+LBM_API lbm_status lbm_domain_destroy(lbm_domain *d);
+
+/* ---- batches of uneven domains (continuous batching) ----------------------------------- */
+
+/* A batch advances many domains of one storage type together: each time step is one
+ * persistent launch over a tile work list covering every resident domain, plus one
+ * force-reduction launch; steps are replayed from captured CUDA graphs.
+ *  max_domains:      slot count (1..4096).
+ *  hbm_budget_bytes: admission limit on the sum of lbm_domain_bytes (0: no limit).
+ *  graph_steps:      steps per captured graph (0: no graphs, one launch per kernel). */
+LBM_API lbm_status lbm_batch_create(int32_t max_domains, size_t hbm_budget_bytes, int32_t storage,
+                            int32_t graph_steps, void *cuda_stream, lbm_alloc_fn alloc,
+                            lbm_free_fn free_fn, void *alloc_ctx, lbm_batch **out);
+
+/* Admit one domain (p->storage must equal the batch's) that will run `nsteps` steps.
+ * Mask from body_mask_host or rasterised from geom as in lbm_domain_create. Returns
+ * LBM_EBUSY (nothing admitted) if no slot is free or the budget would be exceeded.
+ * Synchronises once. */
+LBM_API lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint8_t *body_mask_host,
+                           const lbm_geometry *geom, const lbm_body *bodies, int32_t nbodies,
+                           int64_t nsteps, int32_t *slot);
+
+/* Advance every resident, unfinished domain by up to max_steps steps; a domain stops
+ * at its own nsteps. *steps_run = steps actually run (<= max_steps). Asynchronous.
+ * Returns LBM_EBUSY (nothing run) if a domain's force ring cannot hold the entries. */
+LBM_API lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps_run);
+
+/* Drain a slot's recorded forces (as lbm_forces); *done = 1 once the slot has run all
+ * its steps and its forces are drained. Synchronises the stream. */
+LBM_API lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_entries,
+                          int64_t *written, int32_t *done);
+
+/* Per-slot access, as the single-domain calls of the same name. Synchronise. */
+LBM_API lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, double *ux, double *uy);
+LBM_API lbm_status lbm_batch_get_populations(lbm_batch *b, int32_t slot, void *out, size_t bytes);
+LBM_API lbm_status lbm_batch_set_populations(lbm_batch *b, int32_t slot, const void *in, size_t bytes);
+LBM_API lbm_status lbm_batch_steps_done(lbm_batch *b, int32_t slot, int64_t *steps);
+LBM_API lbm_status lbm_batch_get_mask(lbm_batch *b, int32_t slot, uint8_t *out);
+
+/* Advance every resident, unfinished domain by up to `steps` real time steps launched
+ * one kernel at a time (no graphs), bracketing each force and sweep launch with CUDA
+ * events on the batch stream. Outputs the mean duration per launch in microseconds
+ * (any may be NULL) and the steps run. Synchronises the stream. */
+LBM_API lbm_status lbm_batch_profile(lbm_batch *b, int32_t steps, double *sweep_us,
+                                     double *force_us, int64_t *steps_run);
+
+/* Free a slot and its device memory. */
+LBM_API lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot);
+
+/* Time each sweep tile shape (cells per thread, warps per block, rows per warp) on the
+ * resident domains for `reps` launches each, keep the fastest and rebuild the work
+ * list and graphs. The timing launches write only the spare lattice, so the state is
+ * untouched. *best_us receives the best time per sweep launch (may be NULL). */
+LBM_API lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us);
+
+/* Set the sweep tile shape explicitly: vec = cells per thread (F64 1|2, F32 2|4,
+ * F16S/BF16S 4|8), warps = warps per block (1..16), rows = rows per warp (1..16). */
+LBM_API lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows);
+LBM_API lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows);
+
+/* Resident slots and cells, and kernel launches issued since creation (sweeps, force
+ * reductions, graph replays count each captured kernel). Any output may be NULL. */
+LBM_API lbm_status lbm_batch_info(lbm_batch *b, int32_t *resident, int64_t *cells,
+                          int64_t *kernel_launches, size_t *bytes_in_use);
+
+LBM_API lbm_status lbm_batch_destroy(lbm_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_1901_08766_GB300_LBM_H */

@@ -1,0 +1,268 @@
+"""GB300-native TRT-LBM-VP (arXiv:1901.08766): flows past obstacles with the coupled
+two-relaxation-time lattice Boltzmann / volume-penalization method.
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in include/lbm.h);
+this package marshals arguments to it and provides host-side helpers (force
+coefficients and Strouhal number, the request server). PyTorch supplies device memory
+and the CUDA stream.
+
+    import paper_1901_08766_gb300 as lbm
+    dom = lbm.Domain(spec, storage="f16s")   # spec: see the synth module's description
+    dom.step(1000)
+    forces = dom.forces()                    # [steps, nbodies, 2], force on each body
+    rho, ux, uy = dom.moments()
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+from ._native import (ELEM_SIZE, LBM_EBUSY, LBM_EUNSTABLE, LbmError, STORAGE, STORAGE_DTYPE,
+                      check, load)
+from ._compile import build
+
+__all__ = ["Domain", "Batch", "load", "build", "LbmError", "STORAGE", "domain_bytes"]
+
+
+def _mask_arg(mask):
+    if mask is None:
+        return None, None
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    return m, m.ctypes.data_as(C.c_void_p)
+
+
+def domain_bytes(spec, storage="f32", force_every=1, force_capacity=8192) -> int:
+    L = load()
+    p = _native.params_from_spec(spec, storage, force_every, force_capacity)
+    return int(L.lbm_domain_bytes(C.byref(p), len(spec["bodies"])))
+
+
+class Domain:
+    """One simulation domain on the current CUDA device (lbm_domain_* calls)."""
+
+    def __init__(self, spec, storage="f32", force_every=1, force_capacity=8192, mask=None,
+                 stream=None, allocator="torch"):
+        import torch
+        L = load()
+        self.spec, self.storage = spec, storage
+        self.nx, self.ny = spec["nx"], spec["ny"]
+        self.nbodies = len(spec["bodies"])
+        self._params = _native.params_from_spec(spec, storage, force_every, force_capacity)
+        self._bodies, nb = _native.bodies_from_spec(spec)
+        self._geom, self._shapes = _native.geometry_from_spec(spec)
+        m, mp = _mask_arg(mask)
+        self._alloc = _native.TorchAllocator() if allocator == "torch" else None
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        check(L.lbm_domain_create(C.byref(self._params), mp, C.byref(self._geom), self._bodies,
+                                  nb, C.c_void_p(self._stream.cuda_stream),
+                                  self._alloc.c_alloc if self._alloc else _native.ALLOC_FN(),
+                                  self._alloc.c_free if self._alloc else _native.FREE_FN(),
+                                  None, C.byref(h)), "lbm_domain_create")
+        self._h = h
+
+    def _handle(self):
+        if self._h is None:
+            raise RuntimeError("domain destroyed")
+        return self._h
+
+    def step(self, n: int):
+        check(load().lbm_step(self._handle(), int(n)), "lbm_step")
+
+    def run(self, n: int, chunk: int = 4096):
+        """Advance n steps, draining the force ring between chunks; returns the forces."""
+        out = []
+        left = int(n)
+        while left > 0:
+            k = min(chunk, left)
+            self.step(k)
+            out.append(self.forces())
+            left -= k
+        if not out:
+            return np.zeros((0, self.nbodies, 2))
+        return np.concatenate(out, axis=0)
+
+    def forces(self, max_entries: int | None = None) -> np.ndarray:
+        L = load()
+        cap = self._params.force_capacity if max_entries is None else int(max_entries)
+        buf = np.zeros((cap, max(self.nbodies, 1), 2))
+        w = C.c_int64()
+        check(L.lbm_forces(self._handle(), buf.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                           C.byref(w)), "lbm_forces")
+        return buf[: w.value, : self.nbodies].copy()
+
+    def moments(self):
+        rho, ux, uy = (np.zeros((self.ny, self.nx)) for _ in range(3))
+        check(load().lbm_moments(self._handle(), rho.ctypes.data_as(C.c_void_p),
+                                 ux.ctypes.data_as(C.c_void_p), uy.ctypes.data_as(C.c_void_p)),
+              "lbm_moments")
+        return rho, ux, uy
+
+    def get_populations(self) -> np.ndarray:
+        out = np.zeros((9, self.ny, self.nx), dtype=STORAGE_DTYPE[self.storage])
+        check(load().lbm_get_populations(self._handle(), out.ctypes.data_as(C.c_void_p),
+                                         out.nbytes), "lbm_get_populations")
+        return out
+
+    def set_populations(self, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, dtype=STORAGE_DTYPE[self.storage])
+        if a.shape != (9, self.ny, self.nx):
+            raise ValueError(f"populations must have shape (9, {self.ny}, {self.nx})")
+        check(load().lbm_set_populations(self._handle(), a.ctypes.data_as(C.c_void_p), a.nbytes),
+              "lbm_set_populations")
+
+    def steps_done(self) -> int:
+        v = C.c_int64()
+        check(load().lbm_steps_done(self._handle(), C.byref(v)), "lbm_steps_done")
+        return v.value
+
+    def mask(self) -> np.ndarray:
+        out = np.zeros((self.ny, self.nx), dtype=np.uint8)
+        check(load().lbm_get_mask(self._handle(), out.ctypes.data_as(C.c_void_p)), "lbm_get_mask")
+        return out
+
+    def close(self):
+        if self._h is not None:
+            load().lbm_domain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many uneven domains of one storage type advanced together (lbm_batch_* calls)."""
+
+    def __init__(self, storage="f16s", max_domains=64, hbm_budget=0, graph_steps=32,
+                 stream=None, allocator="torch"):
+        import torch
+        L = load()
+        self.storage = storage
+        self._alloc = _native.TorchAllocator() if allocator == "torch" else None
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        check(L.lbm_batch_create(max_domains, int(hbm_budget), STORAGE[storage], graph_steps,
+                                 C.c_void_p(self._stream.cuda_stream),
+                                 self._alloc.c_alloc if self._alloc else _native.ALLOC_FN(),
+                                 self._alloc.c_free if self._alloc else _native.FREE_FN(),
+                                 None, C.byref(h)), "lbm_batch_create")
+        self._h = h
+        self._meta = {}
+
+    def admit(self, spec, nsteps=None, force_every=1, force_capacity=8192, mask=None) -> int:
+        """Admit a domain; returns its slot. Raises LbmError(LBM_EBUSY) when full."""
+        p = _native.params_from_spec(spec, self.storage, force_every, force_capacity)
+        bodies, nb = _native.bodies_from_spec(spec)
+        geom, shapes = _native.geometry_from_spec(spec)
+        m, mp = _mask_arg(mask)
+        slot = C.c_int32()
+        n = spec["steps"] if nsteps is None else int(nsteps)
+        check(load().lbm_batch_admit(self._h, C.byref(p), mp, C.byref(geom), bodies, nb, n,
+                                     C.byref(slot)), "lbm_batch_admit")
+        self._meta[slot.value] = (spec["nx"], spec["ny"], len(spec["bodies"]), force_capacity)
+        return slot.value
+
+    def try_admit(self, spec, **kw):
+        try:
+            return self.admit(spec, **kw)
+        except LbmError as e:
+            if e.status == LBM_EBUSY:
+                return None
+            raise
+
+    def run(self, max_steps: int) -> int:
+        n = C.c_int64()
+        check(load().lbm_batch_run(self._h, int(max_steps), C.byref(n)), "lbm_batch_run")
+        return n.value
+
+    def poll(self, slot: int, raise_unstable=True):
+        """Drain a slot's forces: returns (forces [n, nbodies, 2], done)."""
+        nx, ny, nb, cap = self._meta[slot]
+        buf = np.zeros((cap, max(nb, 1), 2))
+        w, d = C.c_int64(), C.c_int32()
+        st = load().lbm_batch_poll(self._h, slot, buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                   cap, C.byref(w), C.byref(d))
+        if st != 0 and (raise_unstable or st != LBM_EUNSTABLE):
+            check(st, "lbm_batch_poll")
+        return buf[: w.value, :nb].copy(), bool(d.value)
+
+    def moments(self, slot: int):
+        nx, ny, nb, cap = self._meta[slot]
+        rho, ux, uy = (np.zeros((ny, nx)) for _ in range(3))
+        check(load().lbm_batch_moments(self._h, slot, rho.ctypes.data_as(C.c_void_p),
+                                       ux.ctypes.data_as(C.c_void_p),
+                                       uy.ctypes.data_as(C.c_void_p)), "lbm_batch_moments")
+        return rho, ux, uy
+
+    def get_populations(self, slot: int) -> np.ndarray:
+        nx, ny, nb, cap = self._meta[slot]
+        out = np.zeros((9, ny, nx), dtype=STORAGE_DTYPE[self.storage])
+        check(load().lbm_batch_get_populations(self._h, slot, out.ctypes.data_as(C.c_void_p),
+                                               out.nbytes), "lbm_batch_get_populations")
+        return out
+
+    def set_populations(self, slot: int, arr):
+        a = np.ascontiguousarray(arr, dtype=STORAGE_DTYPE[self.storage])
+        check(load().lbm_batch_set_populations(self._h, slot, a.ctypes.data_as(C.c_void_p),
+                                               a.nbytes), "lbm_batch_set_populations")
+
+    def steps_done(self, slot: int) -> int:
+        v = C.c_int64()
+        check(load().lbm_batch_steps_done(self._h, slot, C.byref(v)), "lbm_batch_steps_done")
+        return v.value
+
+    def mask(self, slot: int) -> np.ndarray:
+        nx, ny, nb, cap = self._meta[slot]
+        out = np.zeros((ny, nx), dtype=np.uint8)
+        check(load().lbm_batch_get_mask(self._h, slot, out.ctypes.data_as(C.c_void_p)),
+              "lbm_batch_get_mask")
+        return out
+
+    def evict(self, slot: int):
+        check(load().lbm_batch_evict(self._h, slot), "lbm_batch_evict")
+        self._meta.pop(slot, None)
+
+    def profile(self, steps: int):
+        """Run `steps` real steps one kernel at a time; returns (sweep_us, force_us,
+        steps_run), the mean event-timed duration of each launch."""
+        a, b, n = C.c_double(), C.c_double(), C.c_int64()
+        check(load().lbm_batch_profile(self._h, int(steps), C.byref(a), C.byref(b), C.byref(n)),
+              "lbm_batch_profile")
+        return a.value, b.value, n.value
+
+    def autotune(self, reps: int = 10) -> float:
+        us = C.c_double()
+        check(load().lbm_batch_autotune(self._h, reps, C.byref(us)), "lbm_batch_autotune")
+        return us.value
+
+    def set_tile(self, vec: int, warps: int, rows: int):
+        check(load().lbm_batch_set_tile(self._h, vec, warps, rows), "lbm_batch_set_tile")
+
+    def get_tile(self):
+        v, w, r = C.c_int32(), C.c_int32(), C.c_int32()
+        check(load().lbm_batch_get_tile(self._h, C.byref(v), C.byref(w), C.byref(r)),
+              "lbm_batch_get_tile")
+        return v.value, w.value, r.value
+
+    def info(self):
+        r, c, k, b = C.c_int32(), C.c_int64(), C.c_int64(), C.c_size_t()
+        check(load().lbm_batch_info(self._h, C.byref(r), C.byref(c), C.byref(k), C.byref(b)),
+              "lbm_batch_info")
+        return {"resident": r.value, "cells": c.value, "kernel_launches": k.value,
+                "bytes_in_use": b.value}
+
+    def close(self):
+        if self._h is not None:
+            load().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

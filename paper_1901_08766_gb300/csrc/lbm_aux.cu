@@ -1,0 +1,295 @@
+// Auxiliary kernels of the TRT-LBM-VP library: geometry -> mask rasteriser (Eq. mask
+// function), initial state (step (1)), solid-node lists, the FP64 body-force reducer
+// (Sec. 3 drag and lift sums) and the moments export.
+#include "lbm_cell.cuh"
+
+namespace lbm {
+
+// ---- rasteriser ------------------------------------------------------------------------
+// Node (i, j) is tested at (i, j) in FP64 with explicitly rounded operations (no
+// contraction), so the predicate takes the same decision as a plain IEEE evaluation of
+// the same expressions on the host.
+
+__device__ __forceinline__ double naca_half_thickness(double xc, double t, double chord) {
+  const double s = __dsqrt_rn(xc);
+  double p = __dadd_rn(__dmul_rn(-0.1015, xc), 0.2843);
+  p = __dsub_rn(__dmul_rn(p, xc), 0.3516);
+  p = __dsub_rn(__dmul_rn(p, xc), 0.1260);
+  p = __dmul_rn(p, xc);
+  return __dmul_rn(__dmul_rn(__dmul_rn(5.0, t), chord), __dadd_rn(__dmul_rn(0.2969, s), p));
+}
+
+__device__ __forceinline__ bool inside(const ShapeDev &s, double x, double y) {
+  if (s.kind == LBM_SHAPE_CIRCLE || s.kind == LBM_SHAPE_ANNULUS_OUTSIDE) {
+    const double dx = __dsub_rn(x, s.cx), dy = __dsub_rn(y, s.cy);
+    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    const double r2 = __dmul_rn(s.radius, s.radius);
+    return s.kind == LBM_SHAPE_CIRCLE ? (d2 < r2) : (d2 > r2);
+  }
+  if (s.kind == LBM_SHAPE_NACA4) {
+    const double qc = __dmul_rn(0.25, s.chord);
+    const double lex = __dsub_rn(s.cx, __dmul_rn(qc, s.ca));
+    const double ley = __dadd_rn(s.cy, __dmul_rn(qc, s.sa));
+    const double dx = __dsub_rn(x, lex), dy = __dsub_rn(y, ley);
+    const double xp = __dsub_rn(__dmul_rn(dx, s.ca), __dmul_rn(dy, s.sa));
+    const double yp = __dadd_rn(__dmul_rn(dx, s.sa), __dmul_rn(dy, s.ca));
+    if (!(xp >= 0.0 && xp <= s.chord)) return false;
+    const double yt = naca_half_thickness(__ddiv_rn(xp, s.chord), s.thickness, s.chord);
+    return fabs(yp) <= yt;
+  }
+  return false;
+}
+
+__global__ void rasterize_kernel(uint8_t *mask, int nx, int ny, int pitch,
+                                 const ShapeDev *shapes, int nshapes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= pitch || j >= ny) return;
+  uint8_t b = 0;
+  if (i < nx) {
+    for (int k = 0; k < nshapes; ++k)
+      if (inside(shapes[k], double(i), double(j))) b = static_cast<uint8_t>(shapes[k].body);
+  }
+  mask[static_cast<size_t>(j) * pitch + i] = b;
+}
+
+cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
+                             const ShapeDev *shapes, int nshapes) {
+  dim3 grid((pitch + 255) / 256, ny);
+  rasterize_kernel<<<grid, 256, 0, st>>>(mask, nx, ny, pitch, shapes, nshapes);
+  return cudaGetLastError();
+}
+
+// ---- initial state: g = f^eq(rho0, u0) at every node, padding zero ----------------------
+
+template <int S>
+__global__ void init_kernel(typename Codec<S>::E *lat, int nx, int ny, int pitch, double rho0,
+                            double ux, double uy) {
+  using Cd = Codec<S>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int a = blockIdx.z;
+  if (i >= pitch || j >= ny) return;
+  const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  const double eu = ex_of(a) * ux + ey_of(a) * uy;
+  const double usq = ux * ux + uy * uy;
+  // Eq. (feq) with c_s^2 = 1/3; shifted storage keeps f^eq - w rho0
+  const double dev = rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+  double val = Cd::kShift ? dev : rho0 * w + dev;
+  if (i >= nx) val = 0.0;
+  lat[(static_cast<size_t>(a) * ny + j) * pitch + i] = Cd::enc(typename Cd::T(val));
+}
+
+cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,
+                        double rho0, double ux, double uy) {
+  dim3 grid((pitch + 255) / 256, ny, kQ);
+  switch (storage) {
+    case LBM_F64: init_kernel<LBM_F64><<<grid, 256, 0, st>>>(static_cast<double *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_F32: init_kernel<LBM_F32><<<grid, 256, 0, st>>>(static_cast<float *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_F16S: init_kernel<LBM_F16S><<<grid, 256, 0, st>>>(static_cast<uint16_t *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_BF16S: init_kernel<LBM_BF16S><<<grid, 256, 0, st>>>(static_cast<uint16_t *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---- solid-node lists -----------------------------------------------------------------
+// counts[k] = number of nodes with body id k (k = 0 counts fluid); *bad_id > 0 if an id
+// exceeds nbodies.
+
+__global__ void count_bodies_kernel(const uint8_t *mask, int nx, int ny, int pitch, int nbodies,
+                                    int32_t *counts, int32_t *bad_id) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= nx || j >= ny) return;
+  const int b = mask[static_cast<size_t>(j) * pitch + i];
+  if (b == 0) return;
+  if (b > nbodies) {
+    atomicMax(bad_id, b);
+    return;
+  }
+  atomicAdd(&counts[b], 1);
+}
+
+cudaError_t launch_count_bodies(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
+                                int nbodies, int32_t *counts, int32_t *bad_id) {
+  dim3 grid((nx + 255) / 256, ny);
+  count_bodies_kernel<<<grid, 256, 0, st>>>(mask, nx, ny, pitch, nbodies, counts, bad_id);
+  return cudaGetLastError();
+}
+
+// One block per body scans the mask in row-major order and appends the body's nodes
+// at offsets[k-1] + rank, the rank from a block-wide prefix count: the list order is
+// row-major and does not depend on the launch shape.
+__global__ void build_solid_kernel(const uint8_t *mask, int nx, int ny, int pitch,
+                                   const int32_t *offsets, int32_t *solid) {
+  const int body = blockIdx.x + 1;
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t base;
+  if (threadIdx.x == 0) base = offsets[body - 1];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long cells = static_cast<long long>(nx) * ny;
+  for (long long c0 = 0; c0 < cells; c0 += blockDim.x) {
+    const long long c = c0 + threadIdx.x;
+    int i = 0, j = 0;
+    bool hit = false;
+    if (c < cells) {
+      j = static_cast<int>(c / nx);
+      i = static_cast<int>(c - static_cast<long long>(j) * nx);
+      hit = mask[static_cast<size_t>(j) * pitch + i] == body;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    const int in_warp = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += warp_tot[w];
+      total += warp_tot[w];
+    }
+    if (hit) solid[base + before + in_warp] = j * pitch + i;
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_build_solid(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
+                               int nbodies, const int32_t *offsets, int32_t *solid) {
+  if (nbodies <= 0) return cudaSuccess;
+  build_solid_kernel<<<nbodies, 1024, 0, st>>>(mask, nx, ny, pitch, offsets, solid);
+  return cudaGetLastError();
+}
+
+// ---- body forces -------------------------------------------------------------------------
+// One block per (slot, body) item: each thread accumulates -F_VP of a strided subset of
+// the body's nodes in FP64 (same pull and node arithmetic as the sweep), then a fixed
+// shuffle + shared-memory tree: the sum order depends only on the node list.
+
+constexpr int kForceThreads = 256;
+
+template <int S>
+__global__ void __launch_bounds__(kForceThreads)
+forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
+              int s) {
+  using Cd = Codec<S>;
+  using T = typename Cd::T;
+  const int nitems = ctr->nforce;
+  const long long run_base = ctr->run_base;
+  __shared__ double red[2][kForceThreads / 32];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ForceItem item = items[it];
+    const DomDev &D = doms[item.dom];
+    const DomDyn dy = dyn[item.dom];
+    const long long n = dy.step0 + run_base + s;  // this launch computes step n + 1
+    if (n >= dy.step_end || D.force_every <= 0) continue;
+    if ((n + 1) % D.force_every != 0) continue;
+    const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
+    const void *src = D.lat[par];
+    const CellConst<T> C = make_const<T>(D);
+    const int beg = D.solid_off[item.body - 1], end = D.solid_off[item.body];
+    double fx = 0.0, fy = 0.0;
+    for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+      const int lin = D.solid[q];
+      const int j = lin / D.pitch, i = lin - j * D.pitch;
+      T x[kQ];
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) x[a] = pull_scalar<S>(D, src, a, i, j);
+      T uox, uoy;
+      body_velocity<T>(D, item.body, i, j, uox, uoy);
+      const NodeMacro<T> m = node_macro<T, Cd::kShift, true>(x, C, true, uox, uoy);
+      fx -= double(m.fx);
+      fy -= double(m.fy);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      fx += __shfl_down_sync(0xffffffffu, fx, off);
+      fy += __shfl_down_sync(0xffffffffu, fy, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][warp] = fx;
+      red[1][warp] = fy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sx = 0.0, sy = 0.0;
+      for (int w = 0; w < kForceThreads / 32; ++w) {
+        sx += red[0][w];
+        sy += red[1][w];
+      }
+      const long long e = (n + 1) / D.force_every - 1;  // entry index of step n + 1
+      double *slot = D.ring + (static_cast<size_t>(e % D.force_cap) * D.nbodies + (item.body - 1)) * 2;
+      slot[0] = sx;
+      slot[1] = sy;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *doms,
+                          const DomDyn *dyn, const ForceItem *items, const Counters *ctr, int s) {
+  switch (storage) {
+    case LBM_F64: forces_kernel<LBM_F64><<<grid, kForceThreads, 0, st>>>(doms, dyn, items, ctr, s); break;
+    case LBM_F32: forces_kernel<LBM_F32><<<grid, kForceThreads, 0, st>>>(doms, dyn, items, ctr, s); break;
+    case LBM_F16S: forces_kernel<LBM_F16S><<<grid, kForceThreads, 0, st>>>(doms, dyn, items, ctr, s); break;
+    case LBM_BF16S: forces_kernel<LBM_BF16S><<<grid, kForceThreads, 0, st>>>(doms, dyn, items, ctr, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Advance the device step counter of a run by k steps (last node of a captured graph).
+__global__ void advance_kernel(Counters *ctr, int k) { ctr->run_base += k; }
+
+cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k) {
+  advance_kernel<<<1, 1, 0, st>>>(ctr, k);
+  return cudaGetLastError();
+}
+
+// ---- moments export ------------------------------------------------------------------------
+
+template <int S>
+__global__ void moments_kernel(const DomDev *dom, int parity, double *rho, double *ux, double *uy) {
+  using Cd = Codec<S>;
+  using T = typename Cd::T;
+  const DomDev &D = *dom;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= D.nx || j >= D.ny) return;
+  const void *src = D.lat[parity];
+  const CellConst<T> C = make_const<T>(D);
+  T x[kQ];
+#pragma unroll
+  for (int a = 0; a < kQ; ++a) x[a] = pull_scalar<S>(D, src, a, i, j);
+  const int b = D.mask[static_cast<size_t>(j) * D.pitch + i];
+  T uox = T(0), uoy = T(0);
+  if (b) body_velocity<T>(D, b, i, j, uox, uoy);
+  const NodeMacro<T> m = node_macro<T, Cd::kShift, true>(x, C, b != 0, uox, uoy);
+  const size_t c = static_cast<size_t>(j) * D.nx + i;
+  if (rho) rho[c] = double(m.rho);
+  if (ux) ux[c] = double(m.ux);
+  if (uy) uy[c] = double(m.uy);
+}
+
+template <int S>
+cudaError_t launch_moments_t(cudaStream_t st, const DomDev *dom, int nx, int ny, int parity,
+                             double *rho, double *ux, double *uy) {
+  dim3 grid((nx + 127) / 128, ny);
+  moments_kernel<S><<<grid, 128, 0, st>>>(dom, parity, rho, ux, uy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_sized(int storage, cudaStream_t st, const DomDev *dom, int nx, int ny,
+                                 int parity, double *rho, double *ux, double *uy) {
+  switch (storage) {
+    case LBM_F64: return launch_moments_t<LBM_F64>(st, dom, nx, ny, parity, rho, ux, uy);
+    case LBM_F32: return launch_moments_t<LBM_F32>(st, dom, nx, ny, parity, rho, ux, uy);
+    case LBM_F16S: return launch_moments_t<LBM_F16S>(st, dom, nx, ny, parity, rho, ux, uy);
+    case LBM_BF16S: return launch_moments_t<LBM_BF16S>(st, dom, nx, ny, parity, rho, ux, uy);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lbm

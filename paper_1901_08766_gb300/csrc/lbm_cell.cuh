@@ -1,0 +1,243 @@
+// Device-side building blocks of the TRT-LBM-VP step: storage codecs, the per-node
+// update (moments, penalization, TRT collision with split Guo forcing) and the scalar
+// pull with the domain-edge rules. The translation units are compiled with
+// --fmad=false: every fused multiply-add below is written out with fma(), so each
+// instantiation of the update performs the same roundings and results do not depend
+// on the tile shape or on which kernel evaluates a node.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// D2Q9 velocity set, Eq. (D2Q9): rest, axes at (alpha-1) pi/2, diagonals at (2 alpha-9) pi/4.
+__device__ __constant__ static const int kEx[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ __constant__ static const int kEy[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// Reflection of a direction across a horizontal wall (e_y -> -e_y): free-slip edges.
+__host__ __device__ constexpr int reflect_y(int a) {
+  return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
+}
+__host__ __device__ constexpr int ex_of(int a) {
+  return (a == 1 || a == 5 || a == 8) ? 1 : (a == 3 || a == 6 || a == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey_of(int a) {
+  return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0;
+}
+
+// ---- storage codecs --------------------------------------------------------------------
+// F64 / F32 store f; F16S / BF16S store f - w_alpha rho0 (rounded to nearest even).
+
+template <int S> struct Codec;
+
+template <> struct Codec<LBM_F64> {
+  using E = double;
+  using T = double;
+  static constexpr bool kShift = false;
+  __device__ static T dec(E e) { return e; }
+  __device__ static E enc(T t) { return t; }
+};
+template <> struct Codec<LBM_F32> {
+  using E = float;
+  using T = float;
+  static constexpr bool kShift = false;
+  __device__ static T dec(E e) { return e; }
+  __device__ static E enc(T t) { return t; }
+};
+template <> struct Codec<LBM_F16S> {
+  using E = uint16_t;
+  using T = float;
+  static constexpr bool kShift = true;
+  __device__ static T dec(E e) { return __half2float(__ushort_as_half(e)); }
+  __device__ static E enc(T t) { return __half_as_ushort(__float2half_rn(t)); }
+  // two packed elements (low = first)
+  __device__ static float2 dec2(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+  }
+  __device__ static uint32_t enc2(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+  }
+};
+template <> struct Codec<LBM_BF16S> {
+  using E = uint16_t;
+  using T = float;
+  static constexpr bool kShift = true;
+  __device__ static T dec(E e) { return __uint_as_float(static_cast<uint32_t>(e) << 16); }
+  __device__ static E enc(T t) { return __bfloat16_as_ushort(__float2bfloat16_rn(t)); }
+  __device__ static float2 dec2(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+  __device__ static uint32_t enc2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+  }
+};
+
+// ---- per-domain constants in compute precision -----------------------------------------
+
+template <typename T> struct CellConst {
+  T omp, omm;        // omega+, omega-
+  T hp, hm;          // omega+/2, omega-/2
+  T kp, km;          // 1 - omega+/2, 1 - omega-/2
+  T one_m_omp;       // 1 - omega+
+  T inv_2eta1;       // 1 / (2 eta + 1)
+  T rho0;
+  T pw0, pw1, pw2;   // omega+ * w for the rest, axis and diagonal classes
+  T mw1, mw2;        // 3 omega- * w for the axis and diagonal classes
+  T kw0, kw1, kw2;   // (1 - omega+/2) * w per class (Guo symmetric part)
+  T qw1, qw2;        // 3 (1 - omega-/2) * w per class (Guo antisymmetric part)
+};
+
+template <typename T> __device__ __forceinline__ CellConst<T> make_const(const DomDev &d) {
+  CellConst<T> c;
+  const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
+  const double op = d.omega_p, om = d.omega_m;
+  c.omp = T(op);
+  c.omm = T(om);
+  c.hp = T(0.5 * op);
+  c.hm = T(0.5 * om);
+  c.kp = T(1.0 - 0.5 * op);
+  c.km = T(1.0 - 0.5 * om);
+  c.one_m_omp = T(1.0 - op);
+  c.inv_2eta1 = T(d.inv_2eta1);
+  c.rho0 = T(d.rho0);
+  c.pw0 = T(op * w0);
+  c.pw1 = T(op * w1);
+  c.pw2 = T(op * w2);
+  c.mw1 = T(3.0 * om * w1);
+  c.mw2 = T(3.0 * om * w2);
+  c.kw0 = T((1.0 - 0.5 * op) * w0);
+  c.kw1 = T((1.0 - 0.5 * op) * w1);
+  c.kw2 = T((1.0 - 0.5 * op) * w2);
+  c.qw1 = T(3.0 * (1.0 - 0.5 * om) * w1);
+  c.qw2 = T(3.0 * (1.0 - 0.5 * om) * w2);
+  return c;
+}
+
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_(double a) { return 1.0 / a; }
+
+// Macroscopic quantities of one node (steps (4)-(5) of the algorithm, Sec. 2.2).
+template <typename T> struct NodeMacro {
+  T d;       // sum of the stored values (rho - rho0 for shifted storage, rho otherwise)
+  T rho;     // Eq. (rho)
+  T ux, uy;  // corrected velocity u = u* + du, Eq. (velocity-r)
+  T fx, fy;  // F_VP, Eq. (force-density); zero in fluid nodes
+};
+
+// x[]: the nine pulled values in compute space. solid: chi = 1 at this node, with
+// obstacle velocity (uox, uoy).
+template <typename T, bool SHIFT, bool FORCE>
+__device__ __forceinline__ NodeMacro<T> node_macro(const T (&x)[kQ], const CellConst<T> &c,
+                                                   bool solid, T uox, T uoy) {
+  NodeMacro<T> m;
+  // Eq. (rho) and Eq. (rho*velocity-star), in a fixed pairwise order
+  m.d = (x[0] + (x[1] + x[3])) + ((x[2] + x[4]) + ((x[5] + x[7]) + (x[6] + x[8])));
+  m.rho = SHIFT ? c.rho0 + m.d : m.d;
+  const T jx = (x[1] - x[3]) + ((x[5] - x[7]) + (x[8] - x[6]));
+  const T jy = (x[2] - x[4]) + ((x[5] - x[7]) + (x[6] - x[8]));
+  const T inv = rcp_(m.rho);
+  m.ux = jx * inv;  // u*
+  m.uy = jy * inv;
+  m.fx = T(0);
+  m.fy = T(0);
+  if (FORCE && solid) {
+    // Eq. (d-V) with chi = 1, dt = 1: du = (U_O - u*) / (2 eta + 1);
+    // Eq. (force-density): F_VP = 2 rho (U_O - u*) / (2 eta + 1) = 2 rho du
+    const T dux = (uox - m.ux) * c.inv_2eta1;
+    const T duy = (uoy - m.uy) * c.inv_2eta1;
+    const T two_rho = m.rho + m.rho;
+    m.fx = two_rho * dux;
+    m.fy = two_rho * duy;
+    m.ux = m.ux + dux;  // Eq. (velocity-r)
+    m.uy = m.uy + duy;
+  }
+  return m;
+}
+
+// TRT collision with the split Guo term, Eq. (TRT-collision) and Eq. (collision-modified):
+//   g_a = f_a - w+ (f^s_a - f^eq,s_a) - w- (f^a_a - f^eq,a_a) + (1 - w+/2) F^s_a + (1 - w-/2) F^a_a
+// evaluated per opposite pair (a, -a), in place on x[]. For shifted storage every
+// symmetric quantity is taken relative to w_a rho0, which cancels in f^s - f^eq,s.
+template <typename T, bool SHIFT, bool FORCE>
+__device__ __forceinline__ void collide(T (&x)[kQ], const NodeMacro<T> &m, const CellConst<T> &c) {
+  const T base = SHIFT ? m.d : m.rho;
+  const T q = T(1.5) * fma_(m.uy, m.uy, m.ux * m.ux);  // 1.5 |u|^2
+  // per class: omega+ w rho, omega+ w base, 3 omega- w rho
+  const T a0 = c.pw0 * m.rho, b0 = c.pw0 * base;
+  const T a1 = c.pw1 * m.rho, b1 = c.pw1 * base;
+  const T a2 = c.pw2 * m.rho, b2 = c.pw2 * base;
+  const T m1 = c.mw1 * m.rho, m2 = c.mw2 * m.rho;
+  T uf = T(0);
+  if (FORCE) uf = fma_(m.uy, m.fy, m.ux * m.fx);
+  // rest population: g0 = f0 - w+ (f0 - w0 rho (1 - 1.5 u^2)) + (1 - w+/2)(-3 w0 u.F)
+  {
+    T g0 = fma_(c.one_m_omp, x[0], fma_(-a0, q, b0));
+    if (FORCE) g0 = fma_(T(-3) * c.kw0, uf, g0);
+    x[0] = g0;
+  }
+  // one opposite pair with direction e (eu = e.u, ef = e.F)
+  auto pair = [&](int ia, int ib, T eu, T ef, T a, T b, T mm, T kw, T qw) {
+    const T xs = x[ia] + x[ib];
+    const T xd = x[ia] - x[ib];
+    const T c1 = fma_(T(4.5) * eu, eu, -q);      // 4.5 (e.u)^2 - 1.5 u^2
+    const T eqs = fma_(a, c1, b);                // w+ * (f^eq,s - shift)
+    T S = fma_(-c.hp, xs, eqs);                  // -w+ (f^s - f^eq,s)
+    T A = fma_(-c.hm, xd, mm * eu);              // -w- (f^a - f^eq,a)
+    if (FORCE) {
+      S = fma_(kw, fma_(T(9) * eu, ef, T(-3) * uf), S);  // (1 - w+/2) F^s
+      A = fma_(qw, ef, A);                               // (1 - w-/2) F^a
+    }
+    x[ia] = (x[ia] + S) + A;
+    x[ib] = (x[ib] + S) - A;
+  };
+  pair(1, 3, m.ux, m.fx, a1, b1, m1, c.kw1, c.qw1);
+  pair(2, 4, m.uy, m.fy, a1, b1, m1, c.kw1, c.qw1);
+  pair(5, 7, m.ux + m.uy, m.fx + m.fy, a2, b2, m2, c.kw2, c.qw2);
+  pair(6, 8, m.uy - m.ux, m.fy - m.fx, a2, b2, m2, c.kw2, c.qw2);
+}
+
+// Obstacle velocity of body id b at node (i, j): V + omega z x (x - c).
+template <typename T>
+__device__ __forceinline__ void body_velocity(const DomDev &d, int b, int i, int j, T &uox,
+                                              T &uoy) {
+  const double *bd = d.bodies + 5 * (b - 1);
+  const double cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
+               om = __ldg(bd + 4);
+  uox = T(__dsub_rn(vx, __dmul_rn(om, __dsub_rn(double(j), cy))));
+  uoy = T(__dadd_rn(vy, __dmul_rn(om, __dsub_rn(double(i), cx))));
+}
+
+// Scalar pull of direction a at node (i, j) with the edge rules (Eq. streaming):
+// source (i - e_x, j - e_y); west inlet -> ghost, east outflow -> last column, x first;
+// then free-slip -> reflected direction in the clamped row; periodic edges wrap.
+template <int S>
+__device__ __forceinline__ typename Codec<S>::T pull_scalar(const DomDev &d, const void *lat,
+                                                           int a, int i, int j) {
+  using Cd = Codec<S>;
+  using E = typename Cd::E;
+  int sx = i - ex_of(a), sy = j - ey_of(a), src = a;
+  if (sx < 0) {
+    if (d.west == LBM_INLET_EQ) return typename Cd::T(d.ghost[a]);
+    sx += d.nx;
+  } else if (sx > d.nx - 1) {
+    sx = (d.east == LBM_OUTFLOW_ZG) ? d.nx - 1 : sx - d.nx;
+  }
+  if (sy < 0) {
+    if (d.south == LBM_FREE_SLIP) { sy = 0; src = reflect_y(a); }
+    else sy += d.ny;
+  } else if (sy > d.ny - 1) {
+    if (d.north == LBM_FREE_SLIP) { sy = d.ny - 1; src = reflect_y(a); }
+    else sy -= d.ny;
+  }
+  const E *p = static_cast<const E *>(lat);
+  return Cd::dec(p[(static_cast<size_t>(src) * d.ny + sy) * d.pitch + sx]);
+}
+
+}  // namespace lbm

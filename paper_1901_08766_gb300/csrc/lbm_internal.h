@@ -1,0 +1,111 @@
+// Internal types shared by the CUDA kernels and the host runtime of the TRT-LBM-VP
+// library. Not part of the public ABI (include/lbm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kQ = 9;
+constexpr int kPitchAlign = 64;  // row pitch in elements is a multiple of this
+constexpr int kMaxBodies = 255;
+
+// Per-domain static description, resident in device memory (one per batch slot).
+struct DomDev {
+  void *lat[2];            // lattice A/B: [9][ny][pitch] elements of the storage type
+  const uint8_t *mask;     // [ny][pitch] body id, 0 = fluid
+  const double *bodies;    // [nbodies][5]: cx, cy, vx, vy, omega
+  const int32_t *solid;    // solid nodes (j * pitch + i), grouped by body, row-major
+  const int32_t *solid_off;// [nbodies + 1] offsets into solid
+  double *ring;            // force ring [cap][nbodies][2]
+  int32_t *status;         // bit 0: unstable
+  int32_t nx, ny, pitch;
+  int32_t west, east, south, north;
+  int32_t nbodies, force_every, force_cap;
+  double omega_p, omega_m;  // 1/tau_s, 1/tau_a
+  double inv_2eta1;         // 1 / (2 eta + 1)
+  double rho0;
+  double ghost[kQ];         // inlet populations in compute space (shifted if storage is)
+};
+
+// Per-domain dynamic state, uploaded at the start of each batch run.
+struct DomDyn {
+  long long step0;     // steps done when the run started
+  long long step_end;  // the domain stops before this step count
+  int32_t parity;      // lattice holding g at step0
+  int32_t pad;
+};
+
+// One sweep tile: a warp-wide strip (32 * vec cells) by (warps * rows) rows.
+struct TileDev {
+  int32_t dom, x0, y0, pad;
+};
+
+// One force-reduction item: (slot, body id).
+struct ForceItem {
+  int32_t dom, body;
+};
+
+// Device-side counters of a batch.
+struct Counters {
+  int32_t ntiles;
+  int32_t nforce;
+  long long run_base;  // steps completed in the current run (advanced by the graphs)
+};
+
+struct SweepArgs {
+  const DomDev *doms;
+  const DomDyn *dyn;
+  const TileDev *tiles;
+  const Counters *ctr;
+  int32_t rows;  // rows per warp
+};
+
+struct ShapeDev {
+  int32_t kind, body;
+  double cx, cy, radius, chord, thickness, ca, sa;  // ca, sa = cos/sin(aoa) from the host
+};
+
+// Kernel launchers (one translation unit per storage type for the sweep).
+cudaError_t launch_sweep(int storage, int vec, int grid, int warps, cudaStream_t st,
+                         const SweepArgs &a, int s);
+int sweep_max_blocks_per_sm(int storage, int vec, int warps);
+bool sweep_vec_supported(int storage, int vec);
+
+cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *doms,
+                          const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
+                          int s);
+cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
+cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
+                             const ShapeDev *shapes, int nshapes);
+cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,
+                        double rho0, double ux, double uy);
+cudaError_t launch_count_bodies(cudaStream_t st, const uint8_t *mask, int nx, int ny,
+                                int pitch, int nbodies, int32_t *counts /* [nbodies+1] */,
+                                int32_t *bad_id);
+cudaError_t launch_build_solid(cudaStream_t st, const uint8_t *mask, int nx, int ny,
+                               int pitch, int nbodies, const int32_t *offsets,
+                               int32_t *solid);
+cudaError_t launch_moments_sized(int storage, cudaStream_t st, const DomDev *dom, int nx,
+                                 int ny, int parity, double *rho, double *ux, double *uy);
+
+// per-storage sweep launchers (one translation unit each)
+cudaError_t launch_sweep_f64(int vec, int grid, int warps, cudaStream_t st,
+                             const SweepArgs &a, int s);
+cudaError_t launch_sweep_f32(int vec, int grid, int warps, cudaStream_t st,
+                             const SweepArgs &a, int s);
+cudaError_t launch_sweep_f16s(int vec, int grid, int warps, cudaStream_t st,
+                              const SweepArgs &a, int s);
+cudaError_t launch_sweep_bf16s(int vec, int grid, int warps, cudaStream_t st,
+                               const SweepArgs &a, int s);
+int max_blocks_f64(int vec, int warps);
+int max_blocks_f32(int vec, int warps);
+int max_blocks_f16s(int vec, int warps);
+int max_blocks_bf16s(int vec, int warps);
+
+}  // namespace lbm

@@ -1,0 +1,1060 @@
+// Host runtime of the TRT-LBM-VP library: domains, batches with tile work lists,
+// CUDA-graph replay of step chunks, the tile autotuner, and the C ABI of include/lbm.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+thread_local std::string g_last_error;
+
+lbm_status fail(lbm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define LBM_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(LBM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                              \
+  } while (0)
+
+size_t elem_size(int storage) {
+  switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16S: return 2;
+    case LBM_BF16S: return 2;
+    default: return 0;
+  }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int pitch_of(int nx) { return static_cast<int>(align_up(static_cast<size_t>(nx), kPitchAlign)); }
+
+struct Alloc {
+  lbm_alloc_fn fn = nullptr;
+  lbm_free_fn ffn = nullptr;
+  void *ctx = nullptr;
+  cudaStream_t st = nullptr;
+  void *get(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (fn) return fn(bytes, ctx);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void *p) {
+    if (!p) return;
+    if (ffn) ffn(p, ctx);
+    else cudaFreeAsync(p, st);
+  }
+};
+
+// Fixed part of a domain's device footprint (populations x2, mask, bodies, offsets,
+// force ring, status word), each piece 256-byte aligned.
+struct Layout {
+  size_t lat_bytes, mask_off, bodies_off, off_off, ring_off, status_off, total;
+};
+
+Layout layout_of(const lbm_params &p, int nbodies) {
+  Layout L;
+  const size_t pitch = pitch_of(p.nx);
+  const size_t es = elem_size(p.storage);
+  const int cap = p.force_capacity > 0 ? p.force_capacity : 8192;
+  L.lat_bytes = align_up(static_cast<size_t>(kQ) * p.ny * pitch * es, 256);
+  size_t o = 2 * L.lat_bytes;
+  L.mask_off = o;
+  o += align_up(static_cast<size_t>(p.ny) * pitch, 256);
+  L.bodies_off = o;
+  o += align_up(sizeof(double) * 5 * std::max(1, nbodies), 256);
+  L.off_off = o;
+  o += align_up(sizeof(int32_t) * (nbodies + 1), 256);
+  L.ring_off = o;
+  o += align_up(p.force_every > 0 ? sizeof(double) * 2 * std::max(1, nbodies) * cap : 16, 256);
+  L.status_off = o;
+  o += 256;
+  L.total = o;
+  return L;
+}
+
+lbm_status validate(const lbm_params *p, int nbodies) {
+  if (!p) return fail(LBM_EINVAL, "params is NULL");
+  if (p->nx < 3 || p->ny < 3) return fail(LBM_EINVAL, "nx, ny must be >= 3 (got %d, %d)", p->nx, p->ny);
+  if (static_cast<long long>(pitch_of(p->nx)) * p->ny > (1ll << 31) / 2)
+    return fail(LBM_EINVAL, "grid too large for 32-bit node indices");
+  if (elem_size(p->storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", p->storage);
+  const double tau = p->nu > 0 ? 3.0 * p->nu + 0.5 : p->tau_plus;
+  if (!(tau > 0.5)) return fail(LBM_EINVAL, "tau_plus must exceed 1/2 (got %g)", tau);
+  if (!(p->magic_lambda > 0)) return fail(LBM_EINVAL, "magic parameter must be > 0");
+  if (!(p->eta > 0)) return fail(LBM_EINVAL, "eta must be > 0");
+  if (!(p->rho0 > 0)) return fail(LBM_EINVAL, "rho0 must be > 0");
+  if (p->west != LBM_PERIODIC && p->west != LBM_INLET_EQ) return fail(LBM_EINVAL, "west edge must be PERIODIC or INLET_EQ");
+  if (p->east != LBM_PERIODIC && p->east != LBM_OUTFLOW_ZG) return fail(LBM_EINVAL, "east edge must be PERIODIC or OUTFLOW_ZG");
+  if ((p->west == LBM_PERIODIC) != (p->east == LBM_PERIODIC)) return fail(LBM_EINVAL, "x edges: both periodic or neither");
+  if (p->south != LBM_PERIODIC && p->south != LBM_FREE_SLIP) return fail(LBM_EINVAL, "south edge must be PERIODIC or FREE_SLIP");
+  if (p->north != LBM_PERIODIC && p->north != LBM_FREE_SLIP) return fail(LBM_EINVAL, "north edge must be PERIODIC or FREE_SLIP");
+  if ((p->south == LBM_PERIODIC) != (p->north == LBM_PERIODIC)) return fail(LBM_EINVAL, "y edges: both periodic or neither");
+  if (nbodies < 0 || nbodies > kMaxBodies) return fail(LBM_EINVAL, "nbodies must be in [0, 255]");
+  if (p->force_every < 0 || p->force_capacity < 0) return fail(LBM_EINVAL, "force_every/capacity must be >= 0");
+  return LBM_OK;
+}
+
+struct Slot {
+  bool used = false;
+  lbm_params p{};
+  int nbodies = 0;
+  int pitch = 0;
+  long long target = 0;
+  long long done = 0;
+  int parity = 0;
+  long long drained = 0;
+  void *block = nullptr;
+  void *solid = nullptr;
+  size_t bytes = 0;
+  DomDev dev{};
+};
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+  int max_domains = 0;
+  size_t budget = 0;
+  int storage = 0;
+  int graph_steps = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  Alloc al;
+  std::vector<Slot> slots;
+  DomDev *d_doms = nullptr;
+  DomDyn *d_dyn = nullptr;
+  DomDyn *h_dyn = nullptr;  // pinned staging
+  cudaEvent_t dyn_ev = nullptr;
+  TileDev *d_tiles = nullptr;
+  int tiles_cap = 0;
+  ForceItem *d_items = nullptr;
+  int items_cap = 0;
+  Counters *d_ctr = nullptr;
+  Counters *h_ctr = nullptr;  // pinned staging for tile/item counts
+  int vec = 0, warps = 0, rows = 0;
+  int grid_sweep = 0, grid_force = 0;
+  int ntiles = 0, nitems = 0;
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  long long launches = 0;
+  size_t bytes_in_use = 0;
+  int sm_count = 0;
+};
+
+struct lbm_domain {
+  lbm_batch *b = nullptr;
+};
+
+namespace lbm {
+namespace {
+
+cudaError_t sweep_launch(lbm_batch *b, int grid, int vec, int warps, int rows, int s) {
+  SweepArgs a{b->d_doms, b->d_dyn, b->d_tiles, b->d_ctr, rows};
+  switch (b->storage) {
+    case LBM_F64: return launch_sweep_f64(vec, grid, warps, b->st, a, s);
+    case LBM_F32: return launch_sweep_f32(vec, grid, warps, b->st, a, s);
+    case LBM_F16S: return launch_sweep_f16s(vec, grid, warps, b->st, a, s);
+    case LBM_BF16S: return launch_sweep_bf16s(vec, grid, warps, b->st, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int sweep_occupancy(int storage, int vec, int warps) {
+  switch (storage) {
+    case LBM_F64: return max_blocks_f64(vec, warps);
+    case LBM_F32: return max_blocks_f32(vec, warps);
+    case LBM_F16S: return max_blocks_f16s(vec, warps);
+    case LBM_BF16S: return max_blocks_bf16s(vec, warps);
+  }
+  return 0;
+}
+
+bool vec_ok(int storage, int vec) {
+  switch (storage) {
+    case LBM_F64: return vec == 1 || vec == 2;
+    case LBM_F32: return vec == 2 || vec == 4;
+    default: return vec == 4 || vec == 8;
+  }
+}
+
+void default_tile(int storage, int &vec, int &warps, int &rows) {
+  vec = storage == LBM_F64 ? 2 : (storage == LBM_F32 ? 4 : 8);
+  warps = 8;
+  rows = 2;
+}
+
+void drop_graph(lbm_batch *b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+lbm_status set_config(lbm_batch *b, int vec, int warps, int rows) {
+  if (!vec_ok(b->storage, vec)) return fail(LBM_EINVAL, "cells per thread %d unsupported for storage %d", vec, b->storage);
+  if (warps < 1 || warps > 16 || rows < 1 || rows > 16) return fail(LBM_EINVAL, "warps and rows must be in [1, 16]");
+  const int occ = sweep_occupancy(b->storage, vec, warps);
+  if (occ <= 0) return fail(LBM_ECUDA, "sweep kernel cannot run with %d warps per block", warps);
+  b->vec = vec;
+  b->warps = warps;
+  b->rows = rows;
+  b->grid_sweep = occ * b->sm_count;
+  b->dirty = true;
+  drop_graph(b);
+  return LBM_OK;
+}
+
+// Rebuild the tile and force-item lists of the resident slots and upload them.
+lbm_status rebuild_lists(lbm_batch *b) {
+  std::vector<TileDev> tiles;
+  std::vector<ForceItem> items;
+  const int tw = 32 * b->vec, th = b->warps * b->rows;
+  for (int k = 0; k < b->max_domains; ++k) {
+    const Slot &s = b->slots[k];
+    if (!s.used) continue;
+    for (int y0 = 0; y0 < s.p.ny; y0 += th)
+      for (int x0 = 0; x0 < s.p.nx; x0 += tw) tiles.push_back(TileDev{k, x0, y0, 0});
+    if (s.p.force_every > 0)
+      for (int body = 1; body <= s.nbodies; ++body) items.push_back(ForceItem{k, body});
+  }
+  if (static_cast<int>(tiles.size()) > b->tiles_cap || !b->d_tiles) {
+    const int cap = std::max<int>(static_cast<int>(tiles.size()) * 2, 1024);
+    LBM_CUDA(cudaStreamSynchronize(b->st));
+    b->al.put(b->d_tiles);
+    b->d_tiles = static_cast<TileDev *>(b->al.get(sizeof(TileDev) * cap));
+    if (!b->d_tiles) { b->tiles_cap = 0; return fail(LBM_ENOMEM, "tile list allocation failed"); }
+    b->tiles_cap = cap;
+    drop_graph(b);
+  }
+  if (static_cast<int>(items.size()) > b->items_cap || !b->d_items) {
+    const int cap = std::max<int>(static_cast<int>(items.size()) * 2, 256);
+    LBM_CUDA(cudaStreamSynchronize(b->st));
+    b->al.put(b->d_items);
+    b->d_items = static_cast<ForceItem *>(b->al.get(sizeof(ForceItem) * cap));
+    if (!b->d_items) { b->items_cap = 0; return fail(LBM_ENOMEM, "force item allocation failed"); }
+    b->items_cap = cap;
+    drop_graph(b);
+  }
+  b->ntiles = static_cast<int>(tiles.size());
+  b->nitems = static_cast<int>(items.size());
+  // synchronous uploads from pageable vectors: the copies complete before return
+  if (!tiles.empty())
+    LBM_CUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(),
+                             cudaMemcpyHostToDevice, b->st));
+  if (!items.empty())
+    LBM_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(ForceItem) * items.size(),
+                             cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaEventSynchronize(b->dyn_ev));
+  b->h_ctr->ntiles = b->ntiles;
+  b->h_ctr->nforce = b->nitems;
+  b->h_ctr->run_base = 0;
+  LBM_CUDA(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  b->dirty = false;
+  return LBM_OK;
+}
+
+// Enqueue step s of the current run: the force reduction reads the same lattice as the
+// sweep, so the two are ordered only against the next step.
+// The force kernel is launched even when no body records forces (it returns at once),
+// so that a captured graph stays valid when the batch membership changes.
+lbm_status enqueue_step(lbm_batch *b, int s) {
+  LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
+                         b->d_ctr, s));
+  b->launches++;
+  LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, s));
+  b->launches++;
+  return LBM_OK;
+}
+
+lbm_status capture_graph(lbm_batch *b) {
+  drop_graph(b);
+  cudaGraph_t g = nullptr;
+  LBM_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  const long long before = b->launches;
+  lbm_status rc = LBM_OK;
+  for (int s = 0; s < b->graph_steps && rc == LBM_OK; ++s) rc = enqueue_step(b, s);
+  cudaError_t e = rc == LBM_OK ? launch_advance(b->st, b->d_ctr, b->graph_steps) : cudaSuccess;
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+  b->launches = before;  // capture only records; replays count
+  if (rc != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) {
+    b->graph = nullptr;
+    return fail(LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+  }
+  return LBM_OK;
+}
+
+lbm_status upload_dyn(lbm_batch *b) {
+  LBM_CUDA(cudaEventSynchronize(b->dyn_ev));
+  for (int k = 0; k < b->max_domains; ++k) {
+    const Slot &s = b->slots[k];
+    DomDyn &d = b->h_dyn[k];
+    d.step0 = s.done;
+    d.step_end = s.used ? s.target : s.done;
+    d.parity = s.parity;
+    d.pad = 0;
+  }
+  LBM_CUDA(cudaMemcpyAsync(b->d_dyn, b->h_dyn, sizeof(DomDyn) * b->max_domains,
+                           cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaMemsetAsync(&b->d_ctr->run_base, 0, sizeof(long long), b->st));
+  LBM_CUDA(cudaEventRecord(b->dyn_ev, b->st));
+  return LBM_OK;
+}
+
+long long entries_at(const Slot &s, long long steps) {
+  return s.p.force_every > 0 ? steps / s.p.force_every : 0;
+}
+
+struct Profile {
+  double sweep_ms = 0.0, force_ms = 0.0;
+};
+
+lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile *prof = nullptr) {
+  if (steps_run) *steps_run = 0;
+  if (max_steps < 0) return fail(LBM_EINVAL, "max_steps must be >= 0");
+  long long steps = 0;
+  for (const Slot &s : b->slots)
+    if (s.used && s.done < s.target) steps = std::max(steps, std::min(max_steps, s.target - s.done));
+  if (steps == 0) return LBM_OK;
+  for (const Slot &s : b->slots) {
+    if (!s.used || s.p.force_every <= 0) continue;
+    const long long end = std::min(s.target, s.done + steps);
+    const int cap = s.dev.force_cap;
+    if (entries_at(s, end) - s.drained > cap)
+      return fail(LBM_EBUSY, "force ring would overflow (%lld undrained + new > %d)",
+                  entries_at(s, end) - s.drained, cap);
+  }
+  if (b->dirty) {
+    lbm_status rc = rebuild_lists(b);
+    if (rc != LBM_OK) return rc;
+  }
+  lbm_status rc = upload_dyn(b);
+  if (rc != LBM_OK) return rc;
+  long long s0 = 0;
+  if (prof) {
+    // one kernel at a time, each bracketed by events on the batch stream
+    std::vector<cudaEvent_t> ev(3 * steps);
+    for (auto &e : ev) LBM_CUDA(cudaEventCreate(&e));
+    lbm_status prc = LBM_OK;
+    for (long long s = 0; s < steps && prc == LBM_OK; ++s) {
+      cudaEventRecord(ev[3 * s], b->st);
+      if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
+                        static_cast<int>(s)) != cudaSuccess)
+        prc = fail(LBM_ECUDA, "force launch failed");
+      cudaEventRecord(ev[3 * s + 1], b->st);
+      if (sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, static_cast<int>(s)) != cudaSuccess)
+        prc = fail(LBM_ECUDA, "sweep launch failed");
+      cudaEventRecord(ev[3 * s + 2], b->st);
+      b->launches += 2;
+    }
+    cudaStreamSynchronize(b->st);
+    for (long long s = 0; s < steps && prc == LBM_OK; ++s) {
+      float a = 0.f, c = 0.f;
+      cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+      cudaEventElapsedTime(&c, ev[3 * s + 1], ev[3 * s + 2]);
+      prof->force_ms += a;
+      prof->sweep_ms += c;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (prc != LBM_OK) return prc;
+    s0 = steps;
+  }
+  if (!prof && b->graph_steps > 0 && steps >= b->graph_steps) {
+    if (!b->graph) {
+      rc = capture_graph(b);
+      if (rc != LBM_OK) return rc;
+    }
+    const long long reps = steps / b->graph_steps;
+    for (long long r = 0; r < reps; ++r) {
+      LBM_CUDA(cudaGraphLaunch(b->graph, b->st));
+      b->launches += 2 * static_cast<long long>(b->graph_steps) + 1;
+    }
+    s0 = reps * b->graph_steps;
+  }
+  // remaining steps as direct launches; the device counter already holds s0
+  for (long long s = s0; s < steps; ++s) {
+    rc = enqueue_step(b, static_cast<int>(s - s0));
+    if (rc != LBM_OK) return rc;
+  }
+  for (Slot &s : b->slots) {
+    if (!s.used || s.done >= s.target) continue;
+    const long long adv = std::min(steps, s.target - s.done);
+    s.done += adv;
+    s.parity = static_cast<int>((s.parity + adv) & 1);
+  }
+  if (steps_run) *steps_run = steps;
+  return LBM_OK;
+}
+
+lbm_status read_status(lbm_batch *b, const Slot &s, int *st) {
+  LBM_CUDA(cudaMemcpyAsync(st, s.dev.status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
+}
+
+lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
+                 const lbm_geometry *geom, const lbm_body *bodies, int nbodies, long long nsteps,
+                 int *slot_out) {
+  lbm_status rc = validate(p, nbodies);
+  if (rc != LBM_OK) return rc;
+  if (p->storage != b->storage) return fail(LBM_EINVAL, "domain storage %d differs from batch storage %d", p->storage, b->storage);
+  if (nbodies > 0 && !bodies) return fail(LBM_EINVAL, "bodies is NULL");
+  if (!mask_host && geom && geom->nshapes > 0 && !geom->shapes) return fail(LBM_EINVAL, "geometry shapes NULL");
+  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+  int k = -1;
+  for (int i = 0; i < b->max_domains; ++i)
+    if (!b->slots[i].used) { k = i; break; }
+  if (k < 0) return fail(LBM_EBUSY, "no free slot");
+  const Layout L = layout_of(*p, nbodies);
+  if (b->budget > 0 && b->bytes_in_use + L.total > b->budget)
+    return fail(LBM_EBUSY, "memory budget exceeded (%zu + %zu > %zu)", b->bytes_in_use, L.total, b->budget);
+  if (geom && !mask_host)
+    for (int i = 0; i < geom->nshapes; ++i) {
+      const lbm_shape &sh = geom->shapes[i];
+      if (sh.kind < 0 || sh.kind > LBM_SHAPE_NACA4) return fail(LBM_EINVAL, "shape %d: unknown kind", i);
+      if (sh.body < 1 || sh.body > nbodies) return fail(LBM_EINVAL, "shape %d: body id %d not in [1, %d]", i, sh.body, nbodies);
+      if (sh.kind == LBM_SHAPE_NACA4 && !(sh.chord > 0)) return fail(LBM_EINVAL, "shape %d: chord must be > 0", i);
+    }
+
+  Slot s;
+  s.p = *p;
+  if (s.p.force_capacity == 0) s.p.force_capacity = 8192;
+  s.nbodies = nbodies;
+  s.pitch = pitch_of(p->nx);
+  s.target = nsteps;
+  s.block = b->al.get(L.total);
+  if (!s.block) return fail(LBM_ENOMEM, "device allocation of %zu bytes failed", L.total);
+  s.bytes = L.total;
+  char *base = static_cast<char *>(s.block);
+  DomDev &D = s.dev;
+  D.lat[0] = base;
+  D.lat[1] = base + L.lat_bytes;
+  uint8_t *mask = reinterpret_cast<uint8_t *>(base + L.mask_off);
+  D.mask = mask;
+  double *bod = reinterpret_cast<double *>(base + L.bodies_off);
+  D.bodies = bod;
+  int32_t *off = reinterpret_cast<int32_t *>(base + L.off_off);
+  D.solid_off = off;
+  D.ring = reinterpret_cast<double *>(base + L.ring_off);
+  D.status = reinterpret_cast<int32_t *>(base + L.status_off);
+  D.nx = p->nx;
+  D.ny = p->ny;
+  D.pitch = s.pitch;
+  D.west = p->west;
+  D.east = p->east;
+  D.south = p->south;
+  D.north = p->north;
+  D.nbodies = nbodies;
+  D.force_every = p->force_every;
+  D.force_cap = s.p.force_capacity;
+  const double tau_s = p->nu > 0 ? 3.0 * p->nu + 0.5 : p->tau_plus;  // tau_s = nu/c_s^2 + 1/2
+  const double tau_a = 0.5 + p->magic_lambda / (tau_s - 0.5);         // Lambda = (tau_s-1/2)(tau_a-1/2)
+  D.omega_p = 1.0 / tau_s;
+  D.omega_m = 1.0 / tau_a;
+  D.inv_2eta1 = 1.0 / (2.0 * p->eta + 1.0);
+  D.rho0 = p->rho0;
+  {
+    // inlet ghost populations f^eq(rho0, u_in), Eq. (feq), in compute space
+    const int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double w[kQ] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const double ux = p->u_in_x, uy = p->u_in_y, usq = ux * ux + uy * uy;
+    const bool shift = p->storage == LBM_F16S || p->storage == LBM_BF16S;
+    for (int a = 0; a < kQ; ++a) {
+      const double eu = ex[a] * ux + ey[a] * uy;
+      const double dev = p->rho0 * w[a] * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+      D.ghost[a] = shift ? dev : p->rho0 * w[a] + dev;
+    }
+  }
+  cudaStream_t st = b->st;
+  auto bail = [&](lbm_status r) {
+    cudaStreamSynchronize(st);
+    b->al.put(s.block);
+    b->al.put(s.solid);
+    return r;
+  };
+#define ADM_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bail(fail(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));      \
+  } while (0)
+
+  // mask: uploaded (pitched, zero padding) or rasterised on the device
+  ADM_CUDA(cudaMemsetAsync(mask, 0, static_cast<size_t>(p->ny) * s.pitch, st));
+  std::vector<ShapeDev> shapes;
+  void *tmp = nullptr;
+  const size_t counts_bytes = sizeof(int32_t) * (nbodies + 2);
+  if (mask_host) {
+    ADM_CUDA(cudaMemcpy2DAsync(mask, s.pitch, mask_host, p->nx, p->nx, p->ny, cudaMemcpyHostToDevice, st));
+    tmp = b->al.get(counts_bytes);
+    if (!tmp) return bail(fail(LBM_ENOMEM, "temporary allocation failed"));
+  } else {
+    const int ns = geom ? geom->nshapes : 0;
+    for (int i = 0; i < ns; ++i) {
+      const lbm_shape &sh = geom->shapes[i];
+      ShapeDev d{sh.kind, sh.body, sh.cx, sh.cy, sh.radius, sh.chord, sh.thickness,
+                 std::cos(sh.aoa_rad), std::sin(sh.aoa_rad)};
+      shapes.push_back(d);
+    }
+    tmp = b->al.get(counts_bytes + sizeof(ShapeDev) * std::max<size_t>(1, shapes.size()) + 256);
+    if (!tmp) return bail(fail(LBM_ENOMEM, "temporary allocation failed"));
+    if (ns > 0) {
+      ShapeDev *dsh = reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + align_up(counts_bytes, 256));
+      ADM_CUDA(cudaMemcpyAsync(dsh, shapes.data(), sizeof(ShapeDev) * ns, cudaMemcpyHostToDevice, st));
+      ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns));
+    }
+  }
+  // body table
+  std::vector<double> hb(5 * std::max(1, nbodies), 0.0);
+  for (int i = 0; i < nbodies; ++i) {
+    hb[5 * i + 0] = bodies[i].cx;
+    hb[5 * i + 1] = bodies[i].cy;
+    hb[5 * i + 2] = bodies[i].vx;
+    hb[5 * i + 3] = bodies[i].vy;
+    hb[5 * i + 4] = bodies[i].omega;
+  }
+  ADM_CUDA(cudaMemcpyAsync(bod, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
+  // count nodes per body, then build the solid-node lists
+  int32_t *counts = static_cast<int32_t *>(tmp);
+  ADM_CUDA(cudaMemsetAsync(counts, 0, counts_bytes, st));
+  ADM_CUDA(launch_count_bodies(st, mask, p->nx, p->ny, s.pitch, nbodies, counts, counts + nbodies + 1));
+  std::vector<int32_t> hc(nbodies + 2, 0);
+  ADM_CUDA(cudaMemcpyAsync(hc.data(), counts, counts_bytes, cudaMemcpyDeviceToHost, st));
+  ADM_CUDA(cudaStreamSynchronize(st));
+  b->al.put(tmp);
+  tmp = nullptr;
+  if (hc[nbodies + 1] > 0)
+    return bail(fail(LBM_EINVAL, "mask holds body id %d but only %d bodies were given", hc[nbodies + 1], nbodies));
+  std::vector<int32_t> ho(nbodies + 1, 0);
+  for (int i = 1; i <= nbodies; ++i) ho[i] = ho[i - 1] + hc[i];
+  const size_t nsolid = static_cast<size_t>(ho[nbodies]);
+  s.solid = b->al.get(sizeof(int32_t) * std::max<size_t>(1, nsolid));
+  if (!s.solid) return bail(fail(LBM_ENOMEM, "solid list allocation failed"));
+  D.solid = static_cast<const int32_t *>(s.solid);
+  ADM_CUDA(cudaMemcpyAsync(off, ho.data(), sizeof(int32_t) * ho.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(launch_build_solid(st, mask, p->nx, p->ny, s.pitch, nbodies, off, static_cast<int32_t *>(s.solid)));
+  // initial state (step (1)): lattice A = f^eq(rho0, u0), lattice B zero
+  ADM_CUDA(launch_init(p->storage, st, D.lat[0], p->nx, p->ny, s.pitch, p->rho0, p->u0_x, p->u0_y));
+  ADM_CUDA(cudaMemsetAsync(D.lat[1], 0, L.lat_bytes, st));
+  ADM_CUDA(cudaMemsetAsync(D.status, 0, sizeof(int32_t), st));
+  if (p->force_every > 0)
+    ADM_CUDA(cudaMemsetAsync(D.ring, 0, sizeof(double) * 2 * std::max(1, nbodies) * s.p.force_capacity, st));
+  ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaStreamSynchronize(st));
+#undef ADM_CUDA
+  s.used = true;
+  s.bytes = L.total + sizeof(int32_t) * std::max<size_t>(1, nsolid);
+  b->bytes_in_use += s.bytes;
+  b->slots[k] = s;
+  b->dirty = true;
+  *slot_out = k;
+  return LBM_OK;
+}
+
+lbm_status check_slot(lbm_batch *b, int slot) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  if (slot < 0 || slot >= b->max_domains || !b->slots[slot].used)
+    return fail(LBM_ENOTFOUND, "slot %d is not resident", slot);
+  return LBM_OK;
+}
+
+lbm_status poll(lbm_batch *b, int slot, double *out, long long max_entries, long long *written,
+                int *done) {
+  if (written) *written = 0;
+  if (done) *done = 0;
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  int status = 0;
+  rc = read_status(b, s, &status);
+  if (rc != LBM_OK) return rc;
+  const long long produced = entries_at(s, s.done);
+  long long n = std::min(produced - s.drained, std::max(0ll, max_entries));
+  if (n > 0 && !out) return fail(LBM_EINVAL, "out is NULL");
+  const size_t per = 2 * static_cast<size_t>(s.nbodies);
+  long long copied = 0;
+  while (copied < n && per > 0) {
+    const long long e = s.drained + copied;
+    const long long pos = e % s.dev.force_cap;
+    const long long chunk = std::min(n - copied, static_cast<long long>(s.dev.force_cap) - pos);
+    LBM_CUDA(cudaMemcpyAsync(out + copied * per, s.dev.ring + pos * per, sizeof(double) * per * chunk,
+                             cudaMemcpyDeviceToHost, b->st));
+    copied += chunk;
+  }
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  s.drained += n;
+  if (written) *written = n;
+  if (done) *done = (s.done >= s.target && s.drained >= produced) ? 1 : 0;
+  if (status & 1) return fail(LBM_EUNSTABLE, "slot %d diverged (rho out of range or not finite)", slot);
+  return LBM_OK;
+}
+
+lbm_status moments(lbm_batch *b, int slot, double *rho, double *ux, double *uy) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  const size_t cells = static_cast<size_t>(s.p.nx) * s.p.ny;
+  double *tmp = static_cast<double *>(b->al.get(sizeof(double) * 3 * cells));
+  if (!tmp) return fail(LBM_ENOMEM, "moments buffer allocation failed");
+  cudaError_t e = launch_moments_sized(b->storage, b->st, b->d_doms + slot, s.p.nx, s.p.ny, s.parity,
+                                       tmp, tmp + cells, tmp + 2 * cells);
+  double *outs[3] = {rho, ux, uy};
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+    if (outs[q]) e = cudaMemcpyAsync(outs[q], tmp + q * cells, sizeof(double) * cells, cudaMemcpyDefault, b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  b->al.put(tmp);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "moments failed: %s", cudaGetErrorString(e));
+  int status = 0;
+  rc = read_status(b, s, &status);
+  if (rc != LBM_OK) return rc;
+  if (status & 1) return fail(LBM_EUNSTABLE, "slot %d diverged", slot);
+  return LBM_OK;
+}
+
+lbm_status populations(lbm_batch *b, int slot, void *out, const void *in, size_t bytes) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  const size_t es = elem_size(b->storage);
+  const size_t want = es * kQ * s.p.nx * s.p.ny;
+  if (bytes != want) return fail(LBM_EINVAL, "population buffer must be %zu bytes (got %zu)", want, bytes);
+  char *lat = static_cast<char *>(s.dev.lat[s.parity]);
+  const size_t rowb = es * s.p.nx, pitchb = es * s.pitch;
+  if (out) {
+    LBM_CUDA(cudaMemcpy2DAsync(out, rowb, lat, pitchb, rowb, static_cast<size_t>(kQ) * s.p.ny, cudaMemcpyDefault, b->st));
+  } else {
+    if (!in) return fail(LBM_EINVAL, "input is NULL");
+    LBM_CUDA(cudaMemcpy2DAsync(lat, pitchb, in, rowb, rowb, static_cast<size_t>(kQ) * s.p.ny, cudaMemcpyDefault, b->st));
+  }
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
+}
+
+lbm_status get_mask(lbm_batch *b, int slot, uint8_t *out) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  const Slot &s = b->slots[slot];
+  LBM_CUDA(cudaMemcpy2DAsync(out, s.p.nx, s.dev.mask, s.pitch, s.p.nx, s.p.ny, cudaMemcpyDefault, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
+}
+
+void destroy(lbm_batch *b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  drop_graph(b);
+  for (Slot &s : b->slots)
+    if (s.used) {
+      b->al.put(s.block);
+      b->al.put(s.solid);
+    }
+  b->al.put(b->d_doms);
+  b->al.put(b->d_dyn);
+  b->al.put(b->d_tiles);
+  b->al.put(b->d_items);
+  b->al.put(b->d_ctr);
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->h_dyn) cudaFreeHost(b->h_dyn);
+  if (b->h_ctr) cudaFreeHost(b->h_ctr);
+  if (b->dyn_ev) cudaEventDestroy(b->dyn_ev);
+  if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, void *stream,
+                  lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx, lbm_batch **out) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_domains < 1 || max_domains > 4096) return fail(LBM_EINVAL, "max_domains must be in [1, 4096]");
+  if (elem_size(storage) == 0) return fail(LBM_EINVAL, "unknown storage %d", storage);
+  if (graph_steps < 0 || graph_steps > 4096) return fail(LBM_EINVAL, "graph_steps must be in [0, 4096]");
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(LBM_EINVAL, "alloc and free must both be given or both NULL");
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return fail(LBM_ENOMEM, "host allocation failed");
+  b->max_domains = max_domains;
+  b->budget = budget;
+  b->storage = storage;
+  b->graph_steps = graph_steps;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(LBM_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+  }
+  if (stream) {
+    b->st = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreate(&b->st);
+    if (e != cudaSuccess) { delete b; return fail(LBM_ECUDA, "stream creation failed: %s", cudaGetErrorString(e)); }
+    b->own_stream = true;
+  }
+  b->al = Alloc{alloc, free_fn, ctx, b->st};
+  b->grid_force = 2 * b->sm_count;
+  b->slots.resize(max_domains);
+  b->d_doms = static_cast<DomDev *>(b->al.get(sizeof(DomDev) * max_domains));
+  b->d_dyn = static_cast<DomDyn *>(b->al.get(sizeof(DomDyn) * max_domains));
+  b->d_ctr = static_cast<Counters *>(b->al.get(sizeof(Counters)));
+  if (!b->d_doms || !b->d_dyn || !b->d_ctr) { destroy(b); return fail(LBM_ENOMEM, "device allocation failed"); }
+  if (cudaMallocHost(&b->h_dyn, sizeof(DomDyn) * max_domains) != cudaSuccess ||
+      cudaMallocHost(&b->h_ctr, sizeof(Counters)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->dyn_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(b);
+    return fail(LBM_ENOMEM, "pinned host allocation failed");
+  }
+  cudaEventRecord(b->dyn_ev, b->st);
+  cudaMemsetAsync(b->d_ctr, 0, sizeof(Counters), b->st);
+  cudaMemsetAsync(b->d_dyn, 0, sizeof(DomDyn) * max_domains, b->st);
+  int vec, warps, rows;
+  default_tile(storage, vec, warps, rows);
+  lbm_status rc = set_config(b, vec, warps, rows);
+  if (rc != LBM_OK) { destroy(b); return rc; }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status autotune(lbm_batch *b, int reps, double *best_us) {
+  if (reps < 1) return fail(LBM_EINVAL, "reps must be >= 1");
+  bool any = false;
+  for (const Slot &s : b->slots) any |= s.used;
+  if (!any) return fail(LBM_EINVAL, "autotune needs resident domains");
+  const int vecs[2] = {b->storage == LBM_F64 ? 1 : (b->storage == LBM_F32 ? 2 : 4),
+                       b->storage == LBM_F64 ? 2 : (b->storage == LBM_F32 ? 4 : 8)};
+  const int warp_opts[3] = {4, 8, 16};
+  const int row_opts[3] = {1, 2, 4};
+  // every resident domain active for the timing launches (s = 0 only: the spare
+  // lattice is written, the current state is read and left as it is)
+  LBM_CUDA(cudaEventSynchronize(b->dyn_ev));
+  for (int k = 0; k < b->max_domains; ++k) {
+    const Slot &s = b->slots[k];
+    b->h_dyn[k] = DomDyn{s.done, s.used ? s.done + 1 : s.done, s.parity, 0};
+  }
+  LBM_CUDA(cudaMemcpyAsync(b->d_dyn, b->h_dyn, sizeof(DomDyn) * b->max_domains, cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaEventRecord(b->dyn_ev, b->st));
+  cudaEvent_t e0, e1;
+  LBM_CUDA(cudaEventCreate(&e0));
+  LBM_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  int bv = b->vec, bw = b->warps, br = b->rows;
+  lbm_status rc = LBM_OK;
+  for (int v : vecs)
+    for (int w : warp_opts)
+      for (int r : row_opts) {
+        if (sweep_occupancy(b->storage, v, w) <= 0) continue;
+        rc = set_config(b, v, w, r);
+        if (rc == LBM_OK) rc = rebuild_lists(b);
+        if (rc != LBM_OK) break;
+        for (int q = 0; q < 2 && rc == LBM_OK; ++q)
+          if (sweep_launch(b, b->grid_sweep, v, w, r, 0) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune launch failed");
+        cudaEventRecord(e0, b->st);
+        for (int q = 0; q < reps && rc == LBM_OK; ++q)
+          if (sweep_launch(b, b->grid_sweep, v, w, r, 0) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune launch failed");
+        cudaEventRecord(e1, b->st);
+        cudaEventSynchronize(e1);
+        if (rc != LBM_OK) break;
+        b->launches += reps + 2;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double us = 1000.0 * ms / reps;
+        if (us < best) { best = us; bv = v; bw = w; br = r; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LBM_OK) return rc;
+  rc = set_config(b, bv, bw, br);
+  if (rc == LBM_OK) rc = rebuild_lists(b);
+  if (best_us) *best_us = best;
+  return rc;
+}
+
+}  // namespace
+}  // namespace lbm
+
+// ======================================================================================
+// C ABI
+
+extern "C" {
+
+void lbm_params_default(lbm_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = 64;
+  p->ny = 64;
+  p->nu = 0.1;
+  p->tau_plus = 0.8;
+  p->magic_lambda = 3.0 / 16.0;
+  p->eta = 1e-4;
+  p->rho0 = 1.0;
+  p->west = p->east = p->south = p->north = LBM_PERIODIC;
+  p->storage = LBM_F32;
+  p->force_every = 1;
+  p->force_capacity = 8192;
+}
+
+const char *lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "simulation diverged";
+    case LBM_ETIMEOUT: return "timed out";
+    case LBM_EBUSY: return "busy";
+    case LBM_ENOTFOUND: return "not found";
+  }
+  return "unknown status";
+}
+
+const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+size_t lbm_domain_bytes(const lbm_params *p, int32_t nbodies) {
+  if (!p || elem_size(p->storage) == 0 || p->nx < 1 || p->ny < 1) return 0;
+  lbm_params q = *p;
+  if (q.force_capacity == 0) q.force_capacity = 8192;
+  return layout_of(q, std::max(0, nbodies)).total;
+}
+
+lbm_status lbm_batch_create(int32_t max_domains, size_t hbm_budget_bytes, int32_t storage,
+                            int32_t graph_steps, void *cuda_stream, lbm_alloc_fn alloc,
+                            lbm_free_fn free_fn, void *alloc_ctx, lbm_batch **out) {
+  return create(max_domains, hbm_budget_bytes, storage, graph_steps, cuda_stream, alloc, free_fn,
+                alloc_ctx, out);
+}
+
+lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask,
+                           const lbm_geometry *geom, const lbm_body *bodies, int32_t nbodies,
+                           int64_t nsteps, int32_t *slot) {
+  if (!b || !slot) return fail(LBM_EINVAL, "batch or slot pointer is NULL");
+  int k = -1;
+  lbm_status rc = admit(b, p, mask, geom, bodies, nbodies, nsteps, &k);
+  if (rc == LBM_OK) *slot = k;
+  return rc;
+}
+
+lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps_run) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  long long n = 0;
+  lbm_status rc = run(b, max_steps, &n);
+  if (steps_run) *steps_run = n;
+  return rc;
+}
+
+lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_entries,
+                          int64_t *written, int32_t *done) {
+  long long w = 0;
+  int d = 0;
+  lbm_status rc = poll(b, slot, out, max_entries, &w, &d);
+  if (written) *written = w;
+  if (done) *done = d;
+  return rc;
+}
+
+lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, double *ux, double *uy) {
+  return moments(b, slot, rho, ux, uy);
+}
+
+lbm_status lbm_batch_get_populations(lbm_batch *b, int32_t slot, void *out, size_t bytes) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  return populations(b, slot, out, nullptr, bytes);
+}
+
+lbm_status lbm_batch_set_populations(lbm_batch *b, int32_t slot, const void *in, size_t bytes) {
+  return populations(b, slot, nullptr, in, bytes);
+}
+
+lbm_status lbm_batch_steps_done(lbm_batch *b, int32_t slot, int64_t *steps) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  if (steps) *steps = b->slots[slot].done;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_mask(lbm_batch *b, int32_t slot, uint8_t *out) {
+  return get_mask(b, slot, out);
+}
+
+lbm_status lbm_batch_profile(lbm_batch *b, int32_t steps, double *sweep_us, double *force_us,
+                             int64_t *steps_run) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  if (steps < 1 || steps > 100000) return fail(LBM_EINVAL, "steps must be in [1, 100000]");
+  Profile prof;
+  long long n = 0;
+  lbm_status rc = run(b, steps, &n, &prof);
+  if (steps_run) *steps_run = n;
+  if (sweep_us) *sweep_us = n > 0 ? 1000.0 * prof.sweep_ms / n : 0.0;
+  if (force_us) *force_us = n > 0 ? 1000.0 * prof.force_ms / n : 0.0;
+  return rc;
+}
+
+lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  b->al.put(s.block);
+  b->al.put(s.solid);
+  b->bytes_in_use -= s.bytes;
+  s = Slot();
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  return autotune(b, reps, best_us);
+}
+
+lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  return set_config(b, vec, warps, rows);
+}
+
+lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  if (vec) *vec = b->vec;
+  if (warps) *warps = b->warps;
+  if (rows) *rows = b->rows;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_info(lbm_batch *b, int32_t *resident, int64_t *cells, int64_t *launches,
+                          size_t *bytes) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  int r = 0;
+  long long c = 0;
+  for (const Slot &s : b->slots)
+    if (s.used) {
+      ++r;
+      c += static_cast<long long>(s.p.nx) * s.p.ny;
+    }
+  if (resident) *resident = r;
+  if (cells) *cells = c;
+  if (launches) *launches = b->launches;
+  if (bytes) *bytes = b->bytes_in_use;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch *b) {
+  destroy(b);
+  return LBM_OK;
+}
+
+// ---- single domain: a batch with one slot and an unbounded step target ------------------
+
+lbm_status lbm_domain_create(const lbm_params *p, const uint8_t *mask, const lbm_geometry *geom,
+                             const lbm_body *bodies, int32_t nbodies, void *cuda_stream,
+                             lbm_alloc_fn alloc, lbm_free_fn free_fn, void *alloc_ctx,
+                             lbm_domain **out) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  lbm_status rc = validate(p, nbodies);
+  if (rc != LBM_OK) return rc;
+  lbm_batch *b = nullptr;
+  rc = create(1, 0, p->storage, 32, cuda_stream, alloc, free_fn, alloc_ctx, &b);
+  if (rc != LBM_OK) return rc;
+  int slot = -1;
+  rc = admit(b, p, mask, geom, bodies, nbodies, std::numeric_limits<long long>::max(), &slot);
+  if (rc != LBM_OK) {
+    destroy(b);
+    return rc;
+  }
+  lbm_domain *d = new (std::nothrow) lbm_domain();
+  if (!d) {
+    destroy(b);
+    return fail(LBM_ENOMEM, "host allocation failed");
+  }
+  d->b = b;
+  *out = d;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_domain *d, int64_t nsteps) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+  long long n = 0;
+  return run(d->b, nsteps, &n);
+}
+
+lbm_status lbm_forces(lbm_domain *d, double *out, int64_t max_entries, int64_t *written) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  long long w = 0;
+  int done = 0;
+  lbm_status rc = poll(d->b, 0, out, max_entries, &w, &done);
+  if (written) *written = w;
+  return rc;
+}
+
+lbm_status lbm_moments(lbm_domain *d, double *rho, double *ux, double *uy) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return moments(d->b, 0, rho, ux, uy);
+}
+
+lbm_status lbm_get_populations(lbm_domain *d, void *out, size_t bytes) {
+  if (!d || !out) return fail(LBM_EINVAL, "domain or out is NULL");
+  return populations(d->b, 0, out, nullptr, bytes);
+}
+
+lbm_status lbm_set_populations(lbm_domain *d, const void *in, size_t bytes) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return populations(d->b, 0, nullptr, in, bytes);
+}
+
+lbm_status lbm_get_mask(lbm_domain *d, uint8_t *out) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return get_mask(d->b, 0, out);
+}
+
+lbm_status lbm_steps_done(lbm_domain *d, int64_t *steps) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  if (steps) *steps = d->b->slots[0].done;
+  return LBM_OK;
+}
+
+lbm_status lbm_domain_destroy(lbm_domain *d) {
+  if (!d) return LBM_OK;
+  destroy(d->b);
+  delete d;
+  return LBM_OK;
+}
+
+}  // extern "C"

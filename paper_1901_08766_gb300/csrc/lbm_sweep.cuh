@@ -1,0 +1,342 @@
+// The fused TRT-LBM-VP sweep: one launch advances every active domain of a batch by
+// one time step (steps (3), (4), (5), (6), (2) of the algorithm of Sec. 2.2, fused per
+// node since volume penalization needs only the node's own variables).
+//
+// Work decomposition. A persistent grid walks a tile list. A tile is a strip of
+// 32 * V cells of one row range: lane l of each warp owns V consecutive cells
+// x0 + l*V .. x0 + l*V + V-1 and a warp walks `rows` rows. Each of the nine
+// populations of a row is read with one aligned vector load per lane from the
+// structure-of-arrays lattice [9][ny][pitch]; the +-1 x-shift of the pull (Eq.
+// streaming) is done in registers with one warp shuffle per direction, the two
+// strip-end cells come from a scalar load by the end lanes, and the domain-edge
+// rules are applied to the row pointers (y) and to the end cells (x). The update is
+// written back with aligned vector stores to the other lattice (double buffering).
+#pragma once
+
+#include "lbm_cell.cuh"
+
+namespace lbm {
+
+// V consecutive storage elements held by one lane.
+template <int S, int V> struct Strip;
+
+// 16-bit storage: V/2 packed 32-bit words, element 2k in the low half of word k.
+template <int S, int V> struct Strip16 {
+  static_assert(V % 2 == 0, "16-bit strips hold an even number of cells");
+  static constexpr int kW = V / 2;
+  uint32_t w[kW];
+  __device__ void load(const uint16_t *p) {
+    if constexpr (kW == 4) {
+      uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if constexpr (kW == 2) {
+      uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+      w[0] = v.x; w[1] = v.y;
+    } else {
+      w[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
+    }
+  }
+  __device__ void store(uint16_t *p) const {
+    if constexpr (kW == 4) {
+      *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (kW == 2) {
+      *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    } else {
+      *reinterpret_cast<uint32_t *>(p) = w[0];
+    }
+  }
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < kW; ++k) w[k] = 0u;
+  }
+  __device__ uint16_t get(int k) const {
+    return static_cast<uint16_t>((k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xffffu));
+  }
+  __device__ void set(int k, uint16_t e) {
+    uint32_t &x = w[k >> 1];
+    x = (k & 1) ? ((x & 0x0000ffffu) | (static_cast<uint32_t>(e) << 16))
+                : ((x & 0xffff0000u) | e);
+  }
+  // element k <- element k-1; element 0 <- `in` (the previous cell)
+  __device__ void shift_up(uint16_t in) {
+#pragma unroll
+    for (int k = kW - 1; k > 0; --k) w[k] = __byte_perm(w[k - 1], w[k], 0x5432);
+    w[0] = __byte_perm(static_cast<uint32_t>(in) << 16, w[0], 0x5432);
+  }
+  // element k <- element k+1; element V-1 <- `in` (the next cell)
+  __device__ void shift_down(uint16_t in) {
+#pragma unroll
+    for (int k = 0; k < kW - 1; ++k) w[k] = __byte_perm(w[k], w[k + 1], 0x5432);
+    w[kW - 1] = __byte_perm(w[kW - 1], static_cast<uint32_t>(in), 0x5432);
+  }
+  __device__ uint16_t last() const { return static_cast<uint16_t>(w[kW - 1] >> 16); }
+  __device__ uint16_t first() const { return static_cast<uint16_t>(w[0] & 0xffffu); }
+};
+
+template <int V> struct Strip<LBM_F16S, V> : Strip16<LBM_F16S, V> {};
+template <int V> struct Strip<LBM_BF16S, V> : Strip16<LBM_BF16S, V> {};
+
+// 32/64-bit storage: one register (pair) per element.
+template <typename E, int V> struct StripW {
+  E w[V];
+  __device__ void load(const E *p) {
+    constexpr int kBytes = V * int(sizeof(E));
+    if constexpr (kBytes == 16) {
+      if constexpr (sizeof(E) == 4) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+      } else {
+        double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        w[0] = v.x; w[1] = v.y;
+      }
+    } else if constexpr (kBytes == 8) {
+      if constexpr (sizeof(E) == 4) {
+        float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        w[0] = v.x; w[1] = v.y;
+      } else {
+        w[0] = __ldg(p);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) w[k] = __ldg(p + k);
+    }
+  }
+  __device__ void store(E *p) const {
+    constexpr int kBytes = V * int(sizeof(E));
+    if constexpr (kBytes == 16) {
+      if constexpr (sizeof(E) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(w[0], w[1], w[2], w[3]);
+      } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(w[0], w[1]);
+      }
+    } else if constexpr (kBytes == 8 && sizeof(E) == 4) {
+      *reinterpret_cast<float2 *>(p) = make_float2(w[0], w[1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) p[k] = w[k];
+    }
+  }
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < V; ++k) w[k] = E(0);
+  }
+  __device__ E get(int k) const { return w[k]; }
+  __device__ void set(int k, E e) { w[k] = e; }
+  __device__ void shift_up(E in) {
+#pragma unroll
+    for (int k = V - 1; k > 0; --k) w[k] = w[k - 1];
+    w[0] = in;
+  }
+  __device__ void shift_down(E in) {
+#pragma unroll
+    for (int k = 0; k < V - 1; ++k) w[k] = w[k + 1];
+    w[V - 1] = in;
+  }
+  __device__ E last() const { return w[V - 1]; }
+  __device__ E first() const { return w[0]; }
+};
+
+template <int V> struct Strip<LBM_F32, V> : StripW<float, V> {};
+template <int V> struct Strip<LBM_F64, V> : StripW<double, V> {};
+
+template <typename E> __device__ __forceinline__ E shfl_up1(E v) {
+  if constexpr (sizeof(E) == 2) {
+    return static_cast<E>(__shfl_up_sync(0xffffffffu, static_cast<uint32_t>(v), 1));
+  } else {
+    return __shfl_up_sync(0xffffffffu, v, 1);
+  }
+}
+template <typename E> __device__ __forceinline__ E shfl_down1(E v) {
+  if constexpr (sizeof(E) == 2) {
+    return static_cast<E>(__shfl_down_sync(0xffffffffu, static_cast<uint32_t>(v), 1));
+  } else {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+  }
+}
+
+// Decode element k of every direction into compute space.
+template <int S, int V>
+__device__ __forceinline__ void decode_cell(const Strip<S, V> (&v)[kQ], int k,
+                                            typename Codec<S>::T (&x)[kQ]) {
+#pragma unroll
+  for (int a = 0; a < kQ; ++a) x[a] = Codec<S>::dec(v[a].get(k));
+}
+
+template <int S, int V>
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
+  using Cd = Codec<S>;
+  using E = typename Cd::E;
+  using T = typename Cd::T;
+  constexpr bool SHIFT = Cd::kShift;
+  constexpr int kStrip = 32 * V;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int ntiles = args.ctr->ntiles;
+  const long long run_base = args.ctr->run_base;
+  int unstable = 0;
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileDev tile = args.tiles[t];
+    const DomDev &D = args.doms[tile.dom];
+    const DomDyn dy = args.dyn[tile.dom];
+    const long long n = dy.step0 + run_base + s;
+    if (n >= dy.step_end) continue;
+    const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
+    const E *__restrict__ src = static_cast<const E *>(D.lat[par]);
+    E *__restrict__ dst = static_cast<E *>(D.lat[par ^ 1]);
+    const int nx = D.nx, ny = D.ny, pitch = D.pitch;
+    const int x0 = tile.x0;
+    const int xl = x0 + lane * V;
+    const bool lane_on = xl < nx;
+    const bool west_edge = (x0 == 0);
+    const bool east_edge = (x0 + kStrip >= nx);
+    const bool west_inlet = D.west == LBM_INLET_EQ;
+    const bool east_out = D.east == LBM_OUTFLOW_ZG;
+    const CellConst<T> C = make_const<T>(D);
+    T ghost[kQ];
+    if (west_edge && west_inlet) {
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) ghost[a] = T(D.ghost[a]);
+    }
+    const size_t plane = static_cast<size_t>(ny) * pitch;
+
+    for (int r = 0; r < args.rows; ++r) {
+      const int j = tile.y0 + warp * args.rows + r;
+      if (j >= ny) break;
+      Strip<S, V> v[kQ];
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) {
+        // y rule for this direction (warp-uniform)
+        const int ey = ey_of(a);
+        int sy = j - ey, sa = a;
+        if (sy < 0) {
+          if (D.south == LBM_FREE_SLIP) { sy = 0; sa = reflect_y(a); }
+          else sy += ny;
+        } else if (sy > ny - 1) {
+          if (D.north == LBM_FREE_SLIP) { sy = ny - 1; sa = reflect_y(a); }
+          else sy -= ny;
+        }
+        const E *row = src + sa * plane + static_cast<size_t>(sy) * pitch;
+        if (lane_on) v[a].load(row + xl);
+        else v[a].zero();
+        const int ex = ex_of(a);
+        if (ex == 1) {
+          // source i - 1: previous lane's last element; lane 0 reads x0 - 1
+          E in = shfl_up1<E>(v[a].last());
+          if (lane == 0) {
+            if (!west_edge) in = row[x0 - 1];
+            else if (!west_inlet) in = row[nx - 1];  // periodic
+            // inlet: replaced by the ghost after decoding
+          }
+          v[a].shift_up(in);
+        } else if (ex == -1) {
+          // source i + 1: next lane's first element; lane 31 reads x0 + 32V
+          E keep = E(0);
+          if (east_edge) {
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+              if (xl + k == nx - 1) keep = v[a].get(k);
+          }
+          E in = shfl_down1<E>(v[a].first());
+          if (lane == 31 && !east_edge) in = row[x0 + kStrip];
+          v[a].shift_down(in);
+          if (east_edge) {
+            const E fix = east_out ? keep : row[0];  // zero gradient or periodic
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+              if (xl + k == nx - 1) v[a].set(k, fix);
+          }
+        }
+      }
+
+      // body ids of the V cells
+      uint8_t b[V];
+      {
+        const uint8_t *mrow = D.mask + static_cast<size_t>(j) * pitch + xl;
+        if (lane_on) {
+          if constexpr (V == 8) {
+            uint2 mw = __ldg(reinterpret_cast<const uint2 *>(mrow));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = (mw.x >> (8 * k)) & 0xff;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[4 + k] = (mw.y >> (8 * k)) & 0xff;
+          } else if constexpr (V == 4) {
+            uint32_t mw = __ldg(reinterpret_cast<const unsigned int *>(mrow));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = (mw >> (8 * k)) & 0xff;
+          } else if constexpr (V == 2) {
+            uint32_t mw = __ldg(reinterpret_cast<const unsigned short *>(mrow));
+            b[0] = mw & 0xff;
+            b[1] = (mw >> 8) & 0xff;
+          } else {
+            b[0] = __ldg(mrow);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < V; ++k) b[k] = 0;
+        }
+      }
+      bool any_solid_lane = false;
+#pragma unroll
+      for (int k = 0; k < V; ++k) any_solid_lane |= (b[k] != 0);
+      const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
+
+      // update the V cells in place
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        T x[kQ];
+        decode_cell<S, V>(v, k, x);
+        if (k == 0 && west_edge && west_inlet && lane == 0) {
+          x[1] = ghost[1];
+          x[5] = ghost[5];
+          x[8] = ghost[8];
+        }
+        NodeMacro<T> m;
+        if (any_solid) {
+          T uox = T(0), uoy = T(0);
+          const bool solid = b[k] != 0;
+          if (solid) body_velocity<T>(D, b[k], xl + k, j, uox, uoy);
+          m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
+          collide<T, SHIFT, true>(x, m, C);
+        } else {
+          m = node_macro<T, SHIFT, false>(x, C, false, T(0), T(0));
+          collide<T, SHIFT, false>(x, m, C);
+        }
+        const bool valid = xl + k < nx;
+        if (valid && !(m.rho > T(0.01) && m.rho < T(100))) unstable = 1;
+        if (east_edge && !valid) {
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) x[a] = T(0);  // keep the row padding at zero
+        }
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
+      }
+      if (lane_on) {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a)
+          v[a].store(dst + a * plane + static_cast<size_t>(j) * pitch + xl);
+      }
+    }
+    if (__any_sync(0xffffffffu, unstable)) {
+      if (lane == 0) atomicOr(D.status, 1);
+      unstable = 0;
+    }
+  }
+}
+
+template <int S, int V>
+cudaError_t launch_sweep_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s) {
+  sweep_kernel<S, V><<<grid, warps * 32, 0, st>>>(a, s);
+  return cudaGetLastError();
+}
+
+template <int S, int V> int max_blocks_t(int warps) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<S, V>, warps * 32, 0) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+}  // namespace lbm

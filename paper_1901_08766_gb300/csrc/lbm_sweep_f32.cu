@@ -1,0 +1,19 @@
+// Sweep instantiations for LBM_F32 storage (cells per thread 2 and 4).
+#include "lbm_sweep.cuh"
+
+namespace lbm {
+
+cudaError_t launch_sweep_f32(int vec, int grid, int warps, cudaStream_t st, const SweepArgs &a,
+                               int s) {
+  if (vec == 2) return launch_sweep_t<LBM_F32, 2>(grid, warps, st, a, s);
+  if (vec == 4) return launch_sweep_t<LBM_F32, 4>(grid, warps, st, a, s);
+  return cudaErrorInvalidValue;
+}
+
+int max_blocks_f32(int vec, int warps) {
+  if (vec == 2) return max_blocks_t<LBM_F32, 2>(warps);
+  if (vec == 4) return max_blocks_t<LBM_F32, 4>(warps);
+  return 0;
+}
+
+}  // namespace lbm

@@ -1,0 +1,61 @@
+"""Test-side storage conversions: FP64 populations to and from the library's stored
+types (F64, F32, F16S, BF16S), with the shift by w_alpha * rho0 for the 16-bit types.
+
+The shift weights come from the oracle's own constants. Encoding is the test's choice
+of inputs (any stored values are valid); decoding is exact, so the oracle receives
+exactly the state the GPU starts from.
+"""
+import numpy as np
+
+import oracle
+
+W = oracle.W[:, None, None]
+
+
+def f32_to_bf16_bits(x):
+    """Round-to-nearest-even of float32 values to bfloat16, as uint16 bits."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return rounded.astype(np.uint16)
+
+
+def bf16_bits_to_f64(bits):
+    return (np.asarray(bits, dtype=np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def encode(g, storage, rho0=1.0):
+    """FP64 populations [9, ny, nx] -> stored array in the library's layout."""
+    if storage == "f64":
+        return np.ascontiguousarray(g, dtype=np.float64)
+    if storage == "f32":
+        return np.ascontiguousarray(g, dtype=np.float32)
+    s = g - W * rho0
+    if storage == "f16s":
+        return np.ascontiguousarray(s.astype(np.float32).astype(np.float16))
+    if storage == "bf16s":
+        return f32_to_bf16_bits(s.astype(np.float32))
+    raise KeyError(storage)
+
+
+def decode(raw, storage, rho0=1.0):
+    """Stored array -> FP64 populations (exact)."""
+    if storage in ("f64", "f32"):
+        return np.asarray(raw, dtype=np.float64)
+    if storage == "f16s":
+        return np.asarray(raw, dtype=np.float16).astype(np.float64) + W * rho0
+    if storage == "bf16s":
+        return bf16_bits_to_f64(raw) + W * rho0
+    raise KeyError(storage)
+
+
+def stored_ulp(values_shifted, storage):
+    """Spacing of the stored type at the given (shifted) magnitudes."""
+    a = np.abs(np.asarray(values_shifted, dtype=np.float64))
+    if storage == "f16s":
+        return np.spacing(a.astype(np.float16)).astype(np.float64)
+    if storage == "bf16s":
+        e = np.floor(np.log2(np.maximum(a, 2.0 ** -126)))
+        return 2.0 ** (e - 7)
+    if storage == "f32":
+        return np.spacing(a.astype(np.float32)).astype(np.float64)
+    return np.spacing(a)

@@ -1,0 +1,134 @@
+"""Batched uneven domains: results do not depend on the batch composition, the tile
+shape, graph replay or the autotuner; admission respects the memory budget."""
+import numpy as np
+import pytest
+
+import codec
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _specs():
+    a = synth.parity_case("channel_256x128")
+    b = synth.parity_case("mixed_edges_61x47")
+    c = synth.batched_domains(3)[2]
+    c = dict(c, nx=420, ny=210, shapes=[synth._circle(1, 105, 105, 20), synth._circle(2, 200, 95, 20)],
+             bodies=[synth._body(105, 105, 40), synth._body(200, 95, 40)])
+    return [a, b, c]
+
+
+@pytest.mark.parametrize("storage", ["f16s", "f32"])
+def test_batch_equals_alone(lbm, storage):
+    specs = _specs()
+    steps = [300, 170, 250]  # uneven step targets: domains finish mid-run
+    batch = lbm.Batch(storage, max_domains=8, graph_steps=16)
+    slots = [batch.admit(s, nsteps=n) for s, n in zip(specs, steps)]
+    forces = {k: [] for k in slots}
+    while True:
+        ran = batch.run(64)
+        for k in slots:
+            f, _ = batch.poll(k)
+            forces[k].append(f)
+        if ran == 0:
+            break
+    for k, s, n in zip(slots, specs, steps):
+        assert batch.steps_done(k) == n
+        alone = lbm.Domain(s, storage=storage)
+        fa = alone.run(n)
+        assert np.array_equal(np.concatenate(forces[k]), fa)
+        pa, pb = alone.get_populations(), batch.get_populations(k)
+        assert np.array_equal(pa, pb) if storage == "f32" else np.array_equal(pa.view(np.uint16), pb.view(np.uint16))
+        alone.close()
+    batch.close()
+
+
+def test_tile_shape_and_graphs_do_not_change_results(lbm):
+    spec = synth.parity_case("channel_256x128")
+    g0 = codec.encode(synth.random_populations(8, 256, 128, 0.05), "f16s")
+    ref = None
+    for vec, warps, rows, graph in [(8, 8, 2, 16), (4, 4, 1, 0), (8, 16, 4, 7), (4, 2, 3, 32)]:
+        batch = lbm.Batch("f16s", max_domains=2, graph_steps=graph)
+        k = batch.admit(spec, nsteps=100)
+        batch.set_tile(vec, warps, rows)
+        batch.set_populations(k, g0)
+        while batch.run(45):
+            pass
+        f, done = batch.poll(k)
+        out = (batch.get_populations(k).view(np.uint16), f)
+        assert done
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        batch.close()
+
+
+def test_autotune_keeps_state_and_results(lbm):
+    specs = _specs()
+    batch = lbm.Batch("f16s", max_domains=4, graph_steps=16)
+    slots = [batch.admit(s, nsteps=60) for s in specs]
+    batch.run(20)
+    before = [batch.get_populations(k).view(np.uint16).copy() for k in slots]
+    us = batch.autotune(reps=3)
+    assert us > 0
+    after = [batch.get_populations(k).view(np.uint16) for k in slots]
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    vec, warps, rows = batch.get_tile()
+    assert vec in (4, 8) and 1 <= warps <= 16 and 1 <= rows <= 16
+    batch.run(40)
+    ref = lbm.Domain(specs[0], storage="f16s")
+    ref.step(60)
+    assert np.array_equal(ref.get_populations().view(np.uint16), batch.get_populations(slots[0]).view(np.uint16))
+    ref.close()
+    batch.close()
+
+
+def test_admission_budget_and_eviction(lbm):
+    spec = synth.parity_case("channel_97x61")
+    need = lbm.domain_bytes(spec, "f16s")
+    batch = lbm.Batch("f16s", max_domains=8, hbm_budget=int(2.5 * need) + 4096)
+    a = batch.admit(spec, nsteps=10)
+    b = batch.admit(spec, nsteps=10)
+    assert batch.try_admit(spec, nsteps=10) is None  # over budget
+    batch.run(10)
+    f, done = batch.poll(a)
+    assert done and f.shape == (10, 2, 2)
+    batch.evict(a)
+    c = batch.try_admit(spec, nsteps=5)
+    assert c is not None
+    assert batch.run(100) == 5  # only the new domain still has steps to run
+    info = batch.info()
+    assert info["resident"] == 2 and info["kernel_launches"] > 0
+    batch.close()
+
+
+def test_full_size_batch_one_step_sampled_parity(lbm):
+    # The batched workload at full size in the benchmark's launch configuration: every
+    # domain starts from seeded FP16-shifted populations and takes one step on the GPU;
+    # each domain's result is compared with the oracle's step of the same decoded state.
+    specs = synth.batched_domains(64)
+    batch = lbm.Batch("f16s", max_domains=64, graph_steps=32)
+    sample = range(0, 64, 9)  # domains of every size class; the others start at rest flow
+    slots = []
+    for d, s in enumerate(specs):
+        k = batch.admit(s, nsteps=1)
+        if d in sample:
+            batch.set_populations(k, codec.encode(
+                synth.random_populations(1000 + d, s["nx"], s["ny"], 0.05), "f16s"))
+        slots.append(k)
+    batch.autotune(reps=3)
+    batch.run(1)
+    for d in sample:
+        s = specs[d]
+        raw0 = codec.encode(synth.random_populations(1000 + d, s["nx"], s["ny"], 0.05), "f16s")
+        ora = oracle.Domain(s, g=codec.decode(raw0, "f16s"))
+        f_ora = ora.run(1)
+        got = codec.decode(batch.get_populations(slots[d]), "f16s")
+        ulp = codec.stored_ulp(ora.g - codec.W, "f16s")
+        assert np.all(np.abs(got - ora.g) <= ulp + 2e-8)
+        f_gpu, _ = batch.poll(slots[d])
+        assert np.allclose(f_gpu, f_ora, rtol=1e-4, atol=1e-5)
+    batch.close()
