@@ -198,7 +198,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     lbm.load()
-    specs = synth.batched_domains(64)
+    specs = synth.batched_domains(64)[: args.domains]
     cells = sum(s["nx"] * s["ny"] for s in specs)
     stream = torch.cuda.Stream()
     nsteps_total = args.warmup + args.steps + args.profile_steps + 10
@@ -206,9 +206,11 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_steps, stream=stream)
         slots = [batch.admit(s, nsteps=nsteps_total, force_capacity=nsteps_total + 8) for s in specs]
-        tune_us = batch.autotune(reps=5) if not args.no_autotune else None
+        if args.tile:
+            batch.set_tile(*[int(x) for x in args.tile.split(",")])
+        tune_us = batch.autotune(reps=5) if not (args.no_autotune or args.tile) else None
         tile = batch.get_tile()
-        args.tile = tile
+        args.tuned_tile = tile
         batch.run(args.warmup)
         for k in slots:
             batch.poll(k)
@@ -292,8 +294,8 @@ def measure_e2e(lbm, torch, specs, args):
         t0 = time.perf_counter()
         batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_steps, stream=stream)
         slots = [batch.admit(s, nsteps=steps, force_capacity=steps + 8) for s in specs]
-        if getattr(args, "tile", None):
-            batch.set_tile(*args.tile)
+        if getattr(args, "tuned_tile", None):
+            batch.set_tile(*args.tuned_tile)
         batch.run(steps)
         nbytes_out = 0
         for k in slots:
@@ -348,6 +350,8 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=32)
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", default="", help="vec,warps,rows: fixed sweep tile, no autotune")
+    ap.add_argument("--domains", type=int, default=64, help="first N domains of the set")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e, plain and CPU legs")
     args = ap.parse_args()

@@ -163,9 +163,12 @@ cudaError_t launch_build_solid(cudaStream_t st, const uint8_t *mask, int nx, int
 }
 
 // ---- body forces -------------------------------------------------------------------------
-// One block per (slot, body) item: each thread accumulates -F_VP of a strided subset of
-// the body's nodes in FP64 (same pull and node arithmetic as the sweep), then a fixed
-// shuffle + shared-memory tree: the sum order depends only on the node list.
+// The sweep of step n+1 writes F_VP of every solid node (Eq. force-density) to the
+// domain's F_VP field; this kernel, launched after it, sums -F_VP over each body's
+// nodes (Sec. 3, drag and lift sums, read as the force on the body) into the force
+// ring. One block per (slot, body) item: each thread accumulates a strided subset of
+// the body's row-major node list in FP64, then a fixed shuffle + shared-memory tree,
+// so the sum order depends only on the node list, not on the tiling or the batch.
 
 constexpr int kForceThreads = 256;
 
@@ -173,8 +176,7 @@ template <int S>
 __global__ void __launch_bounds__(kForceThreads)
 forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
               int s) {
-  using Cd = Codec<S>;
-  using T = typename Cd::T;
+  using T = typename Codec<S>::T;
   const int nitems = ctr->nforce;
   const long long run_base = ctr->run_base;
   __shared__ double red[2][kForceThreads / 32];
@@ -182,25 +184,16 @@ forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, con
     const ForceItem item = items[it];
     const DomDev &D = doms[item.dom];
     const DomDyn dy = dyn[item.dom];
-    const long long n = dy.step0 + run_base + s;  // this launch computes step n + 1
+    const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
     if (n >= dy.step_end || D.force_every <= 0) continue;
     if ((n + 1) % D.force_every != 0) continue;
-    const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
-    const void *src = D.lat[par];
-    const CellConst<T> C = make_const<T>(D);
+    const T *fv = static_cast<const T *>(D.fvp);
     const int beg = D.solid_off[item.body - 1], end = D.solid_off[item.body];
     double fx = 0.0, fy = 0.0;
     for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
-      const int lin = D.solid[q];
-      const int j = lin / D.pitch, i = lin - j * D.pitch;
-      T x[kQ];
-#pragma unroll
-      for (int a = 0; a < kQ; ++a) x[a] = pull_scalar<S>(D, src, a, i, j);
-      T uox, uoy;
-      body_velocity<T>(D, item.body, i, j, uox, uoy);
-      const NodeMacro<T> m = node_macro<T, Cd::kShift, true>(x, C, true, uox, uoy);
-      fx -= double(m.fx);
-      fy -= double(m.fy);
+      const size_t lin = static_cast<size_t>(D.solid[q]);
+      fx -= double(fv[2 * lin]);
+      fy -= double(fv[2 * lin + 1]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -259,7 +252,7 @@ __global__ void moments_kernel(const DomDev *dom, int parity, double *rho, doubl
   const int j = blockIdx.y;
   if (i >= D.nx || j >= D.ny) return;
   const void *src = D.lat[parity];
-  const CellConst<T> C = make_const<T>(D);
+  const CellConst<T> &C = cell_const<T>(D);
   T x[kQ];
 #pragma unroll
   for (int a = 0; a < kQ; ++a) x[a] = pull_scalar<S>(D, src, a, i, j);

@@ -13,9 +13,8 @@
 
 namespace lbm {
 
-// D2Q9 velocity set, Eq. (D2Q9): rest, axes at (alpha-1) pi/2, diagonals at (2 alpha-9) pi/4.
-__device__ __constant__ static const int kEx[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__device__ __constant__ static const int kEy[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+// D2Q9 velocity set, Eq. (D2Q9): alpha = 0 rest, 1..4 axes at (alpha-1) pi/2, 5..8
+// diagonals at (2 alpha-9) pi/4; ex_of/ey_of give the components.
 
 // Reflection of a direction across a horizontal wall (e_y -> -e_y): free-slip edges.
 __host__ __device__ constexpr int reflect_y(int a) {
@@ -79,43 +78,12 @@ template <> struct Codec<LBM_BF16S> {
 
 // ---- per-domain constants in compute precision -----------------------------------------
 
-template <typename T> struct CellConst {
-  T omp, omm;        // omega+, omega-
-  T hp, hm;          // omega+/2, omega-/2
-  T kp, km;          // 1 - omega+/2, 1 - omega-/2
-  T one_m_omp;       // 1 - omega+
-  T inv_2eta1;       // 1 / (2 eta + 1)
-  T rho0;
-  T pw0, pw1, pw2;   // omega+ * w for the rest, axis and diagonal classes
-  T mw1, mw2;        // 3 omega- * w for the axis and diagonal classes
-  T kw0, kw1, kw2;   // (1 - omega+/2) * w per class (Guo symmetric part)
-  T qw1, qw2;        // 3 (1 - omega-/2) * w per class (Guo antisymmetric part)
-};
-
-template <typename T> __device__ __forceinline__ CellConst<T> make_const(const DomDev &d) {
-  CellConst<T> c;
-  const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
-  const double op = d.omega_p, om = d.omega_m;
-  c.omp = T(op);
-  c.omm = T(om);
-  c.hp = T(0.5 * op);
-  c.hm = T(0.5 * om);
-  c.kp = T(1.0 - 0.5 * op);
-  c.km = T(1.0 - 0.5 * om);
-  c.one_m_omp = T(1.0 - op);
-  c.inv_2eta1 = T(d.inv_2eta1);
-  c.rho0 = T(d.rho0);
-  c.pw0 = T(op * w0);
-  c.pw1 = T(op * w1);
-  c.pw2 = T(op * w2);
-  c.mw1 = T(3.0 * om * w1);
-  c.mw2 = T(3.0 * om * w2);
-  c.kw0 = T((1.0 - 0.5 * op) * w0);
-  c.kw1 = T((1.0 - 0.5 * op) * w1);
-  c.kw2 = T((1.0 - 0.5 * op) * w2);
-  c.qw1 = T(3.0 * (1.0 - 0.5 * om) * w1);
-  c.qw2 = T(3.0 * (1.0 - 0.5 * om) * w2);
-  return c;
+template <typename T> __device__ __forceinline__ const CellConst<T> &cell_const(const DomDev &d);
+template <> __device__ __forceinline__ const CellConst<float> &cell_const<float>(const DomDev &d) {
+  return d.cf;
+}
+template <> __device__ __forceinline__ const CellConst<double> &cell_const<double>(const DomDev &d) {
+  return d.cd;
 }
 
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
@@ -224,7 +192,7 @@ __device__ __forceinline__ typename Codec<S>::T pull_scalar(const DomDev &d, con
   using E = typename Cd::E;
   int sx = i - ex_of(a), sy = j - ey_of(a), src = a;
   if (sx < 0) {
-    if (d.west == LBM_INLET_EQ) return typename Cd::T(d.ghost[a]);
+    if (d.west == LBM_INLET_EQ) return cell_const<typename Cd::T>(d).ghost[a];
     sx += d.nx;
   } else if (sx > d.nx - 1) {
     sx = (d.east == LBM_OUTFLOW_ZG) ? d.nx - 1 : sx - d.nx;

@@ -15,6 +15,20 @@ constexpr int kQ = 9;
 constexpr int kPitchAlign = 64;  // row pitch in elements is a multiple of this
 constexpr int kMaxBodies = 255;
 
+// Per-domain constants of the collision in one precision (filled on the host).
+template <typename T> struct CellConst {
+  T omp, omm;        // omega+ = 1/tau_s, omega- = 1/tau_a
+  T hp, hm;          // omega+/2, omega-/2
+  T one_m_omp;       // 1 - omega+
+  T inv_2eta1;       // 1 / (2 eta + 1)
+  T rho0;
+  T pw0, pw1, pw2;   // omega+ * w for the rest, axis and diagonal classes
+  T mw1, mw2;        // 3 omega- * w for the axis and diagonal classes
+  T kw0, kw1, kw2;   // (1 - omega+/2) * w per class (Guo symmetric part)
+  T qw1, qw2;        // 3 (1 - omega-/2) * w per class (Guo antisymmetric part)
+  T ghost[kQ];       // inlet populations in compute space (shifted if storage is)
+};
+
 // Per-domain static description, resident in device memory (one per batch slot).
 struct DomDev {
   void *lat[2];            // lattice A/B: [9][ny][pitch] elements of the storage type
@@ -22,6 +36,7 @@ struct DomDev {
   const double *bodies;    // [nbodies][5]: cx, cy, vx, vy, omega
   const int32_t *solid;    // solid nodes (j * pitch + i), grouped by body, row-major
   const int32_t *solid_off;// [nbodies + 1] offsets into solid
+  void *fvp;               // F_VP of solid nodes, [ny][pitch] pairs in compute precision
   double *ring;            // force ring [cap][nbodies][2]
   int32_t *status;         // bit 0: unstable
   int32_t nx, ny, pitch;
@@ -31,6 +46,8 @@ struct DomDev {
   double inv_2eta1;         // 1 / (2 eta + 1)
   double rho0;
   double ghost[kQ];         // inlet populations in compute space (shifted if storage is)
+  CellConst<float> cf;      // collision constants for FP32 compute
+  CellConst<double> cd;     // collision constants for FP64 compute
 };
 
 // Per-domain dynamic state, uploaded at the start of each batch run.
@@ -80,6 +97,7 @@ bool sweep_vec_supported(int storage, int vec);
 cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *doms,
                           const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
                           int s);
+void fill_cell_const(DomDev &d);
 cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
 cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
                              const ShapeDev *shapes, int nshapes);

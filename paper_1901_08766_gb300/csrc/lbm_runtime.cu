@@ -74,7 +74,7 @@ struct Alloc {
 // Fixed part of a domain's device footprint (populations x2, mask, bodies, offsets,
 // force ring, status word), each piece 256-byte aligned.
 struct Layout {
-  size_t lat_bytes, mask_off, bodies_off, off_off, ring_off, status_off, total;
+  size_t lat_bytes, mask_off, fvp_off, bodies_off, off_off, ring_off, status_off, total;
 };
 
 Layout layout_of(const lbm_params &p, int nbodies) {
@@ -86,6 +86,8 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   size_t o = 2 * L.lat_bytes;
   L.mask_off = o;
   o += align_up(static_cast<size_t>(p.ny) * pitch, 256);
+  L.fvp_off = o;
+  o += align_up(static_cast<size_t>(p.ny) * pitch * 2 * (p.storage == LBM_F64 ? 8 : 4), 256);
   L.bodies_off = o;
   o += align_up(sizeof(double) * 5 * std::max(1, nbodies), 256);
   L.off_off = o;
@@ -136,6 +138,37 @@ struct Slot {
 };
 
 }  // namespace
+
+// Collision constants of a domain in FP32 and FP64 (per-class products of the relaxation
+// rates with the D2Q9 weights, the penalization factor and the inlet ghost).
+template <typename T> void fill_const(CellConst<T> &c, const DomDev &d) {
+  const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
+  const double op = d.omega_p, om = d.omega_m;
+  c.omp = T(op);
+  c.omm = T(om);
+  c.hp = T(0.5 * op);
+  c.hm = T(0.5 * om);
+  c.one_m_omp = T(1.0 - op);
+  c.inv_2eta1 = T(d.inv_2eta1);
+  c.rho0 = T(d.rho0);
+  c.pw0 = T(op * w0);
+  c.pw1 = T(op * w1);
+  c.pw2 = T(op * w2);
+  c.mw1 = T(3.0 * om * w1);
+  c.mw2 = T(3.0 * om * w2);
+  c.kw0 = T((1.0 - 0.5 * op) * w0);
+  c.kw1 = T((1.0 - 0.5 * op) * w1);
+  c.kw2 = T((1.0 - 0.5 * op) * w2);
+  c.qw1 = T(3.0 * (1.0 - 0.5 * om) * w1);
+  c.qw2 = T(3.0 * (1.0 - 0.5 * om) * w2);
+  for (int a = 0; a < kQ; ++a) c.ghost[a] = T(d.ghost[a]);
+}
+
+void fill_cell_const(DomDev &d) {
+  fill_const(d.cf, d);
+  fill_const(d.cd, d);
+}
+
 }  // namespace lbm
 
 using namespace lbm;
@@ -473,6 +506,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.bodies = bod;
   int32_t *off = reinterpret_cast<int32_t *>(base + L.off_off);
   D.solid_off = off;
+  D.fvp = base + L.fvp_off;
   D.ring = reinterpret_cast<double *>(base + L.ring_off);
   D.status = reinterpret_cast<int32_t *>(base + L.status_off);
   D.nx = p->nx;
@@ -503,6 +537,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
       D.ghost[a] = shift ? dev : p->rho0 * w[a] + dev;
     }
   }
+  fill_cell_const(D);
   cudaStream_t st = b->st;
   auto bail = [&](lbm_status r) {
     cudaStreamSynchronize(st);
@@ -575,6 +610,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   ADM_CUDA(launch_init(p->storage, st, D.lat[0], p->nx, p->ny, s.pitch, p->rho0, p->u0_x, p->u0_y));
   ADM_CUDA(cudaMemsetAsync(D.lat[1], 0, L.lat_bytes, st));
   ADM_CUDA(cudaMemsetAsync(D.status, 0, sizeof(int32_t), st));
+  ADM_CUDA(cudaMemsetAsync(D.fvp, 0, L.bodies_off - L.fvp_off, st));
   if (p->force_every > 0)
     ADM_CUDA(cudaMemsetAsync(D.ring, 0, sizeof(double) * 2 * std::max(1, nbodies) * s.p.force_capacity, st));
   ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));

@@ -171,7 +171,6 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
   constexpr int kStrip = 32 * V;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
   const int ntiles = args.ctr->ntiles;
   const long long run_base = args.ctr->run_base;
   int unstable = 0;
@@ -193,80 +192,70 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
     const bool east_edge = (x0 + kStrip >= nx);
     const bool west_inlet = D.west == LBM_INLET_EQ;
     const bool east_out = D.east == LBM_OUTFLOW_ZG;
-    const CellConst<T> C = make_const<T>(D);
-    T ghost[kQ];
-    if (west_edge && west_inlet) {
-#pragma unroll
-      for (int a = 0; a < kQ; ++a) ghost[a] = T(D.ghost[a]);
-    }
+    const bool south_slip = D.south == LBM_FREE_SLIP;
+    const bool north_slip = D.north == LBM_FREE_SLIP;
+    const CellConst<T> &C = cell_const<T>(D);
+    // strip-end columns read by the end lanes (or -1: nothing to read)
+    const int col_left = west_edge ? (west_inlet ? -1 : nx - 1) : x0 - 1;
+    const int col_right = east_edge ? (east_out ? -1 : 0) : x0 + kStrip;
+    // the lane holding column nx-1 (east edge tiles) and its element index
+    const int k_last = nx - 1 - xl;
+    const bool has_last = east_edge && k_last >= 0 && k_last < V;
     const size_t plane = static_cast<size_t>(ny) * pitch;
 
     for (int r = 0; r < args.rows; ++r) {
       const int j = tile.y0 + warp * args.rows + r;
       if (j >= ny) break;
-      Strip<S, V> v[kQ];
+      // ---- phase 1: every load of the row ------------------------------------------
+      const E *row[kQ];
 #pragma unroll
       for (int a = 0; a < kQ; ++a) {
-        // y rule for this direction (warp-uniform)
+        // y rule for this direction (warp-uniform): periodic wrap or free-slip mirror
         const int ey = ey_of(a);
         int sy = j - ey, sa = a;
         if (sy < 0) {
-          if (D.south == LBM_FREE_SLIP) { sy = 0; sa = reflect_y(a); }
+          if (south_slip) { sy = 0; sa = reflect_y(a); }
           else sy += ny;
         } else if (sy > ny - 1) {
-          if (D.north == LBM_FREE_SLIP) { sy = ny - 1; sa = reflect_y(a); }
+          if (north_slip) { sy = ny - 1; sa = reflect_y(a); }
           else sy -= ny;
         }
-        const E *row = src + sa * plane + static_cast<size_t>(sy) * pitch;
-        if (lane_on) v[a].load(row + xl);
+        row[a] = src + sa * plane + static_cast<size_t>(sy) * pitch;
+      }
+      Strip<S, V> v[kQ];
+      E end_in[kQ];
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) {
+        if (lane_on) v[a].load(row[a] + xl);
         else v[a].zero();
         const int ex = ex_of(a);
+        end_in[a] = E(0);
         if (ex == 1) {
-          // source i - 1: previous lane's last element; lane 0 reads x0 - 1
-          E in = shfl_up1<E>(v[a].last());
-          if (lane == 0) {
-            if (!west_edge) in = row[x0 - 1];
-            else if (!west_inlet) in = row[nx - 1];  // periodic
-            // inlet: replaced by the ghost after decoding
-          }
-          v[a].shift_up(in);
+          if (lane == 0 && col_left >= 0) end_in[a] = __ldg(row[a] + col_left);
         } else if (ex == -1) {
-          // source i + 1: next lane's first element; lane 31 reads x0 + 32V
-          E keep = E(0);
-          if (east_edge) {
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-              if (xl + k == nx - 1) keep = v[a].get(k);
-          }
-          E in = shfl_down1<E>(v[a].first());
-          if (lane == 31 && !east_edge) in = row[x0 + kStrip];
-          v[a].shift_down(in);
-          if (east_edge) {
-            const E fix = east_out ? keep : row[0];  // zero gradient or periodic
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-              if (xl + k == nx - 1) v[a].set(k, fix);
+          if (!east_edge) {
+            if (lane == 31) end_in[a] = __ldg(row[a] + col_right);
+          } else if (has_last && col_right >= 0) {
+            end_in[a] = __ldg(row[a] + col_right);  // periodic east edge: column 0
           }
         }
       }
-
-      // body ids of the V cells
       uint8_t b[V];
       {
         const uint8_t *mrow = D.mask + static_cast<size_t>(j) * pitch + xl;
         if (lane_on) {
           if constexpr (V == 8) {
-            uint2 mw = __ldg(reinterpret_cast<const uint2 *>(mrow));
+            const uint2 mw = __ldg(reinterpret_cast<const uint2 *>(mrow));
 #pragma unroll
             for (int k = 0; k < 4; ++k) b[k] = (mw.x >> (8 * k)) & 0xff;
 #pragma unroll
             for (int k = 0; k < 4; ++k) b[4 + k] = (mw.y >> (8 * k)) & 0xff;
           } else if constexpr (V == 4) {
-            uint32_t mw = __ldg(reinterpret_cast<const unsigned int *>(mrow));
+            const uint32_t mw = __ldg(reinterpret_cast<const unsigned int *>(mrow));
 #pragma unroll
             for (int k = 0; k < 4; ++k) b[k] = (mw >> (8 * k)) & 0xff;
           } else if constexpr (V == 2) {
-            uint32_t mw = __ldg(reinterpret_cast<const unsigned short *>(mrow));
+            const uint32_t mw = __ldg(reinterpret_cast<const unsigned short *>(mrow));
             b[0] = mw & 0xff;
             b[1] = (mw >> 8) & 0xff;
           } else {
@@ -277,20 +266,48 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
           for (int k = 0; k < V; ++k) b[k] = 0;
         }
       }
+      // ---- phase 2: the +-1 x-shift of the pull, in registers -----------------------
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) {
+        const int ex = ex_of(a);
+        if (ex == 1) {
+          // source i - 1: previous lane's last element; lane 0 takes the strip-end load
+          E in = shfl_up1<E>(v[a].last());
+          if (lane == 0) in = end_in[a];
+          v[a].shift_up(in);
+        } else if (ex == -1) {
+          // source i + 1: next lane's first element; lane 31 takes the strip-end load
+          E keep = E(0);
+          if (has_last) {
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+              if (k == k_last) keep = v[a].get(k);
+          }
+          E in = shfl_down1<E>(v[a].first());
+          if (lane == 31 && !east_edge) in = end_in[a];
+          v[a].shift_down(in);
+          if (has_last) {
+            const E fix = east_out ? keep : end_in[a];  // zero gradient or periodic
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+              if (k == k_last) v[a].set(k, fix);
+          }
+        }
+      }
       bool any_solid_lane = false;
 #pragma unroll
       for (int k = 0; k < V; ++k) any_solid_lane |= (b[k] != 0);
       const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
 
-      // update the V cells in place
+      // ---- phase 3: update the V nodes in place ----------------------------------------
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         T x[kQ];
         decode_cell<S, V>(v, k, x);
         if (k == 0 && west_edge && west_inlet && lane == 0) {
-          x[1] = ghost[1];
-          x[5] = ghost[5];
-          x[8] = ghost[8];
+          x[1] = C.ghost[1];  // inlet ghost populations entering from x = -1
+          x[5] = C.ghost[5];
+          x[8] = C.ghost[8];
         }
         NodeMacro<T> m;
         if (any_solid) {
@@ -299,6 +316,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
           if (solid) body_velocity<T>(D, b[k], xl + k, j, uox, uoy);
           m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
           collide<T, SHIFT, true>(x, m, C);
+          if (solid) {
+            // F_VP of this node for the body-force reduction
+            T *fv = static_cast<T *>(D.fvp) + 2 * (static_cast<size_t>(j) * pitch + xl + k);
+            fv[0] = m.fx;
+            fv[1] = m.fy;
+          }
         } else {
           m = node_macro<T, SHIFT, false>(x, C, false, T(0), T(0));
           collide<T, SHIFT, false>(x, m, C);
