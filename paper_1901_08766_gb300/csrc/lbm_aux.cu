@@ -170,7 +170,7 @@ cudaError_t launch_build_solid(cudaStream_t st, const uint8_t *mask, int nx, int
 // the body's row-major node list in FP64, then a fixed shuffle + shared-memory tree,
 // so the sum order depends only on the node list, not on the tiling or the batch.
 
-constexpr int kForceThreads = 256;
+constexpr int kForceThreads = 512;
 
 template <int S>
 __global__ void __launch_bounds__(kForceThreads)

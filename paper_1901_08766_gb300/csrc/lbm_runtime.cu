@@ -317,13 +317,14 @@ lbm_status rebuild_lists(lbm_batch *b) {
 
 // Enqueue step s of the current run: the force reduction reads the same lattice as the
 // sweep, so the two are ordered only against the next step.
-// The force kernel is launched even when no body records forces (it returns at once),
-// so that a captured graph stays valid when the batch membership changes.
+// Step s of the current run: the sweep, then the force reduction over the F_VP field the
+// sweep wrote. The force kernel is launched even when no body records forces (it returns
+// at once), so that a captured graph stays valid when the batch membership changes.
 lbm_status enqueue_step(lbm_batch *b, int s) {
+  LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, s));
+  b->launches++;
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
                          b->d_ctr, s));
-  b->launches++;
-  LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, s));
   b->launches++;
   return LBM_OK;
 }
@@ -409,12 +410,12 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
     lbm_status prc = LBM_OK;
     for (long long s = 0; s < steps && prc == LBM_OK; ++s) {
       cudaEventRecord(ev[3 * s], b->st);
+      if (sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, static_cast<int>(s)) != cudaSuccess)
+        prc = fail(LBM_ECUDA, "sweep launch failed");
+      cudaEventRecord(ev[3 * s + 1], b->st);
       if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
                         static_cast<int>(s)) != cudaSuccess)
         prc = fail(LBM_ECUDA, "force launch failed");
-      cudaEventRecord(ev[3 * s + 1], b->st);
-      if (sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, static_cast<int>(s)) != cudaSuccess)
-        prc = fail(LBM_ECUDA, "sweep launch failed");
       cudaEventRecord(ev[3 * s + 2], b->st);
       b->launches += 2;
     }
@@ -423,8 +424,8 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
       float a = 0.f, c = 0.f;
       cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
       cudaEventElapsedTime(&c, ev[3 * s + 1], ev[3 * s + 2]);
-      prof->force_ms += a;
-      prof->sweep_ms += c;
+      prof->sweep_ms += a;
+      prof->force_ms += c;
     }
     for (auto &e : ev) cudaEventDestroy(e);
     if (prc != LBM_OK) return prc;

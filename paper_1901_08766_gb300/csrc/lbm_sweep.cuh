@@ -208,19 +208,25 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
       if (j >= ny) break;
       // ---- phase 1: every load of the row ------------------------------------------
       const E *row[kQ];
+      const E *rj = src + static_cast<size_t>(j) * pitch;
+      if (j > 0 && j < ny - 1) {
 #pragma unroll
-      for (int a = 0; a < kQ; ++a) {
-        // y rule for this direction (warp-uniform): periodic wrap or free-slip mirror
-        const int ey = ey_of(a);
-        int sy = j - ey, sa = a;
-        if (sy < 0) {
-          if (south_slip) { sy = 0; sa = reflect_y(a); }
-          else sy += ny;
-        } else if (sy > ny - 1) {
-          if (north_slip) { sy = ny - 1; sa = reflect_y(a); }
-          else sy -= ny;
+        for (int a = 0; a < kQ; ++a) row[a] = rj + (a * plane - static_cast<ptrdiff_t>(ey_of(a)) * pitch);
+      } else {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+          // y rule for this direction (warp-uniform): periodic wrap or free-slip mirror
+          const int ey = ey_of(a);
+          int sy = j - ey, sa = a;
+          if (sy < 0) {
+            if (south_slip) { sy = 0; sa = reflect_y(a); }
+            else sy += ny;
+          } else if (sy > ny - 1) {
+            if (north_slip) { sy = ny - 1; sa = reflect_y(a); }
+            else sy -= ny;
+          }
+          row[a] = src + sa * plane + static_cast<size_t>(sy) * pitch;
         }
-        row[a] = src + sa * plane + static_cast<size_t>(sy) * pitch;
       }
       Strip<S, V> v[kQ];
       E end_in[kQ];
@@ -300,10 +306,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
       const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
 
       // ---- phase 3: update the V nodes in place ----------------------------------------
-#pragma unroll
-      for (int k = 0; k < V; ++k) {
-        T x[kQ];
-        decode_cell<S, V>(v, k, x);
+      // one node: inlet ghost, moments, penalization, collision, F_VP, stability check
+      auto update = [&](T (&x)[kQ], int k) {
         if (k == 0 && west_edge && west_inlet && lane == 0) {
           x[1] = C.ghost[1];  // inlet ghost populations entering from x = -1
           x[5] = C.ghost[5];
@@ -332,8 +336,32 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) x[a] = T(0);  // keep the row padding at zero
         }
+      };
+      if constexpr (sizeof(E) == 2) {
+        // 16-bit storage: two nodes per packed word, converted pairwise
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
+        for (int k = 0; k < V; k += 2) {
+          T x0[kQ], x1[kQ];
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) {
+            const float2 p = Cd::dec2(v[a].w[k >> 1]);
+            x0[a] = p.x;
+            x1[a] = p.y;
+          }
+          update(x0, k);
+          update(x1, k + 1);
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = Cd::enc2(x0[a], x1[a]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          T x[kQ];
+          decode_cell<S, V>(v, k, x);
+          update(x, k);
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
+        }
       }
       if (lane_on) {
 #pragma unroll
