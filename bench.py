@@ -275,7 +275,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16s storage, f32 compute"
             if args.storage == "f16s" else args.storage, "data": "synthetic",
-            "config": dict(_config(args, specs), tile={"vec": tile[0], "warps": tile[1], "rows": tile[2]},
+            "config": dict(_config(args, specs), tile={"vec": tile[0], "warps": tile[1], "rows": tile[2],
+                                                       "pipeline": "tma" if tile[3] else "direct"},
                            autotune_best_us=tune_us),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "plain_f32_per_domain": plain}
@@ -323,7 +324,7 @@ def measure_plain_f32(lbm, torch, specs, args, steps=30):
         for s in specs[:: max(1, len(specs) // 16)]:
             b = lbm.Batch("f32", max_domains=1, graph_steps=0, stream=stream)
             k = b.admit(s, nsteps=steps + 5, force_capacity=steps + 8)
-            b.set_tile(4, 8, 2)
+            b.set_tile(4, 8, 2, 0)
             b.run(5)
             stream.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -350,7 +351,7 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=32)
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--tile", default="", help="vec,warps,rows: fixed sweep tile, no autotune")
+    ap.add_argument("--tile", default="", help="vec,warps,rows[,pipeline]: fixed sweep tile, no autotune")
     ap.add_argument("--domains", type=int, default=64, help="first N domains of the set")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e, plain and CPU legs")

@@ -47,7 +47,7 @@ typedef enum {
   LBM_ENOMEM = 2,    /* device or host allocation failed */
   LBM_ECUDA = 3,     /* a CUDA runtime call failed (text in lbm_last_error) */
   LBM_EUNSTABLE = 4, /* a domain diverged: rho <= 0.01, rho >= 100 or not finite (sticky) */
-  LBM_ETIMEOUT = 5,  /* reserved: a bounded wait ran out */
+  LBM_ETIMEOUT = 5,  /* a bounded device-side wait ran out (sticky per domain) */
   LBM_EBUSY = 6,     /* no free slot / over the memory budget / force ring full */
   LBM_ENOTFOUND = 7  /* unknown slot */
 } lbm_status;
@@ -220,16 +220,21 @@ LBM_API lbm_status lbm_batch_profile(lbm_batch *b, int32_t steps, double *sweep_
 /* Free a slot and its device memory. */
 LBM_API lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot);
 
-/* Time each sweep tile shape (cells per thread, warps per block, rows per warp) on the
+/* Time each sweep tile shape (cells per thread, warps per block, rows per warp, row
+ * pipeline) on the
  * resident domains for `reps` launches each, keep the fastest and rebuild the work
  * list and graphs. The timing launches write only the spare lattice, so the state is
  * untouched. *best_us receives the best time per sweep launch (may be NULL). */
 LBM_API lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us);
 
 /* Set the sweep tile shape explicitly: vec = cells per thread (F64 1|2, F32 2|4,
- * F16S/BF16S 4|8), warps = warps per block (1..16), rows = rows per warp (1..16). */
-LBM_API lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows);
-LBM_API lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows);
+ * F16S/BF16S 4|8), warps = warps per block (1..16), rows = rows per warp (1..16),
+ * pipeline = 0 (rows read straight into registers) or 1 (rows staged through shared
+ * memory by bulk asynchronous copies, one row ahead). Results do not depend on it. */
+LBM_API lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows,
+                                      int32_t pipeline);
+LBM_API lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows,
+                                      int32_t *pipeline);
 
 /* Resident slots and cells, and kernel launches issued since creation (sweeps, force
  * reductions, graph replays count each captured kernel). Any output may be NULL. */

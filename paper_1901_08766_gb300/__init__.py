@@ -240,14 +240,15 @@ class Batch:
         check(load().lbm_batch_autotune(self._h, reps, C.byref(us)), "lbm_batch_autotune")
         return us.value
 
-    def set_tile(self, vec: int, warps: int, rows: int):
-        check(load().lbm_batch_set_tile(self._h, vec, warps, rows), "lbm_batch_set_tile")
+    def set_tile(self, vec: int, warps: int, rows: int, pipeline: int = 0):
+        check(load().lbm_batch_set_tile(self._h, vec, warps, rows, pipeline), "lbm_batch_set_tile")
 
     def get_tile(self):
-        v, w, r = C.c_int32(), C.c_int32(), C.c_int32()
-        check(load().lbm_batch_get_tile(self._h, C.byref(v), C.byref(w), C.byref(r)),
+        """(cells per thread, warps per block, rows per warp, pipeline)."""
+        v, w, r, p = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        check(load().lbm_batch_get_tile(self._h, C.byref(v), C.byref(w), C.byref(r), C.byref(p)),
               "lbm_batch_get_tile")
-        return v.value, w.value, r.value
+        return v.value, w.value, r.value, p.value
 
     def info(self):
         r, c, k, b = C.c_int32(), C.c_int64(), C.c_int64(), C.c_size_t()

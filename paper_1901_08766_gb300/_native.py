@@ -91,8 +91,9 @@ SIGNATURES = {
     "lbm_batch_profile": (C.c_int, [_VP, _I32, _DP, _DP, C.POINTER(_I64)]),
     "lbm_batch_evict": (C.c_int, [_VP, _I32]),
     "lbm_batch_autotune": (C.c_int, [_VP, _I32, _DP]),
-    "lbm_batch_set_tile": (C.c_int, [_VP, _I32, _I32, _I32]),
-    "lbm_batch_get_tile": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
+    "lbm_batch_set_tile": (C.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    "lbm_batch_get_tile": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
+                                     C.POINTER(_I32)]),
     "lbm_batch_info": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),
                                  C.POINTER(_SZ)]),
     "lbm_batch_destroy": (C.c_int, [_VP]),

@@ -177,15 +177,29 @@ __device__ __forceinline__ void collide(T (&x)[kQ], const NodeMacro<T> &m, const
   pair(6, 8, m.uy - m.ux, m.fy - m.fx, a2, b2, m2, c.kw2, c.qw2);
 }
 
-// Obstacle velocity of body id b at node (i, j): V + omega z x (x - c).
+// Obstacle velocity of body id b at node (i, j): V + omega z x (x - c), in the compute
+// precision (FP64 with explicit roundings for the FP64 storage, FP32 otherwise).
 template <typename T>
-__device__ __forceinline__ void body_velocity(const DomDev &d, int b, int i, int j, T &uox,
-                                              T &uoy) {
+__device__ __forceinline__ void body_velocity(const DomDev &d, int b, int i, int j, T &uox, T &uoy);
+
+template <>
+__device__ __forceinline__ void body_velocity<double>(const DomDev &d, int b, int i, int j,
+                                                      double &uox, double &uoy) {
   const double *bd = d.bodies + 5 * (b - 1);
   const double cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
                om = __ldg(bd + 4);
-  uox = T(__dsub_rn(vx, __dmul_rn(om, __dsub_rn(double(j), cy))));
-  uoy = T(__dadd_rn(vy, __dmul_rn(om, __dsub_rn(double(i), cx))));
+  uox = __dsub_rn(vx, __dmul_rn(om, __dsub_rn(double(j), cy)));
+  uoy = __dadd_rn(vy, __dmul_rn(om, __dsub_rn(double(i), cx)));
+}
+
+template <>
+__device__ __forceinline__ void body_velocity<float>(const DomDev &d, int b, int i, int j,
+                                                     float &uox, float &uoy) {
+  const float *bd = d.bodies_f + 5 * (b - 1);
+  const float cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
+              om = __ldg(bd + 4);
+  uox = vx - om * (float(j) - cy);
+  uoy = vy + om * (float(i) - cx);
 }
 
 // Scalar pull of direction a at node (i, j) with the edge rules (Eq. streaming):

@@ -34,6 +34,7 @@ struct DomDev {
   void *lat[2];            // lattice A/B: [9][ny][pitch] elements of the storage type
   const uint8_t *mask;     // [ny][pitch] body id, 0 = fluid
   const double *bodies;    // [nbodies][5]: cx, cy, vx, vy, omega
+  const float *bodies_f;   // the same table rounded to FP32 (FP32-compute storages)
   const int32_t *solid;    // solid nodes (j * pitch + i), grouped by body, row-major
   const int32_t *solid_off;// [nbodies + 1] offsets into solid
   void *fvp;               // F_VP of solid nodes, [ny][pitch] pairs in compute precision
@@ -89,11 +90,6 @@ struct ShapeDev {
 };
 
 // Kernel launchers (one translation unit per storage type for the sweep).
-cudaError_t launch_sweep(int storage, int vec, int grid, int warps, cudaStream_t st,
-                         const SweepArgs &a, int s);
-int sweep_max_blocks_per_sm(int storage, int vec, int warps);
-bool sweep_vec_supported(int storage, int vec);
-
 cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *doms,
                           const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
                           int s);
@@ -113,17 +109,17 @@ cudaError_t launch_moments_sized(int storage, cudaStream_t st, const DomDev *dom
                                  int ny, int parity, double *rho, double *ux, double *uy);
 
 // per-storage sweep launchers (one translation unit each)
-cudaError_t launch_sweep_f64(int vec, int grid, int warps, cudaStream_t st,
+cudaError_t launch_sweep_f64(int vec, int pipe, int grid, int warps, cudaStream_t st,
                              const SweepArgs &a, int s);
-cudaError_t launch_sweep_f32(int vec, int grid, int warps, cudaStream_t st,
+cudaError_t launch_sweep_f32(int vec, int pipe, int grid, int warps, cudaStream_t st,
                              const SweepArgs &a, int s);
-cudaError_t launch_sweep_f16s(int vec, int grid, int warps, cudaStream_t st,
-                              const SweepArgs &a, int s);
-cudaError_t launch_sweep_bf16s(int vec, int grid, int warps, cudaStream_t st,
-                               const SweepArgs &a, int s);
-int max_blocks_f64(int vec, int warps);
-int max_blocks_f32(int vec, int warps);
-int max_blocks_f16s(int vec, int warps);
-int max_blocks_bf16s(int vec, int warps);
+cudaError_t launch_sweep_f16s(int vec, int pipe, int grid, int warps, cudaStream_t st,
+                             const SweepArgs &a, int s);
+cudaError_t launch_sweep_bf16s(int vec, int pipe, int grid, int warps, cudaStream_t st,
+                             const SweepArgs &a, int s);
+int max_blocks_f64(int vec, int pipe, int warps);
+int max_blocks_f32(int vec, int pipe, int warps);
+int max_blocks_f16s(int vec, int pipe, int warps);
+int max_blocks_bf16s(int vec, int pipe, int warps);
 
 }  // namespace lbm

@@ -74,7 +74,8 @@ struct Alloc {
 // Fixed part of a domain's device footprint (populations x2, mask, bodies, offsets,
 // force ring, status word), each piece 256-byte aligned.
 struct Layout {
-  size_t lat_bytes, mask_off, fvp_off, bodies_off, off_off, ring_off, status_off, total;
+  size_t lat_bytes, mask_off, fvp_off, bodies_off, bodies_f_off, off_off, ring_off, status_off,
+      total;
 };
 
 Layout layout_of(const lbm_params &p, int nbodies) {
@@ -90,6 +91,8 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   o += align_up(static_cast<size_t>(p.ny) * pitch * 2 * (p.storage == LBM_F64 ? 8 : 4), 256);
   L.bodies_off = o;
   o += align_up(sizeof(double) * 5 * std::max(1, nbodies), 256);
+  L.bodies_f_off = o;
+  o += align_up(sizeof(float) * 5 * std::max(1, nbodies), 256);
   L.off_off = o;
   o += align_up(sizeof(int32_t) * (nbodies + 1), 256);
   L.ring_off = o;
@@ -192,7 +195,7 @@ struct lbm_batch {
   int items_cap = 0;
   Counters *d_ctr = nullptr;
   Counters *h_ctr = nullptr;  // pinned staging for tile/item counts
-  int vec = 0, warps = 0, rows = 0;
+  int vec = 0, warps = 0, rows = 0, pipe = 0;
   int grid_sweep = 0, grid_force = 0;
   int ntiles = 0, nitems = 0;
   bool dirty = true;
@@ -209,23 +212,23 @@ struct lbm_domain {
 namespace lbm {
 namespace {
 
-cudaError_t sweep_launch(lbm_batch *b, int grid, int vec, int warps, int rows, int s) {
+cudaError_t sweep_launch(lbm_batch *b, int grid, int vec, int pipe, int warps, int rows, int s) {
   SweepArgs a{b->d_doms, b->d_dyn, b->d_tiles, b->d_ctr, rows};
   switch (b->storage) {
-    case LBM_F64: return launch_sweep_f64(vec, grid, warps, b->st, a, s);
-    case LBM_F32: return launch_sweep_f32(vec, grid, warps, b->st, a, s);
-    case LBM_F16S: return launch_sweep_f16s(vec, grid, warps, b->st, a, s);
-    case LBM_BF16S: return launch_sweep_bf16s(vec, grid, warps, b->st, a, s);
+    case LBM_F64: return launch_sweep_f64(vec, pipe, grid, warps, b->st, a, s);
+    case LBM_F32: return launch_sweep_f32(vec, pipe, grid, warps, b->st, a, s);
+    case LBM_F16S: return launch_sweep_f16s(vec, pipe, grid, warps, b->st, a, s);
+    case LBM_BF16S: return launch_sweep_bf16s(vec, pipe, grid, warps, b->st, a, s);
   }
   return cudaErrorInvalidValue;
 }
 
-int sweep_occupancy(int storage, int vec, int warps) {
+int sweep_occupancy(int storage, int vec, int pipe, int warps) {
   switch (storage) {
-    case LBM_F64: return max_blocks_f64(vec, warps);
-    case LBM_F32: return max_blocks_f32(vec, warps);
-    case LBM_F16S: return max_blocks_f16s(vec, warps);
-    case LBM_BF16S: return max_blocks_bf16s(vec, warps);
+    case LBM_F64: return max_blocks_f64(vec, pipe, warps);
+    case LBM_F32: return max_blocks_f32(vec, pipe, warps);
+    case LBM_F16S: return max_blocks_f16s(vec, pipe, warps);
+    case LBM_BF16S: return max_blocks_bf16s(vec, pipe, warps);
   }
   return 0;
 }
@@ -238,10 +241,11 @@ bool vec_ok(int storage, int vec) {
   }
 }
 
-void default_tile(int storage, int &vec, int &warps, int &rows) {
+void default_tile(int storage, int &vec, int &warps, int &rows, int &pipe) {
   vec = storage == LBM_F64 ? 2 : (storage == LBM_F32 ? 4 : 8);
-  warps = 8;
-  rows = 2;
+  warps = 4;
+  rows = 4;
+  pipe = 0;
 }
 
 void drop_graph(lbm_batch *b) {
@@ -251,14 +255,16 @@ void drop_graph(lbm_batch *b) {
   }
 }
 
-lbm_status set_config(lbm_batch *b, int vec, int warps, int rows) {
+lbm_status set_config(lbm_batch *b, int vec, int warps, int rows, int pipe) {
   if (!vec_ok(b->storage, vec)) return fail(LBM_EINVAL, "cells per thread %d unsupported for storage %d", vec, b->storage);
   if (warps < 1 || warps > 16 || rows < 1 || rows > 16) return fail(LBM_EINVAL, "warps and rows must be in [1, 16]");
-  const int occ = sweep_occupancy(b->storage, vec, warps);
+  if (pipe != 0 && pipe != 1) return fail(LBM_EINVAL, "pipeline must be 0 (direct) or 1 (TMA-staged)");
+  const int occ = sweep_occupancy(b->storage, vec, pipe, warps);
   if (occ <= 0) return fail(LBM_ECUDA, "sweep kernel cannot run with %d warps per block", warps);
   b->vec = vec;
   b->warps = warps;
   b->rows = rows;
+  b->pipe = pipe;
   b->grid_sweep = occ * b->sm_count;
   b->dirty = true;
   drop_graph(b);
@@ -321,7 +327,7 @@ lbm_status rebuild_lists(lbm_batch *b) {
 // sweep wrote. The force kernel is launched even when no body records forces (it returns
 // at once), so that a captured graph stays valid when the batch membership changes.
 lbm_status enqueue_step(lbm_batch *b, int s) {
-  LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, s));
+  LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, s));
   b->launches++;
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
                          b->d_ctr, s));
@@ -410,7 +416,7 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
     lbm_status prc = LBM_OK;
     for (long long s = 0; s < steps && prc == LBM_OK; ++s) {
       cudaEventRecord(ev[3 * s], b->st);
-      if (sweep_launch(b, b->grid_sweep, b->vec, b->warps, b->rows, static_cast<int>(s)) != cudaSuccess)
+      if (sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, static_cast<int>(s)) != cudaSuccess)
         prc = fail(LBM_ECUDA, "sweep launch failed");
       cudaEventRecord(ev[3 * s + 1], b->st);
       if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
@@ -505,6 +511,8 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.mask = mask;
   double *bod = reinterpret_cast<double *>(base + L.bodies_off);
   D.bodies = bod;
+  float *bodf = reinterpret_cast<float *>(base + L.bodies_f_off);
+  D.bodies_f = bodf;
   int32_t *off = reinterpret_cast<int32_t *>(base + L.off_off);
   D.solid_off = off;
   D.fvp = base + L.fvp_off;
@@ -588,6 +596,9 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     hb[5 * i + 4] = bodies[i].omega;
   }
   ADM_CUDA(cudaMemcpyAsync(bod, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
+  std::vector<float> hbf(hb.begin(), hb.end());
+  ADM_CUDA(cudaMemcpyAsync(bodf, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaStreamSynchronize(st));  // the pageable staging vectors leave scope below
   // count nodes per body, then build the solid-node lists
   int32_t *counts = static_cast<int32_t *>(tmp);
   ADM_CUDA(cudaMemsetAsync(counts, 0, counts_bytes, st));
@@ -660,6 +671,7 @@ lbm_status poll(lbm_batch *b, int slot, double *out, long long max_entries, long
   s.drained += n;
   if (written) *written = n;
   if (done) *done = (s.done >= s.target && s.drained >= produced) ? 1 : 0;
+  if (status & 2) return fail(LBM_ETIMEOUT, "slot %d: a sweep gave up waiting for its row copies", slot);
   if (status & 1) return fail(LBM_EUNSTABLE, "slot %d diverged (rho out of range or not finite)", slot);
   return LBM_OK;
 }
@@ -782,9 +794,9 @@ lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, 
   cudaEventRecord(b->dyn_ev, b->st);
   cudaMemsetAsync(b->d_ctr, 0, sizeof(Counters), b->st);
   cudaMemsetAsync(b->d_dyn, 0, sizeof(DomDyn) * max_domains, b->st);
-  int vec, warps, rows;
-  default_tile(storage, vec, warps, rows);
-  lbm_status rc = set_config(b, vec, warps, rows);
+  int vec, warps, rows, pipe;
+  default_tile(storage, vec, warps, rows, pipe);
+  lbm_status rc = set_config(b, vec, warps, rows, pipe);
   if (rc != LBM_OK) { destroy(b); return rc; }
   *out = b;
   return LBM_OK;
@@ -812,33 +824,34 @@ lbm_status autotune(lbm_batch *b, int reps, double *best_us) {
   LBM_CUDA(cudaEventCreate(&e0));
   LBM_CUDA(cudaEventCreate(&e1));
   double best = 1e300;
-  int bv = b->vec, bw = b->warps, br = b->rows;
+  int bv = b->vec, bw = b->warps, br = b->rows, bp = b->pipe;
   lbm_status rc = LBM_OK;
-  for (int v : vecs)
-    for (int w : warp_opts)
-      for (int r : row_opts) {
-        if (sweep_occupancy(b->storage, v, w) <= 0) continue;
-        rc = set_config(b, v, w, r);
-        if (rc == LBM_OK) rc = rebuild_lists(b);
-        if (rc != LBM_OK) break;
-        for (int q = 0; q < 2 && rc == LBM_OK; ++q)
-          if (sweep_launch(b, b->grid_sweep, v, w, r, 0) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune launch failed");
-        cudaEventRecord(e0, b->st);
-        for (int q = 0; q < reps && rc == LBM_OK; ++q)
-          if (sweep_launch(b, b->grid_sweep, v, w, r, 0) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune launch failed");
-        cudaEventRecord(e1, b->st);
-        cudaEventSynchronize(e1);
-        if (rc != LBM_OK) break;
-        b->launches += reps + 2;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double us = 1000.0 * ms / reps;
-        if (us < best) { best = us; bv = v; bw = w; br = r; }
-      }
+  for (int p = 0; p < 2 && rc == LBM_OK; ++p)
+    for (int v : vecs)
+      for (int w : warp_opts)
+        for (int r : row_opts) {
+          if (sweep_occupancy(b->storage, v, p, w) <= 0) continue;
+          rc = set_config(b, v, w, r, p);
+          if (rc == LBM_OK) rc = rebuild_lists(b);
+          if (rc != LBM_OK) break;
+          for (int q = 0; q < 2 && rc == LBM_OK; ++q)
+            if (sweep_launch(b, b->grid_sweep, v, p, w, r, 0) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune launch failed");
+          cudaEventRecord(e0, b->st);
+          for (int q = 0; q < reps && rc == LBM_OK; ++q)
+            if (sweep_launch(b, b->grid_sweep, v, p, w, r, 0) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune launch failed");
+          cudaEventRecord(e1, b->st);
+          cudaEventSynchronize(e1);
+          if (rc != LBM_OK) break;
+          b->launches += reps + 2;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          const double us = 1000.0 * ms / reps;
+          if (us < best) { best = us; bv = v; bw = w; br = r; bp = p; }
+        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != LBM_OK) return rc;
-  rc = set_config(b, bv, bw, br);
+  rc = set_config(b, bv, bw, br, bp);
   if (rc == LBM_OK) rc = rebuild_lists(b);
   if (best_us) *best_us = best;
   return rc;
@@ -981,16 +994,19 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us) {
   return autotune(b, reps, best_us);
 }
 
-lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows) {
+lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows,
+                              int32_t pipeline) {
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
-  return set_config(b, vec, warps, rows);
+  return set_config(b, vec, warps, rows, pipeline);
 }
 
-lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows) {
+lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows,
+                              int32_t *pipeline) {
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   if (vec) *vec = b->vec;
   if (warps) *warps = b->warps;
   if (rows) *rows = b->rows;
+  if (pipeline) *pipeline = b->pipe;
   return LBM_OK;
 }
 

@@ -36,6 +36,18 @@ template <int S, int V> struct Strip16 {
       w[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
     }
   }
+  // aligned vector read from shared memory
+  __device__ void load_shared(const uint16_t *p) {
+    if constexpr (kW == 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(p);
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if constexpr (kW == 2) {
+      const uint2 v = *reinterpret_cast<const uint2 *>(p);
+      w[0] = v.x; w[1] = v.y;
+    } else {
+      w[0] = *reinterpret_cast<const uint32_t *>(p);
+    }
+  }
   __device__ void store(uint16_t *p) const {
     if constexpr (kW == 4) {
       *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -99,6 +111,24 @@ template <typename E, int V> struct StripW {
     } else {
 #pragma unroll
       for (int k = 0; k < V; ++k) w[k] = __ldg(p + k);
+    }
+  }
+  __device__ void load_shared(const E *p) {
+    constexpr int kBytes = V * int(sizeof(E));
+    if constexpr (kBytes == 16) {
+      if constexpr (sizeof(E) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+      } else {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        w[0] = v.x; w[1] = v.y;
+      }
+    } else if constexpr (kBytes == 8 && sizeof(E) == 4) {
+      const float2 v = *reinterpret_cast<const float2 *>(p);
+      w[0] = v.x; w[1] = v.y;
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) w[k] = p[k];
     }
   }
   __device__ void store(E *p) const {
@@ -306,6 +336,10 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
       const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
 
       // ---- phase 3: update the V nodes in place ----------------------------------------
+      // bit k: node xl + k lies inside the domain (all V except at the east edge)
+      const unsigned valid_bits =
+          east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u))
+                    : (1u << V) - 1u;
       // one node: inlet ghost, moments, penalization, collision, F_VP, stability check
       auto update = [&](T (&x)[kQ], int k) {
         if (k == 0 && west_edge && west_inlet && lane == 0) {
@@ -330,12 +364,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
           m = node_macro<T, SHIFT, false>(x, C, false, T(0), T(0));
           collide<T, SHIFT, false>(x, m, C);
         }
-        const bool valid = xl + k < nx;
-        if (valid && !(m.rho > T(0.01) && m.rho < T(100))) unstable = 1;
-        if (east_edge && !valid) {
-#pragma unroll
-          for (int a = 0; a < kQ; ++a) x[a] = T(0);  // keep the row padding at zero
-        }
+        if (((valid_bits >> k) & 1u) && !(m.rho > T(0.01) && m.rho < T(100))) unstable = 1;
       };
       if constexpr (sizeof(E) == 2) {
         // 16-bit storage: two nodes per packed word, converted pairwise
@@ -362,6 +391,15 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
 #pragma unroll
           for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
         }
+      }
+      if (east_edge) {
+        // keep the row padding beyond nx at zero
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+          if (!((valid_bits >> k) & 1u)) {
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) v[a].set(k, E(0));
+          }
       }
       if (lane_on) {
 #pragma unroll

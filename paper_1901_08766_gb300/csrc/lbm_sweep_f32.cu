@@ -1,18 +1,29 @@
-// Sweep instantiations for LBM_F32 storage (cells per thread 2 and 4).
-#include "lbm_sweep.cuh"
+// Sweep instantiations for LBM_F32 storage (cells per thread 2 and 4; direct
+// and TMA-staged row loads).
+#include "lbm_sweep_tma.cuh"
 
 namespace lbm {
 
-cudaError_t launch_sweep_f32(int vec, int grid, int warps, cudaStream_t st, const SweepArgs &a,
-                               int s) {
-  if (vec == 2) return launch_sweep_t<LBM_F32, 2>(grid, warps, st, a, s);
-  if (vec == 4) return launch_sweep_t<LBM_F32, 4>(grid, warps, st, a, s);
+cudaError_t launch_sweep_f32(int vec, int pipe, int grid, int warps, cudaStream_t st,
+                               const SweepArgs &a, int s) {
+  if (pipe == 0) {
+    if (vec == 2) return launch_sweep_t<LBM_F32, 2>(grid, warps, st, a, s);
+    if (vec == 4) return launch_sweep_t<LBM_F32, 4>(grid, warps, st, a, s);
+  } else {
+    if (vec == 2) return launch_sweep_tma_t<LBM_F32, 2>(grid, warps, st, a, s);
+    if (vec == 4) return launch_sweep_tma_t<LBM_F32, 4>(grid, warps, st, a, s);
+  }
   return cudaErrorInvalidValue;
 }
 
-int max_blocks_f32(int vec, int warps) {
-  if (vec == 2) return max_blocks_t<LBM_F32, 2>(warps);
-  if (vec == 4) return max_blocks_t<LBM_F32, 4>(warps);
+int max_blocks_f32(int vec, int pipe, int warps) {
+  if (pipe == 0) {
+    if (vec == 2) return max_blocks_t<LBM_F32, 2>(warps);
+    if (vec == 4) return max_blocks_t<LBM_F32, 4>(warps);
+  } else {
+    if (vec == 2) return max_blocks_tma_t<LBM_F32, 2>(warps);
+    if (vec == 4) return max_blocks_tma_t<LBM_F32, 4>(warps);
+  }
   return 0;
 }
 

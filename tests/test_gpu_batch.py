@@ -48,10 +48,11 @@ def test_tile_shape_and_graphs_do_not_change_results(lbm):
     spec = synth.parity_case("channel_256x128")
     g0 = codec.encode(synth.random_populations(8, 256, 128, 0.05), "f16s")
     ref = None
-    for vec, warps, rows, graph in [(8, 8, 2, 16), (4, 4, 1, 0), (8, 16, 4, 7), (4, 2, 3, 32)]:
+    for vec, warps, rows, pipe, graph in [(8, 8, 2, 0, 16), (4, 4, 1, 0, 0), (8, 16, 4, 1, 7),
+                                          (4, 2, 3, 1, 32), (8, 4, 4, 1, 0)]:
         batch = lbm.Batch("f16s", max_domains=2, graph_steps=graph)
         k = batch.admit(spec, nsteps=100)
-        batch.set_tile(vec, warps, rows)
+        batch.set_tile(vec, warps, rows, pipe)
         batch.set_populations(k, g0)
         while batch.run(45):
             pass
@@ -76,8 +77,8 @@ def test_autotune_keeps_state_and_results(lbm):
     after = [batch.get_populations(k).view(np.uint16) for k in slots]
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
-    vec, warps, rows = batch.get_tile()
-    assert vec in (4, 8) and 1 <= warps <= 16 and 1 <= rows <= 16
+    vec, warps, rows, pipe = batch.get_tile()
+    assert vec in (4, 8) and 1 <= warps <= 16 and 1 <= rows <= 16 and pipe in (0, 1)
     batch.run(40)
     ref = lbm.Domain(specs[0], storage="f16s")
     ref.step(60)
