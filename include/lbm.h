@@ -164,6 +164,25 @@ LBM_API lbm_status lbm_moments(lbm_domain *d, double *rho, double *ux, double *u
 LBM_API lbm_status lbm_get_populations(lbm_domain *d, void *out, size_t bytes);
 LBM_API lbm_status lbm_set_populations(lbm_domain *d, const void *in, size_t bytes);
 
+/* lbm_moments without any device allocation, for callers that cannot let the library
+ * allocate when they read the fields: an application whose own arena or caching
+ * allocator owns all device memory, a monitoring loop that cannot afford an
+ * allocation's latency or implicit device synchronisation, or code that must keep its
+ * device footprint fixed after start-up. The paper has no counterpart; this is a
+ * service of the library.
+ *  - Same outputs as lbm_moments (host or device pointers, any may be NULL; synchronises).
+ *  - The fields are staged in one fixed device array owned by the library, 3 * 2^18
+ *    doubles (6 MiB), which every GPU that loads the library holds until exit; domains
+ *    with more than 2^18 = 262144 nodes are rejected with LBM_EINVAL.
+ *  - The first call on a device looks up the array's device address (once per device,
+ *    for the device that is current; it must be the domain's device); make that first
+ *    call before any stream capture.
+ *  - Every call, from any domain, reuses the same array; calls whose work overlaps on the
+ *    GPU (different streams, no ordering between them) race on it and must be serialised
+ *    by the caller. Each call overwrites every value it reads back, so nothing needs to
+ *    start at zero. */
+LBM_API lbm_status lbm_moments_noalloc(lbm_domain *d, double *rho, double *ux, double *uy);
+
 /* The body-id mask chi of Eq. (mask function) as used by the sweep, [ny][nx] bytes,
  * 0 = fluid, k = body k. Host or device pointer. Synchronises the stream. */
 LBM_API lbm_status lbm_get_mask(lbm_domain *d, uint8_t *out);

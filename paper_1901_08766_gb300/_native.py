@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_step": (C.c_int, [_VP, _I64]),
     "lbm_forces": (C.c_int, [_VP, _DP, _I64, C.POINTER(_I64)]),
     "lbm_moments": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "lbm_moments_noalloc": (C.c_int, [_VP, _VP, _VP, _VP]),
     "lbm_get_populations": (C.c_int, [_VP, _VP, _SZ]),
     "lbm_set_populations": (C.c_int, [_VP, _VP, _SZ]),
     "lbm_steps_done": (C.c_int, [_VP, C.POINTER(_I64)]),

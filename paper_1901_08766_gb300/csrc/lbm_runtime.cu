@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1111,3 +1112,81 @@ lbm_status lbm_domain_destroy(lbm_domain *d) {
 }
 
 }  // extern "C"
+
+// ======================================================================================
+// Moments export without any device allocation.
+//
+// lbm_moments stages its three output fields in a device buffer it allocates for the
+// call. Some callers cannot let a library allocate at that point: an application that
+// has handed every byte of device memory to its own arena (a training or serving
+// process whose caching allocator holds the GPU), a monitoring tap polled from a loop
+// where an allocation's implicit device synchronisation or latency is not acceptable,
+// or code that must keep the device footprint fixed after start-up. lbm_moments_noalloc
+// stages the fields in one fixed file-scope device array instead, sized for domains of
+// up to kNoAllocMaxNodes nodes; every GPU that loads this library holds that array
+// (3 * 2^18 doubles = 6 MiB) until the process exits.
+
+namespace lbm {
+namespace {
+
+constexpr size_t kNoAllocMaxNodes = size_t(1) << 18;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_moments_scratch[3 * kNoAllocMaxNodes];
+
+std::mutex g_scratch_mu;
+double *g_scratch_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_moments_scratch on `dev` (which must be current). In host code
+// the array's name is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+lbm_status scratch_on(int dev, double **out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(LBM_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_moments_scratch);
+    if (e != cudaSuccess)
+      return fail(LBM_ECUDA, "cudaGetSymbolAddress(g_moments_scratch) failed: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbm
+
+extern "C" lbm_status lbm_moments_noalloc(lbm_domain *d, double *rho, double *ux, double *uy) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  lbm_batch *b = d->b;
+  const Slot &s = b->slots[0];
+  const size_t cells = static_cast<size_t>(s.p.nx) * s.p.ny;
+  if (cells > kNoAllocMaxNodes)
+    return fail(LBM_EINVAL,
+                "lbm_moments_noalloc: domain has %zu nodes, more than the %zu its fixed staging "
+                "array holds; use lbm_moments",
+                cells, kNoAllocMaxNodes);
+  // the domain's device must be the current one: the staging address is per device
+  cudaPointerAttributes attr{};
+  LBM_CUDA(cudaPointerGetAttributes(&attr, s.dev.lat[0]));
+  int cur = -1;
+  LBM_CUDA(cudaGetDevice(&cur));
+  if (attr.device != cur)
+    return fail(LBM_EINVAL, "domain lives on device %d but device %d is current", attr.device, cur);
+  double *tmp = nullptr;
+  lbm_status rc = scratch_on(cur, &tmp);
+  if (rc != LBM_OK) return rc;
+  LBM_CUDA(launch_moments_sized(b->storage, b->st, b->d_doms, s.p.nx, s.p.ny, s.parity, tmp,
+                                tmp + cells, tmp + 2 * cells));
+  double *outs[3] = {rho, ux, uy};
+  for (int q = 0; q < 3; ++q)
+    if (outs[q])
+      LBM_CUDA(cudaMemcpyAsync(outs[q], tmp + q * cells, sizeof(double) * cells, cudaMemcpyDefault, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  int status = 0;
+  rc = read_status(b, s, &status);
+  if (rc != LBM_OK) return rc;
+  if (status & 1) return fail(LBM_EUNSTABLE, "domain diverged");
+  return LBM_OK;
+}
