@@ -1,0 +1,141 @@
+"""Host logic of the request server, on a fake batch backend (no GPU): FIFO admission by
+memory budget, continuous batching, force streaming, cancellation, rejection and
+divergence handling, latency statistics."""
+import numpy as np
+import pytest
+
+import synth
+from paper_1901_08766_gb300 import server as srvmod
+from paper_1901_08766_gb300._native import LBM_EBUSY, LBM_EINVAL, LBM_EUNSTABLE, LbmError
+
+
+class FakeBatch:
+    """Mimics lbm.Batch: a slot runs until its own step target; each step records a force
+    that depends only on (request name, step), like the real library's results."""
+
+    def __init__(self, budget_cells, max_slots=64, unstable_names=(), clock=None):
+        self.budget = budget_cells
+        self.max_slots = max_slots
+        self.slots = {}
+        self.unstable = set(unstable_names)
+        self.clock = clock
+        self.runs = []
+
+    def try_admit(self, spec, nsteps, force_every=1, force_capacity=0):
+        if spec["nx"] < 3:
+            raise LbmError(LBM_EINVAL, "lbm_batch_admit", "nx must be >= 3")
+        cells = spec["nx"] * spec["ny"]
+        used = sum(s["cells"] for s in self.slots.values())
+        if used + cells > self.budget or len(self.slots) >= self.max_slots:
+            return None
+        k = next(i for i in range(self.max_slots) if i not in self.slots)
+        self.slots[k] = {"spec": spec, "cells": cells, "target": nsteps, "done": 0, "drained": 0,
+                         "cap": force_capacity, "nb": len(spec["bodies"])}
+        return k
+
+    def run(self, max_steps):
+        rem = [s["target"] - s["done"] for s in self.slots.values() if s["done"] < s["target"]]
+        n = min(max_steps, max(rem)) if rem else 0
+        for s in self.slots.values():
+            adv = min(n, s["target"] - s["done"])
+            assert s["done"] + adv - s["drained"] <= s["cap"], "force ring overflow"
+            s["done"] += adv
+        self.runs.append(n)
+        if self.clock is not None:
+            self.clock.t += 0.001 * n
+        return n
+
+    def poll(self, slot):
+        s = self.slots[slot]
+        if s["spec"]["name"] in self.unstable and s["done"] > 0:
+            raise LbmError(LBM_EUNSTABLE, "lbm_batch_poll", "diverged")
+        steps = np.arange(s["drained"], s["done"])
+        h = sum(map(ord, s["spec"]["name"]))
+        f = np.stack([np.stack([np.sin(h + 0.01 * steps), np.cos(h + 0.02 * steps)], -1)] * s["nb"], 1)
+        s["drained"] = s["done"]
+        return f, s["done"] >= s["target"]
+
+    def evict(self, slot):
+        del self.slots[slot]
+
+    def autotune(self, reps=3):
+        return 1.0
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+def _spec(name, n=100, steps=50):
+    sp = synth.parity_case("channel_97x61")
+    return dict(sp, name=name, nx=n, ny=n // 2, steps=steps)
+
+
+def test_fifo_admission_under_budget_and_streaming():
+    clock = Clock()
+    fb = FakeBatch(budget_cells=2 * 100 * 50, clock=clock)
+    srv = srvmod.Server(backend=fb, chunk_steps=16, clock=clock)
+    seen = {}
+    futs = [srv.submit(_spec(f"r{i}", steps=40 + 10 * i), arrival=0.0,
+                       on_forces=lambda rid, f: seen.setdefault(rid, []).append(len(f)))
+            for i in range(4)]
+    srv.pump()
+    assert len(fb.slots) == 2 and len(srv._queue) == 2  # budget holds two
+    srv.run_until_idle()
+    res = [f.result() for f in futs]
+    assert [r.status for r in res] == ["ok"] * 4
+    assert [r.steps for r in res] == [40, 50, 60, 70]
+    # FIFO: admission times follow arrival order
+    adm = [r.admitted for r in res]
+    assert adm == sorted(adm)
+    # the streamed slices add up to the whole series
+    for r, f in zip(res, futs):
+        assert sum(seen[f.request_id]) == r.steps
+    st = srv.stats()
+    assert st["completed"] == 4 and st["p99_latency_s"] >= st["p50_latency_s"] > 0
+
+
+def test_late_arrival_joins_running_batch():
+    clock = Clock()
+    fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
+    srv = srvmod.Server(backend=fb, chunk_steps=10, clock=clock)
+    a = srv.submit(_spec("long", steps=200), arrival=0.0)
+    b = srv.submit(_spec("late", steps=30), arrival=0.05)
+    while not b.done():
+        srv.pump()
+    assert not a.done()  # the late request finished while the long one kept running
+    srv.run_until_idle()
+    ra, rb = a.result(), b.result()
+    assert rb.admitted < ra.done and rb.done < ra.done
+
+
+def test_cancel_reject_and_unstable():
+    clock = Clock()
+    fb = FakeBatch(budget_cells=100 * 50, unstable_names={"bad"}, clock=clock)
+    srv = srvmod.Server(backend=fb, chunk_steps=8, clock=clock)
+    big = srv.submit(_spec("huge", n=400), arrival=0.0)          # can never fit
+    bad = srv.submit(_spec("bad", steps=30), arrival=0.0)
+    queued = srv.submit(_spec("queued", steps=30), arrival=0.0)  # waits behind "bad"
+    inval = srv.submit(dict(_spec("tiny"), nx=2), arrival=0.0)
+    srv.pump()
+    srv.cancel(queued.request_id)
+    srv.run_until_idle()
+    assert big.result().status == "rejected"
+    assert bad.result().status == "unstable"
+    assert queued.result().status == "cancelled"
+    assert inval.result().status == "rejected"
+    assert not fb.slots  # everything evicted
+
+
+def test_background_thread_serves_submissions():
+    fb = FakeBatch(budget_cells=10 ** 9)
+    srv = srvmod.Server(backend=fb, chunk_steps=32)
+    srv.start()
+    futs = [srv.submit(_spec(f"t{i}", steps=64)) for i in range(5)]
+    res = [f.result(timeout=30) for f in futs]
+    srv.stop()
+    assert all(r.status == "ok" and r.forces.shape == (64, 2, 2) for r in res)
