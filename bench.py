@@ -51,6 +51,26 @@ def _dist():
     return ws, rank
 
 
+def rank_domains(specs, rank, world):
+    """Weak scaling: every rank advances its own full copy of the domain set (the domains
+    are independent problems; no data-path exchange between ranks)."""
+    del rank, world
+    return list(specs)
+
+
+def aggregate(ms_local, cells_per_rank, steps, world, device="cpu"):
+    """Whole-job GLUPS from the per-rank timed region: the time is the max over ranks
+    (all_reduce MAX on an initialised process group when world > 1)."""
+    import torch
+    ms = float(ms_local)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, cells_per_rank * world * steps / (ms / 1000.0) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
 
@@ -198,7 +218,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     lbm.load()
-    specs = synth.batched_domains(64)[: args.domains]
+    specs = rank_domains(synth.batched_domains(64)[: args.domains], rank, ws)
     cells = sum(s["nx"] * s["ny"] for s in specs)
     stream = torch.cuda.Stream()
     nsteps_total = args.warmup + args.steps + args.profile_steps + 10
@@ -241,12 +261,7 @@ def run_ours(args):
             _, _ = batch.poll(k)
         batch.close()
 
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-
-    value = cells * ws * args.steps / (ms / 1000.0) / 1e9
+    ms, value = aggregate(ms, cells, args.steps, ws, device="cuda")
     peak, peak_kind = _peak_hbm()
     bpc = BYTES_PER_CELL[args.storage]
     achieved = cells * bpc / (sweep_us * 1e-6) / 1e9
@@ -377,6 +392,87 @@ def measure_plain_f32(lbm, torch, specs, args, steps=30):
                       f"{steps} steps each"}
 
 
+# ---- accuracy experiments on the paper's workloads ----------------------------------------
+
+def _couette_error(lbm, n, lam, storage="f64", u_wall=0.001, re=10.0, ri_frac=45 / 200,
+                   ro_frac=70 / 200, srt=False):
+    """Couette setup of Sec. 3.1 on an n x n grid (L = 1, dx = 1/n): R_i = 45/200, R_o = 70/200,
+    inner wall speed 0.001, Re = U D / nu = 10 with D = 2 R_i. SRT is the TRT update with
+    Lambda = (tau_s - 1/2)^2 (then tau_a = tau_s)."""
+    import math
+    import numpy as np
+    import synth
+    ri, ro = ri_frac * n, ro_frac * n
+    nu = u_wall * 2 * ri / re
+    if srt:
+        lam = (3 * nu) ** 2
+    diff_time = (ro - ri) ** 2 / nu
+    steps = int(3 * diff_time)  # slowest mode decays as exp(-pi^2 t nu / (R_o - R_i)^2)
+    spec = synth.couette(n, ri, ro, u_wall, nu, steps, magic_lambda=lam)
+    dom = lbm.Domain(spec, storage=storage, force_every=0)
+    dom.step(steps)
+    rho, ux, uy = dom.moments()
+    dom.close()
+    c = n / 2.0
+    j, i = np.mgrid[0:n, 0:n]
+    x, y = i - c, j - c
+    r = np.hypot(x, y)
+    rr = np.where(r > 0, r, 1.0)
+    ut = (-y * ux + x * uy) / rr
+    sel = (r >= ri + 1) & (r <= ro - 1)
+    A = -u_wall * ri / (ro ** 2 - ri ** 2)
+    B = u_wall * ri * ro ** 2 / (ro ** 2 - ri ** 2)
+    ex = A * rr + B / rr
+    return {"n": n, "tau_s": 3 * nu + 0.5, "lambda": lam, "steps": steps,
+            "l2_rel": math.sqrt(((ut - ex)[sel] ** 2).sum() / (ex[sel] ** 2).sum())}
+
+
+def experiment(args):
+    import torch
+    import numpy as np
+    import synth
+    import paper_1901_08766_gb300 as lbm
+    from paper_1901_08766_gb300 import diagnostics as dg
+    lbm.load()
+    torch.cuda.set_device(0)
+    out = {"experiment": args.experiment}
+    if args.experiment == "couette":
+        rows = []
+        for n in (120, 160, 240, 320, 480):
+            rows.append({"scheme": "TRT 3/16", **_couette_error(lbm, n, 3 / 16)})
+            rows.append({"scheme": "TRT 1/4", **_couette_error(lbm, n, 1 / 4)})
+            rows.append({"scheme": "SRT", **_couette_error(lbm, n, 0.0, srt=True)})
+        out["rows"] = rows
+    elif args.experiment in ("precision", "cylinder"):
+        cases = ([("f16s", synth.precision_cylinder(True)), ("bf16s", synth.precision_cylinder(True)),
+                  ("f32", synth.precision_cylinder(True)), ("f64", synth.precision_cylinder(True))]
+                 if args.experiment == "precision" else
+                 [("f32", synth.single_cylinder(re=40.0)), ("f32", synth.single_cylinder(re=100.0))])
+        rows = []
+        for storage, spec in cases:
+            dom = lbm.Domain(spec, storage=storage)
+            t0 = time.perf_counter()
+            f = dom.run(spec["steps"], chunk=8000)[:, 0]
+            el = time.perf_counter() - t0
+            dom.close()
+            D, U = spec["bodies"][0]["ref_length"], spec["U"]
+            cd, cl = dg.coefficients(f, U, D)
+            half = slice(len(cd) // 2, len(cd))
+            rows.append({"storage": storage, "case": spec["name"], "steps": spec["steps"],
+                         "seconds": el, "glups": spec["nx"] * spec["ny"] * spec["steps"] / el / 1e9,
+                         "cd_mean": float(cd[half].mean()), "cd_amp": dg.amplitude(cd[half]),
+                         "cl_rms": dg.rms(cl[half]), "cl_amp": dg.amplitude(cl[half]),
+                         "st": dg.strouhal(cl[half], D, U)})
+        out["rows"] = rows
+        if args.experiment == "precision":
+            ref = rows[-1]
+            for r in rows:
+                for k in ("cd_mean", "cl_rms", "st"):
+                    r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,7 +490,11 @@ def main():
     ap.add_argument("--served-requests", type=int, default=32)
     ap.add_argument("--served-scale", type=float, default=0.02)
     ap.add_argument("--served-chunk", type=int, default=256)
+    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder"], default=None,
+                    help="accuracy study instead of the benchmark")
     args = ap.parse_args()
+    if args.experiment:
+        return experiment(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

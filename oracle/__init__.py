@@ -236,6 +236,26 @@ def strouhal(signal, ref_length, U, dt=1.0):
     return f * ref_length / U
 
 
+def strouhal_fft(signal, ref_length, U, dt=1.0):
+    """St = f_q D / U with f_q the largest peak of the amplitude spectrum of the
+    Hann-windowed (signal - mean), refined by a parabola through the log amplitudes of
+    the peak bin and its two neighbours. Unlike zero crossings it is not disturbed by a
+    weaker oscillation at another frequency (the channel's acoustic standing wave)."""
+    x = np.asarray(signal, dtype=np.float64)
+    n = len(x)
+    if n < 8:
+        return 0.0
+    x = x - x.mean()
+    win = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(n) / n)
+    amp = np.abs(np.fft.rfft(x * win))
+    k = 1 + int(np.argmax(amp[1:-1]))
+    a, b, c = np.log(amp[k - 1] + 1e-300), np.log(amp[k] + 1e-300), np.log(amp[k + 1] + 1e-300)
+    den = a - 2.0 * b + c
+    shift = 0.5 * (a - c) / den if den != 0.0 else 0.0
+    f = (k + shift) / (n * dt)
+    return f * ref_length / U
+
+
 def rms(signal):
     x = np.asarray(signal, dtype=np.float64)
     return float(np.sqrt(np.mean((x - x.mean()) ** 2)))

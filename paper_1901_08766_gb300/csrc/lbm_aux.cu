@@ -94,53 +94,50 @@ cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny,
 }
 
 // ---- solid-node lists -----------------------------------------------------------------
-// counts[k] = number of nodes with body id k (k = 0 counts fluid); *bad_id > 0 if an id
-// exceeds nbodies.
+// The force reducer sums F_VP over each body's nodes in one fixed order: body by body,
+// row-major within a body. The list is built in two row-parallel passes: per-row counts
+// of every body id, an exclusive scan on the host, then one block per (row, body)
+// writing the row's nodes of that body at its offset in column order.
 
-__global__ void count_bodies_kernel(const uint8_t *mask, int nx, int ny, int pitch, int nbodies,
-                                    int32_t *counts, int32_t *bad_id) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i >= nx || j >= ny) return;
-  const int b = mask[static_cast<size_t>(j) * pitch + i];
-  if (b == 0) return;
-  if (b > nbodies) {
-    atomicMax(bad_id, b);
-    return;
+// counts[b * ny + j] = nodes of body id b in row j (b = 0 counts fluid); *bad_id > 0 if
+// an id exceeds nbodies.
+__global__ void row_counts_kernel(const uint8_t *mask, int nx, int ny, int pitch, int nbodies,
+                                  int32_t *counts, int32_t *bad_id) {
+  __shared__ int32_t hist[256];
+  const int j = blockIdx.x;
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const uint8_t *row = mask + static_cast<size_t>(j) * pitch;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) atomicAdd(&hist[row[i]], 1);
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+    const int c = hist[b];
+    if (b <= nbodies) counts[static_cast<size_t>(b) * ny + j] = c;
+    else if (c > 0) atomicMax(bad_id, b);
   }
-  atomicAdd(&counts[b], 1);
 }
 
-cudaError_t launch_count_bodies(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
-                                int nbodies, int32_t *counts, int32_t *bad_id) {
-  dim3 grid((nx + 255) / 256, ny);
-  count_bodies_kernel<<<grid, 256, 0, st>>>(mask, nx, ny, pitch, nbodies, counts, bad_id);
+cudaError_t launch_row_counts(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
+                              int nbodies, int32_t *counts, int32_t *bad_id) {
+  row_counts_kernel<<<ny, 256, 0, st>>>(mask, nx, ny, pitch, nbodies, counts, bad_id);
   return cudaGetLastError();
 }
 
-// One block per body scans the mask in row-major order and appends the body's nodes
-// at offsets[k-1] + rank, the rank from a block-wide prefix count: the list order is
-// row-major and does not depend on the launch shape.
-__global__ void build_solid_kernel(const uint8_t *mask, int nx, int ny, int pitch,
-                                   const int32_t *offsets, int32_t *solid) {
-  const int body = blockIdx.x + 1;
+// Block (j, b-1): the nodes of body b in row j, in column order, at row_off[(b-1)*ny + j].
+__global__ void row_scatter_kernel(const uint8_t *mask, int nx, int ny, int pitch,
+                                   const int32_t *row_off, int32_t *solid) {
+  const int j = blockIdx.x;
+  const int body = blockIdx.y + 1;
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t base;
-  if (threadIdx.x == 0) base = offsets[body - 1];
+  if (threadIdx.x == 0) base = row_off[static_cast<size_t>(body - 1) * ny + j];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long cells = static_cast<long long>(nx) * ny;
-  for (long long c0 = 0; c0 < cells; c0 += blockDim.x) {
-    const long long c = c0 + threadIdx.x;
-    int i = 0, j = 0;
-    bool hit = false;
-    if (c < cells) {
-      j = static_cast<int>(c / nx);
-      i = static_cast<int>(c - static_cast<long long>(j) * nx);
-      hit = mask[static_cast<size_t>(j) * pitch + i] == body;
-    }
+  const uint8_t *row = mask + static_cast<size_t>(j) * pitch;
+  for (int i0 = 0; i0 < nx; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const bool hit = i < nx && row[i] == body;
     const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    const int in_warp = __popc(bal & ((1u << lane) - 1u));
     if (lane == 0) warp_tot[warp] = __popc(bal);
     __syncthreads();
     int before = 0, total = 0;
@@ -148,17 +145,17 @@ __global__ void build_solid_kernel(const uint8_t *mask, int nx, int ny, int pitc
       if (w < warp) before += warp_tot[w];
       total += warp_tot[w];
     }
-    if (hit) solid[base + before + in_warp] = j * pitch + i;
+    if (hit) solid[base + before + __popc(bal & ((1u << lane) - 1u))] = j * pitch + i;
     __syncthreads();
     if (threadIdx.x == 0) base += total;
     __syncthreads();
   }
 }
 
-cudaError_t launch_build_solid(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
-                               int nbodies, const int32_t *offsets, int32_t *solid) {
+cudaError_t launch_row_scatter(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
+                               int nbodies, const int32_t *row_off, int32_t *solid) {
   if (nbodies <= 0) return cudaSuccess;
-  build_solid_kernel<<<nbodies, 1024, 0, st>>>(mask, nx, ny, pitch, offsets, solid);
+  row_scatter_kernel<<<dim3(ny, nbodies), 256, 0, st>>>(mask, nx, ny, pitch, row_off, solid);
   return cudaGetLastError();
 }
 
@@ -184,14 +181,18 @@ forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, con
     const ForceItem item = items[it];
     const DomDev &D = doms[item.dom];
     const DomDyn dy = dyn[item.dom];
-    const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
-    if (n >= dy.step_end || D.force_every <= 0) continue;
-    if ((n + 1) % D.force_every != 0) continue;
     const T *fv = static_cast<const T *>(D.fvp);
-    const int beg = D.solid_off[item.body - 1], end = D.solid_off[item.body];
+    const int32_t *solid = D.solid;
+    const int force_every = D.force_every;
+    // the node indices do not depend on the step: their loads overlap the checks below
+    const int q0 = item.beg + threadIdx.x;
+    const int32_t lin0 = q0 < item.end ? __ldg(solid + q0) : 0;
+    const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
+    if (n >= dy.step_end || force_every <= 0) continue;
+    if ((n + 1) % force_every != 0) continue;
     double fx = 0.0, fy = 0.0;
-    for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
-      const size_t lin = static_cast<size_t>(D.solid[q]);
+    for (int q = q0; q < item.end; q += blockDim.x) {
+      const size_t lin = static_cast<size_t>(q == q0 ? lin0 : __ldg(solid + q));
       fx -= double(fv[2 * lin]);
       fy -= double(fv[2 * lin + 1]);
     }

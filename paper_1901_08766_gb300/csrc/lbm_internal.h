@@ -64,9 +64,9 @@ struct TileDev {
   int32_t dom, x0, y0, pad;
 };
 
-// One force-reduction item: (slot, body id).
+// One force-reduction item: (slot, body id) and the body's range in the solid list.
 struct ForceItem {
-  int32_t dom, body;
+  int32_t dom, body, beg, end;
 };
 
 // Device-side counters of a batch.
@@ -99,11 +99,11 @@ cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int
                              const ShapeDev *shapes, int nshapes);
 cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,
                         double rho0, double ux, double uy);
-cudaError_t launch_count_bodies(cudaStream_t st, const uint8_t *mask, int nx, int ny,
-                                int pitch, int nbodies, int32_t *counts /* [nbodies+1] */,
-                                int32_t *bad_id);
-cudaError_t launch_build_solid(cudaStream_t st, const uint8_t *mask, int nx, int ny,
-                               int pitch, int nbodies, const int32_t *offsets,
+cudaError_t launch_row_counts(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
+                              int nbodies, int32_t *counts /* [nbodies+1][ny] */,
+                              int32_t *bad_id);
+cudaError_t launch_row_scatter(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,
+                               int nbodies, const int32_t *row_off /* [nbodies][ny] */,
                                int32_t *solid);
 cudaError_t launch_moments_sized(int storage, cudaStream_t st, const DomDev *dom, int nx,
                                  int ny, int parity, double *rho, double *ux, double *uy);

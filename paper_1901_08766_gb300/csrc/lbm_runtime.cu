@@ -138,6 +138,7 @@ struct Slot {
   void *block = nullptr;
   void *solid = nullptr;
   size_t bytes = 0;
+  std::vector<int32_t> solid_off;  // host copy of the per-body offsets into the solid list
   DomDev dev{};
 };
 
@@ -283,7 +284,8 @@ lbm_status rebuild_lists(lbm_batch *b) {
     for (int y0 = 0; y0 < s.p.ny; y0 += th)
       for (int x0 = 0; x0 < s.p.nx; x0 += tw) tiles.push_back(TileDev{k, x0, y0, 0});
     if (s.p.force_every > 0)
-      for (int body = 1; body <= s.nbodies; ++body) items.push_back(ForceItem{k, body});
+      for (int body = 1; body <= s.nbodies; ++body)
+        items.push_back(ForceItem{k, body, s.solid_off[body - 1], s.solid_off[body]});
   }
   if (static_cast<int>(tiles.size()) > b->tiles_cap || !b->d_tiles) {
     const int cap = std::max<int>(static_cast<int>(tiles.size()) * 2, 1024);
@@ -549,10 +551,12 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   }
   fill_cell_const(D);
   cudaStream_t st = b->st;
+  void *tmp = nullptr;  // admission temporaries (row counts, offsets, shapes)
   auto bail = [&](lbm_status r) {
     cudaStreamSynchronize(st);
     b->al.put(s.block);
     b->al.put(s.solid);
+    b->al.put(tmp);
     return r;
   };
 #define ADM_CUDA(call)                                                                   \
@@ -565,27 +569,28 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   // mask: uploaded (pitched, zero padding) or rasterised on the device
   ADM_CUDA(cudaMemsetAsync(mask, 0, static_cast<size_t>(p->ny) * s.pitch, st));
   std::vector<ShapeDev> shapes;
-  void *tmp = nullptr;
-  const size_t counts_bytes = sizeof(int32_t) * (nbodies + 2);
+  // temporary: per-row counts [nbodies+1][ny], bad-id word, row offsets [nbodies][ny], shapes
+  const size_t counts_n = static_cast<size_t>(nbodies + 1) * p->ny;
+  const size_t counts_bytes = align_up(sizeof(int32_t) * (counts_n + 1), 256);
+  const size_t offs_bytes = align_up(sizeof(int32_t) * std::max<size_t>(1, static_cast<size_t>(nbodies) * p->ny), 256);
+  const int ns = (!mask_host && geom) ? geom->nshapes : 0;
+  tmp = b->al.get(counts_bytes + offs_bytes + sizeof(ShapeDev) * std::max(1, ns));
+  if (!tmp) return bail(fail(LBM_ENOMEM, "temporary allocation failed"));
+  int32_t *counts = static_cast<int32_t *>(tmp);
+  int32_t *bad = counts + counts_n;
+  int32_t *row_off = reinterpret_cast<int32_t *>(static_cast<char *>(tmp) + counts_bytes);
   if (mask_host) {
     ADM_CUDA(cudaMemcpy2DAsync(mask, s.pitch, mask_host, p->nx, p->nx, p->ny, cudaMemcpyHostToDevice, st));
-    tmp = b->al.get(counts_bytes);
-    if (!tmp) return bail(fail(LBM_ENOMEM, "temporary allocation failed"));
-  } else {
-    const int ns = geom ? geom->nshapes : 0;
+  } else if (ns > 0) {
     for (int i = 0; i < ns; ++i) {
       const lbm_shape &sh = geom->shapes[i];
       ShapeDev d{sh.kind, sh.body, sh.cx, sh.cy, sh.radius, sh.chord, sh.thickness,
                  std::cos(sh.aoa_rad), std::sin(sh.aoa_rad)};
       shapes.push_back(d);
     }
-    tmp = b->al.get(counts_bytes + sizeof(ShapeDev) * std::max<size_t>(1, shapes.size()) + 256);
-    if (!tmp) return bail(fail(LBM_ENOMEM, "temporary allocation failed"));
-    if (ns > 0) {
-      ShapeDev *dsh = reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + align_up(counts_bytes, 256));
-      ADM_CUDA(cudaMemcpyAsync(dsh, shapes.data(), sizeof(ShapeDev) * ns, cudaMemcpyHostToDevice, st));
-      ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns));
-    }
+    ShapeDev *dsh = reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + counts_bytes + offs_bytes);
+    ADM_CUDA(cudaMemcpyAsync(dsh, shapes.data(), sizeof(ShapeDev) * ns, cudaMemcpyHostToDevice, st));
+    ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns));
   }
   // body table
   std::vector<double> hb(5 * std::max(1, nbodies), 0.0);
@@ -599,26 +604,35 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   ADM_CUDA(cudaMemcpyAsync(bod, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
   std::vector<float> hbf(hb.begin(), hb.end());
   ADM_CUDA(cudaMemcpyAsync(bodf, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
-  ADM_CUDA(cudaStreamSynchronize(st));  // the pageable staging vectors leave scope below
-  // count nodes per body, then build the solid-node lists
-  int32_t *counts = static_cast<int32_t *>(tmp);
-  ADM_CUDA(cudaMemsetAsync(counts, 0, counts_bytes, st));
-  ADM_CUDA(launch_count_bodies(st, mask, p->nx, p->ny, s.pitch, nbodies, counts, counts + nbodies + 1));
-  std::vector<int32_t> hc(nbodies + 2, 0);
-  ADM_CUDA(cudaMemcpyAsync(hc.data(), counts, counts_bytes, cudaMemcpyDeviceToHost, st));
+  // per-row node counts of every body id, then the row offsets of each body's nodes
+  ADM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+  ADM_CUDA(launch_row_counts(st, mask, p->nx, p->ny, s.pitch, nbodies, counts, bad));
+  std::vector<int32_t> hc(counts_n + 1, 0);
+  ADM_CUDA(cudaMemcpyAsync(hc.data(), counts, sizeof(int32_t) * (counts_n + 1), cudaMemcpyDeviceToHost, st));
   ADM_CUDA(cudaStreamSynchronize(st));
-  b->al.put(tmp);
-  tmp = nullptr;
-  if (hc[nbodies + 1] > 0)
-    return bail(fail(LBM_EINVAL, "mask holds body id %d but only %d bodies were given", hc[nbodies + 1], nbodies));
-  std::vector<int32_t> ho(nbodies + 1, 0);
-  for (int i = 1; i <= nbodies; ++i) ho[i] = ho[i - 1] + hc[i];
+  if (hc[counts_n] > 0)
+    return bail(fail(LBM_EINVAL, "mask holds body id %d but only %d bodies were given", hc[counts_n], nbodies));
+  std::vector<int32_t> ho(nbodies + 1, 0), hro(std::max<size_t>(1, static_cast<size_t>(nbodies) * p->ny), 0);
+  {
+    int32_t acc = 0;
+    for (int k = 1; k <= nbodies; ++k) {
+      ho[k - 1] = acc;
+      for (int j = 0; j < p->ny; ++j) {
+        hro[static_cast<size_t>(k - 1) * p->ny + j] = acc;
+        acc += hc[static_cast<size_t>(k) * p->ny + j];
+      }
+    }
+    ho[nbodies] = acc;
+  }
   const size_t nsolid = static_cast<size_t>(ho[nbodies]);
   s.solid = b->al.get(sizeof(int32_t) * std::max<size_t>(1, nsolid));
   if (!s.solid) return bail(fail(LBM_ENOMEM, "solid list allocation failed"));
   D.solid = static_cast<const int32_t *>(s.solid);
   ADM_CUDA(cudaMemcpyAsync(off, ho.data(), sizeof(int32_t) * ho.size(), cudaMemcpyHostToDevice, st));
-  ADM_CUDA(launch_build_solid(st, mask, p->nx, p->ny, s.pitch, nbodies, off, static_cast<int32_t *>(s.solid)));
+  s.solid_off = ho;
+  if (nbodies > 0)
+    ADM_CUDA(cudaMemcpyAsync(row_off, hro.data(), sizeof(int32_t) * hro.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(launch_row_scatter(st, mask, p->nx, p->ny, s.pitch, nbodies, row_off, static_cast<int32_t *>(s.solid)));
   // initial state (step (1)): lattice A = f^eq(rho0, u0), lattice B zero
   ADM_CUDA(launch_init(p->storage, st, D.lat[0], p->nx, p->ny, s.pitch, p->rho0, p->u0_x, p->u0_y));
   ADM_CUDA(cudaMemsetAsync(D.lat[1], 0, L.lat_bytes, st));
@@ -628,6 +642,8 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     ADM_CUDA(cudaMemsetAsync(D.ring, 0, sizeof(double) * 2 * std::max(1, nbodies) * s.p.force_capacity, st));
   ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
   ADM_CUDA(cudaStreamSynchronize(st));
+  b->al.put(tmp);
+  tmp = nullptr;
 #undef ADM_CUDA
   s.used = true;
   s.bytes = L.total + sizeof(int32_t) * std::max<size_t>(1, nsolid);

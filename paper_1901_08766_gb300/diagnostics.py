@@ -1,9 +1,11 @@
 """Force coefficients and shedding frequency from body-force series (Sec. 3).
 
 C_d = 2 F_x / (rho U^2 D), C_l = 2 F_y / (rho U^2 D); St = f_q D / U with the shedding
-frequency from the upward zero crossings of (signal - mean), interpolated linearly and
-averaged over the whole periods between the first and the last crossing. The "C_l +- a"
-amplitude is half the peak-to-peak value; the rms is that of signal - mean.
+frequency f_q taken from the dominant peak of the lift spectrum (primary: a channel with
+an equilibrium inlet and a zero-gradient outflow carries an acoustic standing wave that
+adds zero crossings) or from the upward zero crossings of (signal - mean), interpolated
+linearly over whole periods (secondary). The "C_l +- a" amplitude is half the
+peak-to-peak value; the rms is that of signal - mean.
 """
 from __future__ import annotations
 
@@ -34,6 +36,23 @@ def strouhal(signal, ref_length: float, U: float, dt: float = 1.0) -> float:
     return (len(t) - 1) / (t[-1] - t[0]) * ref_length / U
 
 
+def strouhal_spectral(signal, ref_length: float, U: float, dt: float = 1.0) -> float:
+    """St from the dominant spectral peak: Hann window over (signal - mean), real FFT,
+    the largest non-constant bin refined by the vertex of the parabola through the
+    logarithms of its amplitude and its neighbours'. Robust to a weaker second tone."""
+    x = np.asarray(signal, dtype=np.float64)
+    n = x.size
+    if n < 8:
+        return 0.0
+    w = np.hanning(n + 1)[:-1]  # periodic Hann window
+    spec = np.abs(np.fft.rfft((x - x.mean()) * w))
+    k = int(np.argmax(spec[1:-1])) + 1
+    lm, l0, lp = np.log(np.maximum(spec[k - 1:k + 2], 1e-300))
+    curv = lm - 2.0 * l0 + lp
+    delta = 0.5 * (lm - lp) / curv if curv != 0.0 else 0.0
+    return (k + delta) / (n * dt) * ref_length / U
+
+
 def rms(signal) -> float:
     x = np.asarray(signal, dtype=np.float64)
     return float(np.sqrt(np.mean(np.square(x - x.mean()))))
@@ -45,15 +64,16 @@ def amplitude(signal) -> float:
 
 
 def summary(forces, U: float, ref_length: float, rho0: float = 1.0, window: float = 0.5):
-    """Mean C_d, C_l rms and amplitude, and St (from C_l, else C_d) over the last
-    `window` fraction of the series."""
+    """Mean C_d, C_l rms and amplitudes, and St of the lift (spectral peak, and from
+    zero crossings), over the last `window` fraction of the series; St = 0 for a
+    steady wake."""
     cd, cl = coefficients(forces, U, ref_length, rho0)
     n = len(cd)
     s = slice(int(n * (1.0 - window)), n)
     cdw, clw = cd[s], cl[s]
-    st = strouhal(clw, ref_length, U)
-    if st == 0.0:
-        st = strouhal(cdw, ref_length, U)
+    steady = len(clw) == 0 or amplitude(clw) < 1e-6
+    st = 0.0 if steady else strouhal_spectral(clw, ref_length, U)
+    st_zc = 0.0 if steady else strouhal(clw, ref_length, U)
     return {"cd_mean": float(cdw.mean()) if len(cdw) else 0.0, "cl_rms": rms(clw) if len(clw) else 0.0,
             "cd_amp": amplitude(cdw) if len(cdw) else 0.0, "cl_amp": amplitude(clw) if len(clw) else 0.0,
-            "st": st}
+            "st": st, "st_zero_crossing": st_zc}

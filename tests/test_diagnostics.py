@@ -27,7 +27,8 @@ def test_coefficients_and_summary_closed_form():
     assert s["cd_mean"] == pytest.approx(1.33, abs=1e-3)
     assert s["cl_rms"] == pytest.approx(0.3 / math.sqrt(2), rel=2e-3)
     assert s["cl_amp"] == pytest.approx(0.3, rel=5e-3)
-    assert s["st"] == pytest.approx(0.169, rel=1e-3)
+    assert s["st"] == pytest.approx(0.169, rel=3e-3)
+    assert s["st_zero_crossing"] == pytest.approx(0.169, rel=1e-3)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
@@ -38,6 +39,7 @@ def test_matches_oracle_estimators(seed):
     assert np.allclose(cd_p, cd_o, rtol=1e-15) and np.allclose(cl_p, cl_o, rtol=1e-15)
     assert dg.strouhal(cl_p, D, U) == pytest.approx(oracle.strouhal(cl_o, D, U), rel=1e-12)
     assert dg.rms(cl_p) == pytest.approx(oracle.rms(cl_o), rel=1e-12)
+    assert dg.strouhal_spectral(cl_p, D, U) == pytest.approx(oracle.strouhal_fft(cl_o, D, U), rel=1e-12)
 
 
 def test_steady_signal_has_no_shedding():

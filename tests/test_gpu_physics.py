@@ -1,0 +1,108 @@
+"""Physics of the GPU path on the paper's workloads.
+
+- Cylindrical Couette flow (Sec. 3.1), FP64: matches the oracle after 20 000 steps and
+  the closed form u_theta = A r + B/r; reduced storages stay within a velocity-field
+  relative L2 of 1e-3 of FP64 (BF16-shifted: see the bound below).
+- Single cylinder (Sec. 3.2), FP32: C_d and St close to Table (high-Re) / (low-Re) of
+  the paper (plausibility only: domain and edges differ from the paper's).
+- Precision sweep at the oracle's size (600x300, D = 30, Re = 200): mean C_d, C_l rms and
+  St of every storage within 1 % of the stored FP64 oracle values.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1901_08766_gb300 import diagnostics as dg
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _couette_fields(lbm, storage, steps=20000):
+    spec = synth.couette(steps=steps)
+    dom = lbm.Domain(spec, storage=storage, force_every=0)
+    dom.step(steps)
+    rho, ux, uy = dom.moments()
+    pops = dom.get_populations()
+    dom.close()
+    return spec, ux, uy, pops
+
+
+def _utheta(ux, uy, n=128):
+    c = n / 2.0
+    j, i = np.mgrid[0:n, 0:n]
+    x, y = i - c, j - c
+    r = np.hypot(x, y)
+    rr = np.where(r > 0, r, 1.0)
+    return (-y * ux + x * uy) / rr, r
+
+
+def test_couette_fp64_matches_oracle_and_closed_form(lbm):
+    spec, ux, uy, pops = _couette_fields(lbm, "f64")
+    ora = oracle.Domain(spec)
+    ora.run(spec["steps"], want_forces=False)
+    assert np.max(np.abs(pops - ora.g) / np.abs(ora.g)) <= 1e-10
+    ut, r = _utheta(ux, uy)
+    sel = (r >= 21) & (r <= 49)
+    ri, ro, u0 = 20.0, 50.0, 0.01
+    A = -u0 * ri / (ro ** 2 - ri ** 2)
+    B = u0 * ri * ro ** 2 / (ro ** 2 - ri ** 2)
+    exact = A * r + B / np.where(r > 0, r, 1.0)
+    err = math.sqrt(((ut - exact)[sel] ** 2).sum() / (exact[sel] ** 2).sum())
+    assert err < 0.03
+
+
+@pytest.mark.parametrize("storage,bound", [("f32", 1e-3), ("f16s", 1e-3), ("bf16s", 1e-2)])
+def test_couette_reduced_precision_velocity_l2(lbm, storage, bound):
+    # Velocity-field relative L2 against FP64 storage after 20 000 steps. FP16-shifted
+    # and FP32 must meet 1e-3; BF16 keeps 8 mantissa bits, so a population of ~3e-3 is
+    # held to ~1.5e-5, about 1e-3 of the 0.01 wall speed per population: its bound is 1e-2.
+    _, ux64, uy64, _ = _couette_fields(lbm, "f64")
+    _, ux, uy, _ = _couette_fields(lbm, storage)
+    num = np.sqrt(((ux - ux64) ** 2 + (uy - uy64) ** 2).sum())
+    den = np.sqrt((ux64 ** 2 + uy64 ** 2).sum())
+    print(f"{storage}: velocity relative L2 vs FP64 = {num / den:.3e}")
+    assert num / den <= bound
+
+
+@pytest.mark.parametrize("re,cd,st,steps", [(100.0, 1.336, 0.169, 120000), (40.0, 1.55, None, 60000)])
+def test_single_cylinder_against_paper_tables(lbm, re, cd, st, steps):
+    # Table (high-Re): Re 100 gives C_d 1.336, St 0.169; Table (low-Re): Re 40 gives C_d 1.55.
+    # The domain (1600x800, free-slip walls) differs from the paper's 2048x1024: 10 % on
+    # C_d and 5 % on St are plausibility bands.
+    # centre offset half a cell in y: shedding starts from the geometry instead of
+    # waiting for roundoff to break the symmetry of a centred cylinder
+    spec = synth.single_cylinder(re=re, steps=steps, cy=400.5)
+    dom = lbm.Domain(spec, storage="f32")
+    f = dom.run(steps, chunk=8000)[:, 0]
+    dom.close()
+    s = dg.summary(f, spec["U"], spec["bodies"][0]["ref_length"], window=0.3)
+    print(f"Re {re}: {s}")
+    assert abs(s["cd_mean"] - cd) / cd < 0.10
+    if st is not None:
+        assert abs(s["st"] - st) / st < 0.05
+    else:
+        assert s["cl_rms"] < 0.01  # steady wake
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+def test_precision_sweep_against_oracle(lbm, storage):
+    path = os.path.join(GOLDEN, "precision_cylinder_600x300.json")
+    ref = json.load(open(path))
+    spec = synth.precision_cylinder(large=False)
+    dom = lbm.Domain(spec, storage=storage)
+    f = dom.run(spec["steps"], chunk=8000)[:, 0]
+    dom.close()
+    D, U = spec["bodies"][0]["ref_length"], spec["U"]
+    cd, cl = dg.coefficients(f, U, D)
+    half = slice(len(cd) // 2, len(cd))
+    got = {"cd_mean": cd[half].mean(), "cl_rms": dg.rms(cl[half]),
+           "st": dg.strouhal_spectral(cl[half], D, U)}
+    print(storage, got, {k: ref[k] for k in got})
+    for k in got:
+        assert abs(got[k] - ref[k]) / abs(ref[k]) < 0.01, k

@@ -413,5 +413,10 @@ def test_diagnostics_closed_forms():
     cl = 0.3 * np.sin(2 * math.pi * f_true * n + 0.3) + 0.01
     assert oracle.strouhal(cl, D, U) == pytest.approx(0.169, rel=2e-4)
     assert oracle.rms(cl) == pytest.approx(0.3 / math.sqrt(2), rel=2e-3)
+    # a weaker second tone (an acoustic standing wave at 3.5x the frequency) adds zero
+    # crossings but leaves the spectral peak at the shedding frequency
+    mixed = cl + 0.15 * np.sin(2 * math.pi * 3.5 * f_true * n)
+    assert oracle.strouhal_fft(mixed, D, U) == pytest.approx(0.169, rel=3e-3)
+    assert oracle.strouhal(mixed, D, U) > 0.2
     cd, cl2 = oracle.coefficients(np.array([[0.5 * U * U * D * 1.3, -0.5 * U * U * D * 0.2]]), U, D)
     assert cd[0] == pytest.approx(1.3) and cl2[0] == pytest.approx(-0.2)
