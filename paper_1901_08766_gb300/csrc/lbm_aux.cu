@@ -75,7 +75,7 @@ __global__ void init_kernel(typename Codec<S>::E *lat, int nx, int ny, int pitch
   const double usq = ux * ux + uy * uy;
   // Eq. (feq) with c_s^2 = 1/3; shifted storage keeps f^eq - w rho0
   const double dev = rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-  double val = Cd::kShift ? dev : rho0 * w + dev;
+  double val = Cd::kStoreShifted ? dev : rho0 * w + dev;
   if (i >= nx) val = 0.0;
   lat[(static_cast<size_t>(a) * ny + j) * pitch + i] = Cd::enc(typename Cd::T(val));
 }
@@ -260,7 +260,7 @@ __global__ void moments_kernel(const DomDev *dom, int parity, double *rho, doubl
   const int b = D.mask[static_cast<size_t>(j) * D.pitch + i];
   T uox = T(0), uoy = T(0);
   if (b) body_velocity<T>(D, b, i, j, uox, uoy);
-  const NodeMacro<T> m = node_macro<T, Cd::kShift, true>(x, C, b != 0, uox, uoy);
+  const NodeMacro<T> m = node_macro<T, Cd::kShiftCompute, true>(x, C, b != 0, uox, uoy);
   const size_t c = static_cast<size_t>(j) * D.nx + i;
   if (rho) rho[c] = double(m.rho);
   if (ux) ux[c] = double(m.ux);

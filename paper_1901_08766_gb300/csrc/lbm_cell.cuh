@@ -29,27 +29,34 @@ __host__ __device__ constexpr int ey_of(int a) {
 
 // ---- storage codecs --------------------------------------------------------------------
 // F64 / F32 store f; F16S / BF16S store f - w_alpha rho0 (rounded to nearest even).
+// kStoreShifted: the stored value is f - w_alpha rho0. kShiftCompute: the node update
+// works on f - w_alpha rho0 (for F32 storage the shift is subtracted after loading, exactly,
+// and added back before storing), so that no O(1) population meets a rounded relaxation
+// constant: that would bias mass by about one FP32 unit per node and step.
 
 template <int S> struct Codec;
 
 template <> struct Codec<LBM_F64> {
   using E = double;
   using T = double;
-  static constexpr bool kShift = false;
+  static constexpr bool kStoreShifted = false;
+  static constexpr bool kShiftCompute = false;
   __device__ static T dec(E e) { return e; }
   __device__ static E enc(T t) { return t; }
 };
 template <> struct Codec<LBM_F32> {
   using E = float;
   using T = float;
-  static constexpr bool kShift = false;
+  static constexpr bool kStoreShifted = false;
+  static constexpr bool kShiftCompute = true;
   __device__ static T dec(E e) { return e; }
   __device__ static E enc(T t) { return t; }
 };
 template <> struct Codec<LBM_F16S> {
   using E = uint16_t;
   using T = float;
-  static constexpr bool kShift = true;
+  static constexpr bool kStoreShifted = true;
+  static constexpr bool kShiftCompute = true;
   __device__ static T dec(E e) { return __half2float(__ushort_as_half(e)); }
   __device__ static E enc(T t) { return __half_as_ushort(__float2half_rn(t)); }
   // two packed elements (low = first)
@@ -64,7 +71,8 @@ template <> struct Codec<LBM_F16S> {
 template <> struct Codec<LBM_BF16S> {
   using E = uint16_t;
   using T = float;
-  static constexpr bool kShift = true;
+  static constexpr bool kStoreShifted = true;
+  static constexpr bool kShiftCompute = true;
   __device__ static T dec(E e) { return __uint_as_float(static_cast<uint32_t>(e) << 16); }
   __device__ static E enc(T t) { return __bfloat16_as_ushort(__float2bfloat16_rn(t)); }
   __device__ static float2 dec2(uint32_t w) {
@@ -77,6 +85,11 @@ template <> struct Codec<LBM_BF16S> {
 };
 
 // ---- per-domain constants in compute precision -----------------------------------------
+
+// w_alpha rho0 of direction a in compute precision (the shift of the shifted variables)
+template <typename T> __device__ __forceinline__ T shift_of(const CellConst<T> &c, int a) {
+  return a == 0 ? c.wr0 : (a < 5 ? c.wr1 : c.wr2);
+}
 
 template <typename T> __device__ __forceinline__ const CellConst<T> &cell_const(const DomDev &d);
 template <> __device__ __forceinline__ const CellConst<float> &cell_const<float>(const DomDev &d) {
@@ -225,7 +238,9 @@ __device__ __forceinline__ typename Codec<S>::T pull_scalar(const DomDev &d, con
     else sy -= d.ny;
   }
   const E *p = static_cast<const E *>(lat);
-  return Cd::dec(p[(static_cast<size_t>(src) * d.ny + sy) * d.pitch + sx]);
+  typename Cd::T x = Cd::dec(p[(static_cast<size_t>(src) * d.ny + sy) * d.pitch + sx]);
+  if (Cd::kShiftCompute && !Cd::kStoreShifted) x -= shift_of(cell_const<typename Cd::T>(d), a);
+  return x;
 }
 
 }  // namespace lbm

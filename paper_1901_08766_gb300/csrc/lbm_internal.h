@@ -26,7 +26,8 @@ template <typename T> struct CellConst {
   T mw1, mw2;        // 3 omega- * w for the axis and diagonal classes
   T kw0, kw1, kw2;   // (1 - omega+/2) * w per class (Guo symmetric part)
   T qw1, qw2;        // 3 (1 - omega-/2) * w per class (Guo antisymmetric part)
-  T ghost[kQ];       // inlet populations in compute space (shifted if storage is)
+  T wr0, wr1, wr2;   // w * rho0 per class: the shift of the shifted compute variables
+  T ghost[kQ];       // inlet populations in compute space, as a stored node would hold them
 };
 
 // Per-domain static description, resident in device memory (one per batch slot).
@@ -46,7 +47,7 @@ struct DomDev {
   double omega_p, omega_m;  // 1/tau_s, 1/tau_a
   double inv_2eta1;         // 1 / (2 eta + 1)
   double rho0;
-  double ghost[kQ];         // inlet populations in compute space (shifted if storage is)
+  double ghost[kQ];         // inlet populations f^eq(rho0, u_in) (minus w rho0 if storage is shifted)
   CellConst<float> cf;      // collision constants for FP32 compute
   CellConst<double> cd;     // collision constants for FP64 compute
 };
@@ -93,7 +94,7 @@ struct ShapeDev {
 cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *doms,
                           const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
                           int s);
-void fill_cell_const(DomDev &d);
+void fill_cell_const(DomDev &d, int storage);
 cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
 cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
                              const ShapeDev *shapes, int nshapes);

@@ -11,6 +11,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -145,7 +148,7 @@ struct Slot {
 }  // namespace
 
 // Collision constants of a domain in FP32 and FP64 (per-class products of the relaxation
-// rates with the D2Q9 weights, the penalization factor and the inlet ghost).
+// rates with the D2Q9 weights, the penalization factor, the shifts and the inlet ghost).
 template <typename T> void fill_const(CellConst<T> &c, const DomDev &d) {
   const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
   const double op = d.omega_p, om = d.omega_m;
@@ -166,12 +169,30 @@ template <typename T> void fill_const(CellConst<T> &c, const DomDev &d) {
   c.kw2 = T((1.0 - 0.5 * op) * w2);
   c.qw1 = T(3.0 * (1.0 - 0.5 * om) * w1);
   c.qw2 = T(3.0 * (1.0 - 0.5 * om) * w2);
+  c.wr0 = T(w0 * d.rho0);
+  c.wr1 = T(w1 * d.rho0);
+  c.wr2 = T(w2 * d.rho0);
   for (int a = 0; a < kQ; ++a) c.ghost[a] = T(d.ghost[a]);
 }
 
-void fill_cell_const(DomDev &d) {
-  fill_const(d.cf, d);
+// The inlet ghost enters the update like a stored node: in FP32 compute it is the value
+// an FP32/FP16/BF16 lattice would hold for f^eq(rho0, u_in), so that the inflow and the
+// free stream leaving through the outflow carry the same rounding (otherwise the
+// mismatch adds or removes mass at every step).
+void fill_cell_const(DomDev &d, int storage) {
   fill_const(d.cd, d);
+  fill_const(d.cf, d);
+  const double w[kQ] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  for (int a = 0; a < kQ; ++a) {
+    const float shift = float(w[a] * d.rho0);
+    if (storage == LBM_F32) {
+      d.cf.ghost[a] = float(d.ghost[a]) - shift;  // stored f, minus the shift as after loading
+    } else if (storage == LBM_F16S) {
+      d.cf.ghost[a] = __half2float(__float2half_rn(float(d.ghost[a])));
+    } else if (storage == LBM_BF16S) {
+      d.cf.ghost[a] = __bfloat162float(__float2bfloat16_rn(float(d.ghost[a])));
+    }
+  }
 }
 
 }  // namespace lbm
@@ -549,7 +570,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
       D.ghost[a] = shift ? dev : p->rho0 * w[a] + dev;
     }
   }
-  fill_cell_const(D);
+  fill_cell_const(D, p->storage);
   cudaStream_t st = b->st;
   void *tmp = nullptr;  // admission temporaries (row counts, offsets, shapes)
   auto bail = [&](lbm_status r) {

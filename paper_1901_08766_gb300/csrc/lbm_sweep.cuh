@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
   using T = typename Cd::T;
-  constexpr bool SHIFT = Cd::kShift;
+  constexpr bool SHIFT = Cd::kShiftCompute;
+  constexpr bool kAddShift = Cd::kShiftCompute && !Cd::kStoreShifted;
   constexpr int kStrip = 32 * V;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -387,7 +388,15 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
         for (int k = 0; k < V; ++k) {
           T x[kQ];
           decode_cell<S, V>(v, k, x);
+          if constexpr (kAddShift) {
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) x[a] -= shift_of(C, a);  // exact (Sterbenz)
+          }
           update(x, k);
+          if constexpr (kAddShift) {
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) x[a] += shift_of(C, a);
+          }
 #pragma unroll
           for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
         }

@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
   using E = typename Cd::E;
   using T = typename Cd::T;
   using G = TmaGeom<S, V>;
-  constexpr bool SHIFT = Cd::kShift;
+  constexpr bool SHIFT = Cd::kShiftCompute;
+  constexpr bool kAddShift = Cd::kShiftCompute && !Cd::kStoreShifted;
   constexpr int kStrip = G::kStrip;
   constexpr int H = G::kHalo;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -324,7 +325,15 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
       for (int k = 0; k < V; ++k) {
         T x[kQ];
         decode_cell<S, V>(v, k, x);
+        if constexpr (kAddShift) {
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) x[a] -= shift_of(C, a);  // exact (Sterbenz)
+        }
         update(x, k);
+        if constexpr (kAddShift) {
+#pragma unroll
+          for (int a = 0; a < kQ; ++a) x[a] += shift_of(C, a);
+        }
 #pragma unroll
         for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
       }

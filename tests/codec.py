@@ -59,3 +59,14 @@ def stored_ulp(values_shifted, storage):
     if storage == "f32":
         return np.spacing(a.astype(np.float32)).astype(np.float64)
     return np.spacing(a)
+
+
+def ghost_ulp(spec, storage):
+    """One unit of the stored type at the inlet ghost populations f^eq(rho0, u_in) (shifted
+    for the 16-bit types): the library holds the ghost as the stored type would."""
+    g = oracle.equilibrium(spec["rho0"], *spec["u_in"])
+    if storage in ("f16s", "bf16s"):
+        g = g - oracle.W
+    if storage == "f64":
+        return 0.0
+    return float(stored_ulp(g, storage).max())

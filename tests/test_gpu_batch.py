@@ -128,8 +128,9 @@ def test_full_size_batch_one_step_sampled_parity(lbm):
         ora = oracle.Domain(s, g=codec.decode(raw0, "f16s"))
         f_ora = ora.run(1)
         got = codec.decode(batch.get_populations(slots[d]), "f16s")
-        ulp = codec.stored_ulp(ora.g - codec.W, "f16s")
-        assert np.all(np.abs(got - ora.g) <= ulp + 2e-8)
+        tol = codec.stored_ulp(ora.g - codec.W, "f16s") + 2e-8
+        tol[:, :, 0] += codec.ghost_ulp(s, "f16s")  # inlet ghost as the stored type holds it
+        assert np.all(np.abs(got - ora.g) <= tol)
         f_gpu, _ = batch.poll(slots[d])
         assert np.allclose(f_gpu, f_ora, rtol=1e-4, atol=1e-5)
     batch.close()

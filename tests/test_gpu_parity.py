@@ -69,6 +69,10 @@ def test_reduced_precision_one_step_within_one_unit(lbm, storage, case):
     ulp = codec.stored_ulp(want_shifted, storage)
     # FP32 arithmetic on values of order one adds a few 1e-8 before rounding
     tol = ulp + (3e-7 if storage == "f32" else 2e-8)
+    if spec["edges"]["west"] == "inlet":
+        # the GPU's inlet ghost is f^eq(rho0, u_in) as the stored type holds it (the
+        # oracle's is exact): up to one more unit of the ghost's magnitude at column 0
+        tol[:, :, 0] += codec.ghost_ulp(spec, storage)
     assert np.all(np.abs(got - ora.g) <= tol)
 
 
@@ -126,8 +130,9 @@ def test_initial_state_and_moments(lbm, storage):
     rho, ux, uy = dom.moments()
     o = oracle.Domain(spec, g=codec.decode(raw0, storage))
     r2, x2, y2 = o.moments()
-    t = 1e-14 if storage == "f64" else 2e-6
-    assert np.abs(rho - r2).max() <= t and np.abs(ux - x2).max() <= t and np.abs(uy - y2).max() <= t
+    t = np.full(rho.shape, 1e-14 if storage == "f64" else 2e-6)
+    t[:, 0] += 3 * codec.ghost_ulp(spec, storage)  # three ghost populations enter column 0
+    assert np.all(np.abs(rho - r2) <= t) and np.all(np.abs(ux - x2) <= t) and np.all(np.abs(uy - y2) <= t)
     dom.close()
 
 

@@ -21,7 +21,7 @@ def test_served_results_equal_alone(lbm, storage):
     from paper_1901_08766_gb300.server import Server
     specs, steps = _requests()
     # budget for about two requests at a time: later ones queue and join mid-run
-    budget = int(2.2 * max(lbm.domain_bytes(s, storage, force_capacity=72) for s in specs))
+    budget = int(1.6 * max(lbm.domain_bytes(s, storage, force_capacity=72) for s in specs))
     srv = Server(storage=storage, hbm_budget=budget, chunk_steps=64, graph_steps=16)
     futs = [srv.submit(s, nsteps=n, arrival=srv.clock() + 0.002 * i)
             for i, (s, n) in enumerate(zip(specs, steps))]
