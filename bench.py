@@ -458,11 +458,13 @@ def experiment(args):
             D, U = spec["bodies"][0]["ref_length"], spec["U"]
             cd, cl = dg.coefficients(f, U, D)
             half = slice(len(cd) // 2, len(cd))
+            steady = dg.amplitude(cl[half]) < 1e-3
             rows.append({"storage": storage, "case": spec["name"], "steps": spec["steps"],
                          "seconds": el, "glups": spec["nx"] * spec["ny"] * spec["steps"] / el / 1e9,
                          "cd_mean": float(cd[half].mean()), "cd_amp": dg.amplitude(cd[half]),
                          "cl_rms": dg.rms(cl[half]), "cl_amp": dg.amplitude(cl[half]),
-                         "st": dg.strouhal(cl[half], D, U)})
+                         "st": 0.0 if steady else dg.strouhal_spectral(cl[half], D, U),
+                         "st_zero_crossing": 0.0 if steady else dg.strouhal(cl[half], D, U)})
         out["rows"] = rows
         if args.experiment == "precision":
             ref = rows[-1]
