@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
     const unsigned valid_bits =
         east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u))
                   : (1u << V) - 1u;
+    unsigned bad_bits = 0u;
 
     auto update = [&](T (&x)[kQ], int k) {
       if (k == 0 && west_edge && west_inlet && lane == 0) {
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         m = node_macro<T, SHIFT, false>(x, C, false, T(0), T(0));
         collide<T, SHIFT, false>(x, m, C);
       }
-      if (((valid_bits >> k) & 1u) && !(m.rho > T(0.01) && m.rho < T(100))) unstable = 1;
+      bad_bits |= (fabs(m.rho - T(50.005)) < T(49.995) ? 0u : 1u) << k;
     };
     if constexpr (sizeof(E) == 2) {
 #pragma unroll
@@ -338,6 +339,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
       }
     }
+    if (bad_bits & valid_bits) unstable = 1;
     if (east_edge) {
 #pragma unroll
       for (int k = 0; k < V; ++k)
