@@ -293,7 +293,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f16s storage, f32 compute"
             if args.storage == "f16s" else args.storage, "data": "synthetic",
             "config": dict(_config(args, specs), tile={"vec": tile[0], "warps": tile[1], "rows": tile[2],
-                                                       "pipeline": "tma" if tile[3] else "direct"},
+                                                       "pipeline": ["direct", "tma", "prefetch"][tile[3]]},
                            autotune_best_us=tune_us),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "plain_f32_per_domain": plain, "served": served}

@@ -281,7 +281,7 @@ void drop_graph(lbm_batch *b) {
 lbm_status set_config(lbm_batch *b, int vec, int warps, int rows, int pipe) {
   if (!vec_ok(b->storage, vec)) return fail(LBM_EINVAL, "cells per thread %d unsupported for storage %d", vec, b->storage);
   if (warps < 1 || warps > 16 || rows < 1 || rows > 16) return fail(LBM_EINVAL, "warps and rows must be in [1, 16]");
-  if (pipe != 0 && pipe != 1) return fail(LBM_EINVAL, "pipeline must be 0 (direct) or 1 (TMA-staged)");
+  if (pipe < 0 || pipe > 2) return fail(LBM_EINVAL, "pipeline must be 0 (direct), 1 (TMA-staged) or 2 (register-prefetched)");
   const int occ = sweep_occupancy(b->storage, vec, pipe, warps);
   if (occ <= 0) return fail(LBM_ECUDA, "sweep kernel cannot run with %d warps per block", warps);
   b->vec = vec;
@@ -864,7 +864,7 @@ lbm_status autotune(lbm_batch *b, int reps, double *best_us) {
   double best = 1e300;
   int bv = b->vec, bw = b->warps, br = b->rows, bp = b->pipe;
   lbm_status rc = LBM_OK;
-  for (int p = 0; p < 2 && rc == LBM_OK; ++p)
+  for (int p = 0; p < 3 && rc == LBM_OK; ++p)
     for (int v : vecs)
       for (int w : warp_opts)
         for (int r : row_opts) {

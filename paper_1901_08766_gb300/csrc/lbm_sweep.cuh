@@ -194,8 +194,18 @@ __device__ __forceinline__ void decode_cell(const Strip<S, V> (&v)[kQ], int k,
   for (int a = 0; a < kQ; ++a) x[a] = Codec<S>::dec(v[a].get(k));
 }
 
-template <int S, int V>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
+// One strip row of the nine source populations, its strip-end values and body ids.
+template <int S, int V> struct RowData {
+  Strip<S, V> v[kQ];
+  typename Codec<S>::E end_in[kQ];
+  uint8_t b[V];
+};
+
+// The sweep body. PF = false: each warp loads a row, then updates it. PF = true: the
+// loads of the warp's next row are issued into a second register set before the current
+// row is updated, so that they overlap the update (more registers, fewer warps).
+template <int S, int V, bool PF>
+__device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
   using T = typename Cd::T;
@@ -262,10 +272,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
     const bool has_last = east_edge && k_last >= 0 && k_last < V;
     const size_t plane = static_cast<size_t>(ny) * pitch;
 
-    for (int r = 0; r < args.rows; ++r) {
-      const int j = tile.y0 + warp * args.rows + r;
-      if (j >= ny) break;
-      // ---- phase 1: every load of the row ------------------------------------------
+    // ---- phase 1: every load of row j ------------------------------------------------
+    auto load_row = [&](RowData<S, V> &R, const int j) {
       const E *row[kQ];
       const E *rj = src + static_cast<size_t>(j) * pitch;
       if (j > 0 && j < ny - 1) {
@@ -287,8 +295,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
           row[a] = src + sa * plane + static_cast<size_t>(sy) * pitch;
         }
       }
-      Strip<S, V> v[kQ];
-      E end_in[kQ];
+      auto &v = R.v;
+      auto &end_in = R.end_in;
       // Loads are issued by every lane without branches: a lane past the end of the row
       // reads a clamped (valid) strip whose results are neither stored nor used, and the
       // strip-end columns are read by all lanes at one common address (a broadcast) and
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
         if (ex == 1) end_in[a] = __ldg(row[a] + col_l);
         else if (ex == -1) end_in[a] = __ldg(row[a] + col_r);
       }
-      uint8_t b[V];
+      auto &b = R.b;
       {
         const uint8_t *mrow = dmask + static_cast<size_t>(j) * pitch + xl_ld;
         if constexpr (V == 8) {
@@ -327,6 +335,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
 #pragma unroll
         for (int k = 0; k < V; ++k) b[k] = lane_on ? b[k] : uint8_t(0);
       }
+    };
+    // ---- phases 2 and 3: shift, update and store row j ---------------------------------
+    auto process_row = [&](RowData<S, V> &R, const int j) {
+      auto &v = R.v;
+      const auto &end_in = R.end_in;
+      const auto &b = R.b;
       // ---- phase 2: the +-1 x-shift of the pull, in registers -----------------------
 #pragma unroll
       for (int a = 0; a < kQ; ++a) {
@@ -444,6 +458,29 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
         for (int a = 0; a < kQ; ++a)
           v[a].store(dst + a * plane + static_cast<size_t>(j) * pitch + xl);
       }
+    };
+    const int j0 = tile.y0 + warp * args.rows;
+    if constexpr (!PF) {
+      for (int r = 0; r < args.rows; ++r) {
+        const int j = j0 + r;
+        if (j >= ny) break;
+        RowData<S, V> R;
+        load_row(R, j);
+        process_row(R, j);
+      }
+    } else {
+      const int jend = min(j0 + args.rows, ny);
+      if (j0 < jend) {
+        RowData<S, V> A, B;
+        load_row(A, j0);
+        for (int j = j0; j < jend; j += 2) {
+          if (j + 1 < jend) load_row(B, j + 1);
+          process_row(A, j);
+          if (j + 1 >= jend) break;
+          if (j + 2 < jend) load_row(A, j + 2);
+          process_row(B, j + 1);
+        }
+      }
     }
     if (__any_sync(0xffffffffu, unstable)) {
       if (lane == 0) atomicOr(D.status, 1);
@@ -453,16 +490,45 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
 }
 
 template <int S, int V>
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
+  sweep_body<S, V, false>(args, s);
+}
+
+template <int S, int V>
+__global__ void __launch_bounds__(256) sweep_pf_kernel(SweepArgs args, int s) {
+  sweep_body<S, V, true>(args, s);
+}
+
+template <int S, int V>
 cudaError_t launch_sweep_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s) {
   sweep_kernel<S, V><<<grid, warps * 32, 0, st>>>(a, s);
+  return cudaGetLastError();
+}
+
+template <int S, int V>
+cudaError_t launch_sweep_pf_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s) {
+  sweep_pf_kernel<S, V><<<grid, warps * 32, 0, st>>>(a, s);
   return cudaGetLastError();
 }
 
 template <int S, int V> int max_blocks_t(int warps) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<S, V>, warps * 32, 0) !=
-      cudaSuccess)
+      cudaSuccess) {
+    cudaGetLastError();
     return 0;
+  }
+  return n;
+}
+
+template <int S, int V> int max_blocks_pf_t(int warps) {
+  if (warps * 32 > 256) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_pf_kernel<S, V>, warps * 32, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return n;
 }
 

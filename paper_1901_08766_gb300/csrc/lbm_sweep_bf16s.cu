@@ -1,5 +1,5 @@
 // Sweep instantiations for LBM_BF16S storage (cells per thread 4 and 8; direct
-// and TMA-staged row loads).
+// TMA-staged and register-prefetched row loads).
 #include "lbm_sweep_tma.cuh"
 
 namespace lbm {
@@ -9,6 +9,9 @@ cudaError_t launch_sweep_bf16s(int vec, int pipe, int grid, int warps, cudaStrea
   if (pipe == 0) {
     if (vec == 4) return launch_sweep_t<LBM_BF16S, 4>(grid, warps, st, a, s);
     if (vec == 8) return launch_sweep_t<LBM_BF16S, 8>(grid, warps, st, a, s);
+  } else if (pipe == 2) {
+    if (vec == 4) return launch_sweep_pf_t<LBM_BF16S, 4>(grid, warps, st, a, s);
+    if (vec == 8) return launch_sweep_pf_t<LBM_BF16S, 8>(grid, warps, st, a, s);
   } else {
     if (vec == 4) return launch_sweep_tma_t<LBM_BF16S, 4>(grid, warps, st, a, s);
     if (vec == 8) return launch_sweep_tma_t<LBM_BF16S, 8>(grid, warps, st, a, s);
@@ -20,6 +23,9 @@ int max_blocks_bf16s(int vec, int pipe, int warps) {
   if (pipe == 0) {
     if (vec == 4) return max_blocks_t<LBM_BF16S, 4>(warps);
     if (vec == 8) return max_blocks_t<LBM_BF16S, 8>(warps);
+  } else if (pipe == 2) {
+    if (vec == 4) return max_blocks_pf_t<LBM_BF16S, 4>(warps);
+    if (vec == 8) return max_blocks_pf_t<LBM_BF16S, 8>(warps);
   } else {
     if (vec == 4) return max_blocks_tma_t<LBM_BF16S, 4>(warps);
     if (vec == 8) return max_blocks_tma_t<LBM_BF16S, 8>(warps);

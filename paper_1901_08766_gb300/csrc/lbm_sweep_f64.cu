@@ -1,5 +1,5 @@
 // Sweep instantiations for LBM_F64 storage (cells per thread 1 and 2; direct
-// and TMA-staged row loads).
+// TMA-staged and register-prefetched row loads).
 #include "lbm_sweep_tma.cuh"
 
 namespace lbm {
@@ -9,6 +9,9 @@ cudaError_t launch_sweep_f64(int vec, int pipe, int grid, int warps, cudaStream_
   if (pipe == 0) {
     if (vec == 1) return launch_sweep_t<LBM_F64, 1>(grid, warps, st, a, s);
     if (vec == 2) return launch_sweep_t<LBM_F64, 2>(grid, warps, st, a, s);
+  } else if (pipe == 2) {
+    if (vec == 1) return launch_sweep_pf_t<LBM_F64, 1>(grid, warps, st, a, s);
+    if (vec == 2) return launch_sweep_pf_t<LBM_F64, 2>(grid, warps, st, a, s);
   } else {
     if (vec == 1) return launch_sweep_tma_t<LBM_F64, 1>(grid, warps, st, a, s);
     if (vec == 2) return launch_sweep_tma_t<LBM_F64, 2>(grid, warps, st, a, s);
@@ -20,6 +23,9 @@ int max_blocks_f64(int vec, int pipe, int warps) {
   if (pipe == 0) {
     if (vec == 1) return max_blocks_t<LBM_F64, 1>(warps);
     if (vec == 2) return max_blocks_t<LBM_F64, 2>(warps);
+  } else if (pipe == 2) {
+    if (vec == 1) return max_blocks_pf_t<LBM_F64, 1>(warps);
+    if (vec == 2) return max_blocks_pf_t<LBM_F64, 2>(warps);
   } else {
     if (vec == 1) return max_blocks_tma_t<LBM_F64, 1>(warps);
     if (vec == 2) return max_blocks_tma_t<LBM_F64, 2>(warps);

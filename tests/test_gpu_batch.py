@@ -49,7 +49,8 @@ def test_tile_shape_and_graphs_do_not_change_results(lbm):
     g0 = codec.encode(synth.random_populations(8, 256, 128, 0.05), "f16s")
     ref = None
     for vec, warps, rows, pipe, graph in [(8, 8, 2, 0, 16), (4, 4, 1, 0, 0), (8, 16, 4, 1, 7),
-                                          (4, 2, 3, 1, 32), (8, 4, 4, 1, 0)]:
+                                          (4, 2, 3, 1, 32), (8, 4, 4, 1, 0), (8, 8, 3, 2, 16),
+                                          (4, 2, 4, 2, 0)]:
         batch = lbm.Batch("f16s", max_domains=2, graph_steps=graph)
         k = batch.admit(spec, nsteps=100)
         batch.set_tile(vec, warps, rows, pipe)
