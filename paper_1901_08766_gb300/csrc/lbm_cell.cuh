@@ -110,6 +110,62 @@ __device__ __forceinline__ float rcp_(float a) {
 }
 __device__ __forceinline__ double rcp_(double a) { return 1.0 / a; }
 
+// Two nodes' values in the two lanes of a packed FP32 pair. Every operation is the
+// lane-wise IEEE operation rounded to nearest (the paired FP32 instructions of sm_100 and
+// later), so a node updated as half of a pair gets the same bits as when updated alone;
+// the pair halves the instruction count of the FP32 update.
+struct F2 {
+  float2 v;
+  F2() = default;
+  __device__ __forceinline__ explicit F2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ F2(float2 p) : v(p) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, (-b).v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 rcp_(F2 a) { return F2(make_float2(rcp_(a.v.x), rcp_(a.v.y))); }
+
+// Constants of the force-free update broadcast to both lanes of a pair.
+__device__ __forceinline__ CellConst<F2> pair_const(const CellConst<float> &c) {
+  CellConst<F2> p;
+  p.one_m_omp = F2(c.one_m_omp);
+  p.hp = F2(c.hp);
+  p.hm = F2(c.hm);
+  p.rho0 = F2(c.rho0);
+  p.pw0 = F2(c.pw0);
+  p.pw1 = F2(c.pw1);
+  p.pw2 = F2(c.pw2);
+  p.mw1 = F2(c.mw1);
+  p.mw2 = F2(c.mw2);
+  return p;
+}
+
+// Rounding of two nodes' post-collision values (compute space, packed in pairs) to the
+// 16-bit storage words, with each node's mass kept. The collision conserves mass
+// (Eq. (rho) of the post-collision populations equals that of the pulled ones, d), but
+// rounding the nine values separately does not: where a moving population's relaxation
+// increment is below half a unit it is rounded away while the finer-grained rest
+// population keeps its own, and in a wake these dropped increments share a sign and
+// drift the mean density. So the eight moving populations are rounded to nearest and the
+// rest population is stored as d minus their rounded values, rounded once: the stored
+// node mass is d within half a unit of the rest population (whose shifted value is
+// small, so that unit is the finest of the nine). `d` is the pulled mass (the sum of the
+// nine pulled values, in compute space).
+template <int S>
+__device__ __forceinline__ void encode_pair_mass_kept(const F2 (&x)[kQ], F2 d, uint32_t (&w)[kQ]) {
+  F2 r[kQ];
+#pragma unroll
+  for (int a = 1; a < kQ; ++a) {
+    w[a] = Codec<S>::enc2(x[a].v.x, x[a].v.y);
+    r[a] = F2(Codec<S>::dec2(w[a]));
+  }
+  const F2 moved = ((r[1] + r[3]) + (r[2] + r[4])) + ((r[5] + r[7]) + (r[6] + r[8]));
+  const F2 rest = d - moved;
+  w[0] = Codec<S>::enc2(rest.v.x, rest.v.y);
+}
+
 // Macroscopic quantities of one node (steps (4)-(5) of the algorithm, Sec. 2.2).
 template <typename T> struct NodeMacro {
   T d;       // sum of the stored values (rho - rho0 for shifted storage, rho otherwise)

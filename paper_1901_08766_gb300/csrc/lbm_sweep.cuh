@@ -262,6 +262,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
 #else
     const CellConst<T> &CF = C;
 #endif
+    // the same constants broadcast to packed pairs (16-bit storage, force-free rows)
+    CellConst<F2> CP;
+    if constexpr (sizeof(E) == 2) CP = pair_const(CF);
     const uint8_t *__restrict__ dmask = D.mask;
     T *__restrict__ dfvp = static_cast<T *>(D.fvp);
     // strip-end columns read by the end lanes (or -1: nothing to read)
@@ -408,22 +411,55 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
         }
         // rho outside (0.01, 100) or not finite; padding nodes are masked out per row
         bad_bits |= (fabs(m.rho - T(50.005)) < T(49.995) ? 0u : 1u) << k;
+        return m.d;
       };
+#ifndef LBM_PAIRED
+#define LBM_PAIRED 1
+#endif
       if constexpr (sizeof(E) == 2) {
         // 16-bit storage: two nodes per packed word, converted pairwise
+        if (LBM_PAIRED && !any_solid) {
+          // force-free rows: both nodes of a word updated together in packed FP32 pairs
 #pragma unroll
-        for (int k = 0; k < V; k += 2) {
-          T x0[kQ], x1[kQ];
+          for (int k = 0; k < V; k += 2) {
+            F2 x[kQ];
 #pragma unroll
-          for (int a = 0; a < kQ; ++a) {
-            const float2 p = Cd::dec2(v[a].w[k >> 1]);
-            x0[a] = p.x;
-            x1[a] = p.y;
+            for (int a = 0; a < kQ; ++a) x[a] = F2(Cd::dec2(v[a].w[k >> 1]));
+            if (k == 0 && west_edge && west_inlet) {
+              const bool g = lane == 0;
+              x[1].v.x = g ? C.ghost[1] : x[1].v.x;
+              x[5].v.x = g ? C.ghost[5] : x[5].v.x;
+              x[8].v.x = g ? C.ghost[8] : x[8].v.x;
+            }
+            const NodeMacro<F2> m = node_macro<F2, SHIFT, false>(x, CP, false, F2(0.f), F2(0.f));
+            collide<F2, SHIFT, false>(x, m, CP);
+            bad_bits |= (fabsf(m.rho.v.x - 50.005f) < 49.995f ? 0u : 1u) << k;
+            bad_bits |= (fabsf(m.rho.v.y - 50.005f) < 49.995f ? 0u : 1u) << (k + 1);
+            uint32_t w[kQ];
+            encode_pair_mass_kept<S>(x, m.d, w);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
           }
-          update(x0, k);
-          update(x1, k + 1);
+        } else {
 #pragma unroll
-          for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = Cd::enc2(x0[a], x1[a]);
+          for (int k = 0; k < V; k += 2) {
+            T x0[kQ], x1[kQ];
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+              const float2 p = Cd::dec2(v[a].w[k >> 1]);
+              x0[a] = p.x;
+              x1[a] = p.y;
+            }
+            const float d0 = update(x0, k);
+            const float d1 = update(x1, k + 1);
+            F2 xp[kQ];
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0[a], x1[a]));
+            uint32_t w[kQ];
+            encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), w);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
+          }
         }
       } else {
 #pragma unroll
@@ -489,8 +525,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   }
 }
 
+#ifndef LBM_SWEEP_THREADS
+#define LBM_SWEEP_THREADS 512
+#endif
 template <int S, int V>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs args, int s) {
+__global__ void __launch_bounds__(LBM_SWEEP_THREADS) sweep_kernel(SweepArgs args, int s) {
   sweep_body<S, V, false>(args, s);
 }
 

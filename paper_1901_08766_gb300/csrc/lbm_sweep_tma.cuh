@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         collide<T, SHIFT, false>(x, m, C);
       }
       bad_bits |= (fabs(m.rho - T(50.005)) < T(49.995) ? 0u : 1u) << k;
+      return m.d;
     };
     if constexpr (sizeof(E) == 2) {
 #pragma unroll
@@ -316,10 +317,15 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
           x0v[a] = p.x;
           x1v[a] = p.y;
         }
-        update(x0v, k);
-        update(x1v, k + 1);
+        const float d0 = update(x0v, k);
+        const float d1 = update(x1v, k + 1);
+        F2 xp[kQ];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = Cd::enc2(x0v[a], x1v[a]);
+        for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0v[a], x1v[a]));
+        uint32_t w[kQ];
+        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), w);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
       }
     } else {
 #pragma unroll

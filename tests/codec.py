@@ -70,3 +70,29 @@ def ghost_ulp(spec, storage):
     if storage == "f64":
         return 0.0
     return float(stored_ulp(g, storage).max())
+
+
+def step_tol(want, storage, spec=None, arith=None):
+    """Per-population bound for one step of a reduced storage against the oracle's FP64
+    result `want` (populations [9, ny, nx]) from the same decoded state.
+
+    Every stored value is within one unit of the stored type of the FP64 result (ties can
+    round either way; FP32 arithmetic adds `arith`). For the 16-bit storages the rest
+    population is stored as the pulled mass minus the eight rounded moving populations,
+    so it also carries their rounding residuals: half a unit of each. With an inlet, the
+    library holds the ghost populations as the stored type would: one more unit of the
+    ghost's magnitude at column 0 (three such units for the rest population, whose pulled
+    mass includes the three ghost values)."""
+    shift = W if storage != "f32" else 0.0
+    ulp = stored_ulp(want - shift, storage)
+    if arith is None:
+        arith = 3e-7 if storage == "f32" else 2e-8
+    tol = ulp + arith
+    if storage in ("f16s", "bf16s"):
+        tol[0] += 0.5 * ulp[1:].sum(axis=0)
+    if spec is not None and spec["edges"]["west"] == "inlet":
+        g = ghost_ulp(spec, storage)
+        tol[:, :, 0] += g
+        if storage in ("f16s", "bf16s"):
+            tol[0, :, 0] += 2 * g + 0.5 * 3 * g
+    return tol

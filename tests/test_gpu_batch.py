@@ -79,7 +79,7 @@ def test_autotune_keeps_state_and_results(lbm):
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
     vec, warps, rows, pipe = batch.get_tile()
-    assert vec in (4, 8) and 1 <= warps <= 16 and 1 <= rows <= 16 and pipe in (0, 1)
+    assert vec in (4, 8) and 1 <= warps <= 16 and 1 <= rows <= 16 and pipe in (0, 1, 2)
     batch.run(40)
     ref = lbm.Domain(specs[0], storage="f16s")
     ref.step(60)
@@ -129,8 +129,7 @@ def test_full_size_batch_one_step_sampled_parity(lbm):
         ora = oracle.Domain(s, g=codec.decode(raw0, "f16s"))
         f_ora = ora.run(1)
         got = codec.decode(batch.get_populations(slots[d]), "f16s")
-        tol = codec.stored_ulp(ora.g - codec.W, "f16s") + 2e-8
-        tol[:, :, 0] += codec.ghost_ulp(s, "f16s")  # inlet ghost as the stored type holds it
+        tol = codec.step_tol(ora.g, "f16s", s)
         assert np.all(np.abs(got - ora.g) <= tol)
         f_gpu, _ = batch.poll(slots[d])
         assert np.allclose(f_gpu, f_ora, rtol=1e-4, atol=1e-5)

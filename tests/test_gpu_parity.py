@@ -60,20 +60,30 @@ def test_fp64_edge_sizes(lbm, nx, ny, edges):
 def test_reduced_precision_one_step_within_one_unit(lbm, storage, case):
     # Same decoded input on both sides; the GPU computes in FP32 and rounds to the
     # stored type, so each stored value is within one unit of the oracle's FP64
-    # result rounded to that type (ties can round either way).
+    # result rounded to that type (ties can round either way); the 16-bit rest
+    # population also carries the moving populations' rounding residuals (mass kept).
     spec = synth.parity_case(case)
     raw, _, ora, _ = _run_pair(lbm, spec, storage, 1, seed=3)
     got = codec.decode(raw, storage)
-    shift = codec.W if storage != "f32" else 0.0
-    want_shifted = ora.g - shift
-    ulp = codec.stored_ulp(want_shifted, storage)
-    # FP32 arithmetic on values of order one adds a few 1e-8 before rounding
-    tol = ulp + (3e-7 if storage == "f32" else 2e-8)
-    if spec["edges"]["west"] == "inlet":
-        # the GPU's inlet ghost is f^eq(rho0, u_in) as the stored type holds it (the
-        # oracle's is exact): up to one more unit of the ghost's magnitude at column 0
-        tol[:, :, 0] += codec.ghost_ulp(spec, storage)
+    tol = codec.step_tol(ora.g, storage, spec)
     assert np.all(np.abs(got - ora.g) <= tol)
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_reduced_precision_mass_kept(lbm, storage):
+    # 16-bit storages store the rest population as the pulled mass minus the rounded
+    # moving populations: after one step, each node's stored mass equals its pulled mass
+    # (computed by the oracle's pull from the same decoded state) within half a unit of
+    # the stored rest population, plus FP32 arithmetic (periodic box: no ghost inflow).
+    spec = synth.parity_case("mixed_edges_61x47")
+    spec = dict(spec, edges=synth._edges())
+    raw, _, ora, _ = _run_pair(lbm, spec, storage, 1, seed=5, amp=0.05)
+    got = codec.decode(raw, storage)
+    g0 = codec.decode(codec.encode(synth.random_populations(5, spec["nx"], spec["ny"], 0.05), storage), storage)
+    pulled = oracle.stream(spec, g0).sum(axis=0)
+    ulp0 = codec.stored_ulp(got[0] - codec.W[0], storage)
+    err = np.abs(got.sum(axis=0) - pulled)
+    assert np.all(err <= 0.5 * ulp0 + 1e-7), err.max()
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
@@ -81,7 +91,8 @@ def test_reduced_precision_drift(lbm, storage):
     # Each step adds at most one storage rounding (half a unit of the largest stored
     # magnitude) plus the FP32 arithmetic error (a few units of 2^-24 on values of
     # order one); the collision does not amplify them, so after n steps the population
-    # error is below n * (ulp_store + 4 * 2^-24).
+    # error is below n * (ulp_store + 4 * 2^-24). The 16-bit rest population takes the
+    # eight moving populations' residuals as well: n * (5 ulp_store + 4 * 2^-24).
     steps = 200
     spec = synth.parity_case("channel_256x128")
     raw, f_gpu, ora, f_ora = _run_pair(lbm, spec, storage, steps, seed=4, amp=0.05)
@@ -89,8 +100,10 @@ def test_reduced_precision_drift(lbm, storage):
     stored = np.abs(ora.g - (0.0 if storage == "f32" else codec.W)).max()
     ulp = float(codec.stored_ulp(np.array([stored]), storage)[0])
     tol = steps * (ulp + 4 * 2.0 ** -24)
-    err = np.abs(got - ora.g).max()
-    assert err <= tol, f"{storage}: drift {err:.3e} > bound {tol:.3e}"
+    err = np.abs(got - ora.g)
+    assert err[1:].max() <= tol, f"{storage}: drift {err[1:].max():.3e} > bound {tol:.3e}"
+    tol0 = steps * ((5 if storage != "f32" else 1) * ulp + 4 * 2.0 ** -24)
+    assert err[0].max() <= tol0, f"{storage}: rest drift {err[0].max():.3e} > bound {tol0:.3e}"
 
 
 @pytest.mark.parametrize("spec_fn", [
