@@ -53,8 +53,15 @@ typedef enum {
 } lbm_status;
 
 /* Population storage. Collision and penalization run in FP64 for LBM_F64 and in FP32
- * otherwise. LBM_F16S / LBM_BF16S store f_alpha - w_alpha rho0 rounded to nearest
- * even (shifted by the rest weights, so that storage keeps the small deviations). */
+ * otherwise (LBM_F32 rounds to nearest even). LBM_BF16S stores f_alpha - w_alpha rho0
+ * and LBM_F16S stores 1024 (f_alpha - w_alpha rho0) (shifted by the rest weights, so
+ * that storage keeps the small deviations; the power-of-two scale keeps deviations down
+ * to 6e-8 in FP16's normal range, and values up to 64, i.e. rho below about 145, fit).
+ * Both round stochastically with counter-based random bits keyed by the step index and
+ * the node, so that the stored value is exact in expectation; the rest population is
+ * stored as the node's pulled mass minus the eight rounded moving populations, so that
+ * rounding keeps each node's mass (Eq. (rho)) within one unit of the rest population.
+ * The paper stores FP64 only: this rounding rule is the library's. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
 
 /* Domain-edge rules. x edges: west PERIODIC or INLET_EQ (ghost populations at
@@ -159,7 +166,7 @@ LBM_API lbm_status lbm_forces(lbm_domain *d, double *out, int64_t max_entries, i
 LBM_API lbm_status lbm_moments(lbm_domain *d, double *rho, double *ux, double *uy);
 
 /* Raw current populations in the storage type, [9][ny][nx] (element size 8, 4, 2, 2
- * for F64, F32, F16S, BF16S; F16S/BF16S hold f - w rho0). bytes must equal
+ * for F64, F32, F16S, BF16S; F16S holds 1024 (f - w rho0), BF16S f - w rho0). bytes must equal
  * 9*nx*ny*element size. Host or device pointers. Synchronise the stream. */
 LBM_API lbm_status lbm_get_populations(lbm_domain *d, void *out, size_t bytes);
 LBM_API lbm_status lbm_set_populations(lbm_domain *d, const void *in, size_t bytes);
@@ -187,8 +194,15 @@ LBM_API lbm_status lbm_moments_noalloc(lbm_domain *d, double *rho, double *ux, d
  * 0 = fluid, k = body k. Host or device pointer. Synchronises the stream. */
 LBM_API lbm_status lbm_get_mask(lbm_domain *d, uint8_t *out);
 
-/* Steps done so far. */
+/* Steps done so far (the step index of the next step). */
 LBM_API lbm_status lbm_steps_done(lbm_domain *d, int64_t *steps);
+
+/* Sets the step index (steps >= 0). The step index keys the random bits of the 16-bit
+ * storages' rounding and the force-series entries, so a run resumed from saved
+ * populations reproduces the uninterrupted run bit for bit when the index is restored
+ * with them. Force entries not yet read by lbm_forces are discarded. LBM_EINVAL for a
+ * negative index. No counterpart in the paper (a checkpoint facility). */
+LBM_API lbm_status lbm_set_steps_done(lbm_domain *d, int64_t steps);
 
 LBM_API lbm_status lbm_domain_destroy(lbm_domain *d);
 
@@ -227,6 +241,8 @@ LBM_API lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, do
 LBM_API lbm_status lbm_batch_get_populations(lbm_batch *b, int32_t slot, void *out, size_t bytes);
 LBM_API lbm_status lbm_batch_set_populations(lbm_batch *b, int32_t slot, const void *in, size_t bytes);
 LBM_API lbm_status lbm_batch_steps_done(lbm_batch *b, int32_t slot, int64_t *steps);
+/* As lbm_set_steps_done; also LBM_EINVAL beyond the slot's admitted step count. */
+LBM_API lbm_status lbm_batch_set_steps_done(lbm_batch *b, int32_t slot, int64_t steps);
 LBM_API lbm_status lbm_batch_get_mask(lbm_batch *b, int32_t slot, uint8_t *out);
 
 /* Advance every resident, unfinished domain by up to `steps` real time steps launched

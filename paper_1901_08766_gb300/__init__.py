@@ -118,6 +118,10 @@ class Domain:
         check(load().lbm_steps_done(self._handle(), C.byref(v)), "lbm_steps_done")
         return v.value
 
+    def set_steps_done(self, steps: int):
+        """Restore the step index with saved populations (it keys the 16-bit rounding)."""
+        check(load().lbm_set_steps_done(self._handle(), int(steps)), "lbm_set_steps_done")
+
     def mask(self) -> np.ndarray:
         out = np.zeros((self.ny, self.nx), dtype=np.uint8)
         check(load().lbm_get_mask(self._handle(), out.ctypes.data_as(C.c_void_p)), "lbm_get_mask")
@@ -215,6 +219,9 @@ class Batch:
         v = C.c_int64()
         check(load().lbm_batch_steps_done(self._h, slot, C.byref(v)), "lbm_batch_steps_done")
         return v.value
+
+    def set_steps_done(self, slot: int, steps: int):
+        check(load().lbm_batch_set_steps_done(self._h, slot, int(steps)), "lbm_batch_set_steps_done")
 
     def mask(self, slot: int) -> np.ndarray:
         nx, ny, nb, cap = self._meta[slot]

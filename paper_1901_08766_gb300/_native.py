@@ -76,6 +76,7 @@ SIGNATURES = {
     "lbm_get_populations": (C.c_int, [_VP, _VP, _SZ]),
     "lbm_set_populations": (C.c_int, [_VP, _VP, _SZ]),
     "lbm_steps_done": (C.c_int, [_VP, C.POINTER(_I64)]),
+    "lbm_set_steps_done": (C.c_int, [_VP, _I64]),
     "lbm_get_mask": (C.c_int, [_VP, _VP]),
     "lbm_batch_get_mask": (C.c_int, [_VP, _I32, _VP]),
     "lbm_domain_destroy": (C.c_int, [_VP]),
@@ -89,6 +90,7 @@ SIGNATURES = {
     "lbm_batch_get_populations": (C.c_int, [_VP, _I32, _VP, _SZ]),
     "lbm_batch_set_populations": (C.c_int, [_VP, _I32, _VP, _SZ]),
     "lbm_batch_steps_done": (C.c_int, [_VP, _I32, C.POINTER(_I64)]),
+    "lbm_batch_set_steps_done": (C.c_int, [_VP, _I32, _I64]),
     "lbm_batch_profile": (C.c_int, [_VP, _I32, _DP, _DP, C.POINTER(_I64)]),
     "lbm_batch_evict": (C.c_int, [_VP, _I32]),
     "lbm_batch_autotune": (C.c_int, [_VP, _I32, _DP]),

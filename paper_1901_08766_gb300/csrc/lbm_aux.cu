@@ -73,9 +73,9 @@ __global__ void init_kernel(typename Codec<S>::E *lat, int nx, int ny, int pitch
   const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
   const double eu = ex_of(a) * ux + ey_of(a) * uy;
   const double usq = ux * ux + uy * uy;
-  // Eq. (feq) with c_s^2 = 1/3; shifted storage keeps f^eq - w rho0
+  // Eq. (feq) with c_s^2 = 1/3; shifted storage keeps f^eq - w rho0 (times its scale)
   const double dev = rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-  double val = Cd::kStoreShifted ? dev : rho0 * w + dev;
+  double val = Cd::kStoreShifted ? dev * Cd::kScale : rho0 * w + dev;
   if (i >= nx) val = 0.0;
   lat[(static_cast<size_t>(a) * ny + j) * pitch + i] = Cd::enc(typename Cd::T(val));
 }
@@ -262,7 +262,7 @@ __global__ void moments_kernel(const DomDev *dom, int parity, double *rho, doubl
   if (b) body_velocity<T>(D, b, i, j, uox, uoy);
   const NodeMacro<T> m = node_macro<T, Cd::kShiftCompute, true>(x, C, b != 0, uox, uoy);
   const size_t c = static_cast<size_t>(j) * D.nx + i;
-  if (rho) rho[c] = double(m.rho);
+  if (rho) rho[c] = double(m.rho * (T(1) / T(Cd::kScale)));  // unscaled (power of two: exact)
   if (ux) ux[c] = double(m.ux);
   if (uy) uy[c] = double(m.uy);
 }

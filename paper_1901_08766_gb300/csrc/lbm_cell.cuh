@@ -28,11 +28,17 @@ __host__ __device__ constexpr int ey_of(int a) {
 }
 
 // ---- storage codecs --------------------------------------------------------------------
-// F64 / F32 store f; F16S / BF16S store f - w_alpha rho0 (rounded to nearest even).
-// kStoreShifted: the stored value is f - w_alpha rho0. kShiftCompute: the node update
-// works on f - w_alpha rho0 (for F32 storage the shift is subtracted after loading, exactly,
-// and added back before storing), so that no O(1) population meets a rounded relaxation
-// constant: that would bias mass by about one FP32 unit per node and step.
+// F64 / F32 store f (F32 rounded to nearest even); F16S stores kF16Scale (f - w_alpha
+// rho0), BF16S f - w_alpha rho0, both rounded stochastically (see PairEncoder).
+// kStoreShifted: the stored value is the shifted f - w_alpha rho0. kShiftCompute: the
+// node update works on f - w_alpha rho0 (for F32 storage the shift is subtracted after
+// loading, exactly, and added back before storing), so that no O(1) population meets a
+// rounded relaxation constant: that would bias mass by about one FP32 unit per node and
+// step. kScale: the power of two the compute space carries (the update works on the
+// stored values as they are; the domain's rho0 in compute precision carries the scale, so
+// rho, the equilibrium amplitudes and the Guo terms come out scaled and u = j / rho does
+// not). FP16's normal range then starts at 2^-14 / kF16Scale = 6e-8 instead of 6e-5:
+// the small deviations of slow flows keep full relative precision and round exactly.
 
 template <int S> struct Codec;
 
@@ -41,6 +47,7 @@ template <> struct Codec<LBM_F64> {
   using T = double;
   static constexpr bool kStoreShifted = false;
   static constexpr bool kShiftCompute = false;
+  static constexpr float kScale = 1.0f;
   __device__ static T dec(E e) { return e; }
   __device__ static E enc(T t) { return t; }
 };
@@ -49,6 +56,7 @@ template <> struct Codec<LBM_F32> {
   using T = float;
   static constexpr bool kStoreShifted = false;
   static constexpr bool kShiftCompute = true;
+  static constexpr float kScale = 1.0f;
   __device__ static T dec(E e) { return e; }
   __device__ static E enc(T t) { return t; }
 };
@@ -57,6 +65,7 @@ template <> struct Codec<LBM_F16S> {
   using T = float;
   static constexpr bool kStoreShifted = true;
   static constexpr bool kShiftCompute = true;
+  static constexpr float kScale = kF16Scale;
   __device__ static T dec(E e) { return __half2float(__ushort_as_half(e)); }
   __device__ static E enc(T t) { return __half_as_ushort(__float2half_rn(t)); }
   // two packed elements (low = first)
@@ -67,12 +76,29 @@ template <> struct Codec<LBM_F16S> {
     __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
   }
+  // Stochastic rounding: each element rounds away from zero with probability equal to
+  // its distance from the truncated value in units of the last place. 13 random bits are
+  // added below the FP16 mantissa of the FP32 magnitude (lower element bits 12..0, upper
+  // element bits 31..19), then the value is truncated. Exact wherever the FP16 result is
+  // normal (exactly 13 bits are dropped), i.e. for stored values of magnitude >= 2^-14,
+  // shifted populations >= 6e-8 with the storage scale; below that fewer than the dropped
+  // bits are randomized, a bias toward zero of less than one FP16 subnormal unit
+  // (2^-24 / 1024 = 6e-11 in population units). (The sm_100 family's cvt.rs conversion
+  // is exact everywhere but needs more registers in this kernel.)
+  __device__ static uint32_t enc2_sr(float lo, float hi, uint32_t rbits) {
+    const float l = __uint_as_float(__float_as_uint(lo) + (rbits & 0x1fffu));
+    const float h = __uint_as_float(__float_as_uint(hi) + (rbits >> 19));
+    uint32_t d;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(h), "f"(l));
+    return d;
+  }
 };
 template <> struct Codec<LBM_BF16S> {
   using E = uint16_t;
   using T = float;
   static constexpr bool kStoreShifted = true;
   static constexpr bool kShiftCompute = true;
+  static constexpr float kScale = 1.0f;
   __device__ static T dec(E e) { return __uint_as_float(static_cast<uint32_t>(e) << 16); }
   __device__ static E enc(T t) { return __bfloat16_as_ushort(__float2bfloat16_rn(t)); }
   __device__ static float2 dec2(uint32_t w) {
@@ -81,6 +107,16 @@ template <> struct Codec<LBM_BF16S> {
   __device__ static uint32_t enc2(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
+  }
+  // BF16 keeps the FP32 exponent range, so the same form is exact for every normal FP32
+  // value: 16 random bits below the BF16 mantissa (lower element bits 15..0, upper element
+  // bits 31..16), then truncation.
+  __device__ static uint32_t enc2_sr(float lo, float hi, uint32_t rbits) {
+    const float l = __uint_as_float(__float_as_uint(lo) + (rbits & 0xffffu));
+    const float h = __uint_as_float(__float_as_uint(hi) + (rbits >> 16));
+    uint32_t d;
+    asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(h), "f"(l));
+    return d;
   }
 };
 
@@ -143,27 +179,86 @@ __device__ __forceinline__ CellConst<F2> pair_const(const CellConst<float> &c) {
 }
 
 // Rounding of two nodes' post-collision values (compute space, packed in pairs) to the
-// 16-bit storage words, with each node's mass kept. The collision conserves mass
-// (Eq. (rho) of the post-collision populations equals that of the pulled ones, d), but
-// rounding the nine values separately does not: where a moving population's relaxation
-// increment is below half a unit it is rounded away while the finer-grained rest
-// population keeps its own, and in a wake these dropped increments share a sign and
-// drift the mean density. So the eight moving populations are rounded to nearest and the
-// rest population is stored as d minus their rounded values, rounded once: the stored
-// node mass is d within half a unit of the rest population (whose shifted value is
-// small, so that unit is the finest of the nine). `d` is the pulled mass (the sum of the
-// nine pulled values, in compute space).
-template <int S>
-__device__ __forceinline__ void encode_pair_mass_kept(const F2 (&x)[kQ], F2 d, uint32_t (&w)[kQ]) {
-  F2 r[kQ];
-#pragma unroll
-  for (int a = 1; a < kQ; ++a) {
-    w[a] = Codec<S>::enc2(x[a].v.x, x[a].v.y);
-    r[a] = F2(Codec<S>::dec2(w[a]));
+// 16-bit storage words.
+//
+// Stochastic rounding. A 16-bit unit of a moving population (about 1.5e-5 at the
+// magnitudes of flows at U = 0.05) is far above the per-step change of slow modes: the
+// relaxation of the mean-density level of an open channel, a viscous spin-up, the decay
+// of a weak shear wave. Rounded to nearest, such increments are lost every step and
+// those modes freeze. Each value is therefore rounded up or down with probabilities that
+// make the stored value exact in expectation, using counter-based random bits: a hash of
+// (step index, row, aligned group of eight columns), multiplied by an odd constant per
+// column pair of the group (a bijection of the 32-bit words, so both 16-bit halves stay
+// uniformly distributed; the pair's first node takes the low half, the second the high
+// half). The nine values of a node share their bits: each is still exact in
+// expectation. The bits depend on nothing else, so results are the same for every tile
+// shape, kernel variant and batch composition.
+//
+// Mass kept. The collision conserves each node's mass (Eq. (rho) of the post-collision
+// populations equals that of the pulled ones, d), but rounding the nine values
+// separately does not. The eight moving populations are rounded first and the rest
+// population is stored as d minus their rounded values, rounded once: the stored node
+// mass is d within one unit of the rest population (whose shifted value is small, so
+// that unit is the finest of the nine), and exact in expectation. `d` is the pulled
+// mass (the sum of the nine pulled values in compute space).
+
+// 32-bit integer finalizer of the xorshift-multiply family (shift/multiply constants
+// from C. Wellons' published hash-prospector search, "lowbias32").
+__device__ __forceinline__ uint32_t sr_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// hash input of a row: step index and row
+__device__ __forceinline__ uint32_t sr_row_key(long long n, int j) {
+  return static_cast<uint32_t>(n) * 0x9e3779b1u + static_cast<uint32_t>(j) * 0x85ebca77u;
+}
+// bits of the aligned group of eight columns holding column i
+__device__ __forceinline__ uint32_t sr_group_bits(uint32_t row_key, int i) {
+  return sr_hash(row_key + static_cast<uint32_t>(i >> 3) * 0xc2b2ae3du);
+}
+// bits of the column pair (i, i + 1), i even, from its group's bits: odd multiplier per
+// pair of the group
+__device__ __forceinline__ uint32_t sr_pair_bits(uint32_t group_bits, int i) {
+  return group_bits * (0x165667b1u + (static_cast<uint32_t>((i >> 1) & 3) << 1) * 0x27d4eb2eu);
+}
+
+// Encoder of one node pair, fed opposite direction pairs (a, -a) in the order (1,3),
+// (2,4), (5,7), (6,8) as the collision finishes them (so their FP32 values need not stay
+// live), then finished with the pulled mass.
+template <int S> struct PairEncoder {
+  uint32_t bits;
+  uint32_t w[kQ];
+  F2 s[4];  // rounded r_a + r_-a per opposite pair
+  __device__ __forceinline__ explicit PairEncoder(uint32_t b) : bits(b) {}
+  __device__ __forceinline__ void operator()(int ia, int ib, F2 xa, F2 xb) {
+    w[ia] = Codec<S>::enc2_sr(xa.v.x, xa.v.y, bits);
+    w[ib] = Codec<S>::enc2_sr(xb.v.x, xb.v.y, bits);
+    const int q = ia == 1 ? 0 : ia == 2 ? 1 : ia == 5 ? 2 : 3;
+    s[q] = F2(Codec<S>::dec2(w[ia])) + F2(Codec<S>::dec2(w[ib]));
   }
-  const F2 moved = ((r[1] + r[3]) + (r[2] + r[4])) + ((r[5] + r[7]) + (r[6] + r[8]));
-  const F2 rest = d - moved;
-  w[0] = Codec<S>::enc2(rest.v.x, rest.v.y);
+  __device__ __forceinline__ void finish(F2 d) {
+    const F2 moved = (s[0] + s[1]) + (s[2] + s[3]);
+    const F2 rest = d - moved;
+    w[0] = Codec<S>::enc2_sr(rest.v.x, rest.v.y, bits);
+  }
+};
+
+template <int S>
+__device__ __forceinline__ void encode_pair_mass_kept(const F2 (&x)[kQ], F2 d, uint32_t bits,
+                                                      uint32_t (&w)[kQ]) {
+  PairEncoder<S> e(bits);
+  e(1, 3, x[1], x[3]);
+  e(2, 4, x[2], x[4]);
+  e(5, 7, x[5], x[7]);
+  e(6, 8, x[6], x[8]);
+  e.finish(d);
+#pragma unroll
+  for (int a = 0; a < kQ; ++a) w[a] = e.w[a];
 }
 
 // Macroscopic quantities of one node (steps (4)-(5) of the algorithm, Sec. 2.2).
@@ -208,8 +303,14 @@ __device__ __forceinline__ NodeMacro<T> node_macro(const T (&x)[kQ], const CellC
 //   g_a = f_a - w+ (f^s_a - f^eq,s_a) - w- (f^a_a - f^eq,a_a) + (1 - w+/2) F^s_a + (1 - w-/2) F^a_a
 // evaluated per opposite pair (a, -a), in place on x[]. For shifted storage every
 // symmetric quantity is taken relative to w_a rho0, which cancels in f^s - f^eq,s.
-template <typename T, bool SHIFT, bool FORCE>
-__device__ __forceinline__ void collide(T (&x)[kQ], const NodeMacro<T> &m, const CellConst<T> &c) {
+struct NoPairHook {
+  template <typename T> __device__ __forceinline__ void operator()(int, int, T, T) {}
+};
+
+// `done(ia, ib, x[ia], x[ib])` is called as each opposite pair is finished.
+template <typename T, bool SHIFT, bool FORCE, typename Hook = NoPairHook>
+__device__ __forceinline__ void collide(T (&x)[kQ], const NodeMacro<T> &m, const CellConst<T> &c,
+                                        Hook &&done = Hook()) {
   const T base = SHIFT ? m.d : m.rho;
   const T q = T(1.5) * fma_(m.uy, m.uy, m.ux * m.ux);  // 1.5 |u|^2
   // per class: omega+ w rho, omega+ w base, 3 omega- w rho
@@ -239,6 +340,7 @@ __device__ __forceinline__ void collide(T (&x)[kQ], const NodeMacro<T> &m, const
     }
     x[ia] = (x[ia] + S) + A;
     x[ib] = (x[ib] + S) - A;
+    done(ia, ib, x[ia], x[ib]);
   };
   pair(1, 3, m.ux, m.fx, a1, b1, m1, c.kw1, c.qw1);
   pair(2, 4, m.uy, m.fy, a1, b1, m1, c.kw1, c.qw1);

@@ -16,12 +16,16 @@ constexpr int kPitchAlign = 64;  // row pitch in elements is a multiple of this
 constexpr int kMaxBodies = 255;
 
 // Per-domain constants of the collision in one precision (filled on the host).
+// FP16-shifted storage holds kF16Scale (f - w rho0): values up to 65504 / 1024 = 64
+// (rho below about 145) and full FP16 precision down to 2^-24 = 6e-8.
+constexpr float kF16Scale = 1024.0f;
+
 template <typename T> struct CellConst {
   T omp, omm;        // omega+ = 1/tau_s, omega- = 1/tau_a
   T hp, hm;          // omega+/2, omega-/2
   T one_m_omp;       // 1 - omega+
   T inv_2eta1;       // 1 / (2 eta + 1)
-  T rho0;
+  T rho0;            // rho0 times the storage scale (compute space)
   T pw0, pw1, pw2;   // omega+ * w for the rest, axis and diagonal classes
   T mw1, mw2;        // 3 omega- * w for the axis and diagonal classes
   T kw0, kw1, kw2;   // (1 - omega+/2) * w per class (Guo symmetric part)

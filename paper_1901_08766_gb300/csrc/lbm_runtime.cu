@@ -182,13 +182,14 @@ template <typename T> void fill_const(CellConst<T> &c, const DomDev &d) {
 void fill_cell_const(DomDev &d, int storage) {
   fill_const(d.cd, d);
   fill_const(d.cf, d);
+  if (storage == LBM_F16S) d.cf.rho0 = float(d.rho0 * kF16Scale);  // compute space is scaled
   const double w[kQ] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
   for (int a = 0; a < kQ; ++a) {
     const float shift = float(w[a] * d.rho0);
     if (storage == LBM_F32) {
       d.cf.ghost[a] = float(d.ghost[a]) - shift;  // stored f, minus the shift as after loading
     } else if (storage == LBM_F16S) {
-      d.cf.ghost[a] = __half2float(__float2half_rn(float(d.ghost[a])));
+      d.cf.ghost[a] = __half2float(__float2half_rn(float(d.ghost[a] * kF16Scale)));
     } else if (storage == LBM_BF16S) {
       d.cf.ghost[a] = __bfloat162float(__float2bfloat16_rn(float(d.ghost[a])));
     }
@@ -997,6 +998,18 @@ lbm_status lbm_batch_steps_done(lbm_batch *b, int32_t slot, int64_t *steps) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_set_steps_done(lbm_batch *b, int32_t slot, int64_t steps) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  if (steps < 0 || steps > s.target)
+    return fail(LBM_EINVAL, "step index %lld outside [0, %lld]", static_cast<long long>(steps), s.target);
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  s.done = steps;
+  s.drained = entries_at(s, steps);  // nothing pending: entries before the index are gone
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_get_mask(lbm_batch *b, int32_t slot, uint8_t *out) {
   return get_mask(b, slot, out);
 }
@@ -1139,6 +1152,11 @@ lbm_status lbm_steps_done(lbm_domain *d, int64_t *steps) {
   if (!d) return fail(LBM_EINVAL, "domain is NULL");
   if (steps) *steps = d->b->slots[0].done;
   return LBM_OK;
+}
+
+lbm_status lbm_set_steps_done(lbm_domain *d, int64_t steps) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return lbm_batch_set_steps_done(d->b, 0, steps);
 }
 
 lbm_status lbm_domain_destroy(lbm_domain *d) {

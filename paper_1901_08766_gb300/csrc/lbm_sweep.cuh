@@ -198,7 +198,8 @@ __device__ __forceinline__ void decode_cell(const Strip<S, V> (&v)[kQ], int k,
 template <int S, int V> struct RowData {
   Strip<S, V> v[kQ];
   typename Codec<S>::E end_in[kQ];
-  uint8_t b[V];
+  uint32_t mb[(V + 3) / 4];  // body ids of the V cells, four per word (low byte first)
+  __device__ int body(int k) const { return (mb[k >> 2] >> (8 * (k & 3))) & 0xff; }
 };
 
 // The sweep body. PF = false: each warp loads a row, then updates it. PF = true: the
@@ -211,7 +212,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   using T = typename Cd::T;
   constexpr bool SHIFT = Cd::kShiftCompute;
   constexpr bool kAddShift = Cd::kShiftCompute && !Cd::kStoreShifted;
+  // compute space carries the storage scale: stability bounds on rho and the F_VP output
+  constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
+  constexpr T kUnscale = T(1) / T(Cd::kScale);
   constexpr int kStrip = 32 * V;
+  static_assert(sizeof(E) != 2 || (V <= 8 && 8 % V == 0),
+                "a 16-bit strip must lie in one group of eight columns (rounding bits)");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int ntiles = args.ctr->ntiles;
@@ -315,35 +321,29 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
         if (ex == 1) end_in[a] = __ldg(row[a] + col_l);
         else if (ex == -1) end_in[a] = __ldg(row[a] + col_r);
       }
-      auto &b = R.b;
       {
+        // body ids, kept packed (zero for lanes past the end of the row)
         const uint8_t *mrow = dmask + static_cast<size_t>(j) * pitch + xl_ld;
         if constexpr (V == 8) {
           const uint2 mw = __ldg(reinterpret_cast<const uint2 *>(mrow));
-#pragma unroll
-          for (int k = 0; k < 4; ++k) b[k] = (mw.x >> (8 * k)) & 0xff;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) b[4 + k] = (mw.y >> (8 * k)) & 0xff;
+          R.mb[0] = lane_on ? mw.x : 0u;
+          R.mb[1] = lane_on ? mw.y : 0u;
         } else if constexpr (V == 4) {
           const uint32_t mw = __ldg(reinterpret_cast<const unsigned int *>(mrow));
-#pragma unroll
-          for (int k = 0; k < 4; ++k) b[k] = (mw >> (8 * k)) & 0xff;
+          R.mb[0] = lane_on ? mw : 0u;
         } else if constexpr (V == 2) {
           const uint32_t mw = __ldg(reinterpret_cast<const unsigned short *>(mrow));
-          b[0] = mw & 0xff;
-          b[1] = (mw >> 8) & 0xff;
+          R.mb[0] = lane_on ? mw : 0u;
         } else {
-          b[0] = __ldg(mrow);
+          const uint32_t mw = __ldg(mrow);
+          R.mb[0] = lane_on ? mw : 0u;
         }
-#pragma unroll
-        for (int k = 0; k < V; ++k) b[k] = lane_on ? b[k] : uint8_t(0);
       }
     };
     // ---- phases 2 and 3: shift, update and store row j ---------------------------------
     auto process_row = [&](RowData<S, V> &R, const int j) {
       auto &v = R.v;
       const auto &end_in = R.end_in;
-      const auto &b = R.b;
       // ---- phase 2: the +-1 x-shift of the pull, in registers -----------------------
 #pragma unroll
       for (int a = 0; a < kQ; ++a) {
@@ -374,7 +374,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
       }
       bool any_solid_lane = false;
 #pragma unroll
-      for (int k = 0; k < V; ++k) any_solid_lane |= (b[k] != 0);
+      for (int q = 0; q < (V + 3) / 4; ++q) any_solid_lane |= (R.mb[q] != 0u);
       const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
 
       // ---- phase 3: update the V nodes in place ----------------------------------------
@@ -383,6 +383,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
           east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u))
                     : (1u << V) - 1u;
       unsigned bad_bits = 0u;
+      // random bits of the 16-bit rounding (a strip of V <= 8 cells lies in one group)
+      const uint32_t sr_g = sizeof(E) == 2 ? sr_group_bits(sr_row_key(n, j), xl) : 0u;
       // one node: inlet ghost, moments, penalization, collision, F_VP, stability check
       auto update = [&](T (&x)[kQ], int k) {
         if (k == 0 && west_edge && west_inlet) {
@@ -395,22 +397,23 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
         NodeMacro<T> m;
         if (any_solid) {
           T uox = T(0), uoy = T(0);
-          const bool solid = b[k] != 0;
-          if (solid) body_velocity<T>(D, b[k], xl + k, j, uox, uoy);
+          const int bk = R.body(k);
+          const bool solid = bk != 0;
+          if (solid) body_velocity<T>(D, bk, xl + k, j, uox, uoy);
           m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
           collide<T, SHIFT, true>(x, m, C);
           if (solid) {
-            // F_VP of this node for the body-force reduction
+            // F_VP of this node for the body-force reduction (unscaled: power of two)
             T *__restrict__ fv = dfvp + 2 * (static_cast<size_t>(j) * pitch + xl + k);
-            fv[0] = m.fx;
-            fv[1] = m.fy;
+            fv[0] = m.fx * kUnscale;
+            fv[1] = m.fy * kUnscale;
           }
         } else {
           m = node_macro<T, SHIFT, false>(x, CF, false, T(0), T(0));
           collide<T, SHIFT, false>(x, m, CF);
         }
         // rho outside (0.01, 100) or not finite; padding nodes are masked out per row
-        bad_bits |= (fabs(m.rho - T(50.005)) < T(49.995) ? 0u : 1u) << k;
+        bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
         return m.d;
       };
 #ifndef LBM_PAIRED
@@ -432,13 +435,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
               x[8].v.x = g ? C.ghost[8] : x[8].v.x;
             }
             const NodeMacro<F2> m = node_macro<F2, SHIFT, false>(x, CP, false, F2(0.f), F2(0.f));
-            collide<F2, SHIFT, false>(x, m, CP);
-            bad_bits |= (fabsf(m.rho.v.x - 50.005f) < 49.995f ? 0u : 1u) << k;
-            bad_bits |= (fabsf(m.rho.v.y - 50.005f) < 49.995f ? 0u : 1u) << (k + 1);
-            uint32_t w[kQ];
-            encode_pair_mass_kept<S>(x, m.d, w);
+            bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
+            bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (k + 1);
+            // each opposite pair is rounded as soon as the collision finishes it
+            PairEncoder<S> enc(sr_pair_bits(sr_g, xl + k));
+            collide<F2, SHIFT, false>(x, m, CP, enc);
+            enc.finish(m.d);
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
+            for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = enc.w[a];
           }
         } else {
 #pragma unroll
@@ -456,7 +460,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
 #pragma unroll
             for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0[a], x1[a]));
             uint32_t w[kQ];
-            encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), w);
+            encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + k), w);
 #pragma unroll
             for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
           }

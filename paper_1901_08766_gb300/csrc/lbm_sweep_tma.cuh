@@ -297,14 +297,14 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         collide<T, SHIFT, true>(x, m, C);
         if (solid) {
           T *fv = static_cast<T *>(D.fvp) + 2 * (static_cast<size_t>(j) * pitch + xl + k);
-          fv[0] = m.fx;
-          fv[1] = m.fy;
+          fv[0] = m.fx * (T(1) / T(Cd::kScale));  // unscaled (power of two: exact)
+          fv[1] = m.fy * (T(1) / T(Cd::kScale));
         }
       } else {
         m = node_macro<T, SHIFT, false>(x, C, false, T(0), T(0));
         collide<T, SHIFT, false>(x, m, C);
       }
-      bad_bits |= (fabs(m.rho - T(50.005)) < T(49.995) ? 0u : 1u) << k;
+      bad_bits |= (fabs(m.rho - T(50.005) * T(Cd::kScale)) < T(49.995) * T(Cd::kScale) ? 0u : 1u) << k;
       return m.d;
     };
     if constexpr (sizeof(E) == 2) {
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
 #pragma unroll
         for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0v[a], x1v[a]));
         uint32_t w[kQ];
-        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), w);
+        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_group_bits(sr_row_key(dy.step0 + run_base + s, j), xl), xl + k), w);
 #pragma unroll
         for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
       }

@@ -1,5 +1,6 @@
 """Test-side storage conversions: FP64 populations to and from the library's stored
-types (F64, F32, F16S, BF16S), with the shift by w_alpha * rho0 for the 16-bit types.
+types (F64, F32, F16S, BF16S), with the shift by w_alpha * rho0 for the 16-bit types and
+the power-of-two scale F16S stores the shifted values with.
 
 The shift weights come from the oracle's own constants. Encoding is the test's choice
 of inputs (any stored values are valid); decoding is exact, so the oracle receives
@@ -10,6 +11,7 @@ import numpy as np
 import oracle
 
 W = oracle.W[:, None, None]
+F16_SCALE = 1024.0  # F16S stores F16_SCALE * (f - w rho0)
 
 
 def f32_to_bf16_bits(x):
@@ -31,7 +33,7 @@ def encode(g, storage, rho0=1.0):
         return np.ascontiguousarray(g, dtype=np.float32)
     s = g - W * rho0
     if storage == "f16s":
-        return np.ascontiguousarray(s.astype(np.float32).astype(np.float16))
+        return np.ascontiguousarray((s * F16_SCALE).astype(np.float32).astype(np.float16))
     if storage == "bf16s":
         return f32_to_bf16_bits(s.astype(np.float32))
     raise KeyError(storage)
@@ -42,7 +44,7 @@ def decode(raw, storage, rho0=1.0):
     if storage in ("f64", "f32"):
         return np.asarray(raw, dtype=np.float64)
     if storage == "f16s":
-        return np.asarray(raw, dtype=np.float16).astype(np.float64) + W * rho0
+        return np.asarray(raw, dtype=np.float16).astype(np.float64) / F16_SCALE + W * rho0
     if storage == "bf16s":
         return bf16_bits_to_f64(raw) + W * rho0
     raise KeyError(storage)
@@ -52,7 +54,7 @@ def stored_ulp(values_shifted, storage):
     """Spacing of the stored type at the given (shifted) magnitudes."""
     a = np.abs(np.asarray(values_shifted, dtype=np.float64))
     if storage == "f16s":
-        return np.spacing(a.astype(np.float16)).astype(np.float64)
+        return np.spacing((a * F16_SCALE).astype(np.float16)).astype(np.float64) / F16_SCALE
     if storage == "bf16s":
         e = np.floor(np.log2(np.maximum(a, 2.0 ** -126)))
         return 2.0 ** (e - 7)
@@ -76,23 +78,29 @@ def step_tol(want, storage, spec=None, arith=None):
     """Per-population bound for one step of a reduced storage against the oracle's FP64
     result `want` (populations [9, ny, nx]) from the same decoded state.
 
-    Every stored value is within one unit of the stored type of the FP64 result (ties can
-    round either way; FP32 arithmetic adds `arith`). For the 16-bit storages the rest
-    population is stored as the pulled mass minus the eight rounded moving populations,
-    so it also carries their rounding residuals: half a unit of each. With an inlet, the
-    library holds the ghost populations as the stored type would: one more unit of the
-    ghost's magnitude at column 0 (three such units for the rest population, whose pulled
-    mass includes the three ghost values)."""
+    Every stored value is within one unit of the stored type of the FP64 result: FP32
+    rounds to nearest (ties either way), the 16-bit storages round stochastically to
+    one of the two neighbours; FP32 arithmetic adds `arith`. For the 16-bit storages the
+    rest population is stored as the pulled mass minus the eight rounded moving
+    populations, so it also carries their rounding residuals: up to one unit of each.
+    With an inlet, the library holds the ghost populations as the stored type would:
+    one more unit of the ghost's magnitude at column 0 (and the three ghost values enter
+    the rest population's pulled mass)."""
     shift = W if storage != "f32" else 0.0
-    ulp = stored_ulp(want - shift, storage)
     if arith is None:
         arith = 3e-7 if storage == "f32" else 2e-8
-    tol = ulp + arith
-    if storage in ("f16s", "bf16s"):
-        tol[0] += 0.5 * ulp[1:].sum(axis=0)
+    g = 0.0
     if spec is not None and spec["edges"]["west"] == "inlet":
         g = ghost_ulp(spec, storage)
-        tol[:, :, 0] += g
-        if storage in ("f16s", "bf16s"):
-            tol[0, :, 0] += 2 * g + 0.5 * 3 * g
+    mag = np.abs(want - shift)
+    # units taken at the largest magnitude the rounded value can have (a value just
+    # below a power of two may round into the next binade, whose unit is twice as large)
+    ulp = stored_ulp(mag + arith + g, storage)
+    tol = ulp + arith
+    tol[:, :, 0] += g
+    if storage in ("f16s", "bf16s"):
+        carried = ulp[1:].sum(axis=0)
+        carried[:, 0] += 3 * g
+        ulp0 = stored_ulp(mag[0] + arith + carried, storage)
+        tol[0] = ulp0 + carried + arith
     return tol

@@ -59,8 +59,8 @@ def test_fp64_edge_sizes(lbm, nx, ny, edges):
 @pytest.mark.parametrize("case", ["channel_97x61", "mixed_edges_61x47"])
 def test_reduced_precision_one_step_within_one_unit(lbm, storage, case):
     # Same decoded input on both sides; the GPU computes in FP32 and rounds to the
-    # stored type, so each stored value is within one unit of the oracle's FP64
-    # result rounded to that type (ties can round either way); the 16-bit rest
+    # stored type (to nearest for FP32, stochastically for the 16-bit types), so each
+    # stored value is within one unit of the oracle's FP64 result; the 16-bit rest
     # population also carries the moving populations' rounding residuals (mass kept).
     spec = synth.parity_case(case)
     raw, _, ora, _ = _run_pair(lbm, spec, storage, 1, seed=3)
@@ -73,8 +73,9 @@ def test_reduced_precision_one_step_within_one_unit(lbm, storage, case):
 def test_reduced_precision_mass_kept(lbm, storage):
     # 16-bit storages store the rest population as the pulled mass minus the rounded
     # moving populations: after one step, each node's stored mass equals its pulled mass
-    # (computed by the oracle's pull from the same decoded state) within half a unit of
-    # the stored rest population, plus FP32 arithmetic (periodic box: no ghost inflow).
+    # (computed by the oracle's pull from the same decoded state) within one unit of
+    # the stored rest population (stochastic rounding), plus FP32 arithmetic (periodic
+    # box: no ghost inflow).
     spec = synth.parity_case("mixed_edges_61x47")
     spec = dict(spec, edges=synth._edges())
     raw, _, ora, _ = _run_pair(lbm, spec, storage, 1, seed=5, amp=0.05)
@@ -83,16 +84,16 @@ def test_reduced_precision_mass_kept(lbm, storage):
     pulled = oracle.stream(spec, g0).sum(axis=0)
     ulp0 = codec.stored_ulp(got[0] - codec.W[0], storage)
     err = np.abs(got.sum(axis=0) - pulled)
-    assert np.all(err <= 0.5 * ulp0 + 1e-7), err.max()
+    assert np.all(err <= ulp0 + 1e-7), err.max()
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
 def test_reduced_precision_drift(lbm, storage):
-    # Each step adds at most one storage rounding (half a unit of the largest stored
+    # Each step adds at most one storage rounding (one unit of the largest stored
     # magnitude) plus the FP32 arithmetic error (a few units of 2^-24 on values of
     # order one); the collision does not amplify them, so after n steps the population
     # error is below n * (ulp_store + 4 * 2^-24). The 16-bit rest population takes the
-    # eight moving populations' residuals as well: n * (5 ulp_store + 4 * 2^-24).
+    # eight moving populations' residuals as well: n * (9 ulp_store + 4 * 2^-24).
     steps = 200
     spec = synth.parity_case("channel_256x128")
     raw, f_gpu, ora, f_ora = _run_pair(lbm, spec, storage, steps, seed=4, amp=0.05)
@@ -102,7 +103,7 @@ def test_reduced_precision_drift(lbm, storage):
     tol = steps * (ulp + 4 * 2.0 ** -24)
     err = np.abs(got - ora.g)
     assert err[1:].max() <= tol, f"{storage}: drift {err[1:].max():.3e} > bound {tol:.3e}"
-    tol0 = steps * ((5 if storage != "f32" else 1) * ulp + 4 * 2.0 ** -24)
+    tol0 = steps * ((9 if storage != "f32" else 1) * ulp + 4 * 2.0 ** -24)
     assert err[0].max() <= tol0, f"{storage}: rest drift {err[0].max():.3e} > bound {tol0:.3e}"
 
 
@@ -160,6 +161,9 @@ def test_checkpoint_resume_bit_identical(lbm):
     b.close()
     c = lbm.Domain(spec, storage="f16s")
     c.set_populations(snap)
+    c.set_steps_done(100)  # the step index keys the 16-bit rounding's random bits
+    with pytest.raises(lbm.LbmError):
+        c.set_steps_done(-1)
     fb2 = c.run(100)
     assert np.array_equal(c.get_populations().view(np.uint16), pa.view(np.uint16))
     assert np.array_equal(np.concatenate([fb1, fb2]), fa)

@@ -89,6 +89,34 @@ def test_couette_fp16s_rounding_floor(lbm):
     assert num / den <= 5e-4
 
 
+@pytest.mark.parametrize("storage,tol", [("f16s", 0.02), ("bf16s", 0.05)])
+def test_sub_unit_decay_not_frozen(lbm, storage, tol):
+    # A shear wave u_x = A sin(2 pi y / n) in a periodic box decays by viscosity as
+    # exp(-nu k^2 t). With A = 1e-3 its per-step change of a population (about 3e-8) is
+    # far below half a unit of the 16-bit storage (about 1.2e-7 for FP16 at 3e-4):
+    # rounded to nearest the wave would stay frozen; rounded stochastically it decays as
+    # in FP64 storage (projected amplitude after 1/(nu k^2) steps, about 0.38 A).
+    import codec
+    n, A, nu, steps = 64, 1e-3, 0.01, 10000
+    spec = synth._spec("shear", n, n, nu, [], [], steps, A, synth._edges())
+    col = np.stack([oracle.equilibrium(1.0, A * math.sin(2 * math.pi * j / n), 0.0)
+                    for j in range(n)], axis=1)  # [9, ny]
+    g0 = np.repeat(col[:, :, None], n, axis=2)
+    sinj = np.sin(2 * math.pi * np.arange(n) / n)[:, None]
+    amp = {}
+    for st in ("f64", storage):
+        dom = lbm.Domain(spec, storage=st, force_every=0)
+        dom.set_populations(codec.encode(g0, st))
+        dom.step(steps)
+        _, ux, _ = dom.moments()
+        dom.close()
+        amp[st] = 2.0 * (ux * sinj).mean()
+    decay = math.exp(-nu * (2 * math.pi / n) ** 2 * steps)
+    print(f"{storage}: amplitude {amp[storage]:.4e} vs FP64 {amp['f64']:.4e} (A e^(-nu k^2 t) = {A * decay:.4e})")
+    assert abs(amp["f64"] - A * decay) / (A * decay) < 0.01
+    assert abs(amp[storage] - amp["f64"]) / amp["f64"] < tol
+
+
 @pytest.mark.parametrize("re,cd,st,steps", [(100.0, 1.336, 0.169, 120000), (40.0, 1.55, None, 60000)])
 def test_single_cylinder_against_paper_tables(lbm, re, cd, st, steps):
     # Table (high-Re): Re 100 gives C_d 1.336, St 0.169; Table (low-Re): Re 40 gives C_d 1.55.
