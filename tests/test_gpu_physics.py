@@ -3,6 +3,8 @@
 - Cylindrical Couette flow (Sec. 3.1), FP64: matches the oracle after 20 000 steps and
   the closed form u_theta = A r + B/r; reduced storages stay within a velocity-field
   relative L2 of 1e-3 of FP64 (BF16-shifted: see the bound below).
+- A shear wave whose per-step change is below half a unit of the 16-bit storages decays
+  as in FP64 (stochastic rounding keeps sub-unit increments).
 - Single cylinder (Sec. 3.2), FP32: C_d and St close to Table (high-Re) / (low-Re) of
   the paper (plausibility only: domain and edges differ from the paper's).
 - Precision sweep at the oracle's size (600x300, D = 30, Re = 200): mean C_d, C_l rms and
@@ -57,14 +59,13 @@ def test_couette_fp64_matches_oracle_and_closed_form(lbm):
     assert err < 0.03
 
 
-@pytest.mark.parametrize("storage,steps,bound", [("f32", 20000, 1e-3), ("f16s", 100000, 1e-3),
-                                                 ("bf16s", 20000, 5e-2)])
+@pytest.mark.parametrize("storage,steps,bound", [("f32", 20000, 1e-3), ("f16s", 20000, 1e-3),
+                                                 ("f16s", 100000, 1e-3), ("bf16s", 20000, 5e-3)])
 def test_couette_reduced_precision_velocity_l2(lbm, storage, steps, bound):
-    # Velocity-field relative L2 against FP64 storage in the steady state. FP32 reaches it
-    # in the 20 000 steps of the workload. FP16-shifted converges more slowly from rest
-    # (per-step diffusion increments below half a unit are rounded away; 2.2e-3 at 20 000
-    # steps, 1.2e-3 at 40 000), so it is compared at 100 000 steps; its floor is checked
-    # separately. BF16 keeps 8 mantissa bits and misses 1e-3 (3e-2 at 20 000 steps): its
+    # Velocity-field relative L2 against FP64 storage after the 20 000 steps of the
+    # workload (FP32 1.4e-5, FP16-shifted 3.1e-4: stochastic rounding keeps the spin-up's
+    # sub-unit increments that rounding to nearest dropped, 2.2e-3 then), and FP16 once
+    # more at 100 000 steps. BF16 keeps 8 mantissa bits and misses 1e-3 (2.6e-3): its
     # assertion records the achieved level, not the target.
     _, ux64, uy64, _ = _couette_fields(lbm, "f64", steps=20000)
     _, ux, uy, _ = _couette_fields(lbm, storage, steps=steps)
@@ -86,6 +87,7 @@ def test_couette_fp16s_rounding_floor(lbm):
     dom.close()
     num = np.sqrt(((ux - ux64) ** 2 + (uy - uy64) ** 2).sum())
     den = np.sqrt((ux64 ** 2 + uy64 ** 2).sum())
+    print(f"f16s from the converged FP64 state, 20000 steps: velocity relative L2 {num / den:.3e}")
     assert num / den <= 5e-4
 
 
@@ -137,10 +139,10 @@ def test_single_cylinder_against_paper_tables(lbm, re, cd, st, steps):
         assert s["cl_rms"] < 0.01  # steady wake
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 0.01), ("f32", 0.01), ("f16s", 0.01), ("bf16s", 0.25)])
+@pytest.mark.parametrize("storage,tol", [("f64", 0.01), ("f32", 0.01), ("f16s", 0.01), ("bf16s", 0.03)])
 def test_precision_sweep_against_oracle(lbm, storage, tol):
     # Mean C_d, C_l rms and St (lift spectral peak) over steps 40 000..80 000 within 1 % of
-    # the stored FP64 oracle values. BF16-shifted misses this bound (C_d about 17 % low):
+    # the stored FP64 oracle values. BF16-shifted is within 1.5 % (C_d +1.4 %, St +1.0 %):
     # its tolerance records the achieved level, not the target.
     path = os.path.join(GOLDEN, "precision_cylinder_600x300.json")
     ref = json.load(open(path))
