@@ -42,6 +42,26 @@ def test_fp64_matches_oracle_1000_steps(lbm, case):
     assert np.abs(f_gpu - f_ora).max() <= 1e-10 * scale + 1e-14
 
 
+@pytest.mark.parametrize("case", ["channel_97x61", "mixed_edges_61x47"])
+def test_fp64_srt_mode_matches_oracle_srt(lbm, case):
+    # SRT-LBM-VP on the GPU is the TRT sweep with Lambda = (tau_s - 1/2)^2, i.e.
+    # tau_a = tau_s (Sec. 2.1); it must match the oracle's separately written SRT update
+    # (single relaxation time, unsplit Guo term) to the FP64 parity bound.
+    spec = synth.parity_case(case)
+    spec = dict(spec, magic_lambda=(3.0 * spec["nu"]) ** 2)
+    g0 = synth.random_populations(7, spec["nx"], spec["ny"], 0.1)
+    dom = lbm.Domain(spec, storage="f64")
+    dom.set_populations(g0)
+    f_gpu = dom.run(1000)
+    raw = dom.get_populations()
+    dom.close()
+    ora = oracle.Domain(spec, g=g0)
+    f_ora = ora.run(1000, srt=True)
+    rel = np.abs(raw - ora.g) / np.abs(ora.g)
+    assert rel.max() <= 1e-12, f"max relative population difference {rel.max():.3e}"
+    assert np.abs(f_gpu - f_ora).max() <= 1e-10 * np.abs(f_ora).max() + 1e-14
+
+
 @pytest.mark.parametrize("nx,ny", [(3, 3), (5, 4), (64, 3), (65, 7), (130, 5), (257, 9), (513, 4)])
 @pytest.mark.parametrize("edges", ["periodic", "channel"])
 def test_fp64_edge_sizes(lbm, nx, ny, edges):
