@@ -91,6 +91,13 @@ def lib():
         L.ora_init.argtypes = [C.POINTER(_Params), C.c_double, C.c_double, dp]
         L.ora_stream.argtypes = [C.POINTER(_Params), dp, dp]
         L.ora_moments.argtypes = [C.POINTER(_Params), u8p, C.POINTER(_Body), dp, dp, dp, dp]
+        L.ora_rasterize_at.argtypes = [C.c_int32, C.c_int32, C.POINTER(_Shape), C.c_int32,
+                                       C.POINTER(_Body), C.c_int32, C.c_int64, u8p]
+        L.ora_run_moving.restype = C.c_int
+        L.ora_run_moving.argtypes = [C.POINTER(_Params), C.POINTER(_Shape), C.c_int32,
+                                     C.POINTER(_Body), C.c_int32, dp, C.c_int64, C.c_int64, dp,
+                                     C.c_int32]
+        L.ora_bodies_at.argtypes = [C.POINTER(_Body), C.c_int32, C.c_int64, C.POINTER(_Body)]
         _lib = L
     return _lib
 
@@ -155,24 +162,36 @@ def stream(spec, g) -> np.ndarray:
     return f
 
 
-def rasterize(spec) -> np.ndarray:
-    """Body-id mask uint8 [ny, nx] (0 = fluid) from the spec's shapes."""
+def rasterize(spec, step=None) -> np.ndarray:
+    """Body-id mask uint8 [ny, nx] (0 = fluid) from the spec's shapes; with `step`, the
+    mask of a moving domain at that step index (shapes translated with their bodies)."""
     nx, ny = spec["nx"], spec["ny"]
     mask = np.zeros((ny, nx), dtype=np.uint8)
     arr, n = _shapes_of(spec)
-    lib().ora_rasterize(nx, ny, arr, n, mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+    if step is None:
+        lib().ora_rasterize(nx, ny, arr, n, mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+    else:
+        bodies, nb = _bodies_of(spec)
+        lib().ora_rasterize_at(nx, ny, arr, n, bodies, nb, int(step),
+                               mask.ctypes.data_as(C.POINTER(C.c_uint8)))
     return mask
 
 
 class Domain:
-    """One simulation: post-collision populations g [9, ny, nx] in FP64."""
+    """One simulation: post-collision populations g [9, ny, nx] in FP64. A spec with
+    "moving": True has bodies that translate with their velocities (the mask and the
+    body centres follow them, re-rasterised before every step)."""
 
     def __init__(self, spec, mask=None, g=None):
         self.spec = spec
         self.p = params_of(spec)
+        self.moving = bool(spec.get("moving", False))
+        if self.moving and mask is not None:
+            raise ValueError("a moving domain's mask follows its shapes")
         self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask,
                                          dtype=np.uint8)
         self.bodies, self.nb = _bodies_of(spec)
+        self.shapes, self.ns = _shapes_of(spec)
         nx, ny = spec["nx"], spec["ny"]
         if g is None:
             self.g = np.zeros((9, ny, nx))
@@ -184,30 +203,47 @@ class Domain:
     def run(self, n: int, srt: bool = False, want_forces: bool = True) -> np.ndarray:
         """Advance n steps; returns the force on each body per step, [n, nbodies, 2]."""
         forces = np.zeros((n, max(self.nb, 1), 2)) if want_forces else None
-        rc = lib().ora_run(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)),
-                           self.bodies, self.nb, _dp(self.g), n,
-                           _dp(forces) if want_forces else None, 1 if srt else 0)
+        if self.moving:
+            rc = lib().ora_run_moving(C.byref(self.p), self.shapes, self.ns, self.bodies,
+                                      self.nb, _dp(self.g), self.steps_done, n,
+                                      _dp(forces) if want_forces else None, 1 if srt else 0)
+        else:
+            rc = lib().ora_run(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)),
+                               self.bodies, self.nb, _dp(self.g), n,
+                               _dp(forces) if want_forces else None, 1 if srt else 0)
         if rc != 0:
             raise MemoryError("oracle run failed to allocate")
         self.steps_done += n
+        if self.moving:
+            self.mask = rasterize(self.spec, self.steps_done)
         return forces[:, : self.nb] if want_forces else None
+
+    def _bodies_now(self):
+        """Body table at the current step index (centres moved for a moving domain)."""
+        if not self.moving:
+            return self.bodies
+        out = (_Body * max(1, self.nb))()
+        lib().ora_bodies_at(self.bodies, self.nb, self.steps_done, out)
+        return out
 
     def step_once(self, srt: bool = False):
         """One step returning (new g, forces [nbodies, 2]) without the run wrapper."""
         out = np.zeros_like(self.g)
         fb = np.zeros((max(self.nb, 1), 2))
         fn = lib().ora_step_srt if srt else lib().ora_step_trt
-        fn(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)), self.bodies,
+        fn(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)), self._bodies_now(),
            self.nb, _dp(self.g), _dp(out), _dp(fb))
         self.g = out
         self.steps_done += 1
+        if self.moving:
+            self.mask = rasterize(self.spec, self.steps_done)
         return out, fb[: self.nb]
 
     def moments(self):
         nx, ny = self.spec["nx"], self.spec["ny"]
         rho, ux, uy = (np.zeros((ny, nx)) for _ in range(3))
         lib().ora_moments(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)),
-                          self.bodies, _dp(self.g), _dp(rho), _dp(ux), _dp(uy))
+                          self._bodies_now(), _dp(self.g), _dp(rho), _dp(ux), _dp(uy))
         return rho, ux, uy
 
 

@@ -135,6 +135,37 @@ void ora_rasterize(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nsha
     }
 }
 
+/* ---- moving obstacles ---------------------------------------------------------------------
+ * chi(x, t) and U_O(x, t) may depend on time (Sec. 2.2, the penalized equations hold for
+ * moving obstacles). Prescribed translation: at step index n body k has its centre at
+ * c_k + V_k n and each of its shapes is translated by V_k n; rotation enters through
+ * U_O only (exact for circles about their centre). */
+static void shape_at(const ora_shape *s0, const ora_body *bodies, int32_t nbodies, int64_t n,
+                     ora_shape *s) {
+  *s = *s0;
+  if (s0->body >= 1 && s0->body <= nbodies) {
+    const ora_body *b = &bodies[s0->body - 1];
+    s->cx = s0->cx + b->vx * (double)n;
+    s->cy = s0->cy + b->vy * (double)n;
+  }
+}
+
+static void body_at(const ora_body *b0, int64_t n, ora_body *b) {
+  *b = *b0;
+  b->cx = b0->cx + b0->vx * (double)n;
+  b->cy = b0->cy + b0->vy * (double)n;
+}
+
+/* The mask at step index n (shapes translated with their bodies). */
+void ora_rasterize_at(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
+                      const ora_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
+  ora_shape *moved = (ora_shape *)malloc(sizeof(ora_shape) * (nshapes > 0 ? nshapes : 1));
+  if (!moved) abort();
+  for (int k = 0; k < nshapes; k++) shape_at(&shapes[k], bodies, nbodies, n, &moved[k]);
+  ora_rasterize(nx, ny, moved, nshapes, mask);
+  free(moved);
+}
+
 /* ---- streaming with the domain-edge rules (Eq. streaming) ---------------------------- */
 
 static inline double G(const double *g, const ora_params *p, int a, int j, int i) {
@@ -315,6 +346,38 @@ int ora_run(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
   free(tmp);
   free(fb);
   return 0;
+}
+
+/* Run n steps of a domain whose bodies move (prescribed translation), starting at step
+ * index n0: before step n0 + s the mask is rasterised at that index and the bodies'
+ * centres are moved there. Arguments as ora_run, plus the shapes. */
+int ora_run_moving(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
+                   const ora_body *bodies, int32_t nbodies, double *g, int64_t n0, int64_t n,
+                   double *forces, int32_t srt) {
+  size_t cells = (size_t)p->nx * p->ny;
+  double *tmp = (double *)malloc(sizeof(double) * Q * cells);
+  double *fb = (double *)malloc(sizeof(double) * 2 * (nbodies > 0 ? nbodies : 1));
+  uint8_t *mask = (uint8_t *)malloc(cells);
+  ora_body *moved = (ora_body *)malloc(sizeof(ora_body) * (nbodies > 0 ? nbodies : 1));
+  if (!tmp || !fb || !mask || !moved) { free(tmp); free(fb); free(mask); free(moved); return -1; }
+  double *a = g, *b = tmp;
+  for (int64_t s = 0; s < n; s++) {
+    const int64_t m = n0 + s;
+    ora_rasterize_at(p->nx, p->ny, shapes, nshapes, bodies, nbodies, m, mask);
+    for (int k = 0; k < nbodies; k++) body_at(&bodies[k], m, &moved[k]);
+    if (srt) ora_step_srt(p, mask, moved, nbodies, a, b, fb);
+    else ora_step_trt(p, mask, moved, nbodies, a, b, fb);
+    if (forces) memcpy(forces + (size_t)s * 2 * nbodies, fb, sizeof(double) * 2 * nbodies);
+    double *t = a; a = b; b = t;
+  }
+  if (a != g) memcpy(g, a, sizeof(double) * Q * cells);
+  free(tmp); free(fb); free(mask); free(moved);
+  return 0;
+}
+
+/* The bodies of a moving domain at step index n (centres translated). */
+void ora_bodies_at(const ora_body *bodies, int32_t nbodies, int64_t n, ora_body *out) {
+  for (int k = 0; k < nbodies; k++) body_at(&bodies[k], n, &out[k]);
 }
 
 /* Step (1): every node starts at f^eq(rho0, u0). */

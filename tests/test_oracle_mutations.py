@@ -36,6 +36,9 @@ MUTATIONS = [
     ("naca_coefficient", "- 0.3516) * xc", "- 0.3561) * xc"),
     ("naca_aoa_sign", "ley = s->cy + qc * sa;", "ley = s->cy - qc * sa;"),
     ("circle_strict", "(d2 < r2) : (d2 > r2)", "(d2 <= r2) : (d2 > r2)"),
+    ("moving_shape_sign", "s->cx = s0->cx + b->vx * (double)n;", "s->cx = s0->cx - b->vx * (double)n;"),
+    ("moving_centre_fixed", "b->cx = b0->cx + b0->vx * (double)n;", "b->cx = b0->cx;"),
+    ("moving_step_index", "const int64_t m = n0 + s;", "const int64_t m = n0 + s + 1;"),
 ]
 
 # Pins in order of cost; each mutation stops at the first one that fails.
@@ -61,6 +64,11 @@ PINS = [
     lambda: pins.test_shear_wave_decay_rate(0.1, 3 / 16),
     pins.test_srt_reduction,
     pins.test_couette_closed_form_and_trt_properties,
+    pins.test_moving_mask_is_the_translated_mask,
+    pins.test_moving_run_equals_single_steps,
+    pins.test_moving_body_in_comoving_uniform_flow_is_steady,
+    pins.test_moving_bodies_conserve_mass_and_balance_momentum,
+    pins.test_moving_body_velocity_about_the_moving_centre,
 ]
 
 

@@ -309,6 +309,109 @@ def test_fully_penalized_box_closed_form():
         assert np.allclose(fb[0], want, rtol=1e-11)
 
 
+def _moving(sp):
+    return dict(sp, moving=True)
+
+
+def test_moving_mask_is_the_translated_mask():
+    # Moving obstacles (Sec. 2.2: chi and U_O may depend on time). With velocities that
+    # are exact binary fractions the translated shapes land on whole cells after 8 steps
+    # (4 and -2 cells): the mask is the reference mask rolled by those cells (numpy).
+    sp = _moving(_spec(96, 64, shapes=[synth._circle(1, 30.0, 32.0, 7.5),
+                                       {"kind": "naca4", "body": 2, "cx": 60.0, "cy": 20.0,
+                                        "chord": 24.0, "thickness": 0.12, "aoa_rad": 0.1}],
+                       bodies=[synth._body(30.0, 32.0, 15.0, vx=0.5, vy=-0.25),
+                               synth._body(60.0, 20.0, 24.0, vx=-0.125, vy=0.375)]))
+    m0 = oracle.rasterize(sp, 0)
+    assert np.array_equal(m0, oracle.rasterize(sp))
+    m8 = oracle.rasterize(sp, 8)
+    want = np.zeros_like(m0)
+    c1 = np.roll(np.roll(np.where(m0 == 1, 1, 0), 4, axis=1), -2, axis=0)
+    c2 = np.roll(np.roll(np.where(m0 == 2, 2, 0), -1, axis=1), 3, axis=0)
+    want = np.maximum(c1, c2).astype(np.uint8)
+    assert (m0 == 1).sum() > 150 and (m0 == 2).sum() > 40
+    assert np.array_equal(m8, want)
+    # and the run re-rasterises: after 8 steps the domain holds the mask of step 8
+    d = oracle.Domain(sp)
+    d.run(8, want_forces=False)
+    assert np.array_equal(d.mask, m8)
+
+
+def test_moving_run_equals_single_steps():
+    # The step from index n to n + 1 uses the geometry of index n (mask and centres): the
+    # C loop over steps gives bit for bit the state of single steps taken with the mask
+    # and body table of each index.
+    sp = _moving(_spec(37, 26, nu=0.05, lam=0.25, shapes=[synth._circle(1, 10, 12, 5)],
+                       bodies=[synth._body(10, 12, 10, vx=0.3, vy=-0.2, omega=2e-3)]))
+    g0 = synth.random_populations(11, 37, 26)
+    a = oracle.Domain(sp, g=g0)
+    fa = a.run(7)
+    b = oracle.Domain(sp, g=g0)
+    fb = np.array([b.step_once()[1] for _ in range(7)])
+    assert np.array_equal(a.g, b.g) and np.array_equal(fa, fb)
+    assert not np.array_equal(a.mask, oracle.rasterize(sp))
+
+
+def test_moving_body_in_comoving_uniform_flow_is_steady():
+    # A body moving with the velocity of a uniform flow: U_O = u everywhere, so the
+    # penalization does nothing (du = 0, F_VP = 0) and the uniform equilibrium stays
+    # as it is, although the mask moves by a non-integer distance every step.
+    u = (0.03, -0.011)
+    sp = _moving(_spec(40, 30, shapes=[synth._circle(1, 15.0, 14.0, 6.0)],
+                       bodies=[synth._body(15.0, 14.0, 12.0, vx=u[0], vy=u[1])], u0=u))
+    d = oracle.Domain(sp)
+    g0 = d.g.copy()
+    f = d.run(150)
+    # roundoff only: u* - U_O ~ 1e-17 per node (a wrong mask or centre gives ~1e-2)
+    assert np.max(np.abs(d.g - g0)) < 1e-13
+    assert np.max(np.abs(f)) < 1e-13
+    assert not np.array_equal(d.mask, oracle.rasterize(sp))  # it has moved
+
+
+def test_moving_bodies_conserve_mass_and_balance_momentum():
+    # A moving, rotating body in a periodic box: mass is conserved exactly and the
+    # momentum gained each step is minus the force on the bodies (P3, P4 with chi(t)).
+    sp = _moving(_spec(37, 26, nu=0.05, lam=0.25,
+                       shapes=[synth._circle(1, 10, 12, 5), synth._circle(2, 26, 13, 4.5)],
+                       bodies=[synth._body(10, 12, 10, vx=0.05, vy=0.02, omega=-2e-3),
+                               synth._body(26, 13, 9, vx=-0.03)]))
+    d = oracle.Domain(sp, g=synth.random_populations(3, 37, 26))
+    m0 = d.g.sum()
+    for _ in range(60):
+        _, jx0, jy0 = (v.sum() for v in _moments(d.g))
+        _, fb = d.step_once()
+        _, jx1, jy1 = (v.sum() for v in _moments(d.g))
+        net = fb.sum(axis=0)
+        assert abs((jx1 - jx0) + net[0]) < 1e-14 * 37 * 26
+        assert abs((jy1 - jy0) + net[1]) < 1e-14 * 37 * 26
+    assert abs(d.g.sum() - m0) < 1e-12 * m0
+    assert not np.array_equal(d.mask, oracle.rasterize(sp))
+
+
+def test_moving_body_velocity_about_the_moving_centre():
+    # chi = 1 everywhere (an "outside" annulus of radius 0), a body translating at V and
+    # rotating at Omega: the corrected velocity u = u* + du of every node is U_O(x, t) =
+    # V + Omega z x (x - c(t)) within 2 eta |u* - U_O| (Eq. d-V, Eq. velocity-r), with the
+    # centre c(t) = c0 + V t moving; a centre left at c0 would be off by Omega V t.
+    # (|u* - U_O| reaches a few 1e-2 where the periodic wrap meets the rotation's jump.)
+    eta = 1e-6
+    # (the centre never lands on a node, where the radius-0 annulus would leave a fluid node)
+    V, om, c0 = (0.02, 0.01), 1e-3, (10.25, 8.25)
+    sp = _moving(_spec(20, 16, nu=0.1, eta=eta,
+                       shapes=[{"kind": "annulus_outside", "body": 1, "cx": c0[0], "cy": c0[1],
+                                "radius": 0.0}],
+                       bodies=[synth._body(c0[0], c0[1], 1.0, vx=V[0], vy=V[1], omega=om)]))
+    d = oracle.Domain(sp)
+    d.run(200, want_forces=False)
+    assert np.all(d.mask == 1)
+    _, ux, uy = d.moments()
+    j, i = np.mgrid[0:16, 0:20]
+    cx, cy = c0[0] + V[0] * 200, c0[1] + V[1] * 200
+    assert np.max(np.abs(ux - (V[0] - om * (j - cy)))) < 1e-5
+    assert np.max(np.abs(uy - (V[1] + om * (i - cx)))) < 1e-5
+    assert om * V[0] * 200 > 1e-3  # the error a fixed centre would make
+
+
 @pytest.mark.parametrize("nu,lam", [(0.1, 3 / 16), (0.02, 0.25)])
 def test_shear_wave_decay_rate(nu, lam):
     # P6: a shear wave u_x = u0 sin(2 pi j / NY) decays as exp(-nu k^2 t) with
