@@ -114,6 +114,11 @@ typedef struct {
   int32_t storage;        /* lbm_storage */
   int32_t force_every;    /* record body forces every k-th step (0: never) */
   int32_t force_capacity; /* force-ring entries kept on the device (0: 8192) */
+  int32_t moving;         /* 1: the bodies move (prescribed translation): at step index n
+                           * body k is centred at c_k + V_k n and its shapes are translated
+                           * by V_k n (chi(x, t), U_O(x, t) of Sec. 2.2; rotation acts through
+                           * U_O only). Needs device geometry (no host mask), at most 64
+                           * shapes and 8 bodies. 0: fixed mask. */
 } lbm_params;
 
 typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);

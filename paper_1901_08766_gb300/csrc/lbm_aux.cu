@@ -60,6 +60,150 @@ cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int
   return cudaGetLastError();
 }
 
+// ---- moving domains (prescribed translation) ------------------------------------------------
+// chi(x, t) and U_O(x, t) of a domain whose bodies translate (Sec. 2.2): at step index n
+// body k is centred at c_k + V_k n and each of its shapes is translated by V_k n. The
+// step from n to n + 1 uses the geometry of index n; after its sweep, one warp per row
+// (a fixed mapping, so the result does not depend on the launch) first sums -F_VP over
+// the row's nodes of each body under the mask the sweep used (FP64, lane-strided then a
+// fixed shuffle tree; the force kernel adds the rows in order), then rewrites the row's
+// mask for index n + 1. Each node is read and rewritten by the same lane. The warp of
+// row 0 moves the body centres. Positions are c + V n with explicitly rounded FP64
+// operations, as a plain evaluation on the host computes them.
+
+constexpr int kMoveWarps = 8;
+
+__device__ __forceinline__ double moved(double c0, double v, long long n) {
+  return __dadd_rn(c0, __dmul_rn(v, static_cast<double>(n)));
+}
+
+// Translated shapes of a domain at index n and their column range in row j (shared
+// memory of the warp; lo > hi: the row misses the shape).
+struct RowShape {
+  ShapeDev s;
+  int lo, hi;
+};
+
+__device__ void place_row(const DomDev &D, int j, long long n, int lane, RowShape *rs) {
+  for (int k = lane; k < D.nshapes; k += 32) {
+    ShapeDev s = D.shapes[k];
+    if (s.body >= 1 && s.body <= D.nbodies) {
+      const double *b = D.bodies + 5 * (s.body - 1);
+      s.cx = moved(s.cx, b[2], n);
+      s.cy = moved(s.cy, b[3], n);
+    }
+    // a node farther than the reach from the reference point is outside the shape
+    int lo = 0, hi = D.nx - 1;
+    if (s.kind != LBM_SHAPE_ANNULUS_OUTSIDE) {
+      const double reach = (s.kind == LBM_SHAPE_CIRCLE ? s.radius : s.chord) + 1.0;
+      if (fabs(double(j) - s.cy) > reach) {
+        lo = 1;
+        hi = 0;
+      } else {
+        // clamped in FP64 first, so that a shape far outside converts safely
+        const double dlo = fmin(fmax(floor(s.cx - reach), -1.0), double(D.nx));
+        const double dhi = fmin(fmax(ceil(s.cx + reach), -1.0), double(D.nx));
+        lo = max(0, static_cast<int>(dlo));
+        hi = min(D.nx - 1, static_cast<int>(dhi));
+      }
+    }
+    rs[k].s = s;
+    rs[k].lo = lo;
+    rs[k].hi = hi;
+  }
+  __syncwarp();
+  uint8_t *row = D.mask + static_cast<size_t>(j) * D.pitch;
+  for (int i = lane; i < D.pitch; i += 32) {
+    uint8_t id = 0;
+    if (i < D.nx)
+      for (int k = 0; k < D.nshapes; ++k)
+        if (i >= rs[k].lo && i <= rs[k].hi && inside(rs[k].s, double(i), double(j)))
+          id = static_cast<uint8_t>(rs[k].s.body);
+    row[i] = id;
+  }
+  __syncwarp();
+}
+
+__device__ void place_centres(const DomDev &D, long long n, int lane) {
+  if (lane < D.nbodies) {
+    double *b = D.bodies + 5 * lane;
+    const double cx = moved(D.centre0[2 * lane], b[2], n), cy = moved(D.centre0[2 * lane + 1], b[3], n);
+    b[0] = cx;
+    b[1] = cy;
+    D.bodies_f[5 * lane] = float(cx);
+    D.bodies_f[5 * lane + 1] = float(cy);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMoveWarps * 32)
+move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr, int s) {
+  __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nrows = ctr->nmove;
+  const long long run_base = ctr->run_base;
+  for (int q = blockIdx.x * kMoveWarps + warp; q < nrows; q += gridDim.x * kMoveWarps) {
+    const MoveRow mr = rows[q];
+    const DomDev &D = doms[mr.dom];
+    const DomDyn dy = dyn[mr.dom];
+    const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
+    if (n >= dy.step_end) continue;
+    const int j = mr.j;
+    const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
+    if (D.force_every > 0 && (n + 1) % D.force_every == 0) {
+      const T *fv = static_cast<const T *>(D.fvp) + 2 * static_cast<size_t>(j) * D.pitch;
+      for (int body = 1; body <= D.nbodies; ++body) {
+        double fx = 0.0, fy = 0.0;
+        for (int i = lane; i < D.nx; i += 32)
+          if (mrow[i] == body) {
+            fx -= double(fv[2 * i]);
+            fy -= double(fv[2 * i + 1]);
+          }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          fx += __shfl_down_sync(0xffffffffu, fx, off);
+          fy += __shfl_down_sync(0xffffffffu, fy, off);
+        }
+        if (lane == 0) {
+          double *r = D.rowsum + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 2;
+          r[0] = fx;
+          r[1] = fy;
+        }
+      }
+    }
+    __syncwarp();
+    place_row(D, j, n + 1, lane, shapes[warp]);
+    if (j == 0) place_centres(D, n + 1, lane);
+  }
+}
+
+cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                        const MoveRow *rows, const Counters *ctr, int s, int storage) {
+  if (storage == LBM_F64)
+    move_kernel<double><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, s);
+  else
+    move_kernel<float><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, s);
+  return cudaGetLastError();
+}
+
+// Mask and centres of one moving domain at index n (admission, step-index changes).
+__global__ void __launch_bounds__(kMoveWarps * 32) place_kernel(const DomDev *dom, long long n) {
+  __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const DomDev &D = *dom;
+  for (int j = blockIdx.x * kMoveWarps + warp; j < D.ny; j += gridDim.x * kMoveWarps) {
+    place_row(D, j, n, lane, shapes[warp]);
+    if (j == 0) place_centres(D, n, lane);
+  }
+}
+
+cudaError_t launch_place(cudaStream_t st, const DomDev *dom_dev, int nx, int ny, int pitch, long long n) {
+  (void)nx;
+  (void)pitch;
+  place_kernel<<<(ny + kMoveWarps - 1) / kMoveWarps, kMoveWarps * 32, 0, st>>>(dom_dev, n);
+  return cudaGetLastError();
+}
+
 // ---- initial state: g = f^eq(rho0, u0) at every node, padding zero ----------------------
 
 template <int S>
@@ -186,15 +330,24 @@ forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, con
     const int force_every = D.force_every;
     // the node indices do not depend on the step: their loads overlap the checks below
     const int q0 = item.beg + threadIdx.x;
-    const int32_t lin0 = q0 < item.end ? __ldg(solid + q0) : 0;
+    const int32_t lin0 = (!item.rows && q0 < item.end) ? __ldg(solid + q0) : 0;
     const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
     if (n >= dy.step_end || force_every <= 0) continue;
     if ((n + 1) % force_every != 0) continue;
     double fx = 0.0, fy = 0.0;
-    for (int q = q0; q < item.end; q += blockDim.x) {
-      const size_t lin = static_cast<size_t>(q == q0 ? lin0 : __ldg(solid + q));
-      fx -= double(fv[2 * lin]);
-      fy -= double(fv[2 * lin + 1]);
+    if (item.rows) {
+      // moving domain: the per-row sums of -F_VP, rows in order per thread
+      for (int q = q0; q < item.end; q += blockDim.x) {
+        const double *r = D.rowsum + (static_cast<size_t>(q) * D.nbodies + (item.body - 1)) * 2;
+        fx += r[0];
+        fy += r[1];
+      }
+    } else {
+      for (int q = q0; q < item.end; q += blockDim.x) {
+        const size_t lin = static_cast<size_t>(q == q0 ? lin0 : __ldg(solid + q));
+        fx -= double(fv[2 * lin]);
+        fy -= double(fv[2 * lin + 1]);
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

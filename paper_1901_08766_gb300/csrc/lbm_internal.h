@@ -14,6 +14,8 @@ namespace lbm {
 constexpr int kQ = 9;
 constexpr int kPitchAlign = 64;  // row pitch in elements is a multiple of this
 constexpr int kMaxBodies = 255;
+constexpr int kMaxMovingShapes = 64;  // geometry kept on the device by a moving domain
+constexpr int kMaxMovingBodies = 8;
 
 // Per-domain constants of the collision in one precision (filled on the host).
 // FP16-shifted storage holds kF16Scale (f - w rho0): values up to 65504 / 1024 = 64
@@ -35,11 +37,13 @@ template <typename T> struct CellConst {
 };
 
 // Per-domain static description, resident in device memory (one per batch slot).
+struct ShapeDev;
+
 struct DomDev {
   void *lat[2];            // lattice A/B: [9][ny][pitch] elements of the storage type
-  const uint8_t *mask;     // [ny][pitch] body id, 0 = fluid
-  const double *bodies;    // [nbodies][5]: cx, cy, vx, vy, omega
-  const float *bodies_f;   // the same table rounded to FP32 (FP32-compute storages)
+  uint8_t *mask;           // [ny][pitch] body id, 0 = fluid
+  double *bodies;          // [nbodies][5]: cx, cy, vx, vy, omega (centres at the current step)
+  float *bodies_f;         // the same table rounded to FP32 (FP32-compute storages)
   const int32_t *solid;    // solid nodes (j * pitch + i), grouped by body, row-major
   const int32_t *solid_off;// [nbodies + 1] offsets into solid
   void *fvp;               // F_VP of solid nodes, [ny][pitch] pairs in compute precision
@@ -54,6 +58,11 @@ struct DomDev {
   double ghost[kQ];         // inlet populations f^eq(rho0, u_in) (minus w rho0 if storage is shifted)
   CellConst<float> cf;      // collision constants for FP32 compute
   CellConst<double> cd;     // collision constants for FP64 compute
+  // moving domains (prescribed translation; null / 0 otherwise)
+  const ShapeDev *shapes;   // [nshapes] reference geometry (step index 0)
+  const double *centre0;    // [nbodies][2] reference centres
+  double *rowsum;           // [ny][nbodies][2] per-row sums of -F_VP of recorded steps
+  int32_t nshapes, moving;
 };
 
 // Per-domain dynamic state, uploaded at the start of each batch run.
@@ -69,9 +78,15 @@ struct TileDev {
   int32_t dom, x0, y0, pad;
 };
 
-// One force-reduction item: (slot, body id) and the body's range in the solid list.
+// One force-reduction item: (slot, body id) and the body's range in the solid list, or
+// (rows = 1, moving domains) the range of rows of the per-row sums.
 struct ForceItem {
-  int32_t dom, body, beg, end;
+  int32_t dom, body, beg, end, rows, pad;
+};
+
+// One row of a moving domain for the geometry update.
+struct MoveRow {
+  int32_t dom, j;
 };
 
 // Device-side counters of a batch.
@@ -79,6 +94,8 @@ struct Counters {
   int32_t ntiles;
   int32_t nforce;
   long long run_base;  // steps completed in the current run (advanced by the graphs)
+  int32_t nmove;       // rows of moving domains
+  int32_t pad;
 };
 
 struct SweepArgs {
@@ -100,6 +117,12 @@ cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *
                           int s);
 void fill_cell_const(DomDev &d, int storage);
 cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
+// moving domains: after the sweep of a step, per-row -F_VP sums over the mask it used,
+// then the mask and body centres of the next step index
+cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                        const MoveRow *rows, const Counters *ctr, int s, int storage);
+// the mask and body centres of one moving domain at step index n
+cudaError_t launch_place(cudaStream_t st, const DomDev *dom_dev, int nx, int ny, int pitch, long long n);
 cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
                              const ShapeDev *shapes, int nshapes);
 cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,

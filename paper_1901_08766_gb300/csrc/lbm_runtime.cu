@@ -79,7 +79,7 @@ struct Alloc {
 // force ring, status word), each piece 256-byte aligned.
 struct Layout {
   size_t lat_bytes, mask_off, fvp_off, bodies_off, bodies_f_off, off_off, ring_off, status_off,
-      total;
+      shapes_off, centre0_off, rowsum_off, total;
 };
 
 Layout layout_of(const lbm_params &p, int nbodies) {
@@ -103,6 +103,15 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   o += align_up(p.force_every > 0 ? sizeof(double) * 2 * std::max(1, nbodies) * cap : 16, 256);
   L.status_off = o;
   o += 256;
+  // moving domains: reference geometry, reference centres, per-row force sums
+  L.shapes_off = L.centre0_off = L.rowsum_off = o;
+  if (p.moving) {
+    o += align_up(sizeof(ShapeDev) * kMaxMovingShapes, 256);
+    L.centre0_off = o;
+    o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
+    L.rowsum_off = o;
+    o += align_up(sizeof(double) * 2 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
+  }
   L.total = o;
   return L;
 }
@@ -126,6 +135,9 @@ lbm_status validate(const lbm_params *p, int nbodies) {
   if ((p->south == LBM_PERIODIC) != (p->north == LBM_PERIODIC)) return fail(LBM_EINVAL, "y edges: both periodic or neither");
   if (nbodies < 0 || nbodies > kMaxBodies) return fail(LBM_EINVAL, "nbodies must be in [0, 255]");
   if (p->force_every < 0 || p->force_capacity < 0) return fail(LBM_EINVAL, "force_every/capacity must be >= 0");
+  if (p->moving != 0 && p->moving != 1) return fail(LBM_EINVAL, "moving must be 0 or 1");
+  if (p->moving && nbodies > kMaxMovingBodies)
+    return fail(LBM_EINVAL, "a moving domain has at most %d bodies", kMaxMovingBodies);
   return LBM_OK;
 }
 
@@ -217,6 +229,9 @@ struct lbm_batch {
   int tiles_cap = 0;
   ForceItem *d_items = nullptr;
   int items_cap = 0;
+  MoveRow *d_moves = nullptr;  // rows of moving domains (geometry update after each sweep)
+  int moves_cap = 0;
+  int nmove = 0;               // rows in the list; 0: no move kernel in the step
   Counters *d_ctr = nullptr;
   Counters *h_ctr = nullptr;  // pinned staging for tile/item counts
   int vec = 0, warps = 0, rows = 0, pipe = 0;
@@ -299,16 +314,35 @@ lbm_status set_config(lbm_batch *b, int vec, int warps, int rows, int pipe) {
 lbm_status rebuild_lists(lbm_batch *b) {
   std::vector<TileDev> tiles;
   std::vector<ForceItem> items;
+  std::vector<MoveRow> moves;
   const int tw = 32 * b->vec, th = b->warps * b->rows;
   for (int k = 0; k < b->max_domains; ++k) {
     const Slot &s = b->slots[k];
     if (!s.used) continue;
     for (int y0 = 0; y0 < s.p.ny; y0 += th)
       for (int x0 = 0; x0 < s.p.nx; x0 += tw) tiles.push_back(TileDev{k, x0, y0, 0});
+    if (s.p.moving)
+      for (int j = 0; j < s.p.ny; ++j) moves.push_back(MoveRow{k, j});
     if (s.p.force_every > 0)
       for (int body = 1; body <= s.nbodies; ++body)
-        items.push_back(ForceItem{k, body, s.solid_off[body - 1], s.solid_off[body]});
+        items.push_back(s.p.moving ? ForceItem{k, body, 0, s.p.ny, 1, 0}
+                                   : ForceItem{k, body, s.solid_off[body - 1], s.solid_off[body], 0, 0});
   }
+  // a captured graph holds the move kernel only if there were moving rows at capture
+  if ((b->nmove > 0) != !moves.empty()) drop_graph(b);
+  if (static_cast<int>(moves.size()) > b->moves_cap || (!moves.empty() && !b->d_moves)) {
+    const int cap = std::max<int>(static_cast<int>(moves.size()) * 2, 1024);
+    LBM_CUDA(cudaStreamSynchronize(b->st));
+    b->al.put(b->d_moves);
+    b->d_moves = static_cast<MoveRow *>(b->al.get(sizeof(MoveRow) * cap));
+    if (!b->d_moves) { b->moves_cap = 0; return fail(LBM_ENOMEM, "move list allocation failed"); }
+    b->moves_cap = cap;
+    drop_graph(b);
+  }
+  b->nmove = static_cast<int>(moves.size());
+  if (!moves.empty())
+    LBM_CUDA(cudaMemcpyAsync(b->d_moves, moves.data(), sizeof(MoveRow) * moves.size(),
+                             cudaMemcpyHostToDevice, b->st));
   if (static_cast<int>(tiles.size()) > b->tiles_cap || !b->d_tiles) {
     const int cap = std::max<int>(static_cast<int>(tiles.size()) * 2, 1024);
     LBM_CUDA(cudaStreamSynchronize(b->st));
@@ -340,6 +374,8 @@ lbm_status rebuild_lists(lbm_batch *b) {
   b->h_ctr->ntiles = b->ntiles;
   b->h_ctr->nforce = b->nitems;
   b->h_ctr->run_base = 0;
+  b->h_ctr->nmove = b->nmove;
+  b->h_ctr->pad = 0;
   LBM_CUDA(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaStreamSynchronize(b->st));
   b->dirty = false;
@@ -354,6 +390,10 @@ lbm_status rebuild_lists(lbm_batch *b) {
 lbm_status enqueue_step(lbm_batch *b, int s) {
   LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, s));
   b->launches++;
+  if (b->nmove > 0) {  // moving domains: row force sums, then the next step's geometry
+    LBM_CUDA(launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
+    b->launches++;
+  }
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
                          b->d_ctr, s));
   b->launches++;
@@ -444,6 +484,12 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
       if (sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, static_cast<int>(s)) != cudaSuccess)
         prc = fail(LBM_ECUDA, "sweep launch failed");
       cudaEventRecord(ev[3 * s + 1], b->st);
+      if (b->nmove > 0) {
+        if (launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
+                        static_cast<int>(s), b->storage) != cudaSuccess)
+          prc = fail(LBM_ECUDA, "move launch failed");
+        b->launches++;
+      }
       if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
                         static_cast<int>(s)) != cudaSuccess)
         prc = fail(LBM_ECUDA, "force launch failed");
@@ -470,7 +516,7 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
     const long long reps = steps / b->graph_steps;
     for (long long r = 0; r < reps; ++r) {
       LBM_CUDA(cudaGraphLaunch(b->graph, b->st));
-      b->launches += 2 * static_cast<long long>(b->graph_steps) + 1;
+      b->launches += (b->nmove > 0 ? 3 : 2) * static_cast<long long>(b->graph_steps) + 1;
     }
     s0 = reps * b->graph_steps;
   }
@@ -504,6 +550,11 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   if (nbodies > 0 && !bodies) return fail(LBM_EINVAL, "bodies is NULL");
   if (!mask_host && geom && geom->nshapes > 0 && !geom->shapes) return fail(LBM_EINVAL, "geometry shapes NULL");
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+  if (p->moving) {
+    if (mask_host) return fail(LBM_EINVAL, "a moving domain is rasterised from its geometry (mask given)");
+    if (!geom || geom->nshapes < 1 || geom->nshapes > kMaxMovingShapes)
+      return fail(LBM_EINVAL, "a moving domain needs 1..%d shapes", kMaxMovingShapes);
+  }
   int k = -1;
   for (int i = 0; i < b->max_domains; ++i)
     if (!b->slots[i].used) { k = i; break; }
@@ -543,6 +594,11 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.fvp = base + L.fvp_off;
   D.ring = reinterpret_cast<double *>(base + L.ring_off);
   D.status = reinterpret_cast<int32_t *>(base + L.status_off);
+  D.moving = p->moving;
+  D.nshapes = p->moving ? geom->nshapes : 0;
+  D.shapes = p->moving ? reinterpret_cast<const ShapeDev *>(base + L.shapes_off) : nullptr;
+  D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
+  D.rowsum = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
   D.nx = p->nx;
   D.ny = p->ny;
   D.pitch = s.pitch;
@@ -610,9 +666,11 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
                  std::cos(sh.aoa_rad), std::sin(sh.aoa_rad)};
       shapes.push_back(d);
     }
-    ShapeDev *dsh = reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + counts_bytes + offs_bytes);
+    ShapeDev *dsh = p->moving ? const_cast<ShapeDev *>(D.shapes)
+                              : reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + counts_bytes + offs_bytes);
     ADM_CUDA(cudaMemcpyAsync(dsh, shapes.data(), sizeof(ShapeDev) * ns, cudaMemcpyHostToDevice, st));
-    ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns));
+    // a moving domain is placed at its step index below, once its body table is resident
+    if (!p->moving) ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns));
   }
   // body table
   std::vector<double> hb(5 * std::max(1, nbodies), 0.0);
@@ -626,6 +684,18 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   ADM_CUDA(cudaMemcpyAsync(bod, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
   std::vector<float> hbf(hb.begin(), hb.end());
   ADM_CUDA(cudaMemcpyAsync(bodf, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
+  if (p->moving) {
+    // reference centres, then the mask and centres of step index 0
+    std::vector<double> hc0(2 * std::max(1, nbodies), 0.0);
+    for (int i = 0; i < nbodies; ++i) {
+      hc0[2 * i] = bodies[i].cx;
+      hc0[2 * i + 1] = bodies[i].cy;
+    }
+    ADM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.centre0), hc0.data(), sizeof(double) * hc0.size(),
+                             cudaMemcpyHostToDevice, st));
+    ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
+    ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
+  }
   // per-row node counts of every body id, then the row offsets of each body's nodes
   ADM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
   ADM_CUDA(launch_row_counts(st, mask, p->nx, p->ny, s.pitch, nbodies, counts, bad));
@@ -779,6 +849,7 @@ void destroy(lbm_batch *b) {
   b->al.put(b->d_dyn);
   b->al.put(b->d_tiles);
   b->al.put(b->d_items);
+  b->al.put(b->d_moves);
   b->al.put(b->d_ctr);
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->h_dyn) cudaFreeHost(b->h_dyn);
@@ -1004,6 +1075,8 @@ lbm_status lbm_batch_set_steps_done(lbm_batch *b, int32_t slot, int64_t steps) {
   Slot &s = b->slots[slot];
   if (steps < 0 || steps > s.target)
     return fail(LBM_EINVAL, "step index %lld outside [0, %lld]", static_cast<long long>(steps), s.target);
+  if (s.p.moving)  // the mask and centres of the new step index
+    LBM_CUDA(launch_place(b->st, b->d_doms + slot, s.p.nx, s.p.ny, s.pitch, steps));
   LBM_CUDA(cudaStreamSynchronize(b->st));
   s.done = steps;
   s.drained = entries_at(s, steps);  // nothing pending: entries before the index are gone
