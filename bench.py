@@ -196,7 +196,7 @@ def _config(args, specs, extra=None):
     cells = sum(s["nx"] * s["ny"] for s in specs)
     c = {"workload": "batched uneven domains: 64 seeded tandem/side-by-side cylinder pairs, "
                      "W 400..2000, H = W/2, Re 40..200, D = 40, U = 0.05",
-         "domains": len(specs), "cells": cells, "storage": args.storage,
+         "domains": len(specs), "cells": cells, "storage": args.storage, "moving": bool(args.moving),
          "forces": "every step, FP64 per body", "graph_steps": args.graph_steps,
          "l2": "inputs larger than L2 (working set %.2f GB per step)" %
                (cells * BYTES_PER_CELL[args.storage] / 1e9),
@@ -219,6 +219,10 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     lbm.load()
     specs = rank_domains(synth.batched_domains(64)[: args.domains], rank, ws)
+    if args.moving:
+        # every domain carries the per-step geometry update of moving bodies (velocities
+        # unchanged, so the flow is the same): measures the cost of the update
+        specs = [dict(sp, moving=True) for sp in specs]
     cells = sum(s["nx"] * s["ny"] for s in specs)
     stream = torch.cuda.Stream()
     nsteps_total = args.warmup + args.steps + args.profile_steps + 10
@@ -487,6 +491,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="vec,warps,rows[,pipeline]: fixed sweep tile, no autotune")
     ap.add_argument("--domains", type=int, default=64, help="first N domains of the set")
+    ap.add_argument("--moving", action="store_true",
+                    help="mark every domain as moving (per-step geometry update; same flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e, plain, served and CPU legs")
     ap.add_argument("--served-requests", type=int, default=32)

@@ -67,8 +67,10 @@ cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int
 // (a fixed mapping, so the result does not depend on the launch) first sums -F_VP over
 // the row's nodes of each body under the mask the sweep used (FP64, lane-strided then a
 // fixed shuffle tree; the force kernel adds the rows in order), then rewrites the row's
-// mask for index n + 1. Each node is read and rewritten by the same lane. The warp of
-// row 0 moves the body centres. Positions are c + V n with explicitly rounded FP64
+// mask for index n + 1. Both touch only the columns that some shape reaches (its
+// reference point within radius or chord + 1) at index n or n + 1: nothing else can be
+// solid. Each node is read and rewritten by the same lane. The warp of row 0 moves the
+// body centres. Positions are c + V n with explicitly rounded FP64
 // operations, as a plain evaluation on the host computes them.
 
 constexpr int kMoveWarps = 8;
@@ -77,53 +79,109 @@ __device__ __forceinline__ double moved(double c0, double v, long long n) {
   return __dadd_rn(c0, __dmul_rn(v, static_cast<double>(n)));
 }
 
-// Translated shapes of a domain at index n and their column range in row j (shared
-// memory of the warp; lo > hi: the row misses the shape).
+// Shape s0 of a domain at index n (translated with its body) and its column interval in
+// row j: a node farther than the shape's reach from its reference point is outside it
+// (lo > hi: the row misses the shape; the outside-annulus kind spans every column).
+__device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n) {
+  ShapeDev s = s0;
+  if (s0.body >= 1 && s0.body <= D.nbodies) {
+    const double *b = D.bodies + 5 * (s0.body - 1);
+    s.cx = moved(s0.cx, b[2], n);
+    s.cy = moved(s0.cy, b[3], n);
+  }
+  return s;
+}
+
+__device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int j, int &lo, int &hi) {
+  lo = 0;
+  hi = nx - 1;
+  if (s.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
+  const double reach = (s.kind == LBM_SHAPE_CIRCLE ? s.radius : s.chord) + 1.0;
+  if (fabs(double(j) - s.cy) > reach) {
+    lo = 1;
+    hi = 0;
+    return;
+  }
+  // clamped in FP64 first, so that a shape far outside converts safely
+  const double dlo = fmin(fmax(floor(s.cx - reach), -1.0), double(nx));
+  const double dhi = fmin(fmax(ceil(s.cx + reach), -1.0), double(nx));
+  lo = max(0, static_cast<int>(dlo));
+  hi = min(nx - 1, static_cast<int>(dhi));
+}
+
 struct RowShape {
   ShapeDev s;
   int lo, hi;
 };
 
-__device__ void place_row(const DomDev &D, int j, long long n, int lane, RowShape *rs) {
-  for (int k = lane; k < D.nshapes; k += 32) {
-    ShapeDev s = D.shapes[k];
-    if (s.body >= 1 && s.body <= D.nbodies) {
-      const double *b = D.bodies + 5 * (s.body - 1);
-      s.cx = moved(s.cx, b[2], n);
-      s.cy = moved(s.cy, b[3], n);
-    }
-    // a node farther than the reach from the reference point is outside the shape
-    int lo = 0, hi = D.nx - 1;
-    if (s.kind != LBM_SHAPE_ANNULUS_OUTSIDE) {
-      const double reach = (s.kind == LBM_SHAPE_CIRCLE ? s.radius : s.chord) + 1.0;
-      if (fabs(double(j) - s.cy) > reach) {
-        lo = 1;
-        hi = 0;
-      } else {
-        // clamped in FP64 first, so that a shape far outside converts safely
-        const double dlo = fmin(fmax(floor(s.cx - reach), -1.0), double(D.nx));
-        const double dhi = fmin(fmax(ceil(s.cx + reach), -1.0), double(D.nx));
-        lo = max(0, static_cast<int>(dlo));
-        hi = min(D.nx - 1, static_cast<int>(dhi));
-      }
-    }
-    rs[k].s = s;
-    rs[k].lo = lo;
-    rs[k].hi = hi;
+// The column interval of shape s0 at index n in row j from FP32 positions with a margin
+// of 2 cells: conservative (it contains every node within the shape's reach) while
+// positions stay below 10^6 cells and n below 2^24, where the FP32 position error is
+// below 0.15 cell. Rows far from every shape thereby cost no FP64 work.
+__device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &s0, long long n, int j,
+                                               int &lo, int &hi) {
+  lo = 0;
+  hi = D.nx - 1;
+  if (s0.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
+  float vx = 0.f, vy = 0.f;
+  if (s0.body >= 1 && s0.body <= D.nbodies) {
+    vx = float(D.bodies[5 * (s0.body - 1) + 2]);
+    vy = float(D.bodies[5 * (s0.body - 1) + 3]);
   }
-  __syncwarp();
+  const float fn = float(n);
+  const float cx = float(s0.cx) + vx * fn, cy = float(s0.cy) + vy * fn;
+  const float reach = float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 2.0f;
+  if (!(fabsf(float(j) - cy) <= reach)) {
+    lo = 1;
+    hi = 0;
+    return;
+  }
+  const float flo = fminf(fmaxf(floorf(cx - reach), -1.0f), float(D.nx));
+  const float fhi = fminf(fmaxf(ceilf(cx + reach), -1.0f), float(D.nx));
+  lo = max(0, static_cast<int>(flo));
+  hi = min(D.nx - 1, static_cast<int>(fhi));
+}
+
+// inside() with an FP32 pre-test for circles: a node whose FP32 squared distance is
+// farther than 0.5 from r^2 is decided there, the others take the exact FP64 predicate.
+// With centres below 4096 in magnitude (FP32 position error <= 1.2e-4) and radii below
+// 100 (|dx|, |dy| <= r + 2 in the column interval), the FP32 error of d^2 is below
+// 2 (|dx| + |dy|) 1.2e-4 + 3 d^2 2^-24 < 0.06, so the FP32 decision is the exact one.
+__device__ __forceinline__ bool inside_fast(const ShapeDev &s, int i, int j) {
+  if (s.kind == LBM_SHAPE_CIRCLE && fabs(s.cx) < 4096.0 && fabs(s.cy) < 4096.0 && s.radius < 100.0) {
+    const float dx = float(i) - float(s.cx), dy = float(j) - float(s.cy);
+    const float d2 = dx * dx + dy * dy, r2 = float(s.radius) * float(s.radius);
+    if (d2 < r2 - 0.5f) return true;
+    if (d2 > r2 + 0.5f) return false;
+  }
+  return inside(s, double(i), double(j));
+}
+
+// Body ids of row j over columns [c0, c1] at the geometry held in rs (warp-wide).
+__device__ void write_ids(const DomDev &D, int j, int c0, int c1, int lane, const RowShape *rs) {
   uint8_t *row = D.mask + static_cast<size_t>(j) * D.pitch;
-  for (int i = lane; i < D.pitch; i += 32) {
+  for (int i = c0 + lane; i <= c1; i += 32) {
     uint8_t id = 0;
     if (i < D.nx)
       for (int k = 0; k < D.nshapes; ++k)
-        if (i >= rs[k].lo && i <= rs[k].hi && inside(rs[k].s, double(i), double(j)))
+        if (i >= rs[k].lo && i <= rs[k].hi && inside_fast(rs[k].s, i, j))
           id = static_cast<uint8_t>(rs[k].s.body);
     row[i] = id;
   }
+}
+
+// The whole mask row j at index n (admission and step-index changes).
+__device__ void place_row(const DomDev &D, int j, long long n, int lane, RowShape *rs) {
+  for (int k = lane; k < D.nshapes; k += 32) {
+    rs[k].s = shape_at(D, D.shapes[k], n);
+    shape_cols(rs[k].s, D.nx, j, rs[k].lo, rs[k].hi);
+  }
+  __syncwarp();
+  write_ids(D, j, 0, D.pitch - 1, lane, rs);
   __syncwarp();
 }
 
+// Body centres at index n (the warp of row 0).
 __device__ void place_centres(const DomDev &D, long long n, int lane) {
   if (lane < D.nbodies) {
     double *b = D.bodies + 5 * lane;
@@ -140,6 +198,7 @@ __global__ void __launch_bounds__(kMoveWarps * 32)
 move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr, int s) {
   __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RowShape *rs = shapes[warp];
   const int nrows = ctr->nmove;
   const long long run_base = ctr->run_base;
   for (int q = blockIdx.x * kMoveWarps + warp; q < nrows; q += gridDim.x * kMoveWarps) {
@@ -149,12 +208,38 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
     const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
     if (n >= dy.step_end) continue;
     const int j = mr.j;
+    // column intervals of the row at the old index (n) and at the new one (n + 1), from
+    // FP32 positions (conservative); exact FP64 shapes only where the row is reached
+    int olo = D.nx, ohi = -1, nlo = D.nx, nhi = -1;
+    for (int k = lane; k < D.nshapes; k += 32) {
+      int lo, hi;
+      shape_cols_f32(D, D.shapes[k], n, j, lo, hi);
+      if (lo <= hi) { olo = min(olo, lo); ohi = max(ohi, hi); }
+      shape_cols_f32(D, D.shapes[k], n + 1, j, rs[k].lo, rs[k].hi);
+      if (rs[k].lo <= rs[k].hi) {
+        nlo = min(nlo, rs[k].lo);
+        nhi = max(nhi, rs[k].hi);
+        rs[k].s = shape_at(D, D.shapes[k], n + 1);
+      }
+    }
+    olo = __reduce_min_sync(0xffffffffu, olo);
+    ohi = __reduce_max_sync(0xffffffffu, ohi);
+    nlo = __reduce_min_sync(0xffffffffu, nlo);
+    nhi = __reduce_max_sync(0xffffffffu, nhi);
+    __syncwarp();
+    if (olo > ohi && nlo > nhi) {  // no shape near this row at either index
+      if (j == 0) place_centres(D, n + 1, lane);
+      continue;
+    }
     const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
-    if (D.force_every > 0 && (n + 1) % D.force_every == 0) {
+    if (D.force_every > 0 && (n + 1) % D.force_every == 0 && olo <= ohi) {
+      // -F_VP of each body over the row's solid nodes (all inside the old interval), with
+      // the step index as a tag: the force kernel adds only the entries of its step, so
+      // rows that no shape reaches need no entry
       const T *fv = static_cast<const T *>(D.fvp) + 2 * static_cast<size_t>(j) * D.pitch;
       for (int body = 1; body <= D.nbodies; ++body) {
         double fx = 0.0, fy = 0.0;
-        for (int i = lane; i < D.nx; i += 32)
+        for (int i = olo + lane; i <= ohi; i += 32)
           if (mrow[i] == body) {
             fx -= double(fv[2 * i]);
             fy -= double(fv[2 * i + 1]);
@@ -165,14 +250,18 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
           fy += __shfl_down_sync(0xffffffffu, fy, off);
         }
         if (lane == 0) {
-          double *r = D.rowsum + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 2;
+          double *r = D.rowsum + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
           r[0] = fx;
           r[1] = fy;
+          r[2] = static_cast<double>(n);
         }
       }
     }
     __syncwarp();
-    place_row(D, j, n + 1, lane, shapes[warp]);
+    // the mask changes only where a shape reaches at either index
+    const int c0 = min(olo, nlo), c1 = max(ohi, nhi);
+    if (c0 <= c1) write_ids(D, j, c0, c1, lane, rs);
+    __syncwarp();
     if (j == 0) place_centres(D, n + 1, lane);
   }
 }
@@ -338,9 +427,11 @@ forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, con
     if (item.rows) {
       // moving domain: the per-row sums of -F_VP, rows in order per thread
       for (int q = q0; q < item.end; q += blockDim.x) {
-        const double *r = D.rowsum + (static_cast<size_t>(q) * D.nbodies + (item.body - 1)) * 2;
-        fx += r[0];
-        fy += r[1];
+        const double *r = D.rowsum + (static_cast<size_t>(q) * D.nbodies + (item.body - 1)) * 3;
+        if (r[2] == static_cast<double>(n)) {  // written for this step
+          fx += r[0];
+          fy += r[1];
+        }
       }
     } else {
       for (int q = q0; q < item.end; q += blockDim.x) {

@@ -61,7 +61,7 @@ struct DomDev {
   // moving domains (prescribed translation; null / 0 otherwise)
   const ShapeDev *shapes;   // [nshapes] reference geometry (step index 0)
   const double *centre0;    // [nbodies][2] reference centres
-  double *rowsum;           // [ny][nbodies][2] per-row sums of -F_VP of recorded steps
+  double *rowsum;           // [ny][nbodies][3] per-row sums of -F_VP and the step they belong to
   int32_t nshapes, moving;
 };
 

@@ -110,7 +110,7 @@ Layout layout_of(const lbm_params &p, int nbodies) {
     L.centre0_off = o;
     o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
     L.rowsum_off = o;
-    o += align_up(sizeof(double) * 2 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
+    o += align_up(sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
   }
   L.total = o;
   return L;
@@ -693,6 +693,8 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     }
     ADM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.centre0), hc0.data(), sizeof(double) * hc0.size(),
                              cudaMemcpyHostToDevice, st));
+    // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
+    ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
     ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
   }
