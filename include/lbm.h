@@ -68,8 +68,12 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_stora
  * f^eq(rho0, u_in)); east PERIODIC or OUTFLOW_ZG (zero gradient: the missing
  * populations are read from the last column). y edges: PERIODIC or FREE_SLIP
  * (specular reflection, walls half a cell outside the first and last rows). Both
- * edges of an axis are periodic or neither is. The x rule is applied first. */
-typedef enum { LBM_PERIODIC = 0, LBM_INLET_EQ = 1, LBM_OUTFLOW_ZG = 2, LBM_FREE_SLIP = 3 } lbm_edge;
+ * edges of an axis are periodic or neither is. The x rule is applied first.
+ * NEIGHBOR (x edges, set only by lbm_batch_link_x): the pull across the edge reads the
+ * adjacent column of another resident domain of the batch (slab decomposition of one
+ * grid). */
+typedef enum { LBM_PERIODIC = 0, LBM_INLET_EQ = 1, LBM_OUTFLOW_ZG = 2, LBM_FREE_SLIP = 3,
+               LBM_NEIGHBOR = 4 } lbm_edge;
 
 /* Rigid body k (1-based id in the mask): obstacle velocity
  * U_O(x) = (vx, vy) + omega * z x (x - (cx, cy))  (Eq. boundary-condition, Sec. 2.2).
@@ -119,6 +123,12 @@ typedef struct {
                            * by V_k n (chi(x, t), U_O(x, t) of Sec. 2.2; rotation acts through
                            * U_O only). Needs device geometry (no host mask), at most 64
                            * shapes and 8 bodies. 0: fixed mask. */
+  int32_t x_origin;       /* global column of local column 0: a domain that is one slab of
+                           * a larger grid rasterises its shapes and evaluates U_O at the
+                           * global position (i + x_origin, j), so slabs reproduce the
+                           * undivided grid bit for bit. 0 for an undivided domain. With
+                           * 16-bit storage it must be divisible by 8: the stochastic
+                           * rounding bits are keyed by global 8-column groups. */
 } lbm_params;
 
 typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
@@ -256,6 +266,18 @@ LBM_API lbm_status lbm_batch_get_mask(lbm_batch *b, int32_t slot, uint8_t *out);
  * (any may be NULL) and the steps run. Synchronises the stream. */
 LBM_API lbm_status lbm_batch_profile(lbm_batch *b, int32_t steps, double *sweep_us,
                                      double *force_us, int64_t *steps_run);
+
+/* Slab decomposition of one grid along x: link two resident domains so that the west
+ * slab's east edge pulls the first column of the east slab and the east slab's west edge
+ * pulls the last column of the west slab (streaming across the cut, Eq. streaming; both
+ * read the same time level, as the undivided grid does). The pair needs the same ny and
+ * y edges, the same steps done and admitted (they step together in every run) and the
+ * same storage (one batch). With lbm_params.x_origin set to each slab's first global
+ * column, the slabs reproduce the undivided grid bit for bit (tested); each reports the
+ * force on its part of a body. Linking a domain to itself in both directions is the
+ * periodic edge. Evicting a slab restores its partner's own edge rule. LBM_EINVAL if the
+ * domains do not match or an edge is linked already. No counterpart in the paper. */
+LBM_API lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t east_slot);
 
 /* Free a slot and its device memory. */
 LBM_API lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot);

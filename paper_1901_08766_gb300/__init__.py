@@ -223,6 +223,10 @@ class Batch:
     def set_steps_done(self, slot: int, steps: int):
         check(load().lbm_batch_set_steps_done(self._h, slot, int(steps)), "lbm_batch_set_steps_done")
 
+    def link_x(self, west_slot: int, east_slot: int):
+        """Link two resident slabs of one grid across their x edges (see slabs.py)."""
+        check(load().lbm_batch_link_x(self._h, int(west_slot), int(east_slot)), "lbm_batch_link_x")
+
     def mask(self, slot: int) -> np.ndarray:
         nx, ny, nb, cap = self._meta[slot]
         out = np.zeros((ny, nx), dtype=np.uint8)

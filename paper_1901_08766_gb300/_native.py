@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("u0_x", C.c_double), ("u0_y", C.c_double), ("west", C.c_int32),
                 ("east", C.c_int32), ("south", C.c_int32), ("north", C.c_int32),
                 ("storage", C.c_int32), ("force_every", C.c_int32),
-                ("force_capacity", C.c_int32), ("moving", C.c_int32)]
+                ("force_capacity", C.c_int32), ("moving", C.c_int32), ("x_origin", C.c_int32)]
 
 
 class Body(C.Structure):
@@ -90,6 +90,7 @@ SIGNATURES = {
     "lbm_batch_get_populations": (C.c_int, [_VP, _I32, _VP, _SZ]),
     "lbm_batch_set_populations": (C.c_int, [_VP, _I32, _VP, _SZ]),
     "lbm_batch_steps_done": (C.c_int, [_VP, _I32, C.POINTER(_I64)]),
+    "lbm_batch_link_x": (C.c_int, [_VP, _I32, _I32]),
     "lbm_batch_set_steps_done": (C.c_int, [_VP, _I32, _I64]),
     "lbm_batch_profile": (C.c_int, [_VP, _I32, _DP, _DP, C.POINTER(_I64)]),
     "lbm_batch_evict": (C.c_int, [_VP, _I32]),
@@ -142,7 +143,8 @@ def params_from_spec(spec, storage: str, force_every: int = 1, force_capacity: i
     return Params(spec["nx"], spec["ny"], spec["nu"], 0.0, spec["magic_lambda"], spec["eta"],
                   spec["rho0"], spec["u_in"][0], spec["u_in"][1], spec["u0"][0], spec["u0"][1],
                   EDGE[e["west"]], EDGE[e["east"]], EDGE[e["south"]], EDGE[e["north"]],
-                  STORAGE[storage], force_every, force_capacity, 1 if spec.get("moving") else 0)
+                  STORAGE[storage], force_every, force_capacity, 1 if spec.get("moving") else 0,
+                  int(spec.get("x_origin", 0)))
 
 
 def bodies_from_spec(spec):

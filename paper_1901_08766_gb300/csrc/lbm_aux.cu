@@ -41,22 +41,22 @@ __device__ __forceinline__ bool inside(const ShapeDev &s, double x, double y) {
 }
 
 __global__ void rasterize_kernel(uint8_t *mask, int nx, int ny, int pitch,
-                                 const ShapeDev *shapes, int nshapes) {
+                                 const ShapeDev *shapes, int nshapes, int x0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= pitch || j >= ny) return;
   uint8_t b = 0;
   if (i < nx) {
     for (int k = 0; k < nshapes; ++k)
-      if (inside(shapes[k], double(i), double(j))) b = static_cast<uint8_t>(shapes[k].body);
+      if (inside(shapes[k], double(i + x0), double(j))) b = static_cast<uint8_t>(shapes[k].body);
   }
   mask[static_cast<size_t>(j) * pitch + i] = b;
 }
 
 cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
-                             const ShapeDev *shapes, int nshapes) {
+                             const ShapeDev *shapes, int nshapes, int x0) {
   dim3 grid((pitch + 255) / 256, ny);
-  rasterize_kernel<<<grid, 256, 0, st>>>(mask, nx, ny, pitch, shapes, nshapes);
+  rasterize_kernel<<<grid, 256, 0, st>>>(mask, nx, ny, pitch, shapes, nshapes, x0);
   return cudaGetLastError();
 }
 
@@ -92,7 +92,7 @@ __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0
   return s;
 }
 
-__device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int j, int &lo, int &hi) {
+__device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int x0, int j, int &lo, int &hi) {
   lo = 0;
   hi = nx - 1;
   if (s.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
@@ -103,8 +103,9 @@ __device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int j, int
     return;
   }
   // clamped in FP64 first, so that a shape far outside converts safely
-  const double dlo = fmin(fmax(floor(s.cx - reach), -1.0), double(nx));
-  const double dhi = fmin(fmax(ceil(s.cx + reach), -1.0), double(nx));
+  const double lcx = s.cx - double(x0);  // local column of the reference point
+  const double dlo = fmin(fmax(floor(lcx - reach), -1.0), double(nx));
+  const double dhi = fmin(fmax(ceil(lcx + reach), -1.0), double(nx));
   lo = max(0, static_cast<int>(dlo));
   hi = min(nx - 1, static_cast<int>(dhi));
 }
@@ -129,7 +130,7 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
     vy = float(D.bodies[5 * (s0.body - 1) + 3]);
   }
   const float fn = float(n);
-  const float cx = float(s0.cx) + vx * fn, cy = float(s0.cy) + vy * fn;
+  const float cx = (float(s0.cx) - float(D.x0)) + vx * fn, cy = float(s0.cy) + vy * fn;
   const float reach = float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 2.0f;
   if (!(fabsf(float(j) - cy) <= reach)) {
     lo = 1;
@@ -164,7 +165,7 @@ __device__ void write_ids(const DomDev &D, int j, int c0, int c1, int lane, cons
     uint8_t id = 0;
     if (i < D.nx)
       for (int k = 0; k < D.nshapes; ++k)
-        if (i >= rs[k].lo && i <= rs[k].hi && inside_fast(rs[k].s, i, j))
+        if (i >= rs[k].lo && i <= rs[k].hi && inside_fast(rs[k].s, i + D.x0, j))
           id = static_cast<uint8_t>(rs[k].s.body);
     row[i] = id;
   }
@@ -174,7 +175,7 @@ __device__ void write_ids(const DomDev &D, int j, int c0, int c1, int lane, cons
 __device__ void place_row(const DomDev &D, int j, long long n, int lane, RowShape *rs) {
   for (int k = lane; k < D.nshapes; k += 32) {
     rs[k].s = shape_at(D, D.shapes[k], n);
-    shape_cols(rs[k].s, D.nx, j, rs[k].lo, rs[k].hi);
+    shape_cols(rs[k].s, D.nx, D.x0, j, rs[k].lo, rs[k].hi);
   }
   __syncwarp();
   write_ids(D, j, 0, D.pitch - 1, lane, rs);

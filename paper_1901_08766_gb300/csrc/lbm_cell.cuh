@@ -360,7 +360,7 @@ __device__ __forceinline__ void body_velocity<double>(const DomDev &d, int b, in
   const double cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
                om = __ldg(bd + 4);
   uox = __dsub_rn(vx, __dmul_rn(om, __dsub_rn(double(j), cy)));
-  uoy = __dadd_rn(vy, __dmul_rn(om, __dsub_rn(double(i), cx)));
+  uoy = __dadd_rn(vy, __dmul_rn(om, __dsub_rn(double(i + d.x0), cx)));  // global column
 }
 
 template <>
@@ -370,7 +370,7 @@ __device__ __forceinline__ void body_velocity<float>(const DomDev &d, int b, int
   const float cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
               om = __ldg(bd + 4);
   uox = vx - om * (float(j) - cy);
-  uoy = vy + om * (float(i) - cx);
+  uoy = vy + om * (float(i + d.x0) - cx);
 }
 
 // Scalar pull of direction a at node (i, j) with the edge rules (Eq. streaming):
@@ -382,11 +382,28 @@ __device__ __forceinline__ typename Codec<S>::T pull_scalar(const DomDev &d, con
   using Cd = Codec<S>;
   using E = typename Cd::E;
   int sx = i - ex_of(a), sy = j - ey_of(a), src = a;
+  // a NEIGHBOR edge reads the adjacent column of the linked domain's lattice (the same
+  // lattice index: linked domains step together)
+  const void *from = lat;
+  int pitch = d.pitch;
+  const int par = lat == d.lat[1] ? 1 : 0;
   if (sx < 0) {
     if (d.west == LBM_INLET_EQ) return cell_const<typename Cd::T>(d).ghost[a];
-    sx += d.nx;
+    if (d.west == LBM_NEIGHBOR) {
+      from = d.nb_lat[0][par];
+      pitch = d.nb_pitch[0];
+      sx = d.nb_nx[0] - 1;
+    } else {
+      sx += d.nx;
+    }
   } else if (sx > d.nx - 1) {
-    sx = (d.east == LBM_OUTFLOW_ZG) ? d.nx - 1 : sx - d.nx;
+    if (d.east == LBM_NEIGHBOR) {
+      from = d.nb_lat[1][par];
+      pitch = d.nb_pitch[1];
+      sx = 0;
+    } else {
+      sx = (d.east == LBM_OUTFLOW_ZG) ? d.nx - 1 : sx - d.nx;
+    }
   }
   if (sy < 0) {
     if (d.south == LBM_FREE_SLIP) { sy = 0; src = reflect_y(a); }
@@ -395,8 +412,8 @@ __device__ __forceinline__ typename Codec<S>::T pull_scalar(const DomDev &d, con
     if (d.north == LBM_FREE_SLIP) { sy = d.ny - 1; src = reflect_y(a); }
     else sy -= d.ny;
   }
-  const E *p = static_cast<const E *>(lat);
-  typename Cd::T x = Cd::dec(p[(static_cast<size_t>(src) * d.ny + sy) * d.pitch + sx]);
+  const E *p = static_cast<const E *>(from);
+  typename Cd::T x = Cd::dec(p[(static_cast<size_t>(src) * d.ny + sy) * pitch + sx]);
   if (Cd::kShiftCompute && !Cd::kStoreShifted) x -= shift_of(cell_const<typename Cd::T>(d), a);
   return x;
 }

@@ -63,6 +63,11 @@ struct DomDev {
   const double *centre0;    // [nbodies][2] reference centres
   double *rowsum;           // [ny][nbodies][3] per-row sums of -F_VP and the step they belong to
   int32_t nshapes, moving;
+  // slab decomposition: global column of local column 0, and the lattices of linked
+  // neighbour domains ([0] west, [1] east; used where the edge is LBM_NEIGHBOR)
+  int32_t x0;
+  int32_t nb_nx[2], nb_pitch[2];
+  void *nb_lat[2][2];  // [side][lattice A/B]
 };
 
 // Per-domain dynamic state, uploaded at the start of each batch run.
@@ -124,7 +129,7 @@ cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const Dom
 // the mask and body centres of one moving domain at step index n
 cudaError_t launch_place(cudaStream_t st, const DomDev *dom_dev, int nx, int ny, int pitch, long long n);
 cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
-                             const ShapeDev *shapes, int nshapes);
+                             const ShapeDev *shapes, int nshapes, int x0);
 cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,
                         double rho0, double ux, double uy);
 cudaError_t launch_row_counts(cudaStream_t st, const uint8_t *mask, int nx, int ny, int pitch,

@@ -136,6 +136,8 @@ lbm_status validate(const lbm_params *p, int nbodies) {
   if (nbodies < 0 || nbodies > kMaxBodies) return fail(LBM_EINVAL, "nbodies must be in [0, 255]");
   if (p->force_every < 0 || p->force_capacity < 0) return fail(LBM_EINVAL, "force_every/capacity must be >= 0");
   if (p->moving != 0 && p->moving != 1) return fail(LBM_EINVAL, "moving must be 0 or 1");
+  if ((p->storage == LBM_F16S || p->storage == LBM_BF16S) && p->x_origin % 8 != 0)
+    return fail(LBM_EINVAL, "16-bit storage needs x_origin divisible by 8 (rounding bits are keyed by 8-column groups)");
   if (p->moving && nbodies > kMaxMovingBodies)
     return fail(LBM_EINVAL, "a moving domain has at most %d bodies", kMaxMovingBodies);
   return LBM_OK;
@@ -154,6 +156,7 @@ struct Slot {
   void *solid = nullptr;
   size_t bytes = 0;
   std::vector<int32_t> solid_off;  // host copy of the per-body offsets into the solid list
+  int link_west = -1, link_east = -1;  // slots linked across the x edges (-1: none)
   DomDev dev{};
 };
 
@@ -595,6 +598,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.ring = reinterpret_cast<double *>(base + L.ring_off);
   D.status = reinterpret_cast<int32_t *>(base + L.status_off);
   D.moving = p->moving;
+  D.x0 = p->x_origin;
   D.nshapes = p->moving ? geom->nshapes : 0;
   D.shapes = p->moving ? reinterpret_cast<const ShapeDev *>(base + L.shapes_off) : nullptr;
   D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
@@ -670,7 +674,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
                               : reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + counts_bytes + offs_bytes);
     ADM_CUDA(cudaMemcpyAsync(dsh, shapes.data(), sizeof(ShapeDev) * ns, cudaMemcpyHostToDevice, st));
     // a moving domain is placed at its step index below, once its body table is resident
-    if (!p->moving) ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns));
+    if (!p->moving) ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns, p->x_origin));
   }
   // body table
   std::vector<double> hb(5 * std::max(1, nbodies), 0.0);
@@ -1102,10 +1106,56 @@ lbm_status lbm_batch_profile(lbm_batch *b, int32_t steps, double *sweep_us, doub
   return rc;
 }
 
+lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t east_slot) {
+  lbm_status rc = check_slot(b, west_slot);
+  if (rc == LBM_OK) rc = check_slot(b, east_slot);
+  if (rc != LBM_OK) return rc;
+  Slot &A = b->slots[west_slot];
+  Slot &B = b->slots[east_slot];
+  if (A.p.ny != B.p.ny) return fail(LBM_EINVAL, "linked domains need the same ny (%d, %d)", A.p.ny, B.p.ny);
+  if (A.p.south != B.p.south || A.p.north != B.p.north)
+    return fail(LBM_EINVAL, "linked domains need the same y edges");
+  if (A.done != B.done || A.target != B.target || A.parity != B.parity)
+    return fail(LBM_EINVAL, "linked domains must step together (same steps done and admitted)");
+  if (A.link_east >= 0 || B.link_west >= 0) return fail(LBM_EINVAL, "an edge is linked already");
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  // A's east edge pulls B's first column; B's west edge pulls A's last column
+  A.dev.east = LBM_NEIGHBOR;
+  A.dev.nb_nx[1] = B.p.nx;
+  A.dev.nb_pitch[1] = B.pitch;
+  A.dev.nb_lat[1][0] = B.dev.lat[0];
+  A.dev.nb_lat[1][1] = B.dev.lat[1];
+  B.dev.west = LBM_NEIGHBOR;
+  B.dev.nb_nx[0] = A.p.nx;
+  B.dev.nb_pitch[0] = A.pitch;
+  B.dev.nb_lat[0][0] = A.dev.lat[0];
+  B.dev.nb_lat[0][1] = A.dev.lat[1];
+  A.link_east = east_slot;
+  B.link_west = west_slot;
+  LBM_CUDA(cudaMemcpyAsync(b->d_doms + west_slot, &A.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaMemcpyAsync(b->d_doms + east_slot, &B.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot) {
   lbm_status rc = check_slot(b, slot);
   if (rc != LBM_OK) return rc;
   Slot &s = b->slots[slot];
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  // a linked partner gets its own edge rule back
+  if (s.link_west >= 0) {
+    Slot &P = b->slots[s.link_west];
+    P.dev.east = P.p.east;
+    P.link_east = -1;
+    LBM_CUDA(cudaMemcpyAsync(b->d_doms + s.link_west, &P.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  }
+  if (s.link_east >= 0) {
+    Slot &P = b->slots[s.link_east];
+    P.dev.west = P.p.west;
+    P.link_west = -1;
+    LBM_CUDA(cudaMemcpyAsync(b->d_doms + s.link_east, &P.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  }
   LBM_CUDA(cudaStreamSynchronize(b->st));
   b->al.put(s.block);
   b->al.put(s.solid);

@@ -273,9 +273,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
     if constexpr (sizeof(E) == 2) CP = pair_const(CF);
     const uint8_t *__restrict__ dmask = D.mask;
     T *__restrict__ dfvp = static_cast<T *>(D.fvp);
-    // strip-end columns read by the end lanes (or -1: nothing to read)
-    const int col_left = west_edge ? (west_inlet ? -1 : nx - 1) : x0 - 1;
-    const int col_right = east_edge ? (east_out ? -1 : 0) : x0 + kStrip;
+    // strip-end columns read by the end lanes (or -1: nothing to read); at a linked
+    // (NEIGHBOR) edge the value comes from the neighbour's lattice instead (below)
+    const bool west_link = west_edge && D.west == LBM_NEIGHBOR;
+    const bool east_link = east_edge && D.east == LBM_NEIGHBOR;
+    const int col_left = west_edge ? ((west_inlet || west_link) ? -1 : nx - 1) : x0 - 1;
+    const int col_right = east_edge ? ((east_out || east_link) ? -1 : 0) : x0 + kStrip;
     // the lane holding column nx-1 (east edge tiles) and its element index
     const int k_last = nx - 1 - xl;
     const bool has_last = east_edge && k_last >= 0 && k_last < V;
@@ -320,6 +323,28 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
         end_in[a] = E(0);
         if (ex == 1) end_in[a] = __ldg(row[a] + col_l);
         else if (ex == -1) end_in[a] = __ldg(row[a] + col_r);
+      }
+      if (west_link || east_link) {
+        // linked edge: the adjacent column of the neighbour (its last column to the west,
+        // its first to the east), same direction and y rule, same lattice index
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+          const int ex = ex_of(a);
+          const int side = ex == 1 ? 0 : 1;
+          if (ex == 0 || (ex == 1 && !west_link) || (ex == -1 && !east_link)) continue;
+          int sy = j - ey_of(a), sa = a;
+          if (sy < 0) {
+            if (south_slip) { sy = 0; sa = reflect_y(a); }
+            else sy += ny;
+          } else if (sy > ny - 1) {
+            if (north_slip) { sy = ny - 1; sa = reflect_y(a); }
+            else sy -= ny;
+          }
+          const int npitch = D.nb_pitch[side];
+          const E *nrow = static_cast<const E *>(D.nb_lat[side][par]) +
+                          (static_cast<size_t>(sa) * ny + sy) * npitch;
+          end_in[a] = __ldg(nrow + (side == 0 ? D.nb_nx[0] - 1 : 0));
+        }
       }
       {
         // body ids, kept packed (zero for lanes past the end of the row)
@@ -384,7 +409,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
                     : (1u << V) - 1u;
       unsigned bad_bits = 0u;
       // random bits of the 16-bit rounding (a strip of V <= 8 cells lies in one group)
-      const uint32_t sr_g = sizeof(E) == 2 ? sr_group_bits(sr_row_key(n, j), xl) : 0u;
+      // (keyed by the global column: slabs of one grid round as the whole grid does)
+      const uint32_t sr_g = sizeof(E) == 2 ? sr_group_bits(sr_row_key(n, j), xl + D.x0) : 0u;
       // one node: inlet ghost, moments, penalization, collision, F_VP, stability check
       auto update = [&](T (&x)[kQ], int k) {
         if (k == 0 && west_edge && west_inlet) {
@@ -438,7 +464,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
             bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
             bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (k + 1);
             // each opposite pair is rounded as soon as the collision finishes it
-            PairEncoder<S> enc(sr_pair_bits(sr_g, xl + k));
+            PairEncoder<S> enc(sr_pair_bits(sr_g, xl + k + D.x0));
             collide<F2, SHIFT, false>(x, m, CP, enc);
             enc.finish(m.d);
 #pragma unroll
@@ -460,7 +486,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
 #pragma unroll
             for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0[a], x1[a]));
             uint32_t w[kQ];
-            encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + k), w);
+            encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + k + D.x0), w);
 #pragma unroll
             for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
           }

@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
     const unsigned char *sb = wbase + st * G::kStageBytes;
 
     // row pointers are needed only for the periodic strip ends at the domain edges
-    auto edge_row = [&](int a) -> const E * {
+    // (side 0 / 1: the west / east linked neighbour's lattice, same lattice index)
+    auto edge_row = [&](int a, int side = -1) -> const E * {
       const int ey = ey_of(a);
       int sy = j - ey, sa = a;
       if (sy < 0) {
@@ -212,6 +213,9 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         if (D.north == LBM_FREE_SLIP) { sy = ny - 1; sa = reflect_y(a); }
         else sy -= ny;
       }
+      if (side >= 0)
+        return static_cast<const E *>(D.nb_lat[side][par]) +
+               (static_cast<size_t>(sa) * ny + sy) * D.nb_pitch[side];
       return src + sa * plane + static_cast<size_t>(sy) * pitch;
     };
 
@@ -248,6 +252,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         E in = shfl_up1<E>(v[a].last());
         if (lane == 0) {
           if (!west_edge) in = seg[H - 1];
+          else if (D.west == LBM_NEIGHBOR) in = __ldg(edge_row(a, 0) + D.nb_nx[0] - 1);  // linked
           else if (!west_inlet) in = __ldg(edge_row(a) + nx - 1);  // periodic
           else in = E(0);  // inlet: replaced by the ghost after decoding
         }
@@ -263,7 +268,8 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         if (lane == 31 && !east_edge) in = seg[H + kStrip];
         v[a].shift_down(in);
         if (has_last) {
-          const E fix = east_out ? keep : __ldg(edge_row(a));  // zero gradient or periodic
+          // zero gradient, linked neighbour or periodic
+          const E fix = east_out ? keep : __ldg(D.east == LBM_NEIGHBOR ? edge_row(a, 1) : edge_row(a));
 #pragma unroll
           for (int k = 0; k < V; ++k)
             if (k == k_last) v[a].set(k, fix);
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
 #pragma unroll
         for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0v[a], x1v[a]));
         uint32_t w[kQ];
-        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_group_bits(sr_row_key(dy.step0 + run_base + s, j), xl), xl + k), w);
+        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_group_bits(sr_row_key(dy.step0 + run_base + s, j), xl + D.x0), xl + k + D.x0), w);
 #pragma unroll
         for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
       }
