@@ -1,0 +1,206 @@
+"""FP64 CPU oracle of the TRT-LBM-VP method in 3D (D3Q19) — TEST INFRASTRUCTURE.
+
+The arithmetic lives in ``lbm_oracle3d.c`` (plain C, FP64, one node at a time); this
+module builds it with gcc and marshals numpy arrays. Only the tests and the benchmark's
+CPU baseline use it; the CUDA library never does. Pinned by tests/test_oracle3d_pins.py.
+
+Spec of a 3D case: nx, ny, nz, nu, magic_lambda, eta, rho0, u_in (3), u0 (3), edges
+{west, east, south, north, bottom, top}, shapes [{kind: sphere | cylinder_z, body,
+c (3), radius}], bodies [{c, v, w (3 each), ref_length}].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(_HERE, "lbm_oracle3d.c")
+_DEFAULT_LIB = os.path.join(_HERE, "_build", "liboracle3d.so")
+_LIB = _DEFAULT_LIB
+_lock = threading.Lock()
+_lib = None
+
+EDGE = {"periodic": 0, "inlet": 1, "outflow": 2, "free_slip": 3}
+SHAPE = {"sphere": 0, "cylinder_z": 1}
+
+
+class _Params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nu", C.c_double),
+                ("magic_lambda", C.c_double), ("eta", C.c_double), ("rho0", C.c_double),
+                ("u_in", C.c_double * 3), ("west", C.c_int32), ("east", C.c_int32),
+                ("south", C.c_int32), ("north", C.c_int32), ("bottom", C.c_int32),
+                ("top", C.c_int32)]
+
+
+class _Body(C.Structure):
+    _fields_ = [("c", C.c_double * 3), ("v", C.c_double * 3), ("w", C.c_double * 3)]
+
+
+class _Shape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("body", C.c_int32), ("c", C.c_double * 3),
+                ("radius", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    with _lock:
+        if not force and os.path.exists(_LIB) and (
+                _LIB != _DEFAULT_LIB or os.path.getmtime(_LIB) >= os.path.getmtime(SRC)):
+            return _LIB
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-std=c11", "-fopenmp", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        u8p = C.POINTER(C.c_uint8)
+        i32p = C.POINTER(C.c_int32)
+        P, B, S = C.POINTER(_Params), C.POINTER(_Body), C.POINTER(_Shape)
+        L.ora3_tau_s.restype = C.c_double
+        L.ora3_tau_s.argtypes = [P]
+        L.ora3_tau_a.restype = C.c_double
+        L.ora3_tau_a.argtypes = [P]
+        L.ora3_equilibrium.argtypes = [C.c_double, dp, dp]
+        L.ora3_guo.argtypes = [dp, dp, dp]
+        L.ora3_rasterize.argtypes = [C.c_int32, C.c_int32, C.c_int32, S, C.c_int32, u8p]
+        L.ora3_stream.argtypes = [P, dp, dp]
+        L.ora3_step_trt.argtypes = [P, u8p, B, C.c_int32, dp, dp, dp]
+        L.ora3_run.restype = C.c_int
+        L.ora3_run.argtypes = [P, u8p, B, C.c_int32, dp, C.c_int64, dp]
+        L.ora3_init.argtypes = [P, dp, dp]
+        L.ora3_moments.argtypes = [P, u8p, B, dp, dp, dp, dp, dp]
+        L.ora3_lattice.argtypes = [i32p, i32p, i32p, dp, i32p]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _u8(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def _vec(x):
+    return (C.c_double * 3)(*[float(v) for v in x])
+
+
+def lattice():
+    """(EX, EY, EZ, W, OPP) of the oracle's D3Q19 velocity set."""
+    ex, ey, ez, opp = (np.zeros(19, dtype=np.int32) for _ in range(4))
+    w = np.zeros(19)
+    i32 = C.POINTER(C.c_int32)
+    lib().ora3_lattice(ex.ctypes.data_as(i32), ey.ctypes.data_as(i32), ez.ctypes.data_as(i32),
+                       _dp(w), opp.ctypes.data_as(i32))
+    return ex, ey, ez, w, opp
+
+
+def params_of(spec) -> _Params:
+    e = spec["edges"]
+    return _Params(spec["nx"], spec["ny"], spec["nz"], spec["nu"], spec["magic_lambda"],
+                   spec["eta"], spec["rho0"], _vec(spec["u_in"]), EDGE[e["west"]],
+                   EDGE[e["east"]], EDGE[e["south"]], EDGE[e["north"]], EDGE[e["bottom"]],
+                   EDGE[e["top"]])
+
+
+def _shapes_of(spec):
+    shp = spec["shapes"]
+    arr = (_Shape * max(1, len(shp)))()
+    for k, s in enumerate(shp):
+        arr[k] = _Shape(SHAPE[s["kind"]], s["body"], _vec(s["c"]), s["radius"])
+    return arr, len(shp)
+
+
+def _bodies_of(spec):
+    bs = spec["bodies"]
+    arr = (_Body * max(1, len(bs)))()
+    for k, b in enumerate(bs):
+        arr[k] = _Body(_vec(b["c"]), _vec(b["v"]), _vec(b["w"]))
+    return arr, len(bs)
+
+
+def tau_s(spec):
+    return lib().ora3_tau_s(C.byref(params_of(spec)))
+
+
+def equilibrium(rho, u):
+    out = np.zeros(19)
+    lib().ora3_equilibrium(rho, _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
+    return out
+
+
+def guo(u, F):
+    out = np.zeros(19)
+    lib().ora3_guo(_dp(np.ascontiguousarray(u, dtype=np.float64)),
+                   _dp(np.ascontiguousarray(F, dtype=np.float64)), _dp(out))
+    return out
+
+
+def rasterize(spec):
+    """Body-id mask uint8 [nz, ny, nx]."""
+    m = np.zeros((spec["nz"], spec["ny"], spec["nx"]), dtype=np.uint8)
+    arr, n = _shapes_of(spec)
+    lib().ora3_rasterize(spec["nx"], spec["ny"], spec["nz"], arr, n, _u8(m))
+    return m
+
+
+def stream(spec, g):
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    f = np.zeros_like(g)
+    lib().ora3_stream(C.byref(params_of(spec)), _dp(g), _dp(f))
+    return f
+
+
+class Domain:
+    """One 3D simulation: post-collision populations g [19, nz, ny, nx] in FP64."""
+
+    def __init__(self, spec, mask=None, g=None):
+        self.spec = spec
+        self.p = params_of(spec)
+        self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask, dtype=np.uint8)
+        self.bodies, self.nb = _bodies_of(spec)
+        shape = (19, spec["nz"], spec["ny"], spec["nx"])
+        if g is None:
+            self.g = np.zeros(shape)
+            lib().ora3_init(C.byref(self.p), _dp(np.asarray(spec["u0"], dtype=np.float64)), _dp(self.g))
+        else:
+            self.g = np.ascontiguousarray(g, dtype=np.float64).copy()
+        self.steps_done = 0
+
+    def run(self, n: int, want_forces: bool = True):
+        """Advance n steps; the force on each body per step, [n, nbodies, 3]."""
+        forces = np.zeros((n, max(self.nb, 1), 3)) if want_forces else None
+        rc = lib().ora3_run(C.byref(self.p), _u8(self.mask), self.bodies, self.nb, _dp(self.g), n,
+                            _dp(forces) if want_forces else None)
+        if rc != 0:
+            raise MemoryError("oracle run failed to allocate")
+        self.steps_done += n
+        return forces[:, : self.nb] if want_forces else None
+
+    def step_once(self):
+        out = np.zeros_like(self.g)
+        fb = np.zeros((max(self.nb, 1), 3))
+        lib().ora3_step_trt(C.byref(self.p), _u8(self.mask), self.bodies, self.nb, _dp(self.g),
+                            _dp(out), _dp(fb))
+        self.g = out
+        self.steps_done += 1
+        return out, fb[: self.nb]
+
+    def moments(self):
+        shp = (self.spec["nz"], self.spec["ny"], self.spec["nx"])
+        rho, ux, uy, uz = (np.zeros(shp) for _ in range(4))
+        lib().ora3_moments(C.byref(self.p), _u8(self.mask), self.bodies, _dp(self.g), _dp(rho),
+                           _dp(ux), _dp(uy), _dp(uz))
+        return rho, ux, uy, uz

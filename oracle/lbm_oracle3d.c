@@ -1,0 +1,273 @@
+/*
+ * Plain FP64 CPU oracle of the TRT-LBM-VP method in 3D with the D3Q19 lattice (the
+ * paper's closing remark: the method extends to 3D by replacing D2Q9 with D3Q15 or
+ * D3Q19; everything else is the 2D algorithm of Sec. 2.2 written for three axes).
+ * TEST INFRASTRUCTURE ONLY, like lbm_oracle.c: used by the tests and the benchmark's CPU
+ * baseline, never by the library. One node at a time, no fusion; compiled with
+ * -O2 -ffp-contract=off.
+ *
+ * D3Q19 (readings listed in the design notes): e_0 = 0; e_1..6 = +-x, +-y, +-z; e_7..18
+ * the twelve face diagonals; opposite directions come in pairs (2m-1, 2m); weights 1/3,
+ * 1/18, 1/36; c_s^2 = 1/3. f^eq and the Guo term have the 2D form with three components.
+ * Edges: x periodic or equilibrium inlet (west) / zero-gradient outflow (east); y and z
+ * periodic or free slip (specular: e_y or e_z reversed); rules applied x, then y, then z.
+ * U_O = V + omega x (x - c) with an angular velocity vector.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q3 19
+
+static const int EX3[Q3] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int EY3[Q3] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int EZ3[Q3] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+static const double W3[Q3] = {1.0 / 3.0,
+                              1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2_3 = 1.0 / 3.0;
+
+enum { O3_PERIODIC = 0, O3_INLET = 1, O3_OUTFLOW = 2, O3_FREE_SLIP = 3 };
+enum { O3_SPHERE = 0, O3_CYLINDER_Z = 1 };
+
+typedef struct {
+  int32_t nx, ny, nz;
+  double nu, magic_lambda, eta, rho0;
+  double u_in[3];
+  int32_t west, east, south, north, bottom, top;
+} ora3_params;
+
+typedef struct {
+  double c[3], v[3], w[3]; /* centre, velocity, angular velocity */
+} ora3_body;
+
+typedef struct {
+  int32_t kind, body;
+  double c[3], radius; /* sphere: centre and radius; z-cylinder: axis through (c[0], c[1]) */
+} ora3_shape;
+
+/* direction with e_y (or e_z) reversed: the specular reflection of free-slip walls */
+static int reflect3(int a, int axis) {
+  for (int b = 0; b < Q3; b++)
+    if (EX3[b] == EX3[a] && (axis == 1 ? (EY3[b] == -EY3[a] && EZ3[b] == EZ3[a])
+                                       : (EY3[b] == EY3[a] && EZ3[b] == -EZ3[a])))
+      return b;
+  return a;
+}
+
+static int opposite3(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+double ora3_tau_s(const ora3_params *p) { return p->nu / CS2_3 + 0.5; }
+double ora3_tau_a(const ora3_params *p) {
+  return 0.5 + p->magic_lambda / (ora3_tau_s(p) - 0.5);
+}
+
+/* Eq. (feq) with three velocity components */
+void ora3_equilibrium(double rho, const double *u, double *feq) {
+  double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int a = 0; a < Q3; a++) {
+    double eu = EX3[a] * u[0] + EY3[a] * u[1] + EZ3[a] * u[2];
+    feq[a] = W3[a] * rho * (1.0 + eu / CS2_3 + eu * eu / (2.0 * CS2_3 * CS2_3) - usq / (2.0 * CS2_3));
+  }
+}
+
+/* Guo term F_alpha = w_alpha [(e - u)/c_s^2 + (e.u) e / c_s^4] . F (Eq. external-force-term) */
+void ora3_guo(const double *u, const double *F, double *out) {
+  for (int a = 0; a < Q3; a++) {
+    double e[3] = {EX3[a], EY3[a], EZ3[a]};
+    double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+    double s = 0.0;
+    for (int d = 0; d < 3; d++) s += ((e[d] - u[d]) / CS2_3 + eu * e[d] / (CS2_3 * CS2_3)) * F[d];
+    out[a] = W3[a] * s;
+  }
+}
+
+static int inside3(const ora3_shape *s, double x, double y, double z) {
+  double dx = x - s->c[0], dy = y - s->c[1], dz = z - s->c[2];
+  double r2 = s->radius * s->radius;
+  if (s->kind == O3_SPHERE) return dx * dx + dy * dy + dz * dz < r2;
+  if (s->kind == O3_CYLINDER_Z) return dx * dx + dy * dy < r2;
+  return 0;
+}
+
+/* Body id per node [nz][ny][nx]; later shapes overwrite earlier ones. */
+void ora3_rasterize(int32_t nx, int32_t ny, int32_t nz, const ora3_shape *shapes, int32_t nshapes,
+                    uint8_t *mask) {
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        uint8_t b = 0;
+        for (int q = 0; q < nshapes; q++)
+          if (inside3(&shapes[q], (double)i, (double)j, (double)k)) b = (uint8_t)shapes[q].body;
+        mask[((size_t)k * ny + j) * nx + i] = b;
+      }
+}
+
+static inline size_t IDX3(const ora3_params *p, int a, int k, int j, int i) {
+  return (((size_t)a * p->nz + k) * p->ny + j) * p->nx + i;
+}
+
+/* f_alpha(i, j, k) = g_alpha(x - e_alpha) with the edge rules: x, then y, then z. */
+static double pull3(const ora3_params *p, const double *g, const double *feq_inlet, int a, int i,
+                    int j, int k) {
+  int sx = i - EX3[a], sy = j - EY3[a], sz = k - EZ3[a], src = a;
+  if (sx < 0) {
+    if (p->west == O3_INLET) return feq_inlet[a];
+    sx += p->nx;
+  } else if (sx > p->nx - 1) {
+    if (p->east == O3_OUTFLOW) sx = p->nx - 1;
+    else sx -= p->nx;
+  }
+  if (sy < 0) {
+    if (p->south == O3_FREE_SLIP) { sy = 0; src = reflect3(src, 1); }
+    else sy += p->ny;
+  } else if (sy > p->ny - 1) {
+    if (p->north == O3_FREE_SLIP) { sy = p->ny - 1; src = reflect3(src, 1); }
+    else sy -= p->ny;
+  }
+  if (sz < 0) {
+    if (p->bottom == O3_FREE_SLIP) { sz = 0; src = reflect3(src, 2); }
+    else sz += p->nz;
+  } else if (sz > p->nz - 1) {
+    if (p->top == O3_FREE_SLIP) { sz = p->nz - 1; src = reflect3(src, 2); }
+    else sz -= p->nz;
+  }
+  return g[IDX3(p, src, sz, sy, sx)];
+}
+
+void ora3_stream(const ora3_params *p, const double *g, double *f) {
+  double feq_inlet[Q3];
+  ora3_equilibrium(p->rho0, p->u_in, feq_inlet);
+  for (int a = 0; a < Q3; a++)
+    for (int k = 0; k < p->nz; k++)
+      for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) f[IDX3(p, a, k, j, i)] = pull3(p, g, feq_inlet, a, i, j, k);
+}
+
+/* U_O = V + omega x (x - c) */
+static void body_velocity3(const ora3_body *b, int i, int j, int k, double *uo) {
+  double r[3] = {(double)i - b->c[0], (double)j - b->c[1], (double)k - b->c[2]};
+  uo[0] = b->v[0] + (b->w[1] * r[2] - b->w[2] * r[1]);
+  uo[1] = b->v[1] + (b->w[2] * r[0] - b->w[0] * r[2]);
+  uo[2] = b->v[2] + (b->w[0] * r[1] - b->w[1] * r[0]);
+}
+
+/* steps (3)-(5) at one node: rho, u* (Eq. rho, Eq. rho*velocity-star), penalization
+ * (Eq. d-V, Eq. force-density), corrected velocity (Eq. velocity-r) */
+static void node3(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
+                  const double *f, int i, int j, int k, double *rho, double *u, double *fv) {
+  double r = 0.0, jm[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < Q3; a++) {
+    r += f[a];
+    jm[0] += EX3[a] * f[a];
+    jm[1] += EY3[a] * f[a];
+    jm[2] += EZ3[a] * f[a];
+  }
+  int b = mask[((size_t)k * p->ny + j) * p->nx + i];
+  double chi = b ? 1.0 : 0.0, uo[3] = {0.0, 0.0, 0.0};
+  if (b) body_velocity3(&bodies[b - 1], i, j, k, uo);
+  for (int d = 0; d < 3; d++) {
+    double us = jm[d] / r;
+    double du = chi * (uo[d] - us) / (2.0 * p->eta + chi);
+    fv[d] = 2.0 * r * chi * (uo[d] - us) / (2.0 * p->eta + chi);
+    u[d] = us + du;
+  }
+  *rho = r;
+}
+
+/* One TRT-LBM-VP step in 3D (Eq. TRT-collision, Eq. collision-modified); force[3*(b-1)+d]
+ * receives the force on body b (-sum of F_VP over its nodes, serial in index order). */
+void ora3_step_trt(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
+                   int32_t nbodies, const double *g_in, double *g_out, double *force) {
+  const double tau_s = ora3_tau_s(p), tau_a = ora3_tau_a(p);
+  double feq_inlet[Q3];
+  ora3_equilibrium(p->rho0, p->u_in, feq_inlet);
+  size_t cells = (size_t)p->nx * p->ny * p->nz;
+  double *fvall = (double *)malloc(sizeof(double) * 3 * cells);
+  if (!fvall) abort();
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < p->nz; k++)
+    for (int j = 0; j < p->ny; j++)
+      for (int i = 0; i < p->nx; i++) {
+        double f[Q3], feq[Q3], F[Q3], rho, u[3], fv[3];
+        for (int a = 0; a < Q3; a++) f[a] = pull3(p, g_in, feq_inlet, a, i, j, k);
+        node3(p, mask, bodies, f, i, j, k, &rho, u, fv);
+        ora3_equilibrium(rho, u, feq);
+        ora3_guo(u, fv, F);
+        for (int a = 0; a < Q3; a++) {
+          int o = opposite3(a);
+          double fs = 0.5 * (f[a] + f[o]), fa = 0.5 * (f[a] - f[o]);
+          double feqs = 0.5 * (feq[a] + feq[o]), feqa = 0.5 * (feq[a] - feq[o]);
+          double Fs = 0.5 * (F[a] + F[o]), Fa = 0.5 * (F[a] - F[o]);
+          double om = -(fs - feqs) / tau_s - (fa - feqa) / tau_a;
+          g_out[IDX3(p, a, k, j, i)] =
+              f[a] + om + (1.0 - 1.0 / (2.0 * tau_s)) * Fs + (1.0 - 1.0 / (2.0 * tau_a)) * Fa;
+        }
+        size_t c = ((size_t)k * p->ny + j) * p->nx + i;
+        for (int d = 0; d < 3; d++) fvall[3 * c + d] = fv[d];
+      }
+  for (int q = 0; q < 3 * nbodies; q++) force[q] = 0.0;
+  for (size_t c = 0; c < cells; c++) {
+    int b = mask[c];
+    if (b && b <= nbodies)
+      for (int d = 0; d < 3; d++) force[3 * (b - 1) + d] -= fvall[3 * c + d];
+  }
+  free(fvall);
+}
+
+int ora3_run(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies, int32_t nbodies,
+             double *g, int64_t n, double *forces) {
+  size_t cells = (size_t)p->nx * p->ny * p->nz;
+  double *tmp = (double *)malloc(sizeof(double) * Q3 * cells);
+  double *fb = (double *)malloc(sizeof(double) * 3 * (nbodies > 0 ? nbodies : 1));
+  if (!tmp || !fb) { free(tmp); free(fb); return -1; }
+  double *a = g, *b = tmp;
+  for (int64_t s = 0; s < n; s++) {
+    ora3_step_trt(p, mask, bodies, nbodies, a, b, fb);
+    if (forces) memcpy(forces + (size_t)s * 3 * nbodies, fb, sizeof(double) * 3 * nbodies);
+    double *t = a; a = b; b = t;
+  }
+  if (a != g) memcpy(g, a, sizeof(double) * Q3 * cells);
+  free(tmp);
+  free(fb);
+  return 0;
+}
+
+void ora3_init(const ora3_params *p, const double *u0, double *g) {
+  double feq[Q3];
+  ora3_equilibrium(p->rho0, u0, feq);
+  size_t cells = (size_t)p->nx * p->ny * p->nz;
+  for (int a = 0; a < Q3; a++)
+    for (size_t c = 0; c < cells; c++) g[a * cells + c] = feq[a];
+}
+
+void ora3_moments(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
+                  const double *g, double *rho, double *ux, double *uy, double *uz) {
+  double feq_inlet[Q3];
+  ora3_equilibrium(p->rho0, p->u_in, feq_inlet);
+  for (int k = 0; k < p->nz; k++)
+    for (int j = 0; j < p->ny; j++)
+      for (int i = 0; i < p->nx; i++) {
+        double f[Q3], r, u[3], fv[3];
+        for (int a = 0; a < Q3; a++) f[a] = pull3(p, g, feq_inlet, a, i, j, k);
+        node3(p, mask, bodies, f, i, j, k, &r, u, fv);
+        size_t c = ((size_t)k * p->ny + j) * p->nx + i;
+        rho[c] = r;
+        ux[c] = u[0];
+        uy[c] = u[1];
+        uz[c] = u[2];
+      }
+}
+
+/* the velocity set, for the pins */
+void ora3_lattice(int32_t *ex, int32_t *ey, int32_t *ez, double *w, int32_t *opp) {
+  for (int a = 0; a < Q3; a++) {
+    ex[a] = EX3[a];
+    ey[a] = EY3[a];
+    ez[a] = EZ3[a];
+    w[a] = W3[a];
+    opp[a] = opposite3(a);
+  }
+}

@@ -301,3 +301,59 @@ def parity_case(name: str):
 
 
 PARITY_CASES = ("periodic_97x61", "channel_97x61", "channel_256x128", "mixed_edges_61x47")
+
+
+# --------------------------------------------------------------------------------------
+# 3D (D3Q19) inputs: same conventions, nineteen directions (rest, six axis, twelve face
+# diagonals), arrays [19, nz, ny, nx].
+
+_POP_SCALE3 = np.array([0.33] + [0.055] * 6 + [0.028] * 12)
+
+
+def random_populations3(seed: int, nx: int, ny: int, nz: int, amp: float = 0.1) -> np.ndarray:
+    """Positive random populations [19, nz, ny, nx]: scale[q] * (1 + amp * (xi - 0.5)),
+    xi drawn in (q, k, j, i) order (density ~0.99, velocities of order 1e-2)."""
+    xi = SplitMix64(seed).doubles(19 * nz * ny * nx).reshape(19, nz, ny, nx)
+    return _POP_SCALE3[:, None, None, None] * (1.0 + amp * (xi - 0.5))
+
+
+def edges3(west="periodic", east="periodic", south="periodic", north="periodic",
+           bottom="periodic", top="periodic"):
+    return {"west": west, "east": east, "south": south, "north": north, "bottom": bottom,
+            "top": top}
+
+
+def channel_edges3():
+    return edges3("inlet", "outflow", "free_slip", "free_slip", "free_slip", "free_slip")
+
+
+def sphere(body, c, radius):
+    return {"kind": "sphere", "body": int(body), "c": tuple(float(v) for v in c), "radius": float(radius)}
+
+
+def cylinder_z(body, cx, cy, radius):
+    return {"kind": "cylinder_z", "body": int(body), "c": (float(cx), float(cy), 0.0),
+            "radius": float(radius)}
+
+
+def body3(c, ref_length, v=(0.0, 0.0, 0.0), w=(0.0, 0.0, 0.0)):
+    return {"c": tuple(float(x) for x in c), "v": tuple(float(x) for x in v),
+            "w": tuple(float(x) for x in w), "ref_length": float(ref_length)}
+
+
+def spec3(name, nx, ny, nz, nu, shapes, bodies, steps, U, edges, u_in=(0.0, 0.0, 0.0),
+          u0=(0.0, 0.0, 0.0), magic_lambda=3.0 / 16.0, eta=1e-4, rho0=1.0):
+    return {"name": name, "nx": int(nx), "ny": int(ny), "nz": int(nz), "nu": float(nu),
+            "magic_lambda": float(magic_lambda), "eta": float(eta), "rho0": float(rho0),
+            "u_in": tuple(float(v) for v in u_in), "u0": tuple(float(v) for v in u0),
+            "edges": edges, "shapes": shapes, "bodies": bodies, "steps": int(steps), "U": float(U)}
+
+
+def sphere_channel(nx=384, ny=128, nz=128, D=32.0, U=0.05, re=100.0, steps=20000):
+    """Flow past a sphere in a channel (uniform inflow, zero-gradient outflow, free-slip
+    walls): the 3D counterpart of the single-cylinder case, sphere centre off the axes
+    by half a cell."""
+    nu = U * D / re
+    c = (nx / 4.0, ny / 2.0 + 0.5, nz / 2.0 + 0.5)
+    return spec3(f"sphere_{nx}x{ny}x{nz}_re{re:g}", nx, ny, nz, nu, [sphere(1, c, D / 2)],
+                 [body3(c, D)], steps, U, channel_edges3(), u_in=(U, 0.0, 0.0), u0=(U, 0.0, 0.0))

@@ -1,0 +1,86 @@
+"""The 3D oracle's pins are sensitive: each plausible mistake planted in a copy of
+lbm_oracle3d.c (a wrong table entry, weight, term, sign or index) makes at least one pin
+of tests/test_oracle3d_pins.py fail. CPU only; the committed oracle is never modified."""
+import os
+import subprocess
+import warnings
+
+import pytest
+
+import test_oracle3d_pins as pins
+import synth
+from oracle import d3q19 as d3
+
+MUTATIONS = [
+    ("ex_entry", "static const int EX3[Q3] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1,",
+     "static const int EX3[Q3] = {0, 1, -1, 0, 0, 0, 0, 1, -1, -1, -1,"),
+    ("weight_diag", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 30.0};"),
+    ("opposite", "((a & 1) ? a + 1 : a - 1)", "((a & 1) ? a + 1 : a)"),
+    ("feq_quadratic", "eu * eu / (2.0 * CS2_3 * CS2_3)", "eu * eu / (CS2_3 * CS2_3)"),
+    ("guo_drop_u", "((e[d] - u[d]) / CS2_3", "((e[d]) / CS2_3"),
+    ("reflect_axis", "(EY3[b] == -EY3[a] && EZ3[b] == EZ3[a])", "(EY3[b] == EY3[a] && EZ3[b] == EZ3[a])"),
+    ("tau_s_half", "return p->nu / CS2_3 + 0.5;", "return p->nu / CS2_3 + 0.6;"),
+    ("du_sign", "double du = chi * (uo[d] - us)", "double du = chi * (us - uo[d])"),
+    ("force_sign", "force[3 * (b - 1) + d] -= fvall[3 * c + d];", "force[3 * (b - 1) + d] += fvall[3 * c + d];"),
+    ("pull_direction", "int sx = i - EX3[a]", "int sx = i + EX3[a]"),
+    ("rotation_sign", "uo[0] = b->v[0] + (b->w[1] * r[2] - b->w[2] * r[1]);",
+     "uo[0] = b->v[0] + (b->w[2] * r[1] - b->w[1] * r[2]);"),
+    ("sphere_strict", "return dx * dx + dy * dy + dz * dz < r2;", "return dx * dx + dy * dy + dz * dz <= r2;"),
+    ("antisym_factor", "(1.0 - 1.0 / (2.0 * tau_a)) * Fa", "(1.0 - 1.0 / (2.0 * tau_s)) * Fa"),
+    ("outflow_column", "if (p->east == O3_OUTFLOW) sx = p->nx - 1;", "if (p->east == O3_OUTFLOW) sx = p->nx - 2;"),
+    ("inlet_ghost", "if (p->west == O3_INLET) return feq_inlet[a];", "if (p->west == O3_INLET) return feq_inlet[opposite3(a)];"),
+    ("corrected_velocity", "u[d] = us + du;", "u[d] = us;"),
+]
+
+PINS = [
+    pins.test_d3q19_velocity_set_and_isotropy,
+    lambda: pins.test_equilibrium_moments(0.97, (0.05, -0.03, 0.02)),
+    pins.test_guo_term_moments,
+    pins.test_rasterize_brute_force,
+    pins.test_stream_periodic_is_a_roll_and_mirrors,
+    pins.test_stream_inlet_outflow_columns,
+    pins.test_rotating_penalized_box_follows_the_body_velocity,
+    lambda: [pins.test_uniform_flow_invariant(e) for e in (synth.edges3(), synth.channel_edges3())],
+    pins.test_mass_and_momentum_balance_with_bodies,
+    pins.test_fully_penalized_box_closed_form,
+    lambda: pins.test_shear_wave_decay_rate(0.1, 3 / 16),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle3d_mutants")
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(name, old, new, workdir):
+    src = open(d3.SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    c_path = os.path.join(workdir, f"{name}.c")
+    so_path = os.path.join(workdir, f"{name}.so")
+    open(c_path, "w").write(src.replace(old, new, 1))
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                           "-fopenmp", "-o", so_path, c_path, "-lm"])
+    saved_lib, saved_path = d3._lib, d3._LIB
+    try:
+        d3._lib = None
+        d3._LIB = so_path
+        ex, ey, ez, w, opp = d3.lattice()
+        pins.EX, pins.EY, pins.EZ, pins.W, pins.OPP = ex, ey, ez, w, opp
+        pins.E = pins.np.stack([ex, ey, ez], axis=1).astype(float)
+        caught = None
+        for k, pin in enumerate(PINS):
+            try:
+                with warnings.catch_warnings():
+                    warnings.simplefilter("ignore")
+                    pin()
+            except (AssertionError, FloatingPointError, ValueError, ZeroDivisionError,
+                    OverflowError, IndexError):
+                caught = k
+                break
+        assert caught is not None, f"planted mistake {name} passed every pin"
+    finally:
+        d3._lib, d3._LIB = saved_lib, saved_path
+        ex, ey, ez, w, opp = d3.lattice()
+        pins.EX, pins.EY, pins.EZ, pins.W, pins.OPP = ex, ey, ez, w, opp
+        pins.E = pins.np.stack([ex, ey, ez], axis=1).astype(float)
