@@ -307,6 +307,86 @@ LBM_API lbm_status lbm_batch_info(lbm_batch *b, int32_t *resident, int64_t *cell
 
 LBM_API lbm_status lbm_batch_destroy(lbm_batch *b);
 
+/* ---- 3D: D3Q19 TRT-LBM-VP (single domain) --------------------------------------------
+ * The paper's closing remark: the method extends to 3D by replacing D2Q9 with D3Q15 or
+ * D3Q19. This is the step of Sec. 2.2 with D3Q19: e_0 = 0; e_1..6 = +x, -x, +y, -y, +z,
+ * -z; e_7..18 the face diagonals (+x+y, -x-y, +x-y, -x+y, +x+z, -x-z, +x-z, -x+z, +y+z,
+ * -y-z, +y-z, -y+z), so directions 2m-1 and 2m are opposite; weights 1/3, 1/18, 1/36.
+ * Populations [19][nz][ny][nx]; storage types, their rounding and the F16S scale as for
+ * 2D. Edges: x as in 2D (PERIODIC / INLET_EQ west, PERIODIC / OUTFLOW_ZG east); y (south,
+ * north) and z (bottom, top) PERIODIC or FREE_SLIP; rules applied x, then y, then z.
+ * U_O = V + omega x (x - c) with an angular velocity vector. */
+typedef struct {
+  int32_t nx, ny, nz;       /* grid size, each >= 3 */
+  double nu;                /* > 0: tau_plus = nu / c_s^2 + 1/2; else tau_plus is used */
+  double tau_plus, magic_lambda, eta, rho0;
+  double u_in[3];           /* inlet velocity of an INLET_EQ west edge */
+  double u0[3];             /* uniform initial velocity */
+  int32_t west, east, south, north, bottom, top; /* lbm_edge */
+  int32_t storage;          /* lbm_storage */
+  int32_t force_every;      /* record body forces every k-th step (0: never) */
+  int32_t force_capacity;   /* force-ring entries kept on the device (0: 8192) */
+} lbm3_params;
+
+typedef struct {
+  double c[3], v[3], w[3];  /* centre, velocity, angular velocity */
+  double ref_length;        /* for force coefficients only */
+} lbm3_body;
+
+typedef enum { LBM3_SHAPE_SPHERE = 0,      /* chi = 1 where |x - c|^2 < r^2 */
+               LBM3_SHAPE_CYLINDER_Z = 1   /* chi = 1 where (x - cx)^2 + (y - cy)^2 < r^2 */
+} lbm3_shape_kind;
+
+typedef struct {
+  int32_t kind, body;       /* body id 1..255 written where chi = 1; later shapes overwrite */
+  double c[3], radius;
+} lbm3_shape;
+
+typedef struct lbm3_domain lbm3_domain;
+
+/* Defaults: 32^3, nu = 0.1, Lambda = 3/16, eta = 1e-4, rho0 = 1, periodic, FP32,
+ * forces every step, 8192-entry ring. */
+LBM_API void lbm3_params_default(lbm3_params *p);
+
+/* Device bytes of one 3D domain (populations x2, mask, F_VP field, bodies, force sums,
+ * ring). */
+LBM_API size_t lbm3_domain_bytes(const lbm3_params *p, int32_t nbodies);
+
+/* Create a 3D domain on the current device: the mask is rasterised on the device from
+ * `shapes` (FP64 predicates at node positions), g = f^eq(rho0, u0). Allocation and
+ * stream as lbm_domain_create. Synchronises once. */
+LBM_API lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes,
+                                      int32_t nshapes, const lbm3_body *bodies, int32_t nbodies,
+                                      void *cuda_stream, lbm_alloc_fn alloc, lbm_free_fn free_fn,
+                                      void *alloc_ctx, lbm3_domain **out);
+
+/* Advance nsteps time steps (asynchronous; LBM_EBUSY, doing nothing, if the undrained
+ * force entries would exceed the ring). */
+LBM_API lbm_status lbm3_step(lbm3_domain *d, int64_t nsteps);
+
+/* Drain recorded forces into host `out` as [entries][nbodies][3] doubles (force ON body
+ * k: -sum of F_VP over its nodes). Synchronises. LBM_EUNSTABLE if diverged. */
+LBM_API lbm_status lbm3_forces(lbm3_domain *d, double *out, int64_t max_entries, int64_t *written);
+
+/* rho and u = u* + du of the current state, [nz][ny][nx] FP64 each (host or device
+ * pointers, any may be NULL). Synchronises. */
+LBM_API lbm_status lbm3_moments(lbm3_domain *d, double *rho, double *ux, double *uy, double *uz);
+
+/* Raw populations [19][nz][ny][nx] in the storage type; bytes must equal
+ * 19 nx ny nz element size. Synchronise. */
+LBM_API lbm_status lbm3_get_populations(lbm3_domain *d, void *out, size_t bytes);
+LBM_API lbm_status lbm3_set_populations(lbm3_domain *d, const void *in, size_t bytes);
+
+/* The body-id mask [nz][ny][nx]; steps done so far. */
+LBM_API lbm_status lbm3_get_mask(lbm3_domain *d, uint8_t *out);
+LBM_API lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps);
+
+/* Run `steps` steps bracketing the sweep and the force reduction of each with CUDA
+ * events; mean microseconds per launch (either output may be NULL). */
+LBM_API lbm_status lbm3_profile(lbm3_domain *d, int32_t steps, double *sweep_us, double *force_us);
+
+LBM_API lbm_status lbm3_domain_destroy(lbm3_domain *d);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ from ._native import (ELEM_SIZE, LBM_EBUSY, LBM_EUNSTABLE, LbmError, STORAGE, ST
                       check, load)
 from ._compile import build
 
-__all__ = ["Domain", "Batch", "load", "build", "LbmError", "STORAGE", "domain_bytes"]
+__all__ = ["Domain", "Domain3", "Batch", "load", "build", "LbmError", "STORAGE", "domain_bytes"]
 
 
 def _mask_arg(mask):
@@ -130,6 +130,108 @@ class Domain:
     def close(self):
         if self._h is not None:
             load().lbm_domain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Domain3:
+    """One 3D (D3Q19) simulation domain on the current CUDA device (lbm3_* calls).
+
+    Populations are [19, nz, ny, nx]; forces are [entries, nbodies, 3]."""
+
+    def __init__(self, spec, storage="f32", force_every=1, force_capacity=8192, stream=None,
+                 allocator="torch"):
+        import torch
+        L = load()
+        self.spec, self.storage = spec, storage
+        self.nx, self.ny, self.nz = spec["nx"], spec["ny"], spec["nz"]
+        self.nbodies = len(spec["bodies"])
+        self._params = _native.params3_from_spec(spec, storage, force_every, force_capacity)
+        self._bodies, nb = _native.bodies3_from_spec(spec)
+        self._shapes, ns = _native.shapes3_from_spec(spec)
+        self._alloc = _native.TorchAllocator() if allocator == "torch" else None
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        check(L.lbm3_domain_create(C.byref(self._params), self._shapes, ns, self._bodies, nb,
+                                   C.c_void_p(self._stream.cuda_stream),
+                                   self._alloc.c_alloc if self._alloc else _native.ALLOC_FN(),
+                                   self._alloc.c_free if self._alloc else _native.FREE_FN(),
+                                   None, C.byref(h)), "lbm3_domain_create")
+        self._h = h
+
+    def _handle(self):
+        if self._h is None:
+            raise RuntimeError("domain destroyed")
+        return self._h
+
+    def step(self, n: int):
+        check(load().lbm3_step(self._handle(), int(n)), "lbm3_step")
+
+    def run(self, n: int, chunk: int = 4096):
+        """Advance n steps, draining the force ring between chunks; returns the forces."""
+        out = []
+        left = int(n)
+        while left > 0:
+            k = min(chunk, left)
+            self.step(k)
+            out.append(self.forces())
+            left -= k
+        if not out:
+            return np.zeros((0, self.nbodies, 3))
+        return np.concatenate(out, axis=0)
+
+    def forces(self, max_entries: int | None = None) -> np.ndarray:
+        cap = self._params.force_capacity if max_entries is None else int(max_entries)
+        buf = np.zeros((cap, max(self.nbodies, 1), 3))
+        w = C.c_int64()
+        check(load().lbm3_forces(self._handle(), buf.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                                 C.byref(w)), "lbm3_forces")
+        return buf[: w.value, : self.nbodies].copy()
+
+    def moments(self):
+        out = [np.zeros((self.nz, self.ny, self.nx)) for _ in range(4)]
+        check(load().lbm3_moments(self._handle(), *(o.ctypes.data_as(C.c_void_p) for o in out)),
+              "lbm3_moments")
+        return tuple(out)
+
+    def get_populations(self) -> np.ndarray:
+        out = np.zeros((19, self.nz, self.ny, self.nx), dtype=STORAGE_DTYPE[self.storage])
+        check(load().lbm3_get_populations(self._handle(), out.ctypes.data_as(C.c_void_p),
+                                          out.nbytes), "lbm3_get_populations")
+        return out
+
+    def set_populations(self, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, dtype=STORAGE_DTYPE[self.storage])
+        if a.shape != (19, self.nz, self.ny, self.nx):
+            raise ValueError(f"populations must have shape (19, {self.nz}, {self.ny}, {self.nx})")
+        check(load().lbm3_set_populations(self._handle(), a.ctypes.data_as(C.c_void_p), a.nbytes),
+              "lbm3_set_populations")
+
+    def steps_done(self) -> int:
+        v = C.c_int64()
+        check(load().lbm3_steps_done(self._handle(), C.byref(v)), "lbm3_steps_done")
+        return v.value
+
+    def mask(self) -> np.ndarray:
+        out = np.zeros((self.nz, self.ny, self.nx), dtype=np.uint8)
+        check(load().lbm3_get_mask(self._handle(), out.ctypes.data_as(C.c_void_p)), "lbm3_get_mask")
+        return out
+
+    def profile(self, steps: int):
+        """Advance `steps` steps, timing each launch; returns (sweep us, force us) per step."""
+        a, b = C.c_double(), C.c_double()
+        check(load().lbm3_profile(self._handle(), int(steps), C.byref(a), C.byref(b)),
+              "lbm3_profile")
+        return a.value, b.value
+
+    def close(self):
+        if self._h is not None:
+            load().lbm3_domain_destroy(self._h)
             self._h = None
 
     def __del__(self):

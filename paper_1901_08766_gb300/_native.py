@@ -55,6 +55,28 @@ class Geometry(C.Structure):
     _fields_ = [("shapes", C.POINTER(Shape)), ("nshapes", C.c_int32)]
 
 
+class Params3(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nu", C.c_double),
+                ("tau_plus", C.c_double), ("magic_lambda", C.c_double), ("eta", C.c_double),
+                ("rho0", C.c_double), ("u_in", C.c_double * 3), ("u0", C.c_double * 3),
+                ("west", C.c_int32), ("east", C.c_int32), ("south", C.c_int32),
+                ("north", C.c_int32), ("bottom", C.c_int32), ("top", C.c_int32),
+                ("storage", C.c_int32), ("force_every", C.c_int32),
+                ("force_capacity", C.c_int32)]
+
+
+class Body3(C.Structure):
+    _fields_ = [("c", C.c_double * 3), ("v", C.c_double * 3), ("w", C.c_double * 3),
+                ("ref_length", C.c_double)]
+
+
+class Shape3(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("body", C.c_int32), ("c", C.c_double * 3),
+                ("radius", C.c_double)]
+
+
+SHAPE3 = {"sphere": 0, "cylinder_z": 1}
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -101,6 +123,20 @@ SIGNATURES = {
     "lbm_batch_info": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),
                                  C.POINTER(_SZ)]),
     "lbm_batch_destroy": (C.c_int, [_VP]),
+    "lbm3_params_default": (None, [C.POINTER(Params3)]),
+    "lbm3_domain_bytes": (_SZ, [C.POINTER(Params3), _I32]),
+    "lbm3_domain_create": (C.c_int, [C.POINTER(Params3), C.POINTER(Shape3), _I32,
+                                     C.POINTER(Body3), _I32, _VP, ALLOC_FN, FREE_FN, _VP,
+                                     C.POINTER(_VP)]),
+    "lbm3_step": (C.c_int, [_VP, _I64]),
+    "lbm3_forces": (C.c_int, [_VP, _DP, _I64, C.POINTER(_I64)]),
+    "lbm3_moments": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "lbm3_get_populations": (C.c_int, [_VP, _VP, _SZ]),
+    "lbm3_set_populations": (C.c_int, [_VP, _VP, _SZ]),
+    "lbm3_get_mask": (C.c_int, [_VP, _VP]),
+    "lbm3_steps_done": (C.c_int, [_VP, C.POINTER(_I64)]),
+    "lbm3_profile": (C.c_int, [_VP, _I32, _DP, _DP]),
+    "lbm3_domain_destroy": (C.c_int, [_VP]),
 }
 
 _lib = None
@@ -163,6 +199,33 @@ def geometry_from_spec(spec):
                        s.get("chord", 0.0), s.get("thickness", 0.0), s.get("aoa_rad", 0.0))
     g = Geometry(arr, len(shp))
     return g, arr
+
+
+def params3_from_spec(spec, storage: str, force_every: int = 1,
+                      force_capacity: int = 8192) -> Params3:
+    e = spec["edges"]
+    return Params3(spec["nx"], spec["ny"], spec["nz"], spec["nu"], 0.0, spec["magic_lambda"],
+                   spec["eta"], spec["rho0"], (C.c_double * 3)(*spec["u_in"]),
+                   (C.c_double * 3)(*spec["u0"]), EDGE[e["west"]], EDGE[e["east"]],
+                   EDGE[e["south"]], EDGE[e["north"]], EDGE[e["bottom"]], EDGE[e["top"]],
+                   STORAGE[storage], force_every, force_capacity)
+
+
+def bodies3_from_spec(spec):
+    bs = spec["bodies"]
+    arr = (Body3 * max(1, len(bs)))()
+    for k, b in enumerate(bs):
+        arr[k] = Body3((C.c_double * 3)(*b["c"]), (C.c_double * 3)(*b["v"]),
+                       (C.c_double * 3)(*b["w"]), b["ref_length"])
+    return arr, len(bs)
+
+
+def shapes3_from_spec(spec):
+    shp = spec["shapes"]
+    arr = (Shape3 * max(1, len(shp)))()
+    for k, s in enumerate(shp):
+        arr[k] = Shape3(SHAPE3[s["kind"]], s["body"], (C.c_double * 3)(*s["c"]), s["radius"])
+    return arr, len(shp)
 
 
 class TorchAllocator:

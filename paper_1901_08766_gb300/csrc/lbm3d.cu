@@ -1,0 +1,1053 @@
+// 3D TRT-LBM-VP with the D3Q19 lattice: kernels and the single-domain runtime (the C ABI
+// lbm3_* of include/lbm.h). The step is the algorithm of Sec. 2.2 with nineteen
+// directions (the paper's closing remark: D2Q9 is replaced by D3Q15 or D3Q19); storage
+// codecs, stochastic rounding with the node mass kept, and the strip/shuffle pull are
+// those of the 2D sweep. Compiled with --fmad=false: every FMA is written out.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_sweep.cuh"
+
+namespace lbm {
+namespace d3 {
+
+constexpr int kQ3 = 19;
+
+// D3Q19 velocity set: 0 rest; 1..6 +x -x +y -y +z -z; 7..18 +x+y -x-y +x-y -x+y +x+z -x-z
+// +x-z -x+z +y+z -y-z +y-z -y+z. Directions 2m-1 and 2m are opposite.
+__host__ __device__ constexpr int ex3(int a) {
+  return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+       : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey3(int a) {
+  return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+       : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez3(int a) {
+  return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+       : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+// specular reflection across a wall normal to y (e_y reversed) or z (e_z reversed)
+__host__ __device__ constexpr int reflect_y3(int a) {
+  return a == 3 ? 4 : a == 4 ? 3 : a == 7 ? 9 : a == 9 ? 7 : a == 8 ? 10 : a == 10 ? 8
+       : a == 15 ? 18 : a == 18 ? 15 : a == 16 ? 17 : a == 17 ? 16 : a;
+}
+__host__ __device__ constexpr int reflect_z3(int a) {
+  return a == 5 ? 6 : a == 6 ? 5 : a == 11 ? 13 : a == 13 ? 11 : a == 12 ? 14 : a == 14 ? 12
+       : a == 15 ? 17 : a == 17 ? 15 : a == 16 ? 18 : a == 18 ? 16 : a;
+}
+
+// Per-domain constants in compute precision (per class: rest, axis, diagonal).
+template <typename T> struct Const3 {
+  T one_m_omp, hp, hm, inv_2eta1, rho0;
+  T pw0, pw1, pw2, mw1, mw2, kw0, kw1, kw2, qw1, qw2, wr0, wr1, wr2;
+  T ghost[kQ3];  // inlet populations in compute space, as a stored node holds them
+};
+
+struct Dom3 {
+  void *lat[2];
+  uint8_t *mask;
+  void *fvp;              // [cells][3] F_VP of solid nodes (compute precision)
+  double *bodies;         // [nbodies][9]: c, v, w
+  float *bodies_f;
+  double *ring;           // [cap][nbodies][3]
+  double *rowsum;         // [nfrows][nbodies][3]
+  const int32_t *frows;   // rows (k * ny + j) holding solid nodes, ascending
+  int32_t *status;
+  int32_t nx, ny, nz, pitch, nfrows;
+  int32_t west, east, south, north, bottom, top;
+  int32_t nbodies, force_every, force_cap;
+  Const3<float> cf;
+  Const3<double> cd;
+};
+
+template <typename T> __device__ __forceinline__ const Const3<T> &const3(const Dom3 &d);
+template <> __device__ __forceinline__ const Const3<float> &const3<float>(const Dom3 &d) { return d.cf; }
+template <> __device__ __forceinline__ const Const3<double> &const3<double>(const Dom3 &d) { return d.cd; }
+
+template <typename T> __device__ __forceinline__ T shift3(const Const3<T> &c, int a) {
+  return a == 0 ? c.wr0 : (a < 7 ? c.wr1 : c.wr2);
+}
+
+// U_O = V + omega x (x - c) of body b at node (i, j, k), explicitly rounded in FP64
+__device__ __forceinline__ void body_velocity3(const Dom3 &D, int b, int i, int j, int k, double (&uo)[3]) {
+  const double *q = D.bodies + 9 * (b - 1);
+  const double r0 = __dsub_rn(double(i), q[0]), r1 = __dsub_rn(double(j), q[1]), r2 = __dsub_rn(double(k), q[2]);
+  uo[0] = __dadd_rn(q[3], __dsub_rn(__dmul_rn(q[7], r2), __dmul_rn(q[8], r1)));
+  uo[1] = __dadd_rn(q[4], __dsub_rn(__dmul_rn(q[8], r0), __dmul_rn(q[6], r2)));
+  uo[2] = __dadd_rn(q[5], __dsub_rn(__dmul_rn(q[6], r1), __dmul_rn(q[7], r0)));
+}
+__device__ __forceinline__ void body_velocity3(const Dom3 &D, int b, int i, int j, int k, float (&uo)[3]) {
+  const float *q = D.bodies_f + 9 * (b - 1);
+  const float r0 = float(i) - q[0], r1 = float(j) - q[1], r2 = float(k) - q[2];
+  uo[0] = q[3] + (q[7] * r2 - q[8] * r1);
+  uo[1] = q[4] + (q[8] * r0 - q[6] * r2);
+  uo[2] = q[5] + (q[6] * r1 - q[7] * r0);
+}
+
+template <typename T> struct Macro3 {
+  T d, rho, u[3], f[3];
+};
+
+// steps (3)-(5) at one node: Eq. (rho), Eq. (rho*velocity-star), penalization (Eq. d-V,
+// Eq. force-density) and Eq. (velocity-r), in a fixed order of operations
+template <typename T, bool SHIFT, bool FORCE>
+__device__ __forceinline__ Macro3<T> macro3(const T (&x)[kQ3], const Const3<T> &c, bool solid,
+                                            const T (&uo)[3]) {
+  Macro3<T> m;
+  T dm[10];
+#pragma unroll
+  for (int p = 1; p <= 9; ++p) dm[p] = x[2 * p - 1] - x[2 * p];
+  const T s1 = x[1] + x[2], s2 = x[3] + x[4], s3 = x[5] + x[6], s4 = x[7] + x[8], s5 = x[9] + x[10];
+  const T s6 = x[11] + x[12], s7 = x[13] + x[14], s8 = x[15] + x[16], s9 = x[17] + x[18];
+  m.d = (x[0] + ((s1 + s2) + s3)) + (((s4 + s5) + (s6 + s7)) + (s8 + s9));
+  m.rho = SHIFT ? c.rho0 + m.d : m.d;
+  const T jx = (dm[1] + dm[4]) + (dm[5] + (dm[6] + dm[7]));
+  const T jy = (dm[2] + dm[4]) + ((dm[8] + dm[9]) - dm[5]);
+  const T jz = (dm[3] + dm[6]) + ((dm[8] - dm[9]) - dm[7]);
+  const T inv = rcp_(m.rho);
+  m.u[0] = jx * inv;
+  m.u[1] = jy * inv;
+  m.u[2] = jz * inv;
+  m.f[0] = m.f[1] = m.f[2] = T(0);
+  if (FORCE && solid) {
+    const T two_rho = m.rho + m.rho;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const T du = (uo[e] - m.u[e]) * c.inv_2eta1;
+      m.f[e] = two_rho * du;
+      m.u[e] = m.u[e] + du;
+    }
+  }
+  return m;
+}
+
+// TRT collision with the split Guo term per opposite pair (the 2D form, nine pairs)
+template <typename T, bool SHIFT, bool FORCE>
+__device__ __forceinline__ void collide3(T (&x)[kQ3], const Macro3<T> &m, const Const3<T> &c) {
+  const T base = SHIFT ? m.d : m.rho;
+  const T ux = m.u[0], uy = m.u[1], uz = m.u[2];
+  const T q = T(1.5) * fma_(uz, uz, fma_(uy, uy, ux * ux));
+  const T a0 = c.pw0 * m.rho, b0 = c.pw0 * base;
+  const T a1 = c.pw1 * m.rho, b1 = c.pw1 * base;
+  const T a2 = c.pw2 * m.rho, b2 = c.pw2 * base;
+  const T m1 = c.mw1 * m.rho, m2 = c.mw2 * m.rho;
+  T uf = T(0);
+  if (FORCE) uf = fma_(uz, m.f[2], fma_(uy, m.f[1], ux * m.f[0]));
+  {
+    T g0 = fma_(c.one_m_omp, x[0], fma_(-a0, q, b0));
+    if (FORCE) g0 = fma_(T(-3) * c.kw0, uf, g0);
+    x[0] = g0;
+  }
+  auto pair = [&](int ia, int ib, T eu, T ef, T a, T b, T mm, T kw, T qw) {
+    const T xs = x[ia] + x[ib];
+    const T xd = x[ia] - x[ib];
+    const T c1 = fma_(T(4.5) * eu, eu, -q);
+    const T eqs = fma_(a, c1, b);
+    T S = fma_(-c.hp, xs, eqs);
+    T A = fma_(-c.hm, xd, mm * eu);
+    if (FORCE) {
+      S = fma_(kw, fma_(T(9) * eu, ef, T(-3) * uf), S);
+      A = fma_(qw, ef, A);
+    }
+    x[ia] = (x[ia] + S) + A;
+    x[ib] = (x[ib] + S) - A;
+  };
+  const T fx = m.f[0], fy = m.f[1], fz = m.f[2];
+  pair(1, 2, ux, fx, a1, b1, m1, c.kw1, c.qw1);
+  pair(3, 4, uy, fy, a1, b1, m1, c.kw1, c.qw1);
+  pair(5, 6, uz, fz, a1, b1, m1, c.kw1, c.qw1);
+  pair(7, 8, ux + uy, fx + fy, a2, b2, m2, c.kw2, c.qw2);
+  pair(9, 10, ux - uy, fx - fy, a2, b2, m2, c.kw2, c.qw2);
+  pair(11, 12, ux + uz, fx + fz, a2, b2, m2, c.kw2, c.qw2);
+  pair(13, 14, ux - uz, fx - fz, a2, b2, m2, c.kw2, c.qw2);
+  pair(15, 16, uy + uz, fy + fz, a2, b2, m2, c.kw2, c.qw2);
+  pair(17, 18, uy - uz, fy - fz, a2, b2, m2, c.kw2, c.qw2);
+}
+
+// 16-bit words of two nodes' values with stochastic rounding and the node mass kept
+// (the 2D rule: moving values rounded first, the rest value stored as the pulled mass
+// minus their rounded sum, pairs summed in a fixed order)
+template <int S>
+__device__ __forceinline__ void encode3_pair(const float (&x0)[kQ3], const float (&x1)[kQ3], F2 d,
+                                             uint32_t bits, uint32_t (&w)[kQ3]) {
+  F2 sp[10];
+#pragma unroll
+  for (int p = 1; p <= 9; ++p) {
+    w[2 * p - 1] = Codec<S>::enc2_sr(x0[2 * p - 1], x1[2 * p - 1], bits);
+    w[2 * p] = Codec<S>::enc2_sr(x0[2 * p], x1[2 * p], bits);
+    sp[p] = F2(Codec<S>::dec2(w[2 * p - 1])) + F2(Codec<S>::dec2(w[2 * p]));
+  }
+  const F2 moved = (((sp[1] + sp[2]) + sp[3]) + (((sp[4] + sp[5]) + (sp[6] + sp[7])) + (sp[8] + sp[9])));
+  const F2 rest = d - moved;
+  w[0] = Codec<S>::enc2_sr(rest.v.x, rest.v.y, bits);
+}
+
+// source row of direction a for row (j, k): y rule, then z rule
+__device__ __forceinline__ void src_row3(const Dom3 &D, int a, int j, int k, int &sa, int &sy, int &sz) {
+  sa = a;
+  sy = j - ey3(a);
+  sz = k - ez3(a);
+  if (sy < 0) {
+    if (D.south == LBM_FREE_SLIP) { sy = 0; sa = reflect_y3(sa); }
+    else sy += D.ny;
+  } else if (sy > D.ny - 1) {
+    if (D.north == LBM_FREE_SLIP) { sy = D.ny - 1; sa = reflect_y3(sa); }
+    else sy -= D.ny;
+  }
+  if (sz < 0) {
+    if (D.bottom == LBM_FREE_SLIP) { sz = 0; sa = reflect_z3(sa); }
+    else sz += D.nz;
+  } else if (sz > D.nz - 1) {
+    if (D.top == LBM_FREE_SLIP) { sz = D.nz - 1; sa = reflect_z3(sa); }
+    else sz -= D.nz;
+  }
+}
+
+// The fused 3D sweep: one warp per strip of 32 V cells of one row (j, k) at a time
+// (persistent grid), nineteen vector loads per lane, the +-1 x-shift by shuffles, strip
+// ends by broadcast loads, update, nineteen vector stores into the other lattice.
+template <int S, int V>
+__global__ void __launch_bounds__(256) sweep3_kernel(const Dom3 *dom, long long n, int par) {
+  using Cd = Codec<S>;
+  using E = typename Cd::E;
+  using T = typename Cd::T;
+  constexpr bool SHIFT = Cd::kShiftCompute;
+  constexpr bool kAddShift = Cd::kShiftCompute && !Cd::kStoreShifted;
+  constexpr int kStrip = 32 * V;
+  constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
+  constexpr T kUnscale = T(1) / T(Cd::kScale);
+  const Dom3 &D = *dom;
+  const Const3<T> &C = const3<T>(D);
+  const int lane = threadIdx.x & 31;
+  const int nx = D.nx, ny = D.ny, nz = D.nz, pitch = D.pitch;
+  const int strips = (nx + kStrip - 1) / kStrip;
+  const long long items = static_cast<long long>(ny) * nz * strips;
+  const long long wg = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  const E *__restrict__ src = static_cast<const E *>(D.lat[par]);
+  E *__restrict__ dst = static_cast<E *>(D.lat[par ^ 1]);
+  const size_t plane = static_cast<size_t>(ny) * pitch;  // one z plane of one direction
+  const size_t dirsz = plane * nz;                       // one direction
+  const bool west_inlet = D.west == LBM_INLET_EQ, east_out = D.east == LBM_OUTFLOW_ZG;
+  int unstable = 0;
+  for (long long it = wg; it < items; it += nw) {
+    const int row = static_cast<int>(it / strips);
+    const int x0 = static_cast<int>(it % strips) * kStrip;
+    const int j = row % ny, k = row / ny;
+    const int xl = x0 + lane * V;
+    const bool lane_on = xl < nx;
+    const bool west_edge = x0 == 0, east_edge = x0 + kStrip >= nx;
+    const int col_l = west_edge ? (west_inlet ? 0 : nx - 1) : x0 - 1;
+    const int col_r = east_edge ? 0 : x0 + kStrip;
+    const int k_last = nx - 1 - xl;
+    const int xl_ld = min(xl, pitch - V);
+    Strip<S, V> v[kQ3];
+    E end_in[kQ3];
+#pragma unroll
+    for (int a = 0; a < kQ3; ++a) {
+      int sa, sy, sz;
+      src_row3(D, a, j, k, sa, sy, sz);
+      const E *rp = src + sa * dirsz + static_cast<size_t>(sz) * plane + static_cast<size_t>(sy) * pitch;
+      v[a].load(rp + xl_ld);
+      const int ex = ex3(a);
+      end_in[a] = E(0);
+      if (ex == 1) end_in[a] = __ldg(rp + col_l);
+      else if (ex == -1) end_in[a] = __ldg(rp + col_r);
+    }
+    uint8_t b[V];
+    {
+      const uint8_t *mrow = D.mask + (static_cast<size_t>(k) * ny + j) * pitch + xl_ld;
+#pragma unroll
+      for (int q = 0; q < V; ++q) b[q] = lane_on ? __ldg(mrow + q) : uint8_t(0);
+    }
+    // the +-1 x-shift of the pull
+#pragma unroll
+    for (int a = 0; a < kQ3; ++a) {
+      const int ex = ex3(a);
+      if (ex == 1) {
+        E in = shfl_up1<E>(v[a].last());
+        in = lane == 0 ? end_in[a] : in;
+        v[a].shift_up(in);
+      } else if (ex == -1) {
+        E keep = E(0);
+        if (east_edge) {
+#pragma unroll
+          for (int q = 0; q < V; ++q) keep = (q == k_last) ? v[a].get(q) : keep;
+        }
+        E in = shfl_down1<E>(v[a].first());
+        in = (lane == 31 && !east_edge) ? end_in[a] : in;
+        v[a].shift_down(in);
+        if (east_edge) {
+          const E fix = east_out ? keep : end_in[a];
+#pragma unroll
+          for (int q = 0; q < V; ++q)
+            if (q == k_last) v[a].set(q, fix);
+        }
+      }
+    }
+    bool any_lane = false;
+#pragma unroll
+    for (int q = 0; q < V; ++q) any_lane |= b[q] != 0;
+    const bool any_solid = __any_sync(0xffffffffu, any_lane);
+    const unsigned valid_bits =
+        east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u)) : (1u << V) - 1u;
+    unsigned bad_bits = 0u;
+    auto update = [&](T (&x)[kQ3], int q) -> T {
+      if (q == 0 && west_edge && west_inlet && lane == 0) {
+        x[1] = C.ghost[1];
+        x[7] = C.ghost[7];
+        x[9] = C.ghost[9];
+        x[11] = C.ghost[11];
+        x[13] = C.ghost[13];
+      }
+      Macro3<T> m;
+      if (any_solid) {
+        T uo[3] = {T(0), T(0), T(0)};
+        const bool solid = b[q] != 0;
+        if (solid) body_velocity3(D, b[q], xl + q, j, k, uo);
+        m = macro3<T, SHIFT, true>(x, C, solid, uo);
+        collide3<T, SHIFT, true>(x, m, C);
+        if (solid) {
+          T *fv = static_cast<T *>(D.fvp) + 3 * ((static_cast<size_t>(k) * ny + j) * pitch + xl + q);
+          fv[0] = m.f[0] * kUnscale;
+          fv[1] = m.f[1] * kUnscale;
+          fv[2] = m.f[2] * kUnscale;
+        }
+      } else {
+        const T uo[3] = {T(0), T(0), T(0)};
+        m = macro3<T, SHIFT, false>(x, C, false, uo);
+        collide3<T, SHIFT, false>(x, m, C);
+      }
+      bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
+      return m.d;
+    };
+    if constexpr (sizeof(E) == 2) {
+      const uint32_t sr_g = sr_group_bits(sr_row_key(n, row), xl);
+#pragma unroll
+      for (int q = 0; q < V; q += 2) {
+        T x0v[kQ3], x1v[kQ3];
+#pragma unroll
+        for (int a = 0; a < kQ3; ++a) {
+          const float2 p = Cd::dec2(v[a].w[q >> 1]);
+          x0v[a] = p.x;
+          x1v[a] = p.y;
+        }
+        const float d0 = update(x0v, q);
+        const float d1 = update(x1v, q + 1);
+        uint32_t w[kQ3];
+        encode3_pair<S>(x0v, x1v, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
+#pragma unroll
+        for (int a = 0; a < kQ3; ++a) v[a].w[q >> 1] = w[a];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        T x[kQ3];
+#pragma unroll
+        for (int a = 0; a < kQ3; ++a) x[a] = Cd::dec(v[a].get(q));
+        if constexpr (kAddShift) {
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) x[a] -= shift3(C, a);  // exact (Sterbenz)
+        }
+        update(x, q);
+        if constexpr (kAddShift) {
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) x[a] += shift3(C, a);
+        }
+#pragma unroll
+        for (int a = 0; a < kQ3; ++a) v[a].set(q, Cd::enc(x[a]));
+      }
+    }
+    if (bad_bits & valid_bits) unstable = 1;
+    if (east_edge) {
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+        if (!((valid_bits >> q) & 1u)) {
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) v[a].set(q, E(0));
+        }
+    }
+    if (lane_on) {
+#pragma unroll
+      for (int a = 0; a < kQ3; ++a)
+        v[a].store(dst + a * dirsz + static_cast<size_t>(k) * plane + static_cast<size_t>(j) * pitch + xl);
+    }
+  }
+  if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(D.status, 1);
+}
+
+// Scalar pull with the edge rules (moments export).
+template <int S>
+__device__ __forceinline__ typename Codec<S>::T pull3(const Dom3 &D, const void *lat, int a, int i, int j, int k) {
+  using Cd = Codec<S>;
+  using E = typename Cd::E;
+  int sx = i - ex3(a);
+  if (sx < 0) {
+    if (D.west == LBM_INLET_EQ) return const3<typename Cd::T>(D).ghost[a];
+    sx += D.nx;
+  } else if (sx > D.nx - 1) {
+    sx = D.east == LBM_OUTFLOW_ZG ? D.nx - 1 : sx - D.nx;
+  }
+  int sa, sy, sz;
+  src_row3(D, a, j, k, sa, sy, sz);
+  const E *p = static_cast<const E *>(lat);
+  typename Cd::T x = Cd::dec(p[((static_cast<size_t>(sa) * D.nz + sz) * D.ny + sy) * D.pitch + sx]);
+  if (Cd::kShiftCompute && !Cd::kStoreShifted) x -= shift3(const3<typename Cd::T>(D), a);
+  return x;
+}
+
+template <int S>
+__global__ void moments3_kernel(const Dom3 *dom, int par, double *rho, double *ux, double *uy, double *uz) {
+  using Cd = Codec<S>;
+  using T = typename Cd::T;
+  const Dom3 &D = *dom;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= D.nx) return;
+  T x[kQ3];
+#pragma unroll
+  for (int a = 0; a < kQ3; ++a) x[a] = pull3<S>(D, D.lat[par], a, i, j, k);
+  const int b = D.mask[(static_cast<size_t>(k) * D.ny + j) * D.pitch + i];
+  T uo[3] = {T(0), T(0), T(0)};
+  if (b) body_velocity3(D, b, i, j, k, uo);
+  const Macro3<T> m = macro3<T, Cd::kShiftCompute, true>(x, const3<T>(D), b != 0, uo);
+  const size_t c = (static_cast<size_t>(k) * D.ny + j) * D.nx + i;
+  if (rho) rho[c] = double(m.rho * (T(1) / T(Cd::kScale)));
+  if (ux) ux[c] = double(m.u[0]);
+  if (uy) uy[c] = double(m.u[1]);
+  if (uz) uz[c] = double(m.u[2]);
+}
+
+template <int S>
+__global__ void init3_kernel(typename Codec<S>::E *lat, int nx, int nrows, int pitch, double rho0,
+                             double u0x, double u0y, double u0z) {
+  using Cd = Codec<S>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (i >= pitch) return;
+  const double w = a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  const double eu = ex3(a) * u0x + ey3(a) * u0y + ez3(a) * u0z;
+  const double usq = u0x * u0x + u0y * u0y + u0z * u0z;
+  const double dev = rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+  double val = Cd::kStoreShifted ? dev * Cd::kScale : rho0 * w + dev;
+  if (i >= nx) val = 0.0;
+  const typename Cd::E e = Cd::enc(typename Cd::T(val));
+  for (int row = blockIdx.z; row < nrows; row += gridDim.z)  // row = k * ny + j
+    lat[(static_cast<size_t>(a) * nrows + row) * pitch + i] = e;
+}
+
+// sphere / z-cylinder predicates in FP64 with explicit roundings (the plain IEEE order)
+struct Shape3Dev {
+  int32_t kind, body;
+  double c[3], radius;
+};
+
+__global__ void rasterize3_kernel(uint8_t *mask, int nx, int ny, int nz, int pitch, const Shape3Dev *shapes,
+                                  int nshapes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= pitch) return;
+  uint8_t id = 0;
+  if (i < nx)
+    for (int q = 0; q < nshapes; ++q) {
+      const Shape3Dev &s = shapes[q];
+      const double dx = __dsub_rn(double(i), s.c[0]), dy = __dsub_rn(double(j), s.c[1]);
+      double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      if (s.kind == LBM3_SHAPE_SPHERE) {
+        const double dz = __dsub_rn(double(k), s.c[2]);
+        d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+      }
+      if (d2 < __dmul_rn(s.radius, s.radius)) id = static_cast<uint8_t>(s.body);
+    }
+  mask[(static_cast<size_t>(k) * ny + j) * pitch + i] = id;
+}
+
+// Body forces of step index n (the sweep just computed step n + 1): one warp per listed
+// row sums -F_VP per body (lane-strided, fixed shuffle tree), then one block per body adds
+// the rows in list order into the ring entry.
+template <typename T>
+__global__ void rows3_kernel(const Dom3 *dom) {
+  const Dom3 &D = *dom;
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int q = wg; q < D.nfrows; q += nw) {
+    const size_t row = static_cast<size_t>(D.frows[q]);
+    const uint8_t *m = D.mask + row * D.pitch;
+    const T *fv = static_cast<const T *>(D.fvp) + 3 * row * D.pitch;
+    for (int body = 1; body <= D.nbodies; ++body) {
+      double f[3] = {0.0, 0.0, 0.0};
+      for (int i = lane; i < D.nx; i += 32)
+        if (m[i] == body)
+          for (int e = 0; e < 3; ++e) f[e] -= double(fv[3 * i + e]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        for (int e = 0; e < 3; ++e) f[e] += __shfl_down_sync(0xffffffffu, f[e], off);
+      if (lane == 0)
+        for (int e = 0; e < 3; ++e) D.rowsum[(static_cast<size_t>(q) * D.nbodies + body - 1) * 3 + e] = f[e];
+    }
+  }
+}
+
+constexpr int kSumThreads = 256;
+
+__global__ void __launch_bounds__(kSumThreads) sum3_kernel(const Dom3 *dom, long long entry) {
+  const Dom3 &D = *dom;
+  const int body = blockIdx.x + 1;
+  __shared__ double red[3][kSumThreads / 32];
+  double f[3] = {0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < D.nfrows; q += blockDim.x)
+    for (int e = 0; e < 3; ++e) f[e] += D.rowsum[(static_cast<size_t>(q) * D.nbodies + body - 1) * 3 + e];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    for (int e = 0; e < 3; ++e) f[e] += __shfl_down_sync(0xffffffffu, f[e], off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int e = 0; e < 3; ++e) red[e][warp] = f[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double *slot = D.ring + (static_cast<size_t>(entry % D.force_cap) * D.nbodies + body - 1) * 3;
+    for (int e = 0; e < 3; ++e) {
+      double t = 0.0;
+      for (int w = 0; w < kSumThreads / 32; ++w) t += red[e][w];
+      slot[e] = t;
+    }
+  }
+}
+
+}  // namespace d3
+}  // namespace lbm
+
+// ======================================================================================
+// Runtime and C ABI
+
+using namespace lbm;
+using namespace lbm::d3;
+
+namespace {
+
+lbm_status fail3(lbm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return s;
+}
+
+#define LBM3_CUDA(call)                                                               \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail3(LBM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                   __FILE__, __LINE__);                                               \
+  } while (0)
+
+size_t esize(int storage) {
+  return storage == LBM_F64 ? 8 : storage == LBM_F32 ? 4 : (storage == LBM_F16S || storage == LBM_BF16S) ? 2 : 0;
+}
+size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout3 {
+  size_t lat, mask_off, fvp_off, bodies_off, bodiesf_off, ring_off, status_off, total;
+};
+
+Layout3 layout3(const lbm3_params &p, int nb) {
+  Layout3 L;
+  const size_t pitch = up(static_cast<size_t>(p.nx), kPitchAlign);
+  const size_t cells = pitch * p.ny * p.nz;
+  const int cap = p.force_capacity > 0 ? p.force_capacity : 8192;
+  L.lat = up(kQ3 * cells * esize(p.storage), 256);
+  size_t o = 2 * L.lat;
+  L.mask_off = o;
+  o += up(cells, 256);
+  L.fvp_off = o;
+  o += up(cells * 3 * (p.storage == LBM_F64 ? 8 : 4), 256);
+  L.bodies_off = o;
+  o += up(sizeof(double) * 9 * std::max(1, nb), 256);
+  L.bodiesf_off = o;
+  o += up(sizeof(float) * 9 * std::max(1, nb), 256);
+  L.ring_off = o;
+  o += up(p.force_every > 0 ? sizeof(double) * 3 * std::max(1, nb) * cap : 16, 256);
+  L.status_off = o;
+  o += 256;
+  L.total = o;
+  return L;
+}
+
+template <typename T> void fill3(Const3<T> &c, double omp, double omm, double eta, double rho0, double scale) {
+  const double w0 = 1.0 / 3.0, w1 = 1.0 / 18.0, w2 = 1.0 / 36.0;
+  c.one_m_omp = T(1.0 - omp);
+  c.hp = T(0.5 * omp);
+  c.hm = T(0.5 * omm);
+  c.inv_2eta1 = T(1.0 / (2.0 * eta + 1.0));
+  c.rho0 = T(rho0 * scale);
+  c.pw0 = T(omp * w0);
+  c.pw1 = T(omp * w1);
+  c.pw2 = T(omp * w2);
+  c.mw1 = T(3.0 * omm * w1);
+  c.mw2 = T(3.0 * omm * w2);
+  c.kw0 = T((1.0 - 0.5 * omp) * w0);
+  c.kw1 = T((1.0 - 0.5 * omp) * w1);
+  c.kw2 = T((1.0 - 0.5 * omp) * w2);
+  c.qw1 = T(3.0 * (1.0 - 0.5 * omm) * w1);
+  c.qw2 = T(3.0 * (1.0 - 0.5 * omm) * w2);
+  c.wr0 = T(w0 * rho0);
+  c.wr1 = T(w1 * rho0);
+  c.wr2 = T(w2 * rho0);
+}
+
+}  // namespace
+
+struct lbm3_domain {
+  lbm3_params p{};
+  int nbodies = 0, pitch = 0;
+  cudaStream_t st = nullptr;
+  lbm_alloc_fn afn = nullptr;
+  lbm_free_fn ffn = nullptr;
+  void *actx = nullptr;
+  void *block = nullptr, *frows = nullptr, *rowsum = nullptr;
+  Dom3 h{};
+  Dom3 *d_dom = nullptr;
+  long long done = 0, drained = 0;
+  int parity = 0;
+  int grid = 0;
+  void *get(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (afn) return afn(bytes, actx);
+    void *q = nullptr;
+    if (cudaMallocAsync(&q, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return q;
+  }
+  void put(void *q) {
+    if (!q) return;
+    if (ffn) ffn(q, actx);
+    else cudaFreeAsync(q, st);
+  }
+};
+
+namespace {
+
+cudaError_t launch_sweep3(lbm3_domain *d, long long n, int par) {
+  switch (d->p.storage) {
+    case LBM_F64: sweep3_kernel<LBM_F64, 2><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
+    case LBM_F32: sweep3_kernel<LBM_F32, 4><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
+    case LBM_F16S: sweep3_kernel<LBM_F16S, 4><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
+    case LBM_BF16S: sweep3_kernel<LBM_BF16S, 4><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forces3(lbm3_domain *d, long long n) {
+  if (d->p.force_every <= 0 || (n + 1) % d->p.force_every != 0) return cudaSuccess;
+  if (d->nbodies > 0 && d->h.nfrows > 0) {
+    if (d->p.storage == LBM_F64) rows3_kernel<double><<<d->grid, 256, 0, d->st>>>(d->d_dom);
+    else rows3_kernel<float><<<d->grid, 256, 0, d->st>>>(d->d_dom);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (d->nbodies > 0) {
+    const long long entry = (n + 1) / d->p.force_every - 1;
+    if (d->h.nfrows > 0) {
+      sum3_kernel<<<d->nbodies, kSumThreads, 0, d->st>>>(d->d_dom, entry);
+    } else {
+      return cudaMemsetAsync(d->h.ring + (entry % d->h.force_cap) * d->nbodies * 3, 0,
+                             sizeof(double) * 3 * d->nbodies, d->st);
+    }
+  }
+  return cudaGetLastError();
+}
+
+lbm_status validate3(const lbm3_params *p, int nb, int ns, const lbm3_shape *shapes) {
+  if (!p) return fail3(LBM_EINVAL, "params is NULL");
+  if (p->nx < 3 || p->ny < 3 || p->nz < 3) return fail3(LBM_EINVAL, "nx, ny, nz must be >= 3");
+  if (p->ny > 65535 || p->nz > 65535) return fail3(LBM_EINVAL, "ny and nz must be <= 65535");
+  if (static_cast<double>(up(p->nx, kPitchAlign)) * p->ny * p->nz > 1.0e9)
+    return fail3(LBM_EINVAL, "grid too large (more than 1e9 padded nodes)");
+  if (esize(p->storage) == 0) return fail3(LBM_EINVAL, "unknown storage %d", p->storage);
+  const double tau = p->nu > 0 ? 3.0 * p->nu + 0.5 : p->tau_plus;
+  if (!(tau > 0.5)) return fail3(LBM_EINVAL, "tau_plus must exceed 1/2");
+  if (!(p->magic_lambda > 0) || !(p->eta > 0) || !(p->rho0 > 0)) return fail3(LBM_EINVAL, "Lambda, eta, rho0 must be > 0");
+  if (p->west != LBM_PERIODIC && p->west != LBM_INLET_EQ) return fail3(LBM_EINVAL, "west edge must be PERIODIC or INLET_EQ");
+  if (p->east != LBM_PERIODIC && p->east != LBM_OUTFLOW_ZG) return fail3(LBM_EINVAL, "east edge must be PERIODIC or OUTFLOW_ZG");
+  if ((p->west == LBM_PERIODIC) != (p->east == LBM_PERIODIC)) return fail3(LBM_EINVAL, "x edges: both periodic or neither");
+  const int32_t yz[4] = {p->south, p->north, p->bottom, p->top};
+  for (int q = 0; q < 4; ++q)
+    if (yz[q] != LBM_PERIODIC && yz[q] != LBM_FREE_SLIP) return fail3(LBM_EINVAL, "y and z edges must be PERIODIC or FREE_SLIP");
+  if ((p->south == LBM_PERIODIC) != (p->north == LBM_PERIODIC) || (p->bottom == LBM_PERIODIC) != (p->top == LBM_PERIODIC))
+    return fail3(LBM_EINVAL, "y and z edges: both periodic or neither");
+  if (nb < 0 || nb > 255) return fail3(LBM_EINVAL, "nbodies must be in [0, 255]");
+  if (ns < 0 || (ns > 0 && !shapes)) return fail3(LBM_EINVAL, "shapes");
+  for (int q = 0; q < ns; ++q) {
+    if (shapes[q].kind != LBM3_SHAPE_SPHERE && shapes[q].kind != LBM3_SHAPE_CYLINDER_Z)
+      return fail3(LBM_EINVAL, "shape %d: unknown kind", q);
+    if (shapes[q].body < 1 || shapes[q].body > nb) return fail3(LBM_EINVAL, "shape %d: body id not in [1, %d]", q, nb);
+  }
+  if (p->force_every < 0 || p->force_capacity < 0) return fail3(LBM_EINVAL, "force_every/capacity must be >= 0");
+  return LBM_OK;
+}
+
+int sweep3_occupancy(int storage) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (storage) {
+    case LBM_F64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_F64, 2>, 256, 0); break;
+    case LBM_F32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_F32, 4>, 256, 0); break;
+    case LBM_F16S: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_F16S, 4>, 256, 0); break;
+    case LBM_BF16S: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_BF16S, 4>, 256, 0); break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return std::max(1, n);
+}
+
+lbm_status read_status3(lbm3_domain *d) {
+  int32_t status = 0;
+  LBM3_CUDA(cudaMemcpyAsync(&status, d->h.status, sizeof(int32_t), cudaMemcpyDeviceToHost, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  if (status & 1) return fail3(LBM_EUNSTABLE, "3D domain diverged (rho out of range or not finite)");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm3_params_default(lbm3_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = p->ny = p->nz = 32;
+  p->nu = 0.1;
+  p->tau_plus = 0.8;
+  p->magic_lambda = 3.0 / 16.0;
+  p->eta = 1e-4;
+  p->rho0 = 1.0;
+  p->storage = LBM_F32;
+  p->force_every = 1;
+  p->force_capacity = 8192;
+}
+
+size_t lbm3_domain_bytes(const lbm3_params *p, int32_t nbodies) {
+  if (!p || esize(p->storage) == 0 || p->nx < 1 || p->ny < 1 || p->nz < 1) return 0;
+  return layout3(*p, std::max(0, nbodies)).total;
+}
+
+lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, int32_t nshapes,
+                              const lbm3_body *bodies, int32_t nbodies, void *cuda_stream,
+                              lbm_alloc_fn alloc, lbm_free_fn free_fn, void *alloc_ctx,
+                              lbm3_domain **out) {
+  if (!out) return fail3(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  lbm_status rc = validate3(p, nbodies, nshapes, shapes);
+  if (rc != LBM_OK) return rc;
+  if (nbodies > 0 && !bodies) return fail3(LBM_EINVAL, "bodies is NULL");
+  int dev = 0, sms = 0;
+  LBM3_CUDA(cudaGetDevice(&dev));
+  LBM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  lbm3_domain *d = new lbm3_domain();
+  d->p = *p;
+  if (d->p.force_capacity == 0) d->p.force_capacity = 8192;
+  d->nbodies = nbodies;
+  d->pitch = static_cast<int>(up(p->nx, kPitchAlign));
+  d->st = static_cast<cudaStream_t>(cuda_stream);
+  d->afn = alloc;
+  d->ffn = free_fn;
+  d->actx = alloc_ctx;
+  const Layout3 L = layout3(d->p, nbodies);
+  void *dsh = nullptr;  // shape table (admission only)
+  auto bail = [&](lbm_status r) {
+    cudaStreamSynchronize(d->st);
+    d->put(dsh);
+    d->put(d->block);
+    d->put(d->frows);
+    d->put(d->rowsum);
+    d->put(d->d_dom);
+    delete d;
+    return r;
+  };
+#define ADM3(call)                                                                           \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return bail(fail3(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_))); \
+  } while (0)
+  d->block = d->get(L.total);
+  d->d_dom = static_cast<Dom3 *>(d->get(sizeof(Dom3)));
+  if (!d->block || !d->d_dom) return bail(fail3(LBM_ENOMEM, "device allocation of %zu bytes failed", L.total));
+  char *base = static_cast<char *>(d->block);
+  Dom3 &D = d->h;
+  D.lat[0] = base;
+  D.lat[1] = base + L.lat;
+  D.mask = reinterpret_cast<uint8_t *>(base + L.mask_off);
+  D.fvp = base + L.fvp_off;
+  D.bodies = reinterpret_cast<double *>(base + L.bodies_off);
+  D.bodies_f = reinterpret_cast<float *>(base + L.bodiesf_off);
+  D.ring = reinterpret_cast<double *>(base + L.ring_off);
+  D.status = reinterpret_cast<int32_t *>(base + L.status_off);
+  D.nx = p->nx;
+  D.ny = p->ny;
+  D.nz = p->nz;
+  D.pitch = d->pitch;
+  D.west = p->west;
+  D.east = p->east;
+  D.south = p->south;
+  D.north = p->north;
+  D.bottom = p->bottom;
+  D.top = p->top;
+  D.nbodies = nbodies;
+  D.force_every = p->force_every;
+  D.force_cap = d->p.force_capacity;
+  const double tau_s = p->nu > 0 ? 3.0 * p->nu + 0.5 : p->tau_plus;
+  const double tau_a = 0.5 + p->magic_lambda / (tau_s - 0.5);
+  const double omp = 1.0 / tau_s, omm = 1.0 / tau_a;
+  const bool shifted = p->storage == LBM_F16S || p->storage == LBM_BF16S;
+  const double scale = p->storage == LBM_F16S ? double(kF16Scale) : 1.0;
+  fill3(D.cd, omp, omm, p->eta, p->rho0, 1.0);
+  fill3(D.cf, omp, omm, p->eta, p->rho0, scale);
+  {
+    // inlet ghost f^eq(rho0, u_in) in compute space, held as the storage would hold it
+    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    const double *u = p->u_in;
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int a = 0; a < kQ3; ++a) {
+      const double wa = a == 0 ? w[0] : (a < 7 ? w[1] : w[2]);
+      const double eu = ex3(a) * u[0] + ey3(a) * u[1] + ez3(a) * u[2];
+      const double dev = p->rho0 * wa * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+      D.cd.ghost[a] = p->rho0 * wa + dev;
+      float gf;
+      if (p->storage == LBM_F32) gf = float(p->rho0 * wa + dev) - float(wa * p->rho0);
+      else if (p->storage == LBM_F16S) gf = __half2float(__float2half_rn(float(dev * scale)));
+      else if (p->storage == LBM_BF16S) gf = __bfloat162float(__float2bfloat16_rn(float(dev)));
+      else gf = float(dev);
+      D.cf.ghost[a] = gf;
+      (void)shifted;
+    }
+  }
+  cudaStream_t st = d->st;
+  // shapes -> mask
+  std::vector<Shape3Dev> hs(std::max(1, nshapes));
+  for (int q = 0; q < nshapes; ++q)
+    hs[q] = Shape3Dev{shapes[q].kind, shapes[q].body, {shapes[q].c[0], shapes[q].c[1], shapes[q].c[2]}, shapes[q].radius};
+  dsh = d->get(sizeof(Shape3Dev) * hs.size());
+  if (!dsh) return bail(fail3(LBM_ENOMEM, "shape buffer allocation failed"));
+  ADM3(cudaMemcpyAsync(dsh, hs.data(), sizeof(Shape3Dev) * hs.size(), cudaMemcpyHostToDevice, st));
+  rasterize3_kernel<<<dim3((d->pitch + 127) / 128, p->ny, p->nz), 128, 0, st>>>(
+      D.mask, p->nx, p->ny, p->nz, d->pitch, static_cast<const Shape3Dev *>(dsh), nshapes);
+  ADM3(cudaGetLastError());
+  // body tables
+  std::vector<double> hb(9 * std::max(1, nbodies), 0.0);
+  for (int q = 0; q < nbodies; ++q)
+    for (int e = 0; e < 3; ++e) {
+      hb[9 * q + e] = bodies[q].c[e];
+      hb[9 * q + 3 + e] = bodies[q].v[e];
+      hb[9 * q + 6 + e] = bodies[q].w[e];
+    }
+  std::vector<float> hbf(hb.begin(), hb.end());
+  ADM3(cudaMemcpyAsync(D.bodies, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
+  ADM3(cudaMemcpyAsync(D.bodies_f, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
+  // rows that hold solid nodes (the force reduction visits only those)
+  const size_t cells = static_cast<size_t>(d->pitch) * p->ny * p->nz;
+  std::vector<uint8_t> hm(cells);
+  ADM3(cudaMemcpyAsync(hm.data(), D.mask, cells, cudaMemcpyDeviceToHost, st));
+  ADM3(cudaStreamSynchronize(st));
+  d->put(dsh);
+  dsh = nullptr;
+  std::vector<int32_t> rows;
+  for (int r = 0; r < p->ny * p->nz; ++r) {
+    const uint8_t *m = hm.data() + static_cast<size_t>(r) * d->pitch;
+    for (int i = 0; i < p->nx; ++i)
+      if (m[i]) {
+        if (m[i] > nbodies) return bail(fail3(LBM_EINVAL, "mask holds body id %d > %d", m[i], nbodies));
+        rows.push_back(r);
+        break;
+      }
+  }
+  D.nfrows = static_cast<int32_t>(rows.size());
+  d->frows = d->get(sizeof(int32_t) * std::max<size_t>(1, rows.size()));
+  d->rowsum = d->get(sizeof(double) * 3 * std::max<size_t>(1, rows.size()) * std::max(1, nbodies));
+  if (!d->frows || !d->rowsum) return bail(fail3(LBM_ENOMEM, "force row lists allocation failed"));
+  D.frows = static_cast<const int32_t *>(d->frows);
+  D.rowsum = static_cast<double *>(d->rowsum);
+  if (!rows.empty())
+    ADM3(cudaMemcpyAsync(d->frows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, st));
+  // initial state: lattice A = f^eq(rho0, u0); lattice B, F_VP, ring, status zero
+  {
+    const int nrows = p->ny * p->nz;
+    dim3 g((d->pitch + 127) / 128, kQ3, std::min(nrows, 4096));
+    switch (p->storage) {
+      case LBM_F64: init3_kernel<LBM_F64><<<g, 128, 0, st>>>(static_cast<double *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
+      case LBM_F32: init3_kernel<LBM_F32><<<g, 128, 0, st>>>(static_cast<float *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
+      case LBM_F16S: init3_kernel<LBM_F16S><<<g, 128, 0, st>>>(static_cast<uint16_t *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
+      case LBM_BF16S: init3_kernel<LBM_BF16S><<<g, 128, 0, st>>>(static_cast<uint16_t *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
+    }
+    ADM3(cudaGetLastError());
+  }
+  ADM3(cudaMemsetAsync(D.lat[1], 0, L.lat, st));
+  ADM3(cudaMemsetAsync(D.fvp, 0, L.bodies_off - L.fvp_off, st));
+  ADM3(cudaMemsetAsync(D.ring, 0, L.status_off - L.ring_off, st));
+  ADM3(cudaMemsetAsync(D.status, 0, sizeof(int32_t), st));
+  ADM3(cudaMemcpyAsync(d->d_dom, &D, sizeof(Dom3), cudaMemcpyHostToDevice, st));
+  ADM3(cudaStreamSynchronize(st));
+#undef ADM3
+  d->grid = sms * sweep3_occupancy(p->storage);
+  *out = d;
+  return LBM_OK;
+}
+
+lbm_status lbm3_step(lbm3_domain *d, int64_t nsteps) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  if (nsteps < 0) return fail3(LBM_EINVAL, "nsteps must be >= 0");
+  if (d->p.force_every > 0) {
+    const long long produced = (d->done + nsteps) / d->p.force_every;
+    if (produced - d->drained > d->p.force_capacity)
+      return fail3(LBM_EBUSY, "force ring would overflow");
+  }
+  for (long long s = 0; s < nsteps; ++s) {
+    const long long n = d->done + s;
+    LBM3_CUDA(launch_sweep3(d, n, (d->parity + static_cast<int>(s & 1)) & 1));
+    LBM3_CUDA(launch_forces3(d, n));
+  }
+  d->done += nsteps;
+  d->parity = static_cast<int>((d->parity + nsteps) & 1);
+  return LBM_OK;
+}
+
+lbm_status lbm3_profile(lbm3_domain *d, int32_t steps, double *sweep_us, double *force_us) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  if (steps < 1) return fail3(LBM_EINVAL, "steps must be >= 1");
+  if (d->p.force_every > 0 && (d->done + steps) / d->p.force_every - d->drained > d->p.force_capacity)
+    return fail3(LBM_EBUSY, "force ring would overflow");
+  std::vector<cudaEvent_t> ev(3 * steps);
+  for (auto &e : ev) LBM3_CUDA(cudaEventCreate(&e));
+  for (int s = 0; s < steps; ++s) {
+    const long long n = d->done + s;
+    cudaEventRecord(ev[3 * s], d->st);
+    LBM3_CUDA(launch_sweep3(d, n, (d->parity + (s & 1)) & 1));
+    cudaEventRecord(ev[3 * s + 1], d->st);
+    LBM3_CUDA(launch_forces3(d, n));
+    cudaEventRecord(ev[3 * s + 2], d->st);
+  }
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  double a = 0.0, c = 0.0;
+  for (int s = 0; s < steps; ++s) {
+    float x = 0.f, y = 0.f;
+    cudaEventElapsedTime(&x, ev[3 * s], ev[3 * s + 1]);
+    cudaEventElapsedTime(&y, ev[3 * s + 1], ev[3 * s + 2]);
+    a += x;
+    c += y;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  d->done += steps;
+  d->parity = (d->parity + steps) & 1;
+  if (sweep_us) *sweep_us = 1000.0 * a / steps;
+  if (force_us) *force_us = 1000.0 * c / steps;
+  return LBM_OK;
+}
+
+lbm_status lbm3_forces(lbm3_domain *d, double *out, int64_t max_entries, int64_t *written) {
+  if (written) *written = 0;
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  lbm_status rc = read_status3(d);
+  const long long produced = d->p.force_every > 0 ? d->done / d->p.force_every : 0;
+  const long long n = std::min(produced - d->drained, std::max<long long>(0, max_entries));
+  if (n > 0 && !out) return fail3(LBM_EINVAL, "out is NULL");
+  const size_t per = 3 * static_cast<size_t>(d->nbodies);
+  long long copied = 0;
+  while (copied < n && per > 0) {
+    const long long e = d->drained + copied;
+    const long long pos = e % d->p.force_capacity;
+    const long long chunk = std::min(n - copied, static_cast<long long>(d->p.force_capacity) - pos);
+    LBM3_CUDA(cudaMemcpyAsync(out + copied * per, d->h.ring + pos * per, sizeof(double) * per * chunk,
+                              cudaMemcpyDeviceToHost, d->st));
+    copied += chunk;
+  }
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  d->drained += n;
+  if (written) *written = n;
+  return rc;
+}
+
+lbm_status lbm3_moments(lbm3_domain *d, double *rho, double *ux, double *uy, double *uz) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  const size_t cells = static_cast<size_t>(d->p.nx) * d->p.ny * d->p.nz;
+  double *tmp = static_cast<double *>(d->get(sizeof(double) * 4 * cells));
+  if (!tmp) return fail3(LBM_ENOMEM, "moments buffer allocation failed");
+  dim3 g((d->p.nx + 127) / 128, d->p.ny, d->p.nz);
+  double *t0 = tmp, *t1 = tmp + cells, *t2 = tmp + 2 * cells, *t3 = tmp + 3 * cells;
+  switch (d->p.storage) {
+    case LBM_F64: moments3_kernel<LBM_F64><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
+    case LBM_F32: moments3_kernel<LBM_F32><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
+    case LBM_F16S: moments3_kernel<LBM_F16S><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
+    case LBM_BF16S: moments3_kernel<LBM_BF16S><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  double *outs[4] = {rho, ux, uy, uz};
+  for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+    if (outs[q]) e = cudaMemcpyAsync(outs[q], tmp + q * cells, sizeof(double) * cells, cudaMemcpyDefault, d->st);
+  cudaStreamSynchronize(d->st);
+  d->put(tmp);
+  if (e != cudaSuccess) return fail3(LBM_ECUDA, "moments failed: %s", cudaGetErrorString(e));
+  return read_status3(d);
+}
+
+static lbm_status pops3(lbm3_domain *d, void *out, const void *in, size_t bytes) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  const size_t es = esize(d->p.storage);
+  const size_t want = es * kQ3 * static_cast<size_t>(d->p.nx) * d->p.ny * d->p.nz;
+  if (bytes != want) return fail3(LBM_EINVAL, "population buffer must be %zu bytes (got %zu)", want, bytes);
+  char *lat = static_cast<char *>(d->h.lat[d->parity]);
+  const size_t rowb = es * d->p.nx, pitchb = es * d->pitch;
+  const size_t rows = static_cast<size_t>(kQ3) * d->p.ny * d->p.nz;
+  if (out) LBM3_CUDA(cudaMemcpy2DAsync(out, rowb, lat, pitchb, rowb, rows, cudaMemcpyDefault, d->st));
+  else if (in) LBM3_CUDA(cudaMemcpy2DAsync(lat, pitchb, in, rowb, rowb, rows, cudaMemcpyDefault, d->st));
+  else return fail3(LBM_EINVAL, "buffer is NULL");
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  return LBM_OK;
+}
+
+lbm_status lbm3_get_populations(lbm3_domain *d, void *out, size_t bytes) {
+  if (!out) return fail3(LBM_EINVAL, "out is NULL");
+  return pops3(d, out, nullptr, bytes);
+}
+
+lbm_status lbm3_set_populations(lbm3_domain *d, const void *in, size_t bytes) {
+  if (!in) return fail3(LBM_EINVAL, "in is NULL");
+  return pops3(d, nullptr, in, bytes);
+}
+
+lbm_status lbm3_get_mask(lbm3_domain *d, uint8_t *out) {
+  if (!d || !out) return fail3(LBM_EINVAL, "domain or out is NULL");
+  LBM3_CUDA(cudaMemcpy2DAsync(out, d->p.nx, d->h.mask, d->pitch, d->p.nx,
+                              static_cast<size_t>(d->p.ny) * d->p.nz, cudaMemcpyDefault, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  return LBM_OK;
+}
+
+lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  if (steps) *steps = d->done;
+  return LBM_OK;
+}
+
+lbm_status lbm3_domain_destroy(lbm3_domain *d) {
+  if (!d) return LBM_OK;
+  cudaStreamSynchronize(d->st);
+  d->put(d->block);
+  d->put(d->frows);
+  d->put(d->rowsum);
+  d->put(d->d_dom);
+  cudaStreamSynchronize(d->st);
+  delete d;
+  return LBM_OK;
+}
+
+}  // extern "C"

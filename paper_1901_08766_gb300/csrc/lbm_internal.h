@@ -121,6 +121,8 @@ cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *
                           const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
                           int s);
 void fill_cell_const(DomDev &d, int storage);
+// the message lbm_last_error returns (shared by the 2D and 3D entry points)
+void set_last_error(const char *msg);
 cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
 // moving domains: after the sweep of a step, per-row -F_VP sums over the mask it used,
 // then the mask and body centres of the next step index

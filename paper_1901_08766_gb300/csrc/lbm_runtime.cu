@@ -18,8 +18,12 @@
 
 namespace lbm {
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+void set_last_error(const char *msg) { g_last_error = msg; }
+
+namespace {
 
 lbm_status fail(lbm_status s, const char *fmt, ...) {
   char buf[512];

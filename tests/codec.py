@@ -11,6 +11,21 @@ import numpy as np
 import oracle
 
 W = oracle.W[:, None, None]
+_W3 = None
+
+
+def _weights(g):
+    """Shift weights broadcast over populations [9, ny, nx] (D2Q9) or [19, nz, ny, nx]
+    (D3Q19, the 3D oracle's weights)."""
+    global _W3
+    if np.shape(g)[0] == 9:
+        return W
+    if _W3 is None:
+        from oracle import d3q19
+        _W3 = d3q19.lattice()[3][:, None, None, None]
+    return _W3
+
+
 F16_SCALE = 1024.0  # F16S stores F16_SCALE * (f - w rho0)
 
 
@@ -26,12 +41,13 @@ def bf16_bits_to_f64(bits):
 
 
 def encode(g, storage, rho0=1.0):
-    """FP64 populations [9, ny, nx] -> stored array in the library's layout."""
+    """FP64 populations [9, ny, nx] or [19, nz, ny, nx] -> stored array in the library's
+    layout."""
     if storage == "f64":
         return np.ascontiguousarray(g, dtype=np.float64)
     if storage == "f32":
         return np.ascontiguousarray(g, dtype=np.float32)
-    s = g - W * rho0
+    s = g - _weights(g) * rho0
     if storage == "f16s":
         return np.ascontiguousarray((s * F16_SCALE).astype(np.float32).astype(np.float16))
     if storage == "bf16s":
@@ -44,9 +60,9 @@ def decode(raw, storage, rho0=1.0):
     if storage in ("f64", "f32"):
         return np.asarray(raw, dtype=np.float64)
     if storage == "f16s":
-        return np.asarray(raw, dtype=np.float16).astype(np.float64) / F16_SCALE + W * rho0
+        return np.asarray(raw, dtype=np.float16).astype(np.float64) / F16_SCALE + _weights(raw) * rho0
     if storage == "bf16s":
-        return bf16_bits_to_f64(raw) + W * rho0
+        return bf16_bits_to_f64(raw) + _weights(raw) * rho0
     raise KeyError(storage)
 
 
@@ -66,9 +82,15 @@ def stored_ulp(values_shifted, storage):
 def ghost_ulp(spec, storage):
     """One unit of the stored type at the inlet ghost populations f^eq(rho0, u_in) (shifted
     for the 16-bit types): the library holds the ghost as the stored type would."""
-    g = oracle.equilibrium(spec["rho0"], *spec["u_in"])
+    if "nz" in spec:
+        from oracle import d3q19
+        g = d3q19.equilibrium(spec["rho0"], spec["u_in"])
+        w = d3q19.lattice()[3]
+    else:
+        g = oracle.equilibrium(spec["rho0"], *spec["u_in"])
+        w = oracle.W
     if storage in ("f16s", "bf16s"):
-        g = g - oracle.W
+        g = g - w
     if storage == "f64":
         return 0.0
     return float(stored_ulp(g, storage).max())
@@ -76,17 +98,18 @@ def ghost_ulp(spec, storage):
 
 def step_tol(want, storage, spec=None, arith=None):
     """Per-population bound for one step of a reduced storage against the oracle's FP64
-    result `want` (populations [9, ny, nx]) from the same decoded state.
+    result `want` (populations [9, ny, nx] or [19, nz, ny, nx]) from the same decoded state.
 
     Every stored value is within one unit of the stored type of the FP64 result: FP32
     rounds to nearest (ties either way), the 16-bit storages round stochastically to
     one of the two neighbours; FP32 arithmetic adds `arith`. For the 16-bit storages the
-    rest population is stored as the pulled mass minus the eight rounded moving
+    rest population is stored as the pulled mass minus the rounded moving (8 or 18)
     populations, so it also carries their rounding residuals: up to one unit of each.
     With an inlet, the library holds the ghost populations as the stored type would:
-    one more unit of the ghost's magnitude at column 0 (and the three ghost values enter
+    one more unit of the ghost's magnitude at column 0 (and the 3 or 5 ghost values enter
     the rest population's pulled mass)."""
-    shift = W if storage != "f32" else 0.0
+    shift = _weights(want) if storage != "f32" else 0.0
+    n_in = 3 if np.shape(want)[0] == 9 else 5  # directions entering from x = -1
     if arith is None:
         arith = 3e-7 if storage == "f32" else 2e-8
     g = 0.0
@@ -97,10 +120,10 @@ def step_tol(want, storage, spec=None, arith=None):
     # below a power of two may round into the next binade, whose unit is twice as large)
     ulp = stored_ulp(mag + arith + g, storage)
     tol = ulp + arith
-    tol[:, :, 0] += g
+    tol[..., 0] += g
     if storage in ("f16s", "bf16s"):
         carried = ulp[1:].sum(axis=0)
-        carried[:, 0] += 3 * g
+        carried[..., 0] += n_in * g
         ulp0 = stored_ulp(mag[0] + arith + carried, storage)
         tol[0] = ulp0 + carried + arith
     return tol

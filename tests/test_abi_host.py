@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "lbm.h")
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^LBM_API [^(]*?\b(lbm_\w+)\(", txt, flags=re.M)))
+    return sorted(set(re.findall(r"^LBM_API [^(]*?\b(lbm3?_\w+)\(", txt, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -120,3 +120,84 @@ def test_no_cpu_fallback(lib):
             _native.load(os.path.join(ROOT, "does_not_exist.so"))
         finally:
             _native._lib = saved
+
+
+# ---- 3D (D3Q19) ABI ---------------------------------------------------------------------
+
+def _sphere_spec3():
+    return synth.spec3("sphere_40x24x20", 40, 24, 20, 0.05, [synth.sphere(1, (12.3, 11.6, 9.7), 4.2)],
+                       [synth.body3((12.3, 11.6, 9.7), 8.4)], 10, 0.05, synth.channel_edges3(),
+                       u_in=(0.05, 0.0, 0.0), u0=(0.05, 0.0, 0.0))
+
+
+def test_params3_default_and_bytes(lib):
+    from paper_1901_08766_gb300 import _native
+    L = lib.load()
+    p = _native.Params3()
+    L.lbm3_params_default(C.byref(p))
+    assert (p.nx, p.ny, p.nz, p.storage, p.force_every, p.force_capacity) == (32, 32, 32, 1, 1, 8192)
+    assert p.magic_lambda == 3 / 16 and p.eta == 1e-4 and p.rho0 == 1.0 and p.nu == 0.1
+    spec = _sphere_spec3()
+    sizes = {}
+    for st in ("f64", "f32", "f16s"):
+        q = _native.params3_from_spec(spec, st)
+        sizes[st] = L.lbm3_domain_bytes(C.byref(q), 1)
+    pitch, nodes = 64, 24 * 20
+    lat = {st: 2 * 19 * nodes * pitch * e for st, e in (("f64", 8), ("f32", 4), ("f16s", 2))}
+    for st in sizes:
+        assert sizes[st] >= lat[st] + nodes * pitch + 8192 * 3 * 8
+    # lattices x2 and the F_VP field (3 doubles vs 3 floats per node) differ
+    assert sizes["f64"] - sizes["f16s"] == pytest.approx(lat["f64"] - lat["f16s"] + nodes * pitch * 12,
+                                                         abs=2048)
+
+
+BAD3 = [("nz", 2), ("nx", 1), ("nu", -1.0), ("eta", 0.0), ("bottom", 1), ("top", 2),
+        ("south", 2), ("storage", 7), ("force_capacity", -1)]
+
+
+@pytest.mark.parametrize("field,value", BAD3)
+def test_invalid_3d_parameters_rejected_before_cuda(lib, field, value):
+    from paper_1901_08766_gb300 import _native
+    L = lib.load()
+    spec = _sphere_spec3()
+    p = _native.params3_from_spec(spec, "f32")
+    setattr(p, field, value)
+    if field == "nu":
+        p.tau_plus = 0.4
+    shapes, ns = _native.shapes3_from_spec(spec)
+    bodies, nb = _native.bodies3_from_spec(spec)
+    h = C.c_void_p()
+    st = L.lbm3_domain_create(C.byref(p), shapes, ns, bodies, nb, None, _native.ALLOC_FN(),
+                              _native.FREE_FN(), None, C.byref(h))
+    assert st == 1, L.lbm_last_error()
+    assert h.value is None and len(L.lbm_last_error()) > 0
+
+
+def test_3d_shape_body_ids_checked(lib):
+    from paper_1901_08766_gb300 import _native
+    L = lib.load()
+    spec = _sphere_spec3()
+    spec["shapes"][0]["body"] = 2  # only one body
+    p = _native.params3_from_spec(spec, "f32")
+    shapes, ns = _native.shapes3_from_spec(spec)
+    bodies, nb = _native.bodies3_from_spec(spec)
+    h = C.c_void_p()
+    st = L.lbm3_domain_create(C.byref(p), shapes, ns, bodies, nb, None, _native.ALLOC_FN(),
+                              _native.FREE_FN(), None, C.byref(h))
+    assert st == 1 and b"body id" in L.lbm_last_error()
+
+
+def test_3d_no_cpu_fallback(lib):
+    import torch
+    from paper_1901_08766_gb300 import _native
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = lib.load()
+    spec = _sphere_spec3()
+    p = _native.params3_from_spec(spec, "f32")
+    shapes, ns = _native.shapes3_from_spec(spec)
+    bodies, nb = _native.bodies3_from_spec(spec)
+    h = C.c_void_p()
+    st = L.lbm3_domain_create(C.byref(p), shapes, ns, bodies, nb, None, _native.ALLOC_FN(),
+                              _native.FREE_FN(), None, C.byref(h))
+    assert st == 3 and h.value is None

@@ -1,0 +1,157 @@
+"""3D (D3Q19) GPU path vs the FP64 3D oracle, element by element, through the C ABI.
+
+FP64 storage must match the oracle to 1e-12 relative per population after 1000 steps
+(every edge rule, moving and rotating bodies, several strips per row and a ragged
+tail); the reduced storages are checked one step at a time within one unit of the
+stored type (the rest population also carries the rounding residuals of the eighteen
+moving ones); the sphere/cylinder mask must be bit-exact.
+"""
+import numpy as np
+import pytest
+
+import codec
+import synth
+from oracle import d3q19 as ora3
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(name):
+    if name == "sphere_channel_150x20x12":
+        c = (40.3, 9.6, 5.7)
+        return synth.spec3(name, 150, 20, 12, 0.04, [synth.sphere(1, c, 4.3)], [synth.body3(c, 8.6)],
+                           0, 0.05, synth.channel_edges3(), u_in=(0.05, 0.0, 0.0), u0=(0.05, 0.0, 0.0))
+    if name == "periodic_bodies_97x18x14":
+        c1, c2 = (30.2, 8.7, 6.4), (70.6, 9.3, 0.0)
+        return synth.spec3(name, 97, 18, 14, 0.1,
+                           [synth.sphere(1, c1, 4.6), synth.cylinder_z(2, c2[0], c2[1], 3.2)],
+                           [synth.body3(c1, 9.2, v=(0.01, -0.005, 0.003), w=(0.001, -0.002, 0.0015)),
+                            synth.body3(c2, 6.4, v=(-0.004, 0.002, 0.0), w=(0.0, 0.0, 0.003))],
+                           0, 0.01, synth.edges3(), magic_lambda=0.25)
+    if name == "slip_y_periodic_z_70x16x22":
+        c = (20.5, 7.5, 0.0)
+        e = synth.edges3("periodic", "periodic", "free_slip", "free_slip", "periodic", "periodic")
+        return synth.spec3(name, 70, 16, 22, 0.02, [synth.cylinder_z(1, c[0], c[1], 3.7)],
+                           [synth.body3(c, 7.4)], 0, 0.02, e, u0=(0.02, 0.0, 0.01))
+    if name == "inlet_periodic_y_slip_z_261x10x9":
+        c = (60.4, 5.2, 4.1)
+        e = synth.edges3("inlet", "outflow", "periodic", "periodic", "free_slip", "free_slip")
+        return synth.spec3(name, 261, 10, 9, 0.05, [synth.sphere(1, c, 3.1)], [synth.body3(c, 6.2)], 0,
+                           0.04, e, u_in=(0.04, 0.003, -0.002), u0=(0.04, 0.0, 0.0), eta=1e-6)
+    raise KeyError(name)
+
+
+CASES = ["sphere_channel_150x20x12", "periodic_bodies_97x18x14", "slip_y_periodic_z_70x16x22",
+         "inlet_periodic_y_slip_z_261x10x9"]
+
+
+def _start(lbm, spec, storage, seed):
+    g0 = synth.random_populations3(seed, spec["nx"], spec["ny"], spec["nz"], 0.1)
+    raw0 = codec.encode(g0, storage)
+    dom = lbm.Domain3(spec, storage=storage)
+    dom.set_populations(raw0)
+    return dom, codec.decode(raw0, storage)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fp64_3d_matches_oracle_1000_steps(lbm, case):
+    spec = _case(case)
+    dom, g0 = _start(lbm, spec, "f64", 11)
+    f_gpu = dom.run(1000)
+    raw = dom.get_populations()
+    dom.close()
+    ora = ora3.Domain(spec, g=g0)
+    f_ora = ora.run(1000)
+    rel = np.abs(raw - ora.g) / np.abs(ora.g)
+    assert rel.max() <= 1e-12, f"max relative population difference {rel.max():.3e}"
+    assert f_gpu.shape == f_ora.shape == (1000, len(spec["bodies"]), 3)
+    scale = np.abs(f_ora).max()
+    assert np.abs(f_gpu - f_ora).max() <= 1e-10 * scale + 1e-14
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_3d_mask_bit_exact(lbm, case):
+    spec = _case(case)
+    dom = lbm.Domain3(spec, storage="f32")
+    m = dom.mask()
+    dom.close()
+    want = ora3.rasterize(spec)
+    assert m.sum() > 0
+    np.testing.assert_array_equal(m, want)
+
+
+def test_3d_initial_state_and_moments(lbm):
+    spec = _case("periodic_bodies_97x18x14")
+    dom, g0 = _start(lbm, spec, "f64", 5)
+    dom.step(3)
+    rho, ux, uy, uz = dom.moments()
+    raw = dom.get_populations()
+    dom.close()
+    ora = ora3.Domain(spec, g=g0)
+    ora.run(3, want_forces=False)
+    np.testing.assert_allclose(raw, ora.g, rtol=1e-13, atol=0)
+    for a, b in zip((rho, ux, uy, uz), ora.moments()):
+        np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-15)
+    # a fresh domain starts from f^eq(rho0, u0)
+    spec = _case("slip_y_periodic_z_70x16x22")
+    dom = lbm.Domain3(spec, storage="f64")
+    g = dom.get_populations()
+    dom.close()
+    np.testing.assert_allclose(g, ora3.Domain(spec).g, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("case", ["sphere_channel_150x20x12", "periodic_bodies_97x18x14"])
+def test_reduced_storage_one_step(lbm, storage, case):
+    spec = _case(case)
+    dom, g0 = _start(lbm, spec, storage, 3)
+    dom.step(1)
+    got = codec.decode(dom.get_populations(), storage)
+    dom.close()
+    ora = ora3.Domain(spec, g=g0)
+    ora.step_once()
+    tol = codec.step_tol(ora.g, storage, spec)
+    err = np.abs(got - ora.g)
+    assert (err <= tol).all(), f"worst excess {(err - tol).max():.3e} at {np.unravel_index(np.argmax(err - tol), err.shape)}"
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_reduced_storage_200_steps_drift(lbm, storage):
+    # over many steps the reduced storages stay close to the FP64 oracle: bound the
+    # velocity error at 1 percent of the inflow speed and the density error at 1e-4
+    spec = _case("sphere_channel_150x20x12")
+    dom, g0 = _start(lbm, spec, storage, 9)
+    dom.step(200)
+    rho, ux, uy, uz = dom.moments()
+    dom.close()
+    ora = ora3.Domain(spec, g=g0)
+    ora.run(200, want_forces=False)
+    r, x, y, z = ora.moments()
+    assert np.abs(rho - r).max() < 1e-4
+    for a, b in ((ux, x), (uy, y), (uz, z)):
+        assert np.abs(a - b).max() < 0.01 * spec["U"]
+
+
+def test_3d_divergence_reported(lbm):
+    spec = _case("periodic_bodies_97x18x14")
+    dom = lbm.Domain3(spec, storage="f64")
+    dom.set_populations(np.zeros((19, spec["nz"], spec["ny"], spec["nx"])))
+    dom.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        dom.forces()
+    assert e.value.status == 4
+    dom.close()
+
+
+def test_3d_force_ring_and_steps(lbm):
+    spec = _case("sphere_channel_150x20x12")
+    dom = lbm.Domain3(spec, storage="f32", force_every=2, force_capacity=4)
+    dom.step(8)
+    with pytest.raises(lbm.LbmError) as e:
+        dom.step(2)  # a fifth undrained entry
+    assert e.value.status == 6
+    f = dom.forces()
+    assert f.shape == (4, 1, 3) and np.isfinite(f).all()
+    assert dom.steps_done() == 8
+    assert f[-1, 0, 0] != 0.0
+    dom.close()
