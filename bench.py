@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -475,8 +476,57 @@ def experiment(args):
             for r in rows:
                 for k in ("cd_mean", "cl_rms", "st"):
                     r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
+    elif args.experiment == "sphere3d":
+        out.update(sphere3d(lbm, torch, np))
     print(json.dumps(out), flush=True)
     return 0
+
+
+# bytes of one D3Q19 node per sweep: 19 populations read and written, the mask byte read
+BYTES3 = {"f16s": 19 * 2 * 2 + 1, "bf16s": 19 * 2 * 2 + 1, "f32": 19 * 4 * 2 + 1, "f64": 19 * 8 * 2 + 1}
+
+
+def sphere3d(lbm, torch, np):
+    """3D (D3Q19) sweep throughput per storage on a sphere channel larger than L2, and
+    the drag coefficient of each storage against FP64 on a smaller sphere channel."""
+    import synth
+    peak = _peak_hbm()
+    perf = []
+    spec = synth.sphere_channel(384, 128, 128, D=32.0)
+    nodes = spec["nx"] * spec["ny"] * spec["nz"]
+    for st in ("f16s", "bf16s", "f32", "f64"):
+        d = lbm.Domain3(spec, storage=st, force_every=1)
+        d.step(20)
+        d.forces()
+        best = (1e30, 0.0)
+        for _ in range(3):
+            sw, fo = d.profile(30)
+            d.forces()
+            best = min(best, (sw, fo))
+        d.close()
+        sw, fo = best
+        gbs = nodes * BYTES3[st] / sw / 1e3
+        perf.append({"storage": st, "grid": [spec["nx"], spec["ny"], spec["nz"]], "sweep_us": sw,
+                     "force_us": fo, "glups_sweep": nodes / sw / 1e3,
+                     "glups_step": nodes / (sw + fo) / 1e3, "bytes_per_node": BYTES3[st],
+                     "achieved_gbs": gbs, "peak_gbs": peak[0], "frac": gbs / peak[0],
+                     "peak_source": peak[1]})
+    acc = []
+    spec = synth.sphere_channel(192, 64, 64, D=16.0, re=100.0, steps=4000)
+    D, U = spec["bodies"][0]["ref_length"], spec["U"]
+    area = math.pi * D * D / 4.0
+    for st in ("f16s", "bf16s", "f32", "f64"):
+        d = lbm.Domain3(spec, storage=st)
+        f = d.run(spec["steps"])
+        d.close()
+        cd = f[:, 0, 0] / (0.5 * spec["rho0"] * U * U * area)
+        acc.append({"storage": st, "steps": spec["steps"], "cd_last_1000": float(cd[-1000:].mean()),
+                    "cy_last_1000": float((f[-1000:, 0, 1] / (0.5 * U * U * area)).mean())})
+    ref = acc[-1]["cd_last_1000"]
+    for r in acc:
+        r["cd_rel_vs_f64"] = (r["cd_last_1000"] - ref) / ref
+    return {"perf": perf, "drag": acc, "case_perf": "sphere channel 384x128x128, D=32, Re=100",
+            "case_drag": spec["name"]}
 
 
 def main():
@@ -498,7 +548,7 @@ def main():
     ap.add_argument("--served-requests", type=int, default=32)
     ap.add_argument("--served-scale", type=float, default=0.02)
     ap.add_argument("--served-chunk", type=int, default=256)
-    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder"], default=None,
+    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d"], default=None,
                     help="accuracy study instead of the benchmark")
     args = ap.parse_args()
     if args.experiment:

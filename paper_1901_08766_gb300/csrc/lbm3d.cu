@@ -49,6 +49,11 @@ template <typename T> struct Const3 {
   T ghost[kQ3];  // inlet populations in compute space, as a stored node holds them
 };
 
+// force-free constants duplicated for paired FP32 (both halves of a node pair)
+struct Pair3 {
+  float2 one_m_omp, hp, hm, rho0, pw0, pw1, pw2, mw1, mw2;
+};
+
 struct Dom3 {
   void *lat[2];
   uint8_t *mask;
@@ -57,13 +62,15 @@ struct Dom3 {
   float *bodies_f;
   double *ring;           // [cap][nbodies][3]
   double *rowsum;         // [nfrows][nbodies][3]
-  const int32_t *frows;   // rows (k * ny + j) holding solid nodes, ascending
+  const int4 *frows;      // rows holding solid nodes, ascending: (k * ny + j, first, last + 1, 0)
   int32_t *status;
+  uint32_t *rows_done;    // blocks of the force reduction that finished (reset by the last)
   int32_t nx, ny, nz, pitch, nfrows;
   int32_t west, east, south, north, bottom, top;
   int32_t nbodies, force_every, force_cap;
   Const3<float> cf;
   Const3<double> cd;
+  Pair3 pc;
 };
 
 template <typename T> __device__ __forceinline__ const Const3<T> &const3(const Dom3 &d);
@@ -174,18 +181,32 @@ __device__ __forceinline__ void collide3(T (&x)[kQ3], const Macro3<T> &m, const 
 // (the 2D rule: moving values rounded first, the rest value stored as the pulled mass
 // minus their rounded sum, pairs summed in a fixed order)
 template <int S>
-__device__ __forceinline__ void encode3_pair(const float (&x0)[kQ3], const float (&x1)[kQ3], F2 d,
-                                             uint32_t bits, uint32_t (&w)[kQ3]) {
+__device__ __forceinline__ void encode3_pair(const F2 (&x)[kQ3], F2 d, uint32_t bits, uint32_t (&w)[kQ3]) {
   F2 sp[10];
 #pragma unroll
   for (int p = 1; p <= 9; ++p) {
-    w[2 * p - 1] = Codec<S>::enc2_sr(x0[2 * p - 1], x1[2 * p - 1], bits);
-    w[2 * p] = Codec<S>::enc2_sr(x0[2 * p], x1[2 * p], bits);
+    w[2 * p - 1] = Codec<S>::enc2_sr(x[2 * p - 1].v.x, x[2 * p - 1].v.y, bits);
+    w[2 * p] = Codec<S>::enc2_sr(x[2 * p].v.x, x[2 * p].v.y, bits);
     sp[p] = F2(Codec<S>::dec2(w[2 * p - 1])) + F2(Codec<S>::dec2(w[2 * p]));
   }
   const F2 moved = (((sp[1] + sp[2]) + sp[3]) + (((sp[4] + sp[5]) + (sp[6] + sp[7])) + (sp[8] + sp[9])));
   const F2 rest = d - moved;
   w[0] = Codec<S>::enc2_sr(rest.v.x, rest.v.y, bits);
+}
+
+// constants of the force-free update broadcast to both halves of a node pair
+__device__ __forceinline__ Const3<F2> pair_const3(const Pair3 &c) {
+  Const3<F2> p;
+  p.one_m_omp = F2(c.one_m_omp);
+  p.hp = F2(c.hp);
+  p.hm = F2(c.hm);
+  p.rho0 = F2(c.rho0);
+  p.pw0 = F2(c.pw0);
+  p.pw1 = F2(c.pw1);
+  p.pw2 = F2(c.pw2);
+  p.mw1 = F2(c.mw1);
+  p.mw2 = F2(c.mw2);
+  return p;
 }
 
 // source row of direction a for row (j, k): y rule, then z rule
@@ -209,11 +230,25 @@ __device__ __forceinline__ void src_row3(const Dom3 &D, int a, int j, int k, int
   }
 }
 
+// Launch shape per storage (measured on the 384 x 128 x 128 sphere channel): the 16-bit
+// sweeps run 256-thread blocks, two per SM (128 registers); FP32/FP64 128-thread blocks,
+// three per SM (168 registers). Paired FP32 is used where it measured faster (BF16S).
+template <int S> struct Sweep3Shape {
+  static constexpr bool k16 = S == LBM_F16S || S == LBM_BF16S;
+  static constexpr int kThreads = k16 ? 256 : 128;
+  static constexpr int kMinBlocks = k16 ? 2 : 3;
+  static constexpr bool kPaired = S == LBM_BF16S;
+  static constexpr int kV = S == LBM_F64 ? 2 : 4;
+};
+
 // The fused 3D sweep: one warp per strip of 32 V cells of one row (j, k) at a time
 // (persistent grid), nineteen vector loads per lane, the +-1 x-shift by shuffles, strip
-// ends by broadcast loads, update, nineteen vector stores into the other lattice.
+// ends by broadcast loads, update, nineteen vector stores into the other lattice. With
+// 16-bit storage, warps without solid nodes update two nodes at once in paired FP32
+// (the same operations in the same order on each half).
 template <int S, int V>
-__global__ void __launch_bounds__(256) sweep3_kernel(const Dom3 *dom, long long n, int par) {
+__global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMinBlocks)
+    sweep3_kernel(const __grid_constant__ Dom3 dom, long long n, int par) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
   using T = typename Cd::T;
@@ -222,7 +257,7 @@ __global__ void __launch_bounds__(256) sweep3_kernel(const Dom3 *dom, long long 
   constexpr int kStrip = 32 * V;
   constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
   constexpr T kUnscale = T(1) / T(Cd::kScale);
-  const Dom3 &D = *dom;
+  const Dom3 &D = dom;  // kernel parameter: constants are read from the parameter bank
   const Const3<T> &C = const3<T>(D);
   const int lane = threadIdx.x & 31;
   const int nx = D.nx, ny = D.ny, nz = D.nz, pitch = D.pitch;
@@ -329,21 +364,51 @@ __global__ void __launch_bounds__(256) sweep3_kernel(const Dom3 *dom, long long 
     };
     if constexpr (sizeof(E) == 2) {
       const uint32_t sr_g = sr_group_bits(sr_row_key(n, row), xl);
+      if (Sweep3Shape<S>::kPaired && !any_solid) {
+        const Const3<F2> CP = pair_const3(D.pc);
 #pragma unroll
-      for (int q = 0; q < V; q += 2) {
-        T x0v[kQ3], x1v[kQ3];
+        for (int q = 0; q < V; q += 2) {
+          F2 x[kQ3];
 #pragma unroll
-        for (int a = 0; a < kQ3; ++a) {
-          const float2 p = Cd::dec2(v[a].w[q >> 1]);
-          x0v[a] = p.x;
-          x1v[a] = p.y;
+          for (int a = 0; a < kQ3; ++a) x[a] = F2(Cd::dec2(v[a].w[q >> 1]));
+          if (q == 0 && west_edge && west_inlet) {
+            const bool g = lane == 0;
+            x[1].v.x = g ? C.ghost[1] : x[1].v.x;
+            x[7].v.x = g ? C.ghost[7] : x[7].v.x;
+            x[9].v.x = g ? C.ghost[9] : x[9].v.x;
+            x[11].v.x = g ? C.ghost[11] : x[11].v.x;
+            x[13].v.x = g ? C.ghost[13] : x[13].v.x;
+          }
+          const F2 uo[3] = {F2(0.f), F2(0.f), F2(0.f)};
+          const Macro3<F2> m = macro3<F2, SHIFT, false>(x, CP, false, uo);
+          collide3<F2, SHIFT, false>(x, m, CP);
+          bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
+          bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (q + 1);
+          uint32_t w[kQ3];
+          encode3_pair<S>(x, m.d, sr_pair_bits(sr_g, xl + q), w);
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) v[a].w[q >> 1] = w[a];
         }
-        const float d0 = update(x0v, q);
-        const float d1 = update(x1v, q + 1);
-        uint32_t w[kQ3];
-        encode3_pair<S>(x0v, x1v, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
+      } else {
 #pragma unroll
-        for (int a = 0; a < kQ3; ++a) v[a].w[q >> 1] = w[a];
+        for (int q = 0; q < V; q += 2) {
+          T x0v[kQ3], x1v[kQ3];
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) {
+            const float2 p = Cd::dec2(v[a].w[q >> 1]);
+            x0v[a] = p.x;
+            x1v[a] = p.y;
+          }
+          const float d0 = update(x0v, q);
+          const float d1 = update(x1v, q + 1);
+          F2 x[kQ3];
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) x[a] = F2(make_float2(x0v[a], x1v[a]));
+          uint32_t w[kQ3];
+          encode3_pair<S>(x, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
+#pragma unroll
+          for (int a = 0; a < kQ3; ++a) v[a].w[q >> 1] = w[a];
+        }
       }
     } else {
 #pragma unroll
@@ -467,20 +532,24 @@ __global__ void rasterize3_kernel(uint8_t *mask, int nx, int ny, int nz, int pit
 }
 
 // Body forces of step index n (the sweep just computed step n + 1): one warp per listed
-// row sums -F_VP per body (lane-strided, fixed shuffle tree), then one block per body adds
-// the rows in list order into the ring entry.
+// row sums -F_VP per body over the row's solid column range (lane-strided, fixed shuffle
+// tree); the last block to finish then adds the rows in list order (thread-strided, fixed
+// tree) into the ring entry. The result does not depend on which block finishes last.
+constexpr int kRowsThreads = 256;
+
 template <typename T>
-__global__ void rows3_kernel(const Dom3 *dom) {
+__global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const Dom3 *dom, long long entry) {
   const Dom3 &D = *dom;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int q = wg; q < D.nfrows; q += nw) {
-    const size_t row = static_cast<size_t>(D.frows[q]);
+    const int4 it = D.frows[q];
+    const size_t row = static_cast<size_t>(it.x);
     const uint8_t *m = D.mask + row * D.pitch;
     const T *fv = static_cast<const T *>(D.fvp) + 3 * row * D.pitch;
     for (int body = 1; body <= D.nbodies; ++body) {
       double f[3] = {0.0, 0.0, 0.0};
-      for (int i = lane; i < D.nx; i += 32)
+      for (int i = it.y + lane; i < it.z; i += 32)
         if (m[i] == body)
           for (int e = 0; e < 3; ++e) f[e] -= double(fv[3 * i + e]);
 #pragma unroll
@@ -490,32 +559,35 @@ __global__ void rows3_kernel(const Dom3 *dom) {
         for (int e = 0; e < 3; ++e) D.rowsum[(static_cast<size_t>(q) * D.nbodies + body - 1) * 3 + e] = f[e];
     }
   }
-}
-
-constexpr int kSumThreads = 256;
-
-__global__ void __launch_bounds__(kSumThreads) sum3_kernel(const Dom3 *dom, long long entry) {
-  const Dom3 &D = *dom;
-  const int body = blockIdx.x + 1;
-  __shared__ double red[3][kSumThreads / 32];
-  double f[3] = {0.0, 0.0, 0.0};
-  for (int q = threadIdx.x; q < D.nfrows; q += blockDim.x)
-    for (int e = 0; e < 3; ++e) f[e] += D.rowsum[(static_cast<size_t>(q) * D.nbodies + body - 1) * 3 + e];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-    for (int e = 0; e < 3; ++e) f[e] += __shfl_down_sync(0xffffffffu, f[e], off);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int e = 0; e < 3; ++e) red[e][warp] = f[e];
+  __shared__ bool last;
+  __shared__ double red[3][kRowsThreads / 32];
+  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double *slot = D.ring + (static_cast<size_t>(entry % D.force_cap) * D.nbodies + body - 1) * 3;
-    for (int e = 0; e < 3; ++e) {
-      double t = 0.0;
-      for (int w = 0; w < kSumThreads / 32; ++w) t += red[e][w];
-      slot[e] = t;
+  if (threadIdx.x == 0) last = atomicAdd(D.rows_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int body = 1; body <= D.nbodies; ++body) {
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int q = threadIdx.x; q < D.nfrows; q += blockDim.x)
+      for (int e = 0; e < 3; ++e) f[e] += __ldcg(D.rowsum + (static_cast<size_t>(q) * D.nbodies + body - 1) * 3 + e);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+      for (int e = 0; e < 3; ++e) f[e] += __shfl_down_sync(0xffffffffu, f[e], off);
+    if (lane == 0)
+      for (int e = 0; e < 3; ++e) red[e][warp] = f[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double *slot = D.ring + (static_cast<size_t>(entry % D.force_cap) * D.nbodies + body - 1) * 3;
+      for (int e = 0; e < 3; ++e) {
+        double t = 0.0;
+        for (int w = 0; w < kRowsThreads / 32; ++w) t += red[e][w];
+        slot[e] = t;
+      }
     }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *D.rows_done = 0u;
 }
 
 }  // namespace d3
@@ -615,7 +687,8 @@ struct lbm3_domain {
   Dom3 *d_dom = nullptr;
   long long done = 0, drained = 0;
   int parity = 0;
-  int grid = 0;
+  int grid = 0;      // sweep blocks
+  int aux_grid = 0;  // force-row reduction blocks
   void *get(size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (afn) return afn(bytes, actx);
@@ -635,34 +708,30 @@ struct lbm3_domain {
 
 namespace {
 
-cudaError_t launch_sweep3(lbm3_domain *d, long long n, int par) {
-  switch (d->p.storage) {
-    case LBM_F64: sweep3_kernel<LBM_F64, 2><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
-    case LBM_F32: sweep3_kernel<LBM_F32, 4><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
-    case LBM_F16S: sweep3_kernel<LBM_F16S, 4><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
-    case LBM_BF16S: sweep3_kernel<LBM_BF16S, 4><<<d->grid, 256, 0, d->st>>>(d->d_dom, n, par); break;
-    default: return cudaErrorInvalidValue;
-  }
+template <int S> cudaError_t launch_sweep3_as(lbm3_domain *d, long long n, int par) {
+  using Sh = Sweep3Shape<S>;
+  sweep3_kernel<S, Sh::kV><<<d->grid, Sh::kThreads, 0, d->st>>>(d->h, n, par);
   return cudaGetLastError();
 }
 
+cudaError_t launch_sweep3(lbm3_domain *d, long long n, int par) {
+  switch (d->p.storage) {
+    case LBM_F64: return launch_sweep3_as<LBM_F64>(d, n, par);
+    case LBM_F32: return launch_sweep3_as<LBM_F32>(d, n, par);
+    case LBM_F16S: return launch_sweep3_as<LBM_F16S>(d, n, par);
+    case LBM_BF16S: return launch_sweep3_as<LBM_BF16S>(d, n, par);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_forces3(lbm3_domain *d, long long n) {
-  if (d->p.force_every <= 0 || (n + 1) % d->p.force_every != 0) return cudaSuccess;
-  if (d->nbodies > 0 && d->h.nfrows > 0) {
-    if (d->p.storage == LBM_F64) rows3_kernel<double><<<d->grid, 256, 0, d->st>>>(d->d_dom);
-    else rows3_kernel<float><<<d->grid, 256, 0, d->st>>>(d->d_dom);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (d->nbodies > 0) {
-    const long long entry = (n + 1) / d->p.force_every - 1;
-    if (d->h.nfrows > 0) {
-      sum3_kernel<<<d->nbodies, kSumThreads, 0, d->st>>>(d->d_dom, entry);
-    } else {
-      return cudaMemsetAsync(d->h.ring + (entry % d->h.force_cap) * d->nbodies * 3, 0,
-                             sizeof(double) * 3 * d->nbodies, d->st);
-    }
-  }
+  if (d->p.force_every <= 0 || (n + 1) % d->p.force_every != 0 || d->nbodies == 0) return cudaSuccess;
+  const long long entry = (n + 1) / d->p.force_every - 1;
+  if (d->h.nfrows == 0)
+    return cudaMemsetAsync(d->h.ring + (entry % d->h.force_cap) * d->nbodies * 3, 0,
+                           sizeof(double) * 3 * d->nbodies, d->st);
+  if (d->p.storage == LBM_F64) rows3_kernel<double><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->d_dom, entry);
+  else rows3_kernel<float><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->d_dom, entry);
   return cudaGetLastError();
 }
 
@@ -695,20 +764,26 @@ lbm_status validate3(const lbm3_params *p, int nb, int ns, const lbm3_shape *sha
   return LBM_OK;
 }
 
-int sweep3_occupancy(int storage) {
+template <int S> int sweep3_blocks_as(int sms) {
+  using Sh = Sweep3Shape<S>;
   int n = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (storage) {
-    case LBM_F64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_F64, 2>, 256, 0); break;
-    case LBM_F32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_F32, 4>, 256, 0); break;
-    case LBM_F16S: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_F16S, 4>, 256, 0); break;
-    case LBM_BF16S: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<LBM_BF16S, 4>, 256, 0); break;
-  }
-  if (e != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<S, Sh::kV>, Sh::kThreads, 0) !=
+      cudaSuccess) {
     cudaGetLastError();
-    return 1;
+    n = 1;
   }
-  return std::max(1, n);
+  return sms * std::max(1, n);
+}
+
+// persistent grid of the sweep: every resident block slot of every SM
+int sweep3_blocks(int storage, int sms) {
+  switch (storage) {
+    case LBM_F64: return sweep3_blocks_as<LBM_F64>(sms);
+    case LBM_F32: return sweep3_blocks_as<LBM_F32>(sms);
+    case LBM_F16S: return sweep3_blocks_as<LBM_F16S>(sms);
+    case LBM_BF16S: return sweep3_blocks_as<LBM_BF16S>(sms);
+  }
+  return sms;
 }
 
 lbm_status read_status3(lbm3_domain *d) {
@@ -793,6 +868,7 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   D.bodies_f = reinterpret_cast<float *>(base + L.bodiesf_off);
   D.ring = reinterpret_cast<double *>(base + L.ring_off);
   D.status = reinterpret_cast<int32_t *>(base + L.status_off);
+  D.rows_done = reinterpret_cast<uint32_t *>(base + L.status_off + 4);
   D.nx = p->nx;
   D.ny = p->ny;
   D.nz = p->nz;
@@ -813,6 +889,12 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   const double scale = p->storage == LBM_F16S ? double(kF16Scale) : 1.0;
   fill3(D.cd, omp, omm, p->eta, p->rho0, 1.0);
   fill3(D.cf, omp, omm, p->eta, p->rho0, scale);
+  {
+    const Const3<float> &c = D.cf;
+    auto two = [](float x) { return make_float2(x, x); };
+    D.pc = Pair3{two(c.one_m_omp), two(c.hp), two(c.hm), two(c.rho0), two(c.pw0),
+                 two(c.pw1), two(c.pw2), two(c.mw1), two(c.mw2)};
+  }
   {
     // inlet ghost f^eq(rho0, u_in) in compute space, held as the storage would hold it
     const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
@@ -861,24 +943,26 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   ADM3(cudaStreamSynchronize(st));
   d->put(dsh);
   dsh = nullptr;
-  std::vector<int32_t> rows;
+  std::vector<int4> rows;  // (row, first solid column, last solid column + 1, 0)
   for (int r = 0; r < p->ny * p->nz; ++r) {
     const uint8_t *m = hm.data() + static_cast<size_t>(r) * d->pitch;
+    int lo = -1, hi = -1;
     for (int i = 0; i < p->nx; ++i)
       if (m[i]) {
         if (m[i] > nbodies) return bail(fail3(LBM_EINVAL, "mask holds body id %d > %d", m[i], nbodies));
-        rows.push_back(r);
-        break;
+        if (lo < 0) lo = i;
+        hi = i + 1;
       }
+    if (lo >= 0) rows.push_back(make_int4(r, lo, hi, 0));
   }
   D.nfrows = static_cast<int32_t>(rows.size());
-  d->frows = d->get(sizeof(int32_t) * std::max<size_t>(1, rows.size()));
+  d->frows = d->get(sizeof(int4) * std::max<size_t>(1, rows.size()));
   d->rowsum = d->get(sizeof(double) * 3 * std::max<size_t>(1, rows.size()) * std::max(1, nbodies));
   if (!d->frows || !d->rowsum) return bail(fail3(LBM_ENOMEM, "force row lists allocation failed"));
-  D.frows = static_cast<const int32_t *>(d->frows);
+  D.frows = static_cast<const int4 *>(d->frows);
   D.rowsum = static_cast<double *>(d->rowsum);
   if (!rows.empty())
-    ADM3(cudaMemcpyAsync(d->frows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, st));
+    ADM3(cudaMemcpyAsync(d->frows, rows.data(), sizeof(int4) * rows.size(), cudaMemcpyHostToDevice, st));
   // initial state: lattice A = f^eq(rho0, u0); lattice B, F_VP, ring, status zero
   {
     const int nrows = p->ny * p->nz;
@@ -894,11 +978,13 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   ADM3(cudaMemsetAsync(D.lat[1], 0, L.lat, st));
   ADM3(cudaMemsetAsync(D.fvp, 0, L.bodies_off - L.fvp_off, st));
   ADM3(cudaMemsetAsync(D.ring, 0, L.status_off - L.ring_off, st));
-  ADM3(cudaMemsetAsync(D.status, 0, sizeof(int32_t), st));
+  ADM3(cudaMemsetAsync(D.status, 0, 8, st));  // status and the reduction's block counter
   ADM3(cudaMemcpyAsync(d->d_dom, &D, sizeof(Dom3), cudaMemcpyHostToDevice, st));
   ADM3(cudaStreamSynchronize(st));
 #undef ADM3
-  d->grid = sms * sweep3_occupancy(p->storage);
+  d->grid = sweep3_blocks(p->storage, sms);
+  // force reduction: one warp per listed row, at most one block per SM
+  d->aux_grid = std::max(1, std::min(sms, (D.nfrows + kRowsThreads / 32 - 1) / (kRowsThreads / 32)));
   *out = d;
   return LBM_OK;
 }

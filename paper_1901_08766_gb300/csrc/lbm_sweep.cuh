@@ -281,7 +281,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
     const int col_right = east_edge ? ((east_out || east_link) ? -1 : 0) : x0 + kStrip;
     // the lane holding column nx-1 (east edge tiles) and its element index
     const int k_last = nx - 1 - xl;
-    const bool has_last = east_edge && k_last >= 0 && k_last < V;
     const size_t plane = static_cast<size_t>(ny) * pitch;
 
     // ---- phase 1: every load of row j ------------------------------------------------
