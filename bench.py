@@ -477,7 +477,7 @@ def experiment(args):
                 for k in ("cd_mean", "cl_rms", "st"):
                     r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
     elif args.experiment == "sphere3d":
-        out.update(sphere3d(lbm, torch, np))
+        out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None))
     print(json.dumps(out), flush=True)
     return 0
 
@@ -486,15 +486,16 @@ def experiment(args):
 BYTES3 = {"f16s": 19 * 2 * 2 + 1, "bf16s": 19 * 2 * 2 + 1, "f32": 19 * 4 * 2 + 1, "f64": 19 * 8 * 2 + 1}
 
 
-def sphere3d(lbm, torch, np):
+def sphere3d(lbm, torch, np, only=None):
     """3D (D3Q19) sweep throughput per storage on a sphere channel larger than L2, and
-    the drag coefficient of each storage against FP64 on a smaller sphere channel."""
+    the drag coefficient of each storage against FP64 on a smaller sphere channel
+    (`only`: time just these storages, no drag runs)."""
     import synth
     peak = _peak_hbm()
     perf = []
     spec = synth.sphere_channel(384, 128, 128, D=32.0)
     nodes = spec["nx"] * spec["ny"] * spec["nz"]
-    for st in ("f16s", "bf16s", "f32", "f64"):
+    for st in only or ("f16s", "bf16s", "f32", "f64"):
         d = lbm.Domain3(spec, storage=st, force_every=1)
         d.step(20)
         d.forces()
@@ -511,6 +512,8 @@ def sphere3d(lbm, torch, np):
                      "glups_step": nodes / (sw + fo) / 1e3, "bytes_per_node": BYTES3[st],
                      "achieved_gbs": gbs, "peak_gbs": peak[0], "frac": gbs / peak[0],
                      "peak_source": peak[1]})
+    if only:
+        return {"perf": perf, "case_perf": "sphere channel 384x128x128, D=32, Re=100"}
     acc = []
     spec = synth.sphere_channel(192, 64, 64, D=16.0, re=100.0, steps=4000)
     D, U = spec["bodies"][0]["ref_length"], spec["U"]

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm_sweep.cuh"
@@ -71,6 +72,9 @@ struct Dom3 {
   Const3<float> cf;
   Const3<double> cd;
   Pair3 pc;
+  // per-launch: base of each direction's array in the lattice read (src) and written (dst)
+  const void *src[kQ3];
+  void *dst[kQ3];
 };
 
 template <typename T> __device__ __forceinline__ const Const3<T> &const3(const Dom3 &d);
@@ -230,16 +234,89 @@ __device__ __forceinline__ void src_row3(const Dom3 &D, int a, int j, int k, int
   }
 }
 
+#ifndef LBM3_THREADS16
+#define LBM3_THREADS16 256
+#endif
+#ifndef LBM3_MINB16
+#define LBM3_MINB16 2
+#endif
+#ifndef LBM3_THREADS32
+#define LBM3_THREADS32 128
+#endif
+#ifndef LBM3_MINB32
+#define LBM3_MINB32 3
+#endif
+
 // Launch shape per storage (measured on the 384 x 128 x 128 sphere channel): the 16-bit
-// sweeps run 256-thread blocks, two per SM (128 registers); FP32/FP64 128-thread blocks,
-// three per SM (168 registers). Paired FP32 is used where it measured faster (BF16S).
+// sweeps run 256-thread blocks, two per SM (128 registers), force-free warps in paired
+// FP32; FP32/FP64 128-thread blocks, three per SM (168 registers).
 template <int S> struct Sweep3Shape {
   static constexpr bool k16 = S == LBM_F16S || S == LBM_BF16S;
-  static constexpr int kThreads = k16 ? 256 : 128;
-  static constexpr int kMinBlocks = k16 ? 2 : 3;
-  static constexpr bool kPaired = S == LBM_BF16S;
+  static constexpr int kThreads = k16 ? LBM3_THREADS16 : LBM3_THREADS32;
+  static constexpr int kMinBlocks = k16 ? LBM3_MINB16 : LBM3_MINB32;
+  static constexpr bool kPaired = k16;
   static constexpr int kV = S == LBM_F64 ? 2 : 4;
 };
+
+// Source rows of the pull for row (j, k): element offsets within one direction's array of
+// the rows j - e_y (index e_y + 1) and planes k - e_z (index e_z + 1), with the free-slip
+// flags (the source direction is then mirrored). Fits 32 bits: a direction holds < 2^31
+// elements.
+struct RowOff3 {
+  uint32_t y[3], z[3];
+  bool my[3], mz[3];
+};
+
+__device__ __forceinline__ RowOff3 row_off3(const Dom3 &D, int j, int k) {
+  RowOff3 r;
+  const uint32_t pitch = static_cast<uint32_t>(D.pitch), plane = pitch * static_cast<uint32_t>(D.ny);
+  r.my[0] = r.my[1] = r.my[2] = false;
+  r.mz[0] = r.mz[1] = r.mz[2] = false;
+  int sy = j - 1;  // e_y = +1
+  if (sy < 0) {
+    r.my[2] = D.south == LBM_FREE_SLIP;
+    sy = r.my[2] ? 0 : D.ny - 1;
+  }
+  r.y[2] = static_cast<uint32_t>(sy) * pitch;
+  r.y[1] = static_cast<uint32_t>(j) * pitch;
+  sy = j + 1;  // e_y = -1
+  if (sy > D.ny - 1) {
+    r.my[0] = D.north == LBM_FREE_SLIP;
+    sy = r.my[0] ? D.ny - 1 : 0;
+  }
+  r.y[0] = static_cast<uint32_t>(sy) * pitch;
+  int sz = k - 1;  // e_z = +1
+  if (sz < 0) {
+    r.mz[2] = D.bottom == LBM_FREE_SLIP;
+    sz = r.mz[2] ? 0 : D.nz - 1;
+  }
+  r.z[2] = static_cast<uint32_t>(sz) * plane;
+  r.z[1] = static_cast<uint32_t>(k) * plane;
+  sz = k + 1;  // e_z = -1
+  if (sz > D.nz - 1) {
+    r.mz[0] = D.top == LBM_FREE_SLIP;
+    sz = r.mz[0] ? D.nz - 1 : 0;
+  }
+  r.z[0] = static_cast<uint32_t>(sz) * plane;
+  return r;
+}
+
+// source row of direction a (A a compile-time constant after unrolling)
+template <typename E, int A>
+__device__ __forceinline__ const E *src_row_ptr(const Dom3 &D, const RowOff3 &r) {
+  constexpr int iy = ey3(A) + 1, iz = ez3(A) + 1;
+  constexpr int ay = reflect_y3(A), az = reflect_z3(A), ayz = reflect_z3(reflect_y3(A));
+  const bool my = r.my[iy], mz = r.mz[iz];
+  const void *base = my ? (mz ? D.src[ayz] : D.src[ay]) : (mz ? D.src[az] : D.src[A]);
+  return static_cast<const E *>(base) + (r.z[iz] + r.y[iy]);
+}
+
+template <int A, typename F> __device__ __forceinline__ void for_dirs(F &&f) {
+  if constexpr (A < kQ3) {
+    f(std::integral_constant<int, A>{});
+    for_dirs<A + 1>(f);
+  }
+}
 
 // The fused 3D sweep: one warp per strip of 32 V cells of one row (j, k) at a time
 // (persistent grid), nineteen vector loads per lane, the +-1 x-shift by shuffles, strip
@@ -265,10 +342,6 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
   const long long items = static_cast<long long>(ny) * nz * strips;
   const long long wg = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const long long nw = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
-  const E *__restrict__ src = static_cast<const E *>(D.lat[par]);
-  E *__restrict__ dst = static_cast<E *>(D.lat[par ^ 1]);
-  const size_t plane = static_cast<size_t>(ny) * pitch;  // one z plane of one direction
-  const size_t dirsz = plane * nz;                       // one direction
   const bool west_inlet = D.west == LBM_INLET_EQ, east_out = D.east == LBM_OUTFLOW_ZG;
   int unstable = 0;
   for (long long it = wg; it < items; it += nw) {
@@ -284,16 +357,16 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
     const int xl_ld = min(xl, pitch - V);
     Strip<S, V> v[kQ3];
     E end_in[kQ3];
-#pragma unroll
-    for (int a = 0; a < kQ3; ++a) {
-      int sa, sy, sz;
-      src_row3(D, a, j, k, sa, sy, sz);
-      const E *rp = src + sa * dirsz + static_cast<size_t>(sz) * plane + static_cast<size_t>(sy) * pitch;
-      v[a].load(rp + xl_ld);
-      const int ex = ex3(a);
-      end_in[a] = E(0);
-      if (ex == 1) end_in[a] = __ldg(rp + col_l);
-      else if (ex == -1) end_in[a] = __ldg(rp + col_r);
+    {
+      const RowOff3 R = row_off3(D, j, k);
+      for_dirs<0>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        const E *rp = src_row_ptr<E, a>(D, R);
+        v[a].load(rp + xl_ld);
+        end_in[a] = E(0);
+        if constexpr (ex3(a) == 1) end_in[a] = __ldg(rp + col_l);
+        else if constexpr (ex3(a) == -1) end_in[a] = __ldg(rp + col_r);
+      });
     }
     uint8_t b[V];
     {
@@ -439,9 +512,9 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
         }
     }
     if (lane_on) {
+      const uint32_t off = (static_cast<uint32_t>(k) * ny + j) * static_cast<uint32_t>(pitch) + xl;
 #pragma unroll
-      for (int a = 0; a < kQ3; ++a)
-        v[a].store(dst + a * dirsz + static_cast<size_t>(k) * plane + static_cast<size_t>(j) * pitch + xl);
+      for (int a = 0; a < kQ3; ++a) v[a].store(static_cast<E *>(D.dst[a]) + off);
     }
   }
   if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(D.status, 1);
@@ -684,6 +757,7 @@ struct lbm3_domain {
   void *actx = nullptr;
   void *block = nullptr, *frows = nullptr, *rowsum = nullptr;
   Dom3 h{};
+  Dom3 hpar[2]{};  // sweep parameters reading lattice 0 resp. 1
   Dom3 *d_dom = nullptr;
   long long done = 0, drained = 0;
   int parity = 0;
@@ -710,7 +784,7 @@ namespace {
 
 template <int S> cudaError_t launch_sweep3_as(lbm3_domain *d, long long n, int par) {
   using Sh = Sweep3Shape<S>;
-  sweep3_kernel<S, Sh::kV><<<d->grid, Sh::kThreads, 0, d->st>>>(d->h, n, par);
+  sweep3_kernel<S, Sh::kV><<<d->grid, Sh::kThreads, 0, d->st>>>(d->hpar[par], n, par);
   return cudaGetLastError();
 }
 
@@ -982,6 +1056,16 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   ADM3(cudaMemcpyAsync(d->d_dom, &D, sizeof(Dom3), cudaMemcpyHostToDevice, st));
   ADM3(cudaStreamSynchronize(st));
 #undef ADM3
+  {
+    const size_t dir_bytes = esize(p->storage) * static_cast<size_t>(d->pitch) * p->ny * p->nz;
+    for (int par = 0; par < 2; ++par) {
+      d->hpar[par] = D;
+      for (int a = 0; a < kQ3; ++a) {
+        d->hpar[par].src[a] = static_cast<const char *>(D.lat[par]) + a * dir_bytes;
+        d->hpar[par].dst[a] = static_cast<char *>(D.lat[par ^ 1]) + a * dir_bytes;
+      }
+    }
+  }
   d->grid = sweep3_blocks(p->storage, sms);
   // force reduction: one warp per listed row, at most one block per SM
   d->aux_grid = std::max(1, std::min(sms, (D.nfrows + kRowsThreads / 32 - 1) / (kRowsThreads / 32)));

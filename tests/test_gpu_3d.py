@@ -155,3 +155,43 @@ def test_3d_force_ring_and_steps(lbm):
     assert dom.steps_done() == 8
     assert f[-1, 0, 0] != 0.0
     dom.close()
+
+
+@pytest.mark.parametrize("shape,edges", [
+    ((3, 3, 3), synth.edges3()),
+    ((5, 4, 3), synth.edges3("periodic", "periodic", "free_slip", "free_slip", "free_slip", "free_slip")),
+    ((7, 3, 5), synth.channel_edges3()),
+    ((129, 3, 4), synth.edges3("inlet", "outflow", "periodic", "periodic", "free_slip", "free_slip")),
+])
+def test_fp64_3d_degenerate_sizes(lbm, shape, edges):
+    # smallest grids (one strip, both x edges in one lane, y/z of three cells, a strip of
+    # one node past a whole strip) with a sphere covering part of the box
+    nx, ny, nz = shape
+    c = (nx / 2.0 - 0.3, ny / 2.0 - 0.2, nz / 2.0 + 0.1)
+    spec = synth.spec3("tiny", nx, ny, nz, 0.05, [synth.sphere(1, c, 1.3)],
+                       [synth.body3(c, 2.6, v=(0.01, 0.0, 0.0), w=(0.0, 0.002, 0.0))], 0, 0.02, edges,
+                       u_in=(0.02, 0.0, 0.0), u0=(0.02, 0.0, 0.0))
+    dom, g0 = _start(lbm, spec, "f64", 21)
+    f_gpu = dom.run(200)
+    raw = dom.get_populations()
+    dom.close()
+    ora = ora3.Domain(spec, g=g0)
+    f_ora = ora.run(200)
+    np.testing.assert_array_equal(ora.mask, ora3.rasterize(spec))
+    rel = np.abs(raw - ora.g) / np.abs(ora.g)
+    assert rel.max() <= 1e-12
+    assert np.abs(f_gpu - f_ora).max() <= 1e-10 * max(np.abs(f_ora).max(), 1e-30) + 1e-14
+
+
+def test_3d_empty_geometry_and_no_forces(lbm):
+    # no shapes and no bodies: a force-free periodic box; no force entries recorded
+    spec = synth.spec3("empty", 40, 6, 5, 0.1, [], [], 0, 0.01, synth.edges3(), u0=(0.01, 0.0, 0.0))
+    dom, g0 = _start(lbm, spec, "f64", 4)
+    f = dom.run(50)
+    raw = dom.get_populations()
+    assert dom.mask().sum() == 0
+    dom.close()
+    assert f.shape == (50, 0, 3)
+    ora = ora3.Domain(spec, g=g0)
+    ora.run(50, want_forces=False)
+    assert (np.abs(raw - ora.g) / np.abs(ora.g)).max() <= 1e-12
