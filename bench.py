@@ -478,8 +478,49 @@ def experiment(args):
                     r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
     elif args.experiment == "sphere3d":
         out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None))
+    elif args.experiment == "served":
+        out.update(served_stream(lbm, torch, np, args))
     print(json.dumps(out), flush=True)
     return 0
+
+
+def served_stream(lbm, torch, np, args):
+    """The served workload at a sustainable rate in real time: Poisson arrivals at
+    `served_rate` per second over `served_seconds`, every request with its full step count
+    (20k-100k), continuous batching by memory budget; throughput and arrival-to-done
+    latency of the completed requests."""
+    import synth
+    from paper_1901_08766_gb300.server import Server
+    reqs = synth.served_requests(rate=args.served_rate, duration=args.served_seconds)
+    offered = sum(sp["nx"] * sp["ny"] * sp["steps"] for _, sp in reqs) / args.served_seconds / 1e9
+    stream = torch.cuda.Stream()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    resident = []
+    with torch.cuda.stream(stream):
+        srv = Server(storage=args.storage, hbm_budget=budget, chunk_steps=args.served_chunk,
+                     graph_steps=args.graph_steps)
+        t0 = srv.clock()
+        futs = [srv.submit(sp, arrival=t0 + a) for a, sp in reqs]
+        while srv.pump():
+            resident.append(len(srv._resident))
+            if srv.clock() - t0 > args.served_seconds * 20 + 600:
+                raise TimeoutError("served stream did not drain")
+        st = srv.stats()
+        srv.backend.close()
+    res = [f.result() for f in futs]
+    ok = [r for r in res if r.status == "ok"]
+    svc = [r.done - r.admitted for r in ok]
+    wait = [r.admitted - r.arrival for r in ok]
+    return {"rate_per_s": args.served_rate, "window_s": args.served_seconds, "requests": len(reqs),
+            "completed": st["completed"], "not_ok": [r.status for r in res if r.status != "ok"],
+            "offered_glups": offered, "served_glups": st["glups"], "wall_s": st["wall_s"],
+            "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+            "p50_queue_wait_s": float(np.percentile(wait, 50)) if wait else None,
+            "p50_service_s": float(np.percentile(svc, 50)) if svc else None,
+            "max_resident": max(resident) if resident else 0, "max_queue": st["max_queue"],
+            "chunk_steps": args.served_chunk, "storage": args.storage,
+            "latency": "arrival to last force slice on the host", "hbm_budget_bytes": budget}
 
 
 # bytes of one D3Q19 node per sweep: 19 populations read and written, the mask byte read
@@ -551,7 +592,9 @@ def main():
     ap.add_argument("--served-requests", type=int, default=32)
     ap.add_argument("--served-scale", type=float, default=0.02)
     ap.add_argument("--served-chunk", type=int, default=256)
-    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d"], default=None,
+    ap.add_argument("--served-rate", type=float, default=1.2, help="requests/s (--experiment served)")
+    ap.add_argument("--served-seconds", type=float, default=120.0, help="arrival window (--experiment served)")
+    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served"], default=None,
                     help="accuracy study instead of the benchmark")
     args = ap.parse_args()
     if args.experiment:
