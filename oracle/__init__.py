@@ -47,6 +47,12 @@ class _Body(C.Structure):
                 ("vy", C.c_double), ("omega", C.c_double)]
 
 
+class _Dynamics(C.Structure):
+    _fields_ = [("mass", C.c_double), ("kx", C.c_double), ("ky", C.c_double), ("cx", C.c_double),
+                ("cy", C.c_double), ("free_x", C.c_int32), ("free_y", C.c_int32),
+                ("active", C.c_int32)]
+
+
 class _Shape(C.Structure):
     _fields_ = [("kind", C.c_int32), ("body", C.c_int32), ("cx", C.c_double),
                 ("cy", C.c_double), ("radius", C.c_double), ("chord", C.c_double),
@@ -97,6 +103,10 @@ def lib():
         L.ora_run_moving.argtypes = [C.POINTER(_Params), C.POINTER(_Shape), C.c_int32,
                                      C.POINTER(_Body), C.c_int32, dp, C.c_int64, C.c_int64, dp,
                                      C.c_int32]
+        L.ora_run_fsi.restype = C.c_int
+        L.ora_run_fsi.argtypes = [C.POINTER(_Params), C.POINTER(_Shape), C.c_int32,
+                                  C.POINTER(_Body), C.POINTER(_Dynamics), C.c_int32, dp,
+                                  C.c_int64, C.c_int64, dp, dp, dp]
         L.ora_bodies_at.argtypes = [C.POINTER(_Body), C.c_int32, C.c_int64, C.POINTER(_Body)]
         _lib = L
     return _lib
@@ -177,10 +187,25 @@ def rasterize(spec, step=None) -> np.ndarray:
     return mask
 
 
+def _dynamics_of(spec):
+    """Body dynamics of a spec (bodies with a "dynamics" entry respond to their force)."""
+    bs = spec["bodies"]
+    arr = (_Dynamics * max(1, len(bs)))()
+    any_active = False
+    for k, b in enumerate(bs):
+        d = b.get("dynamics")
+        if d:
+            any_active = True
+            arr[k] = _Dynamics(d["mass"], d["stiffness"][0], d["stiffness"][1], d["damping"][0],
+                               d["damping"][1], int(d["free"][0]), int(d["free"][1]), 1)
+    return arr, any_active
+
+
 class Domain:
     """One simulation: post-collision populations g [9, ny, nx] in FP64. A spec with
     "moving": True has bodies that translate with their velocities (the mask and the
-    body centres follow them, re-rasterised before every step)."""
+    body centres follow them, re-rasterised before every step); bodies with a
+    "dynamics" entry move in response to their force (fluid-structure coupling)."""
 
     def __init__(self, spec, mask=None, g=None):
         self.spec = spec
@@ -192,6 +217,12 @@ class Domain:
                                          dtype=np.uint8)
         self.bodies, self.nb = _bodies_of(spec)
         self.shapes, self.ns = _shapes_of(spec)
+        self.dyn, self.fsi = _dynamics_of(spec)
+        if self.fsi and not self.moving:
+            raise ValueError("bodies with dynamics need a moving domain")
+        # (x, y, vx, vy) of every body at the current step index (used by coupled bodies)
+        self.state = np.array([[b["cx"], b["cy"], b["vx"], b["vy"]] for b in spec["bodies"]],
+                              dtype=np.float64).reshape(-1, 4)
         nx, ny = spec["nx"], spec["ny"]
         if g is None:
             self.g = np.zeros((9, ny, nx))
@@ -200,9 +231,29 @@ class Domain:
             self.g = np.ascontiguousarray(g, dtype=np.float64).copy()
         self.steps_done = 0
 
-    def run(self, n: int, srt: bool = False, want_forces: bool = True) -> np.ndarray:
-        """Advance n steps; returns the force on each body per step, [n, nbodies, 2]."""
+    def run(self, n: int, srt: bool = False, want_forces: bool = True, track=None) -> np.ndarray:
+        """Advance n steps; returns the force on each body per step, [n, nbodies, 2].
+        `track`, an array [n, nbodies, 4], receives the body state each step used."""
         forces = np.zeros((n, max(self.nb, 1), 2)) if want_forces else None
+        if self.fsi:
+            if srt:
+                raise ValueError("coupled bodies are run with the TRT update")
+            st = np.ascontiguousarray(self.state).copy()
+            tr = None
+            if track is not None:
+                tr = np.zeros((n, max(self.nb, 1), 4))
+            rc = lib().ora_run_fsi(C.byref(self.p), self.shapes, self.ns, self.bodies, self.dyn,
+                                   self.nb, _dp(self.g), self.steps_done, n, _dp(st),
+                                   _dp(forces) if want_forces else None,
+                                   _dp(tr) if tr is not None else None)
+            if rc != 0:
+                raise MemoryError("oracle run failed to allocate")
+            self.state = st
+            if tr is not None:
+                track[...] = tr[:, : self.nb]
+            self.steps_done += n
+            self.mask = self._mask_now()
+            return forces[:, : self.nb] if want_forces else None
         if self.moving:
             rc = lib().ora_run_moving(C.byref(self.p), self.shapes, self.ns, self.bodies,
                                       self.nb, _dp(self.g), self.steps_done, n,
@@ -224,7 +275,29 @@ class Domain:
             return self.bodies
         out = (_Body * max(1, self.nb))()
         lib().ora_bodies_at(self.bodies, self.nb, self.steps_done, out)
+        for k in range(self.nb):
+            if self.dyn[k].active:
+                out[k].cx, out[k].cy, out[k].vx, out[k].vy = (float(v) for v in self.state[k])
         return out
+
+    def _mask_now(self):
+        """The mask at the current step index (coupled bodies at their current state)."""
+        if not self.fsi:
+            return rasterize(self.spec, self.steps_done)
+        spec = dict(self.spec)
+        shapes = []
+        for s in self.spec["shapes"]:
+            s = dict(s)
+            k = s["body"] - 1
+            if 0 <= k < self.nb and self.dyn[k].active:
+                b = self.spec["bodies"][k]
+                s["cx"] = s["cx"] + (float(self.state[k, 0]) - b["cx"])
+                s["cy"] = s["cy"] + (float(self.state[k, 1]) - b["cy"])
+            shapes.append(s)
+        spec["shapes"] = shapes
+        spec["bodies"] = [dict(b, vx=0.0, vy=0.0) if self.dyn[k].active else b
+                          for k, b in enumerate(self.spec["bodies"])]
+        return rasterize(spec, self.steps_done)
 
     def step_once(self, srt: bool = False):
         """One step returning (new g, forces [nbodies, 2]) without the run wrapper."""
@@ -233,6 +306,8 @@ class Domain:
         fn = lib().ora_step_srt if srt else lib().ora_step_trt
         fn(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)), self._bodies_now(),
            self.nb, _dp(self.g), _dp(out), _dp(fb))
+        if self.fsi:
+            raise ValueError("use run() for coupled bodies")
         self.g = out
         self.steps_done += 1
         if self.moving:

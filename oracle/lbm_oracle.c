@@ -380,6 +380,96 @@ void ora_bodies_at(const ora_body *bodies, int32_t nbodies, int64_t n, ora_body 
   for (int k = 0; k < nbodies; k++) body_at(&bodies[k], n, &out[k]);
 }
 
+/* ---- fluid-structure coupling (reading M4) ---------------------------------------------
+ * The paper prescribes U_O. Coupled motion is an extension: a body with dynamics is a
+ * rigid body of mass M on springs k (anchored at its initial centre x0) with dampers c;
+ * each free axis obeys M dv/dt = F - k (x - x0) - c v, F the force on the body (-sum of
+ * F_VP) of the step just computed. After every step the state advances by semi-implicit
+ * Euler with dt = 1:  v <- v + (F - k (x - x0) - c v) / M,  then  x <- x + v.  An axis
+ * that is not free keeps its velocity (x <- x + v). The mask and U_O of a step use the
+ * state before its update; shapes translate with the centre; the angular velocity stays
+ * as given. Bodies without dynamics keep their prescribed motion (centre c + V n). */
+typedef struct {
+  double mass, kx, ky, cx, cy;
+  int32_t free_x, free_y, active;
+} ora_dynamics;
+
+/* One axis of the update, in the order of the formula above. */
+static void fsi_axis(double F, double k, double c, double M, int32_t free_axis, double x0,
+                     double *x, double *v) {
+  if (free_axis) {
+    double t = F - k * (*x - x0);
+    t = t - c * *v;
+    *v = *v + t / M;
+  }
+  *x = *x + *v;
+}
+
+/* n steps from step index n0 with coupled bodies. state [nbodies][4] holds (x, y, vx, vy)
+ * of the bodies with dynamics at index n0 and is advanced in place; track, if not NULL,
+ * receives the state each step used, [n][nbodies][4]. */
+int ora_run_fsi(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
+                const ora_body *bodies, const ora_dynamics *dyn, int32_t nbodies, double *g,
+                int64_t n0, int64_t n, double *state, double *forces, double *track) {
+  size_t cells = (size_t)p->nx * p->ny;
+  double *tmp = (double *)malloc(sizeof(double) * Q * cells);
+  double *fb = (double *)malloc(sizeof(double) * 2 * (nbodies > 0 ? nbodies : 1));
+  uint8_t *mask = (uint8_t *)malloc(cells);
+  ora_body *now = (ora_body *)malloc(sizeof(ora_body) * (nbodies > 0 ? nbodies : 1));
+  ora_shape *sh = (ora_shape *)malloc(sizeof(ora_shape) * (nshapes > 0 ? nshapes : 1));
+  if (!tmp || !fb || !mask || !now || !sh) {
+    free(tmp); free(fb); free(mask); free(now); free(sh);
+    return -1;
+  }
+  double *a = g, *b = tmp;
+  for (int64_t s = 0; s < n; s++) {
+    const int64_t m = n0 + s;
+    /* bodies and shapes at index m */
+    for (int k = 0; k < nbodies; k++) {
+      if (dyn[k].active) {
+        now[k] = bodies[k];
+        now[k].cx = state[4 * k];
+        now[k].cy = state[4 * k + 1];
+        now[k].vx = state[4 * k + 2];
+        now[k].vy = state[4 * k + 3];
+      } else {
+        body_at(&bodies[k], m, &now[k]);
+      }
+      if (track) {
+        double *tr = track + ((size_t)s * nbodies + k) * 4;
+        tr[0] = now[k].cx;
+        tr[1] = now[k].cy;
+        tr[2] = now[k].vx;
+        tr[3] = now[k].vy;
+      }
+    }
+    for (int q = 0; q < nshapes; q++) {
+      const int k = shapes[q].body - 1;
+      if (k >= 0 && k < nbodies && dyn[k].active) {
+        sh[q] = shapes[q];
+        sh[q].cx = shapes[q].cx + (state[4 * k] - bodies[k].cx);
+        sh[q].cy = shapes[q].cy + (state[4 * k + 1] - bodies[k].cy);
+      } else {
+        shape_at(&shapes[q], bodies, nbodies, m, &sh[q]);
+      }
+    }
+    ora_rasterize(p->nx, p->ny, sh, nshapes, mask);
+    ora_step_trt(p, mask, now, nbodies, a, b, fb);
+    if (forces) memcpy(forces + (size_t)s * 2 * nbodies, fb, sizeof(double) * 2 * nbodies);
+    /* the bodies respond to the force of this step */
+    for (int k = 0; k < nbodies; k++) {
+      if (!dyn[k].active) continue;
+      double *st = &state[4 * k];
+      fsi_axis(fb[2 * k], dyn[k].kx, dyn[k].cx, dyn[k].mass, dyn[k].free_x, bodies[k].cx, &st[0], &st[2]);
+      fsi_axis(fb[2 * k + 1], dyn[k].ky, dyn[k].cy, dyn[k].mass, dyn[k].free_y, bodies[k].cy, &st[1], &st[3]);
+    }
+    double *t = a; a = b; b = t;
+  }
+  if (a != g) memcpy(g, a, sizeof(double) * Q * cells);
+  free(tmp); free(fb); free(mask); free(now); free(sh);
+  return 0;
+}
+
 /* Step (1): every node starts at f^eq(rho0, u0). */
 void ora_init(const ora_params *p, double u0x, double u0y, double *g) {
   double feq[Q];

@@ -108,6 +108,31 @@ def _body(cx, cy, ref_length, vx=0.0, vy=0.0, omega=0.0):
             "omega": float(omega), "ref_length": float(ref_length)}
 
 
+def dynamics(mass, stiffness=(0.0, 0.0), damping=(0.0, 0.0), free=(1, 1)):
+    """Rigid-body dynamics of a coupled body: mass, springs (k_x, k_y) anchored at the
+    initial centre, dampers (c_x, c_y), and which axes respond to the force."""
+    return {"mass": float(mass), "stiffness": (float(stiffness[0]), float(stiffness[1])),
+            "damping": (float(damping[0]), float(damping[1])), "free": (int(free[0]), int(free[1]))}
+
+
+def spring_cylinder(nx=480, ny=240, D=24.0, U=0.05, re=100.0, mass_ratio=10.0,
+                    reduced_velocity=5.0, zeta=0.0, steps=40000):
+    """An elastically mounted cylinder free to move across the stream (y): mass ratio
+    m* = M / (rho0 pi D^2 / 4), natural frequency f_n = U / (U* D), spring k = M (2 pi f_n)^2,
+    damping c = 2 zeta M 2 pi f_n; uniform inflow, zero-gradient outflow, free-slip walls."""
+    nu = U * D / re
+    cx, cy = nx / 4.0, ny / 2.0
+    M = mass_ratio * math.pi * D * D / 4.0
+    wn = 2.0 * math.pi * U / (reduced_velocity * D)
+    body = _body(cx, cy, D)
+    body["dynamics"] = dynamics(M, (0.0, M * wn * wn), (0.0, 2.0 * zeta * M * wn), free=(0, 1))
+    sp = _spec(f"spring_cylinder_{nx}x{ny}_re{re:g}_ur{reduced_velocity:g}", nx, ny, nu,
+               [_circle(1, cx, cy, D / 2.0)], [body], steps, U, _channel_edges(),
+               u_in=(U, 0.0), u0=(U, 0.0))
+    sp["moving"] = True
+    return sp
+
+
 def _spec(name, nx, ny, nu, shapes, bodies, steps, U, edges, u_in=(0.0, 0.0),
           u0=(0.0, 0.0), magic_lambda=3.0 / 16.0, eta=1e-4, rho0=1.0):
     return {"name": name, "nx": int(nx), "ny": int(ny), "nu": float(nu),

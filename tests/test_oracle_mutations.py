@@ -1,6 +1,6 @@
 """The oracle's pins are sensitive: each plausible mistake planted in a copy of the
 oracle source (a dropped term, a wrong sign, index or table entry) makes at least one
-pin of tests/test_oracle_pins.py fail. Runs on the CPU only; the committed oracle is
+pin of tests/test_oracle_pins.py or tests/test_oracle_fsi_pins.py fail. Runs on the CPU only; the committed oracle is
 never modified."""
 import os
 import subprocess
@@ -9,6 +9,7 @@ import warnings
 import pytest
 
 import oracle
+import test_oracle_fsi_pins as fsi_pins
 import test_oracle_pins as pins
 import synth
 
@@ -39,10 +40,24 @@ MUTATIONS = [
     ("moving_shape_sign", "s->cx = s0->cx + b->vx * (double)n;", "s->cx = s0->cx - b->vx * (double)n;"),
     ("moving_centre_fixed", "b->cx = b0->cx + b0->vx * (double)n;", "b->cx = b0->cx;"),
     ("moving_step_index", "const int64_t m = n0 + s;", "const int64_t m = n0 + s + 1;"),
+    ("fsi_force_sign", "double t = F - k * (*x - x0);", "double t = -F - k * (*x - x0);"),
+    ("fsi_spring_anchor", "double t = F - k * (*x - x0);", "double t = F - k * (*x);"),
+    ("fsi_damping_sign", "t = t - c * *v;", "t = t + c * *v;"),
+    ("fsi_explicit_euler", "*v = *v + t / M;", "*x = *x - t / M;\n    *v = *v + t / M;"),
+    ("fsi_shape_not_moved", "sh[q].cy = shapes[q].cy + (state[4 * k + 1] - bodies[k].cy);",
+     "sh[q].cy = shapes[q].cy;"),
+    ("fsi_initial_velocity_for_U_O", "now[k].vy = state[4 * k + 3];", "now[k].vy = bodies[k].vy;"),
 ]
 
 # Pins in order of cost; each mutation stops at the first one that fails.
 PINS = [
+    fsi_pins.test_fluid_plus_body_momentum_is_conserved,
+    lambda: [fsi_pins.test_negligible_fluid_force_gives_the_discrete_oscillator(z) for z in (0.0, 0.4)],
+    fsi_pins.test_infinitely_heavy_body_at_rest_is_the_fixed_body,
+    fsi_pins.test_infinitely_heavy_moving_body_is_the_prescribed_motion,
+    fsi_pins.test_fluid_damps_a_spring_mounted_body,
+    fsi_pins.test_fluid_moves_with_the_body_at_its_current_position,
+    fsi_pins.test_free_body_in_a_stream_is_dragged_downstream,
     lambda: pins.test_equilibrium_moments(0.97, 0.05, -0.03),
     lambda: pins.test_guo_term_moments(0.04, -0.02, -3e-4, 7e-4),
     pins.test_gauss_circle_counts,
