@@ -307,6 +307,42 @@ LBM_API lbm_status lbm_batch_info(lbm_batch *b, int32_t *resident, int64_t *cell
 
 LBM_API lbm_status lbm_batch_destroy(lbm_batch *b);
 
+/* ---- Fluid-structure coupling (moving domains) -----------------------------------------
+ * The paper prescribes the obstacle velocity U_O (Sec. 2.2) for rigid obstacles; here a
+ * body of a moving domain may instead respond to its force. It is a rigid body of mass M
+ * on springs (k_x, k_y) anchored at its initial centre x0, with dampers (c_x, c_y). After
+ * every step each free axis advances by semi-implicit Euler with dt = 1, in FP64, each
+ * operation rounded in this order:
+ *     v <- v + (F - k (x - x0) - c v) / M,     x <- x + v,
+ * F the force on the body of that step (-sum of F_VP over its nodes, Eq. hydrodynamic
+ * force); an axis that is not free keeps its velocity. The next step's mask, centre and
+ * U_O = V + omega x (x - c) use the new state (omega stays as given); shapes translate
+ * with the centre. The coupling is explicit: it is stable for bodies about ten times
+ * heavier than the fluid they displace; lighter bodies excite an oscillation of the
+ * penalized interior that grows every step (reported as LBM_EUNSTABLE once the density
+ * leaves its range). */
+typedef struct {
+  double mass;              /* M > 0 */
+  double stiffness[2];      /* k_x, k_y >= 0 */
+  double damping[2];        /* c_x, c_y >= 0 */
+  int32_t free_axis[2];     /* 1: the axis responds to the force, 0: it keeps its velocity */
+} lbm_body_dynamics;
+
+/* Give body `body` (1-based) of a slot dynamics. The slot must be a moving domain that
+ * records the force of every step (force_every = 1), has not stepped yet and is not
+ * linked; LBM_EINVAL otherwise (the domain is unchanged). Such a slot cannot change its
+ * step index afterwards (lbm_batch_set_steps_done to another index is LBM_EINVAL) nor be
+ * linked. Synchronises. */
+LBM_API lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body,
+                                          const lbm_body_dynamics *dyn);
+LBM_API lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_dynamics *dyn);
+
+/* The body table of the slot's current step into host `out`, [nbodies][5] doubles: centre
+ * x, y, velocity x, y, angular velocity (for coupled bodies the integrated state; for
+ * prescribed motion c + V n). Synchronises. */
+LBM_API lbm_status lbm_batch_body_state(lbm_batch *b, int32_t slot, double *out);
+LBM_API lbm_status lbm_body_state(lbm_domain *d, double *out);
+
 /* ---- 3D: D3Q19 TRT-LBM-VP (single domain) --------------------------------------------
  * The paper's closing remark: the method extends to 3D by replacing D2Q9 with D3Q15 or
  * D3Q19. This is the step of Sec. 2.2 with D3Q19: e_0 = 0; e_1..6 = +x, -x, +y, -y, +z,

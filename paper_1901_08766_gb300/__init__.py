@@ -62,6 +62,18 @@ class Domain:
                                   self._alloc.c_free if self._alloc else _native.FREE_FN(),
                                   None, C.byref(h)), "lbm_domain_create")
         self._h = h
+        for k, b in enumerate(spec["bodies"]):
+            if b.get("dynamics"):
+                dyn = _native.dynamics_from(b["dynamics"])
+                check(L.lbm_set_dynamics(h, k + 1, C.byref(dyn)), "lbm_set_dynamics")
+
+    def body_state(self) -> np.ndarray:
+        """Body table of the current step: [nbodies, 5] (cx, cy, vx, vy, omega); coupled
+        bodies report their integrated state."""
+        out = np.zeros((max(self.nbodies, 1), 5))
+        check(load().lbm_body_state(self._handle(), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm_body_state")
+        return out[: self.nbodies]
 
     def _handle(self):
         if self._h is None:
@@ -271,7 +283,23 @@ class Batch:
         check(load().lbm_batch_admit(self._h, C.byref(p), mp, C.byref(geom), bodies, nb, n,
                                      C.byref(slot)), "lbm_batch_admit")
         self._meta[slot.value] = (spec["nx"], spec["ny"], len(spec["bodies"]), force_capacity)
+        for k, b in enumerate(spec["bodies"]):
+            if b.get("dynamics"):
+                dyn = _native.dynamics_from(b["dynamics"])
+                rc = load().lbm_batch_set_dynamics(self._h, slot.value, k + 1, C.byref(dyn))
+                if rc != _native.LBM_OK:
+                    err = LbmError(rc, "lbm_batch_set_dynamics", load().lbm_last_error().decode())
+                    self.evict(slot.value)
+                    raise err
         return slot.value
+
+    def body_state(self, slot: int) -> np.ndarray:
+        """Body table of the slot's current step: [nbodies, 5] (cx, cy, vx, vy, omega)."""
+        nb = self._meta[slot][2]
+        out = np.zeros((max(nb, 1), 5))
+        check(load().lbm_batch_body_state(self._h, int(slot), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm_batch_body_state")
+        return out[:nb]
 
     def try_admit(self, spec, **kw):
         try:

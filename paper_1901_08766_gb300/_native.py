@@ -55,6 +55,16 @@ class Geometry(C.Structure):
     _fields_ = [("shapes", C.POINTER(Shape)), ("nshapes", C.c_int32)]
 
 
+class BodyDynamics(C.Structure):
+    _fields_ = [("mass", C.c_double), ("stiffness", C.c_double * 2), ("damping", C.c_double * 2),
+                ("free_axis", C.c_int32 * 2)]
+
+
+def dynamics_from(d) -> BodyDynamics:
+    return BodyDynamics(d["mass"], (C.c_double * 2)(*d["stiffness"]), (C.c_double * 2)(*d["damping"]),
+                        (C.c_int32 * 2)(*[int(v) for v in d["free"]]))
+
+
 class Params3(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nu", C.c_double),
                 ("tau_plus", C.c_double), ("magic_lambda", C.c_double), ("eta", C.c_double),
@@ -123,6 +133,10 @@ SIGNATURES = {
     "lbm_batch_info": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),
                                  C.POINTER(_SZ)]),
     "lbm_batch_destroy": (C.c_int, [_VP]),
+    "lbm_batch_set_dynamics": (C.c_int, [_VP, _I32, _I32, C.POINTER(BodyDynamics)]),
+    "lbm_set_dynamics": (C.c_int, [_VP, _I32, C.POINTER(BodyDynamics)]),
+    "lbm_batch_body_state": (C.c_int, [_VP, _I32, _DP]),
+    "lbm_body_state": (C.c_int, [_VP, _DP]),
     "lbm3_params_default": (None, [C.POINTER(Params3)]),
     "lbm3_domain_bytes": (_SZ, [C.POINTER(Params3), _I32]),
     "lbm3_domain_create": (C.c_int, [C.POINTER(Params3), C.POINTER(Shape3), _I32,

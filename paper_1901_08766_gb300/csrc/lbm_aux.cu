@@ -82,8 +82,25 @@ __device__ __forceinline__ double moved(double c0, double v, long long n) {
 // Shape s0 of a domain at index n (translated with its body) and its column interval in
 // row j: a node farther than the shape's reach from its reference point is outside it
 // (lo > hi: the row misses the shape; the outside-annulus kind spans every column).
+__device__ __forceinline__ bool coupled(const DomDev &D, int body) {
+  return D.fsi_on && body >= 1 && body <= D.nbodies && D.fsi_par[8 * (body - 1) + 7] != 0.0;
+}
+
+// a shape of a coupled body, its body's centre at (cx, cy): translated by the centre's
+// displacement from the reference centre
+__device__ __forceinline__ ShapeDev shape_about(const DomDev &D, const ShapeDev &s0, double cx, double cy) {
+  ShapeDev s = s0;
+  s.cx = __dadd_rn(s0.cx, __dsub_rn(cx, D.centre0[2 * (s0.body - 1)]));
+  s.cy = __dadd_rn(s0.cy, __dsub_rn(cy, D.centre0[2 * (s0.body - 1) + 1]));
+  return s;
+}
+
 __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n) {
   ShapeDev s = s0;
+  if (coupled(D, s0.body)) {
+    const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + (s0.body - 1)) * 4;
+    return shape_about(D, s0, st[0], st[1]);
+  }
   if (s0.body >= 1 && s0.body <= D.nbodies) {
     const double *b = D.bodies + 5 * (s0.body - 1);
     s.cx = moved(s0.cx, b[2], n);
@@ -124,13 +141,21 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
   lo = 0;
   hi = D.nx - 1;
   if (s0.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
-  float vx = 0.f, vy = 0.f;
-  if (s0.body >= 1 && s0.body <= D.nbodies) {
-    vx = float(D.bodies[5 * (s0.body - 1) + 2]);
-    vy = float(D.bodies[5 * (s0.body - 1) + 3]);
+  float cx, cy;
+  if (coupled(D, s0.body)) {
+    const ShapeDev s = shape_at(D, s0, n);
+    cx = float(s.cx - double(D.x0));
+    cy = float(s.cy);
+  } else {
+    float vx = 0.f, vy = 0.f;
+    if (s0.body >= 1 && s0.body <= D.nbodies) {
+      vx = float(D.bodies[5 * (s0.body - 1) + 2]);
+      vy = float(D.bodies[5 * (s0.body - 1) + 3]);
+    }
+    const float fn = float(n);
+    cx = (float(s0.cx) - float(D.x0)) + vx * fn;
+    cy = float(s0.cy) + vy * fn;
   }
-  const float fn = float(n);
-  const float cx = (float(s0.cx) - float(D.x0)) + vx * fn, cy = float(s0.cy) + vy * fn;
   const float reach = float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 2.0f;
   if (!(fabsf(float(j) - cy) <= reach)) {
     lo = 1;
@@ -186,6 +211,14 @@ __device__ void place_row(const DomDev &D, int j, long long n, int lane, RowShap
 __device__ void place_centres(const DomDev &D, long long n, int lane) {
   if (lane < D.nbodies) {
     double *b = D.bodies + 5 * lane;
+    if (coupled(D, lane + 1)) {
+      const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + lane) * 4;
+      for (int e = 0; e < 4; ++e) {
+        b[e] = st[e];
+        D.bodies_f[5 * lane + e] = float(st[e]);
+      }
+      return;
+    }
     const double cx = moved(D.centre0[2 * lane], b[2], n), cy = moved(D.centre0[2 * lane + 1], b[3], n);
     b[0] = cx;
     b[1] = cy;
@@ -209,6 +242,9 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
     const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
     if (n >= dy.step_end) continue;
     const int j = mr.j;
+    // (a domain with coupled bodies takes only the row sums here: its next geometry
+    // depends on the force, and fsi_kernel places it after the force reduction)
+    const bool fsi = D.fsi_on != 0;
     // column intervals of the row at the old index (n) and at the new one (n + 1), from
     // FP32 positions (conservative); exact FP64 shapes only where the row is reached
     int olo = D.nx, ohi = -1, nlo = D.nx, nhi = -1;
@@ -216,6 +252,7 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       int lo, hi;
       shape_cols_f32(D, D.shapes[k], n, j, lo, hi);
       if (lo <= hi) { olo = min(olo, lo); ohi = max(ohi, hi); }
+      if (fsi) continue;
       shape_cols_f32(D, D.shapes[k], n + 1, j, rs[k].lo, rs[k].hi);
       if (rs[k].lo <= rs[k].hi) {
         nlo = min(nlo, rs[k].lo);
@@ -229,7 +266,7 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
     nhi = __reduce_max_sync(0xffffffffu, nhi);
     __syncwarp();
     if (olo > ohi && nlo > nhi) {  // no shape near this row at either index
-      if (j == 0) place_centres(D, n + 1, lane);
+      if (j == 0 && !fsi) place_centres(D, n + 1, lane);
       continue;
     }
     const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
@@ -259,12 +296,103 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       }
     }
     __syncwarp();
+    if (fsi) continue;
     // the mask changes only where a shape reaches at either index
     const int c0 = min(olo, nlo), c1 = max(ohi, nhi);
     if (c0 <= c1) write_ids(D, j, c0, c1, lane, rs);
     __syncwarp();
     if (j == 0) place_centres(D, n + 1, lane);
   }
+}
+
+// One axis of a coupled body after step n: v <- v + (F - k (x - x0) - c v) / M, then
+// x <- x + v (semi-implicit Euler, dt = 1), each operation rounded as written; an axis
+// that is not free keeps its velocity.
+__device__ __forceinline__ void fsi_axis(double F, double k, double c, double M, bool free_axis,
+                                         double x0, double &x, double &v) {
+  if (free_axis) {
+    double t = __dsub_rn(F, __dmul_rn(k, __dsub_rn(x, x0)));
+    t = __dsub_rn(t, __dmul_rn(c, v));
+    v = __dadd_rn(v, __ddiv_rn(t, M));
+  }
+  x = __dadd_rn(x, v);
+}
+
+// Coupled bodies after step n (launched after the force reduction, which wrote the
+// force of step n into ring entry n): every warp advances the bodies of its domain
+// from the state of index n (the same operations give the same values in every warp),
+// then rewrites its row's mask at index n + 1 where a shape reaches at n or n + 1; the
+// warp of row 0 stores the new state (the other parity, so that no warp reads a value
+// another warp has replaced) and the body table the next sweep uses.
+__global__ void __launch_bounds__(kMoveWarps * 32)
+fsi_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr, int s) {
+  __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
+  __shared__ double cen[kMoveWarps][kMaxMovingBodies][2];  // centres at index n + 1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RowShape *rs = shapes[warp];
+  const int nrows = ctr->nmove;
+  const long long run_base = ctr->run_base;
+  for (int q = blockIdx.x * kMoveWarps + warp; q < nrows; q += gridDim.x * kMoveWarps) {
+    const MoveRow mr = rows[q];
+    const DomDev &D = doms[mr.dom];
+    if (!D.fsi_on) continue;
+    const DomDyn dy = dyn[mr.dom];
+    const long long n = dy.step0 + run_base + s;
+    if (n >= dy.step_end) continue;
+    const int j = mr.j;
+    if (lane < D.nbodies) {
+      double *b = D.bodies + 5 * lane;
+      if (coupled(D, lane + 1)) {
+        const double *par = D.fsi_par + 8 * lane;
+        const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + lane) * 4;
+        const double *F = D.ring + (static_cast<size_t>(n % D.force_cap) * D.nbodies + lane) * 2;
+        double x = st[0], y = st[1], vx = st[2], vy = st[3];
+        fsi_axis(F[0], par[1], par[3], par[0], par[5] != 0.0, D.centre0[2 * lane], x, vx);
+        fsi_axis(F[1], par[2], par[4], par[0], par[6] != 0.0, D.centre0[2 * lane + 1], y, vy);
+        cen[warp][lane][0] = x;
+        cen[warp][lane][1] = y;
+        if (j == 0) {
+          double *nst = D.fsi + (static_cast<size_t>((n + 1) & 1) * D.nbodies + lane) * 4;
+          const double v4[4] = {x, y, vx, vy};
+          for (int e = 0; e < 4; ++e) {
+            nst[e] = v4[e];
+            b[e] = v4[e];
+            D.bodies_f[5 * lane + e] = float(v4[e]);
+          }
+        }
+      } else if (j == 0) {
+        const double cx = moved(D.centre0[2 * lane], b[2], n + 1), cy = moved(D.centre0[2 * lane + 1], b[3], n + 1);
+        b[0] = cx;
+        b[1] = cy;
+        D.bodies_f[5 * lane] = float(cx);
+        D.bodies_f[5 * lane + 1] = float(cy);
+      }
+    }
+    __syncwarp();
+    // the row's shapes at n + 1 and the columns they or the shapes at n reach (FP64)
+    int c0 = D.nx, c1 = -1;
+    for (int k = lane; k < D.nshapes; k += 32) {
+      const ShapeDev &s0 = D.shapes[k];
+      int lo, hi;
+      shape_cols(shape_at(D, s0, n), D.nx, D.x0, j, lo, hi);
+      if (lo <= hi) { c0 = min(c0, lo); c1 = max(c1, hi); }
+      rs[k].s = coupled(D, s0.body) ? shape_about(D, s0, cen[warp][s0.body - 1][0], cen[warp][s0.body - 1][1])
+                                    : shape_at(D, s0, n + 1);
+      shape_cols(rs[k].s, D.nx, D.x0, j, rs[k].lo, rs[k].hi);
+      if (rs[k].lo <= rs[k].hi) { c0 = min(c0, rs[k].lo); c1 = max(c1, rs[k].hi); }
+    }
+    c0 = __reduce_min_sync(0xffffffffu, c0);
+    c1 = __reduce_max_sync(0xffffffffu, c1);
+    __syncwarp();
+    if (c0 <= c1) write_ids(D, j, c0, c1, lane, rs);
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_fsi(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                       const MoveRow *rows, const Counters *ctr, int s) {
+  fsi_kernel<<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,

@@ -68,6 +68,11 @@ struct DomDev {
   int32_t x0;
   int32_t nb_nx[2], nb_pitch[2];
   void *nb_lat[2][2];  // [side][lattice A/B]
+  // coupled bodies of a moving domain (fluid-structure coupling; null / 0 otherwise)
+  double *fsi;              // [2][nbodies][4] body state (x, y, vx, vy) of step n in [n & 1]
+  const double *fsi_par;    // [nbodies][8]: mass, k_x, k_y, c_x, c_y, free_x, free_y, coupled
+  int32_t fsi_on;           // some body of the domain is coupled
+  int32_t fsi_pad;
 };
 
 // Per-domain dynamic state, uploaded at the start of each batch run.
@@ -130,6 +135,10 @@ cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const Dom
                         const MoveRow *rows, const Counters *ctr, int s, int storage);
 // the mask and body centres of one moving domain at step index n
 cudaError_t launch_place(cudaStream_t st, const DomDev *dom_dev, int nx, int ny, int pitch, long long n);
+// coupled bodies: advance their state with the force of the step just reduced, then the
+// next step's mask of the rows of domains with coupled bodies
+cudaError_t launch_fsi(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                       const MoveRow *rows, const Counters *ctr, int s);
 cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int pitch,
                              const ShapeDev *shapes, int nshapes, int x0);
 cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,

@@ -83,7 +83,7 @@ struct Alloc {
 // force ring, status word), each piece 256-byte aligned.
 struct Layout {
   size_t lat_bytes, mask_off, fvp_off, bodies_off, bodies_f_off, off_off, ring_off, status_off,
-      shapes_off, centre0_off, rowsum_off, total;
+      shapes_off, centre0_off, rowsum_off, fsi_off, total;
 };
 
 Layout layout_of(const lbm_params &p, int nbodies) {
@@ -108,13 +108,16 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   L.status_off = o;
   o += 256;
   // moving domains: reference geometry, reference centres, per-row force sums
-  L.shapes_off = L.centre0_off = L.rowsum_off = o;
+  L.shapes_off = L.centre0_off = L.rowsum_off = L.fsi_off = o;
   if (p.moving) {
     o += align_up(sizeof(ShapeDev) * kMaxMovingShapes, 256);
     L.centre0_off = o;
     o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
     L.rowsum_off = o;
     o += align_up(sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
+    // coupled bodies: state of two step parities [2][nbodies][4], parameters [nbodies][8]
+    L.fsi_off = o;
+    o += align_up(sizeof(double) * 16 * std::max(1, nbodies), 256);
   }
   L.total = o;
   return L;
@@ -161,6 +164,7 @@ struct Slot {
   size_t bytes = 0;
   std::vector<int32_t> solid_off;  // host copy of the per-body offsets into the solid list
   int link_west = -1, link_east = -1;  // slots linked across the x edges (-1: none)
+  bool fsi = false;                    // some body responds to its force
   DomDev dev{};
 };
 
@@ -239,6 +243,7 @@ struct lbm_batch {
   MoveRow *d_moves = nullptr;  // rows of moving domains (geometry update after each sweep)
   int moves_cap = 0;
   int nmove = 0;               // rows in the list; 0: no move kernel in the step
+  bool has_fsi = false;        // some resident domain has coupled bodies: fsi kernel per step
   Counters *d_ctr = nullptr;
   Counters *h_ctr = nullptr;  // pinned staging for tile/item counts
   int vec = 0, warps = 0, rows = 0, pipe = 0;
@@ -335,8 +340,12 @@ lbm_status rebuild_lists(lbm_batch *b) {
         items.push_back(s.p.moving ? ForceItem{k, body, 0, s.p.ny, 1, 0}
                                    : ForceItem{k, body, s.solid_off[body - 1], s.solid_off[body], 0, 0});
   }
-  // a captured graph holds the move kernel only if there were moving rows at capture
-  if ((b->nmove > 0) != !moves.empty()) drop_graph(b);
+  // a captured graph holds the move kernel only if there were moving rows at capture,
+  // and the fsi kernel only if some domain had coupled bodies
+  bool has_fsi = false;
+  for (const Slot &s : b->slots) has_fsi = has_fsi || (s.used && s.fsi);
+  if ((b->nmove > 0) != !moves.empty() || has_fsi != b->has_fsi) drop_graph(b);
+  b->has_fsi = has_fsi;
   if (static_cast<int>(moves.size()) > b->moves_cap || (!moves.empty() && !b->d_moves)) {
     const int cap = std::max<int>(static_cast<int>(moves.size()) * 2, 1024);
     LBM_CUDA(cudaStreamSynchronize(b->st));
@@ -404,6 +413,10 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
                          b->d_ctr, s));
   b->launches++;
+  if (b->has_fsi) {  // coupled bodies: new state from this step's force, next geometry
+    LBM_CUDA(launch_fsi(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s));
+    b->launches++;
+  }
   return LBM_OK;
 }
 
@@ -500,6 +513,12 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
       if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
                         static_cast<int>(s)) != cudaSuccess)
         prc = fail(LBM_ECUDA, "force launch failed");
+      if (b->has_fsi) {
+        if (launch_fsi(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
+                       static_cast<int>(s)) != cudaSuccess)
+          prc = fail(LBM_ECUDA, "fsi launch failed");
+        b->launches++;
+      }
       cudaEventRecord(ev[3 * s + 2], b->st);
       b->launches += 2;
     }
@@ -523,7 +542,7 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
     const long long reps = steps / b->graph_steps;
     for (long long r = 0; r < reps; ++r) {
       LBM_CUDA(cudaGraphLaunch(b->graph, b->st));
-      b->launches += (b->nmove > 0 ? 3 : 2) * static_cast<long long>(b->graph_steps) + 1;
+      b->launches += (2 + (b->nmove > 0 ? 1 : 0) + (b->has_fsi ? 1 : 0)) * static_cast<long long>(b->graph_steps) + 1;
     }
     s0 = reps * b->graph_steps;
   }
@@ -607,6 +626,9 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.shapes = p->moving ? reinterpret_cast<const ShapeDev *>(base + L.shapes_off) : nullptr;
   D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
   D.rowsum = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
+  D.fsi = p->moving ? reinterpret_cast<double *>(base + L.fsi_off) : nullptr;
+  D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 8 * std::max(1, nbodies) : nullptr;
+  D.fsi_on = 0;
   D.nx = p->nx;
   D.ny = p->ny;
   D.pitch = s.pitch;
@@ -703,6 +725,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
                              cudaMemcpyHostToDevice, st));
     // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
     ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
+    ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 16 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
     ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
   }
@@ -1085,6 +1108,8 @@ lbm_status lbm_batch_set_steps_done(lbm_batch *b, int32_t slot, int64_t steps) {
   Slot &s = b->slots[slot];
   if (steps < 0 || steps > s.target)
     return fail(LBM_EINVAL, "step index %lld outside [0, %lld]", static_cast<long long>(steps), s.target);
+  if (s.fsi && steps != s.done)
+    return fail(LBM_EINVAL, "a domain with coupled bodies cannot change its step index (its geometry is state)");
   if (s.p.moving)  // the mask and centres of the new step index
     LBM_CUDA(launch_place(b->st, b->d_doms + slot, s.p.nx, s.p.ny, s.pitch, steps));
   LBM_CUDA(cudaStreamSynchronize(b->st));
@@ -1095,6 +1120,54 @@ lbm_status lbm_batch_set_steps_done(lbm_batch *b, int32_t slot, int64_t steps) {
 
 lbm_status lbm_batch_get_mask(lbm_batch *b, int32_t slot, uint8_t *out) {
   return get_mask(b, slot, out);
+}
+
+lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, const lbm_body_dynamics *dyn) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  if (!dyn) return fail(LBM_EINVAL, "dynamics is NULL");
+  if (!s.p.moving) return fail(LBM_EINVAL, "coupled bodies need a moving domain");
+  if (s.p.force_every != 1) return fail(LBM_EINVAL, "coupled bodies need the force of every step (force_every = 1)");
+  if (s.done != 0) return fail(LBM_EINVAL, "dynamics are set before the first step");
+  if (s.link_west >= 0 || s.link_east >= 0) return fail(LBM_EINVAL, "a linked domain cannot have coupled bodies");
+  if (body < 1 || body > s.nbodies) return fail(LBM_EINVAL, "body %d not in [1, %d]", body, s.nbodies);
+  if (!(dyn->mass > 0) || !std::isfinite(dyn->mass)) return fail(LBM_EINVAL, "mass must be finite and > 0");
+  for (int e = 0; e < 2; ++e) {
+    if (!(dyn->stiffness[e] >= 0) || !std::isfinite(dyn->stiffness[e]) || !(dyn->damping[e] >= 0) ||
+        !std::isfinite(dyn->damping[e]))
+      return fail(LBM_EINVAL, "stiffness and damping must be finite and >= 0");
+    if (dyn->free_axis[e] != 0 && dyn->free_axis[e] != 1) return fail(LBM_EINVAL, "free_axis must be 0 or 1");
+  }
+  DomDev &D = s.dev;
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  // the state of step 0 is the body's own centre and velocity
+  double bt[5];
+  LBM_CUDA(cudaMemcpyAsync(bt, D.bodies + 5 * (body - 1), sizeof(bt), cudaMemcpyDeviceToHost, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  const double st0[4] = {bt[0], bt[1], bt[2], bt[3]};
+  const double par[8] = {dyn->mass, dyn->stiffness[0], dyn->stiffness[1], dyn->damping[0], dyn->damping[1],
+                         double(dyn->free_axis[0]), double(dyn->free_axis[1]), 1.0};
+  LBM_CUDA(cudaMemcpyAsync(D.fsi + 4 * (body - 1), st0, sizeof(st0), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.fsi_par) + 8 * (body - 1), par, sizeof(par),
+                           cudaMemcpyHostToDevice, b->st));
+  D.fsi_on = 1;
+  LBM_CUDA(cudaMemcpyAsync(b->d_doms + slot, &D, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  s.fsi = true;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_body_state(lbm_batch *b, int32_t slot, double *out) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  if (s.nbodies == 0) return LBM_OK;
+  LBM_CUDA(cudaMemcpyAsync(out, s.dev.bodies, sizeof(double) * 5 * s.nbodies, cudaMemcpyDeviceToHost, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
 }
 
 lbm_status lbm_batch_profile(lbm_batch *b, int32_t steps, double *sweep_us, double *force_us,
@@ -1122,6 +1195,7 @@ lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t east_slot) 
   if (A.done != B.done || A.target != B.target || A.parity != B.parity)
     return fail(LBM_EINVAL, "linked domains must step together (same steps done and admitted)");
   if (A.link_east >= 0 || B.link_west >= 0) return fail(LBM_EINVAL, "an edge is linked already");
+  if (A.fsi || B.fsi) return fail(LBM_EINVAL, "domains with coupled bodies cannot be linked");
   LBM_CUDA(cudaStreamSynchronize(b->st));
   // A's east edge pulls B's first column; B's west edge pulls A's last column
   A.dev.east = LBM_NEIGHBOR;
@@ -1286,6 +1360,16 @@ lbm_status lbm_steps_done(lbm_domain *d, int64_t *steps) {
 lbm_status lbm_set_steps_done(lbm_domain *d, int64_t steps) {
   if (!d) return fail(LBM_EINVAL, "domain is NULL");
   return lbm_batch_set_steps_done(d->b, 0, steps);
+}
+
+lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_dynamics *dyn) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return lbm_batch_set_dynamics(d->b, 0, body, dyn);
+}
+
+lbm_status lbm_body_state(lbm_domain *d, double *out) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return lbm_batch_body_state(d->b, 0, out);
 }
 
 lbm_status lbm_domain_destroy(lbm_domain *d) {
