@@ -220,9 +220,10 @@ class Domain:
         self.dyn, self.fsi = _dynamics_of(spec)
         if self.fsi and not self.moving:
             raise ValueError("bodies with dynamics need a moving domain")
-        # (x, y, vx, vy) of every body at the current step index (used by coupled bodies)
-        self.state = np.array([[b["cx"], b["cy"], b["vx"], b["vy"]] for b in spec["bodies"]],
-                              dtype=np.float64).reshape(-1, 4)
+        # (x, y, vx, vy, Fx, Fy) of every body at the current step index (used by coupled
+        # bodies; F is the force of the previous step, zero before the first)
+        self.state = np.array([[b["cx"], b["cy"], b["vx"], b["vy"], 0.0, 0.0] for b in spec["bodies"]],
+                              dtype=np.float64).reshape(-1, 6)
         nx, ny = spec["nx"], spec["ny"]
         if g is None:
             self.g = np.zeros((9, ny, nx))
@@ -277,7 +278,7 @@ class Domain:
         lib().ora_bodies_at(self.bodies, self.nb, self.steps_done, out)
         for k in range(self.nb):
             if self.dyn[k].active:
-                out[k].cx, out[k].cy, out[k].vx, out[k].vy = (float(v) for v in self.state[k])
+                out[k].cx, out[k].cy, out[k].vx, out[k].vy = (float(v) for v in self.state[k, :4])
         return out
 
     def _mask_now(self):

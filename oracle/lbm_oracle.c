@@ -383,31 +383,39 @@ void ora_bodies_at(const ora_body *bodies, int32_t nbodies, int64_t n, ora_body 
 /* ---- fluid-structure coupling (reading M4) ---------------------------------------------
  * The paper prescribes U_O. Coupled motion is an extension: a body with dynamics is a
  * rigid body of mass M on springs k (anchored at its initial centre x0) with dampers c;
- * each free axis obeys M dv/dt = F - k (x - x0) - c v, F the force on the body (-sum of
- * F_VP) of the step just computed. After every step the state advances by semi-implicit
- * Euler with dt = 1:  v <- v + (F - k (x - x0) - c v) / M,  then  x <- x + v.  An axis
- * that is not free keeps its velocity (x <- x + v). The mask and U_O of a step use the
- * state before its update; shapes translate with the centre; the angular velocity stays
- * as given. Bodies without dynamics keep their prescribed motion (centre c + V n). */
+ * each free axis obeys M dv/dt = F - k (x - x0) - c v. With eta -> 0 one step maps the
+ * penalized interior's fluid velocity u* to 2 U_O - u* (Eq. d-V, Eq. force-density), so
+ * the force on the body, F_n = -sum F_VP of step n, carries a component that alternates
+ * every step; a body driven by it feeds that component back through U_O and diverges
+ * for any mass. The body is therefore driven by the mean of the last two steps' forces,
+ * Fm = (F_n + F_{n-1}) / 2 (F_{-1} = 0), which removes the alternating component
+ * exactly. After every step, by semi-implicit Euler with dt = 1:
+ *   v <- v + (Fm - k (x - x0) - c v) / M,  then  x <- x + v.
+ * An axis that is not free keeps its velocity. The mask and U_O of a step use the state
+ * before its update; shapes translate with the centre; the angular velocity stays as
+ * given. Bodies without dynamics keep their prescribed motion (centre c + V n). */
 typedef struct {
   double mass, kx, ky, cx, cy;
   int32_t free_x, free_y, active;
 } ora_dynamics;
 
-/* One axis of the update, in the order of the formula above. */
-static void fsi_axis(double F, double k, double c, double M, int32_t free_axis, double x0,
-                     double *x, double *v) {
+/* One axis of the update, in the order of the formula above; *Fp holds F_{n-1} and
+ * becomes F_n. */
+static void fsi_axis(double F, double *Fp, double k, double c, double M, int32_t free_axis,
+                     double x0, double *x, double *v) {
   if (free_axis) {
-    double t = F - k * (*x - x0);
+    double Fm = (F + *Fp) * 0.5;
+    double t = Fm - k * (*x - x0);
     t = t - c * *v;
     *v = *v + t / M;
   }
   *x = *x + *v;
+  *Fp = F;
 }
 
-/* n steps from step index n0 with coupled bodies. state [nbodies][4] holds (x, y, vx, vy)
- * of the bodies with dynamics at index n0 and is advanced in place; track, if not NULL,
- * receives the state each step used, [n][nbodies][4]. */
+/* n steps from step index n0 with coupled bodies. state [nbodies][6] holds (x, y, vx,
+ * vy, Fx_{n0-1}, Fy_{n0-1}) of the bodies with dynamics at index n0 and is advanced in
+ * place; track, if not NULL, receives (x, y, vx, vy) each step used, [n][nbodies][4]. */
 int ora_run_fsi(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
                 const ora_body *bodies, const ora_dynamics *dyn, int32_t nbodies, double *g,
                 int64_t n0, int64_t n, double *state, double *forces, double *track) {
@@ -428,10 +436,10 @@ int ora_run_fsi(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
     for (int k = 0; k < nbodies; k++) {
       if (dyn[k].active) {
         now[k] = bodies[k];
-        now[k].cx = state[4 * k];
-        now[k].cy = state[4 * k + 1];
-        now[k].vx = state[4 * k + 2];
-        now[k].vy = state[4 * k + 3];
+        now[k].cx = state[6 * k];
+        now[k].cy = state[6 * k + 1];
+        now[k].vx = state[6 * k + 2];
+        now[k].vy = state[6 * k + 3];
       } else {
         body_at(&bodies[k], m, &now[k]);
       }
@@ -447,8 +455,8 @@ int ora_run_fsi(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
       const int k = shapes[q].body - 1;
       if (k >= 0 && k < nbodies && dyn[k].active) {
         sh[q] = shapes[q];
-        sh[q].cx = shapes[q].cx + (state[4 * k] - bodies[k].cx);
-        sh[q].cy = shapes[q].cy + (state[4 * k + 1] - bodies[k].cy);
+        sh[q].cx = shapes[q].cx + (state[6 * k] - bodies[k].cx);
+        sh[q].cy = shapes[q].cy + (state[6 * k + 1] - bodies[k].cy);
       } else {
         shape_at(&shapes[q], bodies, nbodies, m, &sh[q]);
       }
@@ -459,9 +467,9 @@ int ora_run_fsi(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
     /* the bodies respond to the force of this step */
     for (int k = 0; k < nbodies; k++) {
       if (!dyn[k].active) continue;
-      double *st = &state[4 * k];
-      fsi_axis(fb[2 * k], dyn[k].kx, dyn[k].cx, dyn[k].mass, dyn[k].free_x, bodies[k].cx, &st[0], &st[2]);
-      fsi_axis(fb[2 * k + 1], dyn[k].ky, dyn[k].cy, dyn[k].mass, dyn[k].free_y, bodies[k].cy, &st[1], &st[3]);
+      double *st = &state[6 * k];
+      fsi_axis(fb[2 * k], &st[4], dyn[k].kx, dyn[k].cx, dyn[k].mass, dyn[k].free_x, bodies[k].cx, &st[0], &st[2]);
+      fsi_axis(fb[2 * k + 1], &st[5], dyn[k].ky, dyn[k].cy, dyn[k].mass, dyn[k].free_y, bodies[k].cy, &st[1], &st[3]);
     }
     double *t = a; a = b; b = t;
   }

@@ -1,9 +1,10 @@
 """Pins of the oracle's fluid-structure coupling (bodies that move in response to their
-force: semi-implicit Euler of M dv/dt = F - k (x - x0) - c v after every step), each
-against something other than the oracle: exact momentum conservation of fluid plus body
-in a closed box, the closed-form solution of the discrete damped oscillator when the
-fluid force vanishes, bit-identity with the fixed body for an infinitely heavy body at
-rest, the fluid moving with the body at its current position, and the drag direction."""
+force: semi-implicit Euler of M dv/dt = F - k (x - x0) - c v after every step, F the mean
+of the last two steps' forces), each against something other than the oracle: an exact
+momentum invariant of fluid plus body in a closed box, the closed-form solution of the
+discrete damped oscillator when the fluid force vanishes, bit-identity with fixed and
+prescribed motion for an infinitely heavy body, fluid damping, the fluid moving with
+the body at its current position, the drag direction, and stability for light bodies."""
 import math
 
 import numpy as np
@@ -26,27 +27,43 @@ def _box(nx, ny, body, shapes, eta=1e-4, nu=0.05):
 
 
 def test_fluid_plus_body_momentum_is_conserved():
-    # closed periodic box: the fluid gains -F each step (the force on the body is
-    # -sum F_VP) and a free body without springs gains M dv = F in the same step, so
-    # P_fluid + M v is constant. A sign error or a one-step force lag breaks it.
-    # (Mass ratio M / (rho0 pi r^2) = 20: the explicit coupling is stable for ratios of
-    # about 10 and more; lighter bodies excite the penalized interior's period-2 mode.)
-    M = 20.0 * math.pi * 5.2 ** 2
+    # closed periodic box: the fluid gains -F_n in step n (the force on the body is
+    # -sum F_VP) and a free body without springs gains M dv = (F_n + F_{n-1}) / 2, so
+    # Q_n = P_fluid + M v + F_{n-1} / 2 is invariant (telescoping). A sign error, a lost
+    # force memory or an unfiltered force breaks it.
+    M = 3.0 * math.pi * 5.2 ** 2  # three times the mass of the fluid the body displaces
     b = synth._body(20.3, 17.6, 10.0, vx=0.004, vy=-0.003)
     b["dynamics"] = synth.dynamics(M)
     sp = _box(44, 36, b, [synth._circle(1, 20.3, 17.6, 5.2)])
     d = oracle.Domain(sp, g=synth.random_populations(17, 44, 36, 0.1))
-    px, py = _momentum(d.g)
-    tot0 = (px + M * d.state[0, 2], py + M * d.state[0, 3])
-    moved = 0.0
+
+    def q():
+        px, py = _momentum(d.g)
+        return (px + M * d.state[0, 2] + 0.5 * d.state[0, 4], py + M * d.state[0, 3] + 0.5 * d.state[0, 5])
+
+    q0 = q()
     for _ in range(120):
         f = d.run(1)
-        px, py = _momentum(d.g)
-        tot = (px + M * d.state[0, 2], py + M * d.state[0, 3])
-        assert abs(tot[0] - tot0[0]) < 1e-11 and abs(tot[1] - tot0[1]) < 1e-11
+        qn = q()
+        assert abs(qn[0] - q0[0]) < 1e-11 and abs(qn[1] - q0[1]) < 1e-11
         assert np.abs(f).max() > 1e-5
+        assert np.array_equal(d.state[0, 4:6], f[0, 0])  # the force memory is this step's force
     moved = math.hypot(d.state[0, 0] - 20.3, d.state[0, 1] - 17.6)
-    assert moved > 0.1  # the body did move through the lattice
+    assert moved > 0.05  # the body did move through the lattice
+
+
+def test_light_body_stays_bounded():
+    # the two-step mean removes the alternating component of the penalized interior's
+    # force: a body only 1.5 times heavier than the fluid it displaces stays bounded in
+    # a closed box (the force of step n alone makes it diverge within a few dozen steps)
+    M = 1.5 * math.pi * 5.2 ** 2
+    b = synth._body(20.3, 17.6, 10.0, vx=0.004, vy=-0.003)
+    b["dynamics"] = synth.dynamics(M)
+    sp = _box(44, 36, b, [synth._circle(1, 20.3, 17.6, 5.2)])
+    d = oracle.Domain(sp, g=synth.random_populations(17, 44, 36, 0.1))
+    f = d.run(1500)
+    assert np.isfinite(f).all() and np.abs(f[-100:]).max() < 0.01 * np.abs(f[:20]).max()
+    assert np.abs(d.state[0, 2:4]).max() < 0.01
 
 
 @pytest.mark.parametrize("zeta_c", [0.0, 0.4])
@@ -143,10 +160,9 @@ def test_free_body_in_a_stream_is_dragged_downstream():
     track = np.zeros((400, 1, 4))
     d.run(400, track=track)
     vx = track[:, 0, 2]
-    # the impulsive start excites the penalized interior's period-2 mode, which decays;
-    # after it the body accelerates monotonically and stays slower than the stream
-    assert np.abs(np.diff(vx[1:])[-200:]).max() < np.abs(np.diff(vx[1:])[:10]).max() / 50
-    assert (np.diff(vx[40:]) > 0).all() and 0.0 < vx[-1] < U
+    # after the first steps of the impulsive start the body accelerates monotonically
+    # and stays slower than the stream
+    assert (np.diff(vx[3:]) > 0).all() and 0.0 < vx[-1] < U
     assert (track[:, 0, 3] == 0.0).all()
 
 

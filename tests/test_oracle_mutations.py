@@ -40,18 +40,21 @@ MUTATIONS = [
     ("moving_shape_sign", "s->cx = s0->cx + b->vx * (double)n;", "s->cx = s0->cx - b->vx * (double)n;"),
     ("moving_centre_fixed", "b->cx = b0->cx + b0->vx * (double)n;", "b->cx = b0->cx;"),
     ("moving_step_index", "const int64_t m = n0 + s;", "const int64_t m = n0 + s + 1;"),
-    ("fsi_force_sign", "double t = F - k * (*x - x0);", "double t = -F - k * (*x - x0);"),
-    ("fsi_spring_anchor", "double t = F - k * (*x - x0);", "double t = F - k * (*x);"),
+    ("fsi_force_sign", "double Fm = (F + *Fp) * 0.5;", "double Fm = -(F + *Fp) * 0.5;"),
+    ("fsi_unfiltered_force", "double Fm = (F + *Fp) * 0.5;", "double Fm = F;"),
+    ("fsi_force_memory_lost", "  *Fp = F;\n", "  *Fp = 0.0;\n"),
+    ("fsi_spring_anchor", "double t = Fm - k * (*x - x0);", "double t = Fm - k * (*x);"),
     ("fsi_damping_sign", "t = t - c * *v;", "t = t + c * *v;"),
     ("fsi_explicit_euler", "*v = *v + t / M;", "*x = *x - t / M;\n    *v = *v + t / M;"),
-    ("fsi_shape_not_moved", "sh[q].cy = shapes[q].cy + (state[4 * k + 1] - bodies[k].cy);",
+    ("fsi_shape_not_moved", "sh[q].cy = shapes[q].cy + (state[6 * k + 1] - bodies[k].cy);",
      "sh[q].cy = shapes[q].cy;"),
-    ("fsi_initial_velocity_for_U_O", "now[k].vy = state[4 * k + 3];", "now[k].vy = bodies[k].vy;"),
+    ("fsi_initial_velocity_for_U_O", "now[k].vy = state[6 * k + 3];", "now[k].vy = bodies[k].vy;"),
 ]
 
 # Pins in order of cost; each mutation stops at the first one that fails.
 PINS = [
     fsi_pins.test_fluid_plus_body_momentum_is_conserved,
+    fsi_pins.test_light_body_stays_bounded,
     lambda: [fsi_pins.test_negligible_fluid_force_gives_the_discrete_oscillator(z) for z in (0.0, 0.4)],
     fsi_pins.test_infinitely_heavy_body_at_rest_is_the_fixed_body,
     fsi_pins.test_infinitely_heavy_moving_body_is_the_prescribed_motion,
