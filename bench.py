@@ -480,8 +480,52 @@ def experiment(args):
         out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None))
     elif args.experiment == "served":
         out.update(served_stream(lbm, torch, np, args))
+    elif args.experiment == "viv":
+        out.update(viv_sweep(lbm, torch, np, args))
     print(json.dumps(out), flush=True)
     return 0
+
+
+def viv_sweep(lbm, torch, np, args, reduced_velocities=(3.0, 4.0, 5.0, 6.0, 7.0, 8.0), steps=60000,
+              sample=50):
+    """Elastically mounted cylinders free across the stream (fluid-structure coupling):
+    one batch of spring cylinders at several reduced velocities U* = U / (f_n D), mass
+    ratio 10, no structural damping, Re 100; the transverse amplitude A/D and the lift
+    over the last third of the run, the response frequency over f_n."""
+    import synth
+    from paper_1901_08766_gb300 import diagnostics as dg
+    specs = [synth.spring_cylinder(reduced_velocity=u, steps=steps) for u in reduced_velocities]
+    b = lbm.Batch(args.storage, max_domains=len(specs), graph_steps=args.graph_steps)
+    slots = [b.admit(sp, nsteps=steps) for sp in specs]
+    ys = [[] for _ in specs]
+    forces = [[] for _ in specs]
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        ran = b.run(sample)
+        done += ran
+        for q, k in enumerate(slots):
+            ys[q].append(b.body_state(k)[0, 1])
+            f, _ = b.poll(k)
+            forces[q].append(f)
+    el = time.perf_counter() - t0
+    rows = []
+    for q, sp in enumerate(specs):
+        D, U = sp["bodies"][0]["ref_length"], sp["U"]
+        y = (np.array(ys[q]) - sp["bodies"][0]["cy"]) / D
+        f = np.concatenate(forces[q])[:, 0]
+        cd, cl = dg.coefficients(f, U, D)
+        tail = slice(2 * len(cl) // 3, len(cl))
+        ytail = y[2 * len(y) // 3:]
+        st = dg.strouhal_spectral(cl[tail], D, U) if dg.amplitude(cl[tail]) > 1e-6 else 0.0
+        fn = U / (reduced_velocities[q] * D)
+        rows.append({"reduced_velocity": reduced_velocities[q], "amplitude_over_D": float(np.abs(ytail).max()),
+                     "cd_mean": float(cd[tail].mean()), "cl_rms": dg.rms(cl[tail]), "st": st,
+                     "f_over_fn": st * U / D / fn if st else 0.0})
+    b.close()
+    cells = sum(sp["nx"] * sp["ny"] for sp in specs)
+    return {"case": specs[0]["name"].rsplit("_ur", 1)[0], "mass_ratio": 10.0, "zeta": 0.0, "steps": steps,
+            "rows": rows, "seconds": el, "glups": cells * steps / el / 1e9}
 
 
 def served_stream(lbm, torch, np, args):
@@ -594,7 +638,8 @@ def main():
     ap.add_argument("--served-chunk", type=int, default=256)
     ap.add_argument("--served-rate", type=float, default=1.2, help="requests/s (--experiment served)")
     ap.add_argument("--served-seconds", type=float, default=120.0, help="arrival window (--experiment served)")
-    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served"], default=None,
+    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv"],
+                    default=None,
                     help="accuracy study instead of the benchmark")
     args = ap.parse_args()
     if args.experiment:

@@ -313,14 +313,15 @@ LBM_API lbm_status lbm_batch_destroy(lbm_batch *b);
  * on springs (k_x, k_y) anchored at its initial centre x0, with dampers (c_x, c_y). After
  * every step each free axis advances by semi-implicit Euler with dt = 1, in FP64, each
  * operation rounded in this order:
- *     v <- v + (F - k (x - x0) - c v) / M,     x <- x + v,
- * F the force on the body of that step (-sum of F_VP over its nodes, Eq. hydrodynamic
- * force); an axis that is not free keeps its velocity. The next step's mask, centre and
- * U_O = V + omega x (x - c) use the new state (omega stays as given); shapes translate
- * with the centre. The coupling is explicit: it is stable for bodies about ten times
- * heavier than the fluid they displace; lighter bodies excite an oscillation of the
- * penalized interior that grows every step (reported as LBM_EUNSTABLE once the density
- * leaves its range). */
+ *     Fm = (F_n + F_{n-1}) / 2,   v <- v + (Fm - k (x - x0) - c v) / M,   x <- x + v,
+ * F_n the force on the body of step n (-sum of F_VP over its nodes, Eq. hydrodynamic
+ * force), F_{-1} = 0. The two-step mean cancels a component of F_n that alternates every
+ * step (with eta -> 0 the penalization reflects the interior fluid velocity about U_O);
+ * driven by F_n alone a body diverges. An axis that is not free keeps its velocity. The
+ * next step's mask, centre and U_O = V + omega x (x - c) use the new state (omega stays as
+ * given); shapes translate with the centre. The coupling is explicit: a spring-mounted
+ * cylinder is stable at five times the mass of the fluid it displaces and more, not at
+ * two (the instability is reported as LBM_EUNSTABLE once the density leaves its range). */
 typedef struct {
   double mass;              /* M > 0 */
   double stiffness[2];      /* k_x, k_y >= 0 */

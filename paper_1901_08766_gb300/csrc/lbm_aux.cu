@@ -98,7 +98,7 @@ __device__ __forceinline__ ShapeDev shape_about(const DomDev &D, const ShapeDev 
 __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n) {
   ShapeDev s = s0;
   if (coupled(D, s0.body)) {
-    const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + (s0.body - 1)) * 4;
+    const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + (s0.body - 1)) * 6;
     return shape_about(D, s0, st[0], st[1]);
   }
   if (s0.body >= 1 && s0.body <= D.nbodies) {
@@ -212,7 +212,7 @@ __device__ void place_centres(const DomDev &D, long long n, int lane) {
   if (lane < D.nbodies) {
     double *b = D.bodies + 5 * lane;
     if (coupled(D, lane + 1)) {
-      const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + lane) * 4;
+      const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + lane) * 6;
       for (int e = 0; e < 4; ++e) {
         b[e] = st[e];
         D.bodies_f[5 * lane + e] = float(st[e]);
@@ -305,13 +305,16 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
   }
 }
 
-// One axis of a coupled body after step n: v <- v + (F - k (x - x0) - c v) / M, then
-// x <- x + v (semi-implicit Euler, dt = 1), each operation rounded as written; an axis
-// that is not free keeps its velocity.
-__device__ __forceinline__ void fsi_axis(double F, double k, double c, double M, bool free_axis,
+// One axis of a coupled body after step n, driven by the mean of the forces of steps n
+// and n - 1 (Fp), which cancels the force component that alternates every step (the
+// penalized interior's velocity is reflected about U_O each step):
+// v <- v + ((F + Fp) / 2 - k (x - x0) - c v) / M, then x <- x + v (semi-implicit Euler,
+// dt = 1), each operation rounded as written; an axis that is not free keeps its velocity.
+__device__ __forceinline__ void fsi_axis(double F, double Fp, double k, double c, double M, bool free_axis,
                                          double x0, double &x, double &v) {
   if (free_axis) {
-    double t = __dsub_rn(F, __dmul_rn(k, __dsub_rn(x, x0)));
+    const double Fm = __dmul_rn(__dadd_rn(F, Fp), 0.5);
+    double t = __dsub_rn(Fm, __dmul_rn(k, __dsub_rn(x, x0)));
     t = __dsub_rn(t, __dmul_rn(c, v));
     v = __dadd_rn(v, __ddiv_rn(t, M));
   }
@@ -344,20 +347,21 @@ fsi_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Cou
       double *b = D.bodies + 5 * lane;
       if (coupled(D, lane + 1)) {
         const double *par = D.fsi_par + 8 * lane;
-        const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + lane) * 4;
+        const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + lane) * 6;
         const double *F = D.ring + (static_cast<size_t>(n % D.force_cap) * D.nbodies + lane) * 2;
         double x = st[0], y = st[1], vx = st[2], vy = st[3];
-        fsi_axis(F[0], par[1], par[3], par[0], par[5] != 0.0, D.centre0[2 * lane], x, vx);
-        fsi_axis(F[1], par[2], par[4], par[0], par[6] != 0.0, D.centre0[2 * lane + 1], y, vy);
+        const double fx = F[0], fy = F[1];
+        fsi_axis(fx, st[4], par[1], par[3], par[0], par[5] != 0.0, D.centre0[2 * lane], x, vx);
+        fsi_axis(fy, st[5], par[2], par[4], par[0], par[6] != 0.0, D.centre0[2 * lane + 1], y, vy);
         cen[warp][lane][0] = x;
         cen[warp][lane][1] = y;
         if (j == 0) {
-          double *nst = D.fsi + (static_cast<size_t>((n + 1) & 1) * D.nbodies + lane) * 4;
-          const double v4[4] = {x, y, vx, vy};
+          double *nst = D.fsi + (static_cast<size_t>((n + 1) & 1) * D.nbodies + lane) * 6;
+          const double v6[6] = {x, y, vx, vy, fx, fy};
+          for (int e = 0; e < 6; ++e) nst[e] = v6[e];
           for (int e = 0; e < 4; ++e) {
-            nst[e] = v4[e];
-            b[e] = v4[e];
-            D.bodies_f[5 * lane + e] = float(v4[e]);
+            b[e] = v6[e];
+            D.bodies_f[5 * lane + e] = float(v6[e]);
           }
         }
       } else if (j == 0) {

@@ -69,7 +69,8 @@ struct DomDev {
   int32_t nb_nx[2], nb_pitch[2];
   void *nb_lat[2][2];  // [side][lattice A/B]
   // coupled bodies of a moving domain (fluid-structure coupling; null / 0 otherwise)
-  double *fsi;              // [2][nbodies][4] body state (x, y, vx, vy) of step n in [n & 1]
+  double *fsi;              // [2][nbodies][6] body state of step n in [n & 1]: x, y, vx, vy
+                            // and the force of step n - 1 (Fx, Fy)
   const double *fsi_par;    // [nbodies][8]: mass, k_x, k_y, c_x, c_y, free_x, free_y, coupled
   int32_t fsi_on;           // some body of the domain is coupled
   int32_t fsi_pad;

@@ -115,9 +115,9 @@ Layout layout_of(const lbm_params &p, int nbodies) {
     o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
     L.rowsum_off = o;
     o += align_up(sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
-    // coupled bodies: state of two step parities [2][nbodies][4], parameters [nbodies][8]
+    // coupled bodies: state of two step parities [2][nbodies][6], parameters [nbodies][8]
     L.fsi_off = o;
-    o += align_up(sizeof(double) * 16 * std::max(1, nbodies), 256);
+    o += align_up(sizeof(double) * 20 * std::max(1, nbodies), 256);
   }
   L.total = o;
   return L;
@@ -627,7 +627,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
   D.rowsum = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
   D.fsi = p->moving ? reinterpret_cast<double *>(base + L.fsi_off) : nullptr;
-  D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 8 * std::max(1, nbodies) : nullptr;
+  D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 12 * std::max(1, nbodies) : nullptr;
   D.fsi_on = 0;
   D.nx = p->nx;
   D.ny = p->ny;
@@ -725,7 +725,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
                              cudaMemcpyHostToDevice, st));
     // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
     ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
-    ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 16 * std::max(1, nbodies), st));
+    ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 20 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
     ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
   }
@@ -1141,14 +1141,14 @@ lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, cons
   }
   DomDev &D = s.dev;
   LBM_CUDA(cudaStreamSynchronize(b->st));
-  // the state of step 0 is the body's own centre and velocity
+  // the state of step 0 is the body's own centre and velocity, no earlier force
   double bt[5];
   LBM_CUDA(cudaMemcpyAsync(bt, D.bodies + 5 * (body - 1), sizeof(bt), cudaMemcpyDeviceToHost, b->st));
   LBM_CUDA(cudaStreamSynchronize(b->st));
-  const double st0[4] = {bt[0], bt[1], bt[2], bt[3]};
+  const double st0[6] = {bt[0], bt[1], bt[2], bt[3], 0.0, 0.0};
   const double par[8] = {dyn->mass, dyn->stiffness[0], dyn->stiffness[1], dyn->damping[0], dyn->damping[1],
                          double(dyn->free_axis[0]), double(dyn->free_axis[1]), 1.0};
-  LBM_CUDA(cudaMemcpyAsync(D.fsi + 4 * (body - 1), st0, sizeof(st0), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaMemcpyAsync(D.fsi + 6 * (body - 1), st0, sizeof(st0), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.fsi_par) + 8 * (body - 1), par, sizeof(par),
                            cudaMemcpyHostToDevice, b->st));
   D.fsi_on = 1;
