@@ -227,81 +227,102 @@ __device__ void place_centres(const DomDev &D, long long n, int lane) {
   }
 }
 
+// Rows of moving domains, one work item per row. Most rows lie far from every shape: a
+// warp first culls 32 of its items at once (lane l takes the item l strides ahead, FP32
+// column intervals at n and n + 1), then does the exact work on the items a shape
+// reaches, with the whole warp, one after the other. Busy rows stay spread over the
+// warps as in a plain one-row-per-warp loop.
 template <typename T>
-__global__ void __launch_bounds__(kMoveWarps * 32)
+__global__ void __launch_bounds__(kMoveWarps * 32, 2)
 move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr, int s) {
   __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RowShape *rs = shapes[warp];
   const int nrows = ctr->nmove;
   const long long run_base = ctr->run_base;
-  for (int q = blockIdx.x * kMoveWarps + warp; q < nrows; q += gridDim.x * kMoveWarps) {
-    const MoveRow mr = rows[q];
-    const DomDev &D = doms[mr.dom];
-    const DomDyn dy = dyn[mr.dom];
-    const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
-    if (n >= dy.step_end) continue;
-    const int j = mr.j;
-    // (a domain with coupled bodies takes only the row sums here: its next geometry
-    // depends on the force, and fsi_kernel places it after the force reduction)
-    const bool fsi = D.fsi_on != 0;
-    // column intervals of the row at the old index (n) and at the new one (n + 1), from
-    // FP32 positions (conservative); exact FP64 shapes only where the row is reached
-    int olo = D.nx, ohi = -1, nlo = D.nx, nhi = -1;
-    for (int k = lane; k < D.nshapes; k += 32) {
-      int lo, hi;
-      shape_cols_f32(D, D.shapes[k], n, j, lo, hi);
-      if (lo <= hi) { olo = min(olo, lo); ohi = max(ohi, hi); }
-      if (fsi) continue;
-      shape_cols_f32(D, D.shapes[k], n + 1, j, rs[k].lo, rs[k].hi);
-      if (rs[k].lo <= rs[k].hi) {
-        nlo = min(nlo, rs[k].lo);
-        nhi = max(nhi, rs[k].hi);
-        rs[k].s = shape_at(D, D.shapes[k], n + 1);
+  const int stride = gridDim.x * kMoveWarps;
+  for (int base = blockIdx.x * kMoveWarps + warp; base < nrows; base += 32 * stride) {
+    // lane l: item base + l * stride
+    const int ql = base + lane * stride;
+    int olo = 1, ohi = 0, nlo = 1, nhi = 0;
+    bool busy = false;
+    if (ql < nrows) {
+      const MoveRow mr = rows[ql];
+      const DomDev &D = doms[mr.dom];
+      const DomDyn dy = dyn[mr.dom];
+      const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
+      if (n < dy.step_end) {
+        const bool fsi = D.fsi_on != 0;
+        olo = D.nx; ohi = -1; nlo = D.nx; nhi = -1;
+        for (int k = 0; k < D.nshapes; ++k) {
+          int lo, hi;
+          shape_cols_f32(D, D.shapes[k], n, mr.j, lo, hi);
+          if (lo <= hi) { olo = min(olo, lo); ohi = max(ohi, hi); }
+          if (fsi) continue;
+          shape_cols_f32(D, D.shapes[k], n + 1, mr.j, lo, hi);
+          if (lo <= hi) { nlo = min(nlo, lo); nhi = max(nhi, hi); }
+        }
+        // row 0 also moves the body centres (domains without coupled bodies)
+        busy = olo <= ohi || nlo <= nhi || (mr.j == 0 && !fsi);
       }
     }
-    olo = __reduce_min_sync(0xffffffffu, olo);
-    ohi = __reduce_max_sync(0xffffffffu, ohi);
-    nlo = __reduce_min_sync(0xffffffffu, nlo);
-    nhi = __reduce_max_sync(0xffffffffu, nhi);
-    __syncwarp();
-    if (olo > ohi && nlo > nhi) {  // no shape near this row at either index
-      if (j == 0 && !fsi) place_centres(D, n + 1, lane);
-      continue;
-    }
-    const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
-    if (D.force_every > 0 && (n + 1) % D.force_every == 0 && olo <= ohi) {
-      // -F_VP of each body over the row's solid nodes (all inside the old interval), with
-      // the step index as a tag: the force kernel adds only the entries of its step, so
-      // rows that no shape reaches need no entry
-      const T *fv = static_cast<const T *>(D.fvp) + 2 * static_cast<size_t>(j) * D.pitch;
-      for (int body = 1; body <= D.nbodies; ++body) {
-        double fx = 0.0, fy = 0.0;
-        for (int i = olo + lane; i <= ohi; i += 32)
-          if (mrow[i] == body) {
-            fx -= double(fv[2 * i]);
-            fy -= double(fv[2 * i + 1]);
-          }
+    unsigned work = __ballot_sync(0xffffffffu, busy);
+    while (work) {
+      const int l = __ffs(work) - 1;
+      work &= work - 1;
+      const int q = base + l * stride;
+      const int jolo = __shfl_sync(0xffffffffu, olo, l), johi = __shfl_sync(0xffffffffu, ohi, l);
+      const int jnlo = __shfl_sync(0xffffffffu, nlo, l), jnhi = __shfl_sync(0xffffffffu, nhi, l);
+      const MoveRow mr = rows[q];
+      const DomDev &D = doms[mr.dom];
+      const DomDyn dy = dyn[mr.dom];
+      const long long n = dy.step0 + run_base + s;
+      const int j = mr.j;
+      // (a domain with coupled bodies takes only the row sums here: its next geometry
+      // depends on the force, and fsi_kernel places it after the force reduction)
+      const bool fsi = D.fsi_on != 0;
+      const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
+      if (D.force_every > 0 && (n + 1) % D.force_every == 0 && jolo <= johi) {
+        // -F_VP of each body over the row's solid nodes (all inside the old interval),
+        // with the step index as a tag: the force kernel adds only the entries of its
+        // step, so rows that no shape reaches need no entry
+        const T *fv = static_cast<const T *>(D.fvp) + 2 * static_cast<size_t>(j) * D.pitch;
+        for (int body = 1; body <= D.nbodies; ++body) {
+          double fx = 0.0, fy = 0.0;
+          for (int i = jolo + lane; i <= johi; i += 32)
+            if (mrow[i] == body) {
+              fx -= double(fv[2 * i]);
+              fy -= double(fv[2 * i + 1]);
+            }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          fx += __shfl_down_sync(0xffffffffu, fx, off);
-          fy += __shfl_down_sync(0xffffffffu, fy, off);
-        }
-        if (lane == 0) {
-          double *r = D.rowsum + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
-          r[0] = fx;
-          r[1] = fy;
-          r[2] = static_cast<double>(n);
+          for (int off = 16; off > 0; off >>= 1) {
+            fx += __shfl_down_sync(0xffffffffu, fx, off);
+            fy += __shfl_down_sync(0xffffffffu, fy, off);
+          }
+          if (lane == 0) {
+            double *r = D.rowsum + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
+            r[0] = fx;
+            r[1] = fy;
+            r[2] = static_cast<double>(n);
+          }
         }
       }
+      __syncwarp();
+      if (fsi) continue;
+      // the mask changes only where a shape reaches at either index: the shapes at
+      // n + 1 with their column intervals in this row, then their ids over the union
+      const int c0 = min(jolo, jnlo), c1 = max(johi, jnhi);
+      if (c0 <= c1) {
+        for (int k = lane; k < D.nshapes; k += 32) {
+          shape_cols_f32(D, D.shapes[k], n + 1, j, rs[k].lo, rs[k].hi);
+          if (rs[k].lo <= rs[k].hi) rs[k].s = shape_at(D, D.shapes[k], n + 1);
+        }
+        __syncwarp();
+        write_ids(D, j, c0, c1, lane, rs);
+      }
+      __syncwarp();
+      if (j == 0) place_centres(D, n + 1, lane);
     }
-    __syncwarp();
-    if (fsi) continue;
-    // the mask changes only where a shape reaches at either index
-    const int c0 = min(olo, nlo), c1 = max(ohi, nhi);
-    if (c0 <= c1) write_ids(D, j, c0, c1, lane, rs);
-    __syncwarp();
-    if (j == 0) place_centres(D, n + 1, lane);
   }
 }
 
