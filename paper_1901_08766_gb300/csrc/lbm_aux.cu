@@ -285,9 +285,14 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       if (D.force_every > 0 && (n + 1) % D.force_every == 0 && jolo <= johi) {
         // -F_VP of each body over the row's solid nodes (all inside the old interval),
         // with the step index as a tag: the force kernel adds only the entries of its
-        // step, so rows that no shape reaches need no entry
+        // step, so rows (or bodies) without solid nodes here need no entry
         const T *fv = static_cast<const T *>(D.fvp) + 2 * static_cast<size_t>(j) * D.pitch;
-        for (int body = 1; body <= D.nbodies; ++body) {
+        unsigned present = 0u;  // bit b: body b has a node in the interval
+        for (int i = jolo + lane; i <= johi; i += 32) present |= 1u << (mrow[i] & 31);
+        present = __reduce_or_sync(0xffffffffu, present) & ~1u;
+        while (present) {
+          const int body = __ffs(present) - 1;
+          present &= present - 1;
           double fx = 0.0, fy = 0.0;
           for (int i = jolo + lane; i <= johi; i += 32)
             if (mrow[i] == body) {
