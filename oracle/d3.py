@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the TRT-LBM-VP method in 3D (D3Q19) — TEST INFRASTRUCTURE.
+"""FP64 CPU oracle of the TRT-LBM-VP method in 3D (D3Q19 or D3Q15) — TEST INFRASTRUCTURE.
 
 The arithmetic lives in ``lbm_oracle3d.c`` (plain C, FP64, one node at a time); this
 module builds it with gcc and marshals numpy arrays. Only the tests and the benchmark's
@@ -6,7 +6,8 @@ CPU baseline use it; the CUDA library never does. Pinned by tests/test_oracle3d_
 
 Spec of a 3D case: nx, ny, nz, nu, magic_lambda, eta, rho0, u_in (3), u0 (3), edges
 {west, east, south, north, bottom, top}, shapes [{kind: sphere | cylinder_z, body,
-c (3), radius}], bodies [{c, v, w (3 each), ref_length}].
+c (3), radius}], bodies [{c, v, w (3 each), ref_length}], and optionally lattice 19
+(default, D3Q19) or 15 (D3Q15).
 """
 from __future__ import annotations
 
@@ -33,7 +34,7 @@ class _Params(C.Structure):
                 ("magic_lambda", C.c_double), ("eta", C.c_double), ("rho0", C.c_double),
                 ("u_in", C.c_double * 3), ("west", C.c_int32), ("east", C.c_int32),
                 ("south", C.c_int32), ("north", C.c_int32), ("bottom", C.c_int32),
-                ("top", C.c_int32)]
+                ("top", C.c_int32), ("q", C.c_int32)]
 
 
 class _Body(C.Structure):
@@ -71,8 +72,8 @@ def lib():
         L.ora3_tau_s.argtypes = [P]
         L.ora3_tau_a.restype = C.c_double
         L.ora3_tau_a.argtypes = [P]
-        L.ora3_equilibrium.argtypes = [C.c_double, dp, dp]
-        L.ora3_guo.argtypes = [dp, dp, dp]
+        L.ora3_equilibrium.argtypes = [C.c_int32, C.c_double, dp, dp]
+        L.ora3_guo.argtypes = [C.c_int32, dp, dp, dp]
         L.ora3_rasterize.argtypes = [C.c_int32, C.c_int32, C.c_int32, S, C.c_int32, u8p]
         L.ora3_stream.argtypes = [P, dp, dp]
         L.ora3_step_trt.argtypes = [P, u8p, B, C.c_int32, dp, dp, dp]
@@ -80,7 +81,8 @@ def lib():
         L.ora3_run.argtypes = [P, u8p, B, C.c_int32, dp, C.c_int64, dp]
         L.ora3_init.argtypes = [P, dp, dp]
         L.ora3_moments.argtypes = [P, u8p, B, dp, dp, dp, dp, dp]
-        L.ora3_lattice.argtypes = [i32p, i32p, i32p, dp, i32p]
+        L.ora3_lattice.restype = C.c_int32
+        L.ora3_lattice.argtypes = [C.c_int32, i32p, i32p, i32p, dp, i32p]
         _lib = L
     return _lib
 
@@ -97,13 +99,21 @@ def _vec(x):
     return (C.c_double * 3)(*[float(v) for v in x])
 
 
-def lattice():
-    """(EX, EY, EZ, W, OPP) of the oracle's D3Q19 velocity set."""
-    ex, ey, ez, opp = (np.zeros(19, dtype=np.int32) for _ in range(4))
-    w = np.zeros(19)
+def nq(spec_or_q=19) -> int:
+    """Number of directions of a spec's lattice (or of a lattice given as 15 or 19)."""
+    q = spec_or_q.get("lattice", 19) if isinstance(spec_or_q, dict) else int(spec_or_q)
+    return 15 if q == 15 else 19
+
+
+def lattice(q=19):
+    """(EX, EY, EZ, W, OPP) of the oracle's D3Q19 (q = 19) or D3Q15 (q = 15) velocity set."""
+    n = nq(q)
+    ex, ey, ez, opp = (np.zeros(n, dtype=np.int32) for _ in range(4))
+    w = np.zeros(n)
     i32 = C.POINTER(C.c_int32)
-    lib().ora3_lattice(ex.ctypes.data_as(i32), ey.ctypes.data_as(i32), ez.ctypes.data_as(i32),
-                       _dp(w), opp.ctypes.data_as(i32))
+    got = lib().ora3_lattice(n, ex.ctypes.data_as(i32), ey.ctypes.data_as(i32), ez.ctypes.data_as(i32),
+                             _dp(w), opp.ctypes.data_as(i32))
+    assert got == n
     return ex, ey, ez, w, opp
 
 
@@ -112,7 +122,7 @@ def params_of(spec) -> _Params:
     return _Params(spec["nx"], spec["ny"], spec["nz"], spec["nu"], spec["magic_lambda"],
                    spec["eta"], spec["rho0"], _vec(spec["u_in"]), EDGE[e["west"]],
                    EDGE[e["east"]], EDGE[e["south"]], EDGE[e["north"]], EDGE[e["bottom"]],
-                   EDGE[e["top"]])
+                   EDGE[e["top"]], nq(spec))
 
 
 def _shapes_of(spec):
@@ -135,15 +145,15 @@ def tau_s(spec):
     return lib().ora3_tau_s(C.byref(params_of(spec)))
 
 
-def equilibrium(rho, u):
-    out = np.zeros(19)
-    lib().ora3_equilibrium(rho, _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
+def equilibrium(rho, u, q=19):
+    out = np.zeros(nq(q))
+    lib().ora3_equilibrium(nq(q), rho, _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
     return out
 
 
-def guo(u, F):
-    out = np.zeros(19)
-    lib().ora3_guo(_dp(np.ascontiguousarray(u, dtype=np.float64)),
+def guo(u, F, q=19):
+    out = np.zeros(nq(q))
+    lib().ora3_guo(nq(q), _dp(np.ascontiguousarray(u, dtype=np.float64)),
                    _dp(np.ascontiguousarray(F, dtype=np.float64)), _dp(out))
     return out
 
@@ -171,7 +181,7 @@ class Domain:
         self.p = params_of(spec)
         self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask, dtype=np.uint8)
         self.bodies, self.nb = _bodies_of(spec)
-        shape = (19, spec["nz"], spec["ny"], spec["nx"])
+        shape = (nq(spec), spec["nz"], spec["ny"], spec["nx"])
         if g is None:
             self.g = np.zeros(shape)
             lib().ora3_init(C.byref(self.p), _dp(np.asarray(spec["u0"], dtype=np.float64)), _dp(self.g))

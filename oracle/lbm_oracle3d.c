@@ -1,14 +1,15 @@
 /*
- * Plain FP64 CPU oracle of the TRT-LBM-VP method in 3D with the D3Q19 lattice (the
- * paper's closing remark: the method extends to 3D by replacing D2Q9 with D3Q15 or
- * D3Q19; everything else is the 2D algorithm of Sec. 2.2 written for three axes).
+ * Plain FP64 CPU oracle of the TRT-LBM-VP method in 3D with the D3Q19 or the D3Q15
+ * lattice (the paper's closing remark: the method extends to 3D by replacing D2Q9 with
+ * D3Q15 or D3Q19; everything else is the 2D algorithm of Sec. 2.2 written for three axes).
  * TEST INFRASTRUCTURE ONLY, like lbm_oracle.c: used by the tests and the benchmark's CPU
  * baseline, never by the library. One node at a time, no fusion; compiled with
  * -O2 -ffp-contract=off.
  *
  * D3Q19 (readings listed in the design notes): e_0 = 0; e_1..6 = +-x, +-y, +-z; e_7..18
  * the twelve face diagonals; opposite directions come in pairs (2m-1, 2m); weights 1/3,
- * 1/18, 1/36; c_s^2 = 1/3. f^eq and the Guo term have the 2D form with three components.
+ * 1/18, 1/36. D3Q15: e_0, the same six axis directions, e_7..14 the eight cube corners
+ * (+-1, +-1, +-1) in opposite pairs; weights 2/9, 1/9, 1/72. c_s^2 = 1/3 for both. f^eq and the Guo term have the 2D form with three components.
  * Edges: x periodic or equilibrium inlet (west) / zero-gradient outflow (east); y and z
  * periodic or free slip (specular: e_y or e_z reversed); rules applied x, then y, then z.
  * U_O = V + omega x (x - c) with an angular velocity vector.
@@ -18,15 +19,34 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define Q3 19
+#define QMAX 19
 
-static const int EX3[Q3] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-static const int EY3[Q3] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-static const int EZ3[Q3] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-static const double W3[Q3] = {1.0 / 3.0,
-                              1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
-                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
-                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+typedef struct {
+  int q;
+  int ex[QMAX], ey[QMAX], ez[QMAX];
+  double w[QMAX];
+} lattice3;
+
+static const lattice3 D3Q19 = {
+    19,
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
+    {1.0 / 3.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0}};
+
+static const lattice3 D3Q15 = {
+    15,
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1},
+    {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1, 1, -1},
+    {2.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+     1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0}};
+
+/* the lattice of a parameter set: q = 15 selects D3Q15, anything else D3Q19 */
+static const lattice3 *lat3(int32_t q) { return q == 15 ? &D3Q15 : &D3Q19; }
+
 static const double CS2_3 = 1.0 / 3.0;
 
 enum { O3_PERIODIC = 0, O3_INLET = 1, O3_OUTFLOW = 2, O3_FREE_SLIP = 3 };
@@ -37,6 +57,7 @@ typedef struct {
   double nu, magic_lambda, eta, rho0;
   double u_in[3];
   int32_t west, east, south, north, bottom, top;
+  int32_t q; /* 19: D3Q19, 15: D3Q15 */
 } ora3_params;
 
 typedef struct {
@@ -49,10 +70,10 @@ typedef struct {
 } ora3_shape;
 
 /* direction with e_y (or e_z) reversed: the specular reflection of free-slip walls */
-static int reflect3(int a, int axis) {
-  for (int b = 0; b < Q3; b++)
-    if (EX3[b] == EX3[a] && (axis == 1 ? (EY3[b] == -EY3[a] && EZ3[b] == EZ3[a])
-                                       : (EY3[b] == EY3[a] && EZ3[b] == -EZ3[a])))
+static int reflect3(const lattice3 *L, int a, int axis) {
+  for (int b = 0; b < L->q; b++)
+    if (L->ex[b] == L->ex[a] && (axis == 1 ? (L->ey[b] == -L->ey[a] && L->ez[b] == L->ez[a])
+                                           : (L->ey[b] == L->ey[a] && L->ez[b] == -L->ez[a])))
       return b;
   return a;
 }
@@ -65,22 +86,24 @@ double ora3_tau_a(const ora3_params *p) {
 }
 
 /* Eq. (feq) with three velocity components */
-void ora3_equilibrium(double rho, const double *u, double *feq) {
+void ora3_equilibrium(int32_t q, double rho, const double *u, double *feq) {
+  const lattice3 *L = lat3(q);
   double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  for (int a = 0; a < Q3; a++) {
-    double eu = EX3[a] * u[0] + EY3[a] * u[1] + EZ3[a] * u[2];
-    feq[a] = W3[a] * rho * (1.0 + eu / CS2_3 + eu * eu / (2.0 * CS2_3 * CS2_3) - usq / (2.0 * CS2_3));
+  for (int a = 0; a < L->q; a++) {
+    double eu = L->ex[a] * u[0] + L->ey[a] * u[1] + L->ez[a] * u[2];
+    feq[a] = L->w[a] * rho * (1.0 + eu / CS2_3 + eu * eu / (2.0 * CS2_3 * CS2_3) - usq / (2.0 * CS2_3));
   }
 }
 
 /* Guo term F_alpha = w_alpha [(e - u)/c_s^2 + (e.u) e / c_s^4] . F (Eq. external-force-term) */
-void ora3_guo(const double *u, const double *F, double *out) {
-  for (int a = 0; a < Q3; a++) {
-    double e[3] = {EX3[a], EY3[a], EZ3[a]};
+void ora3_guo(int32_t q, const double *u, const double *F, double *out) {
+  const lattice3 *L = lat3(q);
+  for (int a = 0; a < L->q; a++) {
+    double e[3] = {L->ex[a], L->ey[a], L->ez[a]};
     double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
     double s = 0.0;
     for (int d = 0; d < 3; d++) s += ((e[d] - u[d]) / CS2_3 + eu * e[d] / (CS2_3 * CS2_3)) * F[d];
-    out[a] = W3[a] * s;
+    out[a] = L->w[a] * s;
   }
 }
 
@@ -112,7 +135,8 @@ static inline size_t IDX3(const ora3_params *p, int a, int k, int j, int i) {
 /* f_alpha(i, j, k) = g_alpha(x - e_alpha) with the edge rules: x, then y, then z. */
 static double pull3(const ora3_params *p, const double *g, const double *feq_inlet, int a, int i,
                     int j, int k) {
-  int sx = i - EX3[a], sy = j - EY3[a], sz = k - EZ3[a], src = a;
+  const lattice3 *L = lat3(p->q);
+  int sx = i - L->ex[a], sy = j - L->ey[a], sz = k - L->ez[a], src = a;
   if (sx < 0) {
     if (p->west == O3_INLET) return feq_inlet[a];
     sx += p->nx;
@@ -121,26 +145,26 @@ static double pull3(const ora3_params *p, const double *g, const double *feq_inl
     else sx -= p->nx;
   }
   if (sy < 0) {
-    if (p->south == O3_FREE_SLIP) { sy = 0; src = reflect3(src, 1); }
+    if (p->south == O3_FREE_SLIP) { sy = 0; src = reflect3(L, src, 1); }
     else sy += p->ny;
   } else if (sy > p->ny - 1) {
-    if (p->north == O3_FREE_SLIP) { sy = p->ny - 1; src = reflect3(src, 1); }
+    if (p->north == O3_FREE_SLIP) { sy = p->ny - 1; src = reflect3(L, src, 1); }
     else sy -= p->ny;
   }
   if (sz < 0) {
-    if (p->bottom == O3_FREE_SLIP) { sz = 0; src = reflect3(src, 2); }
+    if (p->bottom == O3_FREE_SLIP) { sz = 0; src = reflect3(L, src, 2); }
     else sz += p->nz;
   } else if (sz > p->nz - 1) {
-    if (p->top == O3_FREE_SLIP) { sz = p->nz - 1; src = reflect3(src, 2); }
+    if (p->top == O3_FREE_SLIP) { sz = p->nz - 1; src = reflect3(L, src, 2); }
     else sz -= p->nz;
   }
   return g[IDX3(p, src, sz, sy, sx)];
 }
 
 void ora3_stream(const ora3_params *p, const double *g, double *f) {
-  double feq_inlet[Q3];
-  ora3_equilibrium(p->rho0, p->u_in, feq_inlet);
-  for (int a = 0; a < Q3; a++)
+  double feq_inlet[QMAX];
+  ora3_equilibrium(p->q, p->rho0, p->u_in, feq_inlet);
+  for (int a = 0; a < lat3(p->q)->q; a++)
     for (int k = 0; k < p->nz; k++)
       for (int j = 0; j < p->ny; j++)
         for (int i = 0; i < p->nx; i++) f[IDX3(p, a, k, j, i)] = pull3(p, g, feq_inlet, a, i, j, k);
@@ -158,12 +182,13 @@ static void body_velocity3(const ora3_body *b, int i, int j, int k, double *uo) 
  * (Eq. d-V, Eq. force-density), corrected velocity (Eq. velocity-r) */
 static void node3(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
                   const double *f, int i, int j, int k, double *rho, double *u, double *fv) {
+  const lattice3 *L = lat3(p->q);
   double r = 0.0, jm[3] = {0.0, 0.0, 0.0};
-  for (int a = 0; a < Q3; a++) {
+  for (int a = 0; a < L->q; a++) {
     r += f[a];
-    jm[0] += EX3[a] * f[a];
-    jm[1] += EY3[a] * f[a];
-    jm[2] += EZ3[a] * f[a];
+    jm[0] += L->ex[a] * f[a];
+    jm[1] += L->ey[a] * f[a];
+    jm[2] += L->ez[a] * f[a];
   }
   int b = mask[((size_t)k * p->ny + j) * p->nx + i];
   double chi = b ? 1.0 : 0.0, uo[3] = {0.0, 0.0, 0.0};
@@ -182,8 +207,9 @@ static void node3(const ora3_params *p, const uint8_t *mask, const ora3_body *bo
 void ora3_step_trt(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
                    int32_t nbodies, const double *g_in, double *g_out, double *force) {
   const double tau_s = ora3_tau_s(p), tau_a = ora3_tau_a(p);
-  double feq_inlet[Q3];
-  ora3_equilibrium(p->rho0, p->u_in, feq_inlet);
+  const int nq = lat3(p->q)->q;
+  double feq_inlet[QMAX];
+  ora3_equilibrium(p->q, p->rho0, p->u_in, feq_inlet);
   size_t cells = (size_t)p->nx * p->ny * p->nz;
   double *fvall = (double *)malloc(sizeof(double) * 3 * cells);
   if (!fvall) abort();
@@ -191,12 +217,12 @@ void ora3_step_trt(const ora3_params *p, const uint8_t *mask, const ora3_body *b
   for (int k = 0; k < p->nz; k++)
     for (int j = 0; j < p->ny; j++)
       for (int i = 0; i < p->nx; i++) {
-        double f[Q3], feq[Q3], F[Q3], rho, u[3], fv[3];
-        for (int a = 0; a < Q3; a++) f[a] = pull3(p, g_in, feq_inlet, a, i, j, k);
+        double f[QMAX], feq[QMAX], F[QMAX], rho, u[3], fv[3];
+        for (int a = 0; a < nq; a++) f[a] = pull3(p, g_in, feq_inlet, a, i, j, k);
         node3(p, mask, bodies, f, i, j, k, &rho, u, fv);
-        ora3_equilibrium(rho, u, feq);
-        ora3_guo(u, fv, F);
-        for (int a = 0; a < Q3; a++) {
+        ora3_equilibrium(p->q, rho, u, feq);
+        ora3_guo(p->q, u, fv, F);
+        for (int a = 0; a < nq; a++) {
           int o = opposite3(a);
           double fs = 0.5 * (f[a] + f[o]), fa = 0.5 * (f[a] - f[o]);
           double feqs = 0.5 * (feq[a] + feq[o]), feqa = 0.5 * (feq[a] - feq[o]);
@@ -220,7 +246,8 @@ void ora3_step_trt(const ora3_params *p, const uint8_t *mask, const ora3_body *b
 int ora3_run(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies, int32_t nbodies,
              double *g, int64_t n, double *forces) {
   size_t cells = (size_t)p->nx * p->ny * p->nz;
-  double *tmp = (double *)malloc(sizeof(double) * Q3 * cells);
+  const int nq = lat3(p->q)->q;
+  double *tmp = (double *)malloc(sizeof(double) * nq * cells);
   double *fb = (double *)malloc(sizeof(double) * 3 * (nbodies > 0 ? nbodies : 1));
   if (!tmp || !fb) { free(tmp); free(fb); return -1; }
   double *a = g, *b = tmp;
@@ -229,29 +256,30 @@ int ora3_run(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
     if (forces) memcpy(forces + (size_t)s * 3 * nbodies, fb, sizeof(double) * 3 * nbodies);
     double *t = a; a = b; b = t;
   }
-  if (a != g) memcpy(g, a, sizeof(double) * Q3 * cells);
+  if (a != g) memcpy(g, a, sizeof(double) * nq * cells);
   free(tmp);
   free(fb);
   return 0;
 }
 
 void ora3_init(const ora3_params *p, const double *u0, double *g) {
-  double feq[Q3];
-  ora3_equilibrium(p->rho0, u0, feq);
+  double feq[QMAX];
+  ora3_equilibrium(p->q, p->rho0, u0, feq);
   size_t cells = (size_t)p->nx * p->ny * p->nz;
-  for (int a = 0; a < Q3; a++)
+  for (int a = 0; a < lat3(p->q)->q; a++)
     for (size_t c = 0; c < cells; c++) g[a * cells + c] = feq[a];
 }
 
 void ora3_moments(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
                   const double *g, double *rho, double *ux, double *uy, double *uz) {
-  double feq_inlet[Q3];
-  ora3_equilibrium(p->rho0, p->u_in, feq_inlet);
+  double feq_inlet[QMAX];
+  ora3_equilibrium(p->q, p->rho0, p->u_in, feq_inlet);
+  const int nq = lat3(p->q)->q;
   for (int k = 0; k < p->nz; k++)
     for (int j = 0; j < p->ny; j++)
       for (int i = 0; i < p->nx; i++) {
-        double f[Q3], r, u[3], fv[3];
-        for (int a = 0; a < Q3; a++) f[a] = pull3(p, g, feq_inlet, a, i, j, k);
+        double f[QMAX], r, u[3], fv[3];
+        for (int a = 0; a < nq; a++) f[a] = pull3(p, g, feq_inlet, a, i, j, k);
         node3(p, mask, bodies, f, i, j, k, &r, u, fv);
         size_t c = ((size_t)k * p->ny + j) * p->nx + i;
         rho[c] = r;
@@ -261,13 +289,17 @@ void ora3_moments(const ora3_params *p, const uint8_t *mask, const ora3_body *bo
       }
 }
 
-/* the velocity set, for the pins */
-void ora3_lattice(int32_t *ex, int32_t *ey, int32_t *ez, double *w, int32_t *opp) {
-  for (int a = 0; a < Q3; a++) {
-    ex[a] = EX3[a];
-    ey[a] = EY3[a];
-    ez[a] = EZ3[a];
-    w[a] = W3[a];
+/* the velocity set of lattice q (15 or 19; its size is returned, -1 without writing if the
+ * selected table has another size than the caller's buffers), for the pins */
+int32_t ora3_lattice(int32_t q, int32_t *ex, int32_t *ey, int32_t *ez, double *w, int32_t *opp) {
+  const lattice3 *L = lat3(q);
+  if (L->q != (q == 15 ? 15 : 19)) return -1;
+  for (int a = 0; a < L->q; a++) {
+    ex[a] = L->ex[a];
+    ey[a] = L->ey[a];
+    ez[a] = L->ez[a];
+    w[a] = L->w[a];
     opp[a] = opposite3(a);
   }
+  return L->q;
 }

@@ -332,14 +332,16 @@ PARITY_CASES = ("periodic_97x61", "channel_97x61", "channel_256x128", "mixed_edg
 # 3D (D3Q19) inputs: same conventions, nineteen directions (rest, six axis, twelve face
 # diagonals), arrays [19, nz, ny, nx].
 
-_POP_SCALE3 = np.array([0.33] + [0.055] * 6 + [0.028] * 12)
+_POP_SCALE3 = {19: np.array([0.33] + [0.055] * 6 + [0.028] * 12),
+               15: np.array([0.22] + [0.11] * 6 + [0.014] * 8)}
 
 
-def random_populations3(seed: int, nx: int, ny: int, nz: int, amp: float = 0.1) -> np.ndarray:
-    """Positive random populations [19, nz, ny, nx]: scale[q] * (1 + amp * (xi - 0.5)),
-    xi drawn in (q, k, j, i) order (density ~0.99, velocities of order 1e-2)."""
-    xi = SplitMix64(seed).doubles(19 * nz * ny * nx).reshape(19, nz, ny, nx)
-    return _POP_SCALE3[:, None, None, None] * (1.0 + amp * (xi - 0.5))
+def random_populations3(seed: int, nx: int, ny: int, nz: int, amp: float = 0.1, q: int = 19) -> np.ndarray:
+    """Positive random populations [q, nz, ny, nx] of D3Q19 (q = 19) or D3Q15 (q = 15):
+    scale[a] * (1 + amp * (xi - 0.5)), xi drawn in (a, k, j, i) order (density ~0.99,
+    velocities of order 1e-2)."""
+    xi = SplitMix64(seed).doubles(q * nz * ny * nx).reshape(q, nz, ny, nx)
+    return _POP_SCALE3[q][:, None, None, None] * (1.0 + amp * (xi - 0.5))
 
 
 def edges3(west="periodic", east="periodic", south="periodic", north="periodic",
@@ -367,8 +369,8 @@ def body3(c, ref_length, v=(0.0, 0.0, 0.0), w=(0.0, 0.0, 0.0)):
 
 
 def spec3(name, nx, ny, nz, nu, shapes, bodies, steps, U, edges, u_in=(0.0, 0.0, 0.0),
-          u0=(0.0, 0.0, 0.0), magic_lambda=3.0 / 16.0, eta=1e-4, rho0=1.0):
-    return {"name": name, "nx": int(nx), "ny": int(ny), "nz": int(nz), "nu": float(nu),
+          u0=(0.0, 0.0, 0.0), magic_lambda=3.0 / 16.0, eta=1e-4, rho0=1.0, lattice=19):
+    return {"name": name, "lattice": int(lattice), "nx": int(nx), "ny": int(ny), "nz": int(nz), "nu": float(nu),
             "magic_lambda": float(magic_lambda), "eta": float(eta), "rho0": float(rho0),
             "u_in": tuple(float(v) for v in u_in), "u0": tuple(float(v) for v in u0),
             "edges": edges, "shapes": shapes, "bodies": bodies, "steps": int(steps), "U": float(U)}

@@ -21,8 +21,8 @@ def _weights(g):
     if np.shape(g)[0] == 9:
         return W
     if _W3 is None:
-        from oracle import d3q19
-        _W3 = d3q19.lattice()[3][:, None, None, None]
+        from oracle import d3
+        _W3 = d3.lattice()[3][:, None, None, None]
     return _W3
 
 
@@ -83,9 +83,9 @@ def ghost_ulp(spec, storage):
     """One unit of the stored type at the inlet ghost populations f^eq(rho0, u_in) (shifted
     for the 16-bit types): the library holds the ghost as the stored type would."""
     if "nz" in spec:
-        from oracle import d3q19
-        g = d3q19.equilibrium(spec["rho0"], spec["u_in"])
-        w = d3q19.lattice()[3]
+        from oracle import d3
+        g = d3.equilibrium(spec["rho0"], spec["u_in"])
+        w = d3.lattice()[3]
     else:
         g = oracle.equilibrium(spec["rho0"], *spec["u_in"])
         w = oracle.W

@@ -1,5 +1,5 @@
-"""Pins of the 3D (D3Q19) oracle against what the lattice, the paper's equations and
-mathematics fix: lattice isotropy, equilibrium and Guo moments, the sphere mask by brute
+"""Pins of the 3D oracle, for both lattices (D3Q19 and D3Q15), against what the lattice,
+the paper's equations and mathematics fix: lattice isotropy, equilibrium and Guo moments, the sphere mask by brute
 force, streaming as array rolls and mirror rules, invariant rest and uniform states,
 exact mass and momentum balance with bodies, the closed form of a fully penalized box,
 and the viscous decay rate of a shear wave (tau_s = nu / c_s^2 + 1/2)."""
@@ -10,36 +10,47 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import d3q19 as d3
+from oracle import d3 as d3
 
-EX, EY, EZ, W, OPP = d3.lattice()
-E = np.stack([EX, EY, EZ], axis=1).astype(float)
 CS2 = 1.0 / 3.0
+LATTICES = [19, 15]
+
+
+def _lat(q):
+    ex, ey, ez, w, opp = d3.lattice(q)
+    return np.stack([ex, ey, ez], axis=1).astype(float), w, opp
 
 
 def _moments(g):
+    E, _, _ = _lat(g.shape[0])
     rho = g.sum(axis=0)
     j = [np.tensordot(E[:, d], g, axes=(0, 0)) for d in range(3)]
     return rho, j
 
 
 def _spec(nx, ny, nz, nu=0.05, lam=3 / 16, edges=None, shapes=(), bodies=(), u0=(0, 0, 0),
-          u_in=(0, 0, 0), eta=1e-4):
+          u_in=(0, 0, 0), eta=1e-4, q=19):
     return synth.spec3("pin3", nx, ny, nz, nu, list(shapes), list(bodies), 0, 0.01,
-                       edges or synth.edges3(), u_in=u_in, u0=u0, magic_lambda=lam, eta=eta)
+                       edges or synth.edges3(), u_in=u_in, u0=u0, magic_lambda=lam, eta=eta,
+                       lattice=q)
 
 
-def test_d3q19_velocity_set_and_isotropy():
-    # nineteen distinct vectors: rest, six of length 1, twelve of length sqrt(2); opposite
-    # pairs; weights 1/3, 1/18, 1/36 summing to 1; odd moments vanish and the second and
-    # fourth moments are isotropic: sum w e_i e_j = c_s^2 delta_ij,
+@pytest.mark.parametrize("q", LATTICES)
+def test_velocity_set_and_isotropy(q):
+    # D3Q19: rest, six vectors of length 1, twelve of length sqrt(2), weights 1/3, 1/18,
+    # 1/36; D3Q15: rest, six of length 1, eight of length sqrt(3), weights 2/9, 1/9, 1/72.
+    # Distinct vectors; opposite pairs; weights summing to 1; odd moments vanish and the
+    # second and fourth moments are isotropic: sum w e_i e_j = c_s^2 delta_ij,
     # sum w e_i e_j e_k e_l = c_s^4 (d_ij d_kl + d_ik d_jl + d_il d_jk)
-    assert len({tuple(e) for e in E.astype(int)}) == 19
+    E, W, OPP = _lat(q)
+    assert len({tuple(e) for e in E.astype(int)}) == q
     n2 = (E ** 2).sum(axis=1)
-    assert sorted(n2.tolist()) == [0] + [1] * 6 + [2] * 12
-    for a in range(19):
+    diag = 2 if q == 19 else 3
+    assert sorted(n2.tolist()) == [0] + [1] * 6 + [diag] * (q - 7)
+    cls = {19: {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}, 15: {0: 2 / 9, 1: 1 / 9, 3: 1 / 72}}[q]
+    for a in range(q):
         assert np.array_equal(E[OPP[a]], -E[a])
-        assert W[a] == {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}[int(n2[a])]
+        assert W[a] == cls[int(n2[a])]
     assert W.sum() == pytest.approx(1.0, abs=1e-15)
     d = np.eye(3)
     for i in range(3):
@@ -53,9 +64,11 @@ def test_d3q19_velocity_set_and_isotropy():
                     assert (W * E[:, i] * E[:, j] * E[:, k] * E[:, l]).sum() == pytest.approx(want, abs=1e-15)
 
 
+@pytest.mark.parametrize("q", LATTICES)
 @pytest.mark.parametrize("rho,u", [(1.0, (0.0, 0.0, 0.0)), (0.97, (0.05, -0.03, 0.02))])
-def test_equilibrium_moments(rho, u):
-    f = d3.equilibrium(rho, u)
+def test_equilibrium_moments(rho, u, q):
+    E, _, _ = _lat(q)
+    f = d3.equilibrium(rho, u, q)
     u = np.array(u)
     assert f.sum() == pytest.approx(rho, rel=1e-14)
     assert np.allclose(E.T @ f, rho * u, atol=1e-15)
@@ -63,9 +76,11 @@ def test_equilibrium_moments(rho, u):
     assert np.allclose(pi, rho * (CS2 * np.eye(3) + np.outer(u, u)), atol=1e-15)
 
 
-def test_guo_term_moments():
+@pytest.mark.parametrize("q", LATTICES)
+def test_guo_term_moments(q):
+    E, _, _ = _lat(q)
     u, F = np.array([0.04, -0.02, 0.03]), np.array([-3e-4, 7e-4, 2e-4])
-    g = d3.guo(u, F)
+    g = d3.guo(u, F, q)
     assert abs(g.sum()) < 1e-18
     assert np.allclose(E.T @ g, F, atol=1e-18)
     assert np.allclose(np.einsum("a,ai,aj->ij", g, E, E), np.outer(u, F) + np.outer(F, u), atol=1e-18)
@@ -88,50 +103,57 @@ def test_rasterize_brute_force():
     assert (d3.rasterize(ball) == 1).sum() == n == 485
 
 
-def test_stream_periodic_is_a_roll_and_mirrors():
-    g = synth.random_populations3(3, 7, 6, 5)
-    f = d3.stream(_spec(7, 6, 5), g)
-    for a in range(19):
+@pytest.mark.parametrize("q", LATTICES)
+def test_stream_periodic_is_a_roll_and_mirrors(q):
+    E, _, _ = _lat(q)
+    EX, EY, EZ = (E[:, d].astype(int) for d in range(3))
+    g = synth.random_populations3(3, 7, 6, 5, q=q)
+    f = d3.stream(_spec(7, 6, 5, q=q), g)
+    for a in range(q):
         assert np.array_equal(f[a], np.roll(g[a], (EZ[a], EY[a], EX[a]), axis=(0, 1, 2)))
     # free slip on y and z: a source outside the rows/planes is the mirrored direction at
     # the clamped row/plane
     sp = _spec(7, 6, 5, edges=synth.edges3("periodic", "periodic", "free_slip", "free_slip",
-                                           "free_slip", "free_slip"))
+                                           "free_slip", "free_slip"), q=q)
     f = d3.stream(sp, g)
-    for a in range(19):
+    for a in range(q):
         for k, j, i in itertools.product(range(5), range(6), range(7)):
             sx, sy, sz, src = (i - EX[a]) % 7, j - EY[a], k - EZ[a], a
             if sy < 0 or sy > 5:
                 sy = min(max(sy, 0), 5)
-                src = [b for b in range(19) if EX[b] == EX[src] and EY[b] == -EY[src] and EZ[b] == EZ[src]][0]
+                src = [b for b in range(q) if EX[b] == EX[src] and EY[b] == -EY[src] and EZ[b] == EZ[src]][0]
             if sz < 0 or sz > 4:
                 sz = min(max(sz, 0), 4)
-                src = [b for b in range(19) if EX[b] == EX[src] and EY[b] == EY[src] and EZ[b] == -EZ[src]][0]
+                src = [b for b in range(q) if EX[b] == EX[src] and EY[b] == EY[src] and EZ[b] == -EZ[src]][0]
             assert f[a, k, j, i] == g[src, sz, sy, sx]
 
 
-def test_stream_inlet_outflow_columns():
+@pytest.mark.parametrize("q", LATTICES)
+def test_stream_inlet_outflow_columns(q):
     # x edges: a source west of column 0 is the inlet equilibrium f^eq(rho0, u_in); a source
     # east of the last column is the last column itself (zero gradient)
-    g = synth.random_populations3(4, 6, 5, 4)
+    E, _, _ = _lat(q)
+    EX, EY, EZ = (E[:, d].astype(int) for d in range(3))
+    g = synth.random_populations3(4, 6, 5, 4, q=q)
     u_in = (0.05, 0.01, -0.02)
-    sp = _spec(6, 5, 4, edges=synth.edges3("inlet", "outflow"), u_in=u_in)
+    sp = _spec(6, 5, 4, edges=synth.edges3("inlet", "outflow"), u_in=u_in, q=q)
     f = d3.stream(sp, g)
-    feq = d3.equilibrium(1.0, u_in)
-    for a in range(19):
+    feq = d3.equilibrium(1.0, u_in, q)
+    for a in range(q):
         for k, j, i in itertools.product(range(4), range(5), range(6)):
             sx, sy, sz = i - EX[a], (j - EY[a]) % 5, (k - EZ[a]) % 4
             want = feq[a] if sx < 0 else g[a, sz, sy, min(sx, 5)]
             assert f[a, k, j, i] == want
 
 
-def test_rotating_penalized_box_follows_the_body_velocity():
+@pytest.mark.parametrize("q", LATTICES)
+def test_rotating_penalized_box_follows_the_body_velocity(q):
     # chi = 1 everywhere, body translating at V and rotating at omega about c: the corrected
     # velocity u = u* + du of every node is U_O = V + omega x (x - c) within
     # 2 eta |u* - U_O| (Eq. d-V, Eq. velocity-r); fixes the cross product and its sign
     V, w, c = (0.01, -0.02, 0.005), (1e-3, -2e-3, 1.5e-3), (2.25, 2.75, 3.25)
     sp = _spec(6, 5, 7, nu=0.1, eta=1e-7, shapes=[synth.cylinder_z(1, 3.0, 2.0, 100.0)],
-               bodies=[synth.body3(c, 1, v=V, w=w)])
+               bodies=[synth.body3(c, 1, v=V, w=w)], q=q)
     d = d3.Domain(sp)
     d.run(50, want_forces=False)
     _, ux, uy, uz = d.moments()
@@ -143,22 +165,24 @@ def test_rotating_penalized_box_follows_the_body_velocity():
         assert np.max(np.abs(got - exp)) < 1e-7
 
 
+@pytest.mark.parametrize("q", LATTICES)
 @pytest.mark.parametrize("edges", [synth.edges3(), synth.channel_edges3()])
-def test_uniform_flow_invariant(edges):
+def test_uniform_flow_invariant(edges, q):
     u = (0.05, 0.0, 0.0) if edges["west"] == "inlet" else (0.04, -0.02, 0.03)
-    sp = _spec(9, 6, 5, edges=edges, u0=u, u_in=u)
+    sp = _spec(9, 6, 5, edges=edges, u0=u, u_in=u, q=q)
     d = d3.Domain(sp)
     g0 = d.g.copy()
     d.run(20, want_forces=False)
     assert np.max(np.abs(d.g - g0)) < 1e-15
 
 
-def test_mass_and_momentum_balance_with_bodies():
+@pytest.mark.parametrize("q", LATTICES)
+def test_mass_and_momentum_balance_with_bodies(q):
     shapes = [synth.sphere(1, (6.2, 7.1, 5.3), 3.5), synth.cylinder_z(2, 14.5, 6.0, 2.5)]
     bodies = [synth.body3((6.2, 7.1, 5.3), 7, v=(0.01, 0.0, -0.005), w=(1e-3, -2e-3, 3e-3)),
               synth.body3((14.5, 6.0, 0.0), 5)]
-    sp = _spec(19, 13, 11, lam=0.25, shapes=shapes, bodies=bodies)
-    d = d3.Domain(sp, g=synth.random_populations3(5, 19, 13, 11))
+    sp = _spec(19, 13, 11, lam=0.25, shapes=shapes, bodies=bodies, q=q)
+    d = d3.Domain(sp, g=synth.random_populations3(5, 19, 13, 11, q=q))
     m0 = d.g.sum()
     for _ in range(25):
         _, j0 = _moments(d.g)
@@ -171,14 +195,15 @@ def test_mass_and_momentum_balance_with_bodies():
     assert abs(d.g.sum() - m0) < 1e-12 * m0
 
 
-def test_fully_penalized_box_closed_form():
+@pytest.mark.parametrize("q", LATTICES)
+def test_fully_penalized_box_closed_form(q):
     # chi = 1 everywhere (a z-cylinder covering the box), uniform state: one step maps
     # u* - U_O to (u* - U_O)(2 eta - 1)/(2 eta + 1) and the force on the body is
     # -cells 2 rho (U_O - u*)/(2 eta + 1)
     eta = 0.05
     uo = (0.02, -0.01, 0.015)
     sp = _spec(4, 3, 5, nu=0.1, eta=eta, shapes=[synth.cylinder_z(1, 1.5, 1.0, 100.0)],
-               bodies=[synth.body3((0, 0, 0), 1, v=uo)], u0=(0.07, 0.03, -0.02))
+               bodies=[synth.body3((0, 0, 0), 1, v=uo)], u0=(0.07, 0.03, -0.02), q=q)
     d = d3.Domain(sp)
     assert np.all(d.mask == 1)
     fac = (2 * eta - 1) / (2 * eta + 1)
@@ -192,17 +217,18 @@ def test_fully_penalized_box_closed_form():
         assert np.allclose(fb[0], -60 * 2 * rho[0, 0, 0] * (np.array(uo) - us) / (2 * eta + 1), rtol=1e-11)
 
 
+@pytest.mark.parametrize("q", LATTICES)
 @pytest.mark.parametrize("nu,lam", [(0.1, 3 / 16), (0.02, 0.25)])
-def test_shear_wave_decay_rate(nu, lam):
+def test_shear_wave_decay_rate(nu, lam, q):
     # u_x = A sin(2 pi k / nz) decays as exp(-nu (2 pi / nz)^2 t) (second-order lattice
     # error: about 4x smaller per doubling of nz)
     def rel_err(nz):
         A, steps = 1e-3, int(0.3 * nz * nz / nu / (2 * math.pi) ** 2 * 4)
-        sp = _spec(2, 2, nz, nu=nu, lam=lam)
+        sp = _spec(2, 2, nz, nu=nu, lam=lam, q=q)
         kk = np.arange(nz)
-        g = np.stack([np.stack([np.stack([d3.equilibrium(1.0, (A * math.sin(2 * math.pi * k / nz), 0, 0))
+        g = np.stack([np.stack([np.stack([d3.equilibrium(1.0, (A * math.sin(2 * math.pi * k / nz), 0, 0), q)
                                           for _ in range(2)], axis=1) for _ in range(2)], axis=1)
-                      for k in kk], axis=1)  # [19, nz, 2, 2]
+                      for k in kk], axis=1)  # [q, nz, 2, 2]
         d = d3.Domain(sp, g=g)
         d.run(steps, want_forces=False)
         _, ux, _, _ = d.moments()
