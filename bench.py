@@ -567,8 +567,12 @@ def served_stream(lbm, torch, np, args):
             "latency": "arrival to last force slice on the host", "hbm_budget_bytes": budget}
 
 
-# bytes of one D3Q19 node per sweep: 19 populations read and written, the mask byte read
-BYTES3 = {"f16s": 19 * 2 * 2 + 1, "bf16s": 19 * 2 * 2 + 1, "f32": 19 * 4 * 2 + 1, "f64": 19 * 8 * 2 + 1}
+# bytes of one 3D node per sweep: Q populations read and written, the mask byte read
+ELEM = {"f16s": 2, "bf16s": 2, "f32": 4, "f64": 8}
+
+
+def bytes3(storage, q=19):
+    return q * ELEM[storage] * 2 + 1
 
 
 def sphere3d(lbm, torch, np, only=None):
@@ -580,8 +584,11 @@ def sphere3d(lbm, torch, np, only=None):
     perf = []
     spec = synth.sphere_channel(384, 128, 128, D=32.0)
     nodes = spec["nx"] * spec["ny"] * spec["nz"]
-    for st in only or ("f16s", "bf16s", "f32", "f64"):
-        d = lbm.Domain3(spec, storage=st, force_every=1)
+    runs = [(19, st) for st in (only or ("f16s", "bf16s", "f32", "f64"))]
+    if not only:
+        runs += [(15, st) for st in ("f16s", "bf16s", "f32")]
+    for q, st in runs:
+        d = lbm.Domain3(dict(spec, lattice=q), storage=st, force_every=1)
         d.step(20)
         d.forces()
         best = (1e30, 0.0)
@@ -591,10 +598,11 @@ def sphere3d(lbm, torch, np, only=None):
             best = min(best, (sw, fo))
         d.close()
         sw, fo = best
-        gbs = nodes * BYTES3[st] / sw / 1e3
-        perf.append({"storage": st, "grid": [spec["nx"], spec["ny"], spec["nz"]], "sweep_us": sw,
-                     "force_us": fo, "glups_sweep": nodes / sw / 1e3,
-                     "glups_step": nodes / (sw + fo) / 1e3, "bytes_per_node": BYTES3[st],
+        bpn = bytes3(st, q)
+        gbs = nodes * bpn / sw / 1e3
+        perf.append({"lattice": f"D3Q{q}", "storage": st, "grid": [spec["nx"], spec["ny"], spec["nz"]],
+                     "sweep_us": sw, "force_us": fo, "glups_sweep": nodes / sw / 1e3,
+                     "glups_step": nodes / (sw + fo) / 1e3, "bytes_per_node": bpn,
                      "achieved_gbs": gbs, "peak_gbs": peak[0], "frac": gbs / peak[0],
                      "peak_source": peak[1]})
     if only:
@@ -603,16 +611,20 @@ def sphere3d(lbm, torch, np, only=None):
     spec = synth.sphere_channel(192, 64, 64, D=16.0, re=100.0, steps=4000)
     D, U = spec["bodies"][0]["ref_length"], spec["U"]
     area = math.pi * D * D / 4.0
-    for st in ("f16s", "bf16s", "f32", "f64"):
-        d = lbm.Domain3(spec, storage=st)
-        f = d.run(spec["steps"])
-        d.close()
-        cd = f[:, 0, 0] / (0.5 * spec["rho0"] * U * U * area)
-        acc.append({"storage": st, "steps": spec["steps"], "cd_last_1000": float(cd[-1000:].mean()),
-                    "cy_last_1000": float((f[-1000:, 0, 1] / (0.5 * U * U * area)).mean())})
-    ref = acc[-1]["cd_last_1000"]
-    for r in acc:
-        r["cd_rel_vs_f64"] = (r["cd_last_1000"] - ref) / ref
+    for q in (19, 15):
+        rows = []
+        for st in ("f16s", "bf16s", "f32", "f64"):
+            d = lbm.Domain3(dict(spec, lattice=q), storage=st)
+            f = d.run(spec["steps"])
+            d.close()
+            cd = f[:, 0, 0] / (0.5 * spec["rho0"] * U * U * area)
+            rows.append({"lattice": f"D3Q{q}", "storage": st, "steps": spec["steps"],
+                         "cd_last_1000": float(cd[-1000:].mean()),
+                         "cy_last_1000": float((f[-1000:, 0, 1] / (0.5 * U * U * area)).mean())})
+        ref = rows[-1]["cd_last_1000"]
+        for r in rows:
+            r["cd_rel_vs_f64"] = (r["cd_last_1000"] - ref) / ref
+        acc += rows
     return {"perf": perf, "drag": acc, "case_perf": "sphere channel 384x128x128, D=32, Re=100",
             "case_drag": spec["name"]}
 

@@ -344,13 +344,15 @@ LBM_API lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_
 LBM_API lbm_status lbm_batch_body_state(lbm_batch *b, int32_t slot, double *out);
 LBM_API lbm_status lbm_body_state(lbm_domain *d, double *out);
 
-/* ---- 3D: D3Q19 TRT-LBM-VP (single domain) --------------------------------------------
+/* ---- 3D: D3Q19 / D3Q15 TRT-LBM-VP (single domain) ------------------------------------
  * The paper's closing remark: the method extends to 3D by replacing D2Q9 with D3Q15 or
- * D3Q19. This is the step of Sec. 2.2 with D3Q19: e_0 = 0; e_1..6 = +x, -x, +y, -y, +z,
- * -z; e_7..18 the face diagonals (+x+y, -x-y, +x-y, -x+y, +x+z, -x-z, +x-z, -x+z, +y+z,
- * -y-z, +y-z, -y+z), so directions 2m-1 and 2m are opposite; weights 1/3, 1/18, 1/36.
- * Populations [19][nz][ny][nx]; storage types, their rounding and the F16S scale as for
- * 2D. Edges: x as in 2D (PERIODIC / INLET_EQ west, PERIODIC / OUTFLOW_ZG east); y (south,
+ * D3Q19. This is the step of Sec. 2.2 with either lattice. D3Q19: e_0 = 0; e_1..6 = +x,
+ * -x, +y, -y, +z, -z; e_7..18 the face diagonals (+x+y, -x-y, +x-y, -x+y, +x+z, -x-z,
+ * +x-z, -x+z, +y+z, -y-z, +y-z, -y+z); weights 1/3, 1/18, 1/36. D3Q15: e_0..6 as D3Q19;
+ * e_7..14 the cube corners (+x+y+z, -x-y-z, +x+y-z, -x-y+z, +x-y+z, -x+y-z, -x+y+z,
+ * +x-y-z); weights 2/9, 1/9, 1/72. Directions 2m-1 and 2m are opposite. Populations
+ * [Q][nz][ny][nx] (Q = 19 or 15); storage types, their rounding and the F16S scale as
+ * for 2D. Edges: x as in 2D (PERIODIC / INLET_EQ west, PERIODIC / OUTFLOW_ZG east); y (south,
  * north) and z (bottom, top) PERIODIC or FREE_SLIP; rules applied x, then y, then z.
  * U_O = V + omega x (x - c) with an angular velocity vector. */
 typedef struct {
@@ -363,6 +365,7 @@ typedef struct {
   int32_t storage;          /* lbm_storage */
   int32_t force_every;      /* record body forces every k-th step (0: never) */
   int32_t force_capacity;   /* force-ring entries kept on the device (0: 8192) */
+  int32_t lattice;          /* 19 (or 0): D3Q19; 15: D3Q15 */
 } lbm3_params;
 
 typedef struct {
@@ -409,14 +412,20 @@ LBM_API lbm_status lbm3_forces(lbm3_domain *d, double *out, int64_t max_entries,
  * pointers, any may be NULL). Synchronises. */
 LBM_API lbm_status lbm3_moments(lbm3_domain *d, double *rho, double *ux, double *uy, double *uz);
 
-/* Raw populations [19][nz][ny][nx] in the storage type; bytes must equal
- * 19 nx ny nz element size. Synchronise. */
+/* Raw populations [Q][nz][ny][nx] in the storage type; bytes must equal
+ * Q nx ny nz element size (Q = 19 or 15). Synchronise. */
 LBM_API lbm_status lbm3_get_populations(lbm3_domain *d, void *out, size_t bytes);
 LBM_API lbm_status lbm3_set_populations(lbm3_domain *d, const void *in, size_t bytes);
 
 /* The body-id mask [nz][ny][nx]; steps done so far. */
 LBM_API lbm_status lbm3_get_mask(lbm3_domain *d, uint8_t *out);
 LBM_API lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps);
+
+/* Set the step index (>= 0), e.g. with populations restored by lbm3_set_populations: the
+ * 16-bit storages draw their rounding bits from the step index, so a resumed run repeats
+ * the original one bit for bit. Undrained force entries are dropped; later entries
+ * count from the new index. Synchronises. */
+LBM_API lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps);
 
 /* Run `steps` steps bracketing the sweep and the force reduction of each with CUDA
  * events; mean microseconds per launch (either output may be NULL). */

@@ -152,9 +152,9 @@ class Domain:
 
 
 class Domain3:
-    """One 3D (D3Q19) simulation domain on the current CUDA device (lbm3_* calls).
-
-    Populations are [19, nz, ny, nx]; forces are [entries, nbodies, 3]."""
+    """One 3D simulation domain (D3Q19, or D3Q15 with spec["lattice"] = 15) on the current
+    CUDA device (lbm3_* calls). Populations are [Q, nz, ny, nx]; forces are
+    [entries, nbodies, 3]."""
 
     def __init__(self, spec, storage="f32", force_every=1, force_capacity=8192, stream=None,
                  allocator="torch"):
@@ -162,6 +162,7 @@ class Domain3:
         L = load()
         self.spec, self.storage = spec, storage
         self.nx, self.ny, self.nz = spec["nx"], spec["ny"], spec["nz"]
+        self.q = 15 if spec.get("lattice", 19) == 15 else 19
         self.nbodies = len(spec["bodies"])
         self._params = _native.params3_from_spec(spec, storage, force_every, force_capacity)
         self._bodies, nb = _native.bodies3_from_spec(spec)
@@ -212,15 +213,15 @@ class Domain3:
         return tuple(out)
 
     def get_populations(self) -> np.ndarray:
-        out = np.zeros((19, self.nz, self.ny, self.nx), dtype=STORAGE_DTYPE[self.storage])
+        out = np.zeros((self.q, self.nz, self.ny, self.nx), dtype=STORAGE_DTYPE[self.storage])
         check(load().lbm3_get_populations(self._handle(), out.ctypes.data_as(C.c_void_p),
                                           out.nbytes), "lbm3_get_populations")
         return out
 
     def set_populations(self, arr: np.ndarray):
         a = np.ascontiguousarray(arr, dtype=STORAGE_DTYPE[self.storage])
-        if a.shape != (19, self.nz, self.ny, self.nx):
-            raise ValueError(f"populations must have shape (19, {self.nz}, {self.ny}, {self.nx})")
+        if a.shape != (self.q, self.nz, self.ny, self.nx):
+            raise ValueError(f"populations must have shape ({self.q}, {self.nz}, {self.ny}, {self.nx})")
         check(load().lbm3_set_populations(self._handle(), a.ctypes.data_as(C.c_void_p), a.nbytes),
               "lbm3_set_populations")
 
@@ -228,6 +229,10 @@ class Domain3:
         v = C.c_int64()
         check(load().lbm3_steps_done(self._handle(), C.byref(v)), "lbm3_steps_done")
         return v.value
+
+    def set_steps_done(self, steps: int):
+        """Restore the step index with saved populations (it keys the 16-bit rounding)."""
+        check(load().lbm3_set_steps_done(self._handle(), int(steps)), "lbm3_set_steps_done")
 
     def mask(self) -> np.ndarray:
         out = np.zeros((self.nz, self.ny, self.nx), dtype=np.uint8)

@@ -1,8 +1,9 @@
-// 3D TRT-LBM-VP with the D3Q19 lattice: kernels and the single-domain runtime (the C ABI
-// lbm3_* of include/lbm.h). The step is the algorithm of Sec. 2.2 with nineteen
-// directions (the paper's closing remark: D2Q9 is replaced by D3Q15 or D3Q19); storage
-// codecs, stochastic rounding with the node mass kept, and the strip/shuffle pull are
-// those of the 2D sweep. Compiled with --fmad=false: every FMA is written out.
+// 3D TRT-LBM-VP with the D3Q19 or the D3Q15 lattice: kernels and the single-domain
+// runtime (the C ABI lbm3_* of include/lbm.h). The step is the algorithm of Sec. 2.2 with
+// nineteen or fifteen directions (the paper's closing remark: D2Q9 is replaced by D3Q15
+// or D3Q19); storage codecs, stochastic rounding with the node mass kept, and the
+// strip/shuffle pull are those of the 2D sweep. Compiled with --fmad=false: every FMA is
+// written out.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -17,30 +18,48 @@
 namespace lbm {
 namespace d3 {
 
-constexpr int kQ3 = 19;
+constexpr int kQ3 = 19;  // the larger lattice: array bounds shared by both
 
-// D3Q19 velocity set: 0 rest; 1..6 +x -x +y -y +z -z; 7..18 +x+y -x-y +x-y -x+y +x+z -x-z
-// +x-z -x+z +y+z -y-z +y-z -y+z. Directions 2m-1 and 2m are opposite.
-__host__ __device__ constexpr int ex3(int a) {
+// D3Q19: 0 rest; 1..6 +x -x +y -y +z -z; 7..18 +x+y -x-y +x-y -x+y +x+z -x-z +x-z -x+z
+// +y+z -y-z +y-z -y+z. D3Q15: 0 rest; 1..6 as D3Q19; 7..14 +x+y+z -x-y-z +x+y-z -x-y+z
+// +x-y+z -x+y-z -x+y+z +x-y-z. In both, directions 2m-1 and 2m are opposite; classes by
+// index: 0 rest, 1..6 axis, 7.. diagonal (face diagonals of D3Q19, corners of D3Q15).
+template <int Q> __host__ __device__ constexpr int ex3(int a) {
+  if (Q == 15)
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 14) ? 1
+         : (a == 2 || a == 8 || a == 10 || a == 12 || a == 13) ? -1 : 0;
   return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
        : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
 }
-__host__ __device__ constexpr int ey3(int a) {
+template <int Q> __host__ __device__ constexpr int ey3(int a) {
+  if (Q == 15)
+    return (a == 3 || a == 7 || a == 9 || a == 12 || a == 13) ? 1
+         : (a == 4 || a == 8 || a == 10 || a == 11 || a == 14) ? -1 : 0;
   return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
        : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
 }
-__host__ __device__ constexpr int ez3(int a) {
+template <int Q> __host__ __device__ constexpr int ez3(int a) {
+  if (Q == 15)
+    return (a == 5 || a == 7 || a == 10 || a == 11 || a == 13) ? 1
+         : (a == 6 || a == 8 || a == 9 || a == 12 || a == 14) ? -1 : 0;
   return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
        : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
 }
 // specular reflection across a wall normal to y (e_y reversed) or z (e_z reversed)
-__host__ __device__ constexpr int reflect_y3(int a) {
-  return a == 3 ? 4 : a == 4 ? 3 : a == 7 ? 9 : a == 9 ? 7 : a == 8 ? 10 : a == 10 ? 8
-       : a == 15 ? 18 : a == 18 ? 15 : a == 16 ? 17 : a == 17 ? 16 : a;
+template <int Q> __host__ __device__ constexpr int reflect_y3(int a) {
+  for (int b = 0; b < Q; ++b)
+    if (ex3<Q>(b) == ex3<Q>(a) && ey3<Q>(b) == -ey3<Q>(a) && ez3<Q>(b) == ez3<Q>(a)) return b;
+  return a;
 }
-__host__ __device__ constexpr int reflect_z3(int a) {
-  return a == 5 ? 6 : a == 6 ? 5 : a == 11 ? 13 : a == 13 ? 11 : a == 12 ? 14 : a == 14 ? 12
-       : a == 15 ? 17 : a == 17 ? 15 : a == 16 ? 18 : a == 18 ? 16 : a;
+template <int Q> __host__ __device__ constexpr int reflect_z3(int a) {
+  for (int b = 0; b < Q; ++b)
+    if (ex3<Q>(b) == ex3<Q>(a) && ey3<Q>(b) == ey3<Q>(a) && ez3<Q>(b) == -ez3<Q>(a)) return b;
+  return a;
+}
+// lattice weights per class: rest, axis, diagonal
+template <int Q> constexpr double w3(int cls) {
+  return Q == 15 ? (cls == 0 ? 2.0 / 9.0 : cls == 1 ? 1.0 / 9.0 : 1.0 / 72.0)
+                 : (cls == 0 ? 1.0 / 3.0 : cls == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
 // Per-domain constants in compute precision (per class: rest, axis, diagonal).
@@ -107,20 +126,29 @@ template <typename T> struct Macro3 {
 
 // steps (3)-(5) at one node: Eq. (rho), Eq. (rho*velocity-star), penalization (Eq. d-V,
 // Eq. force-density) and Eq. (velocity-r), in a fixed order of operations
-template <typename T, bool SHIFT, bool FORCE>
-__device__ __forceinline__ Macro3<T> macro3(const T (&x)[kQ3], const Const3<T> &c, bool solid,
+template <int Q, typename T, bool SHIFT, bool FORCE>
+__device__ __forceinline__ Macro3<T> macro3(const T (&x)[Q], const Const3<T> &c, bool solid,
                                             const T (&uo)[3]) {
   Macro3<T> m;
-  T dm[10];
+  T dm[10], sp[10];
 #pragma unroll
-  for (int p = 1; p <= 9; ++p) dm[p] = x[2 * p - 1] - x[2 * p];
-  const T s1 = x[1] + x[2], s2 = x[3] + x[4], s3 = x[5] + x[6], s4 = x[7] + x[8], s5 = x[9] + x[10];
-  const T s6 = x[11] + x[12], s7 = x[13] + x[14], s8 = x[15] + x[16], s9 = x[17] + x[18];
-  m.d = (x[0] + ((s1 + s2) + s3)) + (((s4 + s5) + (s6 + s7)) + (s8 + s9));
+  for (int p = 1; p <= (Q - 1) / 2; ++p) {
+    dm[p] = x[2 * p - 1] - x[2 * p];
+    sp[p] = x[2 * p - 1] + x[2 * p];
+  }
+  T jx, jy, jz;
+  if constexpr (Q == 19) {
+    m.d = (x[0] + ((sp[1] + sp[2]) + sp[3])) + (((sp[4] + sp[5]) + (sp[6] + sp[7])) + (sp[8] + sp[9]));
+    jx = (dm[1] + dm[4]) + (dm[5] + (dm[6] + dm[7]));
+    jy = (dm[2] + dm[4]) + ((dm[8] + dm[9]) - dm[5]);
+    jz = (dm[3] + dm[6]) + ((dm[8] - dm[9]) - dm[7]);
+  } else {
+    m.d = (x[0] + ((sp[1] + sp[2]) + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7]));
+    jx = (dm[1] + dm[4]) + ((dm[5] + dm[6]) - dm[7]);
+    jy = (dm[2] + dm[4]) + ((dm[5] - dm[6]) + dm[7]);
+    jz = (dm[3] + dm[4]) + ((dm[6] - dm[5]) + dm[7]);
+  }
   m.rho = SHIFT ? c.rho0 + m.d : m.d;
-  const T jx = (dm[1] + dm[4]) + (dm[5] + (dm[6] + dm[7]));
-  const T jy = (dm[2] + dm[4]) + ((dm[8] + dm[9]) - dm[5]);
-  const T jz = (dm[3] + dm[6]) + ((dm[8] - dm[9]) - dm[7]);
   const T inv = rcp_(m.rho);
   m.u[0] = jx * inv;
   m.u[1] = jy * inv;
@@ -138,9 +166,10 @@ __device__ __forceinline__ Macro3<T> macro3(const T (&x)[kQ3], const Const3<T> &
   return m;
 }
 
-// TRT collision with the split Guo term per opposite pair (the 2D form, nine pairs)
-template <typename T, bool SHIFT, bool FORCE>
-__device__ __forceinline__ void collide3(T (&x)[kQ3], const Macro3<T> &m, const Const3<T> &c) {
+// TRT collision with the split Guo term per opposite pair (the 2D form; nine pairs for
+// D3Q19, seven for D3Q15)
+template <int Q, typename T, bool SHIFT, bool FORCE>
+__device__ __forceinline__ void collide3(T (&x)[Q], const Macro3<T> &m, const Const3<T> &c) {
   const T base = SHIFT ? m.d : m.rho;
   const T ux = m.u[0], uy = m.u[1], uz = m.u[2];
   const T q = T(1.5) * fma_(uz, uz, fma_(uy, uy, ux * ux));
@@ -173,27 +202,36 @@ __device__ __forceinline__ void collide3(T (&x)[kQ3], const Macro3<T> &m, const 
   pair(1, 2, ux, fx, a1, b1, m1, c.kw1, c.qw1);
   pair(3, 4, uy, fy, a1, b1, m1, c.kw1, c.qw1);
   pair(5, 6, uz, fz, a1, b1, m1, c.kw1, c.qw1);
-  pair(7, 8, ux + uy, fx + fy, a2, b2, m2, c.kw2, c.qw2);
-  pair(9, 10, ux - uy, fx - fy, a2, b2, m2, c.kw2, c.qw2);
-  pair(11, 12, ux + uz, fx + fz, a2, b2, m2, c.kw2, c.qw2);
-  pair(13, 14, ux - uz, fx - fz, a2, b2, m2, c.kw2, c.qw2);
-  pair(15, 16, uy + uz, fy + fz, a2, b2, m2, c.kw2, c.qw2);
-  pair(17, 18, uy - uz, fy - fz, a2, b2, m2, c.kw2, c.qw2);
+  if constexpr (Q == 19) {
+    pair(7, 8, ux + uy, fx + fy, a2, b2, m2, c.kw2, c.qw2);
+    pair(9, 10, ux - uy, fx - fy, a2, b2, m2, c.kw2, c.qw2);
+    pair(11, 12, ux + uz, fx + fz, a2, b2, m2, c.kw2, c.qw2);
+    pair(13, 14, ux - uz, fx - fz, a2, b2, m2, c.kw2, c.qw2);
+    pair(15, 16, uy + uz, fy + fz, a2, b2, m2, c.kw2, c.qw2);
+    pair(17, 18, uy - uz, fy - fz, a2, b2, m2, c.kw2, c.qw2);
+  } else {
+    pair(7, 8, (ux + uy) + uz, (fx + fy) + fz, a2, b2, m2, c.kw2, c.qw2);
+    pair(9, 10, (ux + uy) - uz, (fx + fy) - fz, a2, b2, m2, c.kw2, c.qw2);
+    pair(11, 12, (ux - uy) + uz, (fx - fy) + fz, a2, b2, m2, c.kw2, c.qw2);
+    pair(13, 14, (uy + uz) - ux, (fy + fz) - fx, a2, b2, m2, c.kw2, c.qw2);
+  }
 }
 
 // 16-bit words of two nodes' values with stochastic rounding and the node mass kept
 // (the 2D rule: moving values rounded first, the rest value stored as the pulled mass
 // minus their rounded sum, pairs summed in a fixed order)
-template <int S>
-__device__ __forceinline__ void encode3_pair(const F2 (&x)[kQ3], F2 d, uint32_t bits, uint32_t (&w)[kQ3]) {
+template <int Q, int S>
+__device__ __forceinline__ void encode3_pair(const F2 (&x)[Q], F2 d, uint32_t bits, uint32_t (&w)[Q]) {
   F2 sp[10];
 #pragma unroll
-  for (int p = 1; p <= 9; ++p) {
+  for (int p = 1; p <= (Q - 1) / 2; ++p) {
     w[2 * p - 1] = Codec<S>::enc2_sr(x[2 * p - 1].v.x, x[2 * p - 1].v.y, bits);
     w[2 * p] = Codec<S>::enc2_sr(x[2 * p].v.x, x[2 * p].v.y, bits);
     sp[p] = F2(Codec<S>::dec2(w[2 * p - 1])) + F2(Codec<S>::dec2(w[2 * p]));
   }
-  const F2 moved = (((sp[1] + sp[2]) + sp[3]) + (((sp[4] + sp[5]) + (sp[6] + sp[7])) + (sp[8] + sp[9])));
+  F2 diag = (sp[4] + sp[5]) + (sp[6] + sp[7]);
+  if constexpr (Q == 19) diag = diag + (sp[8] + sp[9]);
+  const F2 moved = ((sp[1] + sp[2]) + sp[3]) + diag;
   const F2 rest = d - moved;
   w[0] = Codec<S>::enc2_sr(rest.v.x, rest.v.y, bits);
 }
@@ -214,22 +252,23 @@ __device__ __forceinline__ Const3<F2> pair_const3(const Pair3 &c) {
 }
 
 // source row of direction a for row (j, k): y rule, then z rule
+template <int Q>
 __device__ __forceinline__ void src_row3(const Dom3 &D, int a, int j, int k, int &sa, int &sy, int &sz) {
   sa = a;
-  sy = j - ey3(a);
-  sz = k - ez3(a);
+  sy = j - ey3<Q>(a);
+  sz = k - ez3<Q>(a);
   if (sy < 0) {
-    if (D.south == LBM_FREE_SLIP) { sy = 0; sa = reflect_y3(sa); }
+    if (D.south == LBM_FREE_SLIP) { sy = 0; sa = reflect_y3<Q>(sa); }
     else sy += D.ny;
   } else if (sy > D.ny - 1) {
-    if (D.north == LBM_FREE_SLIP) { sy = D.ny - 1; sa = reflect_y3(sa); }
+    if (D.north == LBM_FREE_SLIP) { sy = D.ny - 1; sa = reflect_y3<Q>(sa); }
     else sy -= D.ny;
   }
   if (sz < 0) {
-    if (D.bottom == LBM_FREE_SLIP) { sz = 0; sa = reflect_z3(sa); }
+    if (D.bottom == LBM_FREE_SLIP) { sz = 0; sa = reflect_z3<Q>(sa); }
     else sz += D.nz;
   } else if (sz > D.nz - 1) {
-    if (D.top == LBM_FREE_SLIP) { sz = D.nz - 1; sa = reflect_z3(sa); }
+    if (D.top == LBM_FREE_SLIP) { sz = D.nz - 1; sa = reflect_z3<Q>(sa); }
     else sz -= D.nz;
   }
 }
@@ -302,28 +341,28 @@ __device__ __forceinline__ RowOff3 row_off3(const Dom3 &D, int j, int k) {
 }
 
 // source row of direction a (A a compile-time constant after unrolling)
-template <typename E, int A>
+template <int Q, typename E, int A>
 __device__ __forceinline__ const E *src_row_ptr(const Dom3 &D, const RowOff3 &r) {
-  constexpr int iy = ey3(A) + 1, iz = ez3(A) + 1;
-  constexpr int ay = reflect_y3(A), az = reflect_z3(A), ayz = reflect_z3(reflect_y3(A));
+  constexpr int iy = ey3<Q>(A) + 1, iz = ez3<Q>(A) + 1;
+  constexpr int ay = reflect_y3<Q>(A), az = reflect_z3<Q>(A), ayz = reflect_z3<Q>(reflect_y3<Q>(A));
   const bool my = r.my[iy], mz = r.mz[iz];
   const void *base = my ? (mz ? D.src[ayz] : D.src[ay]) : (mz ? D.src[az] : D.src[A]);
   return static_cast<const E *>(base) + (r.z[iz] + r.y[iy]);
 }
 
-template <int A, typename F> __device__ __forceinline__ void for_dirs(F &&f) {
-  if constexpr (A < kQ3) {
+template <int Q, int A, typename F> __device__ __forceinline__ void for_dirs(F &&f) {
+  if constexpr (A < Q) {
     f(std::integral_constant<int, A>{});
-    for_dirs<A + 1>(f);
+    for_dirs<Q, A + 1>(f);
   }
 }
 
 // The fused 3D sweep: one warp per strip of 32 V cells of one row (j, k) at a time
-// (persistent grid), nineteen vector loads per lane, the +-1 x-shift by shuffles, strip
-// ends by broadcast loads, update, nineteen vector stores into the other lattice. With
-// 16-bit storage, warps without solid nodes update two nodes at once in paired FP32
-// (the same operations in the same order on each half).
-template <int S, int V>
+// (persistent grid), Q vector loads per lane, the +-1 x-shift by shuffles, strip ends by
+// broadcast loads, update, Q vector stores into the other lattice. With 16-bit storage,
+// warps without solid nodes update two nodes at once in paired FP32 (the same operations
+// in the same order on each half).
+template <int Q, int S, int V>
 __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMinBlocks)
     sweep3_kernel(const __grid_constant__ Dom3 dom, long long n, int par) {
   using Cd = Codec<S>;
@@ -355,17 +394,17 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
     const int col_r = east_edge ? 0 : x0 + kStrip;
     const int k_last = nx - 1 - xl;
     const int xl_ld = min(xl, pitch - V);
-    Strip<S, V> v[kQ3];
-    E end_in[kQ3];
+    Strip<S, V> v[Q];
+    E end_in[Q];
     {
       const RowOff3 R = row_off3(D, j, k);
-      for_dirs<0>([&](auto ac) {
+      for_dirs<Q, 0>([&](auto ac) {
         constexpr int a = decltype(ac)::value;
-        const E *rp = src_row_ptr<E, a>(D, R);
+        const E *rp = src_row_ptr<Q, E, a>(D, R);
         v[a].load(rp + xl_ld);
         end_in[a] = E(0);
-        if constexpr (ex3(a) == 1) end_in[a] = __ldg(rp + col_l);
-        else if constexpr (ex3(a) == -1) end_in[a] = __ldg(rp + col_r);
+        if constexpr (ex3<Q>(a) == 1) end_in[a] = __ldg(rp + col_l);
+        else if constexpr (ex3<Q>(a) == -1) end_in[a] = __ldg(rp + col_r);
       });
     }
     uint8_t b[V];
@@ -376,8 +415,8 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
     }
     // the +-1 x-shift of the pull
 #pragma unroll
-    for (int a = 0; a < kQ3; ++a) {
-      const int ex = ex3(a);
+    for (int a = 0; a < Q; ++a) {
+      const int ex = ex3<Q>(a);
       if (ex == 1) {
         E in = shfl_up1<E>(v[a].last());
         in = lane == 0 ? end_in[a] : in;
@@ -406,21 +445,19 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
     const unsigned valid_bits =
         east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u)) : (1u << V) - 1u;
     unsigned bad_bits = 0u;
-    auto update = [&](T (&x)[kQ3], int q) -> T {
+    auto update = [&](T (&x)[Q], int q) -> T {
       if (q == 0 && west_edge && west_inlet && lane == 0) {
-        x[1] = C.ghost[1];
-        x[7] = C.ghost[7];
-        x[9] = C.ghost[9];
-        x[11] = C.ghost[11];
-        x[13] = C.ghost[13];
+#pragma unroll
+        for (int a = 1; a < Q; ++a)
+          if (ex3<Q>(a) == 1) x[a] = C.ghost[a];
       }
       Macro3<T> m;
       if (any_solid) {
         T uo[3] = {T(0), T(0), T(0)};
         const bool solid = b[q] != 0;
         if (solid) body_velocity3(D, b[q], xl + q, j, k, uo);
-        m = macro3<T, SHIFT, true>(x, C, solid, uo);
-        collide3<T, SHIFT, true>(x, m, C);
+        m = macro3<Q, T, SHIFT, true>(x, C, solid, uo);
+        collide3<Q, T, SHIFT, true>(x, m, C);
         if (solid) {
           T *fv = static_cast<T *>(D.fvp) + 3 * ((static_cast<size_t>(k) * ny + j) * pitch + xl + q);
           fv[0] = m.f[0] * kUnscale;
@@ -429,8 +466,8 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
         }
       } else {
         const T uo[3] = {T(0), T(0), T(0)};
-        m = macro3<T, SHIFT, false>(x, C, false, uo);
-        collide3<T, SHIFT, false>(x, m, C);
+        m = macro3<Q, T, SHIFT, false>(x, C, false, uo);
+        collide3<Q, T, SHIFT, false>(x, m, C);
       }
       bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
       return m.d;
@@ -441,65 +478,63 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
         const Const3<F2> CP = pair_const3(D.pc);
 #pragma unroll
         for (int q = 0; q < V; q += 2) {
-          F2 x[kQ3];
+          F2 x[Q];
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) x[a] = F2(Cd::dec2(v[a].w[q >> 1]));
+          for (int a = 0; a < Q; ++a) x[a] = F2(Cd::dec2(v[a].w[q >> 1]));
           if (q == 0 && west_edge && west_inlet) {
             const bool g = lane == 0;
-            x[1].v.x = g ? C.ghost[1] : x[1].v.x;
-            x[7].v.x = g ? C.ghost[7] : x[7].v.x;
-            x[9].v.x = g ? C.ghost[9] : x[9].v.x;
-            x[11].v.x = g ? C.ghost[11] : x[11].v.x;
-            x[13].v.x = g ? C.ghost[13] : x[13].v.x;
+#pragma unroll
+            for (int a = 1; a < Q; ++a)
+              if (ex3<Q>(a) == 1) x[a].v.x = g ? C.ghost[a] : x[a].v.x;
           }
           const F2 uo[3] = {F2(0.f), F2(0.f), F2(0.f)};
-          const Macro3<F2> m = macro3<F2, SHIFT, false>(x, CP, false, uo);
-          collide3<F2, SHIFT, false>(x, m, CP);
+          const Macro3<F2> m = macro3<Q, F2, SHIFT, false>(x, CP, false, uo);
+          collide3<Q, F2, SHIFT, false>(x, m, CP);
           bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
           bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (q + 1);
-          uint32_t w[kQ3];
-          encode3_pair<S>(x, m.d, sr_pair_bits(sr_g, xl + q), w);
+          uint32_t w[Q];
+          encode3_pair<Q, S>(x, m.d, sr_pair_bits(sr_g, xl + q), w);
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) v[a].w[q >> 1] = w[a];
+          for (int a = 0; a < Q; ++a) v[a].w[q >> 1] = w[a];
         }
       } else {
 #pragma unroll
         for (int q = 0; q < V; q += 2) {
-          T x0v[kQ3], x1v[kQ3];
+          T x0v[Q], x1v[Q];
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) {
+          for (int a = 0; a < Q; ++a) {
             const float2 p = Cd::dec2(v[a].w[q >> 1]);
             x0v[a] = p.x;
             x1v[a] = p.y;
           }
           const float d0 = update(x0v, q);
           const float d1 = update(x1v, q + 1);
-          F2 x[kQ3];
+          F2 x[Q];
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) x[a] = F2(make_float2(x0v[a], x1v[a]));
-          uint32_t w[kQ3];
-          encode3_pair<S>(x, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
+          for (int a = 0; a < Q; ++a) x[a] = F2(make_float2(x0v[a], x1v[a]));
+          uint32_t w[Q];
+          encode3_pair<Q, S>(x, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) v[a].w[q >> 1] = w[a];
+          for (int a = 0; a < Q; ++a) v[a].w[q >> 1] = w[a];
         }
       }
     } else {
 #pragma unroll
       for (int q = 0; q < V; ++q) {
-        T x[kQ3];
+        T x[Q];
 #pragma unroll
-        for (int a = 0; a < kQ3; ++a) x[a] = Cd::dec(v[a].get(q));
+        for (int a = 0; a < Q; ++a) x[a] = Cd::dec(v[a].get(q));
         if constexpr (kAddShift) {
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) x[a] -= shift3(C, a);  // exact (Sterbenz)
+          for (int a = 0; a < Q; ++a) x[a] -= shift3(C, a);  // exact (Sterbenz)
         }
         update(x, q);
         if constexpr (kAddShift) {
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) x[a] += shift3(C, a);
+          for (int a = 0; a < Q; ++a) x[a] += shift3(C, a);
         }
 #pragma unroll
-        for (int a = 0; a < kQ3; ++a) v[a].set(q, Cd::enc(x[a]));
+        for (int a = 0; a < Q; ++a) v[a].set(q, Cd::enc(x[a]));
       }
     }
     if (bad_bits & valid_bits) unstable = 1;
@@ -508,24 +543,24 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
       for (int q = 0; q < V; ++q)
         if (!((valid_bits >> q) & 1u)) {
 #pragma unroll
-          for (int a = 0; a < kQ3; ++a) v[a].set(q, E(0));
+          for (int a = 0; a < Q; ++a) v[a].set(q, E(0));
         }
     }
     if (lane_on) {
       const uint32_t off = (static_cast<uint32_t>(k) * ny + j) * static_cast<uint32_t>(pitch) + xl;
 #pragma unroll
-      for (int a = 0; a < kQ3; ++a) v[a].store(static_cast<E *>(D.dst[a]) + off);
+      for (int a = 0; a < Q; ++a) v[a].store(static_cast<E *>(D.dst[a]) + off);
     }
   }
   if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(D.status, 1);
 }
 
 // Scalar pull with the edge rules (moments export).
-template <int S>
+template <int Q, int S>
 __device__ __forceinline__ typename Codec<S>::T pull3(const Dom3 &D, const void *lat, int a, int i, int j, int k) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
-  int sx = i - ex3(a);
+  int sx = i - ex3<Q>(a);
   if (sx < 0) {
     if (D.west == LBM_INLET_EQ) return const3<typename Cd::T>(D).ghost[a];
     sx += D.nx;
@@ -533,27 +568,27 @@ __device__ __forceinline__ typename Codec<S>::T pull3(const Dom3 &D, const void 
     sx = D.east == LBM_OUTFLOW_ZG ? D.nx - 1 : sx - D.nx;
   }
   int sa, sy, sz;
-  src_row3(D, a, j, k, sa, sy, sz);
+  src_row3<Q>(D, a, j, k, sa, sy, sz);
   const E *p = static_cast<const E *>(lat);
   typename Cd::T x = Cd::dec(p[((static_cast<size_t>(sa) * D.nz + sz) * D.ny + sy) * D.pitch + sx]);
   if (Cd::kShiftCompute && !Cd::kStoreShifted) x -= shift3(const3<typename Cd::T>(D), a);
   return x;
 }
 
-template <int S>
+template <int Q, int S>
 __global__ void moments3_kernel(const Dom3 *dom, int par, double *rho, double *ux, double *uy, double *uz) {
   using Cd = Codec<S>;
   using T = typename Cd::T;
   const Dom3 &D = *dom;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   if (i >= D.nx) return;
-  T x[kQ3];
+  T x[Q];
 #pragma unroll
-  for (int a = 0; a < kQ3; ++a) x[a] = pull3<S>(D, D.lat[par], a, i, j, k);
+  for (int a = 0; a < Q; ++a) x[a] = pull3<Q, S>(D, D.lat[par], a, i, j, k);
   const int b = D.mask[(static_cast<size_t>(k) * D.ny + j) * D.pitch + i];
   T uo[3] = {T(0), T(0), T(0)};
   if (b) body_velocity3(D, b, i, j, k, uo);
-  const Macro3<T> m = macro3<T, Cd::kShiftCompute, true>(x, const3<T>(D), b != 0, uo);
+  const Macro3<T> m = macro3<Q, T, Cd::kShiftCompute, true>(x, const3<T>(D), b != 0, uo);
   const size_t c = (static_cast<size_t>(k) * D.ny + j) * D.nx + i;
   if (rho) rho[c] = double(m.rho * (T(1) / T(Cd::kScale)));
   if (ux) ux[c] = double(m.u[0]);
@@ -561,15 +596,15 @@ __global__ void moments3_kernel(const Dom3 *dom, int par, double *rho, double *u
   if (uz) uz[c] = double(m.u[2]);
 }
 
-template <int S>
+template <int Q, int S>
 __global__ void init3_kernel(typename Codec<S>::E *lat, int nx, int nrows, int pitch, double rho0,
                              double u0x, double u0y, double u0z) {
   using Cd = Codec<S>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (i >= pitch) return;
-  const double w = a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
-  const double eu = ex3(a) * u0x + ey3(a) * u0y + ez3(a) * u0z;
+  const double w = w3<Q>(a == 0 ? 0 : (a < 7 ? 1 : 2));
+  const double eu = ex3<Q>(a) * u0x + ey3<Q>(a) * u0y + ez3<Q>(a) * u0z;
   const double usq = u0x * u0x + u0y * u0y + u0z * u0z;
   const double dev = rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
   double val = Cd::kStoreShifted ? dev * Cd::kScale : rho0 * w + dev;
@@ -696,6 +731,16 @@ size_t esize(int storage) {
   return storage == LBM_F64 ? 8 : storage == LBM_F32 ? 4 : (storage == LBM_F16S || storage == LBM_BF16S) ? 2 : 0;
 }
 size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+// directions of the lattice a parameter set selects (0 or 19: D3Q19, 15: D3Q15)
+int nq_of(const lbm3_params &p) { return p.lattice == 15 ? 15 : 19; }
+int e_of(int q, int a, int axis) {
+  if (q == 15) return axis == 0 ? ex3<15>(a) : axis == 1 ? ey3<15>(a) : ez3<15>(a);
+  return axis == 0 ? ex3<19>(a) : axis == 1 ? ey3<19>(a) : ez3<19>(a);
+}
+double w_of(int q, int a) {
+  const int cls = a == 0 ? 0 : (a < 7 ? 1 : 2);
+  return q == 15 ? w3<15>(cls) : w3<19>(cls);
+}
 
 struct Layout3 {
   size_t lat, mask_off, fvp_off, bodies_off, bodiesf_off, ring_off, status_off, total;
@@ -706,7 +751,7 @@ Layout3 layout3(const lbm3_params &p, int nb) {
   const size_t pitch = up(static_cast<size_t>(p.nx), kPitchAlign);
   const size_t cells = pitch * p.ny * p.nz;
   const int cap = p.force_capacity > 0 ? p.force_capacity : 8192;
-  L.lat = up(kQ3 * cells * esize(p.storage), 256);
+  L.lat = up(nq_of(p) * cells * esize(p.storage), 256);
   size_t o = 2 * L.lat;
   L.mask_off = o;
   o += up(cells, 256);
@@ -724,8 +769,8 @@ Layout3 layout3(const lbm3_params &p, int nb) {
   return L;
 }
 
-template <typename T> void fill3(Const3<T> &c, double omp, double omm, double eta, double rho0, double scale) {
-  const double w0 = 1.0 / 3.0, w1 = 1.0 / 18.0, w2 = 1.0 / 36.0;
+template <typename T> void fill3(Const3<T> &c, int q, double omp, double omm, double eta, double rho0, double scale) {
+  const double w0 = w_of(q, 0), w1 = w_of(q, 1), w2 = w_of(q, 7);
   c.one_m_omp = T(1.0 - omp);
   c.hp = T(0.5 * omp);
   c.hm = T(0.5 * omm);
@@ -782,20 +827,24 @@ struct lbm3_domain {
 
 namespace {
 
-template <int S> cudaError_t launch_sweep3_as(lbm3_domain *d, long long n, int par) {
+template <int Q, int S> cudaError_t launch_sweep3_as(lbm3_domain *d, long long n, int par) {
   using Sh = Sweep3Shape<S>;
-  sweep3_kernel<S, Sh::kV><<<d->grid, Sh::kThreads, 0, d->st>>>(d->hpar[par], n, par);
+  sweep3_kernel<Q, S, Sh::kV><<<d->grid, Sh::kThreads, 0, d->st>>>(d->hpar[par], n, par);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep3(lbm3_domain *d, long long n, int par) {
+template <int Q> cudaError_t launch_sweep3_q(lbm3_domain *d, long long n, int par) {
   switch (d->p.storage) {
-    case LBM_F64: return launch_sweep3_as<LBM_F64>(d, n, par);
-    case LBM_F32: return launch_sweep3_as<LBM_F32>(d, n, par);
-    case LBM_F16S: return launch_sweep3_as<LBM_F16S>(d, n, par);
-    case LBM_BF16S: return launch_sweep3_as<LBM_BF16S>(d, n, par);
+    case LBM_F64: return launch_sweep3_as<Q, LBM_F64>(d, n, par);
+    case LBM_F32: return launch_sweep3_as<Q, LBM_F32>(d, n, par);
+    case LBM_F16S: return launch_sweep3_as<Q, LBM_F16S>(d, n, par);
+    case LBM_BF16S: return launch_sweep3_as<Q, LBM_BF16S>(d, n, par);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep3(lbm3_domain *d, long long n, int par) {
+  return nq_of(d->p) == 15 ? launch_sweep3_q<15>(d, n, par) : launch_sweep3_q<19>(d, n, par);
 }
 
 cudaError_t launch_forces3(lbm3_domain *d, long long n) {
@@ -816,6 +865,8 @@ lbm_status validate3(const lbm3_params *p, int nb, int ns, const lbm3_shape *sha
   if (static_cast<double>(up(p->nx, kPitchAlign)) * p->ny * p->nz > 1.0e9)
     return fail3(LBM_EINVAL, "grid too large (more than 1e9 padded nodes)");
   if (esize(p->storage) == 0) return fail3(LBM_EINVAL, "unknown storage %d", p->storage);
+  if (p->lattice != 0 && p->lattice != 15 && p->lattice != 19)
+    return fail3(LBM_EINVAL, "lattice must be 15 (D3Q15) or 19 (D3Q19; 0 selects it too)");
   const double tau = p->nu > 0 ? 3.0 * p->nu + 0.5 : p->tau_plus;
   if (!(tau > 0.5)) return fail3(LBM_EINVAL, "tau_plus must exceed 1/2");
   if (!(p->magic_lambda > 0) || !(p->eta > 0) || !(p->rho0 > 0)) return fail3(LBM_EINVAL, "Lambda, eta, rho0 must be > 0");
@@ -838,10 +889,10 @@ lbm_status validate3(const lbm3_params *p, int nb, int ns, const lbm3_shape *sha
   return LBM_OK;
 }
 
-template <int S> int sweep3_blocks_as(int sms) {
+template <int Q, int S> int sweep3_blocks_as(int sms) {
   using Sh = Sweep3Shape<S>;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<S, Sh::kV>, Sh::kThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<Q, S, Sh::kV>, Sh::kThreads, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     n = 1;
@@ -849,15 +900,48 @@ template <int S> int sweep3_blocks_as(int sms) {
   return sms * std::max(1, n);
 }
 
-// persistent grid of the sweep: every resident block slot of every SM
-int sweep3_blocks(int storage, int sms) {
+template <int Q> int sweep3_blocks_q(int storage, int sms) {
   switch (storage) {
-    case LBM_F64: return sweep3_blocks_as<LBM_F64>(sms);
-    case LBM_F32: return sweep3_blocks_as<LBM_F32>(sms);
-    case LBM_F16S: return sweep3_blocks_as<LBM_F16S>(sms);
-    case LBM_BF16S: return sweep3_blocks_as<LBM_BF16S>(sms);
+    case LBM_F64: return sweep3_blocks_as<Q, LBM_F64>(sms);
+    case LBM_F32: return sweep3_blocks_as<Q, LBM_F32>(sms);
+    case LBM_F16S: return sweep3_blocks_as<Q, LBM_F16S>(sms);
+    case LBM_BF16S: return sweep3_blocks_as<Q, LBM_BF16S>(sms);
   }
   return sms;
+}
+
+// persistent grid of the sweep: every resident block slot of every SM
+int sweep3_blocks(int q, int storage, int sms) {
+  return q == 15 ? sweep3_blocks_q<15>(storage, sms) : sweep3_blocks_q<19>(storage, sms);
+}
+
+template <int Q, int S> void launch_init3_as(lbm3_domain *d, void *lat, const lbm3_params *p, int nrows) {
+  dim3 g((d->pitch + 127) / 128, Q, std::min(nrows, 4096));
+  init3_kernel<Q, S><<<g, 128, 0, d->st>>>(static_cast<typename Codec<S>::E *>(lat), p->nx, nrows, d->pitch,
+                                            p->rho0, p->u0[0], p->u0[1], p->u0[2]);
+}
+
+template <int Q> void launch_init3_q(lbm3_domain *d, void *lat, const lbm3_params *p, int nrows) {
+  switch (p->storage) {
+    case LBM_F64: launch_init3_as<Q, LBM_F64>(d, lat, p, nrows); break;
+    case LBM_F32: launch_init3_as<Q, LBM_F32>(d, lat, p, nrows); break;
+    case LBM_F16S: launch_init3_as<Q, LBM_F16S>(d, lat, p, nrows); break;
+    case LBM_BF16S: launch_init3_as<Q, LBM_BF16S>(d, lat, p, nrows); break;
+  }
+}
+
+template <int Q, int S> void launch_moments3_as(lbm3_domain *d, double *t0, double *t1, double *t2, double *t3) {
+  dim3 g((d->p.nx + 127) / 128, d->p.ny, d->p.nz);
+  moments3_kernel<Q, S><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3);
+}
+
+template <int Q> void launch_moments3_q(lbm3_domain *d, double *t0, double *t1, double *t2, double *t3) {
+  switch (d->p.storage) {
+    case LBM_F64: launch_moments3_as<Q, LBM_F64>(d, t0, t1, t2, t3); break;
+    case LBM_F32: launch_moments3_as<Q, LBM_F32>(d, t0, t1, t2, t3); break;
+    case LBM_F16S: launch_moments3_as<Q, LBM_F16S>(d, t0, t1, t2, t3); break;
+    case LBM_BF16S: launch_moments3_as<Q, LBM_BF16S>(d, t0, t1, t2, t3); break;
+  }
 }
 
 lbm_status read_status3(lbm3_domain *d) {
@@ -884,6 +968,7 @@ void lbm3_params_default(lbm3_params *p) {
   p->storage = LBM_F32;
   p->force_every = 1;
   p->force_capacity = 8192;
+  p->lattice = 19;
 }
 
 size_t lbm3_domain_bytes(const lbm3_params *p, int32_t nbodies) {
@@ -961,8 +1046,9 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   const double omp = 1.0 / tau_s, omm = 1.0 / tau_a;
   const bool shifted = p->storage == LBM_F16S || p->storage == LBM_BF16S;
   const double scale = p->storage == LBM_F16S ? double(kF16Scale) : 1.0;
-  fill3(D.cd, omp, omm, p->eta, p->rho0, 1.0);
-  fill3(D.cf, omp, omm, p->eta, p->rho0, scale);
+  const int nq = nq_of(*p);
+  fill3(D.cd, nq, omp, omm, p->eta, p->rho0, 1.0);
+  fill3(D.cf, nq, omp, omm, p->eta, p->rho0, scale);
   {
     const Const3<float> &c = D.cf;
     auto two = [](float x) { return make_float2(x, x); };
@@ -971,12 +1057,11 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   }
   {
     // inlet ghost f^eq(rho0, u_in) in compute space, held as the storage would hold it
-    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
     const double *u = p->u_in;
     const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    for (int a = 0; a < kQ3; ++a) {
-      const double wa = a == 0 ? w[0] : (a < 7 ? w[1] : w[2]);
-      const double eu = ex3(a) * u[0] + ey3(a) * u[1] + ez3(a) * u[2];
+    for (int a = 0; a < nq; ++a) {
+      const double wa = w_of(nq, a);
+      const double eu = e_of(nq, a, 0) * u[0] + e_of(nq, a, 1) * u[1] + e_of(nq, a, 2) * u[2];
       const double dev = p->rho0 * wa * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
       D.cd.ghost[a] = p->rho0 * wa + dev;
       float gf;
@@ -1040,13 +1125,8 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   // initial state: lattice A = f^eq(rho0, u0); lattice B, F_VP, ring, status zero
   {
     const int nrows = p->ny * p->nz;
-    dim3 g((d->pitch + 127) / 128, kQ3, std::min(nrows, 4096));
-    switch (p->storage) {
-      case LBM_F64: init3_kernel<LBM_F64><<<g, 128, 0, st>>>(static_cast<double *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
-      case LBM_F32: init3_kernel<LBM_F32><<<g, 128, 0, st>>>(static_cast<float *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
-      case LBM_F16S: init3_kernel<LBM_F16S><<<g, 128, 0, st>>>(static_cast<uint16_t *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
-      case LBM_BF16S: init3_kernel<LBM_BF16S><<<g, 128, 0, st>>>(static_cast<uint16_t *>(D.lat[0]), p->nx, nrows, d->pitch, p->rho0, p->u0[0], p->u0[1], p->u0[2]); break;
-    }
+    if (nq == 15) launch_init3_q<15>(d, D.lat[0], p, nrows);
+    else launch_init3_q<19>(d, D.lat[0], p, nrows);
     ADM3(cudaGetLastError());
   }
   ADM3(cudaMemsetAsync(D.lat[1], 0, L.lat, st));
@@ -1060,13 +1140,13 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
     const size_t dir_bytes = esize(p->storage) * static_cast<size_t>(d->pitch) * p->ny * p->nz;
     for (int par = 0; par < 2; ++par) {
       d->hpar[par] = D;
-      for (int a = 0; a < kQ3; ++a) {
+      for (int a = 0; a < nq; ++a) {
         d->hpar[par].src[a] = static_cast<const char *>(D.lat[par]) + a * dir_bytes;
         d->hpar[par].dst[a] = static_cast<char *>(D.lat[par ^ 1]) + a * dir_bytes;
       }
     }
   }
-  d->grid = sweep3_blocks(p->storage, sms);
+  d->grid = sweep3_blocks(nq, p->storage, sms);
   // force reduction: one warp per listed row, at most one block per SM
   d->aux_grid = std::max(1, std::min(sms, (D.nfrows + kRowsThreads / 32 - 1) / (kRowsThreads / 32)));
   *out = d;
@@ -1151,14 +1231,9 @@ lbm_status lbm3_moments(lbm3_domain *d, double *rho, double *ux, double *uy, dou
   const size_t cells = static_cast<size_t>(d->p.nx) * d->p.ny * d->p.nz;
   double *tmp = static_cast<double *>(d->get(sizeof(double) * 4 * cells));
   if (!tmp) return fail3(LBM_ENOMEM, "moments buffer allocation failed");
-  dim3 g((d->p.nx + 127) / 128, d->p.ny, d->p.nz);
   double *t0 = tmp, *t1 = tmp + cells, *t2 = tmp + 2 * cells, *t3 = tmp + 3 * cells;
-  switch (d->p.storage) {
-    case LBM_F64: moments3_kernel<LBM_F64><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
-    case LBM_F32: moments3_kernel<LBM_F32><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
-    case LBM_F16S: moments3_kernel<LBM_F16S><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
-    case LBM_BF16S: moments3_kernel<LBM_BF16S><<<g, 128, 0, d->st>>>(d->d_dom, d->parity, t0, t1, t2, t3); break;
-  }
+  if (nq_of(d->p) == 15) launch_moments3_q<15>(d, t0, t1, t2, t3);
+  else launch_moments3_q<19>(d, t0, t1, t2, t3);
   cudaError_t e = cudaGetLastError();
   double *outs[4] = {rho, ux, uy, uz};
   for (int q = 0; q < 4 && e == cudaSuccess; ++q)
@@ -1172,11 +1247,11 @@ lbm_status lbm3_moments(lbm3_domain *d, double *rho, double *ux, double *uy, dou
 static lbm_status pops3(lbm3_domain *d, void *out, const void *in, size_t bytes) {
   if (!d) return fail3(LBM_EINVAL, "domain is NULL");
   const size_t es = esize(d->p.storage);
-  const size_t want = es * kQ3 * static_cast<size_t>(d->p.nx) * d->p.ny * d->p.nz;
+  const size_t want = es * nq_of(d->p) * static_cast<size_t>(d->p.nx) * d->p.ny * d->p.nz;
   if (bytes != want) return fail3(LBM_EINVAL, "population buffer must be %zu bytes (got %zu)", want, bytes);
   char *lat = static_cast<char *>(d->h.lat[d->parity]);
   const size_t rowb = es * d->p.nx, pitchb = es * d->pitch;
-  const size_t rows = static_cast<size_t>(kQ3) * d->p.ny * d->p.nz;
+  const size_t rows = static_cast<size_t>(nq_of(d->p)) * d->p.ny * d->p.nz;
   if (out) LBM3_CUDA(cudaMemcpy2DAsync(out, rowb, lat, pitchb, rowb, rows, cudaMemcpyDefault, d->st));
   else if (in) LBM3_CUDA(cudaMemcpy2DAsync(lat, pitchb, in, rowb, rowb, rows, cudaMemcpyDefault, d->st));
   else return fail3(LBM_EINVAL, "buffer is NULL");
@@ -1205,6 +1280,16 @@ lbm_status lbm3_get_mask(lbm3_domain *d, uint8_t *out) {
 lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps) {
   if (!d) return fail3(LBM_EINVAL, "domain is NULL");
   if (steps) *steps = d->done;
+  return LBM_OK;
+}
+
+lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  if (steps < 0) return fail3(LBM_EINVAL, "step index must be >= 0");
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  d->done = steps;
+  // entries before the index are gone; the ring slot of entry e stays e % capacity
+  d->drained = d->p.force_every > 0 ? steps / d->p.force_every : 0;
   return LBM_OK;
 }
 

@@ -11,19 +11,19 @@ import numpy as np
 import oracle
 
 W = oracle.W[:, None, None]
-_W3 = None
+_W3 = {}
 
 
 def _weights(g):
-    """Shift weights broadcast over populations [9, ny, nx] (D2Q9) or [19, nz, ny, nx]
-    (D3Q19, the 3D oracle's weights)."""
-    global _W3
-    if np.shape(g)[0] == 9:
+    """Shift weights broadcast over populations [9, ny, nx] (D2Q9) or [q, nz, ny, nx]
+    (D3Q19 or D3Q15, the 3D oracle's weights)."""
+    q = np.shape(g)[0]
+    if q == 9:
         return W
-    if _W3 is None:
+    if q not in _W3:
         from oracle import d3
-        _W3 = d3.lattice()[3][:, None, None, None]
-    return _W3
+        _W3[q] = d3.lattice(q)[3][:, None, None, None]
+    return _W3[q]
 
 
 F16_SCALE = 1024.0  # F16S stores F16_SCALE * (f - w rho0)
@@ -84,8 +84,9 @@ def ghost_ulp(spec, storage):
     for the 16-bit types): the library holds the ghost as the stored type would."""
     if "nz" in spec:
         from oracle import d3
-        g = d3.equilibrium(spec["rho0"], spec["u_in"])
-        w = d3.lattice()[3]
+        q = d3.nq(spec)
+        g = d3.equilibrium(spec["rho0"], spec["u_in"], q)
+        w = d3.lattice(q)[3]
     else:
         g = oracle.equilibrium(spec["rho0"], *spec["u_in"])
         w = oracle.W
@@ -109,7 +110,7 @@ def step_tol(want, storage, spec=None, arith=None):
     one more unit of the ghost's magnitude at column 0 (and the 3 or 5 ghost values enter
     the rest population's pulled mass)."""
     shift = _weights(want) if storage != "f32" else 0.0
-    n_in = 3 if np.shape(want)[0] == 9 else 5  # directions entering from x = -1
+    n_in = 3 if np.shape(want)[0] == 9 else 5  # directions entering from x = -1 (D3Q19, D3Q15: 5)
     if arith is None:
         arith = 3e-7 if storage == "f32" else 2e-8
     g = 0.0

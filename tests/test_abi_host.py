@@ -135,7 +135,7 @@ def test_params3_default_and_bytes(lib):
     L = lib.load()
     p = _native.Params3()
     L.lbm3_params_default(C.byref(p))
-    assert (p.nx, p.ny, p.nz, p.storage, p.force_every, p.force_capacity) == (32, 32, 32, 1, 1, 8192)
+    assert (p.nx, p.ny, p.nz, p.storage, p.force_every, p.force_capacity, p.lattice) == (32, 32, 32, 1, 1, 8192, 19)
     assert p.magic_lambda == 3 / 16 and p.eta == 1e-4 and p.rho0 == 1.0 and p.nu == 0.1
     spec = _sphere_spec3()
     sizes = {}
@@ -152,7 +152,7 @@ def test_params3_default_and_bytes(lib):
 
 
 BAD3 = [("nz", 2), ("nx", 1), ("nu", -1.0), ("eta", 0.0), ("bottom", 1), ("top", 2),
-        ("south", 2), ("storage", 7), ("force_capacity", -1)]
+        ("south", 2), ("storage", 7), ("force_capacity", -1), ("lattice", 7)]
 
 
 @pytest.mark.parametrize("field,value", BAD3)

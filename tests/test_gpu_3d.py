@@ -1,10 +1,11 @@
-"""3D (D3Q19) GPU path vs the FP64 3D oracle, element by element, through the C ABI.
+"""3D GPU path (D3Q19 and D3Q15) vs the FP64 3D oracle, element by element, through the
+C ABI.
 
 FP64 storage must match the oracle to 1e-12 relative per population after 1000 steps
 (every edge rule, moving and rotating bodies, several strips per row and a ragged
 tail); the reduced storages are checked one step at a time within one unit of the
-stored type (the rest population also carries the rounding residuals of the eighteen
-moving ones); the sphere/cylinder mask must be bit-exact.
+stored type (the rest population also carries the rounding residuals of the moving
+ones); the sphere/cylinder mask must be bit-exact.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,13 @@ from oracle import d3 as ora3
 pytestmark = pytest.mark.gpu
 
 
-def _case(name):
+def _case(name, q=19):
+    sp = _case19(name)
+    sp["lattice"] = q
+    return sp
+
+
+def _case19(name):
     if name == "sphere_channel_150x20x12":
         c = (40.3, 9.6, 5.7)
         return synth.spec3(name, 150, 20, 12, 0.04, [synth.sphere(1, c, 4.3)], [synth.body3(c, 8.6)],
@@ -46,16 +53,17 @@ CASES = ["sphere_channel_150x20x12", "periodic_bodies_97x18x14", "slip_y_periodi
 
 
 def _start(lbm, spec, storage, seed):
-    g0 = synth.random_populations3(seed, spec["nx"], spec["ny"], spec["nz"], 0.1)
+    g0 = synth.random_populations3(seed, spec["nx"], spec["ny"], spec["nz"], 0.1, q=ora3.nq(spec))
     raw0 = codec.encode(g0, storage)
     dom = lbm.Domain3(spec, storage=storage)
     dom.set_populations(raw0)
     return dom, codec.decode(raw0, storage)
 
 
+@pytest.mark.parametrize("q", [19, 15])
 @pytest.mark.parametrize("case", CASES)
-def test_fp64_3d_matches_oracle_1000_steps(lbm, case):
-    spec = _case(case)
+def test_fp64_3d_matches_oracle_1000_steps(lbm, case, q):
+    spec = _case(case, q)
     dom, g0 = _start(lbm, spec, "f64", 11)
     f_gpu = dom.run(1000)
     raw = dom.get_populations()
@@ -100,10 +108,11 @@ def test_3d_initial_state_and_moments(lbm):
     np.testing.assert_allclose(g, ora3.Domain(spec).g, rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("q", [19, 15])
 @pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
 @pytest.mark.parametrize("case", ["sphere_channel_150x20x12", "periodic_bodies_97x18x14"])
-def test_reduced_storage_one_step(lbm, storage, case):
-    spec = _case(case)
+def test_reduced_storage_one_step(lbm, storage, case, q):
+    spec = _case(case, q)
     dom, g0 = _start(lbm, spec, storage, 3)
     dom.step(1)
     got = codec.decode(dom.get_populations(), storage)
@@ -115,11 +124,12 @@ def test_reduced_storage_one_step(lbm, storage, case):
     assert (err <= tol).all(), f"worst excess {(err - tol).max():.3e} at {np.unravel_index(np.argmax(err - tol), err.shape)}"
 
 
+@pytest.mark.parametrize("q", [19, 15])
 @pytest.mark.parametrize("storage", ["f32", "f16s"])
-def test_reduced_storage_200_steps_drift(lbm, storage):
+def test_reduced_storage_200_steps_drift(lbm, storage, q):
     # over many steps the reduced storages stay close to the FP64 oracle: bound the
     # velocity error at 1 percent of the inflow speed and the density error at 1e-4
-    spec = _case("sphere_channel_150x20x12")
+    spec = _case("sphere_channel_150x20x12", q)
     dom, g0 = _start(lbm, spec, storage, 9)
     dom.step(200)
     rho, ux, uy, uz = dom.moments()
@@ -133,9 +143,9 @@ def test_reduced_storage_200_steps_drift(lbm, storage):
 
 
 def test_3d_divergence_reported(lbm):
-    spec = _case("periodic_bodies_97x18x14")
+    spec = _case("periodic_bodies_97x18x14", 15)
     dom = lbm.Domain3(spec, storage="f64")
-    dom.set_populations(np.zeros((19, spec["nz"], spec["ny"], spec["nx"])))
+    dom.set_populations(np.zeros((15, spec["nz"], spec["ny"], spec["nx"])))
     dom.step(1)
     with pytest.raises(lbm.LbmError) as e:
         dom.forces()
@@ -157,20 +167,21 @@ def test_3d_force_ring_and_steps(lbm):
     dom.close()
 
 
+@pytest.mark.parametrize("q", [19, 15])
 @pytest.mark.parametrize("shape,edges", [
     ((3, 3, 3), synth.edges3()),
     ((5, 4, 3), synth.edges3("periodic", "periodic", "free_slip", "free_slip", "free_slip", "free_slip")),
     ((7, 3, 5), synth.channel_edges3()),
     ((129, 3, 4), synth.edges3("inlet", "outflow", "periodic", "periodic", "free_slip", "free_slip")),
 ])
-def test_fp64_3d_degenerate_sizes(lbm, shape, edges):
+def test_fp64_3d_degenerate_sizes(lbm, shape, edges, q):
     # smallest grids (one strip, both x edges in one lane, y/z of three cells, a strip of
     # one node past a whole strip) with a sphere covering part of the box
     nx, ny, nz = shape
     c = (nx / 2.0 - 0.3, ny / 2.0 - 0.2, nz / 2.0 + 0.1)
     spec = synth.spec3("tiny", nx, ny, nz, 0.05, [synth.sphere(1, c, 1.3)],
                        [synth.body3(c, 2.6, v=(0.01, 0.0, 0.0), w=(0.0, 0.002, 0.0))], 0, 0.02, edges,
-                       u_in=(0.02, 0.0, 0.0), u0=(0.02, 0.0, 0.0))
+                       u_in=(0.02, 0.0, 0.0), u0=(0.02, 0.0, 0.0), lattice=q)
     dom, g0 = _start(lbm, spec, "f64", 21)
     f_gpu = dom.run(200)
     raw = dom.get_populations()
@@ -183,9 +194,10 @@ def test_fp64_3d_degenerate_sizes(lbm, shape, edges):
     assert np.abs(f_gpu - f_ora).max() <= 1e-10 * max(np.abs(f_ora).max(), 1e-30) + 1e-14
 
 
-def test_3d_empty_geometry_and_no_forces(lbm):
+@pytest.mark.parametrize("q", [19, 15])
+def test_3d_empty_geometry_and_no_forces(lbm, q):
     # no shapes and no bodies: a force-free periodic box; no force entries recorded
-    spec = synth.spec3("empty", 40, 6, 5, 0.1, [], [], 0, 0.01, synth.edges3(), u0=(0.01, 0.0, 0.0))
+    spec = synth.spec3("empty", 40, 6, 5, 0.1, [], [], 0, 0.01, synth.edges3(), u0=(0.01, 0.0, 0.0), lattice=q)
     dom, g0 = _start(lbm, spec, "f64", 4)
     f = dom.run(50)
     raw = dom.get_populations()
@@ -197,11 +209,11 @@ def test_3d_empty_geometry_and_no_forces(lbm):
     assert (np.abs(raw - ora.g) / np.abs(ora.g)).max() <= 1e-12
 
 
-@pytest.mark.parametrize("storage", ["f16s", "bf16s", "f32"])
-def test_3d_checkpoint_resume_is_bit_identical(lbm, storage):
+@pytest.mark.parametrize("storage,q", [("f16s", 19), ("bf16s", 19), ("f32", 19), ("f16s", 15)])
+def test_3d_checkpoint_resume_is_bit_identical(lbm, storage, q):
     # a run interrupted after 30 steps and resumed from its populations and step index
     # repeats the uninterrupted run bit for bit (the 16-bit rounding bits follow the step)
-    spec = _case("sphere_channel_150x20x12")
+    spec = _case("sphere_channel_150x20x12", q)
     a = lbm.Domain3(spec, storage=storage)
     fa = a.run(70)
     b = lbm.Domain3(spec, storage=storage)
