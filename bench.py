@@ -482,8 +482,97 @@ def experiment(args):
         out.update(served_stream(lbm, torch, np, args))
     elif args.experiment == "viv":
         out.update(viv_sweep(lbm, torch, np, args))
+    elif args.experiment == "paper":
+        out.update(paper_cases(lbm, np, args))
     print(json.dumps(out), flush=True)
     return 0
+
+
+# The paper's own results ("Present" rows of its tables, Sec. 3.3 and 3.5)
+PAPER_TANDEM = {1.5: (1.091, -0.196, 0.171), 2.0: (1.120, -0.208, 0.179), 3.0: (1.025, -0.136, 0.129),
+                4.0: (1.297, 0.529, 0.179)}  # upstream C_d, downstream C_d, St
+PAPER_SIDE = {1.5: (1.493, -0.441, 1.490, 0.440, None), 2.0: (1.506, -0.223, 1.495, 0.228, None),
+              3.0: (1.468, -0.097, 1.468, 0.097, 0.215), 4.0: (1.450, -0.054, 1.425, 0.054, 0.211)}
+# upper C_d, upper C_l, lower C_d, lower C_l, St
+PAPER_NACA = {"re500_aoa0": {"cd": 0.178}, "re1000_aoa10": {"st_drag": 0.8633}}
+
+
+def _run_to_end(lbm, specs, storage, graph_steps, chunk=4096):
+    """Run a batch of specs to their step counts; the force series of each, [n, nb, 2]."""
+    import numpy as np
+    b = lbm.Batch(storage, max_domains=len(specs), graph_steps=graph_steps)
+    slots = [b.admit(sp) for sp in specs]
+    out = {k: [] for k in slots}
+    while True:
+        ran = b.run(chunk)
+        for k in slots:
+            f, _ = b.poll(k)
+            out[k].append(f)
+        if ran == 0:
+            break
+    b.close()
+    return [np.concatenate(out[k]) for k in slots]
+
+
+def paper_cases(lbm, np, args):
+    """The paper's flows past obstacles other than the single cylinder, each family run as
+    one FP32 batch: cylinder pairs in tandem and side by side (Re 200, L/D 1.5-4),
+    counter-rotating cylinders (Re 150, omega 1.5-4) and the NACA-0012 (Re 500 at 0 deg,
+    Re 1000 at 10 deg); statistics over the second half of each run."""
+    import synth
+    from paper_1901_08766_gb300 import diagnostics as dg
+    storage = "f32"
+    t0 = time.perf_counter()
+    res = {"storage": storage}
+
+    def stats(c, U, L, half=True):
+        cd, cl = dg.coefficients(c, U, L)
+        tail = slice(len(cd) // 2, len(cd))
+        steady = dg.amplitude(cl[tail]) < 1e-3
+        return cd[tail], cl[tail], steady
+
+    spacings = (1.5, 2.0, 3.0, 4.0)
+    specs = [synth.paper_pair("tandem", L) for L in spacings] + [synth.paper_pair("side", L) for L in spacings]
+    series = _run_to_end(lbm, specs, storage, args.graph_steps)
+    rows = []
+    for sp, f in zip(specs, series):
+        D, U = sp["bodies"][0]["ref_length"], sp["U"]
+        cd1, cl1, st1 = stats(f[:, 0], U, D)
+        cd2, cl2, st2 = stats(f[:, 1], U, D)
+        lift = cl2 if sp["arrangement"] == "tandem" else cl1
+        steady = (st2 if sp["arrangement"] == "tandem" else st1)
+        r = {"case": sp["name"], "arrangement": sp["arrangement"], "spacing": sp["spacing"],
+             "cd_1": float(cd1.mean()), "cl_1": float(cl1.mean()), "cd_2": float(cd2.mean()),
+             "cl_2": float(cl2.mean()), "st": 0.0 if steady else dg.strouhal_spectral(lift, D, U)}
+        if sp["arrangement"] == "tandem":
+            r["paper"] = dict(zip(("cd_1", "cd_2", "st"), PAPER_TANDEM[sp["spacing"]]))
+        else:
+            r["paper"] = dict(zip(("cd_1", "cl_1", "cd_2", "cl_2", "st"), PAPER_SIDE[sp["spacing"]]))
+        rows.append(r)
+    res["pairs"] = rows
+    omegas = (1.5, 2.0, 2.5, 3.0, 3.5, 4.0)
+    specs = [synth.paper_rotating_pair(w) for w in omegas]
+    series = _run_to_end(lbm, specs, storage, args.graph_steps)
+    rows = []
+    for w, sp, f in zip(omegas, specs, series):
+        D, U = sp["bodies"][0]["ref_length"], sp["U"]
+        cd, cl, steady = stats(f[:, 1], U, D)  # lower cylinder, as the paper's figure
+        rows.append({"omega": w, "cd_lower": float(cd.mean()), "cl_lower": float(cl.mean()),
+                     "cl_amplitude": dg.amplitude(cl), "steady": bool(steady)})
+    res["rotating"] = rows
+    specs = [synth.naca0012(0.0, 500.0, chord=320.0, U=0.1, nx=2048, ny=1024, steps=100000),
+             synth.naca0012(10.0, 1000.0, chord=320.0, U=0.1, nx=2048, ny=1024, steps=100000)]
+    series = _run_to_end(lbm, specs, storage, args.graph_steps)
+    rows = []
+    for key, sp, f in zip(("re500_aoa0", "re1000_aoa10"), specs, series):
+        c, U = sp["bodies"][0]["ref_length"], sp["U"]
+        cd, cl, steady = stats(f[:, 0], U, c)
+        rows.append({"case": key, "cd": float(cd.mean()), "cl": float(cl.mean()), "steady": bool(steady),
+                     "st_drag": 0.0 if dg.amplitude(cd) < 1e-4 else dg.strouhal_spectral(cd, c, U),
+                     "st_lift": 0.0 if steady else dg.strouhal_spectral(cl, c, U), "paper": PAPER_NACA[key]})
+    res["naca"] = rows
+    res["seconds"] = time.perf_counter() - t0
+    return res
 
 
 def viv_sweep(lbm, torch, np, args, reduced_velocities=(3.0, 4.0, 5.0, 6.0, 7.0, 8.0), steps=60000,
@@ -650,7 +739,8 @@ def main():
     ap.add_argument("--served-chunk", type=int, default=256)
     ap.add_argument("--served-rate", type=float, default=1.2, help="requests/s (--experiment served)")
     ap.add_argument("--served-seconds", type=float, default=120.0, help="arrival window (--experiment served)")
-    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv"],
+    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv",
+                                             "paper"],
                     default=None,
                     help="accuracy study instead of the benchmark")
     args = ap.parse_args()

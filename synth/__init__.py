@@ -272,6 +272,36 @@ def naca0012(aoa_deg, re, chord=200.0, U=0.05, nx=2000, ny=1000, steps=50000):
     return sp
 
 
+def paper_pair(arrangement, spacing, re=200.0, D=40.0, U=0.05, nx=2048, ny=1024, steps=240000):
+    """A pair of fixed cylinders as in the paper's pair experiments (Sec. 3.3): domain
+    2048 x 1024, D = 40, Re 200, centre-to-centre distance `spacing` * D, pair midpoint at
+    (H/2, H/2 + 1/2) (half a cell off the axis so that shedding does not wait for
+    roundoff); "tandem" along the flow, "side" across it. Body 1 is the upstream (tandem)
+    or upper (side-by-side) cylinder."""
+    nu = U * D / re
+    mx, my = ny / 2.0, ny / 2.0 + 0.5
+    half = spacing * D / 2.0
+    c = [(mx - half, my), (mx + half, my)] if arrangement == "tandem" else [(mx, my + half), (mx, my - half)]
+    shapes = [_circle(k + 1, x, y, D / 2) for k, (x, y) in enumerate(c)]
+    bodies = [_body(x, y, D) for (x, y) in c]
+    sp = _spec(f"{arrangement}_{spacing:g}D_re{re:g}", nx, ny, nu, shapes, bodies, steps, U,
+               _channel_edges(), u_in=(U, 0.0), u0=(U, 0.0))
+    sp["arrangement"], sp["spacing"] = arrangement, spacing
+    return sp
+
+
+def paper_rotating_pair(omega_n, re=150.0, D=40.0, U=0.02, nx=2048, ny=1024, steps=300000):
+    """The paper's two counter-rotating cylinders (Sec. 3.4): side by side, centre-to-centre
+    distance 2D, midpoint at (H/2, H/2), Re 150, normalized rotation rate
+    omega_n = Omega D / (2 U); the upper cylinder turns clockwise, the lower one
+    counter-clockwise (their surfaces move upstream in the gap). U = 0.02 keeps the surface
+    speed omega_n U at 0.08 or less (the paper's U = 0.01 gives tau_s = 0.508; at
+    omega_n = 1.5 both give the lower cylinder's C_d and C_l within 1 %)."""
+    sp = counter_rotating_pair(omega_n, re=re, D=D, U=U, nx=nx, ny=ny, gap=1.0, steps=steps)
+    sp["name"] = f"rotating_w{omega_n:g}_re{re:g}"
+    return sp
+
+
 def served_requests(seed=SEED_SERVED, rate=20.0, duration=600.0, step_lo=20000,
                     step_hi=100000):
     """Poisson request stream of the served workload: arrival time, then a 50/50
