@@ -632,7 +632,7 @@ def served_stream(lbm, torch, np, args):
     resident = []
     with torch.cuda.stream(stream):
         srv = Server(storage=args.storage, hbm_budget=budget, chunk_steps=args.served_chunk,
-                     graph_steps=args.graph_steps)
+                     graph_steps=args.graph_steps, max_resident=args.served_max_resident)
         t0 = srv.clock()
         futs = [srv.submit(sp, arrival=t0 + a) for a, sp in reqs]
         while srv.pump():
@@ -653,6 +653,7 @@ def served_stream(lbm, torch, np, args):
             "p50_service_s": float(np.percentile(svc, 50)) if svc else None,
             "max_resident": max(resident) if resident else 0, "max_queue": st["max_queue"],
             "chunk_steps": args.served_chunk, "storage": args.storage,
+            "max_resident": args.served_max_resident,
             "latency": "arrival to last force slice on the host", "hbm_budget_bytes": budget}
 
 
@@ -739,6 +740,8 @@ def main():
     ap.add_argument("--served-chunk", type=int, default=256)
     ap.add_argument("--served-rate", type=float, default=1.2, help="requests/s (--experiment served)")
     ap.add_argument("--served-seconds", type=float, default=120.0, help="arrival window (--experiment served)")
+    ap.add_argument("--served-max-resident", type=int, default=None,
+                    help="cap on requests sharing the GPU (--experiment served; default: memory only)")
     ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv",
                                              "paper"],
                     default=None,

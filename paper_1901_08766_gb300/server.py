@@ -69,7 +69,7 @@ class Server:
 
     def __init__(self, storage="f16s", max_domains=256, hbm_budget=0, chunk_steps=256,
                  graph_steps=32, force_every=1, backend=None, clock=time.perf_counter,
-                 autotune=False):
+                 autotune=False, max_resident=None):
         if backend is None:
             from . import Batch
             backend = Batch(storage, max_domains=max_domains, hbm_budget=hbm_budget,
@@ -81,6 +81,9 @@ class Server:
         self.force_every = int(force_every)
         self.clock = clock
         self.autotune = autotune
+        # at most this many requests share the GPU at once (None: as many as memory holds);
+        # fewer residents finish each sooner, the others wait in the FIFO queue
+        self.max_resident = max_resident
         self._tuned = False
         self._ids = itertools.count()
         self._lock = threading.Lock()
@@ -145,6 +148,8 @@ class Server:
     def _admit(self):
         from ._native import LbmError
         while self._queue:
+            if self.max_resident is not None and len(self._resident) >= self.max_resident:
+                break
             req = self._queue[0]
             try:
                 slot = self.backend.try_admit(req.spec, nsteps=req.nsteps, force_every=self.force_every,

@@ -99,6 +99,23 @@ def test_fifo_admission_under_budget_and_streaming():
     assert st["completed"] == 4 and st["p99_latency_s"] >= st["p50_latency_s"] > 0
 
 
+def test_resident_cap_keeps_fifo_and_limits_sharing():
+    clock = Clock()
+    fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
+    srv = srvmod.Server(backend=fb, chunk_steps=10, clock=clock, max_resident=2)
+    futs = [srv.submit(_spec(f"r{i}", steps=30), arrival=0.0) for i in range(5)]
+    peak = 0
+    while srv.pump():
+        peak = max(peak, len(fb.slots))
+    assert peak == 2
+    res = [f.result() for f in futs]
+    assert all(r.status == "ok" and r.steps == 30 for r in res)
+    adm = [r.admitted for r in res]
+    assert adm == sorted(adm)
+    # pairs finish together: the first two long before the last one
+    assert res[1].done < res[4].admitted
+
+
 def test_late_arrival_joins_running_batch():
     clock = Clock()
     fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
