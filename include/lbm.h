@@ -344,6 +344,21 @@ LBM_API lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_
 LBM_API lbm_status lbm_batch_body_state(lbm_batch *b, int32_t slot, double *out);
 LBM_API lbm_status lbm_body_state(lbm_domain *d, double *out);
 
+/* Checkpoint of a slot with coupled bodies: the full state of its current step into host
+ * `out`, [nbodies][6] doubles (x, y, vx, vy and the force of the previous step Fx, Fy;
+ * rows of bodies without dynamics are zero). Synchronises. */
+LBM_API lbm_status lbm_batch_coupled_state(lbm_batch *b, int32_t slot, double *out);
+LBM_API lbm_status lbm_coupled_state(lbm_domain *d, double *out);
+
+/* Resume a slot with coupled bodies at step index `steps` (with its populations restored
+ * by lbm_batch_set_populations): `in` is a state written by lbm_batch_coupled_state at
+ * that index. Sets the step index, the bodies' state and table, and the mask of that
+ * geometry; undrained force entries are dropped. The resumed run repeats the original
+ * bit for bit. LBM_EINVAL if the slot has no coupled body or steps is outside
+ * [0, admitted steps]. Synchronises. */
+LBM_API lbm_status lbm_batch_restore_coupled(lbm_batch *b, int32_t slot, int64_t steps, const double *in);
+LBM_API lbm_status lbm_restore_coupled(lbm_domain *d, int64_t steps, const double *in);
+
 /* ---- 3D: D3Q19 / D3Q15 TRT-LBM-VP (single domain) ------------------------------------
  * The paper's closing remark: the method extends to 3D by replacing D2Q9 with D3Q15 or
  * D3Q19. This is the step of Sec. 2.2 with either lattice. D3Q19: e_0 = 0; e_1..6 = +x,

@@ -75,6 +75,20 @@ class Domain:
               "lbm_body_state")
         return out[: self.nbodies]
 
+    def coupled_state(self) -> np.ndarray:
+        """Checkpoint of coupled bodies: [nbodies, 6] (x, y, vx, vy, previous Fx, Fy)."""
+        out = np.zeros((max(self.nbodies, 1), 6))
+        check(load().lbm_coupled_state(self._handle(), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm_coupled_state")
+        return out[: self.nbodies]
+
+    def restore_coupled(self, steps: int, state):
+        """Resume a domain with coupled bodies at a step index with a saved coupled state
+        (set the populations first)."""
+        a = np.ascontiguousarray(state, dtype=np.float64).reshape(self.nbodies, 6)
+        check(load().lbm_restore_coupled(self._handle(), int(steps), a.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm_restore_coupled")
+
     def _handle(self):
         if self._h is None:
             raise RuntimeError("domain destroyed")

@@ -137,6 +137,10 @@ SIGNATURES = {
     "lbm_set_dynamics": (C.c_int, [_VP, _I32, C.POINTER(BodyDynamics)]),
     "lbm_batch_body_state": (C.c_int, [_VP, _I32, _DP]),
     "lbm_body_state": (C.c_int, [_VP, _DP]),
+    "lbm_batch_coupled_state": (C.c_int, [_VP, _I32, _DP]),
+    "lbm_coupled_state": (C.c_int, [_VP, _DP]),
+    "lbm_batch_restore_coupled": (C.c_int, [_VP, _I32, _I64, _DP]),
+    "lbm_restore_coupled": (C.c_int, [_VP, _I64, _DP]),
     "lbm3_params_default": (None, [C.POINTER(Params3)]),
     "lbm3_domain_bytes": (_SZ, [C.POINTER(Params3), _I32]),
     "lbm3_domain_create": (C.c_int, [C.POINTER(Params3), C.POINTER(Shape3), _I32,

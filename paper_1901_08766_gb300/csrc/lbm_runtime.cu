@@ -1159,6 +1159,48 @@ lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, cons
   return LBM_OK;
 }
 
+lbm_status lbm_batch_coupled_state(lbm_batch *b, int32_t slot, double *out) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  if (!s.fsi) return fail(LBM_EINVAL, "the slot has no coupled body");
+  std::vector<double> st(6 * s.nbodies), par(8 * s.nbodies);
+  const double *cur = s.dev.fsi + static_cast<size_t>(s.done & 1) * s.nbodies * 6;
+  LBM_CUDA(cudaMemcpyAsync(st.data(), cur, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, b->st));
+  LBM_CUDA(cudaMemcpyAsync(par.data(), s.dev.fsi_par, sizeof(double) * par.size(), cudaMemcpyDeviceToHost, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  for (int k = 0; k < s.nbodies; ++k)
+    for (int e = 0; e < 6; ++e) out[6 * k + e] = par[8 * k + 7] != 0.0 ? st[6 * k + e] : 0.0;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_restore_coupled(lbm_batch *b, int32_t slot, int64_t steps, const double *in) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  if (!in) return fail(LBM_EINVAL, "in is NULL");
+  if (!s.fsi) return fail(LBM_EINVAL, "the slot has no coupled body");
+  if (steps < 0 || steps > s.target)
+    return fail(LBM_EINVAL, "step index %lld outside [0, %lld]", static_cast<long long>(steps), s.target);
+  for (int q = 0; q < 6 * s.nbodies; ++q)
+    if (!std::isfinite(in[q])) return fail(LBM_EINVAL, "coupled state holds a non-finite value");
+  std::vector<double> par(8 * s.nbodies);
+  LBM_CUDA(cudaMemcpyAsync(par.data(), s.dev.fsi_par, sizeof(double) * par.size(), cudaMemcpyDeviceToHost, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  double *cur = s.dev.fsi + static_cast<size_t>(steps & 1) * s.nbodies * 6;
+  for (int k = 0; k < s.nbodies; ++k) {
+    if (par[8 * k + 7] == 0.0) continue;  // prescribed bodies follow the step index
+    LBM_CUDA(cudaMemcpyAsync(cur + 6 * k, in + 6 * k, sizeof(double) * 6, cudaMemcpyHostToDevice, b->st));
+  }
+  // body table and mask of that geometry (coupled bodies from the state just written)
+  LBM_CUDA(launch_place(b->st, b->d_doms + slot, s.p.nx, s.p.ny, s.pitch, steps));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  s.done = steps;
+  s.drained = entries_at(s, steps);
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_body_state(lbm_batch *b, int32_t slot, double *out) {
   lbm_status rc = check_slot(b, slot);
   if (rc != LBM_OK) return rc;
@@ -1370,6 +1412,16 @@ lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_dynamics
 lbm_status lbm_body_state(lbm_domain *d, double *out) {
   if (!d) return fail(LBM_EINVAL, "domain is NULL");
   return lbm_batch_body_state(d->b, 0, out);
+}
+
+lbm_status lbm_coupled_state(lbm_domain *d, double *out) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return lbm_batch_coupled_state(d->b, 0, out);
+}
+
+lbm_status lbm_restore_coupled(lbm_domain *d, int64_t steps, const double *in) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return lbm_batch_restore_coupled(d->b, 0, steps, in);
 }
 
 lbm_status lbm_domain_destroy(lbm_domain *d) {
