@@ -614,7 +614,29 @@ def viv_sweep(lbm, torch, np, args, reduced_velocities=(3.0, 4.0, 5.0, 6.0, 7.0,
     b.close()
     cells = sum(sp["nx"] * sp["ny"] for sp in specs)
     return {"case": specs[0]["name"].rsplit("_ur", 1)[0], "mass_ratio": 10.0, "zeta": 0.0, "steps": steps,
-            "rows": rows, "seconds": el, "glups": cells * steps / el / 1e9}
+            "rows": rows, "seconds": el, "glups": cells * steps / el / 1e9,
+            "cpu_baseline": cpu_baseline_fsi()}
+
+
+def cpu_baseline_fsi(seconds=8.0):
+    """The FP64 oracle with a coupled body, as it stands, on the host cores: one spring
+    cylinder of the sweep (480 x 240, U* = 5), stepped until about `seconds` of CPU work."""
+    import oracle
+    import synth
+    spec = synth.spring_cylinder(reduced_velocity=5.0)
+    dom = oracle.Domain(spec)
+    dom.run(2)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        dom.run(10)
+        steps += 10
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cells = spec["nx"] * spec["ny"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": cells * steps / el / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"spring cylinder 480x240 (coupled body), {steps} steps, FP64, {el:.1f} s"}
 
 
 def served_stream(lbm, torch, np, args):
@@ -697,6 +719,7 @@ def sphere3d(lbm, torch, np, only=None):
                      "peak_source": peak[1]})
     if only:
         return {"perf": perf, "case_perf": "sphere channel 384x128x128, D=32, Re=100"}
+    cpu = [cpu_baseline3(q) for q in (19, 15)]
     acc = []
     spec = synth.sphere_channel(192, 64, 64, D=16.0, re=100.0, steps=4000)
     D, U = spec["bodies"][0]["ref_length"], spec["U"]
@@ -715,8 +738,29 @@ def sphere3d(lbm, torch, np, only=None):
         for r in rows:
             r["cd_rel_vs_f64"] = (r["cd_last_1000"] - ref) / ref
         acc += rows
-    return {"perf": perf, "drag": acc, "case_perf": "sphere channel 384x128x128, D=32, Re=100",
-            "case_drag": spec["name"]}
+    return {"perf": perf, "drag": acc, "cpu_baseline": cpu,
+            "case_perf": "sphere channel 384x128x128, D=32, Re=100", "case_drag": spec["name"]}
+
+
+def cpu_baseline3(q, seconds=8.0):
+    """The FP64 3D oracle as it stands, on the host cores, on a bounded sample: the sphere
+    channel scaled to 96 x 32 x 32 (D = 8), stepped until about `seconds` of CPU work."""
+    import synth
+    from oracle import d3
+    spec = dict(synth.sphere_channel(96, 32, 32, D=8.0), lattice=q)
+    dom = d3.Domain(spec)
+    dom.run(2, want_forces=True)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        dom.run(5, want_forces=True)
+        steps += 5
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    nodes = spec["nx"] * spec["ny"] * spec["nz"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"lattice": f"D3Q{q}", "value": nodes * steps / el / 1e9, "unit": "GLUPS", "cores": cores,
+            "kind": "oracle", "sample": f"sphere channel 96x32x32, {steps} steps, FP64, {el:.1f} s"}
 
 
 def main():
