@@ -81,6 +81,10 @@ def lib():
         L.ora3_run.argtypes = [P, u8p, B, C.c_int32, dp, C.c_int64, dp]
         L.ora3_init.argtypes = [P, dp, dp]
         L.ora3_moments.argtypes = [P, u8p, B, dp, dp, dp, dp, dp]
+        L.ora3_rasterize_at.argtypes = [C.c_int32, C.c_int32, C.c_int32, S, C.c_int32, B, C.c_int32,
+                                        C.c_int64, u8p]
+        L.ora3_run_moving.restype = C.c_int
+        L.ora3_run_moving.argtypes = [P, S, C.c_int32, B, C.c_int32, dp, C.c_int64, C.c_int64, dp]
         L.ora3_lattice.restype = C.c_int32
         L.ora3_lattice.argtypes = [C.c_int32, i32p, i32p, i32p, dp, i32p]
         _lib = L
@@ -158,11 +162,16 @@ def guo(u, F, q=19):
     return out
 
 
-def rasterize(spec):
-    """Body-id mask uint8 [nz, ny, nx]."""
+def rasterize(spec, step=None):
+    """Body-id mask uint8 [nz, ny, nx]; with `step`, the mask of a moving domain at that
+    step index (shapes translated with their bodies)."""
     m = np.zeros((spec["nz"], spec["ny"], spec["nx"]), dtype=np.uint8)
     arr, n = _shapes_of(spec)
-    lib().ora3_rasterize(spec["nx"], spec["ny"], spec["nz"], arr, n, _u8(m))
+    if step is None:
+        lib().ora3_rasterize(spec["nx"], spec["ny"], spec["nz"], arr, n, _u8(m))
+    else:
+        bodies, nb = _bodies_of(spec)
+        lib().ora3_rasterize_at(spec["nx"], spec["ny"], spec["nz"], arr, n, bodies, nb, int(step), _u8(m))
     return m
 
 
@@ -174,13 +183,19 @@ def stream(spec, g):
 
 
 class Domain:
-    """One 3D simulation: post-collision populations g [19, nz, ny, nx] in FP64."""
+    """One 3D simulation: post-collision populations g [Q, nz, ny, nx] in FP64. A spec with
+    "moving": True has bodies that translate with their velocities (mask and centres
+    follow them before every step)."""
 
     def __init__(self, spec, mask=None, g=None):
         self.spec = spec
         self.p = params_of(spec)
+        self.moving = bool(spec.get("moving", False))
+        if self.moving and mask is not None:
+            raise ValueError("a moving domain's mask follows its shapes")
         self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask, dtype=np.uint8)
         self.bodies, self.nb = _bodies_of(spec)
+        self.shapes, self.ns = _shapes_of(spec)
         shape = (nq(spec), spec["nz"], spec["ny"], spec["nx"])
         if g is None:
             self.g = np.zeros(shape)
@@ -192,14 +207,31 @@ class Domain:
     def run(self, n: int, want_forces: bool = True):
         """Advance n steps; the force on each body per step, [n, nbodies, 3]."""
         forces = np.zeros((n, max(self.nb, 1), 3)) if want_forces else None
-        rc = lib().ora3_run(C.byref(self.p), _u8(self.mask), self.bodies, self.nb, _dp(self.g), n,
-                            _dp(forces) if want_forces else None)
+        if self.moving:
+            rc = lib().ora3_run_moving(C.byref(self.p), self.shapes, self.ns, self.bodies, self.nb,
+                                       _dp(self.g), self.steps_done, n, _dp(forces) if want_forces else None)
+        else:
+            rc = lib().ora3_run(C.byref(self.p), _u8(self.mask), self.bodies, self.nb, _dp(self.g), n,
+                                _dp(forces) if want_forces else None)
         if rc != 0:
             raise MemoryError("oracle run failed to allocate")
         self.steps_done += n
+        if self.moving:
+            self.mask = rasterize(self.spec, self.steps_done)
         return forces[:, : self.nb] if want_forces else None
 
+    def bodies_now(self):
+        """Body table at the current step index (centres moved for a moving domain):
+        [nbodies, 9] (c, v, w)."""
+        out = np.array([list(b["c"]) + list(b["v"]) + list(b["w"]) for b in self.spec["bodies"]],
+                       dtype=np.float64).reshape(-1, 9)
+        if self.moving:
+            out[:, 0:3] = out[:, 0:3] + out[:, 3:6] * float(self.steps_done)
+        return out
+
     def step_once(self):
+        if self.moving:
+            raise ValueError("use run() for a moving domain")
         out = np.zeros_like(self.g)
         fb = np.zeros((max(self.nb, 1), 3))
         lib().ora3_step_trt(C.byref(self.p), _u8(self.mask), self.bodies, self.nb, _dp(self.g),
@@ -211,6 +243,11 @@ class Domain:
     def moments(self):
         shp = (self.spec["nz"], self.spec["ny"], self.spec["nx"])
         rho, ux, uy, uz = (np.zeros(shp) for _ in range(4))
-        lib().ora3_moments(C.byref(self.p), _u8(self.mask), self.bodies, _dp(self.g), _dp(rho),
+        bodies = self.bodies
+        if self.moving:
+            bodies = (_Body * max(1, self.nb))()
+            for k, row in enumerate(self.bodies_now()):
+                bodies[k] = _Body(_vec(row[0:3]), _vec(row[3:6]), _vec(row[6:9]))
+        lib().ora3_moments(C.byref(self.p), _u8(self.mask), bodies, _dp(self.g), _dp(rho),
                            _dp(ux), _dp(uy), _dp(uz))
         return rho, ux, uy, uz

@@ -262,6 +262,58 @@ int ora3_run(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
   return 0;
 }
 
+/* ---- moving bodies (prescribed translation, reading M1 in 3D) ----------------------------
+ * Sec. 2.2 lets chi and U_O depend on time. A moving domain's body k is centred at
+ * c_k + V_k n at step index n and each of its shapes is translated by V_k n; the step from
+ * n to n + 1 uses the geometry of index n; the angular velocity acts through U_O about the
+ * moving centre. */
+static void bodies3_at(const ora3_body *b0, int32_t nbodies, int64_t n, ora3_body *out) {
+  for (int k = 0; k < nbodies; k++) {
+    out[k] = b0[k];
+    for (int d = 0; d < 3; d++) out[k].c[d] = b0[k].c[d] + b0[k].v[d] * (double)n;
+  }
+}
+
+/* The mask at step index n (shapes translated with their bodies). */
+void ora3_rasterize_at(int32_t nx, int32_t ny, int32_t nz, const ora3_shape *shapes, int32_t nshapes,
+                       const ora3_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
+  ora3_shape *moved = (ora3_shape *)malloc(sizeof(ora3_shape) * (nshapes > 0 ? nshapes : 1));
+  if (!moved) abort();
+  for (int q = 0; q < nshapes; q++) {
+    moved[q] = shapes[q];
+    const int k = shapes[q].body - 1;
+    if (k >= 0 && k < nbodies)
+      for (int d = 0; d < 3; d++) moved[q].c[d] = shapes[q].c[d] + bodies[k].v[d] * (double)n;
+  }
+  ora3_rasterize(nx, ny, nz, moved, nshapes, mask);
+  free(moved);
+}
+
+/* n steps of a moving domain from step index n0. */
+int ora3_run_moving(const ora3_params *p, const ora3_shape *shapes, int32_t nshapes,
+                    const ora3_body *bodies, int32_t nbodies, double *g, int64_t n0, int64_t n,
+                    double *forces) {
+  size_t cells = (size_t)p->nx * p->ny * p->nz;
+  const int nq = lat3(p->q)->q;
+  double *tmp = (double *)malloc(sizeof(double) * nq * cells);
+  double *fb = (double *)malloc(sizeof(double) * 3 * (nbodies > 0 ? nbodies : 1));
+  uint8_t *mask = (uint8_t *)malloc(cells);
+  ora3_body *now = (ora3_body *)malloc(sizeof(ora3_body) * (nbodies > 0 ? nbodies : 1));
+  if (!tmp || !fb || !mask || !now) { free(tmp); free(fb); free(mask); free(now); return -1; }
+  double *a = g, *b = tmp;
+  for (int64_t s = 0; s < n; s++) {
+    const int64_t m = n0 + s;
+    ora3_rasterize_at(p->nx, p->ny, p->nz, shapes, nshapes, bodies, nbodies, m, mask);
+    bodies3_at(bodies, nbodies, m, now);
+    ora3_step_trt(p, mask, now, nbodies, a, b, fb);
+    if (forces) memcpy(forces + (size_t)s * 3 * nbodies, fb, sizeof(double) * 3 * nbodies);
+    double *t = a; a = b; b = t;
+  }
+  if (a != g) memcpy(g, a, sizeof(double) * nq * cells);
+  free(tmp); free(fb); free(mask); free(now);
+  return 0;
+}
+
 void ora3_init(const ora3_params *p, const double *u0, double *g) {
   double feq[QMAX];
   ora3_equilibrium(p->q, p->rho0, u0, feq);

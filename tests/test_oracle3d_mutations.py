@@ -37,6 +37,12 @@ MUTATIONS = [
     ("outflow_column", "if (p->east == O3_OUTFLOW) sx = p->nx - 1;", "if (p->east == O3_OUTFLOW) sx = p->nx - 2;"),
     ("inlet_ghost", "if (p->west == O3_INLET) return feq_inlet[a];", "if (p->west == O3_INLET) return feq_inlet[opposite3(a)];"),
     ("corrected_velocity", "u[d] = us + du;", "u[d] = us;"),
+    ("moving_shift_sign", "moved[q].c[d] = shapes[q].c[d] + bodies[k].v[d] * (double)n;",
+     "moved[q].c[d] = shapes[q].c[d] - bodies[k].v[d] * (double)n;"),
+    ("moving_step_index", "ora3_rasterize_at(p->nx, p->ny, p->nz, shapes, nshapes, bodies, nbodies, m, mask);",
+     "ora3_rasterize_at(p->nx, p->ny, p->nz, shapes, nshapes, bodies, nbodies, m + 1, mask);"),
+    ("moving_centre_fixed", "for (int d = 0; d < 3; d++) out[k].c[d] = b0[k].c[d] + b0[k].v[d] * (double)n;",
+     "for (int d = 0; d < 3; d++) out[k].c[d] = b0[k].c[d];"),
 ]
 
 Q = (19, 15)
@@ -52,6 +58,10 @@ PINS = [
     lambda: [pins.test_mass_and_momentum_balance_with_bodies(q) for q in Q],
     lambda: [pins.test_fully_penalized_box_closed_form(q) for q in Q],
     lambda: [pins.test_shear_wave_decay_rate(0.1, 3 / 16, q) for q in Q],
+    lambda: [pins.test_moving_mask_is_the_translated_mask(q) for q in Q],
+    lambda: [pins.test_moving_body_in_comoving_uniform_flow_is_steady(q) for q in Q],
+    lambda: [pins.test_moving_bodies_conserve_mass_and_balance_momentum(q) for q in Q],
+    pins.test_moving_run_equals_steps_with_the_geometry_of_each_index,
 ]
 
 

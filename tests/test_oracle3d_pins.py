@@ -238,3 +238,82 @@ def test_shear_wave_decay_rate(nu, lam, q):
     e32, e64 = rel_err(32), rel_err(64)
     assert e64 < 0.01
     assert e32 / e64 > 3.0
+
+
+# ---- moving bodies (prescribed translation) ---------------------------------------------
+
+def _moving(sp):
+    return dict(sp, moving=True)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_moving_mask_is_the_translated_mask(q):
+    # a body moving by (1/4, 0, -1/8) cells per step covers, after 8 steps, the nodes of
+    # the reference mask shifted by (2, 0, -1) (numpy roll, no wrap in this box)
+    V = (0.25, 0.0, -0.125)
+    sp = _moving(_spec(30, 20, 18, shapes=[synth.sphere(1, (9.3, 10.2, 9.6), 4.4), synth.cylinder_z(2, 20.1, 6.3, 2.6)],
+                       bodies=[synth.body3((9.3, 10.2, 9.6), 8.8, v=V), synth.body3((20.1, 6.3, 0.0), 5.2)], q=q))
+    m0 = d3.rasterize(sp)
+    m8 = d3.rasterize(sp, 8)
+    want = m0.copy()
+    want[m0 == 1] = 0
+    want[np.roll(m0 == 1, (-1, 0, 2), axis=(0, 1, 2))] = 1
+    want[m0 == 2] = 2  # the fixed cylinder, drawn later, stays on top
+    assert np.array_equal(m8, want)
+    d = d3.Domain(sp)
+    d.run(8, want_forces=False)
+    assert np.array_equal(d.mask, m8)
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_moving_body_in_comoving_uniform_flow_is_steady(q):
+    # a body moving with the uniform flow of a periodic box: U_O = u everywhere, so the
+    # penalization does nothing and the state stays exactly uniform
+    u = (0.02, -0.01, 0.015)
+    sp = _moving(_spec(24, 16, 14, shapes=[synth.sphere(1, (8.3, 7.9, 6.6), 3.9)],
+                       bodies=[synth.body3((8.3, 7.9, 6.6), 7.8, v=u)], u0=u, q=q))
+    d = d3.Domain(sp)
+    g0 = d.g.copy()
+    f = d.run(60)
+    assert np.abs(d.g - g0).max() < 1e-13
+    assert np.abs(f).max() < 1e-12
+    assert not np.array_equal(d.mask, d3.rasterize(sp))  # it did move
+
+
+@pytest.mark.parametrize("q", LATTICES)
+def test_moving_bodies_conserve_mass_and_balance_momentum(q):
+    shapes = [synth.sphere(1, (6.2, 7.1, 5.3), 3.5), synth.cylinder_z(2, 14.5, 6.0, 2.5)]
+    bodies = [synth.body3((6.2, 7.1, 5.3), 7, v=(0.05, 0.02, -0.03), w=(1e-3, -2e-3, 3e-3)),
+              synth.body3((14.5, 6.0, 0.0), 5, v=(-0.04, 0.03, 0.0))]
+    sp = _moving(_spec(21, 14, 12, lam=0.25, shapes=shapes, bodies=bodies, q=q))
+    d = d3.Domain(sp, g=synth.random_populations3(5, 21, 14, 12, q=q))
+    m0 = d.g.sum()
+    for _ in range(30):
+        _, j0 = _moments(d.g)
+        fb = d.run(1)[0]
+        _, j1 = _moments(d.g)
+        net = fb.sum(axis=0)
+        for c in range(3):
+            assert abs((j1[c].sum() - j0[c].sum()) + net[c]) < 1e-14 * d.g[0].size
+    assert abs(d.g.sum() - m0) < 1e-12 * m0
+    assert not np.array_equal(d.mask, d3.rasterize(sp))
+
+
+def test_moving_run_equals_steps_with_the_geometry_of_each_index():
+    # run(n) is n single steps, step m with the mask and body table of index m
+    shapes = [synth.sphere(1, (7.2, 6.1, 5.4), 3.1)]
+    bodies = [synth.body3((7.2, 6.1, 5.4), 6.2, v=(0.07, -0.03, 0.02), w=(0.0, 0.0, 2e-3))]
+    sp = _moving(_spec(18, 13, 11, shapes=shapes, bodies=bodies))
+    g0 = synth.random_populations3(9, 18, 13, 11)
+    a = d3.Domain(sp, g=g0)
+    fa = a.run(12)
+    g, fs = g0.copy(), []
+    for m in range(12):
+        moved = dict(sp, moving=False,
+                     shapes=[dict(s, c=tuple(c + v * m for c, v in zip(s["c"], bodies[0]["v"]))) for s in shapes],
+                     bodies=[dict(bodies[0], c=tuple(c + v * m for c, v in zip(bodies[0]["c"], bodies[0]["v"])))])
+        b = d3.Domain(moved, g=g)
+        g, f = b.step_once()
+        fs.append(f)
+    assert np.array_equal(a.g, g)
+    assert np.array_equal(fa, np.stack(fs))
