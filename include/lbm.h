@@ -381,6 +381,11 @@ typedef struct {
   int32_t force_every;      /* record body forces every k-th step (0: never) */
   int32_t force_capacity;   /* force-ring entries kept on the device (0: 8192) */
   int32_t lattice;          /* 19 (or 0): D3Q19; 15: D3Q15 */
+  int32_t moving;           /* 1: bodies translate with their velocities (at most 8 bodies,
+                               64 shapes, |V| <= 1 per axis): body k is centred at
+                               c_k + V_k n at step index n, its shapes translated by V_k n,
+                               the mask recomputed after every step; positions are not
+                               wrapped at periodic edges */
 } lbm3_params;
 
 typedef struct {

@@ -72,7 +72,7 @@ class Params3(C.Structure):
                 ("west", C.c_int32), ("east", C.c_int32), ("south", C.c_int32),
                 ("north", C.c_int32), ("bottom", C.c_int32), ("top", C.c_int32),
                 ("storage", C.c_int32), ("force_every", C.c_int32),
-                ("force_capacity", C.c_int32), ("lattice", C.c_int32)]
+                ("force_capacity", C.c_int32), ("lattice", C.c_int32), ("moving", C.c_int32)]
 
 
 class Body3(C.Structure):
@@ -227,7 +227,8 @@ def params3_from_spec(spec, storage: str, force_every: int = 1,
                    spec["eta"], spec["rho0"], (C.c_double * 3)(*spec["u_in"]),
                    (C.c_double * 3)(*spec["u0"]), EDGE[e["west"]], EDGE[e["east"]],
                    EDGE[e["south"]], EDGE[e["north"]], EDGE[e["bottom"]], EDGE[e["top"]],
-                   STORAGE[storage], force_every, force_capacity, int(spec.get("lattice", 19)))
+                   STORAGE[storage], force_every, force_capacity, int(spec.get("lattice", 19)),
+                   1 if spec.get("moving") else 0)
 
 
 def bodies3_from_spec(spec):

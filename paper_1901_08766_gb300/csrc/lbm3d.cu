@@ -91,6 +91,14 @@ struct Dom3 {
   Const3<float> cf;
   Const3<double> cd;
   Pair3 pc;
+  // moving domains (prescribed translation; zero / null otherwise)
+  int32_t moving, nshapes;
+  const struct Shape3Dev *shapes;  // reference geometry (step index 0)
+  const double *centre0;           // [nbodies][3] reference centres
+  float mbox[8][3];                // per body: half extents of the box its shapes reach
+                                   // about its centre (< 0: the whole axis)
+  double *mpart;                   // [8][kMoveBlocks3][3] partial force sums
+  uint32_t *mcount;                // [8] blocks of the moving force reduction finished
   // per-launch: base of each direction's array in the lattice read (src) and written (dst)
   const void *src[kQ3];
   void *dst[kQ3];
@@ -620,23 +628,164 @@ struct Shape3Dev {
   double c[3], radius;
 };
 
+__device__ __forceinline__ bool inside3(const Shape3Dev &s, int i, int j, int k) {
+  const double dx = __dsub_rn(double(i), s.c[0]), dy = __dsub_rn(double(j), s.c[1]);
+  double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  if (s.kind == LBM3_SHAPE_SPHERE) {
+    const double dz = __dsub_rn(double(k), s.c[2]);
+    d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+  }
+  return d2 < __dmul_rn(s.radius, s.radius);
+}
+
+// shape s0 at step index n, translated with its body's velocity (bodies9: [nb][9] table,
+// velocity at 3..5); n = 0 gives the reference shape exactly
+__device__ __forceinline__ Shape3Dev shape3_at(const Shape3Dev &s0, const double *bodies9, int nb, long long n) {
+  Shape3Dev s = s0;
+  if (n != 0 && s0.body >= 1 && s0.body <= nb) {
+    const double *v = bodies9 + 9 * (s0.body - 1) + 3;
+    for (int d = 0; d < 3; ++d) s.c[d] = __dadd_rn(s0.c[d], __dmul_rn(v[d], double(n)));
+  }
+  return s;
+}
+
 __global__ void rasterize3_kernel(uint8_t *mask, int nx, int ny, int nz, int pitch, const Shape3Dev *shapes,
-                                  int nshapes) {
+                                  int nshapes, const double *bodies9, int nb, long long n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   if (i >= pitch) return;
   uint8_t id = 0;
   if (i < nx)
     for (int q = 0; q < nshapes; ++q) {
-      const Shape3Dev &s = shapes[q];
-      const double dx = __dsub_rn(double(i), s.c[0]), dy = __dsub_rn(double(j), s.c[1]);
-      double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-      if (s.kind == LBM3_SHAPE_SPHERE) {
-        const double dz = __dsub_rn(double(k), s.c[2]);
-        d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
-      }
-      if (d2 < __dmul_rn(s.radius, s.radius)) id = static_cast<uint8_t>(s.body);
+      const Shape3Dev s = shape3_at(shapes[q], bodies9, nb, n);
+      if (inside3(s, i, j, k)) id = static_cast<uint8_t>(s.body);
     }
   mask[(static_cast<size_t>(k) * ny + j) * pitch + i] = id;
+}
+
+// body centres at step index n: c0 + V n (explicit roundings, as the oracle's plain
+// evaluation), FP64 and FP32 tables
+__global__ void centres3_kernel(const Dom3 *dom, long long n) {
+  const Dom3 &D = *dom;
+  const int b = threadIdx.x;
+  if (b >= D.nbodies) return;
+  for (int d = 0; d < 3; ++d) {
+    const double c = __dadd_rn(D.centre0[3 * b + d], __dmul_rn(D.bodies[9 * b + 3 + d], double(n)));
+    D.bodies[9 * b + d] = c;
+    D.bodies_f[9 * b + d] = float(c);
+  }
+}
+
+// Node ranges of body b's box at step index n, grown by `grow` nodes (inclusive; empty if
+// some hi < lo): the box its shapes reach about its centre c0 + V n.
+struct Box3 {
+  int lo[3], hi[3];
+};
+
+__device__ __forceinline__ Box3 body_box3(const Dom3 &D, int b, long long n, int grow) {
+  Box3 B;
+  const int N[3] = {D.nx, D.ny, D.nz};
+  for (int d = 0; d < 3; ++d) {
+    const float h = D.mbox[b][d];
+    if (h < 0.f) {
+      B.lo[d] = 0;
+      B.hi[d] = N[d] - 1;
+      continue;
+    }
+    const double c = __dadd_rn(D.centre0[3 * b + d], __dmul_rn(D.bodies[9 * b + 3 + d], double(n)));
+    // clamped to [-1, N] in FP64 first, so that a body far outside converts safely
+    const double lo = fmin(fmax(floor(c - double(h)) - grow, -1.0), double(N[d]));
+    const double hi = fmax(fmin(ceil(c + double(h)) + grow, double(N[d])), -1.0);
+    B.lo[d] = max(0, static_cast<int>(lo));
+    B.hi[d] = min(N[d] - 1, static_cast<int>(hi));
+  }
+  return B;
+}
+
+constexpr int kMoveBlocks3 = 64;   // blocks per body of the moving-domain kernels
+constexpr int kMoveThreads3 = 256;
+
+// Forces of a moving domain at step index n (the sweep just computed step n + 1): per
+// body, the rows of its box at n (where all its nodes of step n lie) split over
+// kMoveBlocks3 blocks, one warp per row, -F_VP of the nodes with its id; each block's sum
+// (fixed tree) goes to a partial slot, and the last block of the body adds the partials
+// in block order into the ring entry. Deterministic: the box depends on n only.
+template <typename T>
+__global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom, long long n, long long entry) {
+  const Dom3 &D = *dom;
+  const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const Box3 B = body_box3(D, b, n, 0);
+  const int ny_b = B.hi[1] - B.lo[1] + 1, nz_b = B.hi[2] - B.lo[2] + 1;
+  const int nrows = (ny_b > 0 && nz_b > 0 && B.hi[0] >= B.lo[0]) ? ny_b * nz_b : 0;
+  double f[3] = {0.0, 0.0, 0.0};
+  for (int r = blockIdx.x * (kMoveThreads3 / 32) + warp; r < nrows; r += gridDim.x * (kMoveThreads3 / 32)) {
+    const int j = B.lo[1] + r % ny_b, k = B.lo[2] + r / ny_b;
+    const size_t row = static_cast<size_t>(k) * D.ny + j;
+    const uint8_t *m = D.mask + row * D.pitch;
+    const T *fv = static_cast<const T *>(D.fvp) + 3 * row * D.pitch;
+    for (int i = B.lo[0] + lane; i <= B.hi[0]; i += 32)
+      if (m[i] == b + 1)
+        for (int e = 0; e < 3; ++e) f[e] -= double(fv[3 * i + e]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    for (int e = 0; e < 3; ++e) f[e] += __shfl_down_sync(0xffffffffu, f[e], off);
+  __shared__ double red[3][kMoveThreads3 / 32];
+  __shared__ bool last;
+  if (lane == 0)
+    for (int e = 0; e < 3; ++e) red[e][warp] = f[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double *part = D.mpart + (static_cast<size_t>(b) * kMoveBlocks3 + blockIdx.x) * 3;
+    for (int e = 0; e < 3; ++e) {
+      double t = 0.0;
+      for (int w = 0; w < kMoveThreads3 / 32; ++w) t += red[e][w];
+      part[e] = t;
+    }
+    __threadfence();
+    last = atomicAdd(D.mcount + b, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double t[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < static_cast<int>(gridDim.x); ++q)
+    for (int e = 0; e < 3; ++e) t[e] += __ldcg(D.mpart + (static_cast<size_t>(b) * kMoveBlocks3 + q) * 3 + e);
+  double *slot = D.ring + (static_cast<size_t>(entry % D.force_cap) * D.nbodies + b) * 3;
+  for (int e = 0; e < 3; ++e) slot[e] = t[e];
+  D.mcount[b] = 0u;
+}
+
+// The mask of a moving domain at step index n + 1, after the forces of step n: per body,
+// the nodes of its box at n grown by one node (|V| <= 1 per axis, so the box at n + 1 lies
+// inside), ids from every shape at n + 1 (later shapes overwrite earlier ones), one warp
+// per row. Boxes of different bodies may overlap: they write the same ids there. Block
+// (0, 0) then moves the body centres to n + 1 (no other block reads them).
+__global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, long long n) {
+  const Dom3 &D = *dom;
+  const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const Box3 B = body_box3(D, b, n, 1);
+  const int ny_b = B.hi[1] - B.lo[1] + 1, nz_b = B.hi[2] - B.lo[2] + 1;
+  const int nrows = (ny_b > 0 && nz_b > 0 && B.hi[0] >= B.lo[0]) ? ny_b * nz_b : 0;
+  for (int r = blockIdx.x * (kMoveThreads3 / 32) + warp; r < nrows; r += gridDim.x * (kMoveThreads3 / 32)) {
+    const int j = B.lo[1] + r % ny_b, k = B.lo[2] + r / ny_b;
+    uint8_t *m = D.mask + (static_cast<size_t>(k) * D.ny + j) * D.pitch;
+    for (int i = B.lo[0] + lane; i <= B.hi[0]; i += 32) {
+      uint8_t id = 0;
+      for (int q = 0; q < D.nshapes; ++q) {
+        const Shape3Dev s = shape3_at(D.shapes[q], D.bodies, D.nbodies, n + 1);
+        if (inside3(s, i, j, k)) id = static_cast<uint8_t>(s.body);
+      }
+      m[i] = id;
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < D.nbodies) {
+    const int c = threadIdx.x;
+    for (int d = 0; d < 3; ++d) {
+      const double x = __dadd_rn(D.centre0[3 * c + d], __dmul_rn(D.bodies[9 * c + 3 + d], double(n + 1)));
+      D.bodies[9 * c + d] = x;
+      D.bodies_f[9 * c + d] = float(x);
+    }
+  }
 }
 
 // Body forces of step index n (the sweep just computed step n + 1): one warp per listed
@@ -743,8 +892,16 @@ double w_of(int q, int a) {
 }
 
 struct Layout3 {
-  size_t lat, mask_off, fvp_off, bodies_off, bodiesf_off, ring_off, status_off, total;
+  size_t lat, mask_off, fvp_off, bodies_off, bodiesf_off, ring_off, status_off, moving_off, total;
 };
+
+// moving domains: shape table, reference centres, partial force sums, block counters
+constexpr int kMaxMoving3 = 8;
+constexpr int kMaxShapes3 = 64;
+size_t moving_bytes3() {
+  return up(sizeof(Shape3Dev) * kMaxShapes3, 256) + up(sizeof(double) * 3 * kMaxMoving3, 256) +
+         up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256);
+}
 
 Layout3 layout3(const lbm3_params &p, int nb) {
   Layout3 L;
@@ -765,6 +922,8 @@ Layout3 layout3(const lbm3_params &p, int nb) {
   o += up(p.force_every > 0 ? sizeof(double) * 3 * std::max(1, nb) * cap : 16, 256);
   L.status_off = o;
   o += 256;
+  L.moving_off = o;
+  if (p.moving) o += moving_bytes3();
   L.total = o;
   return L;
 }
@@ -850,11 +1009,24 @@ cudaError_t launch_sweep3(lbm3_domain *d, long long n, int par) {
 cudaError_t launch_forces3(lbm3_domain *d, long long n) {
   if (d->p.force_every <= 0 || (n + 1) % d->p.force_every != 0 || d->nbodies == 0) return cudaSuccess;
   const long long entry = (n + 1) / d->p.force_every - 1;
+  if (d->p.moving) {
+    const dim3 g(kMoveBlocks3, d->nbodies);
+    if (d->p.storage == LBM_F64) mforce3_kernel<double><<<g, kMoveThreads3, 0, d->st>>>(d->d_dom, n, entry);
+    else mforce3_kernel<float><<<g, kMoveThreads3, 0, d->st>>>(d->d_dom, n, entry);
+    return cudaGetLastError();
+  }
   if (d->h.nfrows == 0)
     return cudaMemsetAsync(d->h.ring + (entry % d->h.force_cap) * d->nbodies * 3, 0,
                            sizeof(double) * 3 * d->nbodies, d->st);
   if (d->p.storage == LBM_F64) rows3_kernel<double><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->d_dom, entry);
   else rows3_kernel<float><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->d_dom, entry);
+  return cudaGetLastError();
+}
+
+// a moving domain's geometry for the next step (after the forces of step n)
+cudaError_t launch_move3(lbm3_domain *d, long long n) {
+  if (!d->p.moving || d->nbodies == 0) return cudaSuccess;
+  mmove3_kernel<<<dim3(kMoveBlocks3, d->nbodies), kMoveThreads3, 0, d->st>>>(d->d_dom, n);
   return cudaGetLastError();
 }
 
@@ -886,6 +1058,9 @@ lbm_status validate3(const lbm3_params *p, int nb, int ns, const lbm3_shape *sha
     if (shapes[q].body < 1 || shapes[q].body > nb) return fail3(LBM_EINVAL, "shape %d: body id not in [1, %d]", q, nb);
   }
   if (p->force_every < 0 || p->force_capacity < 0) return fail3(LBM_EINVAL, "force_every/capacity must be >= 0");
+  if (p->moving != 0 && p->moving != 1) return fail3(LBM_EINVAL, "moving must be 0 or 1");
+  if (p->moving && (nb > kMaxMoving3 || ns > kMaxShapes3))
+    return fail3(LBM_EINVAL, "a moving 3D domain has at most %d bodies and %d shapes", kMaxMoving3, kMaxShapes3);
   return LBM_OK;
 }
 
@@ -1074,17 +1249,7 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
     }
   }
   cudaStream_t st = d->st;
-  // shapes -> mask
-  std::vector<Shape3Dev> hs(std::max(1, nshapes));
-  for (int q = 0; q < nshapes; ++q)
-    hs[q] = Shape3Dev{shapes[q].kind, shapes[q].body, {shapes[q].c[0], shapes[q].c[1], shapes[q].c[2]}, shapes[q].radius};
-  dsh = d->get(sizeof(Shape3Dev) * hs.size());
-  if (!dsh) return bail(fail3(LBM_ENOMEM, "shape buffer allocation failed"));
-  ADM3(cudaMemcpyAsync(dsh, hs.data(), sizeof(Shape3Dev) * hs.size(), cudaMemcpyHostToDevice, st));
-  rasterize3_kernel<<<dim3((d->pitch + 127) / 128, p->ny, p->nz), 128, 0, st>>>(
-      D.mask, p->nx, p->ny, p->nz, d->pitch, static_cast<const Shape3Dev *>(dsh), nshapes);
-  ADM3(cudaGetLastError());
-  // body tables
+  // body tables (before the mask: a moving domain's shapes are placed from them)
   std::vector<double> hb(9 * std::max(1, nbodies), 0.0);
   for (int q = 0; q < nbodies; ++q)
     for (int e = 0; e < 3; ++e) {
@@ -1092,9 +1257,61 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
       hb[9 * q + 3 + e] = bodies[q].v[e];
       hb[9 * q + 6 + e] = bodies[q].w[e];
     }
+  if (p->moving)
+    for (int q = 0; q < nbodies; ++q)
+      for (int e = 0; e < 3; ++e)
+        if (!(std::fabs(bodies[q].v[e]) <= 1.0))
+          return bail(fail3(LBM_EINVAL, "a moving body moves at most one node per step along each axis"));
   std::vector<float> hbf(hb.begin(), hb.end());
   ADM3(cudaMemcpyAsync(D.bodies, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
   ADM3(cudaMemcpyAsync(D.bodies_f, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
+  // shapes -> mask
+  std::vector<Shape3Dev> hs(std::max(1, nshapes));
+  for (int q = 0; q < nshapes; ++q)
+    hs[q] = Shape3Dev{shapes[q].kind, shapes[q].body, {shapes[q].c[0], shapes[q].c[1], shapes[q].c[2]}, shapes[q].radius};
+  D.moving = p->moving;
+  D.nshapes = p->moving ? nshapes : 0;
+  if (p->moving) {
+    // kept for the per-step geometry: shapes, reference centres, force partials, counters
+    char *mb = base + L.moving_off;
+    D.shapes = reinterpret_cast<const Shape3Dev *>(mb);
+    mb += up(sizeof(Shape3Dev) * kMaxShapes3, 256);
+    D.centre0 = reinterpret_cast<const double *>(mb);
+    mb += up(sizeof(double) * 3 * kMaxMoving3, 256);
+    D.mpart = reinterpret_cast<double *>(mb);
+    mb += up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256);
+    D.mcount = reinterpret_cast<uint32_t *>(mb);
+    ADM3(cudaMemsetAsync(base + L.moving_off, 0, moving_bytes3(), st));
+    ADM3(cudaMemcpyAsync(const_cast<Shape3Dev *>(D.shapes), hs.data(), sizeof(Shape3Dev) * nshapes,
+                         cudaMemcpyHostToDevice, st));
+    std::vector<double> c0(3 * kMaxMoving3, 0.0);
+    for (int q = 0; q < nbodies; ++q)
+      for (int e = 0; e < 3; ++e) c0[3 * q + e] = bodies[q].c[e];
+    ADM3(cudaMemcpyAsync(const_cast<double *>(D.centre0), c0.data(), sizeof(double) * c0.size(),
+                         cudaMemcpyHostToDevice, st));
+    // per body: half extents of the box its shapes reach about its centre, two nodes wide
+    // beyond the shapes (a z-cylinder spans the whole z axis)
+    for (int b = 0; b < kMaxMoving3; ++b)
+      for (int e = 0; e < 3; ++e) D.mbox[b][e] = 0.f;
+    for (int q = 0; q < nshapes; ++q) {
+      const int b = shapes[q].body - 1;
+      for (int e = 0; e < 3; ++e) {
+        if (e == 2 && shapes[q].kind == LBM3_SHAPE_CYLINDER_Z) {
+          D.mbox[b][2] = -1.f;
+          continue;
+        }
+        if (D.mbox[b][e] < 0.f) continue;
+        const double h = std::fabs(shapes[q].c[e] - bodies[b].c[e]) + shapes[q].radius + 2.0;
+        D.mbox[b][e] = std::max(D.mbox[b][e], static_cast<float>(h));
+      }
+    }
+  }
+  dsh = d->get(sizeof(Shape3Dev) * hs.size());
+  if (!dsh) return bail(fail3(LBM_ENOMEM, "shape buffer allocation failed"));
+  ADM3(cudaMemcpyAsync(dsh, hs.data(), sizeof(Shape3Dev) * hs.size(), cudaMemcpyHostToDevice, st));
+  rasterize3_kernel<<<dim3((d->pitch + 127) / 128, p->ny, p->nz), 128, 0, st>>>(
+      D.mask, p->nx, p->ny, p->nz, d->pitch, static_cast<const Shape3Dev *>(dsh), nshapes, D.bodies, nbodies, 0);
+  ADM3(cudaGetLastError());
   // rows that hold solid nodes (the force reduction visits only those)
   const size_t cells = static_cast<size_t>(d->pitch) * p->ny * p->nz;
   std::vector<uint8_t> hm(cells);
@@ -1165,6 +1382,7 @@ lbm_status lbm3_step(lbm3_domain *d, int64_t nsteps) {
     const long long n = d->done + s;
     LBM3_CUDA(launch_sweep3(d, n, (d->parity + static_cast<int>(s & 1)) & 1));
     LBM3_CUDA(launch_forces3(d, n));
+    LBM3_CUDA(launch_move3(d, n));
   }
   d->done += nsteps;
   d->parity = static_cast<int>((d->parity + nsteps) & 1);
@@ -1184,6 +1402,7 @@ lbm_status lbm3_profile(lbm3_domain *d, int32_t steps, double *sweep_us, double 
     LBM3_CUDA(launch_sweep3(d, n, (d->parity + (s & 1)) & 1));
     cudaEventRecord(ev[3 * s + 1], d->st);
     LBM3_CUDA(launch_forces3(d, n));
+    LBM3_CUDA(launch_move3(d, n));
     cudaEventRecord(ev[3 * s + 2], d->st);
   }
   LBM3_CUDA(cudaStreamSynchronize(d->st));
@@ -1286,6 +1505,13 @@ lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps) {
 lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps) {
   if (!d) return fail3(LBM_EINVAL, "domain is NULL");
   if (steps < 0) return fail3(LBM_EINVAL, "step index must be >= 0");
+  if (d->p.moving) {  // the mask and centres of that step index
+    rasterize3_kernel<<<dim3((d->pitch + 127) / 128, d->p.ny, d->p.nz), 128, 0, d->st>>>(
+        d->h.mask, d->p.nx, d->p.ny, d->p.nz, d->pitch, d->h.shapes, d->h.nshapes, d->h.bodies, d->nbodies, steps);
+    LBM3_CUDA(cudaGetLastError());
+    centres3_kernel<<<1, 32, 0, d->st>>>(d->d_dom, steps);
+    LBM3_CUDA(cudaGetLastError());
+  }
   LBM3_CUDA(cudaStreamSynchronize(d->st));
   d->done = steps;
   // entries before the index are gone; the ring slot of entry e stays e % capacity

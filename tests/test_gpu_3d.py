@@ -229,3 +229,71 @@ def test_3d_checkpoint_resume_is_bit_identical(lbm, storage, q):
     assert np.array_equal(np.concatenate([fb1, fb2]), fa)
     a.close()
     c.close()
+
+
+
+def _moving3(edges, q):
+    # bodies stay clear of the domain edges and of each other over 400 steps (a body pushed
+    # into a wall or across a periodic edge, or two bodies overlapping, is outside the
+    # model: positions are not wrapped and rigid bodies do not collide)
+    c1, c2 = (20.3, 10.6, 9.7), (44.6, 9.2, 0.0)
+    sp = synth.spec3("moving3", 70, 20, 20, 0.05,
+                     [synth.sphere(1, c1, 4.1), synth.cylinder_z(2, c2[0], c2[1], 2.9)],
+                     [synth.body3(c1, 8.2, v=(0.035, -0.006, 0.005), w=(0.001, -0.0015, 0.002)),
+                      synth.body3(c2, 5.8, v=(0.02, 0.006, 0.0), w=(0.0, 0.0, 0.003))],
+                     0, 0.03, edges, u_in=(0.03, 0.0, 0.0), u0=(0.01, 0.0, 0.0), lattice=q)
+    sp["moving"] = True
+    return sp
+
+
+@pytest.mark.parametrize("q", [19, 15])
+@pytest.mark.parametrize("edges", ["periodic", "channel"])
+def test_fp64_3d_moving_matches_oracle(lbm, edges, q):
+    e = synth.edges3() if edges == "periodic" else synth.channel_edges3()
+    spec = _moving3(e, q)
+    dom, g0 = _start(lbm, spec, "f64", 17)
+    ora = ora3.Domain(spec, g=g0)
+    fg, fo = [], []
+    for chunk in (1, 99, 300):  # masks compared after each chunk
+        fg.append(dom.run(chunk))
+        fo.append(ora.run(chunk))
+        assert np.array_equal(dom.mask(), ora.mask), f"mask differs after {ora.steps_done} steps"
+    assert not np.array_equal(ora.mask, ora3.rasterize(spec))  # the bodies have moved
+    raw = dom.get_populations()
+    dom.close()
+    rel = np.abs(raw - ora.g) / np.abs(ora.g)
+    assert rel.max() <= 1e-12, f"max relative population difference {rel.max():.3e}"
+    fg, fo = np.concatenate(fg), np.concatenate(fo)
+    assert fg.shape == (400, 2, 3)
+    assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max() + 1e-14
+
+
+@pytest.mark.parametrize("storage", ["f16s", "f32"])
+def test_3d_moving_checkpoint_resume_is_bit_identical(lbm, storage):
+    spec = _moving3(synth.channel_edges3(), 19)
+    a = lbm.Domain3(spec, storage=storage)
+    fa = a.run(90)
+    b = lbm.Domain3(spec, storage=storage)
+    fb1 = b.run(40)
+    snap = b.get_populations()
+    b.close()
+    c = lbm.Domain3(spec, storage=storage)
+    c.set_populations(snap)
+    c.set_steps_done(40)  # also the mask and centres of index 40
+    assert np.array_equal(c.mask(), ora3.rasterize(spec, 40))
+    fb2 = c.run(50)
+    assert np.array_equal(c.get_populations().view(np.uint8), a.get_populations().view(np.uint8))
+    assert np.array_equal(np.concatenate([fb1, fb2]), fa)
+    assert np.array_equal(c.mask(), a.mask())
+    a.close()
+    c.close()
+
+
+def test_3d_moving_rejects_fast_or_too_many_bodies(lbm):
+    spec = _moving3(synth.edges3(), 19)
+    fast = dict(spec, bodies=[dict(spec["bodies"][0], v=(1.5, 0.0, 0.0)), spec["bodies"][1]])
+    with pytest.raises(lbm.LbmError):
+        lbm.Domain3(fast, storage="f32")
+    many = dict(spec, bodies=[spec["bodies"][0]] * 9)
+    with pytest.raises(lbm.LbmError):
+        lbm.Domain3(many, storage="f32")
