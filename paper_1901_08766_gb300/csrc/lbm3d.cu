@@ -702,6 +702,7 @@ __device__ __forceinline__ Box3 body_box3(const Dom3 &D, int b, long long n, int
 }
 
 constexpr int kMoveBlocks3 = 64;   // blocks per body of the moving-domain kernels
+constexpr int kMaxShapes3 = 64;    // shapes of a moving 3D domain
 constexpr int kMoveThreads3 = 256;
 
 // Forces of a moving domain at step index n (the sweep just computed step n + 1): per
@@ -745,13 +746,26 @@ __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom,
     last = atomicAdd(D.mcount + b, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
+  // the last block: thread q loads partial q (all at once), then a fixed tree over q
   double t[3] = {0.0, 0.0, 0.0};
-  for (int q = 0; q < static_cast<int>(gridDim.x); ++q)
-    for (int e = 0; e < 3; ++e) t[e] += __ldcg(D.mpart + (static_cast<size_t>(b) * kMoveBlocks3 + q) * 3 + e);
+  if (threadIdx.x < gridDim.x)
+    for (int e = 0; e < 3; ++e) t[e] = __ldcg(D.mpart + (static_cast<size_t>(b) * kMoveBlocks3 + threadIdx.x) * 3 + e);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    for (int e = 0; e < 3; ++e) t[e] += __shfl_down_sync(0xffffffffu, t[e], off);
+  __syncthreads();
+  if (lane == 0)
+    for (int e = 0; e < 3; ++e) red[e][warp] = t[e];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double *slot = D.ring + (static_cast<size_t>(entry % D.force_cap) * D.nbodies + b) * 3;
-  for (int e = 0; e < 3; ++e) slot[e] = t[e];
+  for (int e = 0; e < 3; ++e) {
+    double x = 0.0;
+    for (int w = 0; w < kMoveThreads3 / 32; ++w) x += red[e][w];
+    slot[e] = x;
+  }
   D.mcount[b] = 0u;
 }
 
@@ -760,9 +774,37 @@ __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom,
 // inside), ids from every shape at n + 1 (later shapes overwrite earlier ones), one warp
 // per row. Boxes of different bodies may overlap: they write the same ids there. Block
 // (0, 0) then moves the body centres to n + 1 (no other block reads them).
+// inside3 with an FP32 pre-test: a node whose FP32 squared distance is farther than 0.5
+// from r^2 is decided there, the others take the exact FP64 predicate. With centres below
+// 4096 in magnitude (FP32 position error <= 2.5e-4) and radii below 100 (|dx|, |dy|, |dz|
+// <= r + 3 for nodes near the sphere or cylinder), the FP32 error of d^2 is below
+// 2 (|dx| + |dy| + |dz|) 2.5e-4 + 4 d^2 2^-24 < 0.2, so the FP32 decision is the exact one.
+__device__ __forceinline__ bool inside3_fast(const Shape3Dev &s, const float (&cf)[3], int i, int j, int k) {
+  if (fabs(s.c[0]) < 4096.0 && fabs(s.c[1]) < 4096.0 && fabs(s.c[2]) < 4096.0 && s.radius < 100.0) {
+    const float dx = float(i) - cf[0], dy = float(j) - cf[1];
+    float d2 = dx * dx + dy * dy;
+    if (s.kind == LBM3_SHAPE_SPHERE) {
+      const float dz = float(k) - cf[2];
+      d2 += dz * dz;
+    }
+    const float r2 = float(s.radius) * float(s.radius);
+    if (d2 < r2 - 0.5f) return true;
+    if (d2 > r2 + 0.5f) return false;
+  }
+  return inside3(s, i, j, k);
+}
+
 __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, long long n) {
   const Dom3 &D = *dom;
   const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // every shape at n + 1, translated once per block (FP64, explicit roundings)
+  __shared__ Shape3Dev sh[kMaxShapes3];
+  __shared__ float shc[kMaxShapes3][3];
+  for (int q = threadIdx.x; q < D.nshapes; q += blockDim.x) {
+    sh[q] = shape3_at(D.shapes[q], D.bodies, D.nbodies, n + 1);
+    for (int d = 0; d < 3; ++d) shc[q][d] = float(sh[q].c[d]);
+  }
+  __syncthreads();
   const Box3 B = body_box3(D, b, n, 1);
   const int ny_b = B.hi[1] - B.lo[1] + 1, nz_b = B.hi[2] - B.lo[2] + 1;
   const int nrows = (ny_b > 0 && nz_b > 0 && B.hi[0] >= B.lo[0]) ? ny_b * nz_b : 0;
@@ -771,10 +813,8 @@ __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, 
     uint8_t *m = D.mask + (static_cast<size_t>(k) * D.ny + j) * D.pitch;
     for (int i = B.lo[0] + lane; i <= B.hi[0]; i += 32) {
       uint8_t id = 0;
-      for (int q = 0; q < D.nshapes; ++q) {
-        const Shape3Dev s = shape3_at(D.shapes[q], D.bodies, D.nbodies, n + 1);
-        if (inside3(s, i, j, k)) id = static_cast<uint8_t>(s.body);
-      }
+      for (int q = 0; q < D.nshapes; ++q)
+        if (inside3_fast(sh[q], shc[q], i, j, k)) id = static_cast<uint8_t>(sh[q].body);
       m[i] = id;
     }
   }
@@ -897,7 +937,6 @@ struct Layout3 {
 
 // moving domains: shape table, reference centres, partial force sums, block counters
 constexpr int kMaxMoving3 = 8;
-constexpr int kMaxShapes3 = 64;
 size_t moving_bytes3() {
   return up(sizeof(Shape3Dev) * kMaxShapes3, 256) + up(sizeof(double) * 3 * kMaxMoving3, 256) +
          up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256);
