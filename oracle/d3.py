@@ -41,6 +41,26 @@ class _Body(C.Structure):
     _fields_ = [("c", C.c_double * 3), ("v", C.c_double * 3), ("w", C.c_double * 3)]
 
 
+class _Dynamics(C.Structure):
+    _fields_ = [("mass", C.c_double), ("k", C.c_double * 3), ("c", C.c_double * 3),
+                ("free_axis", C.c_int32 * 3), ("active", C.c_int32)]
+
+
+def _dynamics_of(spec):
+    """Body dynamics of a 3D spec (bodies with a "dynamics" entry respond to their force:
+    mass, stiffness (3), damping (3), free (3))."""
+    bs = spec["bodies"]
+    arr = (_Dynamics * max(1, len(bs)))()
+    active = False
+    for k, b in enumerate(bs):
+        d = b.get("dynamics")
+        if d:
+            active = True
+            arr[k] = _Dynamics(d["mass"], (C.c_double * 3)(*d["stiffness"]), (C.c_double * 3)(*d["damping"]),
+                               (C.c_int32 * 3)(*[int(v) for v in d["free"]]), 1)
+    return arr, active
+
+
 class _Shape(C.Structure):
     _fields_ = [("kind", C.c_int32), ("body", C.c_int32), ("c", C.c_double * 3),
                 ("radius", C.c_double)]
@@ -83,6 +103,9 @@ def lib():
         L.ora3_moments.argtypes = [P, u8p, B, dp, dp, dp, dp, dp]
         L.ora3_rasterize_at.argtypes = [C.c_int32, C.c_int32, C.c_int32, S, C.c_int32, B, C.c_int32,
                                         C.c_int64, u8p]
+        L.ora3_run_fsi.restype = C.c_int
+        L.ora3_run_fsi.argtypes = [P, S, C.c_int32, B, C.POINTER(_Dynamics), C.c_int32, dp, C.c_int64,
+                                   C.c_int64, dp, dp, dp]
         L.ora3_run_moving.restype = C.c_int
         L.ora3_run_moving.argtypes = [P, S, C.c_int32, B, C.c_int32, dp, C.c_int64, C.c_int64, dp]
         L.ora3_lattice.restype = C.c_int32
@@ -196,6 +219,12 @@ class Domain:
         self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask, dtype=np.uint8)
         self.bodies, self.nb = _bodies_of(spec)
         self.shapes, self.ns = _shapes_of(spec)
+        self.dyn, self.fsi = _dynamics_of(spec)
+        if self.fsi and not self.moving:
+            raise ValueError("bodies with dynamics need a moving domain")
+        # x[3], v[3] and the previous step's force[3] of every body (used by coupled bodies)
+        self.state = np.array([list(b["c"]) + list(b["v"]) + [0.0, 0.0, 0.0] for b in spec["bodies"]],
+                              dtype=np.float64).reshape(-1, 9)
         shape = (nq(spec), spec["nz"], spec["ny"], spec["nx"])
         if g is None:
             self.g = np.zeros(shape)
@@ -204,9 +233,24 @@ class Domain:
             self.g = np.ascontiguousarray(g, dtype=np.float64).copy()
         self.steps_done = 0
 
-    def run(self, n: int, want_forces: bool = True):
-        """Advance n steps; the force on each body per step, [n, nbodies, 3]."""
+    def run(self, n: int, want_forces: bool = True, track=None):
+        """Advance n steps; the force on each body per step, [n, nbodies, 3]. `track`, an
+        array [n, nbodies, 6], receives each coupled run's (x, v) of every step."""
         forces = np.zeros((n, max(self.nb, 1), 3)) if want_forces else None
+        if self.fsi:
+            st = np.ascontiguousarray(self.state).copy()
+            tr = np.zeros((n, max(self.nb, 1), 6)) if track is not None else None
+            rc = lib().ora3_run_fsi(C.byref(self.p), self.shapes, self.ns, self.bodies, self.dyn, self.nb,
+                                    _dp(self.g), self.steps_done, n, _dp(st),
+                                    _dp(forces) if want_forces else None, _dp(tr) if tr is not None else None)
+            if rc != 0:
+                raise MemoryError("oracle run failed to allocate")
+            self.state = st
+            if tr is not None:
+                track[...] = tr[:, : self.nb]
+            self.steps_done += n
+            self.mask = self._mask_now()
+            return forces[:, : self.nb] if want_forces else None
         if self.moving:
             rc = lib().ora3_run_moving(C.byref(self.p), self.shapes, self.ns, self.bodies, self.nb,
                                        _dp(self.g), self.steps_done, n, _dp(forces) if want_forces else None)
@@ -221,13 +265,31 @@ class Domain:
         return forces[:, : self.nb] if want_forces else None
 
     def bodies_now(self):
-        """Body table at the current step index (centres moved for a moving domain):
-        [nbodies, 9] (c, v, w)."""
+        """Body table at the current step index (centres moved for a moving domain, coupled
+        bodies at their state): [nbodies, 9] (c, v, w)."""
         out = np.array([list(b["c"]) + list(b["v"]) + list(b["w"]) for b in self.spec["bodies"]],
                        dtype=np.float64).reshape(-1, 9)
         if self.moving:
             out[:, 0:3] = out[:, 0:3] + out[:, 3:6] * float(self.steps_done)
+        for k in range(self.nb):
+            if self.fsi and self.dyn[k].active:
+                out[k, 0:6] = self.state[k, 0:6]
         return out
+
+    def _mask_now(self):
+        """The mask at the current step index (coupled bodies at their current state)."""
+        if not self.fsi:
+            return rasterize(self.spec, self.steps_done)
+        shapes = []
+        for s in self.spec["shapes"]:
+            k = s["body"] - 1
+            if 0 <= k < self.nb and self.dyn[k].active:
+                c0 = self.spec["bodies"][k]["c"]
+                s = dict(s, c=tuple(s["c"][d] + (float(self.state[k, d]) - c0[d]) for d in range(3)))
+            shapes.append(s)
+        bodies = [dict(b, v=(0.0, 0.0, 0.0)) if self.dyn[k].active else b
+                  for k, b in enumerate(self.spec["bodies"])]
+        return rasterize(dict(self.spec, shapes=shapes, bodies=bodies), self.steps_done)
 
     def step_once(self):
         if self.moving:

@@ -314,6 +314,89 @@ int ora3_run_moving(const ora3_params *p, const ora3_shape *shapes, int32_t nsha
   return 0;
 }
 
+/* ---- coupled bodies (fluid-structure coupling, reading M4 in 3D) ------------------------
+ * As in 2D: a body with dynamics is a rigid body of mass M on springs k (anchored at its
+ * initial centre x0) with dampers c; after every step each free axis advances by
+ * semi-implicit Euler (dt = 1) driven by the mean of the forces of this step and the
+ * previous one, Fm = (F_n + F_{n-1}) / 2:  v <- v + (Fm - k (x - x0) - c v) / M, then
+ * x <- x + v; an axis that is not free keeps its velocity. The mask and U_O of a step use
+ * the state before its update; shapes translate with the centre; the angular velocity
+ * stays as given. Bodies without dynamics keep their prescribed motion (c + V n). */
+typedef struct {
+  double mass, k[3], c[3];
+  int32_t free_axis[3], active;
+} ora3_dynamics;
+
+static void fsi3_axis(double F, double *Fp, double k, double c, double M, int32_t free_axis,
+                      double x0, double *x, double *v) {
+  if (free_axis) {
+    double Fm = (F + *Fp) * 0.5;
+    double t = Fm - k * (*x - x0);
+    t = t - c * *v;
+    *v = *v + t / M;
+  }
+  *x = *x + *v;
+  *Fp = F;
+}
+
+/* n steps from step index n0 with coupled bodies; state [nbodies][9] holds x[3], v[3] and
+ * the previous step's force F[3] of the bodies with dynamics, advanced in place; track, if
+ * not NULL, receives (x, v) each step used, [n][nbodies][6]. */
+int ora3_run_fsi(const ora3_params *p, const ora3_shape *shapes, int32_t nshapes,
+                 const ora3_body *bodies, const ora3_dynamics *dyn, int32_t nbodies, double *g,
+                 int64_t n0, int64_t n, double *state, double *forces, double *track) {
+  size_t cells = (size_t)p->nx * p->ny * p->nz;
+  const int nq = lat3(p->q)->q;
+  double *tmp = (double *)malloc(sizeof(double) * nq * cells);
+  double *fb = (double *)malloc(sizeof(double) * 3 * (nbodies > 0 ? nbodies : 1));
+  uint8_t *mask = (uint8_t *)malloc(cells);
+  ora3_body *now = (ora3_body *)malloc(sizeof(ora3_body) * (nbodies > 0 ? nbodies : 1));
+  ora3_shape *sh = (ora3_shape *)malloc(sizeof(ora3_shape) * (nshapes > 0 ? nshapes : 1));
+  if (!tmp || !fb || !mask || !now || !sh) {
+    free(tmp); free(fb); free(mask); free(now); free(sh);
+    return -1;
+  }
+  double *a = g, *b = tmp;
+  for (int64_t s = 0; s < n; s++) {
+    const int64_t m = n0 + s;
+    bodies3_at(bodies, nbodies, m, now);
+    for (int k = 0; k < nbodies; k++) {
+      if (dyn[k].active)
+        for (int d = 0; d < 3; d++) {
+          now[k].c[d] = state[9 * k + d];
+          now[k].v[d] = state[9 * k + 3 + d];
+        }
+      if (track)
+        for (int d = 0; d < 3; d++) {
+          track[((size_t)s * nbodies + k) * 6 + d] = now[k].c[d];
+          track[((size_t)s * nbodies + k) * 6 + 3 + d] = now[k].v[d];
+        }
+    }
+    for (int q = 0; q < nshapes; q++) {
+      sh[q] = shapes[q];
+      const int k = shapes[q].body - 1;
+      if (k < 0 || k >= nbodies) continue;
+      for (int d = 0; d < 3; d++)
+        sh[q].c[d] = dyn[k].active ? shapes[q].c[d] + (state[9 * k + d] - bodies[k].c[d])
+                                   : shapes[q].c[d] + bodies[k].v[d] * (double)m;
+    }
+    ora3_rasterize(p->nx, p->ny, p->nz, sh, nshapes, mask);
+    ora3_step_trt(p, mask, now, nbodies, a, b, fb);
+    if (forces) memcpy(forces + (size_t)s * 3 * nbodies, fb, sizeof(double) * 3 * nbodies);
+    for (int k = 0; k < nbodies; k++) {
+      if (!dyn[k].active) continue;
+      double *st = &state[9 * k];
+      for (int d = 0; d < 3; d++)
+        fsi3_axis(fb[3 * k + d], &st[6 + d], dyn[k].k[d], dyn[k].c[d], dyn[k].mass, dyn[k].free_axis[d],
+                  bodies[k].c[d], &st[d], &st[3 + d]);
+    }
+    double *t = a; a = b; b = t;
+  }
+  if (a != g) memcpy(g, a, sizeof(double) * nq * cells);
+  free(tmp); free(fb); free(mask); free(now); free(sh);
+  return 0;
+}
+
 void ora3_init(const ora3_params *p, const double *u0, double *g) {
   double feq[QMAX];
   ora3_equilibrium(p->q, p->rho0, u0, feq);

@@ -7,6 +7,7 @@ import warnings
 
 import pytest
 
+import test_oracle3d_fsi_pins as fsi_pins
 import test_oracle3d_pins as pins
 import synth
 from oracle import d3 as d3
@@ -43,6 +44,17 @@ MUTATIONS = [
      "ora3_rasterize_at(p->nx, p->ny, p->nz, shapes, nshapes, bodies, nbodies, m + 1, mask);"),
     ("moving_centre_fixed", "for (int d = 0; d < 3; d++) out[k].c[d] = b0[k].c[d] + b0[k].v[d] * (double)n;",
      "for (int d = 0; d < 3; d++) out[k].c[d] = b0[k].c[d];"),
+    # coupled bodies
+    ("fsi_unfiltered_force", "double Fm = (F + *Fp) * 0.5;", "double Fm = F;"),
+    ("fsi_force_memory_lost", "  *Fp = F;\n}", "  *Fp = 0.0;\n}"),
+    ("fsi_spring_anchor", "double t = Fm - k * (*x - x0);", "double t = Fm - k * *x;"),
+    ("fsi_damping_sign", "t = t - c * *v;", "t = t + c * *v;"),
+    ("fsi_explicit_euler", "*v = *v + t / M;", "*x = *x - t / M;\n    *v = *v + t / M;"),
+    ("fsi_shape_not_moved", "sh[q].c[d] = dyn[k].active ? shapes[q].c[d] + (state[9 * k + d] - bodies[k].c[d])",
+     "sh[q].c[d] = dyn[k].active ? shapes[q].c[d]"),
+    ("fsi_state_after_update", "        for (int d = 0; d < 3; d++) {\n          now[k].c[d] = state[9 * k + d];",
+     "        for (int d = 0; d < 3; d++) {\n          now[k].c[d] = state[9 * k + d] + state[9 * k + 3 + d];"),
+    ("fsi_initial_velocity_for_U_O", "          now[k].v[d] = state[9 * k + 3 + d];", "          now[k].v[d] = bodies[k].v[d];"),
 ]
 
 Q = (19, 15)
@@ -62,6 +74,11 @@ PINS = [
     lambda: [pins.test_moving_body_in_comoving_uniform_flow_is_steady(q) for q in Q],
     lambda: [pins.test_moving_bodies_conserve_mass_and_balance_momentum(q) for q in Q],
     pins.test_moving_run_equals_steps_with_the_geometry_of_each_index,
+    lambda: [fsi_pins.test_fluid_plus_body_momentum_is_conserved(q) for q in Q],
+    lambda: [fsi_pins.test_negligible_fluid_force_gives_the_discrete_oscillator(z) for z in (0.0, 0.5)],
+    lambda: [fsi_pins.test_infinitely_heavy_body_at_rest_is_the_fixed_body(q) for q in Q],
+    lambda: [fsi_pins.test_infinitely_heavy_moving_body_is_the_prescribed_motion(q) for q in Q],
+    fsi_pins.test_light_body_stays_bounded,
 ]
 
 
