@@ -447,6 +447,45 @@ LBM_API lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps);
  * count from the new index. Synchronises. */
 LBM_API lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps);
 
+/* Coupled bodies in 3D: the 2D fluid-structure coupling above on three axes. Body k of a
+ * moving domain with dynamics is a rigid body of mass M on springs (k_x, k_y, k_z)
+ * anchored at its initial centre, with dampers (c_x, c_y, c_z); after every step each free
+ * axis advances, in FP64 and rounded in this order,
+ *     Fm = (F_n + F_{n-1}) / 2,   v <- v + (Fm - k (x - x0) - c v) / M,   x <- x + v,
+ * F_n its force of step n (-sum of F_VP over its nodes), F_{-1} = 0; an axis that is not
+ * free keeps its velocity. The next step's mask, centre and U_O use the new state (omega
+ * stays as given); its shapes translate with the centre, by (x - x0). The |V| <= 1 limit
+ * of prescribed motion does not apply to it. */
+typedef struct {
+  double mass;              /* M > 0 */
+  double stiffness[3];      /* k >= 0 per axis */
+  double damping[3];        /* c >= 0 per axis */
+  int32_t free_axis[3];     /* 1: the axis responds to the force, 0: it keeps its velocity */
+} lbm3_body_dynamics;
+
+/* Give body `body` (1-based) dynamics. The domain must be moving, record the force of
+ * every step (force_every = 1) and not have stepped yet; LBM_EINVAL otherwise (the domain is
+ * unchanged). Such a domain changes its step index only through lbm3_restore_coupled
+ * (lbm3_set_steps_done to another index is LBM_EINVAL). Synchronises. */
+LBM_API lbm_status lbm3_set_dynamics(lbm3_domain *d, int32_t body, const lbm3_body_dynamics *dyn);
+
+/* The body table of the current step into host `out`, [nbodies][9] doubles: centre,
+ * velocity, angular velocity (coupled bodies: the integrated state; prescribed motion:
+ * c + V n). Synchronises. */
+LBM_API lbm_status lbm3_body_state(lbm3_domain *d, double *out);
+
+/* Checkpoint of a domain with coupled bodies: the state of its current step into host
+ * `out`, [nbodies][9] doubles (x[3], v[3] and the previous step's force F[3]; rows of
+ * bodies without dynamics are zero). Synchronises. LBM_EINVAL if no body is coupled. */
+LBM_API lbm_status lbm3_coupled_state(lbm3_domain *d, double *out);
+
+/* Resume at step index `steps` >= 0 (populations restored by lbm3_set_populations): `in`
+ * is a state written by lbm3_coupled_state at that index. Sets the step index, the bodies'
+ * state and table and the mask of that geometry; undrained force entries are dropped. The
+ * resumed run repeats the original bit for bit. LBM_EINVAL if no body is coupled.
+ * Synchronises. */
+LBM_API lbm_status lbm3_restore_coupled(lbm3_domain *d, int64_t steps, const double *in);
+
 /* Run `steps` steps bracketing the sweep and the force reduction of each with CUDA
  * events; mean microseconds per launch (either output may be NULL). */
 LBM_API lbm_status lbm3_profile(lbm3_domain *d, int32_t steps, double *sweep_us, double *force_us);

@@ -190,6 +190,13 @@ class Domain3:
                                    self._alloc.c_free if self._alloc else _native.FREE_FN(),
                                    None, C.byref(h)), "lbm3_domain_create")
         self._h = h
+        for k, b in enumerate(spec["bodies"]):  # coupled bodies (fluid-structure coupling)
+            if b.get("dynamics"):
+                dyn = _native.dynamics3_from(b["dynamics"])
+                rc = L.lbm3_set_dynamics(h, k + 1, C.byref(dyn))
+                if rc != 0:
+                    self.close()
+                    check(rc, "lbm3_set_dynamics")
 
     def _handle(self):
         if self._h is None:
@@ -247,6 +254,29 @@ class Domain3:
     def set_steps_done(self, steps: int):
         """Restore the step index with saved populations (it keys the 16-bit rounding)."""
         check(load().lbm3_set_steps_done(self._handle(), int(steps)), "lbm3_set_steps_done")
+
+    def body_state(self) -> np.ndarray:
+        """Body table of the current step, [nbodies, 9]: centre, velocity, angular velocity."""
+        out = np.zeros((max(self.nbodies, 1), 9))
+        check(load().lbm3_body_state(self._handle(), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm3_body_state")
+        return out[: self.nbodies]
+
+    def coupled_state(self) -> np.ndarray:
+        """Checkpoint of the coupled bodies, [nbodies, 9]: x, v and the previous force."""
+        out = np.zeros((max(self.nbodies, 1), 9))
+        check(load().lbm3_coupled_state(self._handle(), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm3_coupled_state")
+        return out[: self.nbodies]
+
+    def restore_coupled(self, steps: int, state: np.ndarray):
+        """Resume at step index `steps` with a coupled_state() taken there (populations set
+        separately)."""
+        a = np.ascontiguousarray(state, dtype=np.float64)
+        if a.shape != (self.nbodies, 9):
+            raise ValueError(f"state must have shape ({self.nbodies}, 9)")
+        check(load().lbm3_restore_coupled(self._handle(), int(steps), a.ctypes.data_as(C.POINTER(C.c_double))),
+              "lbm3_restore_coupled")
 
     def mask(self) -> np.ndarray:
         out = np.zeros((self.nz, self.ny, self.nx), dtype=np.uint8)

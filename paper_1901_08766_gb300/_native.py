@@ -65,6 +65,16 @@ def dynamics_from(d) -> BodyDynamics:
                         (C.c_int32 * 2)(*[int(v) for v in d["free"]]))
 
 
+class BodyDynamics3(C.Structure):
+    _fields_ = [("mass", C.c_double), ("stiffness", C.c_double * 3), ("damping", C.c_double * 3),
+                ("free_axis", C.c_int32 * 3)]
+
+
+def dynamics3_from(d) -> BodyDynamics3:
+    return BodyDynamics3(d["mass"], (C.c_double * 3)(*d["stiffness"]), (C.c_double * 3)(*d["damping"]),
+                         (C.c_int32 * 3)(*[int(v) for v in d["free"]]))
+
+
 class Params3(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nu", C.c_double),
                 ("tau_plus", C.c_double), ("magic_lambda", C.c_double), ("eta", C.c_double),
@@ -154,6 +164,10 @@ SIGNATURES = {
     "lbm3_get_mask": (C.c_int, [_VP, _VP]),
     "lbm3_steps_done": (C.c_int, [_VP, C.POINTER(_I64)]),
     "lbm3_set_steps_done": (C.c_int, [_VP, _I64]),
+    "lbm3_set_dynamics": (C.c_int, [_VP, _I32, C.POINTER(BodyDynamics3)]),
+    "lbm3_body_state": (C.c_int, [_VP, _DP]),
+    "lbm3_coupled_state": (C.c_int, [_VP, _DP]),
+    "lbm3_restore_coupled": (C.c_int, [_VP, _I64, _DP]),
     "lbm3_profile": (C.c_int, [_VP, _I32, _DP, _DP]),
     "lbm3_domain_destroy": (C.c_int, [_VP]),
 }

@@ -74,6 +74,8 @@ struct Pair3 {
   float2 one_m_omp, hp, hm, rho0, pw0, pw1, pw2, mw1, mw2;
 };
 
+constexpr int kMaxMoving3 = 8;  // bodies of a moving 3D domain
+
 struct Dom3 {
   void *lat[2];
   uint8_t *mask;
@@ -99,6 +101,12 @@ struct Dom3 {
                                    // about its centre (< 0: the whole axis)
   double *mpart;                   // [8][kMoveBlocks3][3] partial force sums
   uint32_t *mcount;                // [8] blocks of the moving force reduction finished
+  // coupled bodies (null / zero otherwise): state [2][8][9] by step parity (x, v and the
+  // previous step's force), parameters [8][12] (M, k[3], c[3], free[3]); bit b of
+  // `coupled`: body b + 1 has dynamics
+  double *fsi;
+  const double *fsi_par;
+  uint32_t coupled;
   // per-launch: base of each direction's array in the lattice read (src) and written (dst)
   const void *src[kQ3];
   void *dst[kQ3];
@@ -638,42 +646,76 @@ __device__ __forceinline__ bool inside3(const Shape3Dev &s, int i, int j, int k)
   return d2 < __dmul_rn(s.radius, s.radius);
 }
 
-// shape s0 at step index n, translated with its body's velocity (bodies9: [nb][9] table,
-// velocity at 3..5); n = 0 gives the reference shape exactly
-__device__ __forceinline__ Shape3Dev shape3_at(const Shape3Dev &s0, const double *bodies9, int nb, long long n) {
+// Where the shapes of a moving domain are at a step index: bodies9 [nb][9] (velocity at
+// 3..5); for coupled bodies (bit body - 1 of `coupled`) the state rows of that index, xs
+// [8][9] (centre at 0..2), and the reference centres c0 [8][3].
+struct Place3 {
+  const double *bodies9;
+  int nb;
+  uint32_t coupled;
+  const double *xs, *c0;
+};
+
+// shape s0 at step index n: translated with its body's velocity by V n, or, for a coupled
+// body, by its integrated centre minus its reference centre, x - x0 (explicit roundings);
+// n = 0 and the initial state give the reference shape exactly
+__device__ __forceinline__ Shape3Dev shape3_at(const Shape3Dev &s0, const Place3 &pl, long long n) {
   Shape3Dev s = s0;
-  if (n != 0 && s0.body >= 1 && s0.body <= nb) {
-    const double *v = bodies9 + 9 * (s0.body - 1) + 3;
+  if (s0.body < 1 || s0.body > pl.nb) return s;
+  const int b = s0.body - 1;
+  if (pl.coupled >> b & 1u) {
+    for (int d = 0; d < 3; ++d) s.c[d] = __dadd_rn(s0.c[d], __dsub_rn(pl.xs[9 * b + d], pl.c0[3 * b + d]));
+  } else if (n != 0) {
+    const double *v = pl.bodies9 + 9 * b + 3;
     for (int d = 0; d < 3; ++d) s.c[d] = __dadd_rn(s0.c[d], __dmul_rn(v[d], double(n)));
   }
   return s;
 }
 
 __global__ void rasterize3_kernel(uint8_t *mask, int nx, int ny, int nz, int pitch, const Shape3Dev *shapes,
-                                  int nshapes, const double *bodies9, int nb, long long n) {
+                                  int nshapes, Place3 pl, long long n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   if (i >= pitch) return;
   uint8_t id = 0;
   if (i < nx)
     for (int q = 0; q < nshapes; ++q) {
-      const Shape3Dev s = shape3_at(shapes[q], bodies9, nb, n);
+      const Shape3Dev s = shape3_at(shapes[q], pl, n);
       if (inside3(s, i, j, k)) id = static_cast<uint8_t>(s.body);
     }
   mask[(static_cast<size_t>(k) * ny + j) * pitch + i] = id;
 }
 
-// body centres at step index n: c0 + V n (explicit roundings, as the oracle's plain
-// evaluation), FP64 and FP32 tables
-__global__ void centres3_kernel(const Dom3 *dom, long long n) {
-  const Dom3 &D = *dom;
-  const int b = threadIdx.x;
-  if (b >= D.nbodies) return;
-  for (int d = 0; d < 3; ++d) {
-    const double c = __dadd_rn(D.centre0[3 * b + d], __dmul_rn(D.bodies[9 * b + 3 + d], double(n)));
-    D.bodies[9 * b + d] = c;
-    D.bodies_f[9 * b + d] = float(c);
+// the state row of coupled body b at step index n (x at 0..2, v at 3..5, F_{n-1} at 6..8)
+__device__ __forceinline__ double *fsi_row3(const Dom3 &D, int b, long long n) {
+  return D.fsi + (static_cast<size_t>(n & 1) * kMaxMoving3 + b) * 9;
+}
+
+// centre of body b along axis d at step index n: a coupled body's integrated state, else
+// c0 + V n (explicit roundings, as the oracle's plain evaluation)
+__device__ __forceinline__ double centre3(const Dom3 &D, int b, int d, long long n) {
+  if (D.coupled >> b & 1u) return fsi_row3(D, b, n)[d];
+  return __dadd_rn(D.centre0[3 * b + d], __dmul_rn(D.bodies[9 * b + 3 + d], double(n)));
+}
+
+// body table at step index n (centres; coupled bodies also their velocities), FP64 and
+// FP32, for bodies b = b0, b0 + stride, ...
+__device__ __forceinline__ void place_bodies3(const Dom3 &D, long long n, int b0, int stride) {
+  for (int b = b0; b < D.nbodies; b += stride) {
+    const bool cpl = D.coupled >> b & 1u;
+    const double *st = cpl ? fsi_row3(D, b, n) : nullptr;
+    for (int d = 0; d < 3; ++d) {
+      const double c = centre3(D, b, d, n);
+      D.bodies[9 * b + d] = c;
+      D.bodies_f[9 * b + d] = float(c);
+      if (cpl) {
+        D.bodies[9 * b + 3 + d] = st[3 + d];
+        D.bodies_f[9 * b + 3 + d] = float(st[3 + d]);
+      }
+    }
   }
 }
+
+__global__ void centres3_kernel(const Dom3 *dom, long long n) { place_bodies3(*dom, n, threadIdx.x, blockDim.x); }
 
 // Node ranges of body b's box at step index n, grown by `grow` nodes (inclusive; empty if
 // some hi < lo): the box its shapes reach about its centre c0 + V n.
@@ -691,7 +733,7 @@ __device__ __forceinline__ Box3 body_box3(const Dom3 &D, int b, long long n, int
       B.hi[d] = N[d] - 1;
       continue;
     }
-    const double c = __dadd_rn(D.centre0[3 * b + d], __dmul_rn(D.bodies[9 * b + 3 + d], double(n)));
+    const double c = centre3(D, b, d, n);
     // clamped to [-1, N] in FP64 first, so that a body far outside converts safely
     const double lo = fmin(fmax(floor(c - double(h)) - grow, -1.0), double(N[d]));
     const double hi = fmax(fmin(ceil(c + double(h)) + grow, double(N[d])), -1.0);
@@ -699,6 +741,25 @@ __device__ __forceinline__ Box3 body_box3(const Dom3 &D, int b, long long n, int
     B.hi[d] = min(N[d] - 1, static_cast<int>(hi));
   }
   return B;
+}
+
+__device__ __forceinline__ bool box_empty(const Box3 &B) {
+  return B.hi[0] < B.lo[0] || B.hi[1] < B.lo[1] || B.hi[2] < B.lo[2];
+}
+
+// One axis of a coupled body after step n, driven by the mean of the forces of steps n
+// and n - 1, (F + Fp) / 2 (it cancels the force component that alternates every step):
+// v <- v + (Fm - k (x - x0) - c v) / M, then x <- x + v (semi-implicit Euler, dt = 1),
+// each operation rounded as written; an axis that is not free keeps its velocity.
+__device__ __forceinline__ void fsi3_axis(double F, double Fp, double k, double c, double M, bool free_axis,
+                                          double x0, double &x, double &v) {
+  if (free_axis) {
+    const double Fm = __dmul_rn(__dadd_rn(F, Fp), 0.5);
+    double t = __dsub_rn(Fm, __dmul_rn(k, __dsub_rn(x, x0)));
+    t = __dsub_rn(t, __dmul_rn(c, v));
+    v = __dadd_rn(v, __ddiv_rn(t, M));
+  }
+  x = __dadd_rn(x, v);
 }
 
 constexpr int kMoveBlocks3 = 64;   // blocks per body of the moving-domain kernels
@@ -709,7 +770,8 @@ constexpr int kMoveThreads3 = 256;
 // body, the rows of its box at n (where all its nodes of step n lie) split over
 // kMoveBlocks3 blocks, one warp per row, -F_VP of the nodes with its id; each block's sum
 // (fixed tree) goes to a partial slot, and the last block of the body adds the partials
-// in block order into the ring entry. Deterministic: the box depends on n only.
+// in block order into the ring entry and, for a coupled body, advances its state to n + 1
+// from that force. Deterministic: the box depends on the state of index n only.
 template <typename T>
 __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom, long long n, long long entry) {
   const Dom3 &D = *dom;
@@ -761,19 +823,34 @@ __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom,
   __syncthreads();
   if (threadIdx.x != 0) return;
   double *slot = D.ring + (static_cast<size_t>(entry % D.force_cap) * D.nbodies + b) * 3;
+  double F[3];
   for (int e = 0; e < 3; ++e) {
     double x = 0.0;
     for (int w = 0; w < kMoveThreads3 / 32; ++w) x += red[e][w];
     slot[e] = x;
+    F[e] = x;
   }
   D.mcount[b] = 0u;
+  if (D.coupled >> b & 1u) {
+    const double *par = D.fsi_par + 12 * b;  // M, k[3], c[3], free[3]
+    const double *st = fsi_row3(D, b, n);
+    double *nst = fsi_row3(D, b, n + 1);
+    for (int e = 0; e < 3; ++e) {
+      double x = st[e], v = st[3 + e];
+      fsi3_axis(F[e], st[6 + e], par[1 + e], par[4 + e], par[0], par[7 + e] != 0.0, D.centre0[3 * b + e], x, v);
+      nst[e] = x;
+      nst[3 + e] = v;
+      nst[6 + e] = F[e];
+    }
+  }
 }
 
 // The mask of a moving domain at step index n + 1, after the forces of step n: per body,
 // the nodes of its box at n grown by one node (|V| <= 1 per axis, so the box at n + 1 lies
-// inside), ids from every shape at n + 1 (later shapes overwrite earlier ones), one warp
-// per row. Boxes of different bodies may overlap: they write the same ids there. Block
-// (0, 0) then moves the body centres to n + 1 (no other block reads them).
+// inside; a coupled body: the union of its boxes at n and n + 1), ids from every shape at
+// n + 1 (later shapes overwrite earlier ones), one warp per row. Boxes of different bodies
+// may overlap: they write the same ids there. Block (0, 0) then moves the body table to
+// n + 1 (no other block reads it).
 // inside3 with an FP32 pre-test: a node whose FP32 squared distance is farther than 0.5
 // from r^2 is decided there, the others take the exact FP64 predicate. With centres below
 // 4096 in magnitude (FP32 position error <= 2.5e-4) and radii below 100 (|dx|, |dy|, |dz|
@@ -800,12 +877,25 @@ __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, 
   // every shape at n + 1, translated once per block (FP64, explicit roundings)
   __shared__ Shape3Dev sh[kMaxShapes3];
   __shared__ float shc[kMaxShapes3][3];
+  const Place3 pl{D.bodies, D.nbodies, D.coupled, D.fsi ? fsi_row3(D, 0, n + 1) : nullptr, D.centre0};
   for (int q = threadIdx.x; q < D.nshapes; q += blockDim.x) {
-    sh[q] = shape3_at(D.shapes[q], D.bodies, D.nbodies, n + 1);
+    sh[q] = shape3_at(D.shapes[q], pl, n + 1);
     for (int d = 0; d < 3; ++d) shc[q][d] = float(sh[q].c[d]);
   }
   __syncthreads();
-  const Box3 B = body_box3(D, b, n, 1);
+  Box3 B;
+  if (D.coupled >> b & 1u) {
+    B = body_box3(D, b, n, 0);
+    const Box3 B1 = body_box3(D, b, n + 1, 0);
+    if (box_empty(B)) B = B1;
+    else if (!box_empty(B1))
+      for (int d = 0; d < 3; ++d) {
+        B.lo[d] = min(B.lo[d], B1.lo[d]);
+        B.hi[d] = max(B.hi[d], B1.hi[d]);
+      }
+  } else {
+    B = body_box3(D, b, n, 1);
+  }
   const int ny_b = B.hi[1] - B.lo[1] + 1, nz_b = B.hi[2] - B.lo[2] + 1;
   const int nrows = (ny_b > 0 && nz_b > 0 && B.hi[0] >= B.lo[0]) ? ny_b * nz_b : 0;
   for (int r = blockIdx.x * (kMoveThreads3 / 32) + warp; r < nrows; r += gridDim.x * (kMoveThreads3 / 32)) {
@@ -818,14 +908,7 @@ __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, 
       m[i] = id;
     }
   }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < D.nbodies) {
-    const int c = threadIdx.x;
-    for (int d = 0; d < 3; ++d) {
-      const double x = __dadd_rn(D.centre0[3 * c + d], __dmul_rn(D.bodies[9 * c + 3 + d], double(n + 1)));
-      D.bodies[9 * c + d] = x;
-      D.bodies_f[9 * c + d] = float(x);
-    }
-  }
+  if (blockIdx.x == 0 && blockIdx.y == 0) place_bodies3(D, n + 1, threadIdx.x, blockDim.x);
 }
 
 // Body forces of step index n (the sweep just computed step n + 1): one warp per listed
@@ -935,11 +1018,12 @@ struct Layout3 {
   size_t lat, mask_off, fvp_off, bodies_off, bodiesf_off, ring_off, status_off, moving_off, total;
 };
 
-// moving domains: shape table, reference centres, partial force sums, block counters
-constexpr int kMaxMoving3 = 8;
+// moving domains: shape table, reference centres, partial force sums, block counters,
+// coupled-body state by parity and parameters
 size_t moving_bytes3() {
   return up(sizeof(Shape3Dev) * kMaxShapes3, 256) + up(sizeof(double) * 3 * kMaxMoving3, 256) +
-         up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256);
+         up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256) +
+         up(sizeof(double) * 9 * 2 * kMaxMoving3, 256) + up(sizeof(double) * 12 * kMaxMoving3, 256);
 }
 
 Layout3 layout3(const lbm3_params &p, int nb) {
@@ -1320,6 +1404,11 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
     D.mpart = reinterpret_cast<double *>(mb);
     mb += up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256);
     D.mcount = reinterpret_cast<uint32_t *>(mb);
+    mb += up(sizeof(uint32_t) * kMaxMoving3, 256);
+    D.fsi = reinterpret_cast<double *>(mb);
+    mb += up(sizeof(double) * 9 * 2 * kMaxMoving3, 256);
+    D.fsi_par = reinterpret_cast<const double *>(mb);
+    D.coupled = 0u;
     ADM3(cudaMemsetAsync(base + L.moving_off, 0, moving_bytes3(), st));
     ADM3(cudaMemcpyAsync(const_cast<Shape3Dev *>(D.shapes), hs.data(), sizeof(Shape3Dev) * nshapes,
                          cudaMemcpyHostToDevice, st));
@@ -1349,7 +1438,8 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   if (!dsh) return bail(fail3(LBM_ENOMEM, "shape buffer allocation failed"));
   ADM3(cudaMemcpyAsync(dsh, hs.data(), sizeof(Shape3Dev) * hs.size(), cudaMemcpyHostToDevice, st));
   rasterize3_kernel<<<dim3((d->pitch + 127) / 128, p->ny, p->nz), 128, 0, st>>>(
-      D.mask, p->nx, p->ny, p->nz, d->pitch, static_cast<const Shape3Dev *>(dsh), nshapes, D.bodies, nbodies, 0);
+      D.mask, p->nx, p->ny, p->nz, d->pitch, static_cast<const Shape3Dev *>(dsh), nshapes,
+      Place3{D.bodies, nbodies, 0u, nullptr, nullptr}, 0);
   ADM3(cudaGetLastError());
   // rows that hold solid nodes (the force reduction visits only those)
   const size_t cells = static_cast<size_t>(d->pitch) * p->ny * p->nz;
@@ -1541,12 +1631,13 @@ lbm_status lbm3_steps_done(lbm3_domain *d, int64_t *steps) {
   return LBM_OK;
 }
 
-lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps) {
-  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
-  if (steps < 0) return fail3(LBM_EINVAL, "step index must be >= 0");
-  if (d->p.moving) {  // the mask and centres of that step index
+static lbm_status place_at3(lbm3_domain *d, int64_t steps) {
+  if (d->p.moving) {  // the mask and body table of that step index
+    const Dom3 &D = d->h;
+    const Place3 pl{D.bodies, d->nbodies, D.coupled,
+                    D.fsi ? D.fsi + static_cast<size_t>(steps & 1) * kMaxMoving3 * 9 : nullptr, D.centre0};
     rasterize3_kernel<<<dim3((d->pitch + 127) / 128, d->p.ny, d->p.nz), 128, 0, d->st>>>(
-        d->h.mask, d->p.nx, d->p.ny, d->p.nz, d->pitch, d->h.shapes, d->h.nshapes, d->h.bodies, d->nbodies, steps);
+        D.mask, d->p.nx, d->p.ny, d->p.nz, d->pitch, D.shapes, D.nshapes, pl, steps);
     LBM3_CUDA(cudaGetLastError());
     centres3_kernel<<<1, 32, 0, d->st>>>(d->d_dom, steps);
     LBM3_CUDA(cudaGetLastError());
@@ -1556,6 +1647,81 @@ lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps) {
   // entries before the index are gone; the ring slot of entry e stays e % capacity
   d->drained = d->p.force_every > 0 ? steps / d->p.force_every : 0;
   return LBM_OK;
+}
+
+lbm_status lbm3_set_steps_done(lbm3_domain *d, int64_t steps) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  if (steps < 0) return fail3(LBM_EINVAL, "step index must be >= 0");
+  if (d->h.coupled && steps != d->done)
+    return fail3(LBM_EINVAL, "a domain with coupled bodies changes its step index through lbm3_restore_coupled");
+  return place_at3(d, steps);
+}
+
+lbm_status lbm3_set_dynamics(lbm3_domain *d, int32_t body, const lbm3_body_dynamics *dyn) {
+  if (!d || !dyn) return fail3(LBM_EINVAL, "domain or dynamics is NULL");
+  if (!d->p.moving) return fail3(LBM_EINVAL, "coupled bodies need a moving domain");
+  if (d->p.force_every != 1) return fail3(LBM_EINVAL, "coupled bodies need the force of every step (force_every = 1)");
+  if (d->done != 0) return fail3(LBM_EINVAL, "dynamics are set before the first step");
+  if (body < 1 || body > d->nbodies) return fail3(LBM_EINVAL, "body %d outside 1..%d", body, d->nbodies);
+  if (!(dyn->mass > 0.0) || !std::isfinite(dyn->mass)) return fail3(LBM_EINVAL, "mass must be finite and > 0");
+  for (int e = 0; e < 3; ++e) {
+    if (!(dyn->stiffness[e] >= 0.0) || !std::isfinite(dyn->stiffness[e]) || !(dyn->damping[e] >= 0.0) ||
+        !std::isfinite(dyn->damping[e]))
+      return fail3(LBM_EINVAL, "stiffness and damping must be finite and >= 0");
+    if (dyn->free_axis[e] != 0 && dyn->free_axis[e] != 1) return fail3(LBM_EINVAL, "free_axis must be 0 or 1");
+  }
+  const int b = body - 1;
+  double bt[9];
+  LBM3_CUDA(cudaMemcpyAsync(bt, d->h.bodies + 9 * b, sizeof(bt), cudaMemcpyDeviceToHost, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  // state of index 0: the reference centre, the given velocity, no previous force
+  const double st0[9] = {bt[0], bt[1], bt[2], bt[3], bt[4], bt[5], 0.0, 0.0, 0.0};
+  const double par[12] = {dyn->mass, dyn->stiffness[0], dyn->stiffness[1], dyn->stiffness[2],
+                          dyn->damping[0], dyn->damping[1], dyn->damping[2],
+                          double(dyn->free_axis[0]), double(dyn->free_axis[1]), double(dyn->free_axis[2]), 0.0, 0.0};
+  LBM3_CUDA(cudaMemcpyAsync(d->h.fsi + 9 * b, st0, sizeof(st0), cudaMemcpyHostToDevice, d->st));
+  LBM3_CUDA(cudaMemcpyAsync(const_cast<double *>(d->h.fsi_par) + 12 * b, par, sizeof(par), cudaMemcpyHostToDevice,
+                            d->st));
+  d->h.coupled |= 1u << b;
+  for (int q = 0; q < 2; ++q) d->hpar[q].coupled = d->h.coupled;
+  LBM3_CUDA(cudaMemcpyAsync(d->d_dom, &d->h, sizeof(Dom3), cudaMemcpyHostToDevice, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  return LBM_OK;
+}
+
+lbm_status lbm3_body_state(lbm3_domain *d, double *out) {
+  if (!d || !out) return fail3(LBM_EINVAL, "domain or out is NULL");
+  if (d->nbodies == 0) return LBM_OK;
+  LBM3_CUDA(cudaMemcpyAsync(out, d->h.bodies, sizeof(double) * 9 * d->nbodies, cudaMemcpyDeviceToHost, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  return LBM_OK;
+}
+
+lbm_status lbm3_coupled_state(lbm3_domain *d, double *out) {
+  if (!d || !out) return fail3(LBM_EINVAL, "domain or out is NULL");
+  if (!d->h.coupled) return fail3(LBM_EINVAL, "the domain has no coupled body");
+  std::vector<double> st(9 * kMaxMoving3);
+  LBM3_CUDA(cudaMemcpyAsync(st.data(), d->h.fsi + static_cast<size_t>(d->done & 1) * kMaxMoving3 * 9,
+                            sizeof(double) * st.size(), cudaMemcpyDeviceToHost, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  for (int b = 0; b < d->nbodies; ++b)
+    for (int e = 0; e < 9; ++e) out[9 * b + e] = (d->h.coupled >> b & 1u) ? st[9 * b + e] : 0.0;
+  return LBM_OK;
+}
+
+lbm_status lbm3_restore_coupled(lbm3_domain *d, int64_t steps, const double *in) {
+  if (!d || !in) return fail3(LBM_EINVAL, "domain or state is NULL");
+  if (!d->h.coupled) return fail3(LBM_EINVAL, "the domain has no coupled body");
+  if (steps < 0) return fail3(LBM_EINVAL, "step index must be >= 0");
+  for (int b = 0; b < d->nbodies; ++b)
+    if (d->h.coupled >> b & 1u)
+      for (int e = 0; e < 9; ++e)
+        if (!std::isfinite(in[9 * b + e])) return fail3(LBM_EINVAL, "state of body %d is not finite", b + 1);
+  double *cur = d->h.fsi + static_cast<size_t>(steps & 1) * kMaxMoving3 * 9;
+  for (int b = 0; b < d->nbodies; ++b)
+    if (d->h.coupled >> b & 1u)
+      LBM3_CUDA(cudaMemcpyAsync(cur + 9 * b, in + 9 * b, sizeof(double) * 9, cudaMemcpyHostToDevice, d->st));
+  return place_at3(d, steps);
 }
 
 lbm_status lbm3_domain_destroy(lbm3_domain *d) {
