@@ -700,10 +700,18 @@ def sphere3d(lbm, torch, np, only=None):
     if not only:
         runs += [(15, st, False) for st in ("f16s", "bf16s", "f32")]
         runs += [(19, "f16s", True)]  # the sphere moving upstream: mask updated every step
+        runs += [(19, "f16s", "coupled")]  # the sphere on springs across the stream (y, z)
     for q, st, mv in runs:
         sp = dict(spec, lattice=q)
-        if mv:
+        if mv is True:
             sp = dict(sp, moving=True, bodies=[dict(b, v=(-0.01, 0.0, 0.0)) for b in sp["bodies"]])
+        elif mv == "coupled":
+            b = sp["bodies"][0]
+            M = 10.0 * math.pi * b["ref_length"] ** 3 / 6.0
+            wn = 2.0 * math.pi * spec["U"] / (5.0 * b["ref_length"])
+            dyn = {"mass": M, "stiffness": (0.0, M * wn * wn, M * wn * wn), "damping": (0.0, 0.0, 0.0),
+                   "free": (0, 1, 1)}
+            sp = dict(sp, moving=True, bodies=[dict(b, v=(0.0, 0.01, 0.0), dynamics=dyn)])
         d = lbm.Domain3(sp, storage=st, force_every=1)
         d.step(20)
         d.forces()
@@ -716,7 +724,7 @@ def sphere3d(lbm, torch, np, only=None):
         sw, fo = best
         bpn = bytes3(st, q)
         gbs = nodes * bpn / sw / 1e3
-        perf.append({"lattice": f"D3Q{q}", "storage": st, "moving": mv, "grid": [spec["nx"], spec["ny"], spec["nz"]],
+        perf.append({"lattice": f"D3Q{q}", "storage": st, "moving": bool(mv), "coupled": mv == "coupled", "grid": [spec["nx"], spec["ny"], spec["nz"]],
                      "sweep_us": sw, "force_us": fo, "glups_sweep": nodes / sw / 1e3,
                      "glups_step": nodes / (sw + fo) / 1e3, "bytes_per_node": bpn,
                      "achieved_gbs": gbs, "peak_gbs": peak[0], "frac": gbs / peak[0],
