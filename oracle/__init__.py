@@ -99,6 +99,14 @@ def lib():
         L.ora_moments.argtypes = [C.POINTER(_Params), u8p, C.POINTER(_Body), dp, dp, dp, dp]
         L.ora_rasterize_at.argtypes = [C.c_int32, C.c_int32, C.POINTER(_Shape), C.c_int32,
                                        C.POINTER(_Body), C.c_int32, C.c_int64, u8p]
+        L.ora_rasterize_rot.restype = None
+        L.ora_rasterize_rot.argtypes = L.ora_rasterize_at.argtypes
+        L.ora_sincos.restype = None
+        L.ora_sincos.argtypes = [C.c_double, dp, dp]
+        L.ora_run_moving_mode.restype = C.c_int
+        L.ora_run_moving_mode.argtypes = [C.POINTER(_Params), C.POINTER(_Shape), C.c_int32,
+                                          C.POINTER(_Body), C.c_int32, dp, C.c_int64, C.c_int64,
+                                          dp, C.c_int32, C.c_int32]
         L.ora_run_moving.restype = C.c_int
         L.ora_run_moving.argtypes = [C.POINTER(_Params), C.POINTER(_Shape), C.c_int32,
                                      C.POINTER(_Body), C.c_int32, dp, C.c_int64, C.c_int64, dp,
@@ -172,9 +180,23 @@ def stream(spec, g) -> np.ndarray:
     return f
 
 
+def sincos(t: float):
+    """(sin t, cos t) of the oracle's own FP64 evaluation (reduction by pi/2, Taylor)."""
+    s, c = C.c_double(), C.c_double()
+    lib().ora_sincos(float(t), C.byref(s), C.byref(c))
+    return s.value, c.value
+
+
+def rotating(spec) -> bool:
+    """A spec with "moving": 2 turns its bodies' shapes with their angular velocities."""
+    m = spec.get("moving", False)
+    return not isinstance(m, bool) and m == 2
+
+
 def rasterize(spec, step=None) -> np.ndarray:
     """Body-id mask uint8 [ny, nx] (0 = fluid) from the spec's shapes; with `step`, the
-    mask of a moving domain at that step index (shapes translated with their bodies)."""
+    mask of a moving domain at that step index (shapes translated with their bodies, and
+    turned with them for a rotating domain)."""
     nx, ny = spec["nx"], spec["ny"]
     mask = np.zeros((ny, nx), dtype=np.uint8)
     arr, n = _shapes_of(spec)
@@ -182,8 +204,8 @@ def rasterize(spec, step=None) -> np.ndarray:
         lib().ora_rasterize(nx, ny, arr, n, mask.ctypes.data_as(C.POINTER(C.c_uint8)))
     else:
         bodies, nb = _bodies_of(spec)
-        lib().ora_rasterize_at(nx, ny, arr, n, bodies, nb, int(step),
-                               mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+        fn = lib().ora_rasterize_rot if rotating(spec) else lib().ora_rasterize_at
+        fn(nx, ny, arr, n, bodies, nb, int(step), mask.ctypes.data_as(C.POINTER(C.c_uint8)))
     return mask
 
 
@@ -211,6 +233,7 @@ class Domain:
         self.spec = spec
         self.p = params_of(spec)
         self.moving = bool(spec.get("moving", False))
+        self.rotating = rotating(spec)
         if self.moving and mask is not None:
             raise ValueError("a moving domain's mask follows its shapes")
         self.mask = np.ascontiguousarray(rasterize(spec) if mask is None else mask,
@@ -220,6 +243,8 @@ class Domain:
         self.dyn, self.fsi = _dynamics_of(spec)
         if self.fsi and not self.moving:
             raise ValueError("bodies with dynamics need a moving domain")
+        if self.fsi and self.rotating:
+            raise ValueError("coupled bodies do not turn their shapes (rotating domain)")
         # (x, y, vx, vy, Fx, Fy) of every body at the current step index (used by coupled
         # bodies; F is the force of the previous step, zero before the first)
         self.state = np.array([[b["cx"], b["cy"], b["vx"], b["vy"], 0.0, 0.0] for b in spec["bodies"]],
@@ -256,9 +281,10 @@ class Domain:
             self.mask = self._mask_now()
             return forces[:, : self.nb] if want_forces else None
         if self.moving:
-            rc = lib().ora_run_moving(C.byref(self.p), self.shapes, self.ns, self.bodies,
-                                      self.nb, _dp(self.g), self.steps_done, n,
-                                      _dp(forces) if want_forces else None, 1 if srt else 0)
+            rc = lib().ora_run_moving_mode(C.byref(self.p), self.shapes, self.ns, self.bodies,
+                                           self.nb, _dp(self.g), self.steps_done, n,
+                                           _dp(forces) if want_forces else None, 1 if srt else 0,
+                                           1 if self.rotating else 0)
         else:
             rc = lib().ora_run(C.byref(self.p), self.mask.ctypes.data_as(C.POINTER(C.c_uint8)),
                                self.bodies, self.nb, _dp(self.g), n,

@@ -101,7 +101,9 @@ double ora_naca_half_thickness(double xc, double t, double chord) {
   return 5.0 * t * chord * (0.2969 * s + p);
 }
 
-static int inside_shape(const ora_shape *s, double x, double y) {
+/* inside test of shape s, a NACA section oriented by (ca, sa) = (cos, sin) of its angle
+ * of attack */
+static int inside_shape_cs(const ora_shape *s, double ca, double sa, double x, double y) {
   if (s->kind == ORA_CIRCLE || s->kind == ORA_ANNULUS_OUTSIDE) {
     double dx = x - s->cx, dy = y - s->cy;
     double d2 = dx * dx + dy * dy;
@@ -110,7 +112,6 @@ static int inside_shape(const ora_shape *s, double x, double y) {
   }
   if (s->kind == ORA_NACA4) {
     /* quarter chord at (cx, cy); nose-up angle of attack positive */
-    double ca = cos(s->aoa_rad), sa = sin(s->aoa_rad);
     double qc = 0.25 * s->chord;
     double lex = s->cx - qc * ca, ley = s->cy + qc * sa; /* leading edge */
     double dx = x - lex, dy = y - ley;
@@ -121,6 +122,10 @@ static int inside_shape(const ora_shape *s, double x, double y) {
     return fabs(yp) <= yt;
   }
   return 0;
+}
+
+static int inside_shape(const ora_shape *s, double x, double y) {
+  return inside_shape_cs(s, cos(s->aoa_rad), sin(s->aoa_rad), x, y);
 }
 
 /* Body id per node (0 = fluid); later shapes overwrite earlier ones. */
@@ -154,6 +159,89 @@ static void body_at(const ora_body *b0, int64_t n, ora_body *b) {
   *b = *b0;
   b->cx = b0->cx + b0->vx * (double)n;
   b->cy = b0->cy + b0->vy * (double)n;
+}
+
+/* ---- rotating obstacles (reading M1b) -----------------------------------------------------
+ * A body of a rotating domain turns its shapes with it: at step index n body k has turned
+ * by theta = omega_k n (counter-clockwise, the sense of U_O = omega z x (x - c)) about its
+ * centre, which moves as c_k + V_k n. A shape whose reference point (circle centre, NACA
+ * quarter chord) is offset by d from the body's reference centre sits at c_k + V_k n + R d,
+ * R the rotation by theta, and a NACA section's angle of attack (nose up) decreases by
+ * theta: (cos, sin) of aoa - theta by the angle-difference rule from cos aoa, sin aoa.
+ *
+ * sin and cos are written out in FP64, so that the placement does not depend on a math
+ * library: the argument is reduced by multiples k of pi/2 (Cody and Waite, with pi/2 split
+ * in three parts, the first two of 30 significant bits, so that k times them is exact for
+ * |k| < 2^23, i.e. |theta| < 1.3e7), then sin r and cos r on [-pi/4, pi/4] are the Taylor
+ * series to the terms in r^17 and r^16 (truncation below 1e-17), evaluated by Horner's
+ * rule in r^2; the quadrant k mod 4 selects signs and roles. */
+void ora_sincos(double t, double *s, double *c) {
+  const double P1 = 0x1.921fb54p+0, P2 = 0x1.10b46118p-30, P3 = 0x1.313198a2e037p-61;
+  const double k = nearbyint(t * 0x1.45f306dc9c883p-1); /* t 2/pi, to nearest */
+  const double r = ((t - k * P1) - k * P2) - k * P3;
+  const double r2 = r * r;
+  double ps = -1.0 / 1307674368000.0 + r2 * (1.0 / 355687428096000.0); /* -1/15!, 1/17! */
+  ps = 1.0 / 6227020800.0 + r2 * ps;                                     /* 1/13! */
+  ps = -1.0 / 39916800.0 + r2 * ps;                                      /* -1/11! */
+  ps = 1.0 / 362880.0 + r2 * ps;                                         /* 1/9! */
+  ps = -1.0 / 5040.0 + r2 * ps;                                          /* -1/7! */
+  ps = 1.0 / 120.0 + r2 * ps;                                            /* 1/5! */
+  ps = -1.0 / 6.0 + r2 * ps;                                             /* -1/3! */
+  const double sr = r + (r * r2) * ps;
+  double pc = -1.0 / 87178291200.0 + r2 * (1.0 / 20922789888000.0);     /* -1/14!, 1/16! */
+  pc = 1.0 / 479001600.0 + r2 * pc;                                      /* 1/12! */
+  pc = -1.0 / 3628800.0 + r2 * pc;                                       /* -1/10! */
+  pc = 1.0 / 40320.0 + r2 * pc;                                          /* 1/8! */
+  pc = -1.0 / 720.0 + r2 * pc;                                           /* -1/6! */
+  pc = 1.0 / 24.0 + r2 * pc;                                             /* 1/4! */
+  pc = -0.5 + r2 * pc;                                                   /* -1/2! */
+  const double cr = 1.0 + r2 * pc;
+  switch ((int)((int64_t)k & 3)) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+  }
+}
+
+typedef struct {
+  ora_shape s;
+  double ca, sa; /* cos, sin of the NACA angle of attack */
+} placed_shape;
+
+/* shape s0 of a rotating domain at step index n */
+static void shape_rot_at(const ora_shape *s0, const ora_body *bodies, int32_t nbodies, int64_t n,
+                         placed_shape *out) {
+  out->s = *s0;
+  out->ca = cos(s0->aoa_rad);
+  out->sa = sin(s0->aoa_rad);
+  if (s0->body < 1 || s0->body > nbodies) return;
+  const ora_body *b = &bodies[s0->body - 1];
+  double sn, cs;
+  ora_sincos(b->omega * (double)n, &sn, &cs);
+  const double dx = s0->cx - b->cx, dy = s0->cy - b->cy;
+  const double rx = cs * dx - sn * dy, ry = sn * dx + cs * dy;
+  out->s.cx = (b->cx + b->vx * (double)n) + rx;
+  out->s.cy = (b->cy + b->vy * (double)n) + ry;
+  const double ca = out->ca, sa = out->sa;
+  out->ca = ca * cs + sa * sn; /* cos(aoa - theta) */
+  out->sa = sa * cs - ca * sn; /* sin(aoa - theta) */
+}
+
+/* The mask of a rotating domain at step index n. */
+void ora_rasterize_rot(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
+                       const ora_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
+  placed_shape *ps = (placed_shape *)malloc(sizeof(placed_shape) * (nshapes > 0 ? nshapes : 1));
+  if (!ps) abort();
+  for (int k = 0; k < nshapes; k++) shape_rot_at(&shapes[k], bodies, nbodies, n, &ps[k]);
+  for (int j = 0; j < ny; j++)
+    for (int i = 0; i < nx; i++) {
+      uint8_t b = 0;
+      for (int k = 0; k < nshapes; k++)
+        if (inside_shape_cs(&ps[k].s, ps[k].ca, ps[k].sa, (double)i, (double)j)) b = (uint8_t)ps[k].s.body;
+      mask[(size_t)j * nx + i] = b;
+    }
+  free(ps);
 }
 
 /* The mask at step index n (shapes translated with their bodies). */
@@ -348,12 +436,13 @@ int ora_run(const ora_params *p, const uint8_t *mask, const ora_body *bodies,
   return 0;
 }
 
-/* Run n steps of a domain whose bodies move (prescribed translation), starting at step
- * index n0: before step n0 + s the mask is rasterised at that index and the bodies'
- * centres are moved there. Arguments as ora_run, plus the shapes. */
-int ora_run_moving(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
-                   const ora_body *bodies, int32_t nbodies, double *g, int64_t n0, int64_t n,
-                   double *forces, int32_t srt) {
+/* Run n steps of a domain whose bodies move (prescribed translation; with rotate, also
+ * rotation of their shapes), starting at step index n0: before step n0 + s the mask is
+ * rasterised at that index and the bodies' centres are moved there. Arguments as ora_run,
+ * plus the shapes. */
+int ora_run_moving_mode(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
+                        const ora_body *bodies, int32_t nbodies, double *g, int64_t n0, int64_t n,
+                        double *forces, int32_t srt, int32_t rotate) {
   size_t cells = (size_t)p->nx * p->ny;
   double *tmp = (double *)malloc(sizeof(double) * Q * cells);
   double *fb = (double *)malloc(sizeof(double) * 2 * (nbodies > 0 ? nbodies : 1));
@@ -363,7 +452,8 @@ int ora_run_moving(const ora_params *p, const ora_shape *shapes, int32_t nshapes
   double *a = g, *b = tmp;
   for (int64_t s = 0; s < n; s++) {
     const int64_t m = n0 + s;
-    ora_rasterize_at(p->nx, p->ny, shapes, nshapes, bodies, nbodies, m, mask);
+    if (rotate) ora_rasterize_rot(p->nx, p->ny, shapes, nshapes, bodies, nbodies, m, mask);
+    else ora_rasterize_at(p->nx, p->ny, shapes, nshapes, bodies, nbodies, m, mask);
     for (int k = 0; k < nbodies; k++) body_at(&bodies[k], m, &moved[k]);
     if (srt) ora_step_srt(p, mask, moved, nbodies, a, b, fb);
     else ora_step_trt(p, mask, moved, nbodies, a, b, fb);
@@ -373,6 +463,12 @@ int ora_run_moving(const ora_params *p, const ora_shape *shapes, int32_t nshapes
   if (a != g) memcpy(g, a, sizeof(double) * Q * cells);
   free(tmp); free(fb); free(mask); free(moved);
   return 0;
+}
+
+int ora_run_moving(const ora_params *p, const ora_shape *shapes, int32_t nshapes,
+                   const ora_body *bodies, int32_t nbodies, double *g, int64_t n0, int64_t n,
+                   double *forces, int32_t srt) {
+  return ora_run_moving_mode(p, shapes, nshapes, bodies, nbodies, g, n0, n, forces, srt, 0);
 }
 
 /* The bodies of a moving domain at step index n (centres translated). */

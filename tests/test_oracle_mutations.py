@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import test_oracle_fsi_pins as fsi_pins
+import test_oracle_rotation_pins as rot_pins
 import test_oracle_pins as pins
 import synth
 
@@ -49,6 +50,17 @@ MUTATIONS = [
     ("fsi_shape_not_moved", "sh[q].cy = shapes[q].cy + (state[6 * k + 1] - bodies[k].cy);",
      "sh[q].cy = shapes[q].cy;"),
     ("fsi_initial_velocity_for_U_O", "now[k].vy = state[6 * k + 3];", "now[k].vy = bodies[k].vy;"),
+    # rotating obstacles and the oracle's own sin / cos
+    ("rot_aoa_sign", "out->sa = sa * cs - ca * sn;", "out->sa = sa * cs + ca * sn;"),
+    ("rot_matrix_transposed", "const double rx = cs * dx - sn * dy, ry = sn * dx + cs * dy;",
+     "const double rx = cs * dx + sn * dy, ry = cs * dy - sn * dx;"),
+    ("rot_offset_fixed", "const double rx = cs * dx - sn * dy, ry = sn * dx + cs * dy;",
+     "const double rx = dx, ry = dy;"),
+    ("rot_step_index", "ora_sincos(b->omega * (double)n, &sn, &cs);", "ora_sincos(b->omega * (double)(n + 1), &sn, &cs);"),
+    ("rot_centre_not_translated", "out->s.cx = (b->cx + b->vx * (double)n) + rx;", "out->s.cx = b->cx + rx;"),
+    ("sincos_quadrant", "case 1: *s = cr; *c = -sr; break;", "case 1: *s = cr; *c = sr; break;"),
+    ("sincos_coefficient", "ps = 1.0 / 120.0 + r2 * ps;", "ps = 1.0 / 100.0 + r2 * ps;"),
+    ("sincos_reduction_tail", "((t - k * P1) - k * P2) - k * P3;", "(t - k * P1) - k * P2;"),
 ]
 
 # Pins in order of cost; each mutation stops at the first one that fails.
@@ -61,6 +73,11 @@ PINS = [
     fsi_pins.test_fluid_damps_a_spring_mounted_body,
     fsi_pins.test_fluid_moves_with_the_body_at_its_current_position,
     fsi_pins.test_free_body_in_a_stream_is_dragged_downstream,
+    rot_pins.test_sincos_against_the_c_library,
+    rot_pins.test_turned_mask_is_the_brute_force_mask,
+    rot_pins.test_zero_rotation_is_translation_bit_for_bit,
+    rot_pins.test_half_turn_of_a_symmetric_section,
+    lambda: rot_pins.test_turning_bodies_conserve_mass_and_balance_momentum(3 / 16),
     lambda: pins.test_equilibrium_moments(0.97, 0.05, -0.03),
     lambda: pins.test_guo_term_moments(0.04, -0.02, -3e-4, 7e-4),
     pins.test_gauss_circle_counts,
