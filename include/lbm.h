@@ -121,8 +121,16 @@ typedef struct {
   int32_t moving;         /* 1: the bodies move (prescribed translation): at step index n
                            * body k is centred at c_k + V_k n and its shapes are translated
                            * by V_k n (chi(x, t), U_O(x, t) of Sec. 2.2; rotation acts through
-                           * U_O only). Needs device geometry (no host mask), at most 64
-                           * shapes and 8 bodies. 0: fixed mask. */
+                           * U_O only). 2: the bodies also turn their shapes: body k has
+                           * turned by theta = omega_k n about its centre c_k + V_k n, a shape
+                           * whose reference point (circle centre, NACA quarter chord) is
+                           * offset by d from c_k sits at c_k + V_k n + R(theta) d, and a NACA
+                           * section's angle of attack is aoa - theta; sin and cos of theta are
+                           * evaluated in FP64 by a fixed sequence of rounded operations
+                           * (reduction by pi/2 split in three parts, Taylor series to r^17),
+                           * within 2 ulp of the exact values for |theta| < 1.3e7. Coupled
+                           * bodies need moving = 1. Needs device geometry (no host mask), at
+                           * most 64 shapes and 8 bodies. 0: fixed mask. */
   int32_t x_origin;       /* global column of local column 0: a domain that is one slab of
                            * a larger grid rasterises its shapes and evaluates U_O at the
                            * global position (i + x_origin, j), so slabs reproduce the
@@ -381,7 +389,7 @@ typedef struct {
   int32_t force_every;      /* record body forces every k-th step (0: never) */
   int32_t force_capacity;   /* force-ring entries kept on the device (0: 8192) */
   int32_t lattice;          /* 19 (or 0): D3Q19; 15: D3Q15 */
-  int32_t moving;           /* 1: bodies translate with their velocities (at most 8 bodies,
+  int32_t moving;           /* 0 or 1: bodies translate with their velocities (at most 8 bodies,
                                64 shapes, |V| <= 1 per axis): body k is centred at
                                c_k + V_k n at step index n, its shapes translated by V_k n,
                                the mask recomputed after every step; positions are not

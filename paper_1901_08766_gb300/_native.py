@@ -75,6 +75,15 @@ def dynamics3_from(d) -> BodyDynamics3:
                          (C.c_int32 * 3)(*[int(v) for v in d["free"]]))
 
 
+def moving_mode(spec) -> int:
+    """0 fixed, 1 translating bodies ("moving": True), 2 bodies that also turn their shapes
+    ("moving": 2)."""
+    m = spec.get("moving", False)
+    if isinstance(m, bool) or m in (0, 1):
+        return 1 if m else 0
+    return int(m)
+
+
 class Params3(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nu", C.c_double),
                 ("tau_plus", C.c_double), ("magic_lambda", C.c_double), ("eta", C.c_double),
@@ -212,7 +221,7 @@ def params_from_spec(spec, storage: str, force_every: int = 1, force_capacity: i
     return Params(spec["nx"], spec["ny"], spec["nu"], 0.0, spec["magic_lambda"], spec["eta"],
                   spec["rho0"], spec["u_in"][0], spec["u_in"][1], spec["u0"][0], spec["u0"][1],
                   EDGE[e["west"]], EDGE[e["east"]], EDGE[e["south"]], EDGE[e["north"]],
-                  STORAGE[storage], force_every, force_capacity, 1 if spec.get("moving") else 0,
+                  STORAGE[storage], force_every, force_capacity, moving_mode(spec),
                   int(spec.get("x_origin", 0)))
 
 
@@ -242,7 +251,7 @@ def params3_from_spec(spec, storage: str, force_every: int = 1,
                    (C.c_double * 3)(*spec["u0"]), EDGE[e["west"]], EDGE[e["east"]],
                    EDGE[e["south"]], EDGE[e["north"]], EDGE[e["bottom"]], EDGE[e["top"]],
                    STORAGE[storage], force_every, force_capacity, int(spec.get("lattice", 19)),
-                   1 if spec.get("moving") else 0)
+                   moving_mode(spec))
 
 
 def bodies3_from_spec(spec):

@@ -99,7 +99,7 @@ struct Dom3 {
   const double *centre0;           // [nbodies][3] reference centres
   float mbox[8][3];                // per body: half extents of the box its shapes reach
                                    // about its centre (< 0: the whole axis)
-  double *mpart;                   // [8][kMoveBlocks3][3] partial force sums
+  double *mpart;                   // [8][kMaxMoveBlocks3][3] partial force sums
   uint32_t *mcount;                // [8] blocks of the moving force reduction finished
   // coupled bodies (null / zero otherwise): state [2][8][9] by step parity (x, v and the
   // previous step's force), parameters [8][12] (M, k[3], c[3], free[3]); bit b of
@@ -762,19 +762,20 @@ __device__ __forceinline__ void fsi3_axis(double F, double Fp, double k, double 
   x = __dadd_rn(x, v);
 }
 
-constexpr int kMoveBlocks3 = 64;   // blocks per body of the moving-domain kernels
+constexpr int kMaxMoveBlocks3 = 256;  // blocks per body of the moving-domain kernels, at most
 constexpr int kMaxShapes3 = 64;    // shapes of a moving 3D domain
 constexpr int kMoveThreads3 = 256;
 
 // Forces of a moving domain at step index n (the sweep just computed step n + 1): per
 // body, the rows of its box at n (where all its nodes of step n lie) split over
-// kMoveBlocks3 blocks, one warp per row, -F_VP of the nodes with its id; each block's sum
+// the launch's blocks (at most kMaxMoveBlocks3, sized to the box), one warp per row, -F_VP of the nodes with its id; each block's sum
 // (fixed tree) goes to a partial slot, and the last block of the body adds the partials
 // in block order into the ring entry and, for a coupled body, advances its state to n + 1
 // from that force. Deterministic: the box depends on the state of index n only.
 template <typename T>
-__global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom, long long n, long long entry) {
-  const Dom3 &D = *dom;
+__global__ void __launch_bounds__(kMoveThreads3)
+mforce3_kernel(const __grid_constant__ Dom3 dom, long long n, long long entry) {
+  const Dom3 &D = dom;  // kernel parameter: no dependent loads of the domain's fields
   const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const Box3 B = body_box3(D, b, n, 0);
   const int ny_b = B.hi[1] - B.lo[1] + 1, nz_b = B.hi[2] - B.lo[2] + 1;
@@ -785,9 +786,16 @@ __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom,
     const size_t row = static_cast<size_t>(k) * D.ny + j;
     const uint8_t *m = D.mask + row * D.pitch;
     const T *fv = static_cast<const T *>(D.fvp) + 3 * row * D.pitch;
-    for (int i = B.lo[0] + lane; i <= B.hi[0]; i += 32)
-      if (m[i] == b + 1)
-        for (int e = 0; e < 3; ++e) f[e] -= double(fv[3 * i + e]);
+    for (int i = B.lo[0] + lane; i <= B.hi[0]; i += 32) {
+      // mask byte and F_VP loaded together (in bounds for every node of the box)
+      const uint8_t id = m[i];
+      const T v0 = fv[3 * i], v1 = fv[3 * i + 1], v2 = fv[3 * i + 2];
+      if (id == b + 1) {
+        f[0] -= double(v0);
+        f[1] -= double(v1);
+        f[2] -= double(v2);
+      }
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
@@ -798,7 +806,7 @@ __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom,
     for (int e = 0; e < 3; ++e) red[e][warp] = f[e];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double *part = D.mpart + (static_cast<size_t>(b) * kMoveBlocks3 + blockIdx.x) * 3;
+    double *part = D.mpart + (static_cast<size_t>(b) * kMaxMoveBlocks3 + blockIdx.x) * 3;
     for (int e = 0; e < 3; ++e) {
       double t = 0.0;
       for (int w = 0; w < kMoveThreads3 / 32; ++w) t += red[e][w];
@@ -813,7 +821,7 @@ __global__ void __launch_bounds__(kMoveThreads3) mforce3_kernel(const Dom3 *dom,
   // the last block: thread q loads partial q (all at once), then a fixed tree over q
   double t[3] = {0.0, 0.0, 0.0};
   if (threadIdx.x < gridDim.x)
-    for (int e = 0; e < 3; ++e) t[e] = __ldcg(D.mpart + (static_cast<size_t>(b) * kMoveBlocks3 + threadIdx.x) * 3 + e);
+    for (int e = 0; e < 3; ++e) t[e] = __ldcg(D.mpart + (static_cast<size_t>(b) * kMaxMoveBlocks3 + threadIdx.x) * 3 + e);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
     for (int e = 0; e < 3; ++e) t[e] += __shfl_down_sync(0xffffffffu, t[e], off);
@@ -871,8 +879,8 @@ __device__ __forceinline__ bool inside3_fast(const Shape3Dev &s, const float (&c
   return inside3(s, i, j, k);
 }
 
-__global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, long long n) {
-  const Dom3 &D = *dom;
+__global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const __grid_constant__ Dom3 dom, long long n) {
+  const Dom3 &D = dom;
   const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // every shape at n + 1, translated once per block (FP64, explicit roundings)
   __shared__ Shape3Dev sh[kMaxShapes3];
@@ -918,8 +926,8 @@ __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const Dom3 *dom, 
 constexpr int kRowsThreads = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const Dom3 *dom, long long entry) {
-  const Dom3 &D = *dom;
+__global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const __grid_constant__ Dom3 dom, long long entry) {
+  const Dom3 &D = dom;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int q = wg; q < D.nfrows; q += nw) {
@@ -929,9 +937,15 @@ __global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const Dom3 *dom, lo
     const T *fv = static_cast<const T *>(D.fvp) + 3 * row * D.pitch;
     for (int body = 1; body <= D.nbodies; ++body) {
       double f[3] = {0.0, 0.0, 0.0};
-      for (int i = it.y + lane; i < it.z; i += 32)
-        if (m[i] == body)
-          for (int e = 0; e < 3; ++e) f[e] -= double(fv[3 * i + e]);
+      for (int i = it.y + lane; i < it.z; i += 32) {
+        const uint8_t id = m[i];  // mask byte and F_VP loaded together
+        const T v0 = fv[3 * i], v1 = fv[3 * i + 1], v2 = fv[3 * i + 2];
+        if (id == body) {
+          f[0] -= double(v0);
+          f[1] -= double(v1);
+          f[2] -= double(v2);
+        }
+      }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1)
         for (int e = 0; e < 3; ++e) f[e] += __shfl_down_sync(0xffffffffu, f[e], off);
@@ -949,7 +963,19 @@ __global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const Dom3 *dom, lo
   __threadfence();
   for (int body = 1; body <= D.nbodies; ++body) {
     double f[3] = {0.0, 0.0, 0.0};
-    for (int q = threadIdx.x; q < D.nfrows; q += blockDim.x)
+    int q = threadIdx.x;
+    // four rows' sums loaded at once, added in row order (the order of the plain loop)
+    for (; q + 3 * static_cast<int>(blockDim.x) < D.nfrows; q += 4 * blockDim.x) {
+      double v[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        for (int e = 0; e < 3; ++e)
+          v[u][e] = __ldcg(D.rowsum + (static_cast<size_t>(q + u * blockDim.x) * D.nbodies + body - 1) * 3 + e);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        for (int e = 0; e < 3; ++e) f[e] += v[u][e];
+    }
+    for (; q < D.nfrows; q += blockDim.x)
       for (int e = 0; e < 3; ++e) f[e] += __ldcg(D.rowsum + (static_cast<size_t>(q) * D.nbodies + body - 1) * 3 + e);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -1022,7 +1048,7 @@ struct Layout3 {
 // coupled-body state by parity and parameters
 size_t moving_bytes3() {
   return up(sizeof(Shape3Dev) * kMaxShapes3, 256) + up(sizeof(double) * 3 * kMaxMoving3, 256) +
-         up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256) +
+         up(sizeof(double) * 3 * kMaxMoving3 * kMaxMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256) +
          up(sizeof(double) * 9 * 2 * kMaxMoving3, 256) + up(sizeof(double) * 12 * kMaxMoving3, 256);
 }
 
@@ -1090,6 +1116,7 @@ struct lbm3_domain {
   int parity = 0;
   int grid = 0;      // sweep blocks
   int aux_grid = 0;  // force-row reduction blocks
+  int move_blocks = 0;  // blocks per body of the moving-domain kernels
   void *get(size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (afn) return afn(bytes, actx);
@@ -1133,23 +1160,23 @@ cudaError_t launch_forces3(lbm3_domain *d, long long n) {
   if (d->p.force_every <= 0 || (n + 1) % d->p.force_every != 0 || d->nbodies == 0) return cudaSuccess;
   const long long entry = (n + 1) / d->p.force_every - 1;
   if (d->p.moving) {
-    const dim3 g(kMoveBlocks3, d->nbodies);
-    if (d->p.storage == LBM_F64) mforce3_kernel<double><<<g, kMoveThreads3, 0, d->st>>>(d->d_dom, n, entry);
-    else mforce3_kernel<float><<<g, kMoveThreads3, 0, d->st>>>(d->d_dom, n, entry);
+    const dim3 g(d->move_blocks, d->nbodies);
+    if (d->p.storage == LBM_F64) mforce3_kernel<double><<<g, kMoveThreads3, 0, d->st>>>(d->h, n, entry);
+    else mforce3_kernel<float><<<g, kMoveThreads3, 0, d->st>>>(d->h, n, entry);
     return cudaGetLastError();
   }
   if (d->h.nfrows == 0)
     return cudaMemsetAsync(d->h.ring + (entry % d->h.force_cap) * d->nbodies * 3, 0,
                            sizeof(double) * 3 * d->nbodies, d->st);
-  if (d->p.storage == LBM_F64) rows3_kernel<double><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->d_dom, entry);
-  else rows3_kernel<float><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->d_dom, entry);
+  if (d->p.storage == LBM_F64) rows3_kernel<double><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->h, entry);
+  else rows3_kernel<float><<<d->aux_grid, kRowsThreads, 0, d->st>>>(d->h, entry);
   return cudaGetLastError();
 }
 
 // a moving domain's geometry for the next step (after the forces of step n)
 cudaError_t launch_move3(lbm3_domain *d, long long n) {
   if (!d->p.moving || d->nbodies == 0) return cudaSuccess;
-  mmove3_kernel<<<dim3(kMoveBlocks3, d->nbodies), kMoveThreads3, 0, d->st>>>(d->d_dom, n);
+  mmove3_kernel<<<dim3(d->move_blocks, d->nbodies), kMoveThreads3, 0, d->st>>>(d->h, n);
   return cudaGetLastError();
 }
 
@@ -1402,7 +1429,7 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
     D.centre0 = reinterpret_cast<const double *>(mb);
     mb += up(sizeof(double) * 3 * kMaxMoving3, 256);
     D.mpart = reinterpret_cast<double *>(mb);
-    mb += up(sizeof(double) * 3 * kMaxMoving3 * kMoveBlocks3, 256);
+    mb += up(sizeof(double) * 3 * kMaxMoving3 * kMaxMoveBlocks3, 256);
     D.mcount = reinterpret_cast<uint32_t *>(mb);
     mb += up(sizeof(uint32_t) * kMaxMoving3, 256);
     D.fsi = reinterpret_cast<double *>(mb);
@@ -1495,6 +1522,10 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
   d->grid = sweep3_blocks(nq, p->storage, sms);
   // force reduction: one warp per listed row, at most one block per SM
   d->aux_grid = std::max(1, std::min(sms, (D.nfrows + kRowsThreads / 32 - 1) / (kRowsThreads / 32)));
+  // moving domains: 64 blocks per body (one row per warp for boxes of up to 512 rows; 211
+  // blocks for the 41 x 41 rows of a D = 32 sphere measured slower)
+  d->move_blocks = 64;
+  static_assert(kMaxMoveBlocks3 <= kMoveThreads3, "the last block loads one partial per thread");
   *out = d;
   return LBM_OK;
 }

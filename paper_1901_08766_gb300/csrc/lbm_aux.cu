@@ -95,8 +95,64 @@ __device__ __forceinline__ ShapeDev shape_about(const DomDev &D, const ShapeDev 
   return s;
 }
 
+// sin t and cos t in FP64 with explicitly rounded operations, so that a turned shape is
+// placed by the same operations on every device and on the host: t is reduced by
+// k = rint(2 t / pi) multiples of pi/2 (Cody and Waite's reduction, pi/2 split in three
+// parts whose first two have 30 significant bits: k times them is exact for |k| < 2^23),
+// then sin r and cos r on [-pi/4, pi/4] are their Taylor series to r^17 and r^16 by
+// Horner's rule in r^2, and k mod 4 picks signs and roles.
+__device__ __forceinline__ void turn_sincos(double t, double &sn, double &cs) {
+  constexpr double P1 = 0x1.921fb54p+0, P2 = 0x1.10b46118p-30, P3 = 0x1.313198a2e037p-61;
+  const double k = rint(__dmul_rn(t, 0x1.45f306dc9c883p-1));
+  const double r = __dsub_rn(__dsub_rn(__dsub_rn(t, __dmul_rn(k, P1)), __dmul_rn(k, P2)), __dmul_rn(k, P3));
+  const double r2 = __dmul_rn(r, r);
+  double ps = __dadd_rn(-1.0 / 1307674368000.0, __dmul_rn(r2, 1.0 / 355687428096000.0));
+  ps = __dadd_rn(1.0 / 6227020800.0, __dmul_rn(r2, ps));
+  ps = __dadd_rn(-1.0 / 39916800.0, __dmul_rn(r2, ps));
+  ps = __dadd_rn(1.0 / 362880.0, __dmul_rn(r2, ps));
+  ps = __dadd_rn(-1.0 / 5040.0, __dmul_rn(r2, ps));
+  ps = __dadd_rn(1.0 / 120.0, __dmul_rn(r2, ps));
+  ps = __dadd_rn(-1.0 / 6.0, __dmul_rn(r2, ps));
+  const double sr = __dadd_rn(r, __dmul_rn(__dmul_rn(r, r2), ps));
+  double pc = __dadd_rn(-1.0 / 87178291200.0, __dmul_rn(r2, 1.0 / 20922789888000.0));
+  pc = __dadd_rn(1.0 / 479001600.0, __dmul_rn(r2, pc));
+  pc = __dadd_rn(-1.0 / 3628800.0, __dmul_rn(r2, pc));
+  pc = __dadd_rn(1.0 / 40320.0, __dmul_rn(r2, pc));
+  pc = __dadd_rn(-1.0 / 720.0, __dmul_rn(r2, pc));
+  pc = __dadd_rn(1.0 / 24.0, __dmul_rn(r2, pc));
+  pc = __dadd_rn(-0.5, __dmul_rn(r2, pc));
+  const double cr = __dadd_rn(1.0, __dmul_rn(r2, pc));
+  switch (static_cast<int>(static_cast<long long>(k) & 3)) {
+    case 0: sn = sr; cs = cr; break;
+    case 1: sn = cr; cs = -sr; break;
+    case 2: sn = -sr; cs = -cr; break;
+    default: sn = -cr; cs = sr; break;
+  }
+}
+
+// A rotating domain (moving = 2) turns body b's shapes by theta = omega n about its
+// centre c0 + V n: the reference point offset d from c0 goes to R(theta) d, a NACA
+// section's (cos, sin) of its angle of attack to those of aoa - theta.
+__device__ __forceinline__ ShapeDev shape_turned(const DomDev &D, const ShapeDev &s0, long long n) {
+  ShapeDev s = s0;
+  const int b = s0.body - 1;
+  const double *bt = D.bodies + 5 * b;  // vx, vy at 2, 3; omega at 4 (constant)
+  double sn, cs;
+  turn_sincos(__dmul_rn(bt[4], static_cast<double>(n)), sn, cs);
+  const double c0x = D.centre0[2 * b], c0y = D.centre0[2 * b + 1];
+  const double dx = __dsub_rn(s0.cx, c0x), dy = __dsub_rn(s0.cy, c0y);
+  const double rx = __dsub_rn(__dmul_rn(cs, dx), __dmul_rn(sn, dy));
+  const double ry = __dadd_rn(__dmul_rn(sn, dx), __dmul_rn(cs, dy));
+  s.cx = __dadd_rn(moved(c0x, bt[2], n), rx);
+  s.cy = __dadd_rn(moved(c0y, bt[3], n), ry);
+  s.ca = __dadd_rn(__dmul_rn(s0.ca, cs), __dmul_rn(s0.sa, sn));
+  s.sa = __dsub_rn(__dmul_rn(s0.sa, cs), __dmul_rn(s0.ca, sn));
+  return s;
+}
+
 __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n) {
   ShapeDev s = s0;
+  if (D.moving == 2 && s0.body >= 1 && s0.body <= D.nbodies) return shape_turned(D, s0, n);
   if (coupled(D, s0.body)) {
     const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + (s0.body - 1)) * 6;
     return shape_about(D, s0, st[0], st[1]);
@@ -141,11 +197,20 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
   lo = 0;
   hi = D.nx - 1;
   if (s0.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
-  float cx, cy;
+  float cx, cy, turn = 0.f;
   if (coupled(D, s0.body)) {
     const ShapeDev s = shape_at(D, s0, n);
     cx = float(s.cx - double(D.x0));
     cy = float(s.cy);
+  } else if (D.moving == 2 && s0.body >= 1 && s0.body <= D.nbodies) {
+    // a turning shape stays within its offset from the body centre: cull about the centre
+    // with the reach grown by that offset (no trigonometry here)
+    const int b = s0.body - 1;
+    const float fn = float(n);
+    cx = (float(D.centre0[2 * b]) - float(D.x0)) + float(D.bodies[5 * b + 2]) * fn;
+    cy = float(D.centre0[2 * b + 1]) + float(D.bodies[5 * b + 3]) * fn;
+    const float ox = float(s0.cx - D.centre0[2 * b]), oy = float(s0.cy - D.centre0[2 * b + 1]);
+    turn = sqrtf(ox * ox + oy * oy) + 0.01f;
   } else {
     float vx = 0.f, vy = 0.f;
     if (s0.body >= 1 && s0.body <= D.nbodies) {
@@ -156,7 +221,7 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
     cx = (float(s0.cx) - float(D.x0)) + vx * fn;
     cy = float(s0.cy) + vy * fn;
   }
-  const float reach = float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 2.0f;
+  const float reach = float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 2.0f + turn;
   if (!(fabsf(float(j) - cy) <= reach)) {
     lo = 1;
     hi = 0;

@@ -142,7 +142,7 @@ lbm_status validate(const lbm_params *p, int nbodies) {
   if ((p->south == LBM_PERIODIC) != (p->north == LBM_PERIODIC)) return fail(LBM_EINVAL, "y edges: both periodic or neither");
   if (nbodies < 0 || nbodies > kMaxBodies) return fail(LBM_EINVAL, "nbodies must be in [0, 255]");
   if (p->force_every < 0 || p->force_capacity < 0) return fail(LBM_EINVAL, "force_every/capacity must be >= 0");
-  if (p->moving != 0 && p->moving != 1) return fail(LBM_EINVAL, "moving must be 0 or 1");
+  if (p->moving < 0 || p->moving > 2) return fail(LBM_EINVAL, "moving must be 0, 1 or 2");
   if ((p->storage == LBM_F16S || p->storage == LBM_BF16S) && p->x_origin % 8 != 0)
     return fail(LBM_EINVAL, "16-bit storage needs x_origin divisible by 8 (rounding bits are keyed by 8-column groups)");
   if (p->moving && nbodies > kMaxMovingBodies)
@@ -1128,6 +1128,7 @@ lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, cons
   Slot &s = b->slots[slot];
   if (!dyn) return fail(LBM_EINVAL, "dynamics is NULL");
   if (!s.p.moving) return fail(LBM_EINVAL, "coupled bodies need a moving domain");
+  if (s.p.moving == 2) return fail(LBM_EINVAL, "coupled bodies do not turn their shapes (moving = 2)");
   if (s.p.force_every != 1) return fail(LBM_EINVAL, "coupled bodies need the force of every step (force_every = 1)");
   if (s.done != 0) return fail(LBM_EINVAL, "dynamics are set before the first step");
   if (s.link_west >= 0 || s.link_east >= 0) return fail(LBM_EINVAL, "a linked domain cannot have coupled bodies");
