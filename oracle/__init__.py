@@ -44,7 +44,9 @@ class _Params(C.Structure):
 
 class _Body(C.Structure):
     _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("vx", C.c_double),
-                ("vy", C.c_double), ("omega", C.c_double)]
+                ("vy", C.c_double), ("omega", C.c_double), ("amp", C.c_double),
+                ("rate", C.c_double), ("kappa", C.c_double), ("deform", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class _Dynamics(C.Structure):
@@ -144,7 +146,10 @@ def _bodies_of(spec):
     bs = spec["bodies"]
     arr = (_Body * max(1, len(bs)))()
     for k, b in enumerate(bs):
-        arr[k] = _Body(b["cx"], b["cy"], b["vx"], b["vy"], b["omega"])
+        d = b.get("deform")
+        arr[k] = _Body(b["cx"], b["cy"], b["vx"], b["vy"], b["omega"],
+                       float(d["amplitude"]) if d else 0.0, float(d["rate"]) if d else 0.0, 0.0,
+                       1 if d else 0, 0)
     return arr, len(bs)
 
 
@@ -245,6 +250,11 @@ class Domain:
             raise ValueError("bodies with dynamics need a moving domain")
         if self.fsi and self.rotating:
             raise ValueError("coupled bodies do not turn their shapes (rotating domain)")
+        deforming = any(b.get("deform") for b in spec["bodies"])
+        if deforming and not self.moving:
+            raise ValueError("deforming bodies need a moving domain")
+        if deforming and self.fsi:
+            raise ValueError("coupled bodies do not deform")
         # (x, y, vx, vy, Fx, Fy) of every body at the current step index (used by coupled
         # bodies; F is the force of the previous step, zero before the first)
         self.state = np.array([[b["cx"], b["cy"], b["vx"], b["vy"], 0.0, 0.0] for b in spec["bodies"]],

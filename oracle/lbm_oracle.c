@@ -54,6 +54,10 @@ typedef struct {
 
 typedef struct {
   double cx, cy, vx, vy, omega;
+  /* a deforming body (deform = 1) pulsates: scale s(n) = 1 + amp sin(rate n) about its
+   * centre; kappa = s'(n) / s(n) is its dilation rate at the step being taken */
+  double amp, rate, kappa;
+  int32_t deform, pad;
 } ora_body;
 
 typedef struct {
@@ -155,10 +159,27 @@ static void shape_at(const ora_shape *s0, const ora_body *bodies, int32_t nbodie
   }
 }
 
+void ora_sincos(double t, double *s, double *c);
+
+/* ---- deforming obstacles (reading M1c) ----------------------------------------------------
+ * A deforming body pulsates about its centre: at step index n its shapes are scaled by
+ * s(n) = 1 + amp sin(rate n) (|amp| < 1): radii and chords by s(n), a shape's offset d from
+ * the body centre to s(n) d (after the rotation of a rotating domain). Its material
+ * velocity adds the dilation kappa(n) (x - c), kappa(n) = s'(n) / s(n) =
+ * amp rate cos(rate n) / s(n), to U_O. */
+static double deform_scale(const ora_body *b0, int64_t n, double *kappa) {
+  double sn, cs;
+  ora_sincos(b0->rate * (double)n, &sn, &cs);
+  const double sc = 1.0 + b0->amp * sn;
+  if (kappa) *kappa = ((b0->amp * b0->rate) * cs) / sc;
+  return sc;
+}
+
 static void body_at(const ora_body *b0, int64_t n, ora_body *b) {
   *b = *b0;
   b->cx = b0->cx + b0->vx * (double)n;
   b->cy = b0->cy + b0->vy * (double)n;
+  if (b0->deform) deform_scale(b0, n, &b->kappa);
 }
 
 /* ---- rotating obstacles (reading M1b) -----------------------------------------------------
@@ -209,31 +230,54 @@ typedef struct {
   double ca, sa; /* cos, sin of the NACA angle of attack */
 } placed_shape;
 
-/* shape s0 of a rotating domain at step index n */
+/* shape s0 at step index n of a body that turns (rotate: a rotating domain) or deforms:
+ * reference point at c + V n + s(n) R(theta) d */
 static void shape_rot_at(const ora_shape *s0, const ora_body *bodies, int32_t nbodies, int64_t n,
-                         placed_shape *out) {
+                         int32_t rotate, placed_shape *out) {
   out->s = *s0;
   out->ca = cos(s0->aoa_rad);
   out->sa = sin(s0->aoa_rad);
   if (s0->body < 1 || s0->body > nbodies) return;
   const ora_body *b = &bodies[s0->body - 1];
-  double sn, cs;
-  ora_sincos(b->omega * (double)n, &sn, &cs);
   const double dx = s0->cx - b->cx, dy = s0->cy - b->cy;
-  const double rx = cs * dx - sn * dy, ry = sn * dx + cs * dy;
+  double rx = dx, ry = dy;
+  if (rotate) {
+    double sn, cs;
+    ora_sincos(b->omega * (double)n, &sn, &cs);
+    rx = cs * dx - sn * dy;
+    ry = sn * dx + cs * dy;
+    const double ca = out->ca, sa = out->sa;
+    out->ca = ca * cs + sa * sn; /* cos(aoa - theta) */
+    out->sa = sa * cs - ca * sn; /* sin(aoa - theta) */
+  }
+  if (b->deform) {
+    const double sc = deform_scale(b, n, NULL);
+    rx = sc * rx;
+    ry = sc * ry;
+    out->s.radius = sc * s0->radius;
+    out->s.chord = sc * s0->chord;
+  }
   out->s.cx = (b->cx + b->vx * (double)n) + rx;
   out->s.cy = (b->cy + b->vy * (double)n) + ry;
-  const double ca = out->ca, sa = out->sa;
-  out->ca = ca * cs + sa * sn; /* cos(aoa - theta) */
-  out->sa = sa * cs - ca * sn; /* sin(aoa - theta) */
 }
 
-/* The mask of a rotating domain at step index n. */
-void ora_rasterize_rot(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
-                       const ora_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
+/* The mask of a rotating (rotate = 1) or translating domain with deforming bodies at step
+ * index n. */
+static void rasterize_placed(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
+                             const ora_body *bodies, int32_t nbodies, int64_t n, int32_t rotate,
+                             uint8_t *mask) {
   placed_shape *ps = (placed_shape *)malloc(sizeof(placed_shape) * (nshapes > 0 ? nshapes : 1));
   if (!ps) abort();
-  for (int k = 0; k < nshapes; k++) shape_rot_at(&shapes[k], bodies, nbodies, n, &ps[k]);
+  for (int k = 0; k < nshapes; k++) {
+    const int b = shapes[k].body;
+    if (rotate || (b >= 1 && b <= nbodies && bodies[b - 1].deform)) {
+      shape_rot_at(&shapes[k], bodies, nbodies, n, rotate, &ps[k]);
+    } else {
+      shape_at(&shapes[k], bodies, nbodies, n, &ps[k].s);
+      ps[k].ca = cos(shapes[k].aoa_rad);
+      ps[k].sa = sin(shapes[k].aoa_rad);
+    }
+  }
   for (int j = 0; j < ny; j++)
     for (int i = 0; i < nx; i++) {
       uint8_t b = 0;
@@ -244,9 +288,20 @@ void ora_rasterize_rot(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t 
   free(ps);
 }
 
-/* The mask at step index n (shapes translated with their bodies). */
+void ora_rasterize_rot(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
+                       const ora_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
+  rasterize_placed(nx, ny, shapes, nshapes, bodies, nbodies, n, 1, mask);
+}
+
+/* The mask at step index n (shapes translated with their bodies; those of deforming bodies
+ * also scaled). */
 void ora_rasterize_at(int32_t nx, int32_t ny, const ora_shape *shapes, int32_t nshapes,
                       const ora_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
+  for (int k = 0; k < nbodies; k++)
+    if (bodies[k].deform) {
+      rasterize_placed(nx, ny, shapes, nshapes, bodies, nbodies, n, 0, mask);
+      return;
+    }
   ora_shape *moved = (ora_shape *)malloc(sizeof(ora_shape) * (nshapes > 0 ? nshapes : 1));
   if (!moved) abort();
   for (int k = 0; k < nshapes; k++) shape_at(&shapes[k], bodies, nbodies, n, &moved[k]);
@@ -292,10 +347,15 @@ void ora_stream(const ora_params *p, const double *g, double *f) {
         f[((size_t)a * p->ny + j) * p->nx + i] = pull(p, g, feq_inlet, a, i, j);
 }
 
-/* Obstacle velocity U_O at node (i, j) of body k: V_k + Omega_k z x (x - c_k). */
+/* Obstacle velocity U_O at node (i, j) of body k: V_k + Omega_k z x (x - c_k), plus
+ * kappa_k (x - c_k) for a deforming body (the velocity of its homogeneous dilation). */
 static void body_velocity(const ora_body *b, int i, int j, double *uox, double *uoy) {
   *uox = b->vx - b->omega * ((double)j - b->cy);
   *uoy = b->vy + b->omega * ((double)i - b->cx);
+  if (b->deform) {
+    *uox = *uox + b->kappa * ((double)i - b->cx);
+    *uoy = *uoy + b->kappa * ((double)j - b->cy);
+  }
 }
 
 /* Per-node macroscopic step shared by the TRT and SRT updates: steps (3)-(5) of the

@@ -9,6 +9,7 @@ import warnings
 import pytest
 
 import oracle
+import test_oracle_deform_pins as deform_pins
 import test_oracle_fsi_pins as fsi_pins
 import test_oracle_rotation_pins as rot_pins
 import test_oracle_pins as pins
@@ -61,6 +62,14 @@ MUTATIONS = [
     ("sincos_quadrant", "case 1: *s = cr; *c = -sr; break;", "case 1: *s = cr; *c = sr; break;"),
     ("sincos_coefficient", "ps = 1.0 / 120.0 + r2 * ps;", "ps = 1.0 / 100.0 + r2 * ps;"),
     ("sincos_reduction_tail", "((t - k * P1) - k * P2) - k * P3;", "(t - k * P1) - k * P2;"),
+    # deforming obstacles
+    ("deform_kappa_sign", "*uox = *uox + b->kappa * ((double)i - b->cx);", "*uox = *uox - b->kappa * ((double)i - b->cx);"),
+    ("deform_kappa_axes", "*uoy = *uoy + b->kappa * ((double)j - b->cy);", "*uoy = *uoy + b->kappa * ((double)i - b->cx);"),
+    ("deform_kappa_not_divided", "if (kappa) *kappa = ((b0->amp * b0->rate) * cs) / sc;", "if (kappa) *kappa = (b0->amp * b0->rate) * cs;"),
+    ("deform_scale_cos", "const double sc = 1.0 + b0->amp * sn;", "const double sc = 1.0 + b0->amp * cs;"),
+    ("deform_offset_not_scaled", "    rx = sc * rx;\n    ry = sc * ry;", "    rx = rx;\n    ry = ry;"),
+    ("deform_radius_not_scaled", "out->s.radius = sc * s0->radius;", "out->s.radius = s0->radius;"),
+    ("deform_chord_not_scaled", "out->s.chord = sc * s0->chord;", "out->s.chord = s0->chord;"),
 ]
 
 # Pins in order of cost; each mutation stops at the first one that fails.
@@ -78,6 +87,10 @@ PINS = [
     rot_pins.test_zero_rotation_is_translation_bit_for_bit,
     rot_pins.test_half_turn_of_a_symmetric_section,
     lambda: rot_pins.test_turning_bodies_conserve_mass_and_balance_momentum(3 / 16),
+    lambda: [deform_pins.test_pulsating_mask_is_the_brute_force_mask(m) for m in (True, 2)],
+    deform_pins.test_breathing_circle_area,
+    deform_pins.test_penalized_interior_moves_with_the_dilation,
+    deform_pins.test_zero_amplitude_is_translation_bit_for_bit,
     lambda: pins.test_equilibrium_moments(0.97, 0.05, -0.03),
     lambda: pins.test_guo_term_moments(0.04, -0.02, -3e-4, 7e-4),
     pins.test_gauss_circle_counts,
