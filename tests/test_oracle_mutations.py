@@ -53,10 +53,9 @@ MUTATIONS = [
     ("fsi_initial_velocity_for_U_O", "now[k].vy = state[6 * k + 3];", "now[k].vy = bodies[k].vy;"),
     # rotating obstacles and the oracle's own sin / cos
     ("rot_aoa_sign", "out->sa = sa * cs - ca * sn;", "out->sa = sa * cs + ca * sn;"),
-    ("rot_matrix_transposed", "const double rx = cs * dx - sn * dy, ry = sn * dx + cs * dy;",
-     "const double rx = cs * dx + sn * dy, ry = cs * dy - sn * dx;"),
-    ("rot_offset_fixed", "const double rx = cs * dx - sn * dy, ry = sn * dx + cs * dy;",
-     "const double rx = dx, ry = dy;"),
+    ("rot_matrix_transposed", "rx = cs * dx - sn * dy;\n    ry = sn * dx + cs * dy;",
+     "rx = cs * dx + sn * dy;\n    ry = cs * dy - sn * dx;"),
+    ("rot_offset_fixed", "rx = cs * dx - sn * dy;\n    ry = sn * dx + cs * dy;", "rx = dx;\n    ry = dy;"),
     ("rot_step_index", "ora_sincos(b->omega * (double)n, &sn, &cs);", "ora_sincos(b->omega * (double)(n + 1), &sn, &cs);"),
     ("rot_centre_not_translated", "out->s.cx = (b->cx + b->vx * (double)n) + rx;", "out->s.cx = b->cx + rx;"),
     ("sincos_quadrant", "case 1: *s = cr; *c = -sr; break;", "case 1: *s = cr; *c = sr; break;"),
