@@ -346,6 +346,20 @@ LBM_API lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t bo
                                           const lbm_body_dynamics *dyn);
 LBM_API lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_dynamics *dyn);
 
+/* ---- Deforming obstacles (moving domains) ----------------------------------------------
+ * Sec. 2.2 lets the mask chi and U_O depend on time; here a body of a moving domain may
+ * pulsate about its centre: at step index n its shapes are scaled by
+ *     s(n) = 1 + a sin(nu n),   |a| < 1,
+ * radii and NACA chords by s(n) (the thickness ratio is kept) and each shape's offset d from
+ * the body's reference centre to s(n) d (s(n) R(theta) d in a rotating domain), and U_O at
+ * its nodes adds the velocity of that dilation, kappa(n) (x - c), kappa = s'/s =
+ * a nu cos(nu n) / s(n), in FP64 in that order (sin and cos as for rotating domains). Set
+ * before the first step of a moving slot that is not linked and has no coupled body
+ * (LBM_EINVAL otherwise); it re-places the slot's mask at index 0. Synchronises. */
+LBM_API lbm_status lbm_batch_set_deformation(lbm_batch *b, int32_t slot, int32_t body, double amplitude,
+                                             double rate);
+LBM_API lbm_status lbm_set_deformation(lbm_domain *d, int32_t body, double amplitude, double rate);
+
 /* The body table of the slot's current step into host `out`, [nbodies][5] doubles: centre
  * x, y, velocity x, y, angular velocity (for coupled bodies the integrated state; for
  * prescribed motion c + V n). Synchronises. */

@@ -66,6 +66,9 @@ class Domain:
             if b.get("dynamics"):
                 dyn = _native.dynamics_from(b["dynamics"])
                 check(L.lbm_set_dynamics(h, k + 1, C.byref(dyn)), "lbm_set_dynamics")
+            if b.get("deform"):  # a pulsating body
+                check(L.lbm_set_deformation(h, k + 1, float(b["deform"]["amplitude"]),
+                                            float(b["deform"]["rate"])), "lbm_set_deformation")
 
     def body_state(self) -> np.ndarray:
         """Body table of the current step: [nbodies, 5] (cx, cy, vx, vy, omega); coupled
@@ -338,6 +341,14 @@ class Batch:
                 rc = load().lbm_batch_set_dynamics(self._h, slot.value, k + 1, C.byref(dyn))
                 if rc != _native.LBM_OK:
                     err = LbmError(rc, "lbm_batch_set_dynamics", load().lbm_last_error().decode())
+                    self.evict(slot.value)
+                    raise err
+            if b.get("deform"):  # a pulsating body
+                rc = load().lbm_batch_set_deformation(self._h, slot.value, k + 1,
+                                                      float(b["deform"]["amplitude"]),
+                                                      float(b["deform"]["rate"]))
+                if rc != _native.LBM_OK:
+                    err = LbmError(rc, "lbm_batch_set_deformation", load().lbm_last_error().decode())
                     self.evict(slot.value)
                     raise err
         return slot.value

@@ -154,6 +154,8 @@ SIGNATURES = {
     "lbm_batch_destroy": (C.c_int, [_VP]),
     "lbm_batch_set_dynamics": (C.c_int, [_VP, _I32, _I32, C.POINTER(BodyDynamics)]),
     "lbm_set_dynamics": (C.c_int, [_VP, _I32, C.POINTER(BodyDynamics)]),
+    "lbm_batch_set_deformation": (C.c_int, [_VP, _I32, _I32, C.c_double, C.c_double]),
+    "lbm_set_deformation": (C.c_int, [_VP, _I32, C.c_double, C.c_double]),
     "lbm_batch_body_state": (C.c_int, [_VP, _I32, _DP]),
     "lbm_body_state": (C.c_int, [_VP, _DP]),
     "lbm_batch_coupled_state": (C.c_int, [_VP, _I32, _DP]),

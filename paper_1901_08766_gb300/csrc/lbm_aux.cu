@@ -130,29 +130,54 @@ __device__ __forceinline__ void turn_sincos(double t, double &sn, double &cs) {
   }
 }
 
+__device__ __forceinline__ bool deforms(const DomDev &D, int body) {
+  return D.deform != 0u && body >= 1 && body <= D.nbodies && ((D.deform >> ((body - 1) & 31)) & 1u);
+}
+
+// scale s(n) = 1 + a sin(nu n) of pulsating body b (0-based)
+__device__ __forceinline__ double pulse_scale(const DomDev &D, int b, long long n, double *kappa) {
+  const double a = D.dpar[2 * b], nu = D.dpar[2 * b + 1];
+  double sn, cs;
+  turn_sincos(__dmul_rn(nu, static_cast<double>(n)), sn, cs);
+  const double sc = __dadd_rn(1.0, __dmul_rn(a, sn));
+  if (kappa) *kappa = __ddiv_rn(__dmul_rn(__dmul_rn(a, nu), cs), sc);  // s'/s
+  return sc;
+}
+
 // A rotating domain (moving = 2) turns body b's shapes by theta = omega n about its
-// centre c0 + V n: the reference point offset d from c0 goes to R(theta) d, a NACA
+// centre c0 + V n, and a pulsating body scales them by s(n) about it: the reference point
+// offset d from c0 goes to s(n) R(theta) d, radii and chords to s(n) times theirs, a NACA
 // section's (cos, sin) of its angle of attack to those of aoa - theta.
 __device__ __forceinline__ ShapeDev shape_turned(const DomDev &D, const ShapeDev &s0, long long n) {
   ShapeDev s = s0;
   const int b = s0.body - 1;
   const double *bt = D.bodies + 5 * b;  // vx, vy at 2, 3; omega at 4 (constant)
-  double sn, cs;
-  turn_sincos(__dmul_rn(bt[4], static_cast<double>(n)), sn, cs);
   const double c0x = D.centre0[2 * b], c0y = D.centre0[2 * b + 1];
   const double dx = __dsub_rn(s0.cx, c0x), dy = __dsub_rn(s0.cy, c0y);
-  const double rx = __dsub_rn(__dmul_rn(cs, dx), __dmul_rn(sn, dy));
-  const double ry = __dadd_rn(__dmul_rn(sn, dx), __dmul_rn(cs, dy));
+  double rx = dx, ry = dy;
+  if (D.moving == 2) {
+    double sn, cs;
+    turn_sincos(__dmul_rn(bt[4], static_cast<double>(n)), sn, cs);
+    rx = __dsub_rn(__dmul_rn(cs, dx), __dmul_rn(sn, dy));
+    ry = __dadd_rn(__dmul_rn(sn, dx), __dmul_rn(cs, dy));
+    s.ca = __dadd_rn(__dmul_rn(s0.ca, cs), __dmul_rn(s0.sa, sn));
+    s.sa = __dsub_rn(__dmul_rn(s0.sa, cs), __dmul_rn(s0.ca, sn));
+  }
+  if (deforms(D, s0.body)) {
+    const double sc = pulse_scale(D, b, n, nullptr);
+    rx = __dmul_rn(sc, rx);
+    ry = __dmul_rn(sc, ry);
+    s.radius = __dmul_rn(sc, s0.radius);
+    s.chord = __dmul_rn(sc, s0.chord);
+  }
   s.cx = __dadd_rn(moved(c0x, bt[2], n), rx);
   s.cy = __dadd_rn(moved(c0y, bt[3], n), ry);
-  s.ca = __dadd_rn(__dmul_rn(s0.ca, cs), __dmul_rn(s0.sa, sn));
-  s.sa = __dsub_rn(__dmul_rn(s0.sa, cs), __dmul_rn(s0.ca, sn));
   return s;
 }
 
 __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n) {
   ShapeDev s = s0;
-  if (D.moving == 2 && s0.body >= 1 && s0.body <= D.nbodies) return shape_turned(D, s0, n);
+  if ((D.moving == 2 || deforms(D, s0.body)) && s0.body >= 1 && s0.body <= D.nbodies) return shape_turned(D, s0, n);
   if (coupled(D, s0.body)) {
     const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + (s0.body - 1)) * 6;
     return shape_about(D, s0, st[0], st[1]);
@@ -202,15 +227,18 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
     const ShapeDev s = shape_at(D, s0, n);
     cx = float(s.cx - double(D.x0));
     cy = float(s.cy);
-  } else if (D.moving == 2 && s0.body >= 1 && s0.body <= D.nbodies) {
-    // a turning shape stays within its offset from the body centre: cull about the centre
-    // with the reach grown by that offset (no trigonometry here)
+  } else if ((D.moving == 2 || deforms(D, s0.body)) && s0.body >= 1 && s0.body <= D.nbodies) {
+    // a turning or pulsating shape stays within (1 + |a|) times its offset from the body
+    // centre and (1 + |a|) times its size: cull about the centre with the reach grown by
+    // both (no trigonometry here)
     const int b = s0.body - 1;
     const float fn = float(n);
     cx = (float(D.centre0[2 * b]) - float(D.x0)) + float(D.bodies[5 * b + 2]) * fn;
     cy = float(D.centre0[2 * b + 1]) + float(D.bodies[5 * b + 3]) * fn;
     const float ox = float(s0.cx - D.centre0[2 * b]), oy = float(s0.cy - D.centre0[2 * b + 1]);
-    turn = sqrtf(ox * ox + oy * oy) + 0.01f;
+    const float grow = deforms(D, s0.body) ? fabsf(float(D.dpar[2 * b])) : 0.f;
+    turn = (1.0f + grow) * sqrtf(ox * ox + oy * oy) +
+           grow * float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 0.01f;
   } else {
     float vx = 0.f, vy = 0.f;
     if (s0.body >= 1 && s0.body <= D.nbodies) {
@@ -289,6 +317,12 @@ __device__ void place_centres(const DomDev &D, long long n, int lane) {
     b[1] = cy;
     D.bodies_f[5 * lane] = float(cx);
     D.bodies_f[5 * lane + 1] = float(cy);
+    if (deforms(D, lane + 1)) {  // the dilation rate of step n
+      double kp;
+      pulse_scale(D, lane, n, &kp);
+      D.kappa[lane] = kp;
+      D.kappa_f[lane] = float(kp);
+    }
   }
 }
 

@@ -83,7 +83,7 @@ struct Alloc {
 // force ring, status word), each piece 256-byte aligned.
 struct Layout {
   size_t lat_bytes, mask_off, fvp_off, bodies_off, bodies_f_off, off_off, ring_off, status_off,
-      shapes_off, centre0_off, rowsum_off, fsi_off, total;
+      shapes_off, centre0_off, rowsum_off, fsi_off, def_off, total;
 };
 
 Layout layout_of(const lbm_params &p, int nbodies) {
@@ -108,7 +108,7 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   L.status_off = o;
   o += 256;
   // moving domains: reference geometry, reference centres, per-row force sums
-  L.shapes_off = L.centre0_off = L.rowsum_off = L.fsi_off = o;
+  L.shapes_off = L.centre0_off = L.rowsum_off = L.fsi_off = L.def_off = o;
   if (p.moving) {
     o += align_up(sizeof(ShapeDev) * kMaxMovingShapes, 256);
     L.centre0_off = o;
@@ -118,6 +118,9 @@ Layout layout_of(const lbm_params &p, int nbodies) {
     // coupled bodies: state of two step parities [2][nbodies][6], parameters [nbodies][8]
     L.fsi_off = o;
     o += align_up(sizeof(double) * 20 * std::max(1, nbodies), 256);
+    // pulsating bodies: amplitude and rate [nbodies][2], kappa FP64 [nbodies], FP32 [nbodies]
+    L.def_off = o;
+    o += align_up(sizeof(double) * 4 * std::max(1, nbodies), 256);
   }
   L.total = o;
   return L;
@@ -629,6 +632,10 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.fsi = p->moving ? reinterpret_cast<double *>(base + L.fsi_off) : nullptr;
   D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 12 * std::max(1, nbodies) : nullptr;
   D.fsi_on = 0;
+  D.dpar = p->moving ? reinterpret_cast<const double *>(base + L.def_off) : nullptr;
+  D.kappa = p->moving ? reinterpret_cast<double *>(base + L.def_off) + 2 * std::max(1, nbodies) : nullptr;
+  D.kappa_f = p->moving ? reinterpret_cast<float *>(D.kappa + std::max(1, nbodies)) : nullptr;
+  D.deform = 0u;
   D.nx = p->nx;
   D.ny = p->ny;
   D.pitch = s.pitch;
@@ -726,6 +733,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
     ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
     ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 20 * std::max(1, nbodies), st));
+    ADM_CUDA(cudaMemsetAsync(const_cast<double *>(D.dpar), 0, sizeof(double) * 4 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
     ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
   }
@@ -1132,6 +1140,7 @@ lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, cons
   if (s.p.force_every != 1) return fail(LBM_EINVAL, "coupled bodies need the force of every step (force_every = 1)");
   if (s.done != 0) return fail(LBM_EINVAL, "dynamics are set before the first step");
   if (s.link_west >= 0 || s.link_east >= 0) return fail(LBM_EINVAL, "a linked domain cannot have coupled bodies");
+  if (s.dev.deform) return fail(LBM_EINVAL, "a domain with pulsating bodies cannot have coupled bodies");
   if (body < 1 || body > s.nbodies) return fail(LBM_EINVAL, "body %d not in [1, %d]", body, s.nbodies);
   if (!(dyn->mass > 0) || !std::isfinite(dyn->mass)) return fail(LBM_EINVAL, "mass must be finite and > 0");
   for (int e = 0; e < 2; ++e) {
@@ -1156,6 +1165,31 @@ lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, cons
   LBM_CUDA(cudaMemcpyAsync(b->d_doms + slot, &D, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaStreamSynchronize(b->st));
   s.fsi = true;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_deformation(lbm_batch *b, int32_t slot, int32_t body, double amplitude, double rate) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  Slot &s = b->slots[slot];
+  if (!s.p.moving) return fail(LBM_EINVAL, "pulsating bodies need a moving domain");
+  if (s.done != 0) return fail(LBM_EINVAL, "a deformation is set before the first step");
+  if (s.fsi) return fail(LBM_EINVAL, "coupled bodies do not deform");
+  if (s.link_west >= 0 || s.link_east >= 0) return fail(LBM_EINVAL, "a linked domain cannot have pulsating bodies");
+  if (body < 1 || body > s.nbodies) return fail(LBM_EINVAL, "body %d not in [1, %d]", body, s.nbodies);
+  if (!(std::fabs(amplitude) < 1.0) || !std::isfinite(rate))
+    return fail(LBM_EINVAL, "the amplitude must satisfy |a| < 1 and the rate be finite");
+  DomDev &D = s.dev;
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  const double par[2] = {amplitude, rate};
+  LBM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.dpar) + 2 * (body - 1), par, sizeof(par), cudaMemcpyHostToDevice,
+                           b->st));
+  D.deform |= 1u << (body - 1);
+  LBM_CUDA(cudaMemcpyAsync(b->d_doms + slot, &D, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  // the mask, centres and dilation rates of step index 0 with the pulsating placement
+  LBM_CUDA(launch_place(b->st, b->d_doms + slot, s.p.nx, s.p.ny, s.pitch, 0));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
   b->dirty = true;
   return LBM_OK;
 }
@@ -1239,6 +1273,7 @@ lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t east_slot) 
     return fail(LBM_EINVAL, "linked domains must step together (same steps done and admitted)");
   if (A.link_east >= 0 || B.link_west >= 0) return fail(LBM_EINVAL, "an edge is linked already");
   if (A.fsi || B.fsi) return fail(LBM_EINVAL, "domains with coupled bodies cannot be linked");
+  if (A.dev.deform || B.dev.deform) return fail(LBM_EINVAL, "domains with pulsating bodies cannot be linked");
   LBM_CUDA(cudaStreamSynchronize(b->st));
   // A's east edge pulls B's first column; B's west edge pulls A's last column
   A.dev.east = LBM_NEIGHBOR;
@@ -1408,6 +1443,11 @@ lbm_status lbm_set_steps_done(lbm_domain *d, int64_t steps) {
 lbm_status lbm_set_dynamics(lbm_domain *d, int32_t body, const lbm_body_dynamics *dyn) {
   if (!d) return fail(LBM_EINVAL, "domain is NULL");
   return lbm_batch_set_dynamics(d->b, 0, body, dyn);
+}
+
+lbm_status lbm_set_deformation(lbm_domain *d, int32_t body, double amplitude, double rate) {
+  if (!d) return fail(LBM_EINVAL, "domain is NULL");
+  return lbm_batch_set_deformation(d->b, 0, body, amplitude, rate);
 }
 
 lbm_status lbm_body_state(lbm_domain *d, double *out) {

@@ -134,3 +134,93 @@ def test_pitching_airfoil_turns_the_lift(lbm):
     cl = f[:, 0, 1] / (0.5 * U * U * chord)
     early, late = cl[1000:1500].mean(), cl[-500:].mean()
     assert early > 0.2 and late < -0.2, (early, late)
+
+
+# ---- pulsating (deforming) bodies ------------------------------------------------------
+
+def _pulsating_spec(moving, edges=None):
+    # body 1: a NACA section with a circle riding behind it, pulsating by 20 % (turning too
+    # in a rotating domain); body 2: a circle pulsating by -25 % about an offset centre;
+    # both stay inside the domain over 400 steps
+    sp = _turning_spec(ny=84, edges=edges)
+    sp["moving"] = moving
+    sp["bodies"] = [dict(sp["bodies"][0], deform={"amplitude": 0.2, "rate": 0.023}),
+                    dict(sp["bodies"][1], deform={"amplitude": -0.25, "rate": 0.031})]
+    sp["shapes"] = sp["shapes"] + [synth._circle(1, 56.0, 36.0, 3.0)]
+    return sp
+
+
+@pytest.mark.parametrize("moving", [True, 2])
+@pytest.mark.parametrize("edges", ["periodic", "channel"])
+def test_pulsating_fp64_matches_oracle(lbm, moving, edges):
+    e = synth._edges() if edges == "periodic" else synth._edges("inlet", "outflow", "free_slip", "free_slip")
+    spec = _pulsating_spec(moving, e)
+    g0 = synth.random_populations(43, spec["nx"], spec["ny"], 0.05)
+    dom = lbm.Domain(spec, storage="f64")
+    dom.set_populations(g0)
+    ora = oracle.Domain(spec, g=g0)
+    assert np.array_equal(dom.mask(), ora.mask)
+    f_gpu, f_ora = [], []
+    for chunk in (1, 99, 300):
+        f_gpu.append(dom.run(chunk))
+        f_ora.append(ora.run(chunk))
+        assert np.array_equal(dom.mask(), ora.mask), f"mask differs after {ora.steps_done} steps"
+    raw = dom.get_populations()
+    rel = np.abs(raw - ora.g) / np.abs(ora.g)
+    assert rel.max() <= 1e-12, f"max relative population difference {rel.max():.3e}"
+    fg, fo = np.concatenate(f_gpu), np.concatenate(f_ora)
+    assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max() + 1e-14
+    r_g, ux_g, uy_g = dom.moments()
+    r_o, ux_o, uy_o = ora.moments()
+    assert np.allclose(ux_g, ux_o, rtol=0, atol=1e-13) and np.allclose(uy_g, uy_o, rtol=0, atol=1e-13)
+    dom.close()
+
+
+def test_pulsating_batch_graphs_and_resume(lbm):
+    # FP16-shifted: alone, in a mixed batch with CUDA graphs, and resumed at index 70,
+    # the same bits
+    spec = _pulsating_spec(2)
+    fixed = synth.parity_case("channel_97x61")
+    g0 = codec.encode(synth.random_populations(5, spec["nx"], spec["ny"], 0.05), "f16s")
+    out = []
+    for others, graph in [(0, 0), (2, 16)]:
+        b = lbm.Batch("f16s", max_domains=4, graph_steps=graph)
+        ks = [b.admit(fixed, nsteps=160) for _ in range(others)]
+        k = b.admit(spec, nsteps=160)
+        b.set_populations(k, g0)
+        while b.run(40):
+            pass
+        f, done = b.poll(k)
+        assert done
+        out.append((b.get_populations(k).view(np.uint16).copy(), f, b.mask(k)))
+        for q in ks:
+            b.poll(q)
+        b.close()
+    for x, y in zip(out[1], out[0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(out[0][2], oracle.rasterize(spec, 160))
+    a = lbm.Domain(spec, storage="f16s")
+    a.set_populations(g0)
+    fb1 = a.run(70)
+    snap = a.get_populations()
+    a.close()
+    c = lbm.Domain(spec, storage="f16s")
+    c.set_populations(snap)
+    c.set_steps_done(70)
+    assert np.array_equal(c.mask(), oracle.rasterize(spec, 70))
+    fb2 = c.run(90)
+    assert np.array_equal(c.get_populations().view(np.uint16), out[0][0])
+    assert np.array_equal(np.concatenate([fb1, fb2]), out[0][1])
+    c.close()
+
+
+def test_pulsating_guards(lbm):
+    spec = _pulsating_spec(True)
+    with pytest.raises(lbm.LbmError):  # a fixed mask does not pulsate
+        lbm.Domain(dict(spec, moving=False), storage="f32")
+    big = dict(spec, bodies=[dict(spec["bodies"][0], deform={"amplitude": 1.0, "rate": 0.01}), spec["bodies"][1]])
+    with pytest.raises(lbm.LbmError):
+        lbm.Domain(big, storage="f32")
+    cpl = dict(spec, bodies=[dict(spec["bodies"][0], dynamics=synth.dynamics(1e4)), spec["bodies"][1]])
+    with pytest.raises(lbm.LbmError):  # coupled bodies do not deform
+        lbm.Domain(cpl, storage="f32")
