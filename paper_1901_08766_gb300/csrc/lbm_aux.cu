@@ -761,7 +761,7 @@ __global__ void moments_kernel(const DomDev *dom, int parity, double *rho, doubl
   for (int a = 0; a < kQ; ++a) x[a] = pull_scalar<S>(D, src, a, i, j);
   const int b = D.mask[static_cast<size_t>(j) * D.pitch + i];
   T uox = T(0), uoy = T(0);
-  if (b) body_velocity<T>(D, b, i, j, uox, uoy);
+  if (b) body_velocity<true>(D, b, i, j, uox, uoy);
   const NodeMacro<T> m = node_macro<T, Cd::kShiftCompute, true>(x, C, b != 0, uox, uoy);
   const size_t c = static_cast<size_t>(j) * D.nx + i;
   if (rho) rho[c] = double(m.rho * (T(1) / T(Cd::kScale)));  // unscaled (power of two: exact)

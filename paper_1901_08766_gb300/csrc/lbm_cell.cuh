@@ -348,36 +348,35 @@ __device__ __forceinline__ void collide(T (&x)[kQ], const NodeMacro<T> &m, const
   pair(6, 8, m.uy - m.ux, m.fy - m.fx, a2, b2, m2, c.kw2, c.qw2);
 }
 
-// Obstacle velocity of body id b at node (i, j): V + omega z x (x - c), plus kappa (x - c)
-// for a pulsating body, in the compute precision (FP64 with explicit roundings for the
-// FP64 storage, FP32 otherwise).
-template <typename T>
-__device__ __forceinline__ void body_velocity(const DomDev &d, int b, int i, int j, T &uox, T &uoy);
-
-template <>
-__device__ __forceinline__ void body_velocity<double>(const DomDev &d, int b, int i, int j,
-                                                      double &uox, double &uoy) {
+// Obstacle velocity of body id b at node (i, j): V + omega z x (x - c), plus
+// kappa (x - c) with DEF, in the compute precision (FP64 with explicit roundings for the
+// FP64 storage, FP32 otherwise). kappa is a pulsating body's dilation rate and zero for
+// rigid bodies: with DEF the term is added without a branch on the body; sweeps of
+// batches without pulsating bodies are instantiated without it (it raised their spills).
+template <bool DEF>
+__device__ __forceinline__ void body_velocity(const DomDev &d, int b, int i, int j,
+                                              double &uox, double &uoy) {
   const double *bd = d.bodies + 5 * (b - 1);
   const double cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
                om = __ldg(bd + 4);
   uox = __dsub_rn(vx, __dmul_rn(om, __dsub_rn(double(j), cy)));
   uoy = __dadd_rn(vy, __dmul_rn(om, __dsub_rn(double(i + d.x0), cx)));  // global column
-  if (d.deform != 0u && ((d.deform >> ((b - 1) & 31)) & 1u)) {  // + kappa (x - c)
+  if constexpr (DEF) {
     const double kp = __ldg(d.kappa + (b - 1));
     uox = __dadd_rn(uox, __dmul_rn(kp, __dsub_rn(double(i + d.x0), cx)));
     uoy = __dadd_rn(uoy, __dmul_rn(kp, __dsub_rn(double(j), cy)));
   }
 }
 
-template <>
-__device__ __forceinline__ void body_velocity<float>(const DomDev &d, int b, int i, int j,
-                                                     float &uox, float &uoy) {
+template <bool DEF>
+__device__ __forceinline__ void body_velocity(const DomDev &d, int b, int i, int j,
+                                              float &uox, float &uoy) {
   const float *bd = d.bodies_f + 5 * (b - 1);
   const float cx = __ldg(bd + 0), cy = __ldg(bd + 1), vx = __ldg(bd + 2), vy = __ldg(bd + 3),
               om = __ldg(bd + 4);
   uox = vx - om * (float(j) - cy);
   uoy = vy + om * (float(i + d.x0) - cx);
-  if (d.deform != 0u && ((d.deform >> ((b - 1) & 31)) & 1u)) {  // + kappa (x - c)
+  if constexpr (DEF) {
     const float kp = __ldg(d.kappa_f + (b - 1));
     uox += kp * (float(i + d.x0) - cx);
     uoy += kp * (float(j) - cy);

@@ -74,9 +74,10 @@ struct DomDev {
   const double *fsi_par;    // [nbodies][8]: mass, k_x, k_y, c_x, c_y, free_x, free_y, coupled
   int32_t fsi_on;           // some body of the domain is coupled
   int32_t fsi_pad;
-  // deforming bodies of a moving domain (null / 0 otherwise): [nbodies][2] amplitude a and
-  // rate nu of the pulsation s(n) = 1 + a sin(nu n); the dilation rate kappa = s'/s of the
-  // current step in FP64 and FP32 ([nbodies] each); bit b of `deform`: body b + 1 pulsates
+  // deforming bodies: [nbodies][2] amplitude a and rate nu of the pulsation
+  // s(n) = 1 + a sin(nu n) (moving domains; null otherwise); the dilation rate kappa = s'/s
+  // of the current step in FP64 and FP32 ([nbodies] each, every domain, zero for rigid
+  // bodies); bit b of `deform`: body b + 1 pulsates
   const double *dpar;
   double *kappa;
   float *kappa_f;

@@ -82,7 +82,7 @@ struct Alloc {
 // Fixed part of a domain's device footprint (populations x2, mask, bodies, offsets,
 // force ring, status word), each piece 256-byte aligned.
 struct Layout {
-  size_t lat_bytes, mask_off, fvp_off, bodies_off, bodies_f_off, off_off, ring_off, status_off,
+  size_t lat_bytes, mask_off, fvp_off, bodies_off, bodies_f_off, kappa_off, off_off, ring_off, status_off,
       shapes_off, centre0_off, rowsum_off, fsi_off, def_off, total;
 };
 
@@ -101,6 +101,9 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   o += align_up(sizeof(double) * 5 * std::max(1, nbodies), 256);
   L.bodies_f_off = o;
   o += align_up(sizeof(float) * 5 * std::max(1, nbodies), 256);
+  // dilation rates of the bodies, FP64 then FP32 (zero unless a body pulsates)
+  L.kappa_off = o;
+  o += align_up(sizeof(double) * std::max(1, nbodies), 256) + align_up(sizeof(float) * std::max(1, nbodies), 256);
   L.off_off = o;
   o += align_up(sizeof(int32_t) * (nbodies + 1), 256);
   L.ring_off = o;
@@ -118,9 +121,9 @@ Layout layout_of(const lbm_params &p, int nbodies) {
     // coupled bodies: state of two step parities [2][nbodies][6], parameters [nbodies][8]
     L.fsi_off = o;
     o += align_up(sizeof(double) * 20 * std::max(1, nbodies), 256);
-    // pulsating bodies: amplitude and rate [nbodies][2], kappa FP64 [nbodies], FP32 [nbodies]
+    // pulsating bodies: amplitude and rate [nbodies][2]
     L.def_off = o;
-    o += align_up(sizeof(double) * 4 * std::max(1, nbodies), 256);
+    o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
   }
   L.total = o;
   return L;
@@ -247,6 +250,8 @@ struct lbm_batch {
   int moves_cap = 0;
   int nmove = 0;               // rows in the list; 0: no move kernel in the step
   bool has_fsi = false;        // some resident domain has coupled bodies: fsi kernel per step
+  bool has_deform = false;     // some resident domain has pulsating bodies: the sweep with
+                               // the dilation term of U_O
   Counters *d_ctr = nullptr;
   Counters *h_ctr = nullptr;  // pinned staging for tile/item counts
   int vec = 0, warps = 0, rows = 0, pipe = 0;
@@ -268,6 +273,7 @@ namespace {
 
 cudaError_t sweep_launch(lbm_batch *b, int grid, int vec, int pipe, int warps, int rows, int s) {
   SweepArgs a{b->d_doms, b->d_dyn, b->d_tiles, b->d_ctr, rows};
+  if (pipe == 0 && b->has_deform) pipe = 4;  // the direct sweep instantiated with the kappa term
   switch (b->storage) {
     case LBM_F64: return launch_sweep_f64(vec, pipe, grid, warps, b->st, a, s);
     case LBM_F32: return launch_sweep_f32(vec, pipe, grid, warps, b->st, a, s);
@@ -345,10 +351,14 @@ lbm_status rebuild_lists(lbm_batch *b) {
   }
   // a captured graph holds the move kernel only if there were moving rows at capture,
   // and the fsi kernel only if some domain had coupled bodies
-  bool has_fsi = false;
-  for (const Slot &s : b->slots) has_fsi = has_fsi || (s.used && s.fsi);
-  if ((b->nmove > 0) != !moves.empty() || has_fsi != b->has_fsi) drop_graph(b);
+  bool has_fsi = false, has_deform = false;
+  for (const Slot &s : b->slots) {
+    has_fsi = has_fsi || (s.used && s.fsi);
+    has_deform = has_deform || (s.used && s.dev.deform != 0u);
+  }
+  if ((b->nmove > 0) != !moves.empty() || has_fsi != b->has_fsi || has_deform != b->has_deform) drop_graph(b);
   b->has_fsi = has_fsi;
+  b->has_deform = has_deform;
   if (static_cast<int>(moves.size()) > b->moves_cap || (!moves.empty() && !b->d_moves)) {
     const int cap = std::max<int>(static_cast<int>(moves.size()) * 2, 1024);
     LBM_CUDA(cudaStreamSynchronize(b->st));
@@ -633,8 +643,8 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 12 * std::max(1, nbodies) : nullptr;
   D.fsi_on = 0;
   D.dpar = p->moving ? reinterpret_cast<const double *>(base + L.def_off) : nullptr;
-  D.kappa = p->moving ? reinterpret_cast<double *>(base + L.def_off) + 2 * std::max(1, nbodies) : nullptr;
-  D.kappa_f = p->moving ? reinterpret_cast<float *>(D.kappa + std::max(1, nbodies)) : nullptr;
+  D.kappa = reinterpret_cast<double *>(base + L.kappa_off);
+  D.kappa_f = reinterpret_cast<float *>(base + L.kappa_off + align_up(sizeof(double) * std::max(1, nbodies), 256));
   D.deform = 0u;
   D.nx = p->nx;
   D.ny = p->ny;
@@ -721,6 +731,8 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   ADM_CUDA(cudaMemcpyAsync(bod, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
   std::vector<float> hbf(hb.begin(), hb.end());
   ADM_CUDA(cudaMemcpyAsync(bodf, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemsetAsync(base + L.kappa_off, 0,
+                           align_up(sizeof(double) * std::max(1, nbodies), 256) + sizeof(float) * std::max(1, nbodies), st));
   if (p->moving) {
     // reference centres, then the mask and centres of step index 0
     std::vector<double> hc0(2 * std::max(1, nbodies), 0.0);
@@ -733,7 +745,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
     ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
     ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 20 * std::max(1, nbodies), st));
-    ADM_CUDA(cudaMemsetAsync(const_cast<double *>(D.dpar), 0, sizeof(double) * 4 * std::max(1, nbodies), st));
+    ADM_CUDA(cudaMemsetAsync(const_cast<double *>(D.dpar), 0, sizeof(double) * 2 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
     ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
   }

@@ -205,7 +205,7 @@ template <int S, int V> struct RowData {
 // The sweep body. PF = false: each warp loads a row, then updates it. PF = true: the
 // loads of the warp's next row are issued into a second register set before the current
 // row is updated, so that they overlap the update (more registers, fewer warps).
-template <int S, int V, bool PF>
+template <int S, int V, bool PF, bool DEF = true>
 __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
@@ -424,7 +424,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
           T uox = T(0), uoy = T(0);
           const int bk = R.body(k);
           const bool solid = bk != 0;
-          if (solid) body_velocity<T>(D, bk, xl + k, j, uox, uoy);
+          if (solid) body_velocity<DEF>(D, bk, xl + k, j, uox, uoy);
           m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
           collide<T, SHIFT, true>(x, m, C);
           if (solid) {
@@ -557,9 +557,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
 #ifndef LBM_SWEEP_THREADS
 #define LBM_SWEEP_THREADS 512
 #endif
-template <int S, int V>
+// DEF: some domain of the batch has pulsating bodies (the kappa term of U_O)
+template <int S, int V, bool DEF>
 __global__ void __launch_bounds__(LBM_SWEEP_THREADS) sweep_kernel(SweepArgs args, int s) {
-  sweep_body<S, V, false>(args, s);
+  sweep_body<S, V, false, DEF>(args, s);
 }
 
 template <int S, int V>
@@ -568,8 +569,9 @@ __global__ void __launch_bounds__(256) sweep_pf_kernel(SweepArgs args, int s) {
 }
 
 template <int S, int V>
-cudaError_t launch_sweep_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s) {
-  sweep_kernel<S, V><<<grid, warps * 32, 0, st>>>(a, s);
+cudaError_t launch_sweep_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s, bool def) {
+  if (def) sweep_kernel<S, V, true><<<grid, warps * 32, 0, st>>>(a, s);
+  else sweep_kernel<S, V, false><<<grid, warps * 32, 0, st>>>(a, s);
   return cudaGetLastError();
 }
 
@@ -581,7 +583,7 @@ cudaError_t launch_sweep_pf_t(int grid, int warps, cudaStream_t st, const SweepA
 
 template <int S, int V> int max_blocks_t(int warps) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<S, V>, warps * 32, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<S, V, false>, warps * 32, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -6,9 +6,9 @@ namespace lbm {
 
 cudaError_t launch_sweep_f32(int vec, int pipe, int grid, int warps, cudaStream_t st,
                                const SweepArgs &a, int s) {
-  if (pipe == 0) {
-    if (vec == 2) return launch_sweep_t<LBM_F32, 2>(grid, warps, st, a, s);
-    if (vec == 4) return launch_sweep_t<LBM_F32, 4>(grid, warps, st, a, s);
+  if (pipe == 0 || pipe == 4) {  // 4: the direct sweep with pulsating bodies
+    if (vec == 2) return launch_sweep_t<LBM_F32, 2>(grid, warps, st, a, s, pipe == 4);
+    if (vec == 4) return launch_sweep_t<LBM_F32, 4>(grid, warps, st, a, s, pipe == 4);
   } else if (pipe == 2) {
     if (vec == 2) return launch_sweep_pf_t<LBM_F32, 2>(grid, warps, st, a, s);
     if (vec == 4) return launch_sweep_pf_t<LBM_F32, 4>(grid, warps, st, a, s);

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
       if (any_solid) {
         T uox = T(0), uoy = T(0);
         const bool solid = b[k] != 0;
-        if (solid) body_velocity<T>(D, b[k], xl + k, j, uox, uoy);
+        if (solid) body_velocity<true>(D, b[k], xl + k, j, uox, uoy);
         m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
         collide<T, SHIFT, true>(x, m, C);
         if (solid) {
