@@ -197,7 +197,7 @@ def _config(args, specs, extra=None):
     cells = sum(s["nx"] * s["ny"] for s in specs)
     c = {"workload": "batched uneven domains: 64 seeded tandem/side-by-side cylinder pairs, "
                      "W 400..2000, H = W/2, Re 40..200, D = 40, U = 0.05",
-         "domains": len(specs), "cells": cells, "storage": args.storage, "moving": bool(args.moving),
+         "domains": len(specs), "cells": cells, "storage": args.storage, "moving": args.moving or False,
          "forces": "every step, FP64 per body", "graph_steps": args.graph_steps,
          "l2": "inputs larger than L2 (working set %.2f GB per step)" %
                (cells * BYTES_PER_CELL[args.storage] / 1e9),
@@ -223,7 +223,11 @@ def run_ours(args):
     if args.moving:
         # every domain carries the per-step geometry update of moving bodies (velocities
         # unchanged, so the flow is the same): measures the cost of the update
-        specs = [dict(sp, moving=True) for sp in specs]
+        mode = {"translate": True, "turn": 2, "pulse": True}[args.moving]
+        specs = [dict(sp, moving=mode) for sp in specs]
+        if args.moving == "pulse":
+            pulse = {"amplitude": 0.05, "rate": 2.0 * math.pi / 2000.0}
+            specs = [dict(sp, bodies=[dict(b, deform=pulse) for b in sp["bodies"]]) for sp in specs]
     cells = sum(s["nx"] * s["ny"] for s in specs)
     stream = torch.cuda.Stream()
     nsteps_total = args.warmup + args.steps + args.profile_steps + 10
@@ -787,8 +791,11 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="vec,warps,rows[,pipeline]: fixed sweep tile, no autotune")
     ap.add_argument("--domains", type=int, default=64, help="first N domains of the set")
-    ap.add_argument("--moving", action="store_true",
-                    help="mark every domain as moving (per-step geometry update; same flow)")
+    ap.add_argument("--moving", nargs="?", const="translate", default=None,
+                    choices=["translate", "turn", "pulse"],
+                    help="mark every domain as moving (per-step geometry update; same flow): "
+                         "translate (default), turn (shapes turned with the bodies, omega = 0 "
+                         "here), pulse (every body pulsating by 5 %% over 2000 steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e, plain, served and CPU legs")
     ap.add_argument("--served-requests", type=int, default=32)

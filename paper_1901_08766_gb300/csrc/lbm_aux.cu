@@ -148,23 +148,47 @@ __device__ __forceinline__ double pulse_scale(const DomDev &D, int b, long long 
 // centre c0 + V n, and a pulsating body scales them by s(n) about it: the reference point
 // offset d from c0 goes to s(n) R(theta) d, radii and chords to s(n) times theirs, a NACA
 // section's (cos, sin) of its angle of attack to those of aoa - theta.
-__device__ __forceinline__ ShapeDev shape_turned(const DomDev &D, const ShapeDev &s0, long long n) {
+// cos theta, sin theta and the scale of body b (0-based) at step index n, evaluated
+__device__ __forceinline__ void turn_of(const DomDev &D, int b, long long n, double &cs, double &sn, double &sc) {
+  cs = 1.0;
+  sn = 0.0;
+  sc = 1.0;
+  if (D.moving == 2) turn_sincos(__dmul_rn(D.bodies[5 * b + 4], static_cast<double>(n)), sn, cs);
+  if (deforms(D, b + 1)) sc = pulse_scale(D, b, n, nullptr);
+}
+
+// The same, stored one step ahead: the body-table update of index m writes index m + 1
+// into slot (m + 1) & 1, while the move kernel of the step to m reads slot m & 1
+__device__ __forceinline__ void store_turn(const DomDev &D, int b, long long m) {
+  double *t = D.turn + (static_cast<size_t>(m & 1) * D.nbodies + b) * 3;
+  turn_of(D, b, m, t[0], t[1], t[2]);
+}
+
+// table: read cos, sin and scale from the one-step-ahead table (the move kernel's index
+// n + 1), else evaluate them (admission, step-index changes)
+__device__ __forceinline__ ShapeDev shape_turned(const DomDev &D, const ShapeDev &s0, long long n, bool table) {
   ShapeDev s = s0;
   const int b = s0.body - 1;
-  const double *bt = D.bodies + 5 * b;  // vx, vy at 2, 3; omega at 4 (constant)
+  const double *bt = D.bodies + 5 * b;  // vx, vy at 2, 3
+  double cs, sn, sc;
+  if (table) {
+    const double *t = D.turn + (static_cast<size_t>(n & 1) * D.nbodies + b) * 3;
+    cs = t[0];
+    sn = t[1];
+    sc = t[2];
+  } else {
+    turn_of(D, b, n, cs, sn, sc);
+  }
   const double c0x = D.centre0[2 * b], c0y = D.centre0[2 * b + 1];
   const double dx = __dsub_rn(s0.cx, c0x), dy = __dsub_rn(s0.cy, c0y);
   double rx = dx, ry = dy;
   if (D.moving == 2) {
-    double sn, cs;
-    turn_sincos(__dmul_rn(bt[4], static_cast<double>(n)), sn, cs);
     rx = __dsub_rn(__dmul_rn(cs, dx), __dmul_rn(sn, dy));
     ry = __dadd_rn(__dmul_rn(sn, dx), __dmul_rn(cs, dy));
     s.ca = __dadd_rn(__dmul_rn(s0.ca, cs), __dmul_rn(s0.sa, sn));
     s.sa = __dsub_rn(__dmul_rn(s0.sa, cs), __dmul_rn(s0.ca, sn));
   }
   if (deforms(D, s0.body)) {
-    const double sc = pulse_scale(D, b, n, nullptr);
     rx = __dmul_rn(sc, rx);
     ry = __dmul_rn(sc, ry);
     s.radius = __dmul_rn(sc, s0.radius);
@@ -175,9 +199,10 @@ __device__ __forceinline__ ShapeDev shape_turned(const DomDev &D, const ShapeDev
   return s;
 }
 
-__device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n) {
+__device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0, long long n, bool table = false) {
   ShapeDev s = s0;
-  if ((D.moving == 2 || deforms(D, s0.body)) && s0.body >= 1 && s0.body <= D.nbodies) return shape_turned(D, s0, n);
+  if ((D.moving == 2 || deforms(D, s0.body)) && s0.body >= 1 && s0.body <= D.nbodies)
+    return shape_turned(D, s0, n, table);
   if (coupled(D, s0.body)) {
     const double *st = D.fsi + (static_cast<size_t>(n & 1) * D.nbodies + (s0.body - 1)) * 6;
     return shape_about(D, s0, st[0], st[1]);
@@ -323,6 +348,7 @@ __device__ void place_centres(const DomDev &D, long long n, int lane) {
       D.kappa[lane] = kp;
       D.kappa_f[lane] = float(kp);
     }
+    if (D.moving == 2 || deforms(D, lane + 1)) store_turn(D, lane, n + 1);  // one step ahead
   }
 }
 
@@ -419,7 +445,7 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       if (c0 <= c1) {
         for (int k = lane; k < D.nshapes; k += 32) {
           shape_cols_f32(D, D.shapes[k], n + 1, j, rs[k].lo, rs[k].hi);
-          if (rs[k].lo <= rs[k].hi) rs[k].s = shape_at(D, D.shapes[k], n + 1);
+          if (rs[k].lo <= rs[k].hi) rs[k].s = shape_at(D, D.shapes[k], n + 1, true);
         }
         __syncwarp();
         write_ids(D, j, c0, c1, lane, rs);

@@ -81,6 +81,9 @@ struct DomDev {
   const double *dpar;
   double *kappa;
   float *kappa_f;
+  // turning or pulsating bodies: cos theta, sin theta and the scale s of step index m in
+  // [m & 1][nbodies][3] (written one step ahead by the body-table update)
+  double *turn;
   uint32_t deform;
   int32_t deform_pad;
 };

@@ -121,9 +121,10 @@ Layout layout_of(const lbm_params &p, int nbodies) {
     // coupled bodies: state of two step parities [2][nbodies][6], parameters [nbodies][8]
     L.fsi_off = o;
     o += align_up(sizeof(double) * 20 * std::max(1, nbodies), 256);
-    // pulsating bodies: amplitude and rate [nbodies][2]
+    // pulsating bodies: amplitude and rate [nbodies][2]; turning or pulsating bodies: cos,
+    // sin and scale of the next step index [2][nbodies][3]
     L.def_off = o;
-    o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
+    o += align_up(sizeof(double) * 8 * std::max(1, nbodies), 256);
   }
   L.total = o;
   return L;
@@ -643,6 +644,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 12 * std::max(1, nbodies) : nullptr;
   D.fsi_on = 0;
   D.dpar = p->moving ? reinterpret_cast<const double *>(base + L.def_off) : nullptr;
+  D.turn = p->moving ? reinterpret_cast<double *>(base + L.def_off) + 2 * std::max(1, nbodies) : nullptr;
   D.kappa = reinterpret_cast<double *>(base + L.kappa_off);
   D.kappa_f = reinterpret_cast<float *>(base + L.kappa_off + align_up(sizeof(double) * std::max(1, nbodies), 256));
   D.deform = 0u;
@@ -745,7 +747,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
     ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
     ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 20 * std::max(1, nbodies), st));
-    ADM_CUDA(cudaMemsetAsync(const_cast<double *>(D.dpar), 0, sizeof(double) * 2 * std::max(1, nbodies), st));
+    ADM_CUDA(cudaMemsetAsync(const_cast<double *>(D.dpar), 0, sizeof(double) * 8 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
     ADM_CUDA(launch_place(st, b->d_doms + k, p->nx, p->ny, s.pitch, 0));
   }
