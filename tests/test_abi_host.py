@@ -64,6 +64,7 @@ def test_domain_bytes(lib):
 BAD = [
     ("nx", 2), ("ny", 1), ("nu", -1.0), ("magic_lambda", 0.0), ("eta", 0.0), ("rho0", -1.0),
     ("west", 2), ("east", 1), ("south", 1), ("north", 2), ("storage", 9), ("force_every", -1),
+    ("moving", 3), ("moving", -1),
 ]
 
 
@@ -152,7 +153,8 @@ def test_params3_default_and_bytes(lib):
 
 
 BAD3 = [("nz", 2), ("nx", 1), ("nu", -1.0), ("eta", 0.0), ("bottom", 1), ("top", 2),
-        ("south", 2), ("storage", 7), ("force_capacity", -1), ("lattice", 7)]
+        ("south", 2), ("storage", 7), ("force_capacity", -1), ("lattice", 7),
+        ("moving", 2)]  # shapes turned with their body: 2D only
 
 
 @pytest.mark.parametrize("field,value", BAD3)
