@@ -85,6 +85,31 @@ def test_three_slab_ring_with_moving_bodies(lbm):
     assert np.abs(split[1] - whole[1]).max() <= 1e-12 * np.abs(whole[1]).max()
 
 
+def test_three_slab_ring_with_turning_shapes(lbm):
+    # shapes turned with their bodies (moving = 2) across the cuts: the NACA section turns
+    # about a centre 6 cells behind its quarter chord and the circle orbits its body's
+    # centre, both placed at global columns; the slabs equal the undivided grid bit for bit
+    spec = _grid("periodic", moving=True)
+    spec["moving"] = 2
+    spec["shapes"] = [synth._circle(1, 95.3, 30.7, 9.0), synth._circle(1, 82.0, 30.7, 3.0), spec["shapes"][1]]
+    spec["bodies"] = [dict(spec["bodies"][0], omega=0.02),
+                      dict(spec["bodies"][1], cx=176.0, omega=-0.008)]
+    g0 = codec.encode(synth.random_populations(33, 250, 64, 0.05), "f16s")
+    whole = _run_whole(lbm, spec, "f16s", g0, 60, (8, 8, 2, 0))
+    split = _run_split(lbm, spec, "f16s", g0, 60, (8, 8, 2, 0), [80, 88, 82])
+    assert np.array_equal(split[2], whole[2])
+    assert np.array_equal(split[2], oracle.rasterize(spec, 60))
+    assert not np.array_equal(whole[2], oracle.rasterize(dict(spec, moving=True), 60))
+    assert np.array_equal(split[0].view(np.uint16), whole[0].view(np.uint16))
+    assert np.abs(split[1] - whole[1]).max() <= 1e-12 * np.abs(whole[1]).max()
+    # pulsating domains are not linked
+    pulse = dict(spec, bodies=[dict(spec["bodies"][0], deform={"amplitude": 0.1, "rate": 0.01}), spec["bodies"][1]])
+    b = lbm.Batch("f16s", max_domains=3, graph_steps=16)
+    with pytest.raises(lbm.LbmError):
+        slabs.admit_split(b, pulse, [80, 88, 82], nsteps=10)
+    b.close()
+
+
 def test_16bit_origin_must_be_a_multiple_of_8(lbm):
     spec = dict(_grid("channel"), nx=100, x_origin=97)
     b = lbm.Batch("f16s", max_domains=1, graph_steps=0)
