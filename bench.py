@@ -82,7 +82,10 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the raw samples (the JSON line carries their summary); LBM_CLOCKS_DIR keeps them
+        import tempfile
+        out = os.environ.get("LBM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"lbm_clocks_rank{device_index}.csv")
 
     def start(self):
         try:
