@@ -38,7 +38,9 @@ class _Params(C.Structure):
 
 
 class _Body(C.Structure):
-    _fields_ = [("c", C.c_double * 3), ("v", C.c_double * 3), ("w", C.c_double * 3)]
+    _fields_ = [("c", C.c_double * 3), ("v", C.c_double * 3), ("w", C.c_double * 3),
+                ("amp", C.c_double), ("rate", C.c_double), ("kappa", C.c_double),
+                ("deform", C.c_int32), ("pad", C.c_int32)]
 
 
 class _Dynamics(C.Structure):
@@ -106,6 +108,8 @@ def lib():
         L.ora3_run_fsi.restype = C.c_int
         L.ora3_run_fsi.argtypes = [P, S, C.c_int32, B, C.POINTER(_Dynamics), C.c_int32, dp, C.c_int64,
                                    C.c_int64, dp, dp, dp]
+        L.ora3_bodies_at.restype = None
+        L.ora3_bodies_at.argtypes = [B, C.c_int32, C.c_int64, B]
         L.ora3_run_moving.restype = C.c_int
         L.ora3_run_moving.argtypes = [P, S, C.c_int32, B, C.c_int32, dp, C.c_int64, C.c_int64, dp]
         L.ora3_lattice.restype = C.c_int32
@@ -164,7 +168,9 @@ def _bodies_of(spec):
     bs = spec["bodies"]
     arr = (_Body * max(1, len(bs)))()
     for k, b in enumerate(bs):
-        arr[k] = _Body(_vec(b["c"]), _vec(b["v"]), _vec(b["w"]))
+        d = b.get("deform")
+        arr[k] = _Body(_vec(b["c"]), _vec(b["v"]), _vec(b["w"]), float(d["amplitude"]) if d else 0.0,
+                       float(d["rate"]) if d else 0.0, 0.0, 1 if d else 0, 0)
     return arr, len(bs)
 
 
@@ -222,6 +228,11 @@ class Domain:
         self.dyn, self.fsi = _dynamics_of(spec)
         if self.fsi and not self.moving:
             raise ValueError("bodies with dynamics need a moving domain")
+        deforming = any(b.get("deform") for b in spec["bodies"])
+        if deforming and not self.moving:
+            raise ValueError("deforming bodies need a moving domain")
+        if deforming and self.fsi:
+            raise ValueError("coupled bodies do not deform")
         # x[3], v[3] and the previous step's force[3] of every body (used by coupled bodies)
         self.state = np.array([list(b["c"]) + list(b["v"]) + [0.0, 0.0, 0.0] for b in spec["bodies"]],
                               dtype=np.float64).reshape(-1, 9)
@@ -308,8 +319,10 @@ class Domain:
         bodies = self.bodies
         if self.moving:
             bodies = (_Body * max(1, self.nb))()
+            lib().ora3_bodies_at(self.bodies, self.nb, self.steps_done, bodies)  # incl. kappa
             for k, row in enumerate(self.bodies_now()):
-                bodies[k] = _Body(_vec(row[0:3]), _vec(row[3:6]), _vec(row[6:9]))
+                for d in range(3):
+                    bodies[k].c[d], bodies[k].v[d] = float(row[d]), float(row[3 + d])
         lib().ora3_moments(C.byref(self.p), _u8(self.mask), bodies, _dp(self.g), _dp(rho),
                            _dp(ux), _dp(uy), _dp(uz))
         return rho, ux, uy, uz

@@ -62,6 +62,10 @@ typedef struct {
 
 typedef struct {
   double c[3], v[3], w[3]; /* centre, velocity, angular velocity */
+  /* a deforming body (deform = 1) pulsates: scale s(n) = 1 + amp sin(rate n) about its
+   * centre; kappa = s'(n) / s(n) is its dilation rate at the step being taken */
+  double amp, rate, kappa;
+  int32_t deform, pad;
 } ora3_body;
 
 typedef struct {
@@ -170,12 +174,15 @@ void ora3_stream(const ora3_params *p, const double *g, double *f) {
         for (int i = 0; i < p->nx; i++) f[IDX3(p, a, k, j, i)] = pull3(p, g, feq_inlet, a, i, j, k);
 }
 
-/* U_O = V + omega x (x - c) */
+/* U_O = V + omega x (x - c), plus kappa (x - c) for a deforming body (the velocity of its
+ * homogeneous dilation) */
 static void body_velocity3(const ora3_body *b, int i, int j, int k, double *uo) {
   double r[3] = {(double)i - b->c[0], (double)j - b->c[1], (double)k - b->c[2]};
   uo[0] = b->v[0] + (b->w[1] * r[2] - b->w[2] * r[1]);
   uo[1] = b->v[1] + (b->w[2] * r[0] - b->w[0] * r[2]);
   uo[2] = b->v[2] + (b->w[0] * r[1] - b->w[1] * r[0]);
+  if (b->deform)
+    for (int d = 0; d < 3; d++) uo[d] = uo[d] + b->kappa * r[d];
 }
 
 /* steps (3)-(5) at one node: rho, u* (Eq. rho, Eq. rho*velocity-star), penalization
@@ -267,14 +274,66 @@ int ora3_run(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
  * c_k + V_k n at step index n and each of its shapes is translated by V_k n; the step from
  * n to n + 1 uses the geometry of index n; the angular velocity acts through U_O about the
  * moving centre. */
+/* ---- deforming bodies (reading M1c in 3D) -------------------------------------------------
+ * A deforming body pulsates about its centre: at step index n its shapes are scaled by
+ * s(n) = 1 + amp sin(rate n) (|amp| < 1), radii by s(n) and each shape's offset d from the
+ * body's reference centre to s(n) d; U_O adds kappa(n) (x - c), kappa = s'/s =
+ * amp rate cos(rate n) / s(n). sin and cos are written out in FP64 (Cody and Waite's
+ * reduction by pi/2 split in three parts, the first two of 30 significant bits; Taylor
+ * series of sin and cos on [-pi/4, pi/4] to r^17 and r^16 by Horner's rule in r^2; the
+ * quadrant k mod 4), so that the mask depends on no math library. */
+static void sincos3(double t, double *s, double *c) {
+  const double P1 = 0x1.921fb54p+0, P2 = 0x1.10b46118p-30, P3 = 0x1.313198a2e037p-61;
+  const double k = nearbyint(t * 0x1.45f306dc9c883p-1);
+  const double r = ((t - k * P1) - k * P2) - k * P3;
+  const double r2 = r * r;
+  double ps = -1.0 / 1307674368000.0 + r2 * (1.0 / 355687428096000.0);
+  ps = 1.0 / 6227020800.0 + r2 * ps;
+  ps = -1.0 / 39916800.0 + r2 * ps;
+  ps = 1.0 / 362880.0 + r2 * ps;
+  ps = -1.0 / 5040.0 + r2 * ps;
+  ps = 1.0 / 120.0 + r2 * ps;
+  ps = -1.0 / 6.0 + r2 * ps;
+  const double sr = r + (r * r2) * ps;
+  double pc = -1.0 / 87178291200.0 + r2 * (1.0 / 20922789888000.0);
+  pc = 1.0 / 479001600.0 + r2 * pc;
+  pc = -1.0 / 3628800.0 + r2 * pc;
+  pc = 1.0 / 40320.0 + r2 * pc;
+  pc = -1.0 / 720.0 + r2 * pc;
+  pc = 1.0 / 24.0 + r2 * pc;
+  pc = -0.5 + r2 * pc;
+  const double cr = 1.0 + r2 * pc;
+  switch ((int)((int64_t)k & 3)) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+  }
+}
+
+static double pulse3(const ora3_body *b0, int64_t n, double *kappa) {
+  double sn, cs;
+  sincos3(b0->rate * (double)n, &sn, &cs);
+  const double sc = 1.0 + b0->amp * sn;
+  if (kappa) *kappa = ((b0->amp * b0->rate) * cs) / sc;
+  return sc;
+}
+
 static void bodies3_at(const ora3_body *b0, int32_t nbodies, int64_t n, ora3_body *out) {
   for (int k = 0; k < nbodies; k++) {
     out[k] = b0[k];
     for (int d = 0; d < 3; d++) out[k].c[d] = b0[k].c[d] + b0[k].v[d] * (double)n;
+    if (b0[k].deform) pulse3(&b0[k], n, &out[k].kappa);
   }
 }
 
-/* The mask at step index n (shapes translated with their bodies). */
+/* The body table at step index n (centres moved; dilation rates of deforming bodies). */
+void ora3_bodies_at(const ora3_body *b0, int32_t nbodies, int64_t n, ora3_body *out) {
+  bodies3_at(b0, nbodies, n, out);
+}
+
+/* The mask at step index n (shapes translated with their bodies; those of deforming bodies
+ * also scaled about the body's centre). */
 void ora3_rasterize_at(int32_t nx, int32_t ny, int32_t nz, const ora3_shape *shapes, int32_t nshapes,
                        const ora3_body *bodies, int32_t nbodies, int64_t n, uint8_t *mask) {
   ora3_shape *moved = (ora3_shape *)malloc(sizeof(ora3_shape) * (nshapes > 0 ? nshapes : 1));
@@ -282,8 +341,14 @@ void ora3_rasterize_at(int32_t nx, int32_t ny, int32_t nz, const ora3_shape *sha
   for (int q = 0; q < nshapes; q++) {
     moved[q] = shapes[q];
     const int k = shapes[q].body - 1;
-    if (k >= 0 && k < nbodies)
+    if (k >= 0 && k < nbodies && bodies[k].deform) {
+      const double sc = pulse3(&bodies[k], n, NULL);
+      for (int d = 0; d < 3; d++)
+        moved[q].c[d] = (bodies[k].c[d] + bodies[k].v[d] * (double)n) + sc * (shapes[q].c[d] - bodies[k].c[d]);
+      moved[q].radius = sc * shapes[q].radius;
+    } else if (k >= 0 && k < nbodies) {
       for (int d = 0; d < 3; d++) moved[q].c[d] = shapes[q].c[d] + bodies[k].v[d] * (double)n;
+    }
   }
   ora3_rasterize(nx, ny, nz, moved, nshapes, mask);
   free(moved);

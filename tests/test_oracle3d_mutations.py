@@ -7,6 +7,7 @@ import warnings
 
 import pytest
 
+import test_oracle3d_deform_pins as deform_pins
 import test_oracle3d_fsi_pins as fsi_pins
 import test_oracle3d_pins as pins
 import synth
@@ -55,6 +56,14 @@ MUTATIONS = [
     ("fsi_state_after_update", "        for (int d = 0; d < 3; d++) {\n          now[k].c[d] = state[9 * k + d];",
      "        for (int d = 0; d < 3; d++) {\n          now[k].c[d] = state[9 * k + d] + state[9 * k + 3 + d];"),
     ("fsi_initial_velocity_for_U_O", "          now[k].v[d] = state[9 * k + 3 + d];", "          now[k].v[d] = bodies[k].v[d];"),
+    # deforming bodies
+    ("deform_kappa_sign", "for (int d = 0; d < 3; d++) uo[d] = uo[d] + b->kappa * r[d];",
+     "for (int d = 0; d < 3; d++) uo[d] = uo[d] - b->kappa * r[d];"),
+    ("deform_kappa_not_divided", "if (kappa) *kappa = ((b0->amp * b0->rate) * cs) / sc;", "if (kappa) *kappa = (b0->amp * b0->rate) * cs;"),
+    ("deform_scale_cos", "const double sc = 1.0 + b0->amp * sn;", "const double sc = 1.0 + b0->amp * cs;"),
+    ("deform_offset_not_scaled", "+ sc * (shapes[q].c[d] - bodies[k].c[d]);", "+ (shapes[q].c[d] - bodies[k].c[d]);"),
+    ("deform_radius_not_scaled", "moved[q].radius = sc * shapes[q].radius;", "moved[q].radius = shapes[q].radius;"),
+    ("sincos3_quadrant", "case 1: *s = cr; *c = -sr; break;", "case 1: *s = cr; *c = sr; break;"),
 ]
 
 Q = (19, 15)
@@ -79,6 +88,11 @@ PINS = [
     lambda: [fsi_pins.test_infinitely_heavy_body_at_rest_is_the_fixed_body(q) for q in Q],
     lambda: [fsi_pins.test_infinitely_heavy_moving_body_is_the_prescribed_motion(q) for q in Q],
     fsi_pins.test_light_body_stays_bounded,
+    lambda: [deform_pins.test_pulsating_mask_is_the_brute_force_mask(q) for q in Q],
+    deform_pins.test_pulsating_sphere_volume,
+    lambda: [deform_pins.test_penalized_interior_moves_with_the_dilation(q) for q in Q],
+    lambda: [deform_pins.test_zero_amplitude_is_translation_bit_for_bit(q) for q in Q],
+    lambda: [deform_pins.test_pulsating_bodies_conserve_mass_and_balance_momentum(q) for q in Q],
 ]
 
 
