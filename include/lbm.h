@@ -491,6 +491,14 @@ typedef struct {
  * (lbm3_set_steps_done to another index is LBM_EINVAL). Synchronises. */
 LBM_API lbm_status lbm3_set_dynamics(lbm3_domain *d, int32_t body, const lbm3_body_dynamics *dyn);
 
+/* A body of a moving 3D domain pulsating about its centre, as lbm_batch_set_deformation in
+ * 2D: shapes scaled by s(n) = 1 + a sin(nu n) (|a| < 1), radii and each shape's offset from
+ * the body's reference centre; U_O adds kappa (x - c), kappa = a nu cos(nu n) / s(n). The
+ * dilation is isotropic, so the body must be made of spheres. Set before the first step,
+ * not with coupled bodies (LBM_EINVAL otherwise); it re-places the mask at index 0.
+ * Synchronises. */
+LBM_API lbm_status lbm3_set_deformation(lbm3_domain *d, int32_t body, double amplitude, double rate);
+
 /* The body table of the current step into host `out`, [nbodies][9] doubles: centre,
  * velocity, angular velocity (coupled bodies: the integrated state; prescribed motion:
  * c + V n). Synchronises. */

@@ -200,6 +200,11 @@ class Domain3:
                 if rc != 0:
                     self.close()
                     check(rc, "lbm3_set_dynamics")
+            if b.get("deform"):  # a pulsating body
+                rc = L.lbm3_set_deformation(h, k + 1, float(b["deform"]["amplitude"]), float(b["deform"]["rate"]))
+                if rc != 0:
+                    self.close()
+                    check(rc, "lbm3_set_deformation")
 
     def _handle(self):
         if self._h is None:

@@ -177,6 +177,7 @@ SIGNATURES = {
     "lbm3_set_steps_done": (C.c_int, [_VP, _I64]),
     "lbm3_set_dynamics": (C.c_int, [_VP, _I32, C.POINTER(BodyDynamics3)]),
     "lbm3_body_state": (C.c_int, [_VP, _DP]),
+    "lbm3_set_deformation": (C.c_int, [_VP, _I32, C.c_double, C.c_double]),
     "lbm3_coupled_state": (C.c_int, [_VP, _DP]),
     "lbm3_restore_coupled": (C.c_int, [_VP, _I64, _DP]),
     "lbm3_profile": (C.c_int, [_VP, _I32, _DP, _DP]),

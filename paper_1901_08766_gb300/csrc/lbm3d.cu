@@ -107,6 +107,13 @@ struct Dom3 {
   double *fsi;
   const double *fsi_par;
   uint32_t coupled;
+  // pulsating bodies (null / zero otherwise): [8][2] amplitude a and rate nu of
+  // s(n) = 1 + a sin(nu n); the dilation rate kappa = s'/s of the current step [8] in FP64
+  // and FP32 (zero for rigid bodies); bit b of `deform`: body b + 1 pulsates
+  const double *dpar;
+  double *kappa;
+  float *kappa_f;
+  uint32_t deform;
   // per-launch: base of each direction's array in the lattice read (src) and written (dst)
   const void *src[kQ3];
   void *dst[kQ3];
@@ -120,20 +127,36 @@ template <typename T> __device__ __forceinline__ T shift3(const Const3<T> &c, in
   return a == 0 ? c.wr0 : (a < 7 ? c.wr1 : c.wr2);
 }
 
-// U_O = V + omega x (x - c) of body b at node (i, j, k), explicitly rounded in FP64
+// U_O = V + omega x (x - c) of body b at node (i, j, k), explicitly rounded in FP64; with
+// DEF (some body pulsates) plus kappa (x - c), kappa zero for rigid bodies (the sweep is
+// instantiated without the term unless a body of the domain pulsates)
+template <bool DEF>
 __device__ __forceinline__ void body_velocity3(const Dom3 &D, int b, int i, int j, int k, double (&uo)[3]) {
   const double *q = D.bodies + 9 * (b - 1);
   const double r0 = __dsub_rn(double(i), q[0]), r1 = __dsub_rn(double(j), q[1]), r2 = __dsub_rn(double(k), q[2]);
   uo[0] = __dadd_rn(q[3], __dsub_rn(__dmul_rn(q[7], r2), __dmul_rn(q[8], r1)));
   uo[1] = __dadd_rn(q[4], __dsub_rn(__dmul_rn(q[8], r0), __dmul_rn(q[6], r2)));
   uo[2] = __dadd_rn(q[5], __dsub_rn(__dmul_rn(q[6], r1), __dmul_rn(q[7], r0)));
+  if constexpr (DEF) {
+    const double kp = D.kappa[b - 1];
+    uo[0] = __dadd_rn(uo[0], __dmul_rn(kp, r0));
+    uo[1] = __dadd_rn(uo[1], __dmul_rn(kp, r1));
+    uo[2] = __dadd_rn(uo[2], __dmul_rn(kp, r2));
+  }
 }
+template <bool DEF>
 __device__ __forceinline__ void body_velocity3(const Dom3 &D, int b, int i, int j, int k, float (&uo)[3]) {
   const float *q = D.bodies_f + 9 * (b - 1);
   const float r0 = float(i) - q[0], r1 = float(j) - q[1], r2 = float(k) - q[2];
   uo[0] = q[3] + (q[7] * r2 - q[8] * r1);
   uo[1] = q[4] + (q[8] * r0 - q[6] * r2);
   uo[2] = q[5] + (q[6] * r1 - q[7] * r0);
+  if constexpr (DEF) {
+    const float kp = D.kappa_f[b - 1];
+    uo[0] += kp * r0;
+    uo[1] += kp * r1;
+    uo[2] += kp * r2;
+  }
 }
 
 template <typename T> struct Macro3 {
@@ -378,7 +401,7 @@ template <int Q, int A, typename F> __device__ __forceinline__ void for_dirs(F &
 // broadcast loads, update, Q vector stores into the other lattice. With 16-bit storage,
 // warps without solid nodes update two nodes at once in paired FP32 (the same operations
 // in the same order on each half).
-template <int Q, int S, int V>
+template <int Q, int S, int V, bool DEF>
 __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMinBlocks)
     sweep3_kernel(const __grid_constant__ Dom3 dom, long long n, int par) {
   using Cd = Codec<S>;
@@ -471,7 +494,7 @@ __global__ void __launch_bounds__(Sweep3Shape<S>::kThreads, Sweep3Shape<S>::kMin
       if (any_solid) {
         T uo[3] = {T(0), T(0), T(0)};
         const bool solid = b[q] != 0;
-        if (solid) body_velocity3(D, b[q], xl + q, j, k, uo);
+        if (solid) body_velocity3<DEF>(D, b[q], xl + q, j, k, uo);
         m = macro3<Q, T, SHIFT, true>(x, C, solid, uo);
         collide3<Q, T, SHIFT, true>(x, m, C);
         if (solid) {
@@ -603,7 +626,11 @@ __global__ void moments3_kernel(const Dom3 *dom, int par, double *rho, double *u
   for (int a = 0; a < Q; ++a) x[a] = pull3<Q, S>(D, D.lat[par], a, i, j, k);
   const int b = D.mask[(static_cast<size_t>(k) * D.ny + j) * D.pitch + i];
   T uo[3] = {T(0), T(0), T(0)};
-  if (b) body_velocity3(D, b, i, j, k, uo);
+  // kappa exists only in moving domains: the dilation term only where a body pulsates
+  if (b) {
+    if (D.deform) body_velocity3<true>(D, b, i, j, k, uo);
+    else body_velocity3<false>(D, b, i, j, k, uo);
+  }
   const Macro3<T> m = macro3<Q, T, Cd::kShiftCompute, true>(x, const3<T>(D), b != 0, uo);
   const size_t c = (static_cast<size_t>(k) * D.ny + j) * D.nx + i;
   if (rho) rho[c] = double(m.rho * (T(1) / T(Cd::kScale)));
@@ -654,7 +681,18 @@ struct Place3 {
   int nb;
   uint32_t coupled;
   const double *xs, *c0;
+  uint32_t deform;     // bit b: body b + 1 pulsates ([8][2] amplitude and rate in dpar)
+  const double *dpar;
 };
+
+// scale s(n) = 1 + a sin(nu n) of a pulsating body (a, nu at p[0], p[1]); kappa = s'/s
+__device__ __forceinline__ double pulse3(const double *p, long long n, double *kappa) {
+  double sn, cs;
+  turn_sincos(__dmul_rn(p[1], static_cast<double>(n)), sn, cs);
+  const double sc = __dadd_rn(1.0, __dmul_rn(p[0], sn));
+  if (kappa) *kappa = __ddiv_rn(__dmul_rn(__dmul_rn(p[0], p[1]), cs), sc);
+  return sc;
+}
 
 // shape s0 at step index n: translated with its body's velocity by V n, or, for a coupled
 // body, by its integrated centre minus its reference centre, x - x0 (explicit roundings);
@@ -665,6 +703,14 @@ __device__ __forceinline__ Shape3Dev shape3_at(const Shape3Dev &s0, const Place3
   const int b = s0.body - 1;
   if (pl.coupled >> b & 1u) {
     for (int d = 0; d < 3; ++d) s.c[d] = __dadd_rn(s0.c[d], __dsub_rn(pl.xs[9 * b + d], pl.c0[3 * b + d]));
+  } else if (pl.deform >> b & 1u) {
+    // a pulsating body: the offset from its reference centre and the radius scaled by s(n)
+    const double sc = pulse3(pl.dpar + 2 * b, n, nullptr);
+    const double *v = pl.bodies9 + 9 * b + 3;
+    for (int d = 0; d < 3; ++d)
+      s.c[d] = __dadd_rn(__dadd_rn(pl.c0[3 * b + d], __dmul_rn(v[d], double(n))),
+                         __dmul_rn(sc, __dsub_rn(s0.c[d], pl.c0[3 * b + d])));
+    s.radius = __dmul_rn(sc, s0.radius);
   } else if (n != 0) {
     const double *v = pl.bodies9 + 9 * b + 3;
     for (int d = 0; d < 3; ++d) s.c[d] = __dadd_rn(s0.c[d], __dmul_rn(v[d], double(n)));
@@ -701,6 +747,12 @@ __device__ __forceinline__ double centre3(const Dom3 &D, int b, int d, long long
 // FP32, for bodies b = b0, b0 + stride, ...
 __device__ __forceinline__ void place_bodies3(const Dom3 &D, long long n, int b0, int stride) {
   for (int b = b0; b < D.nbodies; b += stride) {
+    if (D.deform >> b & 1u) {  // the dilation rate of step n
+      double kp;
+      pulse3(D.dpar + 2 * b, n, &kp);
+      D.kappa[b] = kp;
+      D.kappa_f[b] = float(kp);
+    }
     const bool cpl = D.coupled >> b & 1u;
     const double *st = cpl ? fsi_row3(D, b, n) : nullptr;
     for (int d = 0; d < 3; ++d) {
@@ -885,7 +937,8 @@ __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const __grid_cons
   // every shape at n + 1, translated once per block (FP64, explicit roundings)
   __shared__ Shape3Dev sh[kMaxShapes3];
   __shared__ float shc[kMaxShapes3][3];
-  const Place3 pl{D.bodies, D.nbodies, D.coupled, D.fsi ? fsi_row3(D, 0, n + 1) : nullptr, D.centre0};
+  const Place3 pl{D.bodies, D.nbodies, D.coupled, D.fsi ? fsi_row3(D, 0, n + 1) : nullptr, D.centre0, D.deform,
+                  D.dpar};
   for (int q = threadIdx.x; q < D.nshapes; q += blockDim.x) {
     sh[q] = shape3_at(D.shapes[q], pl, n + 1);
     for (int d = 0; d < 3; ++d) shc[q][d] = float(sh[q].c[d]);
@@ -1049,7 +1102,28 @@ struct Layout3 {
 size_t moving_bytes3() {
   return up(sizeof(Shape3Dev) * kMaxShapes3, 256) + up(sizeof(double) * 3 * kMaxMoving3, 256) +
          up(sizeof(double) * 3 * kMaxMoving3 * kMaxMoveBlocks3, 256) + up(sizeof(uint32_t) * kMaxMoving3, 256) +
-         up(sizeof(double) * 9 * 2 * kMaxMoving3, 256) + up(sizeof(double) * 12 * kMaxMoving3, 256);
+         up(sizeof(double) * 9 * 2 * kMaxMoving3, 256) + up(sizeof(double) * 12 * kMaxMoving3, 256) +
+         up(sizeof(double) * 3 * kMaxMoving3 + sizeof(float) * kMaxMoving3, 256);
+}
+
+// Half extents of the box body b's shapes reach about its centre c (null: no body), two
+// nodes wide beyond the shapes, the offsets and radii grown by `grow` (1 + |a| for a
+// pulsating body); a z-cylinder spans the whole z axis (< 0)
+void set_mbox3(Dom3 &D, const std::vector<Shape3Dev> &shapes, int b, const double *c, double grow) {
+  for (int e = 0; e < 3; ++e) D.mbox[b][e] = 0.f;
+  if (!c) return;
+  for (const Shape3Dev &s : shapes) {
+    if (s.body - 1 != b) continue;
+    for (int e = 0; e < 3; ++e) {
+      if (e == 2 && s.kind == LBM3_SHAPE_CYLINDER_Z) {
+        D.mbox[b][2] = -1.f;
+        continue;
+      }
+      if (D.mbox[b][e] < 0.f) continue;
+      const double h = grow * (std::fabs(s.c[e] - c[e]) + s.radius) + 2.0;
+      D.mbox[b][e] = std::max(D.mbox[b][e], static_cast<float>(h));
+    }
+  }
 }
 
 Layout3 layout3(const lbm3_params &p, int nb) {
@@ -1109,6 +1183,7 @@ struct lbm3_domain {
   lbm_free_fn ffn = nullptr;
   void *actx = nullptr;
   void *block = nullptr, *frows = nullptr, *rowsum = nullptr;
+  std::vector<Shape3Dev> hshapes;  // moving domains: the reference shapes (body boxes)
   Dom3 h{};
   Dom3 hpar[2]{};  // sweep parameters reading lattice 0 resp. 1
   Dom3 *d_dom = nullptr;
@@ -1138,7 +1213,8 @@ namespace {
 
 template <int Q, int S> cudaError_t launch_sweep3_as(lbm3_domain *d, long long n, int par) {
   using Sh = Sweep3Shape<S>;
-  sweep3_kernel<Q, S, Sh::kV><<<d->grid, Sh::kThreads, 0, d->st>>>(d->hpar[par], n, par);
+  if (d->h.deform) sweep3_kernel<Q, S, Sh::kV, true><<<d->grid, Sh::kThreads, 0, d->st>>>(d->hpar[par], n, par);
+  else sweep3_kernel<Q, S, Sh::kV, false><<<d->grid, Sh::kThreads, 0, d->st>>>(d->hpar[par], n, par);
   return cudaGetLastError();
 }
 
@@ -1217,7 +1293,7 @@ lbm_status validate3(const lbm3_params *p, int nb, int ns, const lbm3_shape *sha
 template <int Q, int S> int sweep3_blocks_as(int sms) {
   using Sh = Sweep3Shape<S>;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<Q, S, Sh::kV>, Sh::kThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep3_kernel<Q, S, Sh::kV, false>, Sh::kThreads, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     n = 1;
@@ -1436,6 +1512,11 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
     mb += up(sizeof(double) * 9 * 2 * kMaxMoving3, 256);
     D.fsi_par = reinterpret_cast<const double *>(mb);
     D.coupled = 0u;
+    mb += up(sizeof(double) * 12 * kMaxMoving3, 256);
+    D.dpar = reinterpret_cast<const double *>(mb);
+    D.kappa = reinterpret_cast<double *>(mb) + 2 * kMaxMoving3;
+    D.kappa_f = reinterpret_cast<float *>(D.kappa + kMaxMoving3);
+    D.deform = 0u;
     ADM3(cudaMemsetAsync(base + L.moving_off, 0, moving_bytes3(), st));
     ADM3(cudaMemcpyAsync(const_cast<Shape3Dev *>(D.shapes), hs.data(), sizeof(Shape3Dev) * nshapes,
                          cudaMemcpyHostToDevice, st));
@@ -1444,29 +1525,15 @@ lbm_status lbm3_domain_create(const lbm3_params *p, const lbm3_shape *shapes, in
       for (int e = 0; e < 3; ++e) c0[3 * q + e] = bodies[q].c[e];
     ADM3(cudaMemcpyAsync(const_cast<double *>(D.centre0), c0.data(), sizeof(double) * c0.size(),
                          cudaMemcpyHostToDevice, st));
-    // per body: half extents of the box its shapes reach about its centre, two nodes wide
-    // beyond the shapes (a z-cylinder spans the whole z axis)
-    for (int b = 0; b < kMaxMoving3; ++b)
-      for (int e = 0; e < 3; ++e) D.mbox[b][e] = 0.f;
-    for (int q = 0; q < nshapes; ++q) {
-      const int b = shapes[q].body - 1;
-      for (int e = 0; e < 3; ++e) {
-        if (e == 2 && shapes[q].kind == LBM3_SHAPE_CYLINDER_Z) {
-          D.mbox[b][2] = -1.f;
-          continue;
-        }
-        if (D.mbox[b][e] < 0.f) continue;
-        const double h = std::fabs(shapes[q].c[e] - bodies[b].c[e]) + shapes[q].radius + 2.0;
-        D.mbox[b][e] = std::max(D.mbox[b][e], static_cast<float>(h));
-      }
-    }
+    d->hshapes.assign(hs.begin(), hs.begin() + nshapes);
+    for (int b = 0; b < kMaxMoving3; ++b) set_mbox3(D, d->hshapes, b, b < nbodies ? bodies[b].c : nullptr, 1.0);
   }
   dsh = d->get(sizeof(Shape3Dev) * hs.size());
   if (!dsh) return bail(fail3(LBM_ENOMEM, "shape buffer allocation failed"));
   ADM3(cudaMemcpyAsync(dsh, hs.data(), sizeof(Shape3Dev) * hs.size(), cudaMemcpyHostToDevice, st));
   rasterize3_kernel<<<dim3((d->pitch + 127) / 128, p->ny, p->nz), 128, 0, st>>>(
       D.mask, p->nx, p->ny, p->nz, d->pitch, static_cast<const Shape3Dev *>(dsh), nshapes,
-      Place3{D.bodies, nbodies, 0u, nullptr, nullptr}, 0);
+      Place3{D.bodies, nbodies, 0u, nullptr, nullptr, 0u, nullptr}, 0);
   ADM3(cudaGetLastError());
   // rows that hold solid nodes (the force reduction visits only those)
   const size_t cells = static_cast<size_t>(d->pitch) * p->ny * p->nz;
@@ -1666,7 +1733,8 @@ static lbm_status place_at3(lbm3_domain *d, int64_t steps) {
   if (d->p.moving) {  // the mask and body table of that step index
     const Dom3 &D = d->h;
     const Place3 pl{D.bodies, d->nbodies, D.coupled,
-                    D.fsi ? D.fsi + static_cast<size_t>(steps & 1) * kMaxMoving3 * 9 : nullptr, D.centre0};
+                    D.fsi ? D.fsi + static_cast<size_t>(steps & 1) * kMaxMoving3 * 9 : nullptr, D.centre0, D.deform,
+                    D.dpar};
     rasterize3_kernel<<<dim3((d->pitch + 127) / 128, d->p.ny, d->p.nz), 128, 0, d->st>>>(
         D.mask, d->p.nx, d->p.ny, d->p.nz, d->pitch, D.shapes, D.nshapes, pl, steps);
     LBM3_CUDA(cudaGetLastError());
@@ -1693,6 +1761,7 @@ lbm_status lbm3_set_dynamics(lbm3_domain *d, int32_t body, const lbm3_body_dynam
   if (!d->p.moving) return fail3(LBM_EINVAL, "coupled bodies need a moving domain");
   if (d->p.force_every != 1) return fail3(LBM_EINVAL, "coupled bodies need the force of every step (force_every = 1)");
   if (d->done != 0) return fail3(LBM_EINVAL, "dynamics are set before the first step");
+  if (d->h.deform) return fail3(LBM_EINVAL, "a domain with pulsating bodies cannot have coupled bodies");
   if (body < 1 || body > d->nbodies) return fail3(LBM_EINVAL, "body %d outside 1..%d", body, d->nbodies);
   if (!(dyn->mass > 0.0) || !std::isfinite(dyn->mass)) return fail3(LBM_EINVAL, "mass must be finite and > 0");
   for (int e = 0; e < 3; ++e) {
@@ -1718,6 +1787,34 @@ lbm_status lbm3_set_dynamics(lbm3_domain *d, int32_t body, const lbm3_body_dynam
   LBM3_CUDA(cudaMemcpyAsync(d->d_dom, &d->h, sizeof(Dom3), cudaMemcpyHostToDevice, d->st));
   LBM3_CUDA(cudaStreamSynchronize(d->st));
   return LBM_OK;
+}
+
+lbm_status lbm3_set_deformation(lbm3_domain *d, int32_t body, double amplitude, double rate) {
+  if (!d) return fail3(LBM_EINVAL, "domain is NULL");
+  if (!d->p.moving) return fail3(LBM_EINVAL, "pulsating bodies need a moving domain");
+  if (d->done != 0) return fail3(LBM_EINVAL, "a deformation is set before the first step");
+  if (d->h.coupled) return fail3(LBM_EINVAL, "coupled bodies do not deform");
+  if (body < 1 || body > d->nbodies) return fail3(LBM_EINVAL, "body %d outside 1..%d", body, d->nbodies);
+  if (!(std::fabs(amplitude) < 1.0) || !std::isfinite(rate))
+    return fail3(LBM_EINVAL, "the amplitude must satisfy |a| < 1 and the rate be finite");
+  const int b = body - 1;
+  for (const Shape3Dev &s : d->hshapes)
+    if (s.body == body && s.kind != LBM3_SHAPE_SPHERE)
+      return fail3(LBM_EINVAL, "a pulsating body is made of spheres (its dilation is isotropic)");
+  double c0[3];
+  LBM3_CUDA(cudaMemcpyAsync(c0, d->h.centre0 + 3 * b, sizeof(c0), cudaMemcpyDeviceToHost, d->st));
+  LBM3_CUDA(cudaStreamSynchronize(d->st));
+  const double par[2] = {amplitude, rate};
+  LBM3_CUDA(cudaMemcpyAsync(const_cast<double *>(d->h.dpar) + 2 * b, par, sizeof(par), cudaMemcpyHostToDevice,
+                            d->st));
+  d->h.deform |= 1u << b;
+  set_mbox3(d->h, d->hshapes, b, c0, 1.0 + std::fabs(amplitude));
+  for (int q = 0; q < 2; ++q) {
+    d->hpar[q].deform = d->h.deform;
+    for (int e = 0; e < 3; ++e) d->hpar[q].mbox[b][e] = d->h.mbox[b][e];
+  }
+  LBM3_CUDA(cudaMemcpyAsync(d->d_dom, &d->h, sizeof(Dom3), cudaMemcpyHostToDevice, d->st));
+  return place_at3(d, 0);  // the mask, centres and dilation rates of index 0
 }
 
 lbm_status lbm3_body_state(lbm3_domain *d, double *out) {
