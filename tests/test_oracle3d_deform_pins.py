@@ -57,9 +57,10 @@ def _brute(spec, n, margin=1e-9):
 @pytest.mark.parametrize("q", LATTICES)
 def test_pulsating_mask_is_the_brute_force_mask(q):
     shapes = [synth.sphere(1, (14.3, 12.2, 11.6), 5.0), synth.sphere(1, (21.3, 12.2, 11.6), 2.5),
-              synth.cylinder_z(2, 36.0, 13.0, 3.5)]
+              synth.sphere(2, (36.0, 13.0, 12.1), 3.5), synth.cylinder_z(3, 44.0, 6.0, 2.0)]
     bodies = [_pulsing(synth.body3((15.3, 12.2, 11.6), 10.0, v=(0.03, -0.01, 0.02)), 0.3, 0.05),
-              _pulsing(synth.body3((36.0, 13.0, 0.0), 7.0, v=(-0.02, 0.0, 0.0)), -0.25, 0.08)]
+              _pulsing(synth.body3((36.0, 13.0, 12.1), 7.0, v=(-0.02, 0.0, 0.0)), -0.25, 0.08),
+              synth.body3((44.0, 6.0, 0.0), 4.0, v=(0.0, 0.01, 0.0))]
     sp = _spec((48, 26, 24), shapes, bodies, q=q)
     for n in (0, 9, 31, 200):
         got = d3.rasterize(sp, n)
@@ -101,7 +102,7 @@ def test_penalized_interior_moves_with_the_dilation(q):
 def test_zero_amplitude_is_translation_bit_for_bit(q):
     shapes = [synth.sphere(1, (10.3, 9.2, 8.7), 4.0), synth.cylinder_z(2, 24.0, 10.0, 3.0)]
     rigid = [synth.body3((10.3, 9.2, 8.7), 8.0, v=(0.05, 0.02, -0.03)), synth.body3((24.0, 10.0, 0.0), 6.0, v=(-0.04, 0.0, 0.0))]
-    flat = [_pulsing(rigid[0], 0.0, 0.05), _pulsing(rigid[1], 0.0, 0.03)]
+    flat = [_pulsing(rigid[0], 0.0, 0.05), rigid[1]]
     g0 = synth.random_populations3(7, 32, 20, 18, q=q)
     a = d3.Domain(_spec((32, 20, 18), shapes, rigid, q=q), g=g0)
     b = d3.Domain(_spec((32, 20, 18), shapes, flat, q=q), g=g0)
@@ -111,9 +112,9 @@ def test_zero_amplitude_is_translation_bit_for_bit(q):
 
 @pytest.mark.parametrize("q", LATTICES)
 def test_pulsating_bodies_conserve_mass_and_balance_momentum(q):
-    shapes = [synth.sphere(1, (8.2, 9.1, 7.3), 3.5), synth.cylinder_z(2, 19.5, 8.0, 2.5)]
+    shapes = [synth.sphere(1, (8.2, 9.1, 7.3), 3.5), synth.sphere(2, (19.5, 8.0, 7.6), 2.5)]
     bodies = [_pulsing(synth.body3((8.2, 9.1, 7.3), 7.0, v=(0.03, 0.01, -0.02)), 0.3, 0.07),
-              _pulsing(synth.body3((19.5, 8.0, 0.0), 5.0, w=(0.0, 0.0, 0.02)), -0.3, 0.11)]
+              _pulsing(synth.body3((19.5, 8.0, 7.6), 5.0, w=(0.0, 0.0, 0.02)), -0.3, 0.11)]
     sp = _spec((26, 17, 15), shapes, bodies, q=q, lam=0.25)
     d = d3.Domain(sp, g=synth.random_populations3(5, 26, 17, 15, q=q))
     ex, ey, ez, _, _ = d3.lattice(q)
@@ -128,3 +129,18 @@ def test_pulsating_bodies_conserve_mass_and_balance_momentum(q):
             assert abs((j1[c] - j0[c]) + net[c]) < 1e-14 * d.g[0].size
     assert abs(d.g.sum() - m0) < 1e-12 * m0
     assert (d.mask == 1).sum() != (d3.rasterize(sp, 0) == 1).sum()
+
+
+def test_oracle_rejects_pulsating_cylinders_and_coupled_pulsation():
+    cyl = _spec((20, 16, 12), [synth.cylinder_z(1, 10.0, 8.0, 3.0)],
+                [_pulsing(synth.body3((10.0, 8.0, 0.0), 6.0), 0.1, 0.05)])
+    with pytest.raises(ValueError):  # isotropic dilation: spheres only
+        d3.Domain(cyl)
+    b = _pulsing(synth.body3((10.0, 8.0, 6.0), 6.0), 0.1, 0.05)
+    b["dynamics"] = {"mass": 1e3, "stiffness": (0.0, 0.0, 0.0), "damping": (0.0, 0.0, 0.0), "free": (1, 1, 1)}
+    with pytest.raises(ValueError):  # coupled bodies do not deform
+        d3.Domain(_spec((20, 16, 12), [synth.sphere(1, (10.0, 8.0, 6.0), 3.0)], [b]))
+    fixed = dict(_spec((20, 16, 12), [synth.sphere(1, (10.0, 8.0, 6.0), 3.0)],
+                       [_pulsing(synth.body3((10.0, 8.0, 6.0), 6.0), 0.1, 0.05)]), moving=False)
+    with pytest.raises(ValueError):  # a fixed mask does not pulsate
+        d3.Domain(fixed)

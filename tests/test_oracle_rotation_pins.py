@@ -149,3 +149,16 @@ def test_turning_bodies_conserve_mass_and_balance_momentum(lam):
         assert abs((jy1 - jy0) + net[1]) < 1e-14 * 64 * 38
     assert abs(d.g.sum() - m0) < 1e-12 * m0
     assert not np.array_equal(d.mask, oracle.rasterize(dict(sp, moving=True), 60))
+
+
+def test_oracle_rejects_turning_or_pulsating_coupled_bodies():
+    b = synth._body(20.0, 15.0, 10.0, omega=0.01)
+    b["dynamics"] = synth.dynamics(1e3)
+    with pytest.raises(ValueError):  # coupled bodies translate their shapes only
+        oracle.Domain(_spec(40, 30, [synth._circle(1, 20.0, 15.0, 5.0)], [b]))
+    p = dict(synth._body(20.0, 15.0, 10.0), deform={"amplitude": 0.1, "rate": 0.02})
+    with pytest.raises(ValueError):  # a fixed mask does not pulsate
+        oracle.Domain(_spec(40, 30, [synth._circle(1, 20.0, 15.0, 5.0)], [p], moving=False))
+    p["dynamics"] = synth.dynamics(1e3)
+    with pytest.raises(ValueError):  # coupled bodies do not deform
+        oracle.Domain(_spec(40, 30, [synth._circle(1, 20.0, 15.0, 5.0)], [p], moving=True))
