@@ -60,18 +60,21 @@ cudaError_t launch_rasterize(cudaStream_t st, uint8_t *mask, int nx, int ny, int
   return cudaGetLastError();
 }
 
-// ---- moving domains (prescribed translation) ------------------------------------------------
+// ---- moving domains (prescribed translation, turning and pulsating shapes) ------------------
 // chi(x, t) and U_O(x, t) of a domain whose bodies translate (Sec. 2.2): at step index n
-// body k is centred at c_k + V_k n and each of its shapes is translated by V_k n. The
+// body k is centred at c_k + V_k n and each of its shapes is translated by V_k n (turned
+// by omega_k n about the centre in a rotating domain, scaled by s_k(n) for a pulsating
+// body: shape_turned below). The
 // step from n to n + 1 uses the geometry of index n; after its sweep, one warp per row
 // (a fixed mapping, so the result does not depend on the launch) first sums -F_VP over
 // the row's nodes of each body under the mask the sweep used (FP64, lane-strided then a
 // fixed shuffle tree; the force kernel adds the rows in order), then rewrites the row's
 // mask for index n + 1. Both touch only the columns that some shape reaches (its
 // reference point within radius or chord + 1) at index n or n + 1: nothing else can be
-// solid. Each node is read and rewritten by the same lane. The warp of row 0 moves the
-// body centres. Positions are c + V n with explicitly rounded FP64
-// operations, as a plain evaluation on the host computes them.
+// solid (a turning or pulsating shape: within its grown reach of the body centre). Each
+// node is read and rewritten by the same lane. The warp of row 0 moves the body table.
+// Positions are c + V n with explicitly rounded FP64 operations, as a plain evaluation on
+// the host computes them.
 
 constexpr int kMoveWarps = 8;
 
