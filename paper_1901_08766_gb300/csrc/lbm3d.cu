@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "lbm_sweep.cuh"
+#include "lbm_turn.cuh"
 
 namespace lbm {
 namespace d3 {

@@ -2,6 +2,7 @@
 // function), initial state (step (1)), solid-node lists, the FP64 body-force reducer
 // (Sec. 3 drag and lift sums) and the moments export.
 #include "lbm_cell.cuh"
+#include "lbm_turn.cuh"
 
 namespace lbm {
 
