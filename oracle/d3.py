@@ -231,6 +231,9 @@ class Domain:
         deforming = any(b.get("deform") for b in spec["bodies"])
         if deforming and not self.moving:
             raise ValueError("deforming bodies need a moving domain")
+        for s in spec["shapes"]:
+            if s["kind"] != "sphere" and spec["bodies"][s["body"] - 1].get("deform"):
+                raise ValueError("a pulsating 3D body is made of spheres (its dilation is isotropic)")
         if deforming and self.fsi:
             raise ValueError("coupled bodies do not deform")
         # x[3], v[3] and the previous step's force[3] of every body (used by coupled bodies)

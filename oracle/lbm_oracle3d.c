@@ -277,7 +277,8 @@ int ora3_run(const ora3_params *p, const uint8_t *mask, const ora3_body *bodies,
 /* ---- deforming bodies (reading M1c in 3D) -------------------------------------------------
  * A deforming body pulsates about its centre: at step index n its shapes are scaled by
  * s(n) = 1 + amp sin(rate n) (|amp| < 1), radii by s(n) and each shape's offset d from the
- * body's reference centre to s(n) d; U_O adds kappa(n) (x - c), kappa = s'/s =
+ * body's reference centre to s(n) d; the dilation is isotropic, so such a body is made of
+ * spheres (an infinite z-cylinder has no centre along z); U_O adds kappa(n) (x - c), kappa = s'/s =
  * amp rate cos(rate n) / s(n). sin and cos are written out in FP64 (Cody and Waite's
  * reduction by pi/2 split in three parts, the first two of 30 significant bits; Taylor
  * series of sin and cos on [-pi/4, pi/4] to r^17 and r^16 by Horner's rule in r^2; the
