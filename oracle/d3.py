@@ -108,6 +108,8 @@ def lib():
         L.ora3_run_fsi.restype = C.c_int
         L.ora3_run_fsi.argtypes = [P, S, C.c_int32, B, C.POINTER(_Dynamics), C.c_int32, dp, C.c_int64,
                                    C.c_int64, dp, dp, dp]
+        L.ora3_sincos.restype = None
+        L.ora3_sincos.argtypes = [C.c_double, dp, dp]
         L.ora3_bodies_at.restype = None
         L.ora3_bodies_at.argtypes = [B, C.c_int32, C.c_int64, B]
         L.ora3_run_moving.restype = C.c_int
@@ -189,6 +191,13 @@ def guo(u, F, q=19):
     lib().ora3_guo(nq(q), _dp(np.ascontiguousarray(u, dtype=np.float64)),
                    _dp(np.ascontiguousarray(F, dtype=np.float64)), _dp(out))
     return out
+
+
+def sincos(t: float):
+    """(sin t, cos t) of the 3D oracle's own FP64 evaluation (reduction by pi/2, Taylor)."""
+    s, c = C.c_double(), C.c_double()
+    lib().ora3_sincos(float(t), C.byref(s), C.byref(c))
+    return s.value, c.value
 
 
 def rasterize(spec, step=None):

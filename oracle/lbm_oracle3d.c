@@ -312,6 +312,8 @@ static void sincos3(double t, double *s, double *c) {
   }
 }
 
+void ora3_sincos(double t, double *s, double *c) { sincos3(t, s, c); }
+
 static double pulse3(const ora3_body *b0, int64_t n, double *kappa) {
   double sn, cs;
   sincos3(b0->rate * (double)n, &sn, &cs);

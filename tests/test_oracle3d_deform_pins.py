@@ -144,3 +144,12 @@ def test_oracle_rejects_pulsating_cylinders_and_coupled_pulsation():
                        [_pulsing(synth.body3((10.0, 8.0, 6.0), 6.0), 0.1, 0.05)]), moving=False)
     with pytest.raises(ValueError):  # a fixed mask does not pulsate
         d3.Domain(fixed)
+
+
+def test_sincos_against_the_c_library_and_the_2d_oracle():
+    import oracle
+    for t in np.concatenate([np.linspace(-2e4, 2e4, 40001), np.linspace(-6.5, 6.5, 13001)]):
+        s, c = d3.sincos(float(t))
+        for mine, ref in ((s, math.sin(t)), (c, math.cos(t))):
+            assert abs(mine - ref) <= 2.0 * math.ulp(max(abs(ref), 2.0 ** -60)), (t, mine, ref)
+        assert (s, c) == oracle.sincos(float(t))  # the same published method, the same bits

@@ -90,6 +90,7 @@ PINS = [
     fsi_pins.test_light_body_stays_bounded,
     lambda: [deform_pins.test_pulsating_mask_is_the_brute_force_mask(q) for q in Q],
     deform_pins.test_pulsating_sphere_volume,
+    deform_pins.test_sincos_against_the_c_library_and_the_2d_oracle,
     lambda: [deform_pins.test_penalized_interior_moves_with_the_dilation(q) for q in Q],
     lambda: [deform_pins.test_zero_amplitude_is_translation_bit_for_bit(q) for q in Q],
     lambda: [deform_pins.test_pulsating_bodies_conserve_mass_and_balance_momentum(q) for q in Q],
