@@ -9,8 +9,10 @@ node counted, solid nodes included).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line. Under torchrun (N > 1) every rank runs its own copy of the
-domain set (weak scaling, no data-path collective), timing is max over ranks.
+Prints one JSON line. Under torchrun (N > 1) the domain set is sharded over the ranks,
+balanced by node count (strong scaling over the batch; `--replicas copy` gives every rank
+its own full copy instead, weak scaling); the domains are independent, so there is no
+data-path collective; the time is the max over ranks, the nodes are summed.
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded sample of
 the same workload.
 """
@@ -52,24 +54,44 @@ def _dist():
     return ws, rank
 
 
-def rank_domains(specs, rank, world):
-    """Weak scaling: every rank advances its own full copy of the domain set (the domains
-    are independent problems; no data-path exchange between ranks)."""
-    del rank, world
-    return list(specs)
+def rank_domains(specs, rank, world, mode="shard"):
+    """The domains rank `rank` of `world` advances. The domains are independent problems,
+    so no data-path exchange between ranks is needed.
+
+    mode "shard" (default, strong scaling over the batch): a disjoint subset per rank,
+    balanced by node count (largest domain first onto the least loaded rank, ties to the
+    lower rank); the union over ranks is the whole set. mode "copy" (weak scaling): every
+    rank advances its own full copy of the set."""
+    specs = list(specs)
+    if mode == "copy" or world <= 1:
+        return specs
+    if mode != "shard":
+        raise ValueError(f"unknown mode {mode!r}")
+    load = [0] * world
+    owner = {}
+    order = sorted(range(len(specs)), key=lambda i: (-specs[i]["nx"] * specs[i]["ny"], i))
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        owner[i] = r
+        load[r] += specs[i]["nx"] * specs[i]["ny"]
+    return [specs[i] for i in range(len(specs)) if owner[i] == rank]
 
 
-def aggregate(ms_local, cells_per_rank, steps, world, device="cpu"):
-    """Whole-job GLUPS from the per-rank timed region: the time is the max over ranks
-    (all_reduce MAX on an initialised process group when world > 1)."""
+def aggregate(ms_local, cells_local, steps, world, device="cpu"):
+    """Whole-job GLUPS from the per-rank timed region: the time is the max over ranks and
+    the nodes are summed over ranks (all_reduce on an initialised process group when
+    world > 1). Returns (ms, GLUPS, total nodes)."""
     import torch
     ms = float(ms_local)
+    cells = float(cells_local)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms, cells_per_rank * world * steps / (ms / 1000.0) / 1e9
+        c = torch.tensor([cells], dtype=torch.float64, device=device)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        ms, cells = float(t.item()), float(c.item())
+    return ms, cells * steps / (ms / 1000.0) / 1e9, int(cells)
 
 
 class ClockSampler:
@@ -201,10 +223,12 @@ def _config(args, specs, extra=None):
     c = {"workload": "batched uneven domains: 64 seeded tandem/side-by-side cylinder pairs, "
                      "W 400..2000, H = W/2, Re 40..200, D = 40, U = 0.05",
          "domains": len(specs), "cells": cells, "storage": args.storage, "moving": args.moving or False,
-         "forces": "every step, FP64 per body", "graph_steps": args.graph_steps,
+         "forces": "every step, FP64 per body", "graph_steps": getattr(args, "graph_used", args.graph_steps),
          "l2": "inputs larger than L2 (working set %.2f GB per step)" %
                (cells * BYTES_PER_CELL[args.storage] / 1e9),
-         "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+         "parallelism": ("single GPU" if args.gpus <= 1 else
+                         f"domains sharded over {args.gpus} GPUs (cell-balanced, no collective)"
+                         if args.replicas == "shard" else f"replicas x{args.gpus}")}
     if extra:
         c["note"] = extra
     return c
@@ -222,7 +246,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     lbm.load()
-    specs = rank_domains(synth.batched_domains(64)[: args.domains], rank, ws)
+    specs = rank_domains(synth.batched_domains(64)[: args.domains], rank, ws, args.replicas)
     if args.moving:
         # every domain carries the per-step geometry update of moving bodies (velocities
         # unchanged, so the flow is the same): measures the cost of the update
@@ -235,8 +259,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     nsteps_total = args.warmup + args.steps + args.profile_steps + 10
 
+    # the timed steps replay CUDA graphs of at most `steps` steps, captured before the
+    # timed region
+    args.graph_used = min(args.graph_steps, args.steps)
     with torch.cuda.stream(stream):
-        batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_steps, stream=stream)
+        batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_used, stream=stream)
         slots = [batch.admit(s, nsteps=nsteps_total, force_capacity=nsteps_total + 8) for s in specs]
         if args.tile:
             batch.set_tile(*[int(x) for x in args.tile.split(",")])
@@ -246,6 +273,7 @@ def run_ours(args):
         batch.run(args.warmup)
         for k in slots:
             batch.poll(k)
+        batch.capture()
         stream.synchronize()
         launches0 = batch.info()["kernel_launches"]
         sampler = ClockSampler(local)
@@ -273,7 +301,7 @@ def run_ours(args):
             _, _ = batch.poll(k)
         batch.close()
 
-    ms, value = aggregate(ms, cells, args.steps, ws, device="cuda")
+    ms, value, cells_all = aggregate(ms, cells, args.steps, ws, device="cuda")
     peak, peak_kind = _peak_hbm()
     bpc = BYTES_PER_CELL[args.storage]
     achieved = cells * bpc / (sweep_us * 1e-6) / 1e9
@@ -302,7 +330,8 @@ def run_ours(args):
         return 0
     line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f16s storage, f32 compute"
+            "scaling": "strong" if args.replicas == "shard" else "weak", "vs_baseline": None,
+            "dtype": "f16s storage, f32 compute"
             if args.storage == "f16s" else args.storage, "data": "synthetic",
             "config": dict(_config(args, specs), tile={"vec": tile[0], "warps": tile[1], "rows": tile[2],
                                                        "pipeline": ["direct", "tma", "prefetch"][tile[3]]},
@@ -322,7 +351,10 @@ def measure_e2e(lbm, torch, specs, args):
     with torch.cuda.stream(stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_steps, stream=stream)
+        # a job of few steps launches directly (capturing a graph would cost more than it
+        # saves); longer jobs replay graphs, their capture included
+        gsteps = args.graph_steps if steps >= 4 * args.graph_steps else 0
+        batch = lbm.Batch(args.storage, max_domains=64, graph_steps=gsteps, stream=stream)
         slots = [batch.admit(s, nsteps=steps, force_capacity=steps + 8) for s in specs]
         if getattr(args, "tuned_tile", None):
             batch.set_tile(*args.tuned_tile)
@@ -340,7 +372,9 @@ def measure_e2e(lbm, torch, specs, args):
     h2d = sum(120 + 56 * len(s["shapes"]) + 48 * len(s["bodies"]) for s in specs)
     return {"value": cells * steps / el / 1e9, "unit": "GLUPS",
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": nbytes_out / steps,
-            "includes": "batch creation, admission (rasterise + init), steps, force readback"}
+            "graph_steps": gsteps,
+            "includes": "batch creation, admission of every domain from host geometry "
+                        "(rasterise, solid lists, init), the steps, force readback"}
 
 
 def measure_served(lbm, torch, args, plain=None):
@@ -378,16 +412,24 @@ def measure_served(lbm, torch, args, plain=None):
 
 
 def measure_plain_f32(lbm, torch, specs, args, steps=30):
-    """The plain per-domain FP32 baseline: the same domains run one at a time in FP32,
-    one launch per kernel (no graphs, no batching); aggregate GLUPS of the sweeps."""
+    """The plain per-domain FP32 baseline: every domain of the set run on its own in FP32,
+    one launch per kernel and step (no graphs, no batching), with the FP32 tile shape the
+    autotuner picks on the median-sized domain; aggregate GLUPS of the sweeps and their
+    fraction of FP32's own roofline (73 B per node)."""
     stream = torch.cuda.Stream()
     total_cells_steps = 0
     total_s = 0.0
+    by_size = sorted(specs, key=lambda sp: sp["nx"] * sp["ny"])
     with torch.cuda.stream(stream):
-        for s in specs[:: max(1, len(specs) // 16)]:
+        b = lbm.Batch("f32", max_domains=1, graph_steps=0, stream=stream)
+        b.admit(by_size[len(by_size) // 2], nsteps=10**6, force_capacity=64)
+        b.autotune(reps=3)
+        tile = b.get_tile()
+        b.close()
+        for s in specs:
             b = lbm.Batch("f32", max_domains=1, graph_steps=0, stream=stream)
             k = b.admit(s, nsteps=steps + 5, force_capacity=steps + 8)
-            b.set_tile(4, 8, 2, 0)
+            b.set_tile(*tile)
             b.run(5)
             stream.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -399,9 +441,12 @@ def measure_plain_f32(lbm, torch, specs, args, steps=30):
             total_s += e0.elapsed_time(e1) / 1000.0
             total_cells_steps += s["nx"] * s["ny"] * steps
             b.close()
-    return {"value": total_cells_steps / total_s / 1e9, "unit": "GLUPS",
-            "sample": "16 of the 64 domains, one at a time, FP32 storage, no graphs, "
-                      f"{steps} steps each"}
+    value = total_cells_steps / total_s / 1e9
+    peak, _ = _peak_hbm()
+    return {"value": value, "unit": "GLUPS", "hbm_frac_at_73_bytes": value * 73 / peak,
+            "tile": {"vec": tile[0], "warps": tile[1], "rows": tile[2], "pipeline": tile[3]},
+            "sample": f"all {len(specs)} domains, one at a time, FP32 storage, one launch per "
+                      f"kernel and step (no graphs), {steps} steps each, autotuned FP32 tile"}
 
 
 # ---- accuracy experiments on the paper's workloads ----------------------------------------
@@ -790,6 +835,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f16s", "bf16s", "f32", "f64"], default="f16s")
     ap.add_argument("--graph-steps", type=int, default=32)
+    ap.add_argument("--replicas", choices=["shard", "copy"], default="shard",
+                    help="N > 1: shard the domain set over the ranks (default, strong scaling) "
+                         "or give every rank a full copy (weak scaling)")
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="vec,warps,rows[,pipeline]: fixed sweep tile, no autotune")

@@ -204,9 +204,11 @@ LBM_API lbm_status lbm_set_populations(lbm_domain *d, const void *in, size_t byt
  *  - The fields are staged in one fixed device array owned by the library, 3 * 2^18
  *    doubles (6 MiB), which every GPU that loads the library holds until exit; domains
  *    with more than 2^18 = 262144 nodes are rejected with LBM_EINVAL.
- *  - The first call on a device looks up the array's device address (once per device,
- *    for the device that is current; it must be the domain's device); make that first
- *    call before any stream capture.
+ *  - lbm_domain_create looks up the array's device address for its device (once per
+ *    device; with CUDA's lazy module loading that is also when the array's 6 MiB are
+ *    taken), so calls on such a domain load nothing. Should that look-up have failed,
+ *    the first call retries it (for the current device, which must be the domain's):
+ *    make that first call before any stream capture.
  *  - Every call, from any domain, reuses the same array; calls whose work overlaps on the
  *    GPU (different streams, no ordering between them) race on it and must be serialised
  *    by the caller. Each call overwrites every value it reads back, so nothing needs to
@@ -289,6 +291,30 @@ LBM_API lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t eas
 
 /* Free a slot and its device memory. */
 LBM_API lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot);
+
+/* Build the work lists of the resident slots and capture the CUDA graph of graph_steps
+ * steps now, so that the next lbm_batch_run of at least graph_steps steps replays it
+ * instead of capturing it first (capture is host work of a few milliseconds; do it
+ * outside latency- or time-critical regions). No step is run. A graph stays valid
+ * until the membership of the batch or its tile shape changes. No-op when graph_steps
+ * is 0. No counterpart in the paper (launch scheduling). */
+LBM_API lbm_status lbm_batch_capture(lbm_batch *b);
+
+/* Host-side failure injection, for tests of the error paths; no GPU fault, trap or hang
+ * is raised. No counterpart in the paper.
+ *   LBM_INJECT_NONE: clear the injection of later sweep launches.
+ *   LBM_INJECT_UNSTABLE: set the slot's "unstable" status bit from the host, in stream
+ *     order, as if its sweep had seen a density out of range; the next poll, forces or
+ *     moments call of the slot returns LBM_EUNSTABLE (sticky).
+ *   LBM_INJECT_WAIT_TIMEOUT: every later launch of the shared-memory-staged sweep
+ *     (pipeline 1) takes its timeout path at its first row, after that row's bulk
+ *     copies have completed and after waiting for the copies of the row it prefetched,
+ *     so no copy is in flight when the block exits; the slots it covered report
+ *     LBM_ETIMEOUT (sticky). Other pipelines ignore it.
+ * `slot` is used by LBM_INJECT_UNSTABLE only. A captured graph is rebuilt when the
+ * injection changes. LBM_EINVAL for an unknown kind, LBM_ENOTFOUND for a free slot. */
+typedef enum { LBM_INJECT_NONE = 0, LBM_INJECT_UNSTABLE = 1, LBM_INJECT_WAIT_TIMEOUT = 2 } lbm_inject;
+LBM_API lbm_status lbm_batch_inject(lbm_batch *b, int32_t slot, int32_t kind);
 
 /* Time each sweep tile shape (cells per thread, warps per block, rows per warp, row
  * pipeline) on the

@@ -33,6 +33,14 @@ def _mask_arg(mask):
     return m, m.ctypes.data_as(C.c_void_p)
 
 
+def _allocator(allocator):
+    """"torch": PyTorch's caching allocator; None: the library's own stream-ordered
+    allocation; otherwise an object with ctypes callbacks `c_alloc` and `c_free`."""
+    if allocator == "torch":
+        return _native.TorchAllocator()
+    return allocator
+
+
 def domain_bytes(spec, storage="f32", force_every=1, force_capacity=8192) -> int:
     L = load()
     p = _native.params_from_spec(spec, storage, force_every, force_capacity)
@@ -53,7 +61,7 @@ class Domain:
         self._bodies, nb = _native.bodies_from_spec(spec)
         self._geom, self._shapes = _native.geometry_from_spec(spec)
         m, mp = _mask_arg(mask)
-        self._alloc = _native.TorchAllocator() if allocator == "torch" else None
+        self._alloc = _allocator(allocator)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         check(L.lbm_domain_create(C.byref(self._params), mp, C.byref(self._geom), self._bodies,
@@ -184,7 +192,7 @@ class Domain3:
         self._params = _native.params3_from_spec(spec, storage, force_every, force_capacity)
         self._bodies, nb = _native.bodies3_from_spec(spec)
         self._shapes, ns = _native.shapes3_from_spec(spec)
-        self._alloc = _native.TorchAllocator() if allocator == "torch" else None
+        self._alloc = _allocator(allocator)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         check(L.lbm3_domain_create(C.byref(self._params), self._shapes, ns, self._bodies, nb,
@@ -318,7 +326,7 @@ class Batch:
         import torch
         L = load()
         self.storage = storage
-        self._alloc = _native.TorchAllocator() if allocator == "torch" else None
+        self._alloc = _allocator(allocator)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         check(L.lbm_batch_create(max_domains, int(hbm_budget), STORAGE[storage], graph_steps,
@@ -432,6 +440,19 @@ class Batch:
     def evict(self, slot: int):
         check(load().lbm_batch_evict(self._h, slot), "lbm_batch_evict")
         self._meta.pop(slot, None)
+
+    def capture(self):
+        """Build the work lists and capture the step graph now (no steps run), so that the
+        next run replays it without capturing."""
+        check(load().lbm_batch_capture(self._h), "lbm_batch_capture")
+
+    INJECT = {"none": 0, "unstable": 1, "wait_timeout": 2}
+
+    def inject(self, kind: str, slot: int = -1):
+        """Host-side failure injection for tests of the error paths (no GPU fault):
+        "unstable" marks a slot as diverged, "wait_timeout" makes later launches of the
+        shared-memory-staged sweep report a timed-out wait, "none" clears the latter."""
+        check(load().lbm_batch_inject(self._h, int(slot), self.INJECT[kind]), "lbm_batch_inject")
 
     def profile(self, steps: int):
         """Run `steps` real steps one kernel at a time; returns (sweep_us, force_us,

@@ -145,6 +145,8 @@ SIGNATURES = {
     "lbm_batch_set_steps_done": (C.c_int, [_VP, _I32, _I64]),
     "lbm_batch_profile": (C.c_int, [_VP, _I32, _DP, _DP, C.POINTER(_I64)]),
     "lbm_batch_evict": (C.c_int, [_VP, _I32]),
+    "lbm_batch_inject": (C.c_int, [_VP, _I32, _I32]),
+    "lbm_batch_capture": (C.c_int, [_VP]),
     "lbm_batch_autotune": (C.c_int, [_VP, _I32, _DP]),
     "lbm_batch_set_tile": (C.c_int, [_VP, _I32, _I32, _I32, _I32]),
     "lbm_batch_get_tile": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),

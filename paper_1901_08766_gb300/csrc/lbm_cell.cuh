@@ -213,7 +213,9 @@ __device__ __forceinline__ uint32_t sr_hash(uint32_t x) {
   return x;
 }
 
-// hash input of a row: step index and row
+// hash input of a row: step index and row. The odd multipliers here and below are the
+// five 32-bit primes of Y. Collet's published xxHash32 (PRIME32_1, _2, _3, _5, and _4 less
+// one, doubled per column pair), used only as well-mixed odd constants.
 __device__ __forceinline__ uint32_t sr_row_key(long long n, int j) {
   return static_cast<uint32_t>(n) * 0x9e3779b1u + static_cast<uint32_t>(j) * 0x85ebca77u;
 }

@@ -48,7 +48,7 @@ struct DomDev {
   const int32_t *solid_off;// [nbodies + 1] offsets into solid
   void *fvp;               // F_VP of solid nodes, [ny][pitch] pairs in compute precision
   double *ring;            // force ring [cap][nbodies][2]
-  int32_t *status;         // bit 0: unstable
+  int32_t *status;         // bit 0: unstable; bit 1: a bounded device-side wait ran out
   int32_t nx, ny, pitch;
   int32_t west, east, south, north;
   int32_t nbodies, force_every, force_cap;
@@ -127,6 +127,9 @@ struct SweepArgs {
   const TileDev *tiles;
   const Counters *ctr;
   int32_t rows;  // rows per warp
+  // host-side failure injection (tests of the error paths; no GPU fault): bit 0 makes the
+  // TMA-staged sweep report its first row wait as timed out after that wait has completed
+  int32_t inject;
 };
 
 struct ShapeDev {

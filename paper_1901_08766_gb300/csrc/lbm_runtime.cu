@@ -263,6 +263,7 @@ struct lbm_batch {
   long long launches = 0;
   size_t bytes_in_use = 0;
   int sm_count = 0;
+  int inject = 0;  // SweepArgs::inject of later sweep launches (host failure injection)
 };
 
 struct lbm_domain {
@@ -273,7 +274,7 @@ namespace lbm {
 namespace {
 
 cudaError_t sweep_launch(lbm_batch *b, int grid, int vec, int pipe, int warps, int rows, int s) {
-  SweepArgs a{b->d_doms, b->d_dyn, b->d_tiles, b->d_ctr, rows};
+  SweepArgs a{b->d_doms, b->d_dyn, b->d_tiles, b->d_ctr, rows, b->inject};
   if (pipe == 0 && b->has_deform) pipe = 4;  // the direct sweep instantiated with the kappa term
   switch (b->storage) {
     case LBM_F64: return launch_sweep_f64(vec, pipe, grid, warps, b->st, a, s);
@@ -858,6 +859,7 @@ lbm_status moments(lbm_batch *b, int slot, double *rho, double *ux, double *uy) 
   int status = 0;
   rc = read_status(b, s, &status);
   if (rc != LBM_OK) return rc;
+  if (status & 2) return fail(LBM_ETIMEOUT, "slot %d: a sweep gave up waiting for its row copies", slot);
   if (status & 1) return fail(LBM_EUNSTABLE, "slot %d diverged", slot);
   return LBM_OK;
 }
@@ -1023,6 +1025,11 @@ lbm_status autotune(lbm_batch *b, int reps, double *best_us) {
 }
 
 }  // namespace
+}  // namespace lbm
+
+namespace lbm {
+// Device address of lbm_moments_noalloc's fixed staging array on `dev` (defined below).
+lbm_status noalloc_scratch_on(int dev, double **out);
 }  // namespace lbm
 
 // ======================================================================================
@@ -1335,6 +1342,44 @@ lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_capture(lbm_batch *b) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  if (b->graph_steps <= 0) return LBM_OK;  // the batch steps with direct launches
+  if (b->dirty) {
+    lbm_status rc = rebuild_lists(b);
+    if (rc != LBM_OK) return rc;
+  }
+  if (!b->graph) return capture_graph(b);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_inject(lbm_batch *b, int32_t slot, int32_t kind) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  switch (kind) {
+    case LBM_INJECT_NONE:
+    case LBM_INJECT_WAIT_TIMEOUT: {
+      const int want = kind == LBM_INJECT_WAIT_TIMEOUT ? 1 : 0;
+      if (want != b->inject) {
+        b->inject = want;
+        drop_graph(b);  // a captured graph holds the launch arguments
+      }
+      return LBM_OK;
+    }
+    case LBM_INJECT_UNSTABLE: {
+      lbm_status rc = check_slot(b, slot);
+      if (rc != LBM_OK) return rc;
+      static const int32_t kUnstable = 1;
+      // the status word is only ever OR-ed: a plain write would race with the sweep's
+      // atomics, so the host stores the bit in stream order (no sweep runs meanwhile)
+      LBM_CUDA(cudaMemcpyAsync(b->slots[slot].dev.status, &kUnstable, sizeof(int32_t),
+                               cudaMemcpyHostToDevice, b->st));
+      LBM_CUDA(cudaStreamSynchronize(b->st));
+      return LBM_OK;
+    }
+  }
+  return fail(LBM_EINVAL, "unknown injection kind %d", kind);
+}
+
 lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us) {
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   return autotune(b, reps, best_us);
@@ -1403,6 +1448,13 @@ lbm_status lbm_domain_create(const lbm_params *p, const uint8_t *mask, const lbm
     return fail(LBM_ENOMEM, "host allocation failed");
   }
   d->b = b;
+  // resolve lbm_moments_noalloc's staging array on this device now (with lazy module
+  // loading, its module and the array's memory are loaded here), so that the
+  // allocation-free call itself loads nothing; a failure is retried by that call
+  int dev = 0;
+  double *scratch = nullptr;
+  if (cudaGetDevice(&dev) == cudaSuccess && noalloc_scratch_on(dev, &scratch) != LBM_OK)
+    cudaGetLastError();
   *out = d;
   return LBM_OK;
 }
@@ -1512,10 +1564,12 @@ static __device__ __align__(256) double g_moments_scratch[3 * kNoAllocMaxNodes];
 std::mutex g_scratch_mu;
 double *g_scratch_addr[kNoAllocMaxDevices] = {};
 
+}  // namespace
+
 // Device address of g_moments_scratch on `dev` (which must be current). In host code
 // the array's name is only a host-side stand-in, so the address is looked up once per
 // device with cudaGetSymbolAddress and cached.
-lbm_status scratch_on(int dev, double **out) {
+lbm_status noalloc_scratch_on(int dev, double **out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(LBM_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
@@ -1529,7 +1583,6 @@ lbm_status scratch_on(int dev, double **out) {
   return LBM_OK;
 }
 
-}  // namespace
 }  // namespace lbm
 
 extern "C" lbm_status lbm_moments_noalloc(lbm_domain *d, double *rho, double *ux, double *uy) {
@@ -1550,7 +1603,7 @@ extern "C" lbm_status lbm_moments_noalloc(lbm_domain *d, double *rho, double *ux
   if (attr.device != cur)
     return fail(LBM_EINVAL, "domain lives on device %d but device %d is current", attr.device, cur);
   double *tmp = nullptr;
-  lbm_status rc = scratch_on(cur, &tmp);
+  lbm_status rc = noalloc_scratch_on(cur, &tmp);
   if (rc != LBM_OK) return rc;
   LBM_CUDA(launch_moments_sized(b->storage, b->st, b->d_doms, s.p.nx, s.p.ny, s.parity, tmp,
                                 tmp + cells, tmp + 2 * cells));
@@ -1562,6 +1615,7 @@ extern "C" lbm_status lbm_moments_noalloc(lbm_domain *d, double *rho, double *ux
   int status = 0;
   rc = read_status(b, s, &status);
   if (rc != LBM_OK) return rc;
+  if (status & 2) return fail(LBM_ETIMEOUT, "a sweep gave up waiting for its row copies");
   if (status & 1) return fail(LBM_EUNSTABLE, "domain diverged");
   return LBM_OK;
 }

@@ -11,7 +11,10 @@
 //
 // Every wait is bounded: if a stage does not complete within the spin limit the warp
 // sets bit 1 of the domain status word (reported as LBM_ETIMEOUT), waits a bounded time
-// for its other stage and returns.
+// for its other stage and returns. A stage that never completed may still have copies in
+// flight when the block exits; the host reports the domain as failed and does not use
+// its state. Tests reach this path by host-side injection (bit 0 of SweepArgs::inject),
+// which takes it only after the stage's wait has completed.
 #pragma once
 
 #include "lbm_sweep.cuh"
@@ -174,9 +177,14 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
     }
     const TileDev tile = args.tiles[t];
     const DomDev &D = args.doms[tile.dom];
-    // bounded wait; the vote keeps the warp's decision uniform
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], (phase >> st) & 1u))) {
+    // bounded wait; the vote keeps the warp's decision uniform. Injected failure (bit 0
+    // of args.inject): the wait has completed, then the warp takes the timeout path, so
+    // the path runs with no copy of this stage in flight.
+    const bool arrived = mbar_wait_bounded(&bar[st], (phase >> st) & 1u);
+    if (!__all_sync(0xffffffffu, arrived && !(args.inject & 1))) {
       if (lane == 0) atomicOr(D.status, 2);
+      // the other stage's copies (issued above) are awaited, again with a bound. After a
+      // real timeout the copies of this stage may still be in flight when the block exits.
       if (have_n) mbar_wait_bounded(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
       return;
     }
