@@ -202,6 +202,152 @@ template <int S, int V> struct RowData {
   __device__ int body(int k) const { return (mb[k >> 2] >> (8 * (k & 3))) & 0xff; }
 };
 
+// Phase 3 of a strip row, shared by the row pipelines: update the V pulled nodes of a
+// lane in place (inlet ghost, moments, penalization, collision, F_VP of solid nodes,
+// stability check, rounding to the storage type) and zero the padding beyond nx. mb: the
+// nodes' body ids, four per word. The caller stores v[].
+template <int S, int V, bool DEF>
+__device__ __forceinline__ void update_strip(Strip<S, V> (&v)[kQ], const uint32_t (&mb)[(V + 3) / 4],
+                                             const DomDev &D,
+                                             const CellConst<typename Codec<S>::T> &C,
+                                             const CellConst<typename Codec<S>::T> &CF,
+                                             const CellConst<F2> &CP, const int lane, const int xl,
+                                             const int j, const long long n, const bool west_edge,
+                                             const bool west_inlet, const bool east_edge,
+                                             const int nx, int &unstable) {
+  using Cd = Codec<S>;
+  using E = typename Cd::E;
+  using T = typename Cd::T;
+  constexpr bool SHIFT = Cd::kShiftCompute;
+  constexpr bool kAddShift = Cd::kShiftCompute && !Cd::kStoreShifted;
+  constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
+  constexpr T kUnscale = T(1) / T(Cd::kScale);
+  const int pitch = D.pitch;
+  T *__restrict__ dfvp = static_cast<T *>(D.fvp);
+  bool any_solid_lane = false;
+#pragma unroll
+  for (int q = 0; q < (V + 3) / 4; ++q) any_solid_lane |= (mb[q] != 0u);
+  const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
+
+  // ---- phase 3: update the V nodes in place ----------------------------------------
+  // bit k: node xl + k lies inside the domain (all V except at the east edge)
+  const unsigned valid_bits =
+      east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u))
+                : (1u << V) - 1u;
+  unsigned bad_bits = 0u;
+  // random bits of the 16-bit rounding (a strip of V <= 8 cells lies in one group)
+  // (keyed by the global column: slabs of one grid round as the whole grid does)
+  const uint32_t sr_g = sizeof(E) == 2 ? sr_group_bits(sr_row_key(n, j), xl + D.x0) : 0u;
+  // one node: inlet ghost, moments, penalization, collision, F_VP, stability check
+  auto update = [&](T (&x)[kQ], int k) {
+    if (k == 0 && west_edge && west_inlet) {
+      // inlet ghost populations entering node 0 from x = -1
+      const bool g = lane == 0;
+      x[1] = g ? C.ghost[1] : x[1];
+      x[5] = g ? C.ghost[5] : x[5];
+      x[8] = g ? C.ghost[8] : x[8];
+    }
+    NodeMacro<T> m;
+    if (any_solid) {
+      T uox = T(0), uoy = T(0);
+      const int bk = ((mb[k >> 2] >> (8 * (k & 3))) & 0xff);
+      const bool solid = bk != 0;
+      if (solid) body_velocity<DEF>(D, bk, xl + k, j, uox, uoy);
+      m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
+      collide<T, SHIFT, true>(x, m, C);
+      if (solid) {
+        // F_VP of this node for the body-force reduction (unscaled: power of two)
+        T *__restrict__ fv = dfvp + 2 * (static_cast<size_t>(j) * pitch + xl + k);
+        fv[0] = m.fx * kUnscale;
+        fv[1] = m.fy * kUnscale;
+      }
+    } else {
+      m = node_macro<T, SHIFT, false>(x, CF, false, T(0), T(0));
+      collide<T, SHIFT, false>(x, m, CF);
+    }
+    // rho outside (0.01, 100) or not finite; padding nodes are masked out per row
+    bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
+    return m.d;
+  };
+#ifndef LBM_PAIRED
+#define LBM_PAIRED 1
+#endif
+  if constexpr (sizeof(E) == 2) {
+    // 16-bit storage: two nodes per packed word, converted pairwise
+    if (LBM_PAIRED && !any_solid) {
+      // force-free rows: both nodes of a word updated together in packed FP32 pairs
+#pragma unroll
+      for (int k = 0; k < V; k += 2) {
+        F2 x[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) x[a] = F2(Cd::dec2(v[a].w[k >> 1]));
+        if (k == 0 && west_edge && west_inlet) {
+          const bool g = lane == 0;
+          x[1].v.x = g ? C.ghost[1] : x[1].v.x;
+          x[5].v.x = g ? C.ghost[5] : x[5].v.x;
+          x[8].v.x = g ? C.ghost[8] : x[8].v.x;
+        }
+        const NodeMacro<F2> m = node_macro<F2, SHIFT, false>(x, CP, false, F2(0.f), F2(0.f));
+        bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
+        bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (k + 1);
+        // each opposite pair is rounded as soon as the collision finishes it
+        PairEncoder<S> enc(sr_pair_bits(sr_g, xl + k + D.x0));
+        collide<F2, SHIFT, false>(x, m, CP, enc);
+        enc.finish(m.d);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = enc.w[a];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; k += 2) {
+        T x0[kQ], x1[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+          const float2 p = Cd::dec2(v[a].w[k >> 1]);
+          x0[a] = p.x;
+          x1[a] = p.y;
+        }
+        const float d0 = update(x0, k);
+        const float d1 = update(x1, k + 1);
+        F2 xp[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0[a], x1[a]));
+        uint32_t w[kQ];
+        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + k + D.x0), w);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      T x[kQ];
+      decode_cell<S, V>(v, k, x);
+      if constexpr (kAddShift) {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) x[a] -= shift_of(CF, a);  // exact (Sterbenz)
+      }
+      update(x, k);
+      if constexpr (kAddShift) {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) x[a] += shift_of(CF, a);
+      }
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
+    }
+  }
+  if (bad_bits & valid_bits) unstable = 1;
+  if (east_edge) {
+    // keep the row padding beyond nx at zero
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (!((valid_bits >> k) & 1u)) {
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) v[a].set(k, E(0));
+      }
+  }
+}
+
 // The sweep body. PF = false: each warp loads a row, then updates it. PF = true: the
 // loads of the warp's next row are issued into a second register set before the current
 // row is updated, so that they overlap the update (more registers, fewer warps).
@@ -210,11 +356,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
   using T = typename Cd::T;
-  constexpr bool SHIFT = Cd::kShiftCompute;
-  constexpr bool kAddShift = Cd::kShiftCompute && !Cd::kStoreShifted;
-  // compute space carries the storage scale: stability bounds on rho and the F_VP output
-  constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
-  constexpr T kUnscale = T(1) / T(Cd::kScale);
   constexpr int kStrip = 32 * V;
   static_assert(sizeof(E) != 2 || (V <= 8 && 8 % V == 0),
                 "a 16-bit strip must lie in one group of eight columns (rounding bits)");
@@ -272,7 +413,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
     CellConst<F2> CP;
     if constexpr (sizeof(E) == 2) CP = pair_const(CF);
     const uint8_t *__restrict__ dmask = D.mask;
-    T *__restrict__ dfvp = static_cast<T *>(D.fvp);
     // strip-end columns read by the end lanes (or -1: nothing to read); at a linked
     // (NEIGHBOR) edge the value comes from the neighbour's lattice instead (below)
     const bool west_link = west_edge && D.west == LBM_NEIGHBOR;
@@ -396,128 +536,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
           }
         }
       }
-      bool any_solid_lane = false;
-#pragma unroll
-      for (int q = 0; q < (V + 3) / 4; ++q) any_solid_lane |= (R.mb[q] != 0u);
-      const bool any_solid = __any_sync(0xffffffffu, any_solid_lane);
-
-      // ---- phase 3: update the V nodes in place ----------------------------------------
-      // bit k: node xl + k lies inside the domain (all V except at the east edge)
-      const unsigned valid_bits =
-          east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u))
-                    : (1u << V) - 1u;
-      unsigned bad_bits = 0u;
-      // random bits of the 16-bit rounding (a strip of V <= 8 cells lies in one group)
-      // (keyed by the global column: slabs of one grid round as the whole grid does)
-      const uint32_t sr_g = sizeof(E) == 2 ? sr_group_bits(sr_row_key(n, j), xl + D.x0) : 0u;
-      // one node: inlet ghost, moments, penalization, collision, F_VP, stability check
-      auto update = [&](T (&x)[kQ], int k) {
-        if (k == 0 && west_edge && west_inlet) {
-          // inlet ghost populations entering node 0 from x = -1
-          const bool g = lane == 0;
-          x[1] = g ? C.ghost[1] : x[1];
-          x[5] = g ? C.ghost[5] : x[5];
-          x[8] = g ? C.ghost[8] : x[8];
-        }
-        NodeMacro<T> m;
-        if (any_solid) {
-          T uox = T(0), uoy = T(0);
-          const int bk = R.body(k);
-          const bool solid = bk != 0;
-          if (solid) body_velocity<DEF>(D, bk, xl + k, j, uox, uoy);
-          m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
-          collide<T, SHIFT, true>(x, m, C);
-          if (solid) {
-            // F_VP of this node for the body-force reduction (unscaled: power of two)
-            T *__restrict__ fv = dfvp + 2 * (static_cast<size_t>(j) * pitch + xl + k);
-            fv[0] = m.fx * kUnscale;
-            fv[1] = m.fy * kUnscale;
-          }
-        } else {
-          m = node_macro<T, SHIFT, false>(x, CF, false, T(0), T(0));
-          collide<T, SHIFT, false>(x, m, CF);
-        }
-        // rho outside (0.01, 100) or not finite; padding nodes are masked out per row
-        bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
-        return m.d;
-      };
-#ifndef LBM_PAIRED
-#define LBM_PAIRED 1
-#endif
-      if constexpr (sizeof(E) == 2) {
-        // 16-bit storage: two nodes per packed word, converted pairwise
-        if (LBM_PAIRED && !any_solid) {
-          // force-free rows: both nodes of a word updated together in packed FP32 pairs
-#pragma unroll
-          for (int k = 0; k < V; k += 2) {
-            F2 x[kQ];
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) x[a] = F2(Cd::dec2(v[a].w[k >> 1]));
-            if (k == 0 && west_edge && west_inlet) {
-              const bool g = lane == 0;
-              x[1].v.x = g ? C.ghost[1] : x[1].v.x;
-              x[5].v.x = g ? C.ghost[5] : x[5].v.x;
-              x[8].v.x = g ? C.ghost[8] : x[8].v.x;
-            }
-            const NodeMacro<F2> m = node_macro<F2, SHIFT, false>(x, CP, false, F2(0.f), F2(0.f));
-            bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << k;
-            bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (k + 1);
-            // each opposite pair is rounded as soon as the collision finishes it
-            PairEncoder<S> enc(sr_pair_bits(sr_g, xl + k + D.x0));
-            collide<F2, SHIFT, false>(x, m, CP, enc);
-            enc.finish(m.d);
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = enc.w[a];
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < V; k += 2) {
-            T x0[kQ], x1[kQ];
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) {
-              const float2 p = Cd::dec2(v[a].w[k >> 1]);
-              x0[a] = p.x;
-              x1[a] = p.y;
-            }
-            const float d0 = update(x0, k);
-            const float d1 = update(x1, k + 1);
-            F2 xp[kQ];
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0[a], x1[a]));
-            uint32_t w[kQ];
-            encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + k + D.x0), w);
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
-          }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-          T x[kQ];
-          decode_cell<S, V>(v, k, x);
-          if constexpr (kAddShift) {
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) x[a] -= shift_of(CF, a);  // exact (Sterbenz)
-          }
-          update(x, k);
-          if constexpr (kAddShift) {
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) x[a] += shift_of(CF, a);
-          }
-#pragma unroll
-          for (int a = 0; a < kQ; ++a) v[a].set(k, Cd::enc(x[a]));
-        }
-      }
-      if (bad_bits & valid_bits) unstable = 1;
-      if (east_edge) {
-        // keep the row padding beyond nx at zero
-#pragma unroll
-        for (int k = 0; k < V; ++k)
-          if (!((valid_bits >> k) & 1u)) {
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) v[a].set(k, E(0));
-          }
-      }
+      update_strip<S, V, DEF>(v, R.mb, D, C, CF, CP, lane, xl, j, n, west_edge, west_inlet,
+                              east_edge, nx, unstable);
       if (lane_on) {
 #pragma unroll
         for (int a = 0; a < kQ; ++a)
