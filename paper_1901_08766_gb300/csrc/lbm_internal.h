@@ -119,6 +119,9 @@ struct Counters {
   long long run_base;  // steps completed in the current run (advanced by the graphs)
   int32_t nmove;       // rows of moving domains
   int32_t pad;
+  // work items of the direct sweep, taken by warps in turn: the next item and the warps
+  // that have run out; the last warp to run out resets both for the next launch
+  int32_t item_next, item_done;
 };
 
 struct SweepArgs {

@@ -407,6 +407,8 @@ lbm_status rebuild_lists(lbm_batch *b) {
   b->h_ctr->run_base = 0;
   b->h_ctr->nmove = b->nmove;
   b->h_ctr->pad = 0;
+  b->h_ctr->item_next = 0;
+  b->h_ctr->item_done = 0;
   LBM_CUDA(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaStreamSynchronize(b->st));
   b->dirty = false;

@@ -4,7 +4,8 @@
 //
 // Work decomposition. A persistent grid walks a tile list. A tile is a strip of
 // 32 * V cells of one row range: lane l of each warp owns V consecutive cells
-// x0 + l*V .. x0 + l*V + V-1 and a warp walks `rows` rows. Each of the nine
+// x0 + l*V .. x0 + l*V + V-1 and a warp walks `rows` rows of it; the warps take these
+// (tile, rows) items in turn from a device counter. Each of the nine
 // populations of a row is read with one aligned vector load per lane from the
 // structure-of-arrays lattice [9][ny][pitch]; the +-1 x-shift of the pull (Eq.
 // streaming) is done in registers with one warp shuffle per direction, the two
@@ -360,17 +361,34 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   static_assert(sizeof(E) != 2 || (V <= 8 && 8 % V == 0),
                 "a 16-bit strip must lie in one group of eight columns (rounding bits)");
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
   const int ntiles = args.ctr->ntiles;
   const long long run_base = args.ctr->run_base;
   int unstable = 0;
 
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // Work items are (tile, warp slot) pairs: the `rows` rows y0 + slot * rows ... of a tile.
+  // Warps take them in turn from a counter (the next index is fetched while the current
+  // item is processed), so the warps finish together however unevenly the items cost
+  // (tiles holding bodies take the force path). The last warp to run out resets the
+  // counters for the next launch; items are visited in tile order.
+  Counters *const ctr = const_cast<Counters *>(args.ctr);
+  const int slots = static_cast<int>(blockDim.x >> 5);
+  const int nitems = ntiles * slots;
+  int item = 0;
+  if (lane == 0) item = atomicAdd(&ctr->item_next, 1);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item < nitems) {
+    int next = 0;
+    if (lane == 0) next = atomicAdd(&ctr->item_next, 1);
+    const int t = item / slots;
+    const int slot = item - t * slots;
     const TileDev tile = args.tiles[t];
     const DomDev &D = args.doms[tile.dom];
     const DomDyn dy = args.dyn[tile.dom];
     const long long n = dy.step0 + run_base + s;
-    if (n >= dy.step_end) continue;
+    if (n >= dy.step_end) {
+      item = __shfl_sync(0xffffffffu, next, 0);
+      continue;
+    }
     const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
     const E *__restrict__ src = static_cast<const E *>(D.lat[par]);
     E *__restrict__ dst = static_cast<E *>(D.lat[par ^ 1]);
@@ -544,7 +562,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
           v[a].store(dst + a * plane + static_cast<size_t>(j) * pitch + xl);
       }
     };
-    const int j0 = tile.y0 + warp * args.rows;
+    const int j0 = tile.y0 + slot * args.rows;
     if constexpr (!PF) {
       for (int r = 0; r < args.rows; ++r) {
         const int j = j0 + r;
@@ -570,6 +588,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
     if (__any_sync(0xffffffffu, unstable)) {
       if (lane == 0) atomicOr(D.status, 1);
       unstable = 0;
+    }
+    item = __shfl_sync(0xffffffffu, next, 0);
+  }
+  if (lane == 0) {
+    __threadfence();  // this warp's last fetch is ordered before its count
+    if (atomicAdd(&ctr->item_done, 1) == static_cast<int>(gridDim.x) * slots - 1) {
+      ctr->item_next = 0;
+      ctr->item_done = 0;
     }
   }
 }
