@@ -345,9 +345,9 @@ def run_ours(args):
 def measure_e2e(lbm, torch, specs, args):
     """The same metric through the public API with host inputs and outputs: admit every
     domain from its host-side geometry, run the steps, read every force series back."""
-    import numpy as np
     steps = args.steps
     stream = torch.cuda.Stream()
+    marks = []
     with torch.cuda.stream(stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -355,14 +355,16 @@ def measure_e2e(lbm, torch, specs, args):
         # saves); longer jobs replay graphs, their capture included
         gsteps = args.graph_steps if steps >= 4 * args.graph_steps else 0
         batch = lbm.Batch(args.storage, max_domains=64, graph_steps=gsteps, stream=stream)
-        slots = [batch.admit(s, nsteps=steps, force_capacity=steps + 8) for s in specs]
+        marks.append(("create", time.perf_counter()))
+        slots = batch.admit_many(specs, nsteps=steps, force_capacity=steps + 8)
         if getattr(args, "tuned_tile", None):
             batch.set_tile(*args.tuned_tile)
+        marks.append(("admit", time.perf_counter()))
         batch.run(steps)
-        nbytes_out = 0
-        for k in slots:
-            f, done = batch.poll(k)
-            nbytes_out += f.nbytes
+        marks.append(("enqueue steps", time.perf_counter()))
+        forces = batch.poll_many(slots)
+        nbytes_out = sum(f.nbytes for f, _ in forces)
+        marks.append(("run + force readback", time.perf_counter()))
         stream.synchronize()
         el = time.perf_counter() - t0
         batch.close()
@@ -370,11 +372,15 @@ def measure_e2e(lbm, torch, specs, args):
     # host -> device per domain: parameters, shapes and bodies (the mask is rasterised
     # on the device); device -> host: the force series
     h2d = sum(120 + 56 * len(s["shapes"]) + 48 * len(s["bodies"]) for s in specs)
+    prev, phases = t0, {}
+    for name, t in marks:
+        phases[name] = 1000.0 * (t - prev)
+        prev = t
     return {"value": cells * steps / el / 1e9, "unit": "GLUPS",
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": nbytes_out / steps,
-            "graph_steps": gsteps,
-            "includes": "batch creation, admission of every domain from host geometry "
-                        "(rasterise, solid lists, init), the steps, force readback"}
+            "graph_steps": gsteps, "job_ms": 1000.0 * el, "phases_ms": phases,
+            "includes": "batch creation, admission of every domain from host geometry (one "
+                        "batched admission: rasterise, solid lists, init), the steps, force readback"}
 
 
 def measure_served(lbm, torch, args, plain=None):
@@ -404,7 +410,8 @@ def measure_served(lbm, torch, args, plain=None):
     out = {"requests": len(reqs), "scale": args.served_scale, "chunk_steps": args.served_chunk,
            "completed": st["completed"], "not_ok": bad, "glups": st["glups"],
            "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
-           "max_queue": st["max_queue"], "hbm_budget_bytes": budget,
+           "max_queue": st["max_queue"], "hbm_budget_bytes": budget, "wall_s": st["wall_s"],
+           "host_s": st["host_s"],
            "latency": "arrival to last force slice on the host"}
     if plain and st["glups"]:
         out["served_vs_plain_f32"] = st["glups"] / plain["value"]

@@ -251,6 +251,21 @@ LBM_API lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint
                            const lbm_geometry *geom, const lbm_body *bodies, int32_t nbodies,
                            int64_t nsteps, int32_t *slot);
 
+/* Admit n fixed-geometry domains at once, each rasterised on the device from its
+ * geometry (no host masks, no moving domains: use lbm_batch_admit for those): the same
+ * state, slots and results as n calls of lbm_batch_admit, with one rasterise/count, one
+ * solid-list, one initial-state and two copy launches over the rows of all of them and
+ * two synchronisations in all (one to size the solid-node lists from the per-row
+ * counts, one at the end), instead of two per domain. params, geoms, nbodies, nsteps:
+ * arrays of n; bodies: n pointers to each domain's body table (may be NULL where
+ * nbodies is 0). slots[i] receives domain i's slot. All or none: on any error nothing is
+ * admitted and every allocation is given back. LBM_EBUSY when fewer than n slots are free
+ * or the memory budget would be exceeded; LBM_EINVAL as lbm_batch_admit, with the
+ * domain's index in the message. No counterpart in the paper (admission scheduling). */
+LBM_API lbm_status lbm_batch_admit_many(lbm_batch *b, int32_t n, const lbm_params *params,
+                                        const lbm_geometry *geoms, const lbm_body *const *bodies,
+                                        const int32_t *nbodies, const int64_t *nsteps, int32_t *slots);
+
 /* Advance every resident, unfinished domain by up to max_steps steps; a domain stops
  * at its own nsteps. *steps_run = steps actually run (<= max_steps). Asynchronous.
  * Returns LBM_EBUSY (nothing run) if a domain's force ring cannot hold the entries. */
@@ -258,6 +273,17 @@ LBM_API lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps
 
 /* Drain a slot's recorded forces (as lbm_forces); *done = 1 once the slot has run all
  * its steps and its forces are drained. Synchronises the stream. */
+/* lbm_batch_poll for n slots with one synchronisation (their entries and status words
+ * are staged in pinned host memory by asynchronous copies): outs[i] receives up to
+ * max_entries[i] entries of slot slots[i], [entries][nbodies][2] FP64, written[i] their
+ * number, done[i] as lbm_batch_poll, status[i] the slot's own state (LBM_OK, LBM_EUNSTABLE
+ * or LBM_ETIMEOUT; a failed slot's entries are still drained). Returns LBM_EINVAL or
+ * LBM_ENOTFOUND (nothing drained) for a bad argument, LBM_ENOMEM if the pinned staging
+ * cannot grow, LBM_ECUDA if a copy fails. No counterpart in the paper (host I/O). */
+LBM_API lbm_status lbm_batch_poll_many(lbm_batch *b, int32_t n, const int32_t *slots,
+                                       double *const *outs, const int64_t *max_entries,
+                                       int64_t *written, int32_t *done, int32_t *status);
+
 LBM_API lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_entries,
                           int64_t *written, int32_t *done);
 

@@ -366,6 +366,48 @@ class Batch:
                     raise err
         return slot.value
 
+    def admit_many(self, specs, nsteps=None, force_every=1, force_capacity=8192) -> list:
+        """Admit many domains; returns their slots in order (`nsteps`: one count for all,
+        a list of per-domain counts, or None for each spec's own). Fixed-geometry domains are
+        admitted together by one lbm_batch_admit_many call (one batched rasterise, solid
+        list and initial-state pass, two synchronisations); moving or coupled ones one by
+        one. Raises LbmError (nothing of the batched group admitted) on failure."""
+        specs = list(specs)
+        plain = [k for k, sp in enumerate(specs)
+                 if not sp.get("moving") and not any(b.get("dynamics") or b.get("deform")
+                                                     for b in sp["bodies"])]
+        out = [None] * len(specs)
+        if plain:
+            n = len(plain)
+            P = (_native.Params * n)()
+            G = (_native.Geometry * n)()
+            BP = (C.POINTER(_native.Body) * n)()
+            NB = (C.c_int32 * n)()
+            NS = (C.c_int64 * n)()
+            keep = []
+            for q, k in enumerate(plain):
+                sp = specs[k]
+                P[q] = _native.params_from_spec(sp, self.storage, force_every, force_capacity)
+                g, shapes = _native.geometry_from_spec(sp)
+                bodies, nb = _native.bodies_from_spec(sp)
+                keep += [shapes, bodies]
+                G[q] = g
+                BP[q] = C.cast(bodies, C.POINTER(_native.Body))
+                NB[q] = nb
+                NS[q] = int(sp["steps"] if nsteps is None else
+                            (nsteps[k] if isinstance(nsteps, (list, tuple)) else nsteps))
+            S = (C.c_int32 * n)()
+            check(load().lbm_batch_admit_many(self._h, n, P, G, BP, NB, NS, S), "lbm_batch_admit_many")
+            for q, k in enumerate(plain):
+                sp = specs[k]
+                self._meta[S[q]] = (sp["nx"], sp["ny"], len(sp["bodies"]), force_capacity)
+                out[k] = S[q]
+        for k, sp in enumerate(specs):
+            if out[k] is None:
+                n_k = nsteps[k] if isinstance(nsteps, (list, tuple)) else nsteps
+                out[k] = self.admit(sp, nsteps=n_k, force_every=force_every, force_capacity=force_capacity)
+        return out
+
     def body_state(self, slot: int) -> np.ndarray:
         """Body table of the slot's current step: [nbodies, 5] (cx, cy, vx, vy, omega)."""
         nb = self._meta[slot][2]
@@ -397,6 +439,37 @@ class Batch:
         if st != 0 and (raise_unstable or st != LBM_EUNSTABLE):
             check(st, "lbm_batch_poll")
         return buf[: w.value, :nb].copy(), bool(d.value)
+
+    def poll_many(self, slots, raise_unstable=True):
+        """poll() for many slots with one synchronisation; a list of (forces, done)."""
+        out = []
+        for k, (f, done, st) in zip(slots, self.poll_many_status(slots)):
+            if st != 0 and (raise_unstable or st != LBM_EUNSTABLE):
+                raise LbmError(st, "lbm_batch_poll_many", f"slot {k}")
+            out.append((f, done))
+        return out
+
+    def poll_many_status(self, slots):
+        """poll_many without raising: a list of (forces, done, status) with each slot's own
+        status (0 ok, LBM_EUNSTABLE, LBM_ETIMEOUT)."""
+        slots = list(slots)
+        n = len(slots)
+        if n == 0:
+            return []
+        bufs = []
+        S = (C.c_int32 * n)(*slots)
+        O = (_native._DP * n)()
+        M = (C.c_int64 * n)()
+        for q, k in enumerate(slots):
+            nx, ny, nb, cap = self._meta[k]
+            buf = np.zeros((cap, max(nb, 1), 2))
+            bufs.append(buf)
+            O[q] = buf.ctypes.data_as(_native._DP)
+            M[q] = cap
+        W, D, ST = (C.c_int64 * n)(), (C.c_int32 * n)(), (C.c_int32 * n)()
+        check(load().lbm_batch_poll_many(self._h, n, S, O, M, W, D, ST), "lbm_batch_poll_many")
+        return [(bufs[q][: W[q], : self._meta[k][2]].copy(), bool(D[q]), int(ST[q]))
+                for q, k in enumerate(slots)]
 
     def moments(self, slot: int):
         nx, ny, nb, cap = self._meta[slot]

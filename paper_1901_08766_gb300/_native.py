@@ -136,8 +136,13 @@ SIGNATURES = {
     "lbm_batch_admit": (C.c_int, [_VP, C.POINTER(Params), C.c_void_p, C.POINTER(Geometry),
                                   C.POINTER(Body), _I32, _I64, C.POINTER(_I32)]),
     "lbm_batch_run": (C.c_int, [_VP, _I64, C.POINTER(_I64)]),
+    "lbm_batch_admit_many": (C.c_int, [_VP, _I32, C.POINTER(Params), C.POINTER(Geometry),
+                                       C.POINTER(C.POINTER(Body)), C.POINTER(_I32), C.POINTER(_I64),
+                                       C.POINTER(_I32)]),
     "lbm_batch_poll": (C.c_int, [_VP, _I32, _DP, _I64, C.POINTER(_I64), C.POINTER(_I32)]),
     "lbm_batch_moments": (C.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "lbm_batch_poll_many": (C.c_int, [_VP, _I32, C.POINTER(_I32), C.POINTER(_DP), C.POINTER(_I64),
+                                      C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32)]),
     "lbm_batch_get_populations": (C.c_int, [_VP, _I32, _VP, _SZ]),
     "lbm_batch_set_populations": (C.c_int, [_VP, _I32, _VP, _SZ]),
     "lbm_batch_steps_done": (C.c_int, [_VP, _I32, C.POINTER(_I64)]),

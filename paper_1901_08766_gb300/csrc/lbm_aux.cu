@@ -645,6 +645,159 @@ cudaError_t launch_row_scatter(cudaStream_t st, const uint8_t *mask, int nx, int
   return cudaGetLastError();
 }
 
+// ---- batched admission ------------------------------------------------------------------
+// The same rasteriser, per-row counts, solid-node lists and initial state as above, for
+// many domains in one launch each: block r of a launch takes row r of the flat row list
+// of all admitted domains (domain d owns rows row0 .. row0 + ny - 1).
+
+__device__ __forceinline__ int admit_domain_of(const AdmitDev *ad, int n, int r) {
+  int lo = 0, hi = n - 1;  // the last domain with row0 <= r
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ad[mid].row0 <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Mask row j (all pitch columns, padding zero) from the domain's shapes, then its per-row
+// node counts of every body id.
+__global__ void admit_raster_count_kernel(AdmitDev *ad, int n) {
+  __shared__ int32_t hist[256];
+  __shared__ int dsh;
+  if (threadIdx.x == 0) dsh = admit_domain_of(ad, n, blockIdx.x);
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  AdmitDev &A = ad[dsh];
+  const int j = blockIdx.x - A.row0;
+  uint8_t *row = A.mask + static_cast<size_t>(j) * A.pitch;
+  for (int i = threadIdx.x; i < A.pitch; i += blockDim.x) {
+    uint8_t b = 0;
+    if (i < A.nx) {
+      for (int k = 0; k < A.nshapes; ++k)
+        if (inside(A.shapes[k], double(i + A.x0), double(j))) b = static_cast<uint8_t>(A.shapes[k].body);
+      atomicAdd(&hist[b], 1);
+    }
+    row[i] = b;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+    const int c = hist[b];
+    if (b <= A.nbodies) A.counts[static_cast<size_t>(b) * A.ny + j] = c;
+    else if (c > 0) atomicMax(&A.bad, b);
+  }
+}
+
+cudaError_t launch_admit_raster_count(cudaStream_t st, AdmitDev *ad, int n, int rows) {
+  if (rows <= 0) return cudaSuccess;
+  admit_raster_count_kernel<<<rows, 256, 0, st>>>(ad, n);
+  return cudaGetLastError();
+}
+
+// Block (r, b - 1): the nodes of body b in row r of the flat list, as row_scatter_kernel.
+__global__ void admit_scatter_kernel(const AdmitDev *ad, int n) {
+  __shared__ int dsh;
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t base;
+  if (threadIdx.x == 0) dsh = admit_domain_of(ad, n, blockIdx.x);
+  __syncthreads();
+  const AdmitDev &A = ad[dsh];
+  const int body = blockIdx.y + 1;
+  if (body > A.nbodies) return;  // uniform over the block
+  const int j = blockIdx.x - A.row0;
+  if (threadIdx.x == 0) base = A.row_off[static_cast<size_t>(body - 1) * A.ny + j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint8_t *row = A.mask + static_cast<size_t>(j) * A.pitch;
+  for (int i0 = 0; i0 < A.nx; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const bool hit = i < A.nx && row[i] == body;
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += warp_tot[w];
+      total += warp_tot[w];
+    }
+    if (hit) A.solid[base + before + __popc(bal & ((1u << lane) - 1u))] = j * A.pitch + i;
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_admit_scatter(cudaStream_t st, const AdmitDev *ad, int n, int rows, int max_bodies) {
+  if (rows <= 0 || max_bodies <= 0) return cudaSuccess;
+  admit_scatter_kernel<<<dim3(rows, max_bodies), 256, 0, st>>>(ad, n);
+  return cudaGetLastError();
+}
+
+// Block (r, a): row r of direction a of lattice A set to f^eq(rho0, u0) as init_kernel
+// does, and the same row of lattice B to zero.
+template <int S>
+__global__ void admit_init_kernel(const AdmitDev *ad, int n) {
+  using Cd = Codec<S>;
+  using E = typename Cd::E;
+  __shared__ int dsh;
+  if (threadIdx.x == 0) dsh = admit_domain_of(ad, n, blockIdx.x);
+  __syncthreads();
+  const AdmitDev &A = ad[dsh];
+  const int j = blockIdx.x - A.row0;
+  const int a = blockIdx.y;
+  const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  const double eu = ex_of(a) * A.u0x + ey_of(a) * A.u0y;
+  const double usq = A.u0x * A.u0x + A.u0y * A.u0y;
+  const double dev = A.rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+  const E val = Cd::enc(typename Cd::T(Cd::kStoreShifted ? dev * Cd::kScale : A.rho0 * w + dev));
+  const size_t off = (static_cast<size_t>(a) * A.ny + j) * A.pitch;
+  E *la = static_cast<E *>(A.lat[0]) + off;
+  E *lb = static_cast<E *>(A.lat[1]) + off;
+  for (int i = threadIdx.x; i < A.pitch; i += blockDim.x) {
+    la[i] = i < A.nx ? val : E(0);
+    lb[i] = E(0);
+  }
+}
+
+cudaError_t launch_admit_init(int storage, cudaStream_t st, const AdmitDev *ad, int n, int rows) {
+  if (rows <= 0) return cudaSuccess;
+  const dim3 grid(rows, kQ);
+  switch (storage) {
+    case LBM_F64: admit_init_kernel<LBM_F64><<<grid, 256, 0, st>>>(ad, n); break;
+    case LBM_F32: admit_init_kernel<LBM_F32><<<grid, 256, 0, st>>>(ad, n); break;
+    case LBM_F16S: admit_init_kernel<LBM_F16S><<<grid, 256, 0, st>>>(ad, n); break;
+    case LBM_BF16S: admit_init_kernel<LBM_BF16S><<<grid, 256, 0, st>>>(ad, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Fill each span: a copy from its source, or zeros (16-byte words where both ends are
+// aligned, bytes otherwise). Block (x, k) strides over span k.
+__global__ void fill_kernel(const FillSeg *segs, int nseg) {
+  for (int k = blockIdx.y; k < nseg; k += gridDim.y) {
+    unsigned char *d = static_cast<unsigned char *>(segs[k].dst);
+    const unsigned char *src = static_cast<const unsigned char *>(segs[k].src);
+    const size_t bytes = segs[k].bytes;
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    const size_t t0 = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(src) | bytes) & 15) == 0;
+    if (vec) {
+      uint4 *dv = reinterpret_cast<uint4 *>(d);
+      const uint4 *sv = reinterpret_cast<const uint4 *>(src);
+      for (size_t i = t0; i < bytes / 16; i += stride) dv[i] = src ? sv[i] : make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      for (size_t i = t0; i < bytes; i += stride) d[i] = src ? src[i] : 0;
+    }
+  }
+}
+
+cudaError_t launch_fill(cudaStream_t st, const FillSeg *segs, int nseg) {
+  if (nseg <= 0) return cudaSuccess;
+  fill_kernel<<<dim3(32, nseg < 65535 ? nseg : 65535), 256, 0, st>>>(segs, nseg);
+  return cudaGetLastError();
+}
+
 // ---- body forces -------------------------------------------------------------------------
 // The sweep of step n+1 writes F_VP of every solid node (Eq. force-density) to the
 // domain's F_VP field; this kernel, launched after it, sums -F_VP over each body's

@@ -140,6 +140,28 @@ struct ShapeDev {
   double cx, cy, radius, chord, thickness, ca, sa;  // ca, sa = cos/sin(aoa) from the host
 };
 
+// One domain of a batched admission (lbm_batch_admit_many): where its mask, lattices and
+// solid-node list live, its geometry, and the position of its rows in the flat row list
+// of all admitted domains (rows row0 .. row0 + ny - 1).
+struct AdmitDev {
+  uint8_t *mask;
+  void *lat[2];
+  int32_t *counts;         // [nbodies + 1][ny] per-row node counts of each body id
+  const int32_t *row_off;  // [nbodies][ny] offsets of each body's nodes of a row in `solid`
+  int32_t *solid;          // the domain's solid-node list
+  const ShapeDev *shapes;
+  int32_t nshapes, nx, ny, pitch, nbodies, x0, row0, bad;  // bad: largest unknown body id
+  double rho0, u0x, u0y;
+};
+
+// A span of device memory to fill (batched admission): a copy of `bytes` from src, or
+// zeros when src is null.
+struct FillSeg {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+
 // Kernel launchers (one translation unit per storage type for the sweep).
 cudaError_t launch_forces(int storage, int grid, cudaStream_t st, const DomDev *doms,
                           const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
@@ -170,6 +192,11 @@ cudaError_t launch_row_scatter(cudaStream_t st, const uint8_t *mask, int nx, int
                                int32_t *solid);
 cudaError_t launch_moments_sized(int storage, cudaStream_t st, const DomDev *dom, int nx,
                                  int ny, int parity, double *rho, double *ux, double *uy);
+// batched admission over the flat row list of n domains (rows: total rows)
+cudaError_t launch_admit_raster_count(cudaStream_t st, AdmitDev *ad, int n, int rows);
+cudaError_t launch_admit_scatter(cudaStream_t st, const AdmitDev *ad, int n, int rows, int max_bodies);
+cudaError_t launch_admit_init(int storage, cudaStream_t st, const AdmitDev *ad, int n, int rows);
+cudaError_t launch_fill(cudaStream_t st, const FillSeg *segs, int nseg);
 
 // per-storage sweep launchers (one translation unit each)
 cudaError_t launch_sweep_f64(int vec, int pipe, int grid, int warps, cudaStream_t st,

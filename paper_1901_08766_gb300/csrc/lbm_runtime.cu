@@ -264,6 +264,8 @@ struct lbm_batch {
   size_t bytes_in_use = 0;
   int sm_count = 0;
   int inject = 0;  // SweepArgs::inject of later sweep launches (host failure injection)
+  char *h_poll = nullptr;  // pinned staging of lbm_batch_poll_many (grows as needed)
+  size_t h_poll_cap = 0;
 };
 
 struct lbm_domain {
@@ -584,36 +586,12 @@ lbm_status read_status(lbm_batch *b, const Slot &s, int *st) {
   return LBM_OK;
 }
 
-lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
-                 const lbm_geometry *geom, const lbm_body *bodies, int nbodies, long long nsteps,
-                 int *slot_out) {
-  lbm_status rc = validate(p, nbodies);
-  if (rc != LBM_OK) return rc;
-  if (p->storage != b->storage) return fail(LBM_EINVAL, "domain storage %d differs from batch storage %d", p->storage, b->storage);
-  if (nbodies > 0 && !bodies) return fail(LBM_EINVAL, "bodies is NULL");
-  if (!mask_host && geom && geom->nshapes > 0 && !geom->shapes) return fail(LBM_EINVAL, "geometry shapes NULL");
-  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
-  if (p->moving) {
-    if (mask_host) return fail(LBM_EINVAL, "a moving domain is rasterised from its geometry (mask given)");
-    if (!geom || geom->nshapes < 1 || geom->nshapes > kMaxMovingShapes)
-      return fail(LBM_EINVAL, "a moving domain needs 1..%d shapes", kMaxMovingShapes);
-  }
-  int k = -1;
-  for (int i = 0; i < b->max_domains; ++i)
-    if (!b->slots[i].used) { k = i; break; }
-  if (k < 0) return fail(LBM_EBUSY, "no free slot");
-  const Layout L = layout_of(*p, nbodies);
-  if (b->budget > 0 && b->bytes_in_use + L.total > b->budget)
-    return fail(LBM_EBUSY, "memory budget exceeded (%zu + %zu > %zu)", b->bytes_in_use, L.total, b->budget);
-  if (geom && !mask_host)
-    for (int i = 0; i < geom->nshapes; ++i) {
-      const lbm_shape &sh = geom->shapes[i];
-      if (sh.kind < 0 || sh.kind > LBM_SHAPE_NACA4) return fail(LBM_EINVAL, "shape %d: unknown kind", i);
-      if (sh.body < 1 || sh.body > nbodies) return fail(LBM_EINVAL, "shape %d: body id %d not in [1, %d]", i, sh.body, nbodies);
-      if (sh.kind == LBM_SHAPE_NACA4 && !(sh.chord > 0)) return fail(LBM_EINVAL, "shape %d: chord must be > 0", i);
-    }
-
-  Slot s;
+// Host-side part of admitting a domain: the slot's parameters, its device block (one
+// allocation holding lattices, mask, F_VP field, body tables, force ring, status word)
+// and its device description with the collision constants. No GPU work is issued.
+lbm_status prepare_slot(lbm_batch *b, const lbm_params *p, const lbm_geometry *geom, int nbodies,
+                        long long nsteps, const Layout &L, Slot &s) {
+  s = Slot();
   s.p = *p;
   if (s.p.force_capacity == 0) s.p.force_capacity = 8192;
   s.nbodies = nbodies;
@@ -680,6 +658,49 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     }
   }
   fill_cell_const(D, p->storage);
+  return LBM_OK;
+}
+
+lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
+                 const lbm_geometry *geom, const lbm_body *bodies, int nbodies, long long nsteps,
+                 int *slot_out) {
+  lbm_status rc = validate(p, nbodies);
+  if (rc != LBM_OK) return rc;
+  if (p->storage != b->storage) return fail(LBM_EINVAL, "domain storage %d differs from batch storage %d", p->storage, b->storage);
+  if (nbodies > 0 && !bodies) return fail(LBM_EINVAL, "bodies is NULL");
+  if (!mask_host && geom && geom->nshapes > 0 && !geom->shapes) return fail(LBM_EINVAL, "geometry shapes NULL");
+  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+  if (p->moving) {
+    if (mask_host) return fail(LBM_EINVAL, "a moving domain is rasterised from its geometry (mask given)");
+    if (!geom || geom->nshapes < 1 || geom->nshapes > kMaxMovingShapes)
+      return fail(LBM_EINVAL, "a moving domain needs 1..%d shapes", kMaxMovingShapes);
+  }
+  int k = -1;
+  for (int i = 0; i < b->max_domains; ++i)
+    if (!b->slots[i].used) { k = i; break; }
+  if (k < 0) return fail(LBM_EBUSY, "no free slot");
+  const Layout L = layout_of(*p, nbodies);
+  if (b->budget > 0 && b->bytes_in_use + L.total > b->budget)
+    return fail(LBM_EBUSY, "memory budget exceeded (%zu + %zu > %zu)", b->bytes_in_use, L.total, b->budget);
+  if (geom && !mask_host)
+    for (int i = 0; i < geom->nshapes; ++i) {
+      const lbm_shape &sh = geom->shapes[i];
+      if (sh.kind < 0 || sh.kind > LBM_SHAPE_NACA4) return fail(LBM_EINVAL, "shape %d: unknown kind", i);
+      if (sh.body < 1 || sh.body > nbodies) return fail(LBM_EINVAL, "shape %d: body id %d not in [1, %d]", i, sh.body, nbodies);
+      if (sh.kind == LBM_SHAPE_NACA4 && !(sh.chord > 0)) return fail(LBM_EINVAL, "shape %d: chord must be > 0", i);
+    }
+
+  Slot s;
+  {
+    lbm_status prc = prepare_slot(b, p, geom, nbodies, nsteps, L, s);
+    if (prc != LBM_OK) return prc;
+  }
+  char *base = static_cast<char *>(s.block);
+  DomDev &D = s.dev;
+  uint8_t *mask = D.mask;
+  double *bod = D.bodies;
+  float *bodf = D.bodies_f;
+  int32_t *off = const_cast<int32_t *>(D.solid_off);
   cudaStream_t st = b->st;
   void *tmp = nullptr;  // admission temporaries (row counts, offsets, shapes)
   auto bail = [&](lbm_status r) {
@@ -804,6 +825,254 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   return LBM_OK;
 }
 
+// Many fixed-geometry domains at once: the work of admit() for every domain, batched
+// into a few launches over the rows of all of them, one upload of host tables, one
+// read-back of the per-row counts (the only synchronisation before the solid lists can
+// be sized) and a final one. All or none are admitted.
+lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geometry *geoms,
+                      const lbm_body *const *bodies, const int32_t *nbs, const int64_t *nsteps,
+                      int32_t *slots_out) {
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  if (n == 0) return LBM_OK;
+  if (!ps || !geoms || !nbs || !nsteps || !slots_out) return fail(LBM_EINVAL, "an argument array is NULL");
+  for (int i = 0; i < n; ++i) {
+    const lbm_params *p = &ps[i];
+    lbm_status rc = validate(p, nbs[i]);
+    if (rc != LBM_OK) return fail(rc, "domain %d: %s", i, lbm_last_error());
+    if (p->storage != b->storage) return fail(LBM_EINVAL, "domain %d: storage %d differs from batch storage %d", i, p->storage, b->storage);
+    if (p->moving) return fail(LBM_EINVAL, "domain %d: moving domains are admitted with lbm_batch_admit", i);
+    if (nbs[i] > 0 && (!bodies || !bodies[i])) return fail(LBM_EINVAL, "domain %d: bodies is NULL", i);
+    if (nsteps[i] < 0) return fail(LBM_EINVAL, "domain %d: nsteps must be >= 0", i);
+    const lbm_geometry &g = geoms[i];
+    if (g.nshapes < 0 || (g.nshapes > 0 && !g.shapes)) return fail(LBM_EINVAL, "domain %d: geometry shapes NULL", i);
+    for (int q = 0; q < g.nshapes; ++q) {
+      const lbm_shape &sh = g.shapes[q];
+      if (sh.kind < 0 || sh.kind > LBM_SHAPE_NACA4) return fail(LBM_EINVAL, "domain %d shape %d: unknown kind", i, q);
+      if (sh.body < 1 || sh.body > nbs[i]) return fail(LBM_EINVAL, "domain %d shape %d: body id %d not in [1, %d]", i, q, sh.body, nbs[i]);
+      if (sh.kind == LBM_SHAPE_NACA4 && !(sh.chord > 0)) return fail(LBM_EINVAL, "domain %d shape %d: chord must be > 0", i, q);
+    }
+  }
+  std::vector<int> ks;
+  for (int k = 0; k < b->max_domains && static_cast<int>(ks.size()) < n; ++k)
+    if (!b->slots[k].used) ks.push_back(k);
+  if (static_cast<int>(ks.size()) < n) return fail(LBM_EBUSY, "%d free slots for %d domains", static_cast<int>(ks.size()), n);
+  std::vector<Layout> Ls(n);
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    Ls[i] = layout_of(ps[i], nbs[i]);
+    need += Ls[i].total;
+  }
+  if (b->budget > 0 && b->bytes_in_use + need > b->budget)
+    return fail(LBM_EBUSY, "memory budget exceeded (%zu + %zu > %zu)", b->bytes_in_use, need, b->budget);
+
+  cudaStream_t st = b->st;
+  std::vector<Slot> S(n);
+  void *tmp = nullptr;
+  auto release = [&](lbm_status r) {
+    cudaStreamSynchronize(st);
+    for (Slot &x : S) {
+      b->al.put(x.block);
+      b->al.put(x.solid);
+    }
+    b->al.put(tmp);
+    return r;
+  };
+  for (int i = 0; i < n; ++i) {
+    lbm_status rc = prepare_slot(b, &ps[i], &geoms[i], nbs[i], nsteps[i], Ls[i], S[i]);
+    if (rc != LBM_OK) return release(rc);
+  }
+
+  // device temporaries, packed: descriptors, per-row counts, row offsets, shapes, body
+  // tables and solid offsets (staged for copying into each domain's block), fill spans
+  size_t rows = 0, counts_n = 0, offs_n = 0, nsh = 0, nbt = 0, nso = 0;
+  for (int i = 0; i < n; ++i) {
+    rows += ps[i].ny;
+    counts_n += static_cast<size_t>(nbs[i] + 1) * ps[i].ny;
+    offs_n += static_cast<size_t>(nbs[i]) * ps[i].ny;
+    nsh += geoms[i].nshapes;
+    nbt += 5 * static_cast<size_t>(std::max(1, nbs[i]));
+    nso += static_cast<size_t>(nbs[i]) + 1;
+  }
+  int nrings = 0;
+  for (int i = 0; i < n; ++i) nrings += ps[i].force_every > 0 ? 1 : 0;
+  const int nseg1 = 5 * n + nrings, nseg2 = 2 * n;  // fills before and after the counts are known
+  const size_t o_ad = 0;
+  const size_t o_cnt = align_up(o_ad + sizeof(AdmitDev) * n, 256);
+  const size_t o_ro = align_up(o_cnt + sizeof(int32_t) * counts_n, 256);
+  const size_t o_sh = align_up(o_ro + sizeof(int32_t) * std::max<size_t>(1, offs_n), 256);
+  const size_t o_bd = align_up(o_sh + sizeof(ShapeDev) * std::max<size_t>(1, nsh), 256);
+  const size_t o_bf = align_up(o_bd + sizeof(double) * nbt, 256);
+  const size_t o_so = align_up(o_bf + sizeof(float) * nbt, 256);
+  const size_t o_dd = align_up(o_so + sizeof(int32_t) * nso, 256);
+  const size_t o_s1 = align_up(o_dd + sizeof(DomDev) * n, 256);
+  const size_t o_s2 = align_up(o_s1 + sizeof(FillSeg) * nseg1, 256);
+  const size_t tmp_bytes = o_s2 + sizeof(FillSeg) * nseg2;
+  tmp = b->al.get(tmp_bytes);
+  if (!tmp) return release(fail(LBM_ENOMEM, "temporary allocation of %zu bytes failed", tmp_bytes));
+  char *t = static_cast<char *>(tmp);
+  std::vector<AdmitDev> ad(n);
+  std::vector<ShapeDev> shapes;
+  std::vector<double> hb;
+  std::vector<float> hbf;
+  std::vector<FillSeg> seg1;
+  seg1.reserve(nseg1);
+  shapes.reserve(nsh);
+  hb.reserve(nbt);
+  hbf.reserve(nbt);
+  size_t r0 = 0, c0 = 0, s0 = 0;
+  for (int i = 0; i < n; ++i) {
+    const lbm_params &p = ps[i];
+    Slot &x = S[i];
+    DomDev &D = x.dev;
+    AdmitDev &A = ad[i];
+    A.mask = D.mask;
+    A.lat[0] = D.lat[0];
+    A.lat[1] = D.lat[1];
+    A.counts = reinterpret_cast<int32_t *>(t + o_cnt) + c0;
+    A.row_off = nullptr;
+    A.solid = nullptr;
+    A.shapes = reinterpret_cast<const ShapeDev *>(t + o_sh) + s0;
+    A.nshapes = geoms[i].nshapes;
+    A.nx = p.nx;
+    A.ny = p.ny;
+    A.pitch = x.pitch;
+    A.nbodies = nbs[i];
+    A.x0 = p.x_origin;
+    A.row0 = static_cast<int32_t>(r0);
+    A.bad = 0;
+    A.rho0 = p.rho0;
+    A.u0x = p.u0_x;
+    A.u0y = p.u0_y;
+    for (int q = 0; q < geoms[i].nshapes; ++q) {
+      const lbm_shape &sh = geoms[i].shapes[q];
+      shapes.push_back(ShapeDev{sh.kind, sh.body, sh.cx, sh.cy, sh.radius, sh.chord, sh.thickness,
+                                std::cos(sh.aoa_rad), std::sin(sh.aoa_rad)});
+    }
+    const size_t bt0 = hb.size();
+    for (int q = 0; q < std::max(1, nbs[i]); ++q) {
+      const bool real = q < nbs[i];
+      const double v[5] = {real ? bodies[i][q].cx : 0.0, real ? bodies[i][q].cy : 0.0,
+                           real ? bodies[i][q].vx : 0.0, real ? bodies[i][q].vy : 0.0,
+                           real ? bodies[i][q].omega : 0.0};
+      for (double e : v) {
+        hb.push_back(e);
+        hbf.push_back(static_cast<float>(e));
+      }
+    }
+    const size_t bt = hb.size() - bt0;
+    const Layout &L = Ls[i];
+    char *base = static_cast<char *>(x.block);
+    seg1.push_back(FillSeg{D.bodies, t + o_bd + sizeof(double) * bt0, sizeof(double) * bt});
+    seg1.push_back(FillSeg{D.bodies_f, t + o_bf + sizeof(float) * bt0, sizeof(float) * bt});
+    // dilation rates (zero: no body pulsates), status word, F_VP field, force ring
+    seg1.push_back(FillSeg{base + L.kappa_off, nullptr,
+                           align_up(sizeof(double) * std::max(1, nbs[i]), 256) + sizeof(float) * std::max(1, nbs[i])});
+    seg1.push_back(FillSeg{D.status, nullptr, sizeof(int32_t)});
+    seg1.push_back(FillSeg{D.fvp, nullptr, L.bodies_off - L.fvp_off});
+    r0 += p.ny;
+    c0 += static_cast<size_t>(nbs[i] + 1) * p.ny;
+    s0 += geoms[i].nshapes;
+  }
+  // force rings (of the domains that record forces)
+  for (int i = 0; i < n; ++i)
+    if (ps[i].force_every > 0)
+      seg1.push_back(FillSeg{S[i].dev.ring, nullptr,
+                             sizeof(double) * 2 * std::max(1, nbs[i]) * S[i].p.force_capacity});
+  FillSeg *d_fill1 = reinterpret_cast<FillSeg *>(t + o_s1);
+#define ADM_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return release(fail(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));  \
+  } while (0)
+  ADM_CUDA(cudaMemcpyAsync(t + o_ad, ad.data(), sizeof(AdmitDev) * n, cudaMemcpyHostToDevice, st));
+  if (!shapes.empty())
+    ADM_CUDA(cudaMemcpyAsync(t + o_sh, shapes.data(), sizeof(ShapeDev) * shapes.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(t + o_bd, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(t + o_bf, hbf.data(), sizeof(float) * hbf.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(d_fill1, seg1.data(), sizeof(FillSeg) * seg1.size(), cudaMemcpyHostToDevice, st));
+  AdmitDev *d_ad = reinterpret_cast<AdmitDev *>(t + o_ad);
+  ADM_CUDA(launch_fill(st, d_fill1, static_cast<int>(seg1.size())));
+  ADM_CUDA(launch_admit_raster_count(st, d_ad, n, static_cast<int>(rows)));
+  ADM_CUDA(launch_admit_init(b->storage, st, d_ad, n, static_cast<int>(rows)));
+  // per-row counts and unknown body ids back to the host: the one synchronisation needed
+  std::vector<int32_t> hc(counts_n);
+  ADM_CUDA(cudaMemcpyAsync(hc.data(), t + o_cnt, sizeof(int32_t) * counts_n, cudaMemcpyDeviceToHost, st));
+  ADM_CUDA(cudaMemcpyAsync(ad.data(), d_ad, sizeof(AdmitDev) * n, cudaMemcpyDeviceToHost, st));
+  ADM_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i)
+    if (ad[i].bad > 0)
+      return release(fail(LBM_EINVAL, "domain %d: mask holds body id %d but only %d bodies were given", i, ad[i].bad, nbs[i]));
+  // solid-node offsets per body and per (body, row); the solid lists
+  std::vector<int32_t> hro(std::max<size_t>(1, offs_n), 0), hso;
+  hso.reserve(nso);
+  std::vector<size_t> nsolid(n);
+  {
+    size_t cc = 0, oo = 0;
+    for (int i = 0; i < n; ++i) {
+      const int ny = ps[i].ny, nb = nbs[i];
+      int32_t acc = 0;
+      std::vector<int32_t> ho(nb + 1, 0);
+      for (int q = 1; q <= nb; ++q) {
+        ho[q - 1] = acc;
+        for (int j = 0; j < ny; ++j) {
+          hro[oo + static_cast<size_t>(q - 1) * ny + j] = acc;
+          acc += hc[cc + static_cast<size_t>(q) * ny + j];
+        }
+      }
+      ho[nb] = acc;
+      hso.insert(hso.end(), ho.begin(), ho.end());
+      S[i].solid_off = ho;
+      nsolid[i] = static_cast<size_t>(acc);
+      S[i].solid = b->al.get(sizeof(int32_t) * std::max<size_t>(1, nsolid[i]));
+      if (!S[i].solid) return release(fail(LBM_ENOMEM, "solid list allocation failed"));
+      S[i].dev.solid = static_cast<const int32_t *>(S[i].solid);
+      ad[i].solid = static_cast<int32_t *>(S[i].solid);
+      ad[i].row_off = reinterpret_cast<const int32_t *>(t + o_ro) + oo;
+      cc += static_cast<size_t>(nb + 1) * ny;
+      oo += static_cast<size_t>(nb) * ny;
+    }
+  }
+  // second upload: row offsets, descriptors with the solid lists, per-domain solid
+  // offsets and the domains' device descriptions, copied into place by one fill launch
+  std::vector<DomDev> dd(n);
+  std::vector<FillSeg> seg2;
+  {
+    size_t so = 0;
+    for (int i = 0; i < n; ++i) {
+      dd[i] = S[i].dev;
+      seg2.push_back(FillSeg{const_cast<int32_t *>(S[i].dev.solid_off), t + o_so + sizeof(int32_t) * so,
+                             sizeof(int32_t) * (nbs[i] + 1)});
+      seg2.push_back(FillSeg{b->d_doms + ks[i], t + o_dd + sizeof(DomDev) * i, sizeof(DomDev)});
+      so += static_cast<size_t>(nbs[i]) + 1;
+    }
+  }
+  if (offs_n > 0)
+    ADM_CUDA(cudaMemcpyAsync(t + o_ro, hro.data(), sizeof(int32_t) * offs_n, cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(d_ad, ad.data(), sizeof(AdmitDev) * n, cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(t + o_so, hso.data(), sizeof(int32_t) * hso.size(), cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(t + o_dd, dd.data(), sizeof(DomDev) * n, cudaMemcpyHostToDevice, st));
+  ADM_CUDA(cudaMemcpyAsync(t + o_s2, seg2.data(), sizeof(FillSeg) * seg2.size(), cudaMemcpyHostToDevice, st));
+  int max_nb = 0;
+  for (int i = 0; i < n; ++i) max_nb = std::max(max_nb, nbs[i]);
+  ADM_CUDA(launch_admit_scatter(st, d_ad, n, static_cast<int>(rows), max_nb));
+  ADM_CUDA(launch_fill(st, reinterpret_cast<const FillSeg *>(t + o_s2), static_cast<int>(seg2.size())));
+  ADM_CUDA(cudaStreamSynchronize(st));
+#undef ADM_CUDA
+  b->al.put(tmp);
+  tmp = nullptr;
+  for (int i = 0; i < n; ++i) {
+    Slot &x = S[i];
+    x.used = true;
+    x.bytes = Ls[i].total + sizeof(int32_t) * std::max<size_t>(1, nsolid[i]);
+    b->bytes_in_use += x.bytes;
+    b->slots[ks[i]] = x;
+    slots_out[i] = ks[i];
+  }
+  b->dirty = true;
+  return LBM_OK;
+}
+
 lbm_status check_slot(lbm_batch *b, int slot) {
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   if (slot < 0 || slot >= b->max_domains || !b->slots[slot].used)
@@ -840,6 +1109,67 @@ lbm_status poll(lbm_batch *b, int slot, double *out, long long max_entries, long
   if (done) *done = (s.done >= s.target && s.drained >= produced) ? 1 : 0;
   if (status & 2) return fail(LBM_ETIMEOUT, "slot %d: a sweep gave up waiting for its row copies", slot);
   if (status & 1) return fail(LBM_EUNSTABLE, "slot %d diverged (rho out of range or not finite)", slot);
+  return LBM_OK;
+}
+
+// Many slots' new force entries and status words, staged in pinned host memory by
+// asynchronous copies and read after one synchronisation.
+lbm_status poll_many(lbm_batch *b, int n, const int32_t *slots, double *const *outs,
+                     const int64_t *max_entries, int64_t *written, int32_t *done, int32_t *status) {
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  if (n == 0) return LBM_OK;
+  if (!slots || !outs || !max_entries || !written || !done || !status)
+    return fail(LBM_EINVAL, "an argument array is NULL");
+  std::vector<long long> cnt(n);
+  std::vector<size_t> at(n);
+  size_t bytes = align_up(sizeof(int32_t) * n, 16);
+  for (int i = 0; i < n; ++i) {
+    lbm_status rc = check_slot(b, slots[i]);
+    if (rc != LBM_OK) return rc;
+    const Slot &s = b->slots[slots[i]];
+    cnt[i] = std::min(entries_at(s, s.done) - s.drained, std::max<long long>(0, max_entries[i]));
+    if (cnt[i] > 0 && !outs[i]) return fail(LBM_EINVAL, "outs[%d] is NULL", i);
+    at[i] = bytes;
+    bytes += sizeof(double) * 2 * static_cast<size_t>(s.nbodies) * static_cast<size_t>(std::max(0ll, cnt[i]));
+  }
+  if (bytes > b->h_poll_cap) {
+    if (b->h_poll) cudaFreeHost(b->h_poll);
+    b->h_poll = nullptr;
+    b->h_poll_cap = 0;
+    const size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
+    if (cudaMallocHost(&b->h_poll, cap) != cudaSuccess) {
+      cudaGetLastError();
+      b->h_poll = nullptr;
+      return fail(LBM_ENOMEM, "pinned staging of %zu bytes failed", cap);
+    }
+    b->h_poll_cap = cap;
+  }
+  int32_t *st_words = reinterpret_cast<int32_t *>(b->h_poll);
+  for (int i = 0; i < n; ++i) {
+    const Slot &s = b->slots[slots[i]];
+    LBM_CUDA(cudaMemcpyAsync(st_words + i, s.dev.status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->st));
+    const size_t per = 2 * static_cast<size_t>(s.nbodies);
+    long long copied = 0;
+    while (copied < cnt[i] && per > 0) {
+      const long long e = s.drained + copied;
+      const long long pos = e % s.dev.force_cap;
+      const long long chunk = std::min(cnt[i] - copied, static_cast<long long>(s.dev.force_cap) - pos);
+      LBM_CUDA(cudaMemcpyAsync(b->h_poll + at[i] + sizeof(double) * copied * per, s.dev.ring + pos * per,
+                               sizeof(double) * per * chunk, cudaMemcpyDeviceToHost, b->st));
+      copied += chunk;
+    }
+  }
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  for (int i = 0; i < n; ++i) {
+    Slot &s = b->slots[slots[i]];
+    const size_t per = 2 * static_cast<size_t>(s.nbodies);
+    if (cnt[i] > 0 && per > 0) std::memcpy(outs[i], b->h_poll + at[i], sizeof(double) * per * cnt[i]);
+    s.drained += std::max(0ll, cnt[i]);
+    written[i] = std::max(0ll, cnt[i]);
+    done[i] = (s.done >= s.target && s.drained >= entries_at(s, s.done)) ? 1 : 0;
+    const int w = st_words[i];
+    status[i] = (w & 2) ? LBM_ETIMEOUT : ((w & 1) ? LBM_EUNSTABLE : LBM_OK);
+  }
   return LBM_OK;
 }
 
@@ -913,6 +1243,7 @@ void destroy(lbm_batch *b) {
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->h_dyn) cudaFreeHost(b->h_dyn);
   if (b->h_ctr) cudaFreeHost(b->h_ctr);
+  if (b->h_poll) cudaFreeHost(b->h_poll);
   if (b->dyn_ev) cudaEventDestroy(b->dyn_ev);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
   delete b;
@@ -1095,6 +1426,13 @@ lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint8_t *mas
   return rc;
 }
 
+lbm_status lbm_batch_admit_many(lbm_batch *b, int32_t n, const lbm_params *params,
+                                const lbm_geometry *geoms, const lbm_body *const *bodies,
+                                const int32_t *nbodies, const int64_t *nsteps, int32_t *slots) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  return admit_many(b, n, params, geoms, bodies, nbodies, nsteps, slots);
+}
+
 lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps_run) {
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   long long n = 0;
@@ -1111,6 +1449,13 @@ lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_e
   if (written) *written = w;
   if (done) *done = d;
   return rc;
+}
+
+lbm_status lbm_batch_poll_many(lbm_batch *b, int32_t n, const int32_t *slots, double *const *outs,
+                               const int64_t *max_entries, int64_t *written, int32_t *done,
+                               int32_t *status) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  return poll_many(b, n, slots, outs, max_entries, written, done, status);
 }
 
 lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, double *ux, double *uy) {

@@ -35,7 +35,7 @@ from . import diagnostics
 class Result:
     request_id: int
     name: str
-    status: str                      # "ok", "unstable", "cancelled" or "rejected"
+    status: str                      # "ok", "unstable", "failed", "cancelled" or "rejected"
     forces: np.ndarray               # [steps, nbodies, 2]: force on each body per step
     steps: int
     cells: int
@@ -75,10 +75,12 @@ class Server:
             backend = Batch(storage, max_domains=max_domains, hbm_budget=hbm_budget,
                             graph_steps=graph_steps)
         self.backend = backend
+        self.max_domains = max_domains
         self.storage = storage
         self.hbm_budget = hbm_budget
         self.chunk_steps = int(chunk_steps)
         self.force_every = int(force_every)
+        self.force_capacity = self.chunk_steps + 8  # force entries of one chunk per request
         self.clock = clock
         self.autotune = autotune
         # at most this many requests share the GPU at once (None: as many as memory holds);
@@ -98,6 +100,9 @@ class Server:
         self.t_start = None
         self.chunks_run = 0
         self.max_queue = 0
+        # host time per part of the loop (seconds): admission, enqueueing the chunk, draining
+        # (which waits for the chunk on the GPU)
+        self.host_s = {"admit": 0.0, "run": 0.0, "drain": 0.0}
 
     # ---- client side ---------------------------------------------------------------
     def submit(self, spec, nsteps=None, arrival=None, on_forces=None) -> Future:
@@ -145,15 +150,57 @@ class Server:
                     del self._resident[slot]
                     self._finish(q, "cancelled")
 
+    def _admit_group(self):
+        """Admit the longest FIFO prefix of the queue that fits the free slots and the
+        memory budget with one batched admission (backends that offer it). False when
+        nothing was admitted that way (the one-by-one path then decides)."""
+        from . import domain_bytes
+        from ._native import LbmError
+        if not hasattr(self.backend, "admit_many") or len(self._queue) < 2:
+            return False
+        info = self.backend.info()
+        room = self.max_domains - info["resident"]
+        if self.max_resident is not None:
+            room = min(room, self.max_resident - len(self._resident))
+        left = self.hbm_budget - info["bytes_in_use"] if self.hbm_budget > 0 else None
+        group = []
+        for req in self._queue:
+            if len(group) >= room:
+                break
+            if req.spec.get("moving") or any(b.get("dynamics") or b.get("deform") for b in req.spec["bodies"]):
+                break
+            need = domain_bytes(req.spec, self.storage, self.force_every, self.force_capacity)
+            if left is not None:
+                if need > left:
+                    break
+                left -= need
+            group.append(req)
+        if len(group) < 2:
+            return False
+        try:
+            slots = self.backend.admit_many([r.spec for r in group], nsteps=[r.nsteps for r in group],
+                                            force_every=self.force_every,
+                                            force_capacity=self.force_capacity)
+        except LbmError:
+            return False  # nothing admitted: the one-by-one path finds the culprit
+        now = self.clock()
+        for req, slot in zip(group, slots):
+            self._queue.popleft()
+            req.slot = slot
+            req.admitted = now
+            self._resident[slot] = req
+        return True
+
     def _admit(self):
         from ._native import LbmError
+        self._admit_group()
         while self._queue:
             if self.max_resident is not None and len(self._resident) >= self.max_resident:
                 break
             req = self._queue[0]
             try:
                 slot = self.backend.try_admit(req.spec, nsteps=req.nsteps, force_every=self.force_every,
-                                              force_capacity=self.chunk_steps + 8)
+                                              force_capacity=self.force_capacity)
             except LbmError as e:  # invalid request
                 self._queue.popleft()
                 self._finish(req, "rejected", str(e))
@@ -172,6 +219,24 @@ class Server:
 
     def _drain(self):
         from ._native import LBM_EUNSTABLE, LbmError
+        if hasattr(self.backend, "poll_many_status"):
+            # every resident's new force slice with one synchronisation
+            items = list(self._resident.items())
+            for (slot, req), (f, done, st) in zip(items, self.backend.poll_many_status([s for s, _ in items])):
+                if len(f):
+                    req.chunks.append(f)
+                    if req.on_forces is not None:
+                        req.on_forces(req.rid, f)
+                if st != 0:
+                    self.backend.evict(slot)
+                    del self._resident[slot]
+                    self._finish(req, "unstable" if st == LBM_EUNSTABLE else "failed",
+                                 f"device status {st}")
+                elif done:
+                    self.backend.evict(slot)
+                    del self._resident[slot]
+                    self._finish(req, "ok")
+            return
         for slot, req in list(self._resident.items()):
             try:
                 f, done = self.backend.poll(slot)
@@ -197,16 +262,22 @@ class Server:
         if self.t_start is None:
             self.t_start = now
         self._arrivals(now)
+        t0 = time.perf_counter()
         self._admit()
+        t1 = time.perf_counter()
+        self.host_s["admit"] += t1 - t0
         if self._resident:
             if self.autotune and not self._tuned:
                 self.backend.autotune(reps=3)
                 self._tuned = True
             ran = self.backend.run(self.chunk_steps)
+            t2 = time.perf_counter()
             self.chunks_run += 1
             self._drain()
             if ran == 0:
                 self._drain()
+            self.host_s["run"] += t2 - t1
+            self.host_s["drain"] += time.perf_counter() - t2
         with self._lock:
             pending = bool(self._pending)
             next_arrival = self._pending[0][0] if pending else None
@@ -245,4 +316,5 @@ class Server:
                 "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
                 "glups": self.cell_updates / wall / 1e9 if wall > 0 else None,
-                "wall_s": wall, "chunks": self.chunks_run, "max_queue": self.max_queue}
+                "wall_s": wall, "chunks": self.chunks_run, "max_queue": self.max_queue,
+                "host_s": dict(self.host_s)}

@@ -1,0 +1,118 @@
+"""Batched admission (lbm_batch_admit_many) against admitting the same domains one by one
+(lbm_batch_admit): the same masks, solid-node lists (seen through the force series),
+initial states and, after stepping, the same populations bit for bit, for every storage
+type, ragged sizes, NACA sections and domains without bodies. Failures admit nothing."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+LBM_EINVAL, LBM_EBUSY = 1, 6
+
+
+def _mixed_specs():
+    specs = synth.batched_domains(6)
+    specs.append(synth.naca0012(7.0, 800.0, chord=60.0, U=0.05, nx=301, ny=133, steps=100))
+    specs.append(synth._spec("empty", 65, 7, 0.05, [], [], 0, 0.02,
+                             synth._edges("inlet", "outflow", "free_slip", "free_slip"), u_in=(0.02, 0.0)))
+    specs.append(synth.parity_case("periodic_97x61"))
+    return specs
+
+
+def _run(lbm, storage, specs, batched, steps=23):
+    b = lbm.Batch(storage, max_domains=len(specs) + 2, graph_steps=8)
+    if batched:
+        slots = b.admit_many(specs, nsteps=steps + 5, force_capacity=64)
+    else:
+        slots = [b.admit(sp, nsteps=steps + 5, force_capacity=64) for sp in specs]
+    masks = [b.mask(k) for k in slots]
+    init = [b.get_populations(k) for k in slots]
+    b.run(steps)
+    out = [(b.get_populations(k), b.poll(k)[0]) for k in slots]
+    info = b.info()
+    b.close()
+    return slots, masks, init, out, info
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+def test_admit_many_equals_one_by_one(lbm, storage):
+    specs = _mixed_specs()
+    s1, m1, i1, o1, info1 = _run(lbm, storage, specs, False)
+    s2, m2, i2, o2, info2 = _run(lbm, storage, specs, True)
+    assert s1 == s2
+    assert info1["bytes_in_use"] == info2["bytes_in_use"] and info1["cells"] == info2["cells"]
+    for a, b in zip(m1, m2):
+        assert np.array_equal(a, b)
+    for a, b in zip(i1, i2):
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    for (pa, fa), (pb, fb) in zip(o1, o2):
+        assert np.array_equal(pa.view(np.uint8), pb.view(np.uint8))
+        assert np.array_equal(fa, fb)
+
+
+def test_admit_many_into_a_batch_with_residents_and_mixed_kinds(lbm):
+    # slots already taken, then a batched group that also holds a moving domain (admitted
+    # on its own); the whole batch steps as when every domain was admitted one by one
+    specs = _mixed_specs()
+    moving = dict(synth.parity_case("channel_97x61"), moving=True)
+    b = lbm.Batch("f16s", max_domains=16, graph_steps=0)
+    first = b.admit(specs[0], nsteps=30)
+    rest = b.admit_many(specs[1:] + [moving], nsteps=30)
+    assert first not in rest and len(set(rest)) == len(rest)
+    b.run(30)
+    got = [b.get_populations(k) for k in [first] + rest]
+    b.close()
+    ref = lbm.Batch("f16s", max_domains=16, graph_steps=0)
+    ks = [ref.admit(sp, nsteps=30) for sp in specs + [moving]]
+    ref.run(30)
+    want = [ref.get_populations(k) for k in ks]
+    ref.close()
+    for g, w in zip(got, want):
+        assert np.array_equal(g.view(np.uint16), w.view(np.uint16))
+
+
+def test_admit_many_failures_admit_nothing(lbm):
+    specs = synth.batched_domains(4)
+    b = lbm.Batch("f16s", max_domains=8, graph_steps=0)
+    k0 = b.admit(specs[0], nsteps=10)
+    before = b.info()
+    # a shape naming a body that does not exist
+    bad = dict(specs[2], shapes=[dict(s, body=3) for s in specs[2]["shapes"]])
+    with pytest.raises(lbm.LbmError) as ei:
+        b.admit_many([specs[1], bad], nsteps=10)
+    assert ei.value.status == LBM_EINVAL
+    assert b.info() == before
+    # more domains than free slots
+    with pytest.raises(lbm.LbmError) as ei:
+        b.admit_many(synth.batched_domains(8), nsteps=10)
+    assert ei.value.status == LBM_EBUSY
+    assert b.info() == before
+    b.close()
+    # over the memory budget
+    need = sum(lbm.domain_bytes(sp, "f16s") for sp in specs)
+    c = lbm.Batch("f16s", max_domains=8, hbm_budget=need // 2, graph_steps=0)
+    with pytest.raises(lbm.LbmError) as ei:
+        c.admit_many(specs, nsteps=10)
+    assert ei.value.status == LBM_EBUSY
+    assert c.info()["resident"] == 0 and c.info()["bytes_in_use"] == 0
+    c.close()
+    del k0
+
+
+def test_poll_many_equals_polls(lbm):
+    specs = synth.batched_domains(6)
+    got, want = [], []
+    for many in (True, False):
+        b = lbm.Batch("f16s", max_domains=8, graph_steps=0)
+        slots = b.admit_many(specs, nsteps=[11 + k for k in range(len(specs))], force_capacity=32)
+        for _ in range(3):
+            b.run(5)
+            out = b.poll_many(slots) if many else [b.poll(k) for k in slots]
+            (got if many else want).append(out)
+        b.close()
+    for ga, wa in zip(got, want):
+        for (fa, da), (fb, db) in zip(ga, wa):
+            assert da == db and np.array_equal(fa, fb)
+    assert [d for _, d in got[-1]] == [True] * 5 + [False]  # nsteps 11..16 after 15 steps

@@ -62,6 +62,38 @@ class FakeBatch:
         return 1.0
 
 
+class FakeBatchMany(FakeBatch):
+    """FakeBatch with the batched calls: all-or-none admission of many requests and one
+    poll for many slots that reports each slot's status instead of raising."""
+
+    def info(self):
+        return {"resident": len(self.slots), "bytes_in_use": 0}
+
+    def admit_many(self, specs, nsteps, force_every=1, force_capacity=0):
+        used = sum(s["cells"] for s in self.slots.values())
+        for sp in specs:
+            if sp["nx"] < 3:
+                raise LbmError(LBM_EINVAL, "lbm_batch_admit_many", "nx must be >= 3")
+            used += sp["nx"] * sp["ny"]
+        if used > self.budget or len(self.slots) + len(specs) > self.max_slots:
+            raise LbmError(LBM_EBUSY, "lbm_batch_admit_many", "does not fit")
+        self.groups = getattr(self, "groups", 0) + 1
+        return [self.try_admit(sp, n, force_every, force_capacity) for sp, n in zip(specs, nsteps)]
+
+    def poll_many_status(self, slots):
+        out = []
+        for k in slots:
+            try:
+                f, done = self.poll(k)
+                out.append((f, done, 0))
+            except LbmError as e:
+                out.append((np.zeros((0, self.slots[k]["nb"], 2)), False, e.status))
+        return out
+
+
+FAKES = [FakeBatch, FakeBatchMany]
+
+
 class Clock:
     def __init__(self):
         self.t = 0.0
@@ -75,9 +107,10 @@ def _spec(name, n=100, steps=50):
     return dict(sp, name=name, nx=n, ny=n // 2, steps=steps)
 
 
-def test_fifo_admission_under_budget_and_streaming():
+@pytest.mark.parametrize("Fake", FAKES)
+def test_fifo_admission_under_budget_and_streaming(Fake):
     clock = Clock()
-    fb = FakeBatch(budget_cells=2 * 100 * 50, clock=clock)
+    fb = Fake(budget_cells=2 * 100 * 50, clock=clock)
     srv = srvmod.Server(backend=fb, chunk_steps=16, clock=clock)
     seen = {}
     futs = [srv.submit(_spec(f"r{i}", steps=40 + 10 * i), arrival=0.0,
@@ -99,9 +132,10 @@ def test_fifo_admission_under_budget_and_streaming():
     assert st["completed"] == 4 and st["p99_latency_s"] >= st["p50_latency_s"] > 0
 
 
-def test_resident_cap_keeps_fifo_and_limits_sharing():
+@pytest.mark.parametrize("Fake", FAKES)
+def test_resident_cap_keeps_fifo_and_limits_sharing(Fake):
     clock = Clock()
-    fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
+    fb = Fake(budget_cells=10 ** 9, clock=clock)
     srv = srvmod.Server(backend=fb, chunk_steps=10, clock=clock, max_resident=2)
     futs = [srv.submit(_spec(f"r{i}", steps=30), arrival=0.0) for i in range(5)]
     peak = 0
@@ -116,9 +150,10 @@ def test_resident_cap_keeps_fifo_and_limits_sharing():
     assert res[1].done < res[4].admitted
 
 
-def test_late_arrival_joins_running_batch():
+@pytest.mark.parametrize("Fake", FAKES)
+def test_late_arrival_joins_running_batch(Fake):
     clock = Clock()
-    fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
+    fb = Fake(budget_cells=10 ** 9, clock=clock)
     srv = srvmod.Server(backend=fb, chunk_steps=10, clock=clock)
     a = srv.submit(_spec("long", steps=200), arrival=0.0)
     b = srv.submit(_spec("late", steps=30), arrival=0.05)
@@ -130,9 +165,10 @@ def test_late_arrival_joins_running_batch():
     assert rb.admitted < ra.done and rb.done < ra.done
 
 
-def test_cancel_reject_and_unstable():
+@pytest.mark.parametrize("Fake", FAKES)
+def test_cancel_reject_and_unstable(Fake):
     clock = Clock()
-    fb = FakeBatch(budget_cells=100 * 50, unstable_names={"bad"}, clock=clock)
+    fb = Fake(budget_cells=100 * 50, unstable_names={"bad"}, clock=clock)
     srv = srvmod.Server(backend=fb, chunk_steps=8, clock=clock)
     big = srv.submit(_spec("huge", n=400), arrival=0.0)          # can never fit
     bad = srv.submit(_spec("bad", steps=30), arrival=0.0)
@@ -148,11 +184,24 @@ def test_cancel_reject_and_unstable():
     assert not fb.slots  # everything evicted
 
 
-def test_background_thread_serves_submissions():
-    fb = FakeBatch(budget_cells=10 ** 9)
+@pytest.mark.parametrize("Fake", FAKES)
+def test_background_thread_serves_submissions(Fake):
+    fb = Fake(budget_cells=10 ** 9)
     srv = srvmod.Server(backend=fb, chunk_steps=32)
     srv.start()
     futs = [srv.submit(_spec(f"t{i}", steps=64)) for i in range(5)]
     res = [f.result(timeout=30) for f in futs]
     srv.stop()
     assert all(r.status == "ok" and r.forces.shape == (64, 2, 2) for r in res)
+
+
+def test_group_admission_is_fifo_and_used():
+    clock = Clock()
+    fb = FakeBatchMany(budget_cells=10 ** 9, clock=clock)
+    srv = srvmod.Server(backend=fb, chunk_steps=16, clock=clock)
+    futs = [srv.submit(_spec(f"g{i}", steps=20 + i), arrival=0.0) for i in range(6)]
+    srv.run_until_idle()
+    assert getattr(fb, "groups", 0) >= 1  # the arrived requests went in as one group
+    res = [f.result() for f in futs]
+    assert all(r.status == "ok" for r in res) and [r.steps for r in res] == [20 + i for i in range(6)]
+    assert [r.admitted for r in res] == sorted(r.admitted for r in res)
