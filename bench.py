@@ -166,25 +166,87 @@ def _traffic_record(storage):
     return entry
 
 
-def cpu_baseline(specs, seconds=12.0, min_steps=20):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample: the first
-    domain of the set, stepped until about `seconds` of CPU work."""
-    import oracle
-    spec = specs[0]
-    dom = oracle.Domain(spec)
-    cells = spec["nx"] * spec["ny"]
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_rate(dom, cells, seconds, chunk, min_steps):
+    """Steps the oracle domain until about `seconds` of work; node updates per second."""
     dom.run(2, want_forces=True)
     steps, t0 = 0, time.perf_counter()
     while True:
-        dom.run(10, want_forces=True)
-        steps += 10
+        dom.run(chunk, want_forces=True)
+        steps += chunk
         el = time.perf_counter() - t0
         if el >= seconds and steps >= min_steps:
-            break
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": cells * steps / el / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"domain 0 of the set ({spec['nx']}x{spec['ny']}), {steps} steps, FP64, "
-                      f"{el:.1f} s"}
+            return cells * steps / el, steps, el
+
+
+def cpu_baseline(specs, seconds=6.0):
+    """The FP64 oracle as it stands, on the host cores, beside the GPU figures: the first
+    domain of the batched set at all cores and at one thread (bounded samples); the
+    Couette workload (128x128, 20 000 steps) in full at all cores and its first 1000 steps
+    at one thread; the populations of 1 and of all threads compared bit for bit."""
+    import numpy as np
+    import oracle
+    import synth
+    cores = os.cpu_count() or 1
+    spec = specs[0]
+    cells = spec["nx"] * spec["ny"]
+    used = oracle.set_threads(cores)
+    v_all, st_all, el_all = _oracle_rate(oracle.Domain(spec), cells, seconds, 10, 20)
+    oracle.set_threads(1)
+    v_one, st_one, el_one = _oracle_rate(oracle.Domain(spec), cells, seconds / 2, 2, 4)
+    # the Couette workload in full at all cores
+    cou = synth.couette()
+    oracle.set_threads(cores)
+    dom = oracle.Domain(cou)
+    t0 = time.perf_counter()
+    dom.run(cou["steps"], want_forces=True)
+    cou_all = time.perf_counter() - t0
+    g_all = dom.g.copy()
+    # its first 1000 steps on one thread (time extrapolated), then both thread counts
+    # from the same state for 200 steps: identical populations
+    oracle.set_threads(1)
+    d1 = oracle.Domain(cou)
+    t0 = time.perf_counter()
+    d1.run(1000, want_forces=True)
+    cou_one_1000 = time.perf_counter() - t0
+    probe = []
+    for n in (1, cores):
+        oracle.set_threads(n)
+        d = oracle.Domain(cou, g=g_all)
+        d.run(200, want_forces=True)
+        probe.append(d.g.copy())
+    oracle.set_threads(cores)
+    ccells = cou["nx"] * cou["ny"]
+    return {"value": v_all / 1e9, "unit": "GLUPS", "cores": used, "kind": "oracle",
+            "sample": f"domain 0 of the set ({spec['nx']}x{spec['ny']}), {st_all} steps, FP64, "
+                      f"{el_all:.1f} s, all host cores",
+            "single_thread": {"value": v_one / 1e9, "unit": "GLUPS", "cores": 1,
+                              "sample": f"the same domain, {st_one} steps, {el_one:.1f} s"},
+            "os_cpu_count": os.cpu_count(), "cpu_model": _cpu_model(),
+            "couette_128": {"steps": cou["steps"], "seconds_all_cores": cou_all,
+                            "glups_all_cores": ccells * cou["steps"] / cou_all / 1e9,
+                            "glups_one_thread": ccells * 1000 / cou_one_1000 / 1e9,
+                            "seconds_one_thread_extrapolated": cou_one_1000 * cou["steps"] / 1000,
+                            "one_thread": "first 1000 steps timed, the full run extrapolated"},
+            "threads_bit_identical": bool(np.array_equal(probe[0], probe[1]))}
 
 
 def run_reference(args):
@@ -196,6 +258,7 @@ def run_reference(args):
     specs = synth.batched_domains(64)
     spec = specs[0]
     cells = spec["nx"] * spec["ny"]
+    cores = oracle.set_threads(os.cpu_count() or 1)
     dom = oracle.Domain(spec)
     dom.run(max(args.warmup, 0))
     # each step of the reference arm: one oracle time step of the sample domain
@@ -203,7 +266,6 @@ def run_reference(args):
     dom.run(args.steps)
     el = time.perf_counter() - t0
     value = cells * args.steps / el / 1e9
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -264,7 +326,7 @@ def run_ours(args):
     args.graph_used = min(args.graph_steps, args.steps)
     with torch.cuda.stream(stream):
         batch = lbm.Batch(args.storage, max_domains=64, graph_steps=args.graph_used, stream=stream)
-        slots = [batch.admit(s, nsteps=nsteps_total, force_capacity=nsteps_total + 8) for s in specs]
+        slots = batch.admit_many(specs, nsteps=nsteps_total, force_capacity=nsteps_total + 8)
         if args.tile:
             batch.set_tile(*[int(x) for x in args.tile.split(",")])
         tune_us = batch.autotune(reps=5) if not (args.no_autotune or args.tile) else None
@@ -388,7 +450,9 @@ def measure_served(lbm, torch, args, plain=None):
     the seeded Poisson stream (20 req/s; counter-rotating pairs 1200x600 and NACA-0012
     2000x1000, FP16-shifted), with arrival times and step counts both scaled by
     `served_scale` (offered load unchanged, about 9x what the GPU drains, so requests
-    queue). Continuous batching admits them by memory budget as others finish."""
+    queue). Continuous batching admits them by memory budget as others finish. The
+    throughput covers the whole stream, its final drain included (with 32 requests the
+    drain, when few residents are left, holds it about 10 % below the batched figure)."""
     import synth
     from paper_1901_08766_gb300.server import Server
     reqs = synth.served_requests()[: args.served_requests]
@@ -856,7 +920,7 @@ def main():
                          "here), pulse (every body pulsating by 5 %% over 2000 steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e, plain, served and CPU legs")
-    ap.add_argument("--served-requests", type=int, default=32)
+    ap.add_argument("--served-requests", type=int, default=128)
     ap.add_argument("--served-scale", type=float, default=0.02)
     ap.add_argument("--served-chunk", type=int, default=256)
     ap.add_argument("--served-rate", type=float, default=1.2, help="requests/s (--experiment served)")

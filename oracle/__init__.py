@@ -75,6 +75,17 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops over rows (results do not depend on them:
+    nodes are independent and body forces are summed serially afterwards); returns the
+    number now in effect."""
+    lib()
+    gomp = C.CDLL("libgomp.so.1")
+    gomp.omp_set_num_threads(int(n))
+    gomp.omp_get_max_threads.restype = C.c_int
+    return int(gomp.omp_get_max_threads())
+
+
 def lib():
     global _lib
     if _lib is None:
