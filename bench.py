@@ -406,7 +406,16 @@ def run_ours(args):
 
 def measure_e2e(lbm, torch, specs, args):
     """The same metric through the public API with host inputs and outputs: admit every
-    domain from its host-side geometry, run the steps, read every force series back."""
+    domain from its host-side geometry, run the steps, read every force series back. The
+    job runs twice and the second is reported: the first in a process also pays one-time
+    costs (the caching allocator growing its pool), recorded as first_job_ms."""
+    first = _e2e_job(lbm, torch, specs, args)
+    res = _e2e_job(lbm, torch, specs, args)
+    res["first_job_ms"] = first["job_ms"]
+    return res
+
+
+def _e2e_job(lbm, torch, specs, args):
     steps = args.steps
     stream = torch.cuda.Stream()
     marks = []
@@ -522,25 +531,20 @@ def measure_plain_f32(lbm, torch, specs, args, steps=30):
 
 # ---- accuracy experiments on the paper's workloads ----------------------------------------
 
-def _couette_error(lbm, n, lam, storage="f64", u_wall=0.001, re=10.0, ri_frac=45 / 200,
-                   ro_frac=70 / 200, srt=False):
+def _couette_setup(n, u_wall=0.001, re=10.0, ri_frac=45 / 200, ro_frac=70 / 200):
     """Couette setup of Sec. 3.1 on an n x n grid (L = 1, dx = 1/n): R_i = 45/200, R_o = 70/200,
-    inner wall speed 0.001, Re = U D / nu = 10 with D = 2 R_i. SRT is the TRT update with
-    Lambda = (tau_s - 1/2)^2 (then tau_a = tau_s)."""
-    import math
-    import numpy as np
-    import synth
+    inner wall speed 0.001, Re = U D / nu = 10 with D = 2 R_i; run for three times the
+    slowest diffusion time (the slowest mode decays as exp(-pi^2 t nu / (R_o - R_i)^2))."""
     ri, ro = ri_frac * n, ro_frac * n
     nu = u_wall * 2 * ri / re
-    if srt:
-        lam = (3 * nu) ** 2
-    diff_time = (ro - ri) ** 2 / nu
-    steps = int(3 * diff_time)  # slowest mode decays as exp(-pi^2 t nu / (R_o - R_i)^2)
-    spec = synth.couette(n, ri, ro, u_wall, nu, steps, magic_lambda=lam)
-    dom = lbm.Domain(spec, storage=storage, force_every=0)
-    dom.step(steps)
-    rho, ux, uy = dom.moments()
-    dom.close()
+    steps = int(3 * (ro - ri) ** 2 / nu)
+    return ri, ro, nu, steps
+
+
+def _couette_l2(n, ri, ro, u_wall, ux, uy):
+    """Relative L2 of u_theta against the closed form A r + B / r over R_i + 1 <= r <= R_o - 1."""
+    import math
+    import numpy as np
     c = n / 2.0
     j, i = np.mgrid[0:n, 0:n]
     x, y = i - c, j - c
@@ -551,8 +555,44 @@ def _couette_error(lbm, n, lam, storage="f64", u_wall=0.001, re=10.0, ri_frac=45
     A = -u_wall * ri / (ro ** 2 - ri ** 2)
     B = u_wall * ri * ro ** 2 / (ro ** 2 - ri ** 2)
     ex = A * rr + B / rr
-    return {"n": n, "tau_s": 3 * nu + 0.5, "lambda": lam, "steps": steps,
-            "l2_rel": math.sqrt(((ut - ex)[sel] ** 2).sum() / (ex[sel] ** 2).sum())}
+    return math.sqrt(((ut - ex)[sel] ** 2).sum() / (ex[sel] ** 2).sum())
+
+
+def couette_study(lbm, np, sizes=(120, 160, 240, 320, 480), lambdas=(3 / 16, 1 / 4), etas=(1e-4, 1e-6),
+                  u_wall=0.001):
+    """Grid refinement of the Couette flow of Sec. 3.1 (the paper's TRT-versus-SRT
+    comparison), FP64 storage: every scheme of one resolution in one batch -- TRT with
+    each magic parameter and SRT (TRT with Lambda = (tau_s - 1/2)^2, tau_a = tau_s), each
+    with each penalization parameter eta. On the smallest grid every scheme is also run
+    for 2000 steps beside the FP64 oracle (largest relative population difference)."""
+    import synth
+    import oracle
+    rows = []
+    for n in sizes:
+        ri, ro, nu, steps = _couette_setup(n, u_wall)
+        schemes = [(f"TRT {lam:g}", lam, eta) for lam in lambdas for eta in etas]
+        schemes += [("SRT", (3 * nu) ** 2, eta) for eta in etas]
+        specs = [synth.couette(n, ri, ro, u_wall, nu, steps, magic_lambda=lam, eta=eta)
+                 for _, lam, eta in schemes]
+        b = lbm.Batch("f64", max_domains=len(specs), graph_steps=64)
+        slots = b.admit_many(specs, nsteps=steps, force_every=0)
+        while b.run(8192):
+            pass
+        for (name, lam, eta), sp, k in zip(schemes, specs, slots):
+            rho, ux, uy = b.moments(k)
+            row = {"n": n, "scheme": name, "lambda": lam, "eta": eta, "tau_s": 3 * nu + 0.5,
+                   "steps": steps, "l2_rel": _couette_l2(n, ri, ro, u_wall, ux, uy)}
+            if n == min(sizes):
+                d = lbm.Domain(sp, storage="f64", force_every=0)
+                d.step(2000)
+                g = d.get_populations()
+                d.close()
+                ora = oracle.Domain(sp)
+                ora.run(2000, want_forces=False)
+                row["oracle_max_rel_2000_steps"] = float(np.max(np.abs(g - ora.g) / np.abs(ora.g)))
+            rows.append(row)
+        b.close()
+    return rows
 
 
 def experiment(args):
@@ -565,12 +605,7 @@ def experiment(args):
     torch.cuda.set_device(0)
     out = {"experiment": args.experiment}
     if args.experiment == "couette":
-        rows = []
-        for n in (120, 160, 240, 320, 480):
-            rows.append({"scheme": "TRT 3/16", **_couette_error(lbm, n, 3 / 16)})
-            rows.append({"scheme": "TRT 1/4", **_couette_error(lbm, n, 1 / 4)})
-            rows.append({"scheme": "SRT", **_couette_error(lbm, n, 0.0, srt=True)})
-        out["rows"] = rows
+        out["rows"] = couette_study(lbm, np)
     elif args.experiment in ("precision", "cylinder"):
         cases = ([("f16s", synth.precision_cylinder(True)), ("bf16s", synth.precision_cylinder(True)),
                   ("f32", synth.precision_cylinder(True)), ("f64", synth.precision_cylinder(True))]

@@ -1,14 +1,17 @@
 """Physics of the GPU path on the paper's workloads.
 
 - Cylindrical Couette flow (Sec. 3.1), FP64: matches the oracle after 20 000 steps and
-  the closed form u_theta = A r + B/r; reduced storages stay within a velocity-field
-  relative L2 of 1e-3 of FP64 (BF16-shifted: see the bound below).
+  the closed form u_theta = A r + B/r; FP32 and FP16-shifted storage stay within a
+  velocity-field relative L2 of 1e-3 of FP64. BF16-shifted storage is not claimed to meet
+  that bound: its rounding floor alone (8 mantissa bits) is above it, which one test
+  records; another keeps its measured level as a regression check.
 - A shear wave whose per-step change is below half a unit of the 16-bit storages decays
   as in FP64 (stochastic rounding keeps sub-unit increments).
 - Single cylinder (Sec. 3.2), FP32: C_d and St close to Table (high-Re) / (low-Re) of
   the paper (plausibility only: domain and edges differ from the paper's).
 - Precision sweep at the oracle's size (600x300, D = 30, Re = 200): mean C_d, C_l rms and
-  St of every storage within 1 % of the stored FP64 oracle values.
+  St of FP64, FP32 and FP16-shifted storage within 1 % of the stored FP64 oracle values
+  (BF16-shifted: measured level only, as for Couette).
 """
 import json
 import math
@@ -59,20 +62,53 @@ def test_couette_fp64_matches_oracle_and_closed_form(lbm):
     assert err < 0.03
 
 
-@pytest.mark.parametrize("storage,steps,bound", [("f32", 20000, 1e-3), ("f16s", 20000, 1e-3),
-                                                 ("f16s", 100000, 1e-3), ("bf16s", 20000, 5e-3)])
-def test_couette_reduced_precision_velocity_l2(lbm, storage, steps, bound):
-    # Velocity-field relative L2 against FP64 storage after the 20 000 steps of the
-    # workload (FP32 1.4e-5, FP16-shifted 3.1e-4: stochastic rounding keeps the spin-up's
-    # sub-unit increments that rounding to nearest dropped, 2.2e-3 then), and FP16 once
-    # more at 100 000 steps. BF16 keeps 8 mantissa bits and misses 1e-3 (2.6e-3): its
-    # assertion records the achieved level, not the target.
+def _couette_l2_vs_fp64(ux, uy, ux64, uy64):
+    num = np.sqrt(((ux - ux64) ** 2 + (uy - uy64) ** 2).sum())
+    den = np.sqrt((ux64 ** 2 + uy64 ** 2).sum())
+    return num / den
+
+
+@pytest.mark.parametrize("storage,steps", [("f32", 20000), ("f16s", 20000), ("f16s", 100000)])
+def test_couette_reduced_precision_velocity_l2(lbm, storage, steps):
+    # The bound: velocity-field relative L2 against FP64 storage <= 1e-3 after the 20 000
+    # steps of the workload (FP32 1.4e-5, FP16-shifted 3.1e-4: stochastic rounding keeps
+    # the spin-up's sub-unit increments that rounding to nearest dropped, 2.2e-3 then),
+    # and FP16 once more at 100 000 steps.
+    bound = 1e-3
     _, ux64, uy64, _ = _couette_fields(lbm, "f64", steps=20000)
     _, ux, uy, _ = _couette_fields(lbm, storage, steps=steps)
     num = np.sqrt(((ux - ux64) ** 2 + (uy - uy64) ** 2).sum())
     den = np.sqrt((ux64 ** 2 + uy64 ** 2).sum())
     print(f"{storage} after {steps} steps: velocity relative L2 vs FP64 = {num / den:.3e}")
     assert num / den <= bound
+
+
+def test_couette_bf16s_rounding_floor_is_above_the_bound(lbm):
+    # Why BF16-shifted storage is excluded from the 1e-3 Couette bound: started from the
+    # converged FP64 state itself, it stays 2.6e-3 away from it (measured 2.56e-3): the
+    # stochastic-rounding noise of 8-mantissa-bit values that carry the velocity is above
+    # the bound whatever the path to the steady state (FP16-shifted, 11 bits: 3.2e-4).
+    import codec
+    spec, ux64, uy64, pops = _couette_fields(lbm, "f64")
+    dom = lbm.Domain(spec, storage="bf16s", force_every=0)
+    dom.set_populations(codec.encode(pops, "bf16s"))
+    dom.step(20000)
+    _, ux, uy = dom.moments()
+    dom.close()
+    floor = _couette_l2_vs_fp64(ux, uy, ux64, uy64)
+    print(f"bf16s from the converged FP64 state, 20000 steps: velocity relative L2 {floor:.3e}")
+    assert 1e-3 < floor < 5e-3
+
+
+def test_couette_bf16s_measured_level(lbm):
+    # Regression check of BF16-shifted storage (not a bound: see the test above): the
+    # velocity-field relative L2 against FP64 after the workload's 20 000 steps, measured
+    # 2.6e-3, stays below 5e-3.
+    _, ux64, uy64, _ = _couette_fields(lbm, "f64", steps=20000)
+    _, ux, uy, _ = _couette_fields(lbm, "bf16s", steps=20000)
+    level = _couette_l2_vs_fp64(ux, uy, ux64, uy64)
+    print(f"bf16s after 20000 steps: velocity relative L2 vs FP64 = {level:.3e}")
+    assert level <= 5e-3
 
 
 def test_couette_fp16s_rounding_floor(lbm):
@@ -139,11 +175,7 @@ def test_single_cylinder_against_paper_tables(lbm, re, cd, st, steps):
         assert s["cl_rms"] < 0.01  # steady wake
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 0.01), ("f32", 0.01), ("f16s", 0.01), ("bf16s", 0.03)])
-def test_precision_sweep_against_oracle(lbm, storage, tol):
-    # Mean C_d, C_l rms and St (lift spectral peak) over steps 40 000..80 000 within 1 % of
-    # the stored FP64 oracle values. BF16-shifted is within 1.5 % (C_d +1.4 %, St +1.0 %):
-    # its tolerance records the achieved level, not the target.
+def _precision_sweep(lbm, storage):
     path = os.path.join(GOLDEN, "precision_cylinder_600x300.json")
     ref = json.load(open(path))
     spec = synth.precision_cylinder(large=False)
@@ -156,5 +188,21 @@ def test_precision_sweep_against_oracle(lbm, storage, tol):
     got = {"cd_mean": cd[half].mean(), "cl_rms": dg.rms(cl[half]),
            "st": dg.strouhal_spectral(cl[half], D, U)}
     print(storage, got, {k: ref[k] for k in got})
+    return got, ref
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_precision_sweep_against_oracle(lbm, storage):
+    # The bound: mean C_d, C_l rms and St (lift spectral peak) over steps 40 000..80 000
+    # within 1 % of the stored FP64 oracle values.
+    got, ref = _precision_sweep(lbm, storage)
     for k in got:
-        assert abs(got[k] - ref[k]) / abs(ref[k]) < tol, k
+        assert abs(got[k] - ref[k]) / abs(ref[k]) < 0.01, k
+
+
+def test_precision_sweep_bf16s_measured_level(lbm):
+    # Regression check of BF16-shifted storage, which is not claimed to meet the 1 % bound
+    # (measured: C_d +1.4 %, St +1.0 %, C_l rms -1.0 %): each within 3 %.
+    got, ref = _precision_sweep(lbm, "bf16s")
+    for k in got:
+        assert abs(got[k] - ref[k]) / abs(ref[k]) < 0.03, k
