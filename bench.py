@@ -404,6 +404,93 @@ def run_ours(args):
     return 0
 
 
+def slab_grid_spec(steps):
+    """The single-grid workload of the slab mode: the Re 200 precision cylinder scaled
+    three times (7200 x 3600 nodes, D = 180 at (1800, 1800), U = 0.05)."""
+    import synth
+    return synth.single_cylinder(7200, 3600, 180.0, 1800.0, 1800.0, 0.05, 200.0, steps)
+
+
+def run_slabs(args):
+    """One grid cut into `args.slabs` slabs of whole columns whose cuts are halo edges:
+    before every step each batch packs its halo columns (a cut inside a rank reads the
+    packed buffer of its other side directly) and cuts between ranks exchange them by NCCL
+    send/recv, then one step runs. Under torchrun the slabs are shared out in consecutive
+    blocks (strong scaling of the one grid); at N = 1 the undivided grid is timed beside."""
+    import torch
+    import paper_1901_08766_gb300 as lbm
+    from paper_1901_08766_gb300 import slabs as sl
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    lbm.load()
+    total = args.warmup + args.steps + 8
+    spec = slab_grid_spec(total)
+    k = args.slabs
+    base = (spec["nx"] // k) // 8 * 8  # cuts on multiples of 8 columns (16-bit rounding)
+    widths = [base] * (k - 1) + [spec["nx"] - base * (k - 1)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        hg = sl.HaloGrid(spec, widths, storage=args.storage, rank=rank, world=ws, nsteps=total,
+                         force_capacity=total + 8, stream=stream)
+        hg.step(args.warmup)
+        hg.forces()
+        stream.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches0 = hg.batch.info()["kernel_launches"]
+        e0.record(stream)
+        hg.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = hg.batch.info()["kernel_launches"] - launches0
+        hg.forces()
+        cells_local = sum(spec["ny"] * widths[i] for i in hg.mine)
+        hg.close()
+    ms, value, cells = aggregate(ms, cells_local, args.steps, ws, device="cuda")
+    undivided = None
+    if ws == 1:
+        with torch.cuda.stream(stream):
+            d = lbm.Batch(args.storage, max_domains=1, graph_steps=32, stream=stream)
+            slot = d.admit(spec, nsteps=total, force_capacity=total + 8)
+            d.run(args.warmup)
+            d.poll(slot)
+            d.capture()
+            stream.synchronize()
+            e0.record(stream)
+            d.run(args.steps)
+            e1.record(stream)
+            e1.synchronize()
+            undivided = {"value": spec["nx"] * spec["ny"] * args.steps / (e0.elapsed_time(e1) / 1000.0) / 1e9,
+                         "unit": "GLUPS", "note": "the same grid as one domain, graph-replayed steps"}
+            d.close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "f16s storage, f32 compute" if args.storage == "f16s" else args.storage,
+            "data": "synthetic",
+            "config": {"workload": f"one grid as {k} slabs with halo edges: cylinder channel "
+                                   f"{spec['nx']}x{spec['ny']}, D = 180, Re 200, U = 0.05",
+                       "cells": cells, "slabs": k, "widths": widths, "storage": args.storage,
+                       "exchange": "per step: pack halo columns (one launch); inside a rank each "
+                                   "side reads the other's packed buffer, between ranks NCCL send/recv",
+                       "parallelism": f"slabs over {ws} GPUs" if ws > 1 else "single GPU"},
+            "gpu_launches": launches, "undivided": undivided}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def measure_e2e(lbm, torch, specs, args):
     """The same metric through the public API with host inputs and outputs: admit every
     domain from its host-side geometry, run the steps, read every force series back. The
@@ -941,6 +1028,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f16s", "bf16s", "f32", "f64"], default="f16s")
     ap.add_argument("--graph-steps", type=int, default=32)
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="one large grid cut into this many slabs with halo edges (a multiple "
+                         "of the GPU count) instead of the batched workload")
     ap.add_argument("--replicas", choices=["shard", "copy"], default="shard",
                     help="N > 1: shard the domain set over the ranks (default, strong scaling) "
                          "or give every rank a full copy (weak scaling)")
@@ -973,6 +1063,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.slabs:
+        return run_slabs(args)
     return run_ours(args)
 
 

@@ -318,6 +318,32 @@ LBM_API lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t eas
 /* Free a slot and its device memory. */
 LBM_API lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot);
 
+/* Halo edges: one grid cut into slabs over several devices (or batches). Streaming
+ * (Eq. streaming) across a cut pulls, at the same time level, the neighbouring slab's
+ * column next to the cut. Only the three populations that cross the cut are needed:
+ * e_x = +1 (directions 1, 5, 8) eastward and e_x = -1 (3, 6, 7) westward, for every row.
+ * lbm_batch_set_halo turns the x edge `side` (0 west, 1 east) of a slot into a halo
+ * edge fed from caller-owned device buffers, both [9][ny] elements of the batch's
+ * storage type (element (a, j) at a * ny + j):
+ *   recv: read by every later sweep as the column beyond the edge; the caller fills
+ *         planes 1, 5, 8 (west edge) or 3, 6, 7 (east edge) before every step with the
+ *         neighbour's send buffer for this cut;
+ *   send: written by lbm_batch_pack_halos with this slot's own column at the edge,
+ *         planes 3, 6, 7 (west edge, column 0) or 1, 5, 8 (east edge, column nx - 1).
+ * Per step: lbm_batch_pack_halos, the exchange (device copies, peer copies or NCCL
+ * send/recv, ordered on or after the batch stream), then lbm_batch_run of one step. The
+ * slabs' x_origin values place each slab in the grid (shapes, obstacle velocities and
+ * the 16-bit rounding keyed by global columns), so the slabs reproduce the undivided
+ * grid bit for bit. recv = send = NULL restores the edge given at admission. The buffers
+ * stay the caller's (not freed by the library) and must outlive their use. LBM_EINVAL if
+ * the edge is linked to a slot (lbm_batch_link_x), the slot has coupled or pulsating
+ * bodies, or only one buffer is given. No counterpart in the paper (its method is local,
+ * Sec. 2.2, which is what lets a grid be cut). */
+LBM_API lbm_status lbm_batch_set_halo(lbm_batch *b, int32_t slot, int32_t side, void *recv, void *send);
+/* Enqueue on the batch stream the packing of every halo edge's send buffer from the
+ * current state (one launch for up to 64 edges). Asynchronous. */
+LBM_API lbm_status lbm_batch_pack_halos(lbm_batch *b);
+
 /* Build the work lists of the resident slots and capture the CUDA graph of graph_steps
  * steps now, so that the next lbm_batch_run of at least graph_steps steps replays it
  * instead of capturing it first (capture is host work of a few milliseconds; do it

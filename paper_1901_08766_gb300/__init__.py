@@ -514,6 +514,18 @@ class Batch:
         check(load().lbm_batch_evict(self._h, slot), "lbm_batch_evict")
         self._meta.pop(slot, None)
 
+    def set_halo(self, slot: int, side: int, recv=None, send=None):
+        """Make x edge `side` (0 west, 1 east) of a slot a halo edge fed from `recv` and
+        packed into `send`: device tensors of [9, ny] storage elements that the caller
+        keeps alive (None, None restores the admitted edge). See slabs.HaloGrid."""
+        rp = C.c_void_p(recv.data_ptr()) if recv is not None else None
+        sp = C.c_void_p(send.data_ptr()) if send is not None else None
+        check(load().lbm_batch_set_halo(self._h, int(slot), int(side), rp, sp), "lbm_batch_set_halo")
+
+    def pack_halos(self):
+        """Enqueue the packing of every halo edge's send buffer from the current state."""
+        check(load().lbm_batch_pack_halos(self._h), "lbm_batch_pack_halos")
+
     def capture(self):
         """Build the work lists and capture the step graph now (no steps run), so that the
         next run replays it without capturing."""

@@ -151,6 +151,8 @@ SIGNATURES = {
     "lbm_batch_profile": (C.c_int, [_VP, _I32, _DP, _DP, C.POINTER(_I64)]),
     "lbm_batch_evict": (C.c_int, [_VP, _I32]),
     "lbm_batch_inject": (C.c_int, [_VP, _I32, _I32]),
+    "lbm_batch_set_halo": (C.c_int, [_VP, _I32, _I32, _VP, _VP]),
+    "lbm_batch_pack_halos": (C.c_int, [_VP]),
     "lbm_batch_capture": (C.c_int, [_VP]),
     "lbm_batch_autotune": (C.c_int, [_VP, _I32, _DP]),
     "lbm_batch_set_tile": (C.c_int, [_VP, _I32, _I32, _I32, _I32]),

@@ -798,6 +798,37 @@ cudaError_t launch_fill(cudaStream_t st, const FillSeg *segs, int nseg) {
   return cudaGetLastError();
 }
 
+// ---- halo edges (slab decomposition over devices) -------------------------------------
+// Block (x, k) copies rows x*256 .. of halo item k: the three populations that leave the
+// domain through that edge, from the edge column into the send buffer's planes.
+template <typename E>
+__global__ void halo_pack_kernel(const __grid_constant__ HaloPack pack) {
+  const HaloItem &it = pack.item[blockIdx.y];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= it.ny) return;
+  const E *lat = static_cast<const E *>(it.lat);
+  E *send = static_cast<E *>(it.send);
+  const size_t plane = static_cast<size_t>(it.ny) * it.pitch;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    // east edge: e_x = +1 (1, 5, 8); west edge: e_x = -1 (3, 6, 7)
+    const int a = it.east ? (q == 0 ? 1 : (q == 1 ? 5 : 8)) : (q == 0 ? 3 : (q == 1 ? 6 : 7));
+    send[static_cast<size_t>(a) * it.ny + j] = lat[a * plane + static_cast<size_t>(j) * it.pitch + it.col];
+  }
+}
+
+cudaError_t launch_halo_pack(cudaStream_t st, const HaloPack &pack, int max_ny) {
+  if (pack.n <= 0) return cudaSuccess;
+  const dim3 grid((max_ny + 255) / 256, pack.n);
+  switch (pack.elem) {
+    case 2: halo_pack_kernel<uint16_t><<<grid, 256, 0, st>>>(pack); break;
+    case 4: halo_pack_kernel<uint32_t><<<grid, 256, 0, st>>>(pack); break;
+    case 8: halo_pack_kernel<unsigned long long><<<grid, 256, 0, st>>>(pack); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ---- body forces -------------------------------------------------------------------------
 // The sweep of step n+1 writes F_VP of every solid node (Eq. force-density) to the
 // domain's F_VP field; this kernel, launched after it, sums -F_VP over each body's

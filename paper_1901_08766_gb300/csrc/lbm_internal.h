@@ -154,6 +154,22 @@ struct AdmitDev {
   double rho0, u0x, u0y;
 };
 
+// One halo edge to pack (slab decomposition over devices): the populations of the three
+// directions that cross the edge outward, taken from column `col` of the current lattice
+// `lat` ([9][ny][pitch]), written to `send` ([9][ny], those three planes only). east:
+// the east edge (directions 1, 5, 8 from the last column), else the west edge (3, 6, 7
+// from column 0).
+struct HaloItem {
+  const void *lat;
+  void *send;
+  int32_t ny, pitch, col, east;
+};
+constexpr int kMaxHaloItems = 64;  // halo edges packed by one launch
+struct HaloPack {
+  HaloItem item[kMaxHaloItems];
+  int32_t n, elem;  // items, element size in bytes
+};
+
 // A span of device memory to fill (batched admission): a copy of `bytes` from src, or
 // zeros when src is null.
 struct FillSeg {
@@ -197,6 +213,7 @@ cudaError_t launch_admit_raster_count(cudaStream_t st, AdmitDev *ad, int n, int 
 cudaError_t launch_admit_scatter(cudaStream_t st, const AdmitDev *ad, int n, int rows, int max_bodies);
 cudaError_t launch_admit_init(int storage, cudaStream_t st, const AdmitDev *ad, int n, int rows);
 cudaError_t launch_fill(cudaStream_t st, const FillSeg *segs, int nseg);
+cudaError_t launch_halo_pack(cudaStream_t st, const HaloPack &pack, int max_ny);
 
 // per-storage sweep launchers (one translation unit each)
 cudaError_t launch_sweep_f64(int vec, int pipe, int grid, int warps, cudaStream_t st,

@@ -170,7 +170,9 @@ struct Slot {
   void *solid = nullptr;
   size_t bytes = 0;
   std::vector<int32_t> solid_off;  // host copy of the per-body offsets into the solid list
-  int link_west = -1, link_east = -1;  // slots linked across the x edges (-1: none)
+  int link_west = -1, link_east = -1;  // slots linked across the x edges (-1: none, -2: a
+                                       // halo edge fed from a caller's buffer)
+  void *halo_send[2] = {nullptr, nullptr};  // halo edges: where lbm_batch_pack_halos writes
   bool fsi = false;                    // some body responds to its force
   DomDev dev{};
 };
@@ -1507,7 +1509,7 @@ lbm_status lbm_batch_set_dynamics(lbm_batch *b, int32_t slot, int32_t body, cons
   if (s.p.moving == 2) return fail(LBM_EINVAL, "coupled bodies do not turn their shapes (moving = 2)");
   if (s.p.force_every != 1) return fail(LBM_EINVAL, "coupled bodies need the force of every step (force_every = 1)");
   if (s.done != 0) return fail(LBM_EINVAL, "dynamics are set before the first step");
-  if (s.link_west >= 0 || s.link_east >= 0) return fail(LBM_EINVAL, "a linked domain cannot have coupled bodies");
+  if (s.link_west != -1 || s.link_east != -1) return fail(LBM_EINVAL, "a linked domain cannot have coupled bodies");
   if (s.dev.deform) return fail(LBM_EINVAL, "a domain with pulsating bodies cannot have coupled bodies");
   if (body < 1 || body > s.nbodies) return fail(LBM_EINVAL, "body %d not in [1, %d]", body, s.nbodies);
   if (!(dyn->mass > 0) || !std::isfinite(dyn->mass)) return fail(LBM_EINVAL, "mass must be finite and > 0");
@@ -1544,7 +1546,7 @@ lbm_status lbm_batch_set_deformation(lbm_batch *b, int32_t slot, int32_t body, d
   if (!s.p.moving) return fail(LBM_EINVAL, "pulsating bodies need a moving domain");
   if (s.done != 0) return fail(LBM_EINVAL, "a deformation is set before the first step");
   if (s.fsi) return fail(LBM_EINVAL, "coupled bodies do not deform");
-  if (s.link_west >= 0 || s.link_east >= 0) return fail(LBM_EINVAL, "a linked domain cannot have pulsating bodies");
+  if (s.link_west != -1 || s.link_east != -1) return fail(LBM_EINVAL, "a linked domain cannot have pulsating bodies");
   if (body < 1 || body > s.nbodies) return fail(LBM_EINVAL, "body %d not in [1, %d]", body, s.nbodies);
   if (!(std::fabs(amplitude) < 1.0) || !std::isfinite(rate))
     return fail(LBM_EINVAL, "the amplitude must satisfy |a| < 1 and the rate be finite");
@@ -1639,7 +1641,7 @@ lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t east_slot) 
     return fail(LBM_EINVAL, "linked domains need the same y edges");
   if (A.done != B.done || A.target != B.target || A.parity != B.parity)
     return fail(LBM_EINVAL, "linked domains must step together (same steps done and admitted)");
-  if (A.link_east >= 0 || B.link_west >= 0) return fail(LBM_EINVAL, "an edge is linked already");
+  if (A.link_east != -1 || B.link_west != -1) return fail(LBM_EINVAL, "an edge is linked already");
   if (A.fsi || B.fsi) return fail(LBM_EINVAL, "domains with coupled bodies cannot be linked");
   if (A.dev.deform || B.dev.deform) return fail(LBM_EINVAL, "domains with pulsating bodies cannot be linked");
   LBM_CUDA(cudaStreamSynchronize(b->st));
@@ -1659,6 +1661,72 @@ lbm_status lbm_batch_link_x(lbm_batch *b, int32_t west_slot, int32_t east_slot) 
   LBM_CUDA(cudaMemcpyAsync(b->d_doms + west_slot, &A.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaMemcpyAsync(b->d_doms + east_slot, &B.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_halo(lbm_batch *b, int32_t slot, int32_t side, void *recv, void *send) {
+  lbm_status rc = check_slot(b, slot);
+  if (rc != LBM_OK) return rc;
+  if (side != 0 && side != 1) return fail(LBM_EINVAL, "side must be 0 (west) or 1 (east)");
+  Slot &s = b->slots[slot];
+  int &link = side == 0 ? s.link_west : s.link_east;
+  int32_t &edge = side == 0 ? s.dev.west : s.dev.east;
+  if (link >= 0) return fail(LBM_EINVAL, "the %s edge is linked to slot %d", side ? "east" : "west", link);
+  if ((recv == nullptr) != (send == nullptr)) return fail(LBM_EINVAL, "recv and send must both be given or both NULL");
+  if (recv) {
+    if (s.fsi) return fail(LBM_EINVAL, "domains with coupled bodies cannot have halo edges");
+    if (s.dev.deform) return fail(LBM_EINVAL, "domains with pulsating bodies cannot have halo edges");
+    if ((reinterpret_cast<uintptr_t>(recv) | reinterpret_cast<uintptr_t>(send)) % elem_size(b->storage))
+      return fail(LBM_EINVAL, "halo buffers must be aligned to the element size");
+  }
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  if (recv) {
+    // the linked-edge read of the sweep, with the caller's buffer as a one-column lattice
+    edge = LBM_NEIGHBOR;
+    s.dev.nb_nx[side] = 1;
+    s.dev.nb_pitch[side] = 1;
+    s.dev.nb_lat[side][0] = recv;
+    s.dev.nb_lat[side][1] = recv;
+    s.halo_send[side] = send;
+    link = -2;
+  } else {
+    edge = side == 0 ? s.p.west : s.p.east;
+    s.dev.nb_nx[side] = 0;
+    s.dev.nb_pitch[side] = 0;
+    s.dev.nb_lat[side][0] = nullptr;
+    s.dev.nb_lat[side][1] = nullptr;
+    s.halo_send[side] = nullptr;
+    link = -1;
+  }
+  LBM_CUDA(cudaMemcpyAsync(b->d_doms + slot, &s.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
+  LBM_CUDA(cudaStreamSynchronize(b->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_pack_halos(lbm_batch *b) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  HaloPack pack{};
+  pack.elem = static_cast<int32_t>(elem_size(b->storage));
+  int max_ny = 0;
+  for (const Slot &s : b->slots) {
+    if (!s.used) continue;
+    for (int side = 0; side < 2; ++side) {
+      if (!s.halo_send[side]) continue;
+      if (pack.n == kMaxHaloItems) {
+        LBM_CUDA(launch_halo_pack(b->st, pack, max_ny));
+        b->launches++;
+        pack.n = 0;
+        max_ny = 0;
+      }
+      pack.item[pack.n++] = HaloItem{s.dev.lat[s.parity], s.halo_send[side], s.p.ny, s.pitch,
+                                     side == 1 ? s.p.nx - 1 : 0, side};
+      max_ny = std::max(max_ny, s.p.ny);
+    }
+  }
+  if (pack.n > 0) {
+    LBM_CUDA(launch_halo_pack(b->st, pack, max_ny));
+    b->launches++;
+  }
   return LBM_OK;
 }
 

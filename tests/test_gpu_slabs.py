@@ -2,7 +2,8 @@
 as linked slabs of one batch (each slab a domain whose cut edges pull the adjacent
 column of its neighbour) reproduces the undivided grid bit for bit, for every storage,
 uneven widths (different row pitches), every row pipeline, moving bodies crossing a cut,
-and a periodic ring of three slabs."""
+and a periodic ring of three slabs. The same with every cut a halo edge fed from device
+buffers (the form slabs on several GPUs take), exchanged by device copies."""
 import numpy as np
 import pytest
 
@@ -140,3 +141,29 @@ def test_link_checks_and_evict_unlinks(lbm):
     f, done = b.poll(ka)
     assert done and np.isfinite(f).all()
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("edges", ["periodic", "channel"])
+def test_halo_edges_reproduce_the_grid(lbm, storage, edges):
+    # every cut a halo edge fed from device buffers (lbm_batch_set_halo), packed on the
+    # device before each step; inside one batch each side reads the other's packed
+    # buffer (ranks on several GPUs move the same buffers by NCCL)
+    from paper_1901_08766_gb300 import slabs as sl
+    spec = _grid(edges)
+    g0 = codec.encode(synth.random_populations(37, 250, 64, 0.05), storage)
+    steps = 40
+    whole = _run_whole(lbm, spec, storage, g0, steps, {"f64": (2, 8, 2, 0), "f32": (4, 8, 2, 0)}.get(storage, (8, 8, 2, 0)))
+    hg = sl.HaloGrid(spec, [96, 64, 90], storage=storage, nsteps=steps, force_capacity=64)
+    x0 = 0
+    for k, w in zip(hg.slots, (96, 64, 90)):
+        hg.batch.set_populations(k, np.ascontiguousarray(g0[:, :, x0:x0 + w]))
+        x0 += w
+    hg.step(steps)
+    got = hg.populations()
+    f = hg.forces()
+    masks = np.concatenate([hg.batch.mask(k) for k in hg.slots], axis=1)
+    hg.close()
+    assert np.array_equal(masks, whole[2])
+    assert np.array_equal(got.view(np.uint8), whole[0].view(np.uint8))
+    assert np.abs(f - whole[1]).max() <= 1e-12 * np.abs(whole[1]).max()

@@ -78,3 +78,17 @@ def test_shard_of_one_rank_is_the_whole_set():
     assert sorted(s["name"] for part in four for s in part) == sorted(s["name"] for s in every)
     loads = [sum(s["nx"] * s["ny"] for s in part) for part in four]
     assert max(loads) - min(loads) <= max(s["nx"] * s["ny"] for s in every)
+
+
+def test_halo_topology_of_slabs_over_ranks():
+    from paper_1901_08766_gb300 import slabs
+    owner, peers = slabs.halo_topology(4, 2, periodic=True)
+    assert owner == [0, 0, 1, 1] and peers == [(1, 1), (0, 0)]
+    owner, peers = slabs.halo_topology(4, 2, periodic=False)
+    assert peers == [(None, 1), (0, None)]
+    owner, peers = slabs.halo_topology(6, 3, periodic=True)
+    assert owner == [0, 0, 1, 1, 2, 2] and peers == [(2, 1), (0, 2), (1, 0)]
+    owner, peers = slabs.halo_topology(3, 1, periodic=True)
+    assert peers == [(None, None)]  # every cut inside the one rank
+    with pytest.raises(ValueError):
+        slabs.halo_topology(3, 2, periodic=True)
