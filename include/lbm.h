@@ -378,9 +378,10 @@ LBM_API lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_u
 /* Set the sweep tile shape explicitly: vec = cells per thread (F64 1|2, F32 2|4,
  * F16S/BF16S 4|8), warps = warps per block (1..16), rows = rows per warp (1..16),
  * pipeline = 0 (rows read straight into registers), 1 (rows staged through shared
- * memory by bulk asynchronous copies, one row ahead) or 2 (the next row's loads issued
+ * memory by bulk asynchronous copies, one row ahead), 2 (the next row's loads issued
  * into a second register set before the current row is updated; at most 8 warps per
- * block). Results do not depend on it. */
+ * block), 3 or 4 (as 0, compiled for 20 or 24 resident warps per SM: at most 10 or 12
+ * warps per block, fewer registers per thread). Results do not depend on it. */
 LBM_API lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows,
                                       int32_t pipeline);
 LBM_API lbm_status lbm_batch_get_tile(lbm_batch *b, int32_t *vec, int32_t *warps, int32_t *rows,

@@ -215,15 +215,16 @@ cudaError_t launch_admit_init(int storage, cudaStream_t st, const AdmitDev *ad, 
 cudaError_t launch_fill(cudaStream_t st, const FillSeg *segs, int nseg);
 cudaError_t launch_halo_pack(cudaStream_t st, const HaloPack &pack, int max_ny);
 
-// per-storage sweep launchers (one translation unit each)
+// per-storage sweep launchers (one translation unit each); def: a resident domain has
+// pulsating bodies (the direct sweep's instantiation with the kappa term of U_O)
 cudaError_t launch_sweep_f64(int vec, int pipe, int grid, int warps, cudaStream_t st,
-                             const SweepArgs &a, int s);
+                             const SweepArgs &a, int s, bool def);
 cudaError_t launch_sweep_f32(int vec, int pipe, int grid, int warps, cudaStream_t st,
-                             const SweepArgs &a, int s);
+                             const SweepArgs &a, int s, bool def);
 cudaError_t launch_sweep_f16s(int vec, int pipe, int grid, int warps, cudaStream_t st,
-                             const SweepArgs &a, int s);
+                             const SweepArgs &a, int s, bool def);
 cudaError_t launch_sweep_bf16s(int vec, int pipe, int grid, int warps, cudaStream_t st,
-                             const SweepArgs &a, int s);
+                             const SweepArgs &a, int s, bool def);
 int max_blocks_f64(int vec, int pipe, int warps);
 int max_blocks_f32(int vec, int pipe, int warps);
 int max_blocks_f16s(int vec, int pipe, int warps);

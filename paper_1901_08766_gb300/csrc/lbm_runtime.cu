@@ -279,12 +279,12 @@ namespace {
 
 cudaError_t sweep_launch(lbm_batch *b, int grid, int vec, int pipe, int warps, int rows, int s) {
   SweepArgs a{b->d_doms, b->d_dyn, b->d_tiles, b->d_ctr, rows, b->inject};
-  if (pipe == 0 && b->has_deform) pipe = 4;  // the direct sweep instantiated with the kappa term
+  const bool def = b->has_deform;  // the direct sweep instantiated with the kappa term
   switch (b->storage) {
-    case LBM_F64: return launch_sweep_f64(vec, pipe, grid, warps, b->st, a, s);
-    case LBM_F32: return launch_sweep_f32(vec, pipe, grid, warps, b->st, a, s);
-    case LBM_F16S: return launch_sweep_f16s(vec, pipe, grid, warps, b->st, a, s);
-    case LBM_BF16S: return launch_sweep_bf16s(vec, pipe, grid, warps, b->st, a, s);
+    case LBM_F64: return launch_sweep_f64(vec, pipe, grid, warps, b->st, a, s, def);
+    case LBM_F32: return launch_sweep_f32(vec, pipe, grid, warps, b->st, a, s, def);
+    case LBM_F16S: return launch_sweep_f16s(vec, pipe, grid, warps, b->st, a, s, def);
+    case LBM_BF16S: return launch_sweep_bf16s(vec, pipe, grid, warps, b->st, a, s, def);
   }
   return cudaErrorInvalidValue;
 }
@@ -324,7 +324,9 @@ void drop_graph(lbm_batch *b) {
 lbm_status set_config(lbm_batch *b, int vec, int warps, int rows, int pipe) {
   if (!vec_ok(b->storage, vec)) return fail(LBM_EINVAL, "cells per thread %d unsupported for storage %d", vec, b->storage);
   if (warps < 1 || warps > 16 || rows < 1 || rows > 16) return fail(LBM_EINVAL, "warps and rows must be in [1, 16]");
-  if (pipe < 0 || pipe > 2) return fail(LBM_EINVAL, "pipeline must be 0 (direct), 1 (TMA-staged) or 2 (register-prefetched)");
+  if (pipe < 0 || pipe > 4)
+    return fail(LBM_EINVAL, "pipeline must be 0 (direct), 1 (TMA-staged), 2 (register-prefetched), "
+                            "3 or 4 (direct for 20 or 24 resident warps)");
   const int occ = sweep_occupancy(b->storage, vec, pipe, warps);
   if (occ <= 0) return fail(LBM_ECUDA, "sweep kernel cannot run with %d warps per block", warps);
   b->vec = vec;
@@ -1311,7 +1313,9 @@ lbm_status autotune(lbm_batch *b, int reps, double *best_us) {
   if (!any) return fail(LBM_EINVAL, "autotune needs resident domains");
   const int vecs[2] = {b->storage == LBM_F64 ? 1 : (b->storage == LBM_F32 ? 2 : 4),
                        b->storage == LBM_F64 ? 2 : (b->storage == LBM_F32 ? 4 : 8)};
-  const int warp_opts[3] = {4, 8, 16};
+  // warps per block that fit each pipeline: the direct sweep at 16, 20 and 24 resident
+  // warps per SM (pipelines 0, 3, 4), the TMA-staged and register-prefetched rows
+  const std::vector<int> warp_opts[5] = {{4, 8, 16}, {4, 8, 16}, {4, 8}, {5, 10}, {6, 8, 12}};
   const int row_opts[3] = {1, 2, 4};
   // every resident domain active for the timing launches (s = 0 only: the spare
   // lattice is written, the current state is read and left as it is)
@@ -1328,9 +1332,9 @@ lbm_status autotune(lbm_batch *b, int reps, double *best_us) {
   double best = 1e300;
   int bv = b->vec, bw = b->warps, br = b->rows, bp = b->pipe;
   lbm_status rc = LBM_OK;
-  for (int p = 0; p < 3 && rc == LBM_OK; ++p)
+  for (int p = 0; p < 5 && rc == LBM_OK; ++p)
     for (int v : vecs)
-      for (int w : warp_opts)
+      for (int w : warp_opts[p])
         for (int r : row_opts) {
           if (sweep_occupancy(b->storage, v, p, w) <= 0) continue;
           rc = set_config(b, v, w, r, p);

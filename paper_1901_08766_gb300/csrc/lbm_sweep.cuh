@@ -600,12 +600,22 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
   }
 }
 
-#ifndef LBM_SWEEP_THREADS
-#define LBM_SWEEP_THREADS 512
-#endif
+// Register budgets of the direct sweep: the resident warps per SM it is compiled for.
+// Row pipeline 0: 16 warps (blocks of up to 16 warps, 128 registers); 3: 20 warps (blocks
+// of up to 10 warps, two or more per SM, at most 102 registers); 4: 24 warps (blocks of up
+// to 12 warps, at most 85 registers). More resident warps cover more DRAM latency at the
+// price of spilled registers; with warps taking work items from the counter (rows of
+// unequal cost finish together) 24 warps measured fastest on the 64-domain batch.
+template <int R> struct Budget;
+template <> struct Budget<16> { static constexpr int kThreads = 512, kBlocks = 1; };
+template <> struct Budget<20> { static constexpr int kThreads = 320, kBlocks = 2; };
+template <> struct Budget<24> { static constexpr int kThreads = 384, kBlocks = 2; };
+
+constexpr int budget_of_pipe(int pipe) { return pipe == 3 ? 20 : (pipe == 4 ? 24 : 16); }
+
 // DEF: some domain of the batch has pulsating bodies (the kappa term of U_O)
-template <int S, int V, bool DEF>
-__global__ void __launch_bounds__(LBM_SWEEP_THREADS) sweep_kernel(SweepArgs args, int s) {
+template <int S, int V, bool DEF, int R>
+__global__ void __launch_bounds__(Budget<R>::kThreads, Budget<R>::kBlocks) sweep_kernel(SweepArgs args, int s) {
   sweep_body<S, V, false, DEF>(args, s);
 }
 
@@ -614,11 +624,22 @@ __global__ void __launch_bounds__(256) sweep_pf_kernel(SweepArgs args, int s) {
   sweep_body<S, V, true>(args, s);
 }
 
-template <int S, int V>
-cudaError_t launch_sweep_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s, bool def) {
-  if (def) sweep_kernel<S, V, true><<<grid, warps * 32, 0, st>>>(a, s);
-  else sweep_kernel<S, V, false><<<grid, warps * 32, 0, st>>>(a, s);
+template <int S, int V, int R>
+cudaError_t launch_sweep_r(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s, bool def) {
+  if (def) sweep_kernel<S, V, true, R><<<grid, warps * 32, 0, st>>>(a, s);
+  else sweep_kernel<S, V, false, R><<<grid, warps * 32, 0, st>>>(a, s);
   return cudaGetLastError();
+}
+
+// The direct sweep (row pipelines 0, 3, 4: its register budgets)
+template <int S, int V>
+cudaError_t launch_sweep_t(int grid, int warps, cudaStream_t st, const SweepArgs &a, int s, bool def,
+                           int pipe) {
+  switch (budget_of_pipe(pipe)) {
+    case 20: return launch_sweep_r<S, V, 20>(grid, warps, st, a, s, def);
+    case 24: return launch_sweep_r<S, V, 24>(grid, warps, st, a, s, def);
+    default: return launch_sweep_r<S, V, 16>(grid, warps, st, a, s, def);
+  }
 }
 
 template <int S, int V>
@@ -627,14 +648,23 @@ cudaError_t launch_sweep_pf_t(int grid, int warps, cudaStream_t st, const SweepA
   return cudaGetLastError();
 }
 
-template <int S, int V> int max_blocks_t(int warps) {
+template <int S, int V, int R> int max_blocks_r(int warps) {
+  if (warps * 32 > Budget<R>::kThreads) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<S, V, false>, warps * 32, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<S, V, false, R>, warps * 32, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
+}
+
+template <int S, int V> int max_blocks_t(int warps, int pipe) {
+  switch (budget_of_pipe(pipe)) {
+    case 20: return max_blocks_r<S, V, 20>(warps);
+    case 24: return max_blocks_r<S, V, 24>(warps);
+    default: return max_blocks_r<S, V, 16>(warps);
+  }
 }
 
 template <int S, int V> int max_blocks_pf_t(int warps) {

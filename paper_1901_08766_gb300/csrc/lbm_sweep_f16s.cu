@@ -5,10 +5,10 @@
 namespace lbm {
 
 cudaError_t launch_sweep_f16s(int vec, int pipe, int grid, int warps, cudaStream_t st,
-                               const SweepArgs &a, int s) {
-  if (pipe == 0 || pipe == 4) {  // 4: the direct sweep with pulsating bodies
-    if (vec == 4) return launch_sweep_t<LBM_F16S, 4>(grid, warps, st, a, s, pipe == 4);
-    if (vec == 8) return launch_sweep_t<LBM_F16S, 8>(grid, warps, st, a, s, pipe == 4);
+                               const SweepArgs &a, int s, bool def) {
+  if (pipe == 0 || pipe == 3 || pipe == 4) {  // the direct sweep at its register budgets
+    if (vec == 4) return launch_sweep_t<LBM_F16S, 4>(grid, warps, st, a, s, def, pipe);
+    if (vec == 8) return launch_sweep_t<LBM_F16S, 8>(grid, warps, st, a, s, def, pipe);
   } else if (pipe == 2) {
     if (vec == 4) return launch_sweep_pf_t<LBM_F16S, 4>(grid, warps, st, a, s);
     if (vec == 8) return launch_sweep_pf_t<LBM_F16S, 8>(grid, warps, st, a, s);
@@ -20,9 +20,9 @@ cudaError_t launch_sweep_f16s(int vec, int pipe, int grid, int warps, cudaStream
 }
 
 int max_blocks_f16s(int vec, int pipe, int warps) {
-  if (pipe == 0) {
-    if (vec == 4) return max_blocks_t<LBM_F16S, 4>(warps);
-    if (vec == 8) return max_blocks_t<LBM_F16S, 8>(warps);
+  if (pipe == 0 || pipe == 3 || pipe == 4) {
+    if (vec == 4) return max_blocks_t<LBM_F16S, 4>(warps, pipe);
+    if (vec == 8) return max_blocks_t<LBM_F16S, 8>(warps, pipe);
   } else if (pipe == 2) {
     if (vec == 4) return max_blocks_pf_t<LBM_F16S, 4>(warps);
     if (vec == 8) return max_blocks_pf_t<LBM_F16S, 8>(warps);

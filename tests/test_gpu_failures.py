@@ -130,8 +130,8 @@ def test_guard_bands_untouched_on_ragged_sizes(lbm, storage):
         slots.append(b.admit(spec, nsteps=100))
     vecs = {"f64": (1, 2), "f32": (2, 4)}.get(storage, (4, 8))
     for vec in vecs:
-        for pipe in (0, 1, 2):
-            b.set_tile(vec, 8, 2, pipe)
+        for pipe in (0, 1, 2, 3, 4):
+            b.set_tile(vec, 8 if pipe != 3 else 5, 2, pipe)
             b.run(5)
     for k in slots:
         b.poll(k)

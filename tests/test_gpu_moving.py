@@ -56,7 +56,7 @@ def test_moving_domain_alone_equals_in_a_mixed_batch(lbm):
     fixed = synth.parity_case("channel_97x61")
     g0 = codec.encode(synth.random_populations(5, moving["nx"], moving["ny"], 0.05), "f16s")
     out = []
-    for others, tile, graph in [(0, (8, 8, 2, 0), 0), (2, (4, 4, 3, 0), 16), (1, (8, 16, 1, 0), 7)]:
+    for others, tile, graph in [(0, (8, 8, 2, 0), 0), (2, (4, 4, 3, 0), 16), (1, (8, 16, 1, 0), 7), (1, (8, 12, 4, 4), 16), (0, (4, 5, 2, 3), 0)]:
         b = lbm.Batch("f16s", max_domains=4, graph_steps=graph)
         ks = [b.admit(fixed, nsteps=90) for _ in range(others)]
         k = b.admit(moving, nsteps=90)

@@ -64,7 +64,7 @@ def test_turning_domain_alone_equals_in_a_mixed_batch(lbm):
     tr = dict(_turning_spec(), moving=True)
     g0 = codec.encode(synth.random_populations(5, spec["nx"], spec["ny"], 0.05), "f16s")
     out = []
-    for others, tile, graph in [(0, (8, 8, 2, 0), 0), (2, (4, 4, 3, 0), 16), (1, (8, 16, 1, 0), 7)]:
+    for others, tile, graph in [(0, (8, 8, 2, 0), 0), (2, (4, 4, 3, 0), 16), (1, (8, 16, 1, 0), 7), (1, (8, 12, 4, 4), 16), (0, (4, 5, 2, 3), 0)]:
         b = lbm.Batch("f16s", max_domains=4, graph_steps=graph)
         ks = [b.admit(fixed if q % 2 == 0 else tr, nsteps=90) for q in range(others)]
         k = b.admit(spec, nsteps=90)
@@ -177,16 +177,18 @@ def test_pulsating_fp64_matches_oracle(lbm, moving, edges):
 
 
 def test_pulsating_batch_graphs_and_resume(lbm):
-    # FP16-shifted: alone, in a mixed batch with CUDA graphs, and resumed at index 70,
-    # the same bits
+    # FP16-shifted: alone, in a mixed batch with CUDA graphs, with the direct sweep at 24
+    # resident warps, and resumed at index 70, the same bits
     spec = _pulsating_spec(2)
     fixed = synth.parity_case("channel_97x61")
     g0 = codec.encode(synth.random_populations(5, spec["nx"], spec["ny"], 0.05), "f16s")
     out = []
-    for others, graph in [(0, 0), (2, 16)]:
+    for others, graph, tile in [(0, 0, None), (2, 16, None), (1, 8, (8, 12, 4, 4))]:
         b = lbm.Batch("f16s", max_domains=4, graph_steps=graph)
         ks = [b.admit(fixed, nsteps=160) for _ in range(others)]
         k = b.admit(spec, nsteps=160)
+        if tile:
+            b.set_tile(*tile)
         b.set_populations(k, g0)
         while b.run(40):
             pass
@@ -196,8 +198,9 @@ def test_pulsating_batch_graphs_and_resume(lbm):
         for q in ks:
             b.poll(q)
         b.close()
-    for x, y in zip(out[1], out[0]):
-        assert np.array_equal(x, y)
+    for o in out[1:]:
+        for x, y in zip(o, out[0]):
+            assert np.array_equal(x, y)
     assert np.array_equal(out[0][2], oracle.rasterize(spec, 160))
     a = lbm.Domain(spec, storage="f16s")
     a.set_populations(g0)

@@ -56,7 +56,8 @@ def _run_split(lbm, spec, storage, g0, steps, tile, widths):
 
 @pytest.mark.parametrize("storage", ["f64", "f16s"])
 @pytest.mark.parametrize("edges", ["periodic", "channel"])
-@pytest.mark.parametrize("tile", [(8, 8, 2, 0), (4, 4, 3, 1), (8, 4, 2, 2)], ids=["direct", "tma", "prefetch"])
+@pytest.mark.parametrize("tile", [(8, 8, 2, 0), (4, 4, 3, 1), (8, 4, 2, 2), (8, 12, 4, 4)],
+                         ids=["direct", "tma", "prefetch", "direct24"])
 def test_two_slabs_reproduce_the_grid(lbm, storage, edges, tile):
     vec = tile[0] if storage != "f64" else tile[0] // 4
     tile = (vec,) + tile[1:]
