@@ -13,6 +13,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm_internal.h"
 
@@ -24,6 +25,14 @@ thread_local std::string g_last_error;
 void set_last_error(const char *msg) { g_last_error = msg; }
 
 namespace {
+
+// A named NVTX range over a scope (seen by profilers that record NVTX; inert otherwise).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 lbm_status fail(lbm_status s, const char *fmt, ...) {
   char buf[512];
@@ -1425,6 +1434,7 @@ lbm_status lbm_batch_create(int32_t max_domains, size_t hbm_budget_bytes, int32_
 lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask,
                            const lbm_geometry *geom, const lbm_body *bodies, int32_t nbodies,
                            int64_t nsteps, int32_t *slot) {
+  Range range("lbm_batch_admit");
   if (!b || !slot) return fail(LBM_EINVAL, "batch or slot pointer is NULL");
   int k = -1;
   lbm_status rc = admit(b, p, mask, geom, bodies, nbodies, nsteps, &k);
@@ -1435,11 +1445,13 @@ lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint8_t *mas
 lbm_status lbm_batch_admit_many(lbm_batch *b, int32_t n, const lbm_params *params,
                                 const lbm_geometry *geoms, const lbm_body *const *bodies,
                                 const int32_t *nbodies, const int64_t *nsteps, int32_t *slots) {
+  Range range("lbm_batch_admit_many");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   return admit_many(b, n, params, geoms, bodies, nbodies, nsteps, slots);
 }
 
 lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps_run) {
+  Range range("lbm_batch_run");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   long long n = 0;
   lbm_status rc = run(b, max_steps, &n);
@@ -1449,6 +1461,7 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps_run) {
 
 lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_entries,
                           int64_t *written, int32_t *done) {
+  Range range("lbm_batch_poll");
   long long w = 0;
   int d = 0;
   lbm_status rc = poll(b, slot, out, max_entries, &w, &d);
@@ -1460,11 +1473,13 @@ lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_e
 lbm_status lbm_batch_poll_many(lbm_batch *b, int32_t n, const int32_t *slots, double *const *outs,
                                const int64_t *max_entries, int64_t *written, int32_t *done,
                                int32_t *status) {
+  Range range("lbm_batch_poll_many");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   return poll_many(b, n, slots, outs, max_entries, written, done, status);
 }
 
 lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, double *ux, double *uy) {
+  Range range("lbm_batch_moments");
   return moments(b, slot, rho, ux, uy);
 }
 
@@ -1708,6 +1723,7 @@ lbm_status lbm_batch_set_halo(lbm_batch *b, int32_t slot, int32_t side, void *re
 }
 
 lbm_status lbm_batch_pack_halos(lbm_batch *b) {
+  Range range("lbm_batch_pack_halos");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   HaloPack pack{};
   pack.elem = static_cast<int32_t>(elem_size(b->storage));
@@ -1762,6 +1778,7 @@ lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot) {
 }
 
 lbm_status lbm_batch_capture(lbm_batch *b) {
+  Range range("lbm_batch_capture");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   if (b->graph_steps <= 0) return LBM_OK;  // the batch steps with direct launches
   if (b->dirty) {
@@ -1800,6 +1817,7 @@ lbm_status lbm_batch_inject(lbm_batch *b, int32_t slot, int32_t kind) {
 }
 
 lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us) {
+  Range range("lbm_batch_autotune");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   return autotune(b, reps, best_us);
 }
@@ -1879,6 +1897,7 @@ lbm_status lbm_domain_create(const lbm_params *p, const uint8_t *mask, const lbm
 }
 
 lbm_status lbm_step(lbm_domain *d, int64_t nsteps) {
+  Range range("lbm_step");
   if (!d) return fail(LBM_EINVAL, "domain is NULL");
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
   long long n = 0;
@@ -1895,6 +1914,7 @@ lbm_status lbm_forces(lbm_domain *d, double *out, int64_t max_entries, int64_t *
 }
 
 lbm_status lbm_moments(lbm_domain *d, double *rho, double *ux, double *uy) {
+  Range range("lbm_moments");
   if (!d) return fail(LBM_EINVAL, "domain is NULL");
   return moments(d->b, 0, rho, ux, uy);
 }

@@ -27,6 +27,14 @@ from concurrent.futures import Future
 from dataclasses import dataclass, field
 
 import numpy as np
+import torch
+
+
+def _nvtx(name):
+    """A named NVTX range (seen by profilers that record NVTX; inert otherwise). The
+    library's own entry points (lbm_batch_run, lbm_batch_admit_many, lbm_batch_poll_many,
+    ...) push ranges of their own inside these."""
+    return torch.cuda.nvtx.range(name)
 
 from . import diagnostics
 
@@ -263,19 +271,23 @@ class Server:
             self.t_start = now
         self._arrivals(now)
         t0 = time.perf_counter()
-        self._admit()
+        with _nvtx("server.admit"):
+            self._admit()
         t1 = time.perf_counter()
         self.host_s["admit"] += t1 - t0
         if self._resident:
             if self.autotune and not self._tuned:
-                self.backend.autotune(reps=3)
+                with _nvtx("server.autotune"):
+                    self.backend.autotune(reps=3)
                 self._tuned = True
-            ran = self.backend.run(self.chunk_steps)
+            with _nvtx(f"server.chunk {self.chunks_run}"):
+                ran = self.backend.run(self.chunk_steps)
             t2 = time.perf_counter()
             self.chunks_run += 1
-            self._drain()
-            if ran == 0:
+            with _nvtx("server.drain"):
                 self._drain()
+                if ran == 0:
+                    self._drain()
             self.host_s["run"] += t2 - t1
             self.host_s["drain"] += time.perf_counter() - t2
         with self._lock:

@@ -197,7 +197,8 @@ class HaloGrid:
         with torch.cuda.stream(self.stream):
             for _ in range(int(n)):
                 self.batch.pack_halos()
-                self._exchange()
+                with torch.cuda.nvtx.range("slabs.exchange"):
+                    self._exchange()
                 self.batch.run(1)
 
     def _exchange(self):
