@@ -557,10 +557,13 @@ def measure_served(lbm, torch, args, plain=None):
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
     with torch.cuda.stream(stream):
+        # the compressed stream lasts about a second, too short to amortise retuning per
+        # workload class: it keeps the tile tuned on the batched workload (the same widths)
+        tuned = getattr(args, "tuned_tile", None)
         srv = Server(storage=args.storage, hbm_budget=budget, chunk_steps=args.served_chunk,
-                     graph_steps=args.graph_steps)
-        if getattr(args, "tuned_tile", None):
-            srv.backend.set_tile(*args.tuned_tile)
+                     graph_steps=args.graph_steps, autotune=not tuned)
+        if tuned:
+            srv.backend.set_tile(*tuned)
         t0 = srv.clock()
         futs = [srv.submit(sp, nsteps=max(1, int(sp["steps"] * args.served_scale)),
                            arrival=t0 + a * args.served_scale) for a, sp in reqs]
@@ -572,7 +575,7 @@ def measure_served(lbm, torch, args, plain=None):
            "completed": st["completed"], "not_ok": bad, "glups": st["glups"],
            "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
            "max_queue": st["max_queue"], "hbm_budget_bytes": budget, "wall_s": st["wall_s"],
-           "host_s": st["host_s"],
+           "host_s": st["host_s"], "retunes": st["retunes"],
            "latency": "arrival to last force slice on the host"}
     if plain and st["glups"]:
         out["served_vs_plain_f32"] = st["glups"] / plain["value"]
@@ -921,7 +924,8 @@ def served_stream(lbm, torch, np, args):
             "p50_service_s": float(np.percentile(svc, 50)) if svc else None,
             "max_resident": max(resident) if resident else 0, "max_queue": st["max_queue"],
             "chunk_steps": args.served_chunk, "storage": args.storage,
-            "max_resident": args.served_max_resident,
+            "resident_cap": args.served_max_resident, "retunes": st["retunes"],
+            "tune_cache": st["tune_cache"], "host_s": st["host_s"],
             "latency": "arrival to last force slice on the host", "hbm_budget_bytes": budget}
 
 

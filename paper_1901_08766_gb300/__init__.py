@@ -336,6 +336,7 @@ class Batch:
                                  None, C.byref(h)), "lbm_batch_create")
         self._h = h
         self._meta = {}
+        self._deform = set()  # slots with pulsating bodies (another sweep variant)
 
     def admit(self, spec, nsteps=None, force_every=1, force_capacity=8192, mask=None) -> int:
         """Admit a domain; returns its slot. Raises LbmError(LBM_EBUSY) when full."""
@@ -357,6 +358,7 @@ class Batch:
                     self.evict(slot.value)
                     raise err
             if b.get("deform"):  # a pulsating body
+                self._deform.add(slot.value)
                 rc = load().lbm_batch_set_deformation(self._h, slot.value, k + 1,
                                                       float(b["deform"]["amplitude"]),
                                                       float(b["deform"]["rate"]))
@@ -513,6 +515,7 @@ class Batch:
     def evict(self, slot: int):
         check(load().lbm_batch_evict(self._h, slot), "lbm_batch_evict")
         self._meta.pop(slot, None)
+        self._deform.discard(slot)
 
     def set_halo(self, slot: int, side: int, recv=None, send=None):
         """Make x edge `side` (0 west, 1 east) of a slot a halo edge fed from `recv` and
@@ -547,10 +550,28 @@ class Batch:
               "lbm_batch_profile")
         return a.value, b.value, n.value
 
-    def autotune(self, reps: int = 10) -> float:
-        us = C.c_double()
-        check(load().lbm_batch_autotune(self._h, reps, C.byref(us)), "lbm_batch_autotune")
-        return us.value
+    def workload_key(self) -> str:
+        """The class of the resident workload that tuned tile shapes are cached under
+        (device, storage, kernel variant, cells and width classes: `tuning.workload_key`)."""
+        import torch
+        from .tuning import workload_key
+        prop = torch.cuda.get_device_properties(self._stream.device)
+        return workload_key(prop.name, prop.multi_processor_count, self.storage,
+                            bool(self._deform), [m[:2] for m in self._meta.values()])
+
+    def autotune(self, reps: int = 10, cache=None) -> float:
+        """Time the tile shapes on the resident domains and keep the fastest; returns
+        its time per sweep launch in microseconds. With a `tuning.TuneCache`, a shape
+        already tuned for this workload class is set without timing (and the time it
+        was tuned at is returned), and a newly tuned one is stored."""
+        def tune():
+            us = C.c_double()
+            check(load().lbm_batch_autotune(self._h, reps, C.byref(us)), "lbm_batch_autotune")
+            return us.value
+        if cache is None:
+            return tune()
+        from .tuning import cached_autotune
+        return cached_autotune(cache, self.workload_key(), tune, self.set_tile, self.get_tile)
 
     def set_tile(self, vec: int, warps: int, rows: int, pipeline: int = 0):
         check(load().lbm_batch_set_tile(self._h, vec, warps, rows, pipeline), "lbm_batch_set_tile")

@@ -21,6 +21,7 @@ from __future__ import annotations
 import collections
 import heapq
 import itertools
+import os
 import threading
 import time
 from concurrent.futures import Future
@@ -37,6 +38,7 @@ def _nvtx(name):
     return torch.cuda.nvtx.range(name)
 
 from . import diagnostics
+from .tuning import TuneCache
 
 
 @dataclass
@@ -77,7 +79,7 @@ class Server:
 
     def __init__(self, storage="f16s", max_domains=256, hbm_budget=0, chunk_steps=256,
                  graph_steps=32, force_every=1, backend=None, clock=time.perf_counter,
-                 autotune=False, max_resident=None):
+                 autotune=True, tune_cache=None, max_resident=None):
         if backend is None:
             from . import Batch
             backend = Batch(storage, max_domains=max_domains, hbm_budget=hbm_budget,
@@ -90,11 +92,17 @@ class Server:
         self.force_every = int(force_every)
         self.force_capacity = self.chunk_steps + 8  # force entries of one chunk per request
         self.clock = clock
+        # the tile shape is retuned whenever the resident workload changes class
+        # (tuning.workload_key); shapes tuned once per class come from the cache, which
+        # persists in a JSON file when `tune_cache` is a path
         self.autotune = autotune
+        if isinstance(tune_cache, (str, bytes, os.PathLike)):
+            tune_cache = TuneCache(os.fsdecode(tune_cache))
+        self.tune_cache = tune_cache if tune_cache is not None else TuneCache()
+        self._tuned_key = None
         # at most this many requests share the GPU at once (None: as many as memory holds);
         # fewer residents finish each sooner, the others wait in the FIFO queue
         self.max_resident = max_resident
-        self._tuned = False
         self._ids = itertools.count()
         self._lock = threading.Lock()
         self._pending = []                      # heap of (arrival, rid, req) not yet arrived
@@ -110,7 +118,8 @@ class Server:
         self.max_queue = 0
         # host time per part of the loop (seconds): admission, enqueueing the chunk, draining
         # (which waits for the chunk on the GPU)
-        self.host_s = {"admit": 0.0, "run": 0.0, "drain": 0.0}
+        self.host_s = {"admit": 0.0, "tune": 0.0, "run": 0.0, "drain": 0.0}
+        self.retunes = 0
 
     # ---- client side ---------------------------------------------------------------
     def submit(self, spec, nsteps=None, arrival=None, on_forces=None) -> Future:
@@ -276,10 +285,16 @@ class Server:
         t1 = time.perf_counter()
         self.host_s["admit"] += t1 - t0
         if self._resident:
-            if self.autotune and not self._tuned:
-                with _nvtx("server.autotune"):
-                    self.backend.autotune(reps=3)
-                self._tuned = True
+            if self.autotune:
+                key = self.backend.workload_key()
+                if key != self._tuned_key:
+                    with _nvtx("server.autotune"):
+                        self.backend.autotune(reps=3, cache=self.tune_cache)
+                    self._tuned_key = key
+                    self.retunes += 1
+                t_tune = time.perf_counter()
+                self.host_s["tune"] += t_tune - t1
+                t1 = t_tune
             with _nvtx(f"server.chunk {self.chunks_run}"):
                 ran = self.backend.run(self.chunk_steps)
             t2 = time.perf_counter()
@@ -329,4 +344,5 @@ class Server:
                 "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
                 "glups": self.cell_updates / wall / 1e9 if wall > 0 else None,
                 "wall_s": wall, "chunks": self.chunks_run, "max_queue": self.max_queue,
-                "host_s": dict(self.host_s)}
+                "host_s": dict(self.host_s), "retunes": self.retunes,
+                "tune_cache": {"hits": self.tune_cache.hits, "misses": self.tune_cache.misses}}

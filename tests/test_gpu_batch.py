@@ -89,6 +89,34 @@ def test_autotune_keeps_state_and_results(lbm):
     batch.close()
 
 
+def test_autotune_cache_reuses_shapes_per_workload_class(lbm, tmp_path):
+    from paper_1901_08766_gb300.tuning import TuneCache
+    specs = _specs()
+    path = str(tmp_path / "tune.json")
+    cache = TuneCache(path)
+    a = lbm.Batch("f16s", max_domains=4, graph_steps=0)
+    for s in specs:
+        a.admit(s, nsteps=40)
+    us = a.autotune(reps=2, cache=cache)
+    tile = a.get_tile()
+    assert cache.misses == 1 and us > 0
+    # a second batch of the same workload class takes the stored shape without timing
+    b = lbm.Batch("f16s", max_domains=4, graph_steps=0)
+    slots = [b.admit(s, nsteps=40) for s in specs]
+    b.set_tile(4, 4, 1, 0)
+    n0 = b.info()["kernel_launches"]
+    assert b.workload_key() == a.workload_key()
+    assert b.autotune(reps=2, cache=TuneCache(path)) == us
+    assert b.get_tile() == tile and b.info()["kernel_launches"] == n0
+    # and steps as the tuned batch does, bit for bit
+    b.run(40)
+    a.run(40)
+    for k in slots:
+        assert np.array_equal(a.get_populations(k).view(np.uint16), b.get_populations(k).view(np.uint16))
+    a.close()
+    b.close()
+
+
 def test_admission_budget_and_eviction(lbm):
     spec = synth.parity_case("channel_97x61")
     need = lbm.domain_bytes(spec, "f16s")

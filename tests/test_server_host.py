@@ -6,6 +6,7 @@ import pytest
 
 import synth
 from paper_1901_08766_gb300 import server as srvmod
+from paper_1901_08766_gb300 import tuning
 from paper_1901_08766_gb300._native import LBM_EBUSY, LBM_EINVAL, LBM_EUNSTABLE, LbmError
 
 
@@ -58,8 +59,29 @@ class FakeBatch:
     def evict(self, slot):
         del self.slots[slot]
 
-    def autotune(self, reps=3):
-        return 1.0
+    # tile tuning: the fake's "best" tile depends on the resident cells, like a real batch
+    tile = (8, 16, 1, 0)
+    timed = 0
+
+    def workload_key(self):
+        return tuning.workload_key("fake", 2, "f16s", False,
+                                   [(s["spec"]["nx"], s["spec"]["ny"]) for s in self.slots.values()])
+
+    def set_tile(self, *t):
+        self.tile = tuple(t)
+
+    def get_tile(self):
+        return self.tile
+
+    def autotune(self, reps=3, cache=None):
+        def tune():
+            self.timed += 1
+            cells = sum(s["cells"] for s in self.slots.values())
+            self.tile = (8, 12 if cells > 4000 else 8, 4, 4)
+            return 100.0 + cells
+        if cache is None:
+            return tune()
+        return tuning.cached_autotune(cache, self.workload_key(), tune, self.set_tile, self.get_tile)
 
 
 class FakeBatchMany(FakeBatch):
@@ -205,3 +227,39 @@ def test_group_admission_is_fifo_and_used():
     res = [f.result() for f in futs]
     assert all(r.status == "ok" for r in res) and [r.steps for r in res] == [20 + i for i in range(6)]
     assert [r.admitted for r in res] == sorted(r.admitted for r in res)
+
+
+def test_server_retunes_per_workload_class_and_persists(tmp_path):
+    # autotuning is on by default: the server tunes when the resident workload changes
+    # class, takes shapes it has tuned before from the cache, and a second server reading
+    # the same JSON file times nothing
+    path = tmp_path / "tune.json"
+    runs = []
+    for _ in range(2):
+        clock = Clock()
+        fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
+        srv = srvmod.Server(backend=fb, chunk_steps=10, clock=clock, tune_cache=str(path))
+        futs = [srv.submit(_spec("small", n=40, steps=30), arrival=0.0),
+                srv.submit(_spec("big", n=200, steps=60), arrival=0.015),
+                srv.submit(_spec("small2", n=40, steps=60), arrival=0.05)]
+        srv.run_until_idle()
+        assert all(f.result().status == "ok" for f in futs)
+        runs.append((fb.timed, srv.retunes, srv.stats()["tune_cache"]))
+    (timed1, retunes1, c1), (timed2, retunes2, c2) = runs
+    # classes seen: small alone; small + big (big alone and big + small2 are the same
+    # class: the small domains hold under a quarter of the cells); small2 alone, the
+    # first class again, so from the cache
+    assert retunes1 == retunes2 == 3
+    assert timed1 == c1["misses"] and c1["hits"] == retunes1 - timed1 and timed1 < retunes1
+    assert timed2 == 0 and c2["hits"] == retunes2
+    saved = tuning.TuneCache(str(path)).entries
+    assert len(saved) == timed1 and all(len(e["tile"]) == 4 for e in saved.values())
+
+
+def test_server_without_autotune_keeps_the_tile():
+    clock = Clock()
+    fb = FakeBatch(budget_cells=10 ** 9, clock=clock)
+    srv = srvmod.Server(backend=fb, chunk_steps=10, clock=clock, autotune=False)
+    srv.submit(_spec("a", steps=20), arrival=0.0)
+    srv.run_until_idle()
+    assert fb.timed == 0 and srv.retunes == 0 and fb.tile == (8, 16, 1, 0)
