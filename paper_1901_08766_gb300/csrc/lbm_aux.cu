@@ -184,11 +184,20 @@ __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0
   return s;
 }
 
+// Largest distance of a shape's node from its reference point: the radius of a circle;
+// for a NACA section (reference at the quarter chord) 3/4 of the chord along it plus the
+// largest half thickness across it, 5 |t| c max(poly) < 5 |t| c (0.2969 + 0.2843) < 3 |t| c,
+// and never less than the chord.
+__host__ __device__ __forceinline__ double shape_extent(const ShapeDev &s) {
+  if (s.kind == LBM_SHAPE_CIRCLE) return s.radius;
+  return fmax(s.chord, 0.75 * s.chord + 3.0 * fabs(s.thickness) * s.chord);
+}
+
 __device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int x0, int j, int &lo, int &hi) {
   lo = 0;
   hi = nx - 1;
   if (s.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
-  const double reach = (s.kind == LBM_SHAPE_CIRCLE ? s.radius : s.chord) + 1.0;
+  const double reach = shape_extent(s) + 1.0;
   if (fabs(double(j) - s.cy) > reach) {
     lo = 1;
     hi = 0;
@@ -231,8 +240,7 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
     cy = float(D.centre0[2 * b + 1]) + float(D.bodies[5 * b + 3]) * fn;
     const float ox = float(s0.cx - D.centre0[2 * b]), oy = float(s0.cy - D.centre0[2 * b + 1]);
     const float grow = deforms(D, s0.body) ? fabsf(float(D.dpar[2 * b])) : 0.f;
-    turn = (1.0f + grow) * sqrtf(ox * ox + oy * oy) +
-           grow * float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 0.01f;
+    turn = (1.0f + grow) * sqrtf(ox * ox + oy * oy) + grow * float(shape_extent(s0)) + 0.01f;
   } else {
     float vx = 0.f, vy = 0.f;
     if (s0.body >= 1 && s0.body <= D.nbodies) {
@@ -243,7 +251,7 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
     cx = (float(s0.cx) - float(D.x0)) + vx * fn;
     cy = float(s0.cy) + vy * fn;
   }
-  const float reach = float(s0.kind == LBM_SHAPE_CIRCLE ? s0.radius : s0.chord) + 2.0f + turn;
+  const float reach = float(shape_extent(s0)) + 2.0f + turn;
   if (!(fabsf(float(j) - cy) <= reach)) {
     lo = 1;
     hi = 0;
@@ -552,28 +560,38 @@ template <int S>
 __global__ void init_kernel(typename Codec<S>::E *lat, int nx, int ny, int pitch, double rho0,
                             double ux, double uy) {
   using Cd = Codec<S>;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  using E = typename Cd::E;
+  // 16-byte stores: rows start on 16-byte boundaries (the pitch is a multiple of 64
+  // elements, the lattice starts on a 256-byte boundary)
+  constexpr int kPer = 16 / static_cast<int>(sizeof(E));
+  const int wd = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   const int a = blockIdx.z;
-  if (i >= pitch || j >= ny) return;
+  if (wd >= pitch / kPer || j >= ny) return;
   const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
   const double eu = ex_of(a) * ux + ey_of(a) * uy;
   const double usq = ux * ux + uy * uy;
   // Eq. (feq) with c_s^2 = 1/3; shifted storage keeps f^eq - w rho0 (times its scale)
   const double dev = rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-  double val = Cd::kStoreShifted ? dev * Cd::kScale : rho0 * w + dev;
-  if (i >= nx) val = 0.0;
-  lat[(static_cast<size_t>(a) * ny + j) * pitch + i] = Cd::enc(typename Cd::T(val));
+  const E val = Cd::enc(typename Cd::T(Cd::kStoreShifted ? dev * Cd::kScale : rho0 * w + dev));
+  union {
+    uint4 v;
+    E e[kPer];
+  } u;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) u.e[q] = wd * kPer + q < nx ? val : E(0);
+  reinterpret_cast<uint4 *>(lat + (static_cast<size_t>(a) * ny + j) * pitch)[wd] = u.v;
 }
 
 cudaError_t launch_init(int storage, cudaStream_t st, void *lat, int nx, int ny, int pitch,
                         double rho0, double ux, double uy) {
-  dim3 grid((pitch + 255) / 256, ny, kQ);
+  const int per = storage == LBM_F64 ? 2 : (storage == LBM_F32 ? 4 : 8);  // elements per 16 bytes
+  dim3 grid((pitch / per + 127) / 128, ny, kQ);
   switch (storage) {
-    case LBM_F64: init_kernel<LBM_F64><<<grid, 256, 0, st>>>(static_cast<double *>(lat), nx, ny, pitch, rho0, ux, uy); break;
-    case LBM_F32: init_kernel<LBM_F32><<<grid, 256, 0, st>>>(static_cast<float *>(lat), nx, ny, pitch, rho0, ux, uy); break;
-    case LBM_F16S: init_kernel<LBM_F16S><<<grid, 256, 0, st>>>(static_cast<uint16_t *>(lat), nx, ny, pitch, rho0, ux, uy); break;
-    case LBM_BF16S: init_kernel<LBM_BF16S><<<grid, 256, 0, st>>>(static_cast<uint16_t *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_F64: init_kernel<LBM_F64><<<grid, 128, 0, st>>>(static_cast<double *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_F32: init_kernel<LBM_F32><<<grid, 128, 0, st>>>(static_cast<float *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_F16S: init_kernel<LBM_F16S><<<grid, 128, 0, st>>>(static_cast<uint16_t *>(lat), nx, ny, pitch, rho0, ux, uy); break;
+    case LBM_BF16S: init_kernel<LBM_BF16S><<<grid, 128, 0, st>>>(static_cast<uint16_t *>(lat), nx, ny, pitch, rho0, ux, uy); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -661,107 +679,139 @@ __device__ __forceinline__ int admit_domain_of(const AdmitDev *ad, int n, int r)
 }
 
 // Mask row j (all pitch columns, padding zero) from the domain's shapes, then its per-row
-// node counts of every body id.
-__global__ void admit_raster_count_kernel(AdmitDev *ad, int n) {
-  __shared__ int32_t hist[256];
-  __shared__ int dsh;
-  if (threadIdx.x == 0) dsh = admit_domain_of(ad, n, blockIdx.x);
-  for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-  __syncthreads();
-  AdmitDev &A = ad[dsh];
-  const int j = blockIdx.x - A.row0;
+// node counts of every body id. One warp per row of the flat list, eight rows per block.
+// Only the columns within some shape's reach (shape_cols) take the FP64 predicate; the
+// rest are fluid. A lane writes four columns with one 32-bit store (rows start on
+// 64-byte boundaries: the pitch is a multiple of 64).
+constexpr int kAdmitCull = 64;        // shapes per domain whose column intervals are culled
+constexpr int kAdmitRowsPerBlock = 8;  // rows (warps) per block of the rasteriser
+
+__global__ void __launch_bounds__(32 * kAdmitRowsPerBlock) admit_raster_count_kernel(AdmitDev *ad, int n, int rows) {
+  __shared__ int32_t hist_s[kAdmitRowsPerBlock][256];
+  __shared__ int lo_s[kAdmitRowsPerBlock][kAdmitCull], hi_s[kAdmitRowsPerBlock][kAdmitCull];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kAdmitRowsPerBlock + warp;
+  if (r >= rows) return;  // warp-uniform; the warps of a block do not synchronise
+  int32_t *hist = hist_s[warp];
+  int *lo = lo_s[warp], *hi = hi_s[warp];
+  for (int b = lane; b < 256; b += 32) hist[b] = 0;
+  AdmitDev &A = ad[admit_domain_of(ad, n, r)];
+  const int j = r - A.row0;
+  const bool cull = A.nshapes <= kAdmitCull;
+  if (cull)
+    for (int k = lane; k < A.nshapes; k += 32) shape_cols(A.shapes[k], A.nx, A.x0, j, lo[k], hi[k]);
+  __syncwarp();
   uint8_t *row = A.mask + static_cast<size_t>(j) * A.pitch;
-  for (int i = threadIdx.x; i < A.pitch; i += blockDim.x) {
-    uint8_t b = 0;
-    if (i < A.nx) {
-      for (int k = 0; k < A.nshapes; ++k)
+  int fluid = 0;
+  for (int c0 = 4 * lane; c0 < A.pitch; c0 += 4 * 32) {
+    uint32_t word = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int i = c0 + q;
+      if (i >= A.nx) break;
+      uint32_t b = 0;
+      for (int k = 0; k < A.nshapes; ++k) {
+        if (cull && (i < lo[k] || i > hi[k])) continue;
         if (inside(A.shapes[k], double(i + A.x0), double(j))) b = static_cast<uint8_t>(A.shapes[k].body);
-      atomicAdd(&hist[b], 1);
+      }
+      if (b == 0) ++fluid;
+      else atomicAdd(&hist[b], 1);
+      word |= b << (8 * q);
     }
-    row[i] = b;
+    *reinterpret_cast<uint32_t *>(row + c0) = word;
   }
-  __syncthreads();
-  for (int b = threadIdx.x; b < 256; b += blockDim.x) {
-    const int c = hist[b];
-    if (b <= A.nbodies) A.counts[static_cast<size_t>(b) * A.ny + j] = c;
-    else if (c > 0) atomicMax(&A.bad, b);
+  for (int o = 16; o > 0; o >>= 1) fluid += __shfl_xor_sync(0xffffffffu, fluid, o);
+  __syncwarp();
+  if (lane == 0) hist[0] = fluid;
+  __syncwarp();
+  for (int b = lane; b < 256; b += 32) {
+    const int cnt = hist[b];
+    if (b <= A.nbodies) A.counts[static_cast<size_t>(b) * A.ny + j] = cnt;
+    else if (cnt > 0) atomicMax(&A.bad, b);
   }
 }
 
 cudaError_t launch_admit_raster_count(cudaStream_t st, AdmitDev *ad, int n, int rows) {
   if (rows <= 0) return cudaSuccess;
-  admit_raster_count_kernel<<<rows, 256, 0, st>>>(ad, n);
+  admit_raster_count_kernel<<<(rows + kAdmitRowsPerBlock - 1) / kAdmitRowsPerBlock, 32 * kAdmitRowsPerBlock, 0, st>>>(
+      ad, n, rows);
   return cudaGetLastError();
 }
 
-// Block (r, b - 1): the nodes of body b in row r of the flat list, as row_scatter_kernel.
-__global__ void admit_scatter_kernel(const AdmitDev *ad, int n) {
-  __shared__ int dsh;
-  __shared__ int32_t warp_tot[32];
-  __shared__ int32_t base;
-  if (threadIdx.x == 0) dsh = admit_domain_of(ad, n, blockIdx.x);
-  __syncthreads();
-  const AdmitDev &A = ad[dsh];
-  const int body = blockIdx.y + 1;
-  if (body > A.nbodies) return;  // uniform over the block
-  const int j = blockIdx.x - A.row0;
-  if (threadIdx.x == 0) base = A.row_off[static_cast<size_t>(body - 1) * A.ny + j];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// The nodes of each body in row r of the flat list, in column order, at the row's offset
+// in the body's part of the solid list (as row_scatter_kernel). One warp per row, eight
+// rows per block; a row without nodes of a body (its count) is not scanned for it.
+__global__ void __launch_bounds__(32 * kAdmitRowsPerBlock) admit_scatter_kernel(const AdmitDev *ad, int n, int rows) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kAdmitRowsPerBlock + warp;
+  if (r >= rows) return;  // warp-uniform
+  const AdmitDev &A = ad[admit_domain_of(ad, n, r)];
+  const int j = r - A.row0;
   const uint8_t *row = A.mask + static_cast<size_t>(j) * A.pitch;
-  for (int i0 = 0; i0 < A.nx; i0 += blockDim.x) {
-    const int i = i0 + threadIdx.x;
-    const bool hit = i < A.nx && row[i] == body;
-    const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) warp_tot[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < nw; ++w) {
-      if (w < warp) before += warp_tot[w];
-      total += warp_tot[w];
+  for (int body = 1; body <= A.nbodies; ++body) {
+    if (A.counts[static_cast<size_t>(body) * A.ny + j] == 0) continue;
+    int base = A.row_off[static_cast<size_t>(body - 1) * A.ny + j];
+    for (int i0 = 0; i0 < A.nx; i0 += 32) {
+      const int i = i0 + lane;
+      const bool hit = i < A.nx && row[i] == body;
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) A.solid[base + __popc(bal & ((1u << lane) - 1u))] = j * A.pitch + i;
+      base += __popc(bal);
     }
-    if (hit) A.solid[base + before + __popc(bal & ((1u << lane) - 1u))] = j * A.pitch + i;
-    __syncthreads();
-    if (threadIdx.x == 0) base += total;
-    __syncthreads();
   }
 }
 
 cudaError_t launch_admit_scatter(cudaStream_t st, const AdmitDev *ad, int n, int rows, int max_bodies) {
   if (rows <= 0 || max_bodies <= 0) return cudaSuccess;
-  admit_scatter_kernel<<<dim3(rows, max_bodies), 256, 0, st>>>(ad, n);
+  admit_scatter_kernel<<<(rows + kAdmitRowsPerBlock - 1) / kAdmitRowsPerBlock, 32 * kAdmitRowsPerBlock, 0, st>>>(
+      ad, n, rows);
   return cudaGetLastError();
 }
 
-// Block (r, a): row r of direction a of lattice A set to f^eq(rho0, u0) as init_kernel
-// does, and the same row of lattice B to zero.
+static_assert(kPitchAlign % 16 == 0, "16-byte row stores need pitches of 16 elements");
+
+// Block r: row r of every direction of lattice A set to f^eq(rho0, u0) as init_kernel
+// does, and the same rows of lattice B to zero, with 16-byte stores (a row starts on a
+// 16-byte boundary: lattices start on 256-byte boundaries and the pitch is a multiple of
+// 64 elements).
 template <int S>
 __global__ void admit_init_kernel(const AdmitDev *ad, int n) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
+  constexpr int kPer = 16 / static_cast<int>(sizeof(E));
   __shared__ int dsh;
+  __shared__ E val_s[kQ];
   if (threadIdx.x == 0) dsh = admit_domain_of(ad, n, blockIdx.x);
   __syncthreads();
   const AdmitDev &A = ad[dsh];
   const int j = blockIdx.x - A.row0;
-  const int a = blockIdx.y;
-  const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-  const double eu = ex_of(a) * A.u0x + ey_of(a) * A.u0y;
-  const double usq = A.u0x * A.u0x + A.u0y * A.u0y;
-  const double dev = A.rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-  const E val = Cd::enc(typename Cd::T(Cd::kStoreShifted ? dev * Cd::kScale : A.rho0 * w + dev));
-  const size_t off = (static_cast<size_t>(a) * A.ny + j) * A.pitch;
-  E *la = static_cast<E *>(A.lat[0]) + off;
-  E *lb = static_cast<E *>(A.lat[1]) + off;
-  for (int i = threadIdx.x; i < A.pitch; i += blockDim.x) {
-    la[i] = i < A.nx ? val : E(0);
-    lb[i] = E(0);
+  if (threadIdx.x < kQ) {
+    const int a = threadIdx.x;
+    const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const double eu = ex_of(a) * A.u0x + ey_of(a) * A.u0y;
+    const double usq = A.u0x * A.u0x + A.u0y * A.u0y;
+    const double dev = A.rho0 * w * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+    val_s[a] = Cd::enc(typename Cd::T(Cd::kStoreShifted ? dev * Cd::kScale : A.rho0 * w + dev));
+  }
+  __syncthreads();
+  const int words = A.pitch / kPer;
+  for (int t = threadIdx.x; t < kQ * words; t += blockDim.x) {
+    const int a = t / words, wd = t - a * words;
+    const size_t off = (static_cast<size_t>(a) * A.ny + j) * A.pitch;
+    const E val = val_s[a];
+    union {
+      uint4 v;
+      E e[kPer];
+    } u;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) u.e[q] = wd * kPer + q < A.nx ? val : E(0);
+    reinterpret_cast<uint4 *>(static_cast<E *>(A.lat[0]) + off)[wd] = u.v;
+    reinterpret_cast<uint4 *>(static_cast<E *>(A.lat[1]) + off)[wd] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
 cudaError_t launch_admit_init(int storage, cudaStream_t st, const AdmitDev *ad, int n, int rows) {
   if (rows <= 0) return cudaSuccess;
-  const dim3 grid(rows, kQ);
+  const int grid = rows;
   switch (storage) {
     case LBM_F64: admit_init_kernel<LBM_F64><<<grid, 256, 0, st>>>(ad, n); break;
     case LBM_F32: admit_init_kernel<LBM_F32><<<grid, 256, 0, st>>>(ad, n); break;

@@ -18,7 +18,37 @@ def _mixed_specs():
     specs.append(synth._spec("empty", 65, 7, 0.05, [], [], 0, 0.02,
                              synth._edges("inlet", "outflow", "free_slip", "free_slip"), u_in=(0.02, 0.0)))
     specs.append(synth.parity_case("periodic_97x61"))
+    specs.append(synth.couette(n=70, r_inner=12.0, r_outer=30.0))
+    specs.append(_thick_and_many())
     return specs
+
+
+def _thick_and_many():
+    # a NACA section whose thickness ratio (2.6) takes it beyond one chord of its quarter
+    # chord across the chord line, tilted; and 70 small circles on three bodies (more
+    # shapes than the rasteriser culls per row)
+    sh = [{"kind": "naca4", "body": 1, "cx": 60.3, "cy": 50.2, "chord": 16.0, "thickness": 2.6,
+           "aoa_rad": 1.2}]
+    for q in range(70):
+        sh.append(synth._circle(2 + q % 3, 110.0 + 7.3 * (q % 10), 12.0 + 11.1 * (q // 10), 2.6 + 0.1 * (q % 4)))
+    bodies = [synth._body(60.3, 50.2, 16.0)] + [synth._body(140.0, 50.0, 10.0) for _ in range(3)]
+    return synth._spec("thick_many", 197, 101, 0.05, sh, bodies, 0, 0.02,
+                       synth._edges("inlet", "outflow", "free_slip", "free_slip"), u_in=(0.02, 0.0))
+
+
+def test_admit_many_masks_equal_the_oracle(lbm):
+    import oracle
+    specs = _mixed_specs()
+    b = lbm.Batch("f16s", max_domains=len(specs), graph_steps=0)
+    slots = b.admit_many(specs, nsteps=1)
+    for sp, k in zip(specs, slots):
+        ref = oracle.rasterize(sp)
+        assert np.array_equal(b.mask(k), ref), sp["name"]
+    # the thick section reaches beyond one chord across its chord line
+    m = oracle.rasterize(specs[-1])
+    ys, xs = np.nonzero(m == 1)
+    assert np.hypot(xs - 60.3, ys - 50.2).max() > 16.0 + 2.0
+    b.close()
 
 
 def _run(lbm, storage, specs, batched, steps=23):
@@ -116,3 +146,17 @@ def test_poll_many_equals_polls(lbm):
         for (fa, da), (fb, db) in zip(ga, wa):
             assert da == db and np.array_equal(fa, fb)
     assert [d for _, d in got[-1]] == [True] * 5 + [False]  # nsteps 11..16 after 15 steps
+
+
+@pytest.mark.parametrize("moving", [True, 2])
+def test_thick_section_moving_masks_equal_the_oracle(lbm, moving):
+    # the per-row column culling of moving and rotating domains reaches the thick section
+    sp = _thick_and_many()
+    sp = dict(sp, shapes=sp["shapes"][:1], bodies=[dict(sp["bodies"][0], vx=0.05, vy=-0.02, omega=0.01)],
+              moving=moving)
+    import oracle
+    d = lbm.Domain(sp, storage="f32")
+    assert np.array_equal(d.mask(), oracle.rasterize(sp, 0))
+    d.run(40)
+    assert np.array_equal(d.mask(), oracle.rasterize(sp, 40))
+    d.close()
