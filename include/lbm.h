@@ -599,6 +599,23 @@ LBM_API lbm_status lbm3_restore_coupled(lbm3_domain *d, int64_t steps, const dou
  * events; mean microseconds per launch (either output may be NULL). */
 LBM_API lbm_status lbm3_profile(lbm3_domain *d, int32_t steps, double *sweep_us, double *force_us);
 
+/* The 3D sweep's register budget: pipeline 0 (16-bit storage: 16 resident warps per SM at
+ * 128 registers; FP32/FP64: 12 warps at 168), 3 or 4 (16-bit storage only: 20 or 24
+ * resident warps per SM at 102 or 85 registers). A new domain starts at pipeline 3 for
+ * 16-bit D3Q15 and 0 otherwise (the faster on a 384 x 128 x 128 sphere channel). With
+ * 16-bit storage the sweep's warps
+ * take strips from a device counter, otherwise every (grid warps)-th strip. Results do
+ * not depend on it. LBM_EINVAL for another value or a pipeline the storage does not
+ * have. */
+LBM_API lbm_status lbm3_set_tile(lbm3_domain *d, int32_t pipeline);
+LBM_API lbm_status lbm3_get_tile(lbm3_domain *d, int32_t *pipeline);
+
+/* Time each pipeline the storage has on the domain for `reps` sweep launches each (two
+ * more untimed) and keep the fastest. The timing launches read the current lattice and
+ * write only the spare one, so the state is untouched. *best_us receives the best time
+ * per sweep launch (may be NULL). Synchronises. */
+LBM_API lbm_status lbm3_autotune(lbm3_domain *d, int32_t reps, double *best_us);
+
 LBM_API lbm_status lbm3_domain_destroy(lbm3_domain *d);
 
 #ifdef __cplusplus

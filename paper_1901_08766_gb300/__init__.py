@@ -306,6 +306,23 @@ class Domain3:
               "lbm3_profile")
         return a.value, b.value
 
+    def set_tile(self, pipeline: int):
+        """The sweep's register budget: 0, or 3 / 4 (20 / 24 resident warps per SM, 16-bit
+        storage only). Results do not depend on it."""
+        check(load().lbm3_set_tile(self._handle(), int(pipeline)), "lbm3_set_tile")
+
+    def get_tile(self) -> int:
+        p = C.c_int32()
+        check(load().lbm3_get_tile(self._handle(), C.byref(p)), "lbm3_get_tile")
+        return p.value
+
+    def autotune(self, reps: int = 10) -> float:
+        """Time each register budget on this domain (state untouched), keep the fastest;
+        returns its time per sweep launch in microseconds."""
+        us = C.c_double()
+        check(load().lbm3_autotune(self._handle(), int(reps), C.byref(us)), "lbm3_autotune")
+        return us.value
+
     def close(self):
         if self._h is not None:
             load().lbm3_domain_destroy(self._h)

@@ -190,6 +190,9 @@ SIGNATURES = {
     "lbm3_coupled_state": (C.c_int, [_VP, _DP]),
     "lbm3_restore_coupled": (C.c_int, [_VP, _I64, _DP]),
     "lbm3_profile": (C.c_int, [_VP, _I32, _DP, _DP]),
+    "lbm3_set_tile": (C.c_int, [_VP, _I32]),
+    "lbm3_get_tile": (C.c_int, [_VP, C.POINTER(_I32)]),
+    "lbm3_autotune": (C.c_int, [_VP, _I32, _DP]),
     "lbm3_domain_destroy": (C.c_int, [_VP]),
 }
 

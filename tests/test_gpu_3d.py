@@ -231,6 +231,41 @@ def test_3d_checkpoint_resume_is_bit_identical(lbm, storage, q):
     c.close()
 
 
+@pytest.mark.parametrize("q", [19, 15])
+@pytest.mark.parametrize("storage", ["f16s", "bf16s", "f32"])
+def test_3d_register_budgets_give_the_same_bits(lbm, storage, q):
+    # every register budget (16, 20, 24 resident warps for 16-bit storage) and the autotuner
+    # step the same bits, bodies and ragged strips included; the autotuner leaves the
+    # state as it was
+    spec = _case("periodic_bodies_97x18x14", q)
+    pipes = [0, 3, 4] if storage != "f32" else [0]
+    g0 = codec.encode(synth.random_populations3(17, spec["nx"], spec["ny"], spec["nz"], 0.05, q=q), storage)
+    out = []
+    for pipe in pipes + ["auto"]:
+        d = lbm.Domain3(spec, storage=storage)
+        d.set_populations(g0)
+        if pipe == "auto":
+            before = d.get_populations().view(np.uint8).copy()
+            us = d.autotune(reps=2)
+            assert us > 0 and d.get_tile() in pipes
+            assert np.array_equal(d.get_populations().view(np.uint8), before)
+        else:
+            d.set_tile(pipe)
+            assert d.get_tile() == pipe
+        f = d.run(60)
+        out.append((d.get_populations().view(np.uint8).copy(), f))
+        d.close()
+    for x, fx in out[1:]:
+        assert np.array_equal(x, out[0][0]) and np.array_equal(fx, out[0][1])
+    d = lbm.Domain3(spec, storage=storage)
+    assert d.get_tile() == (3 if storage != "f32" and q == 15 else 0)  # the measured default
+    with pytest.raises(lbm.LbmError):
+        d.set_tile(2)
+    if storage == "f32":
+        with pytest.raises(lbm.LbmError):
+            d.set_tile(4)
+    d.close()
+
 
 def _moving3(edges, q):
     # bodies stay clear of the domain edges and of each other over 400 steps (a body pushed
