@@ -238,7 +238,10 @@ LBM_API lbm_status lbm_domain_destroy(lbm_domain *d);
  * force-reduction launch; steps are replayed from captured CUDA graphs.
  *  max_domains:      slot count (1..4096).
  *  hbm_budget_bytes: admission limit on the sum of lbm_domain_bytes (0: no limit).
- *  graph_steps:      steps per captured graph (0: no graphs, one launch per kernel). */
+ *  graph_steps:      steps per captured graph (0: no graphs, one launch per kernel).
+ * The sweep starts with the tile the autotuner picks on a 64-domain batch of uneven
+ * cylinder-pair domains: 16-bit storage (vec 8, 12 warps, 4 rows, pipeline 4), FP32
+ * (4, 16, 4, 0), FP64 (2, 4, 4, 0); lbm_batch_set_tile / lbm_batch_autotune change it. */
 LBM_API lbm_status lbm_batch_create(int32_t max_domains, size_t hbm_budget_bytes, int32_t storage,
                             int32_t graph_steps, void *cuda_stream, lbm_alloc_fn alloc,
                             lbm_free_fn free_fn, void *alloc_ctx, lbm_batch **out);

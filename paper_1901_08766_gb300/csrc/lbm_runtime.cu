@@ -316,11 +316,14 @@ bool vec_ok(int storage, int vec) {
   }
 }
 
+// The tile a batch starts with: the autotuner's choice on the 64-domain batched workload
+// (16-bit storage: 8 cells per thread, 12-warp blocks at 24 resident warps per SM, 376 us;
+// FP32: 4 cells per thread, 16-warp blocks, 623 us); FP64 (ALU-bound) 4-warp blocks.
 void default_tile(int storage, int &vec, int &warps, int &rows, int &pipe) {
   vec = storage == LBM_F64 ? 2 : (storage == LBM_F32 ? 4 : 8);
-  warps = 4;
+  warps = storage == LBM_F64 ? 4 : (storage == LBM_F32 ? 16 : 12);
   rows = 4;
-  pipe = 0;
+  pipe = (storage == LBM_F16S || storage == LBM_BF16S) ? 4 : 0;
 }
 
 void drop_graph(lbm_batch *b) {
