@@ -727,6 +727,14 @@ def experiment(args):
                     r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
     elif args.experiment == "sphere3d":
         out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None))
+    elif args.experiment == "admission":
+        # the end-to-end jobs of the batched workload alone (admission, steps, readback),
+        # repeated, for the cost of each phase
+        specs = synth.batched_domains(args.domains)
+        stream = torch.cuda.Stream()
+        jobs = [_e2e_job(lbm, torch, specs, args, stream) for _ in range(args.jobs)]
+        out.update({"domains": args.domains, "steps": args.steps, "jobs": [
+            {"value": j["value"], "job_ms": j["job_ms"], "phases_ms": j["phases_ms"]} for j in jobs]})
     elif args.experiment == "served":
         out.update(served_stream(lbm, torch, np, args))
     elif args.experiment == "viv":
@@ -1067,7 +1075,8 @@ def main():
     ap.add_argument("--served-seconds", type=float, default=120.0, help="arrival window (--experiment served)")
     ap.add_argument("--served-max-resident", type=int, default=None,
                     help="cap on requests sharing the GPU (--experiment served; default: memory only)")
-    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv",
+    ap.add_argument("--jobs", type=int, default=4, help="end-to-end jobs (--experiment admission)")
+    ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv", "admission",
                                              "paper"],
                     default=None,
                     help="accuracy study instead of the benchmark")
