@@ -726,7 +726,7 @@ def experiment(args):
                 for k in ("cd_mean", "cl_rms", "st"):
                     r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
     elif args.experiment == "sphere3d":
-        out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None))
+        out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None, args.lattice))
     elif args.experiment == "admission":
         # the end-to-end jobs of the batched workload alone (admission, steps, readback),
         # repeated, for the cost of each phase
@@ -945,16 +945,16 @@ def bytes3(storage, q=19):
     return q * ELEM[storage] * 2 + 1
 
 
-def sphere3d(lbm, torch, np, only=None):
-    """3D (D3Q19) sweep throughput per storage on a sphere channel larger than L2, and
-    the drag coefficient of each storage against FP64 on a smaller sphere channel
-    (`only`: time just these storages, no drag runs)."""
+def sphere3d(lbm, torch, np, only=None, lattice=19):
+    """3D (D3Q19, D3Q15) sweep throughput per storage on a sphere channel larger than L2,
+    and the drag coefficient of each storage against FP64 on a smaller sphere channel
+    (`only`: time just these storages on `lattice`, no drag runs)."""
     import synth
     peak = _peak_hbm()
     perf = []
     spec = synth.sphere_channel(384, 128, 128, D=32.0)
     nodes = spec["nx"] * spec["ny"] * spec["nz"]
-    runs = [(19, st, False) for st in (only or ("f16s", "bf16s", "f32", "f64"))]
+    runs = [(lattice if only else 19, st, False) for st in (only or ("f16s", "bf16s", "f32", "f64"))]
     if not only:
         runs += [(15, st, False) for st in ("f16s", "bf16s", "f32")]
         runs += [(19, "f16s", True)]  # the sphere moving upstream: mask updated every step
@@ -1076,6 +1076,8 @@ def main():
     ap.add_argument("--served-max-resident", type=int, default=None,
                     help="cap on requests sharing the GPU (--experiment served; default: memory only)")
     ap.add_argument("--jobs", type=int, default=4, help="end-to-end jobs (--experiment admission)")
+    ap.add_argument("--lattice", type=int, default=19, choices=[19, 15],
+                    help="3D lattice of --experiment sphere3d --quick")
     ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv", "admission",
                                              "paper"],
                     default=None,
