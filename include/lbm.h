@@ -621,6 +621,61 @@ LBM_API lbm_status lbm3_autotune(lbm3_domain *d, int32_t reps, double *best_us);
 
 LBM_API lbm_status lbm3_domain_destroy(lbm3_domain *d);
 
+/* ---- batches of 3D domains --------------------------------------------------------------
+ * A 3D batch advances many fixed-geometry 3D domains of one storage type and one lattice
+ * together (the 2D batch's recipe for Sec. 2.2's 3D step): each time step is one
+ * persistent sweep launch per group of up to 16 domains with steps left, whose warps take
+ * strips of every domain of the group from one device counter (the domains' parameters
+ * travel in the launch's), then one force-reduction launch per group. Every result is
+ * that of the same domain run alone (lbm3_step), bit for bit.
+ *  max_domains: slots (1..4096); hbm_budget_bytes: admission limit on the sum of
+ *  lbm3_domain_bytes (0: none); storage, lattice (19 or 15) of every domain; memory from the
+ *  allocator callbacks (both NULL: stream-ordered cudaMallocAsync), launches on
+ *  cuda_stream. LBM_EINVAL for an argument out of range. */
+typedef struct lbm3_batch lbm3_batch;
+LBM_API lbm_status lbm3_batch_create(int32_t max_domains, size_t hbm_budget_bytes, int32_t storage,
+                                     int32_t lattice, void *cuda_stream, lbm_alloc_fn alloc,
+                                     lbm_free_fn free_fn, void *alloc_ctx, lbm3_batch **out);
+
+/* Admit a domain (arguments as lbm3_domain_create) that runs `nsteps` steps; *slot
+ * receives its slot. LBM_EINVAL for another storage or lattice than the batch's, or a
+ * moving domain (p->moving != 0); LBM_EBUSY when every slot is taken or the budget would
+ * be exceeded. Synchronises. */
+LBM_API lbm_status lbm3_batch_admit(lbm3_batch *b, const lbm3_params *p, const lbm3_shape *shapes,
+                                    int32_t nshapes, const lbm3_body *bodies, int32_t nbodies,
+                                    int64_t nsteps, int32_t *slot);
+
+/* Enqueue up to max_steps steps of every resident domain with steps left (asynchronous);
+ * *steps_run receives the steps enqueued (0: nothing left). LBM_EBUSY, enqueueing
+ * nothing, if a domain's undrained force entries would exceed its ring. */
+LBM_API lbm_status lbm3_batch_run(lbm3_batch *b, int64_t max_steps, int64_t *steps_run);
+
+/* Drain a slot's force entries as lbm3_forces does ([entry][body][3], FP64, into host
+ * memory); *done = 1 once the slot reached its step target. Synchronises.
+ * LBM_EUNSTABLE if the domain diverged; LBM_ENOTFOUND for a free slot. */
+LBM_API lbm_status lbm3_batch_poll(lbm3_batch *b, int32_t slot, double *out, int64_t max_entries,
+                                   int64_t *written, int32_t *done);
+
+/* The slot's domain, for lbm3_get_populations, lbm3_set_populations, lbm3_moments,
+ * lbm3_get_mask and lbm3_steps_done. It stays owned by the batch: do not step, destroy
+ * or change its step index through the lbm3_* calls. */
+LBM_API lbm_status lbm3_batch_domain(lbm3_batch *b, int32_t slot, lbm3_domain **out);
+
+/* Free a slot and its device memory (synchronises). LBM_ENOTFOUND for a free slot. */
+LBM_API lbm_status lbm3_batch_evict(lbm3_batch *b, int32_t slot);
+
+/* The batched sweep's register budget, as lbm3_set_tile (a new batch takes pipeline 3
+ * for 16-bit D3Q15, 0 otherwise). Results do not depend on it. */
+LBM_API lbm_status lbm3_batch_set_tile(lbm3_batch *b, int32_t pipeline);
+
+/* Resident slots and cells, kernel launches enqueued by lbm3_batch_run, bytes admitted
+ * and the current pipeline. Any output may be NULL. */
+LBM_API lbm_status lbm3_batch_info(lbm3_batch *b, int32_t *resident, int64_t *cells,
+                                   int64_t *launches, size_t *bytes, int32_t *pipeline);
+
+/* Destroy the batch and every resident domain (synchronises). NULL is a no-op. */
+LBM_API lbm_status lbm3_batch_destroy(lbm3_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -335,6 +335,111 @@ class Domain3:
             pass
 
 
+class _BatchDomain3(Domain3):
+    """A resident domain of a Batch3, for its populations, moments, mask and step index.
+    The batch owns it: it is not stepped or destroyed through this view."""
+
+    def __init__(self, batch, slot, spec, storage, force_capacity):
+        self.spec, self.storage = spec, storage
+        self.nx, self.ny, self.nz = spec["nx"], spec["ny"], spec["nz"]
+        self.q = 15 if spec.get("lattice", 19) == 15 else 19
+        self.nbodies = len(spec["bodies"])
+        self._params = _native.params3_from_spec(spec, storage, 1, force_capacity)
+        h = C.c_void_p()
+        check(load().lbm3_batch_domain(batch._h, int(slot), C.byref(h)), "lbm3_batch_domain")
+        self._h = h
+
+    def step(self, n: int):
+        raise RuntimeError("a batch's domain is stepped by Batch3.run")
+
+    def set_steps_done(self, steps: int):
+        raise RuntimeError("a batch's domain keeps the batch's step index")
+
+    def close(self):
+        self._h = None  # owned by the batch
+
+
+class Batch3:
+    """Many fixed-geometry 3D domains of one storage and lattice advanced together: one
+    persistent sweep launch per step over every resident domain (lbm3_batch_* calls)."""
+
+    def __init__(self, storage="f16s", lattice=19, max_domains=16, hbm_budget=0, stream=None,
+                 allocator="torch"):
+        import torch
+        self.storage, self.lattice = storage, int(lattice)
+        self._alloc = _allocator(allocator)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        check(load().lbm3_batch_create(int(max_domains), int(hbm_budget), STORAGE[storage], self.lattice,
+                                       C.c_void_p(self._stream.cuda_stream),
+                                       self._alloc.c_alloc if self._alloc else _native.ALLOC_FN(),
+                                       self._alloc.c_free if self._alloc else _native.FREE_FN(),
+                                       None, C.byref(h)), "lbm3_batch_create")
+        self._h = h
+        self._meta = {}  # slot -> (spec, force_capacity)
+
+    def admit(self, spec, nsteps=None, force_every=1, force_capacity=8192) -> int:
+        """Admit a fixed-geometry domain; returns its slot. Raises LbmError(LBM_EBUSY) when
+        the slots or the memory budget are used up."""
+        sp = dict(spec, lattice=spec.get("lattice", self.lattice))
+        params = _native.params3_from_spec(sp, self.storage, force_every, force_capacity)
+        bodies, nb = _native.bodies3_from_spec(sp)
+        shapes, ns = _native.shapes3_from_spec(sp)
+        slot = C.c_int32()
+        n = sp["steps"] if nsteps is None else int(nsteps)
+        check(load().lbm3_batch_admit(self._h, C.byref(params), shapes, ns, bodies, nb, n, C.byref(slot)),
+              "lbm3_batch_admit")
+        self._meta[slot.value] = (sp, force_capacity)
+        return slot.value
+
+    def run(self, max_steps: int) -> int:
+        """Enqueue up to max_steps steps of every domain with steps left; returns the steps
+        enqueued (0: every domain reached its target)."""
+        n = C.c_int64()
+        check(load().lbm3_batch_run(self._h, int(max_steps), C.byref(n)), "lbm3_batch_run")
+        return n.value
+
+    def poll(self, slot: int):
+        """(forces [entries, nbodies, 3] since the last poll, done)."""
+        sp, cap = self._meta[slot]
+        nb = len(sp["bodies"])
+        buf = np.zeros((cap, max(nb, 1), 3))
+        w, d = C.c_int64(), C.c_int32()
+        check(load().lbm3_batch_poll(self._h, int(slot), buf.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                                     C.byref(w), C.byref(d)), "lbm3_batch_poll")
+        return buf[: w.value, :nb].copy(), bool(d.value)
+
+    def domain(self, slot: int) -> Domain3:
+        """The slot's domain (populations, moments, mask, steps_done)."""
+        sp, cap = self._meta[slot]
+        return _BatchDomain3(self, slot, sp, self.storage, cap)
+
+    def evict(self, slot: int):
+        check(load().lbm3_batch_evict(self._h, int(slot)), "lbm3_batch_evict")
+        self._meta.pop(slot, None)
+
+    def set_tile(self, pipeline: int):
+        check(load().lbm3_batch_set_tile(self._h, int(pipeline)), "lbm3_batch_set_tile")
+
+    def info(self):
+        r, c, k, b, p = C.c_int32(), C.c_int64(), C.c_int64(), C.c_size_t(), C.c_int32()
+        check(load().lbm3_batch_info(self._h, C.byref(r), C.byref(c), C.byref(k), C.byref(b), C.byref(p)),
+              "lbm3_batch_info")
+        return {"resident": r.value, "cells": c.value, "kernel_launches": k.value,
+                "bytes_in_use": b.value, "pipeline": p.value}
+
+    def close(self):
+        if self._h is not None:
+            load().lbm3_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Many uneven domains of one storage type advanced together (lbm_batch_* calls)."""
 

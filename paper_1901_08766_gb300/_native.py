@@ -194,6 +194,18 @@ SIGNATURES = {
     "lbm3_get_tile": (C.c_int, [_VP, C.POINTER(_I32)]),
     "lbm3_autotune": (C.c_int, [_VP, _I32, _DP]),
     "lbm3_domain_destroy": (C.c_int, [_VP]),
+    "lbm3_batch_create": (C.c_int, [_I32, C.c_size_t, _I32, _I32, _VP, ALLOC_FN, FREE_FN, _VP,
+                                    C.POINTER(_VP)]),
+    "lbm3_batch_admit": (C.c_int, [_VP, C.POINTER(Params3), C.POINTER(Shape3), _I32,
+                                   C.POINTER(Body3), _I32, _I64, C.POINTER(_I32)]),
+    "lbm3_batch_run": (C.c_int, [_VP, _I64, C.POINTER(_I64)]),
+    "lbm3_batch_poll": (C.c_int, [_VP, _I32, _DP, _I64, C.POINTER(_I64), C.POINTER(_I32)]),
+    "lbm3_batch_domain": (C.c_int, [_VP, _I32, C.POINTER(_VP)]),
+    "lbm3_batch_evict": (C.c_int, [_VP, _I32]),
+    "lbm3_batch_set_tile": (C.c_int, [_VP, _I32]),
+    "lbm3_batch_info": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),
+                                  C.POINTER(C.c_size_t), C.POINTER(_I32)]),
+    "lbm3_batch_destroy": (C.c_int, [_VP]),
 }
 
 _lib = None

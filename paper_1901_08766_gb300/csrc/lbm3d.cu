@@ -391,11 +391,14 @@ __global__ void __launch_bounds__(kMoveThreads3) mmove3_kernel(const __grid_cons
 // tree) into the ring entry. The result does not depend on which block finishes last.
 constexpr int kRowsThreads = 256;
 
-template <typename T>
-__global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const __grid_constant__ Dom3 dom, long long entry) {
-  const Dom3 &D = dom;
+// The force entry `entry` of a domain D (Dom3, or Rows3Dom in a batch): block bx of gx
+// sums -F_VP per body over every gx-th group of its rows (one warp per row), the last
+// block to finish adds the row sums in row order into the ring.
+template <typename T, typename DomT>
+__device__ __forceinline__ void rows3_run(const DomT &D, long long entry, int bx, int gx) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int wg = (bx * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x)) >> 5;
+  const int nw = (gx * static_cast<int>(blockDim.x)) >> 5;
   for (int q = wg; q < D.nfrows; q += nw) {
     const int4 it = D.frows[q];
     const size_t row = static_cast<size_t>(it.x);
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const __grid_consta
   __shared__ double red[3][kRowsThreads / 32];
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(D.rows_done, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(D.rows_done, 1u) == static_cast<unsigned>(gx) - 1u;
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -460,6 +463,40 @@ __global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const __grid_consta
     __syncthreads();
   }
   if (threadIdx.x == 0) *D.rows_done = 0u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRowsThreads) rows3_kernel(const __grid_constant__ Dom3 dom, long long entry) {
+  rows3_run<T>(dom, entry, blockIdx.x, gridDim.x);
+}
+
+// What the force reduction of a batch reads of one domain.
+struct Rows3Dom {
+  const int4 *frows;
+  const uint8_t *mask;
+  const void *fvp;
+  double *rowsum, *ring;
+  uint32_t *rows_done;
+  long long entry;  // the ring entry this launch writes
+  int32_t pitch, nfrows, nbodies, force_cap;
+};
+
+struct Rows3Args {
+  Rows3Dom dom[kGroup3];
+  int32_t ndom;
+};
+
+// The force entries of up to kGroup3 domains of a batch: blocks (bx, d) reduce domain d
+// as rows3_kernel's gridDim.x blocks would; a domain without solid rows gets a zero entry.
+template <typename T>
+__global__ void __launch_bounds__(kRowsThreads) rows3_batch_kernel(const __grid_constant__ Rows3Args args) {
+  const Rows3Dom &D = args.dom[blockIdx.y];
+  if (D.nfrows == 0) {
+    if (blockIdx.x == 0 && threadIdx.x < 3 * D.nbodies)
+      D.ring[static_cast<size_t>(D.entry % D.force_cap) * D.nbodies * 3 + threadIdx.x] = 0.0;
+    return;
+  }
+  rows3_run<T>(D, D.entry, blockIdx.x, gridDim.x);
 }
 
 }  // namespace d3
@@ -746,7 +783,117 @@ lbm_status read_status3(lbm3_domain *d) {
   return LBM_OK;
 }
 
+// A batch of fixed-geometry 3D domains of one storage and lattice (lbm3_batch_*): every
+// slot is a domain of its own (lbm3_domain: memory, initial state, rasteriser, force
+// ring). A step is one persistent sweep launch per group of up to kGroup3 domains that
+// still have steps left, their parameters in the launch's, then one force-reduction
+// launch per group.
+struct Batch3 {
+  int max_domains = 0, storage = 0, q = 19, pipe = 0, sms = 0, grid = 0;
+  size_t budget = 0, bytes_in_use = 0;
+  cudaStream_t st = nullptr;
+  lbm_alloc_fn afn = nullptr;
+  lbm_free_fn ffn = nullptr;
+  void *actx = nullptr;
+  std::vector<lbm3_domain *> slot;  // nullptr: free
+  std::vector<long long> target;    // step target per slot
+  std::vector<size_t> bytes;        // lbm3_domain_bytes per slot
+  uint32_t *d_ctr = nullptr;        // [groups][2] work-item counters
+  long long launches = 0;
+  void *get(size_t n) {
+    if (n == 0) n = 256;
+    if (afn) return afn(n, actx);
+    void *q = nullptr;
+    if (cudaMallocAsync(&q, n, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return q;
+  }
+  void put(void *q) {
+    if (!q) return;
+    if (ffn) ffn(q, actx);
+    else cudaFreeAsync(q, st);
+  }
+};
+
+int groups3(int max_domains) { return (max_domains + kGroup3 - 1) / kGroup3; }
+
+cudaError_t launch_sweep3b(Batch3 *b, const Batch3Args &a) {
+  switch (b->storage) {
+    case LBM_F64: return launch_sweep3b_f64(b->q, b->pipe, b->grid, b->st, a);
+    case LBM_F32: return launch_sweep3b_f32(b->q, b->pipe, b->grid, b->st, a);
+    case LBM_F16S: return launch_sweep3b_f16s(b->q, b->pipe, b->grid, b->st, a);
+    case LBM_BF16S: return launch_sweep3b_bf16s(b->q, b->pipe, b->grid, b->st, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int sweep3b_fits(int q, int storage, int pipe) {
+  switch (storage) {
+    case LBM_F64: return sweep3b_fits_f64(q, pipe);
+    case LBM_F32: return sweep3b_fits_f32(q, pipe);
+    case LBM_F16S: return sweep3b_fits_f16s(q, pipe);
+    case LBM_BF16S: return sweep3b_fits_bf16s(q, pipe);
+  }
+  return 0;
+}
+
+// One step (index within the chunk s) of the domains listed in `ks`: the sweep, then the
+// force entries that fall due.
+lbm_status batch3_step(Batch3 &b, const std::vector<int> &ks, long long s, int group) {
+  const int strip = 32 * (b.storage == LBM_F64 ? 2 : 4);
+  Batch3Args a{};
+  long long acc = 0;
+  a.ndom = static_cast<int32_t>(ks.size());
+  for (int i = 0; i < a.ndom; ++i) {
+    const lbm3_domain *d = b.slot[ks[i]];
+    const long long n = d->done + s;
+    a.dom[i] = d->hpar[(d->parity + static_cast<int>(s & 1)) & 1];
+    a.n[i] = n;
+    a.base[i] = static_cast<int32_t>(acc);
+    acc += static_cast<long long>(d->p.ny) * d->p.nz * ((d->p.nx + strip - 1) / strip);
+  }
+  if (acc >= (1ll << 31)) return fail3(LBM_EINVAL, "a group of the batch holds 2^31 strips or more");
+  a.base[a.ndom] = static_cast<int32_t>(acc);
+  a.ctr = b.d_ctr + 2 * group;
+  LBM3_CUDA(launch_sweep3b(&b, a));
+  ++b.launches;
+  Rows3Args r{};
+  int gx = 1;
+  for (int i = 0; i < a.ndom; ++i) {
+    const lbm3_domain *d = b.slot[ks[i]];
+    const long long n = d->done + s;
+    if (d->p.force_every <= 0 || (n + 1) % d->p.force_every != 0 || d->nbodies == 0) continue;
+    Rows3Dom &x = r.dom[r.ndom++];
+    x.frows = d->h.frows;
+    x.mask = d->h.mask;
+    x.fvp = d->h.fvp;
+    x.rowsum = d->h.rowsum;
+    x.ring = d->h.ring;
+    x.rows_done = d->h.rows_done;
+    x.entry = (n + 1) / d->p.force_every - 1;
+    x.pitch = d->h.pitch;
+    x.nfrows = d->h.nfrows;
+    x.nbodies = d->nbodies;
+    x.force_cap = d->h.force_cap;
+    gx = std::max(gx, d->aux_grid);
+  }
+  if (r.ndom > 0) {
+    const dim3 g(gx, r.ndom);
+    if (b.storage == LBM_F64) rows3_batch_kernel<double><<<g, kRowsThreads, 0, b.st>>>(r);
+    else rows3_batch_kernel<float><<<g, kRowsThreads, 0, b.st>>>(r);
+    LBM3_CUDA(cudaGetLastError());
+    ++b.launches;
+  }
+  return LBM_OK;
+}
+
 }  // namespace
+
+struct lbm3_batch {
+  Batch3 b;
+};
 
 extern "C" {
 
@@ -1321,6 +1468,210 @@ lbm_status lbm3_domain_destroy(lbm3_domain *d) {
   d->put(d->d_dom);
   cudaStreamSynchronize(d->st);
   delete d;
+  return LBM_OK;
+}
+
+// ---- batches of fixed-geometry 3D domains -----------------------------------------------
+
+lbm_status lbm3_batch_create(int32_t max_domains, size_t hbm_budget_bytes, int32_t storage, int32_t lattice,
+                             void *cuda_stream, lbm_alloc_fn alloc, lbm_free_fn free_fn, void *alloc_ctx,
+                             lbm3_batch **out) {
+  if (!out) return fail3(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_domains < 1 || max_domains > 4096) return fail3(LBM_EINVAL, "max_domains must be in [1, 4096]");
+  if (esize(storage) == 0) return fail3(LBM_EINVAL, "unknown storage %d", storage);
+  if (lattice != 19 && lattice != 15) return fail3(LBM_EINVAL, "lattice must be 19 or 15");
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail3(LBM_EINVAL, "alloc and free callbacks go together");
+  lbm3_batch *h = new (std::nothrow) lbm3_batch();
+  if (!h) return fail3(LBM_ENOMEM, "host allocation failed");
+  Batch3 &b = h->b;
+  b.max_domains = max_domains;
+  b.storage = storage;
+  b.q = lattice;
+  b.budget = hbm_budget_bytes;
+  b.st = static_cast<cudaStream_t>(cuda_stream);
+  b.afn = alloc;
+  b.ffn = free_fn;
+  b.actx = alloc_ctx;
+  b.slot.assign(max_domains, nullptr);
+  b.target.assign(max_domains, 0);
+  b.bytes.assign(max_domains, 0);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail3(LBM_ECUDA, "no CUDA device");
+  }
+  const bool k16 = storage == LBM_F16S || storage == LBM_BF16S;
+  b.pipe = (k16 && lattice == 15 && sweep3b_fits(lattice, storage, 3) > 0) ? 3 : 0;
+  b.grid = std::max(1, sweep3b_fits(lattice, storage, b.pipe)) * b.sms;
+  b.d_ctr = static_cast<uint32_t *>(b.get(sizeof(uint32_t) * 2 * groups3(max_domains)));
+  if (!b.d_ctr) {
+    lbm3_batch_destroy(h);
+    return fail3(LBM_ENOMEM, "batch allocation failed");
+  }
+  if (cudaMemsetAsync(b.d_ctr, 0, sizeof(uint32_t) * 2 * groups3(max_domains), b.st) != cudaSuccess) {
+    cudaGetLastError();
+    lbm3_batch_destroy(h);
+    return fail3(LBM_ECUDA, "batch initialisation failed");
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm3_batch_admit(lbm3_batch *h, const lbm3_params *p, const lbm3_shape *shapes, int32_t nshapes,
+                            const lbm3_body *bodies, int32_t nbodies, int64_t nsteps, int32_t *slot_out) {
+  if (!h || !p || !slot_out) return fail3(LBM_EINVAL, "batch, params or slot is NULL");
+  Batch3 &b = h->b;
+  if (p->storage != b.storage) return fail3(LBM_EINVAL, "storage %d differs from the batch's %d", p->storage, b.storage);
+  if (nq_of(*p) != b.q) return fail3(LBM_EINVAL, "lattice D3Q%d differs from the batch's D3Q%d", nq_of(*p), b.q);
+  if (p->moving) return fail3(LBM_EINVAL, "a batch holds fixed-geometry domains only");
+  if (nsteps < 0) return fail3(LBM_EINVAL, "nsteps must be >= 0");
+  int k = -1;
+  for (int q = 0; q < b.max_domains && k < 0; ++q)
+    if (!b.slot[q]) k = q;
+  if (k < 0) return fail3(LBM_EBUSY, "all %d slots are taken", b.max_domains);
+  const size_t need = lbm3_domain_bytes(p, nbodies);
+  if (need == 0) return fail3(LBM_EINVAL, "invalid domain parameters");
+  if (b.budget > 0 && b.bytes_in_use + need > b.budget)
+    return fail3(LBM_EBUSY, "memory budget exceeded (%zu + %zu > %zu)", b.bytes_in_use, need, b.budget);
+  lbm3_domain *d = nullptr;
+  lbm_status rc = lbm3_domain_create(p, shapes, nshapes, bodies, nbodies, b.st, b.afn, b.ffn, b.actx, &d);
+  if (rc != LBM_OK) return rc;
+  b.slot[k] = d;
+  b.target[k] = nsteps;
+  b.bytes[k] = need;
+  b.bytes_in_use += need;
+  *slot_out = k;
+  return LBM_OK;
+}
+
+static lbm_status batch3_slot(lbm3_batch *h, int32_t k, lbm3_domain **d) {
+  if (!h) return fail3(LBM_EINVAL, "batch is NULL");
+  if (k < 0 || k >= h->b.max_domains || !h->b.slot[k]) return fail3(LBM_ENOTFOUND, "slot %d is not resident", k);
+  *d = h->b.slot[k];
+  return LBM_OK;
+}
+
+lbm_status lbm3_batch_run(lbm3_batch *h, int64_t max_steps, int64_t *steps_run) {
+  if (steps_run) *steps_run = 0;
+  if (!h) return fail3(LBM_EINVAL, "batch is NULL");
+  if (max_steps < 0) return fail3(LBM_EINVAL, "max_steps must be >= 0");
+  Batch3 &b = h->b;
+  long long steps = 0;
+  for (int k = 0; k < b.max_domains; ++k)
+    if (b.slot[k]) steps = std::max(steps, std::min<long long>(max_steps, b.target[k] - b.slot[k]->done));
+  if (steps <= 0) return LBM_OK;
+  // every domain's force ring must hold the entries of its steps of this chunk
+  for (int k = 0; k < b.max_domains; ++k) {
+    const lbm3_domain *d = b.slot[k];
+    if (!d || d->p.force_every <= 0) continue;
+    const long long adv = std::max(0ll, std::min(steps, b.target[k] - d->done));
+    if ((d->done + adv) / d->p.force_every - d->drained > d->p.force_capacity)
+      return fail3(LBM_EBUSY, "slot %d: force ring would overflow (poll it first)", k);
+  }
+  // per step: the domains with steps left, in slot order, in groups of kGroup3
+  std::vector<int> ks;
+  ks.reserve(kGroup3);
+  for (long long s = 0; s < steps; ++s) {
+    int group = 0;
+    ks.clear();
+    for (int k = 0; k <= b.max_domains; ++k) {
+      if (k < b.max_domains) {
+        const lbm3_domain *d = b.slot[k];
+        if (!d || d->done + s >= b.target[k]) continue;
+        ks.push_back(k);
+      }
+      if (!ks.empty() && (static_cast<int>(ks.size()) == kGroup3 || k == b.max_domains)) {
+        lbm_status rc = batch3_step(b, ks, s, group++);
+        if (rc != LBM_OK) return rc;
+        ks.clear();
+      }
+    }
+  }
+  for (int k = 0; k < b.max_domains; ++k) {
+    lbm3_domain *d = b.slot[k];
+    if (!d) continue;
+    const long long adv = std::max(0ll, std::min(steps, b.target[k] - d->done));
+    d->done += adv;
+    d->parity = static_cast<int>((d->parity + adv) & 1);
+  }
+  if (steps_run) *steps_run = steps;
+  return LBM_OK;
+}
+
+lbm_status lbm3_batch_poll(lbm3_batch *h, int32_t slot, double *out, int64_t max_entries, int64_t *written,
+                           int32_t *done) {
+  if (written) *written = 0;
+  if (done) *done = 0;
+  lbm3_domain *d = nullptr;
+  lbm_status rc = batch3_slot(h, slot, &d);
+  if (rc != LBM_OK) return rc;
+  rc = lbm3_forces(d, out, max_entries, written);
+  if (done) *done = d->done >= h->b.target[slot] ? 1 : 0;
+  return rc;
+}
+
+lbm_status lbm3_batch_domain(lbm3_batch *h, int32_t slot, lbm3_domain **out) {
+  if (!out) return fail3(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  return batch3_slot(h, slot, out);
+}
+
+lbm_status lbm3_batch_evict(lbm3_batch *h, int32_t slot) {
+  lbm3_domain *d = nullptr;
+  lbm_status rc = batch3_slot(h, slot, &d);
+  if (rc != LBM_OK) return rc;
+  Batch3 &b = h->b;
+  lbm3_domain_destroy(d);  // synchronises the stream: no launch still reads the domain
+  b.slot[slot] = nullptr;
+  b.bytes_in_use -= b.bytes[slot];
+  b.bytes[slot] = 0;
+  b.target[slot] = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm3_batch_set_tile(lbm3_batch *h, int32_t pipeline) {
+  if (!h) return fail3(LBM_EINVAL, "batch is NULL");
+  if (pipeline != 0 && pipeline != 3 && pipeline != 4) return fail3(LBM_EINVAL, "pipeline must be 0, 3 or 4");
+  const int fits = sweep3b_fits(h->b.q, h->b.storage, pipeline);
+  if (fits <= 0) return fail3(LBM_EINVAL, "pipeline %d is not available for storage %d", pipeline, h->b.storage);
+  h->b.pipe = pipeline;
+  h->b.grid = fits * h->b.sms;
+  return LBM_OK;
+}
+
+lbm_status lbm3_batch_info(lbm3_batch *h, int32_t *resident, int64_t *cells, int64_t *launches, size_t *bytes,
+                           int32_t *pipeline) {
+  if (!h) return fail3(LBM_EINVAL, "batch is NULL");
+  int r = 0;
+  long long c = 0;
+  for (const lbm3_domain *d : h->b.slot)
+    if (d) {
+      ++r;
+      c += static_cast<long long>(d->p.nx) * d->p.ny * d->p.nz;
+    }
+  if (resident) *resident = r;
+  if (cells) *cells = c;
+  if (launches) *launches = h->b.launches;
+  if (bytes) *bytes = h->b.bytes_in_use;
+  if (pipeline) *pipeline = h->b.pipe;
+  return LBM_OK;
+}
+
+lbm_status lbm3_batch_destroy(lbm3_batch *h) {
+  if (!h) return LBM_OK;
+  Batch3 &b = h->b;
+  cudaStreamSynchronize(b.st);
+  for (lbm3_domain *&d : b.slot)
+    if (d) {
+      lbm3_domain_destroy(d);
+      d = nullptr;
+    }
+  b.put(b.d_ctr);
+  cudaStreamSynchronize(b.st);
+  delete h;
   return LBM_OK;
 }
 

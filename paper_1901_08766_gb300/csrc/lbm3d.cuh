@@ -395,14 +395,15 @@ template <int Q, int A, typename F> __device__ __forceinline__ void for_dirs(F &
   }
 }
 
-// The fused 3D sweep: one warp per strip of 32 V cells of one row (j, k) at a time
-// (persistent grid), Q vector loads per lane, the +-1 x-shift by shuffles, strip ends by
-// broadcast loads, update, Q vector stores into the other lattice. With 16-bit storage,
-// warps without solid nodes update two nodes at once in paired FP32 (the same operations
-// in the same order on each half).
-template <int Q, int S, int V, bool DEF, int P>
-__global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>::kMinBlocks)
-    sweep3_kernel(const __grid_constant__ Dom3 dom, long long n, int par) {
+// One strip of 32 V cells of row `row` (= k ny + j) of domain D starting at column x0, at
+// step index n: Q vector loads per lane from the lattice D.src, the +-1 x-shift by
+// shuffles, strip ends by broadcast loads, the node update, Q vector stores into D.dst.
+// With 16-bit storage, warps without solid nodes update two nodes at once in paired FP32
+// (the same operations in the same order on each half). `unstable` is set when a node's
+// density leaves (0.01, 100) or is not finite.
+template <int Q, int S, int V, bool DEF>
+__device__ __forceinline__ void sweep3_strip(const Dom3 &D, const int row, const int x0, const long long n,
+                                             const int lane, int &unstable) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
   using T = typename Cd::T;
@@ -411,13 +412,186 @@ __global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>
   constexpr int kStrip = 32 * V;
   constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
   constexpr T kUnscale = T(1) / T(Cd::kScale);
-  const Dom3 &D = dom;  // kernel parameter: constants are read from the parameter bank
   const Const3<T> &C = const3<T>(D);
-  const int lane = threadIdx.x & 31;
-  const int nx = D.nx, ny = D.ny, nz = D.nz, pitch = D.pitch;
-  const int strips = (nx + kStrip - 1) / kStrip;
-  const int items = ny * nz * strips;  // < 2^31: a direction holds < 2^31 elements
+  const int nx = D.nx, ny = D.ny, pitch = D.pitch;
   const bool west_inlet = D.west == LBM_INLET_EQ, east_out = D.east == LBM_OUTFLOW_ZG;
+  const int j = row % ny, k = row / ny;
+  const int xl = x0 + lane * V;
+  const bool lane_on = xl < nx;
+  const bool west_edge = x0 == 0, east_edge = x0 + kStrip >= nx;
+  const int col_l = west_edge ? (west_inlet ? 0 : nx - 1) : x0 - 1;
+  const int col_r = east_edge ? 0 : x0 + kStrip;
+  const int k_last = nx - 1 - xl;
+  const int xl_ld = min(xl, pitch - V);
+  Strip<S, V> v[Q];
+  E end_in[Q];
+  {
+    const RowOff3 R = row_off3(D, j, k);
+    for_dirs<Q, 0>([&](auto ac) {
+      constexpr int a = decltype(ac)::value;
+      const E *rp = src_row_ptr<Q, E, a>(D, R);
+      v[a].load(rp + xl_ld);
+      end_in[a] = E(0);
+      if constexpr (ex3<Q>(a) == 1) end_in[a] = __ldg(rp + col_l);
+      else if constexpr (ex3<Q>(a) == -1) end_in[a] = __ldg(rp + col_r);
+    });
+  }
+  uint8_t b[V];
+  {
+    const uint8_t *mrow = D.mask + (static_cast<size_t>(k) * ny + j) * pitch + xl_ld;
+#pragma unroll
+    for (int q = 0; q < V; ++q) b[q] = lane_on ? __ldg(mrow + q) : uint8_t(0);
+  }
+  // the +-1 x-shift of the pull
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ex = ex3<Q>(a);
+    if (ex == 1) {
+      E in = shfl_up1<E>(v[a].last());
+      in = lane == 0 ? end_in[a] : in;
+      v[a].shift_up(in);
+    } else if (ex == -1) {
+      E keep = E(0);
+      if (east_edge) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) keep = (q == k_last) ? v[a].get(q) : keep;
+      }
+      E in = shfl_down1<E>(v[a].first());
+      in = (lane == 31 && !east_edge) ? end_in[a] : in;
+      v[a].shift_down(in);
+      if (east_edge) {
+        const E fix = east_out ? keep : end_in[a];
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+          if (q == k_last) v[a].set(q, fix);
+      }
+    }
+  }
+  bool any_lane = false;
+#pragma unroll
+  for (int q = 0; q < V; ++q) any_lane |= b[q] != 0;
+  const bool any_solid = __any_sync(0xffffffffu, any_lane);
+  const unsigned valid_bits =
+      east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u)) : (1u << V) - 1u;
+  unsigned bad_bits = 0u;
+  auto update = [&](T (&x)[Q], int q) -> T {
+    if (q == 0 && west_edge && west_inlet && lane == 0) {
+#pragma unroll
+      for (int a = 1; a < Q; ++a)
+        if (ex3<Q>(a) == 1) x[a] = C.ghost[a];
+    }
+    Macro3<T> m;
+    if (any_solid) {
+      T uo[3] = {T(0), T(0), T(0)};
+      const bool solid = b[q] != 0;
+      if (solid) body_velocity3<DEF>(D, b[q], xl + q, j, k, uo);
+      m = macro3<Q, T, SHIFT, true>(x, C, solid, uo);
+      collide3<Q, T, SHIFT, true>(x, m, C);
+      if (solid) {
+        T *fv = static_cast<T *>(D.fvp) + 3 * ((static_cast<size_t>(k) * ny + j) * pitch + xl + q);
+        fv[0] = m.f[0] * kUnscale;
+        fv[1] = m.f[1] * kUnscale;
+        fv[2] = m.f[2] * kUnscale;
+      }
+    } else {
+      const T uo[3] = {T(0), T(0), T(0)};
+      m = macro3<Q, T, SHIFT, false>(x, C, false, uo);
+      collide3<Q, T, SHIFT, false>(x, m, C);
+    }
+    bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
+    return m.d;
+  };
+  if constexpr (sizeof(E) == 2) {
+    const uint32_t sr_g = sr_group_bits(sr_row_key(n, row), xl);
+    if (Sweep3Shape<S>::kPaired && !any_solid) {
+      const Const3<F2> CP = pair_const3(D.pc);
+#pragma unroll
+      for (int q = 0; q < V; q += 2) {
+        F2 x[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) x[a] = F2(Cd::dec2(v[a].w[q >> 1]));
+        if (q == 0 && west_edge && west_inlet) {
+          const bool g = lane == 0;
+#pragma unroll
+          for (int a = 1; a < Q; ++a)
+            if (ex3<Q>(a) == 1) x[a].v.x = g ? C.ghost[a] : x[a].v.x;
+        }
+        const F2 uo[3] = {F2(0.f), F2(0.f), F2(0.f)};
+        const Macro3<F2> m = macro3<Q, F2, SHIFT, false>(x, CP, false, uo);
+        collide3<Q, F2, SHIFT, false>(x, m, CP);
+        bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
+        bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (q + 1);
+        uint32_t w[Q];
+        encode3_pair<Q, S>(x, m.d, sr_pair_bits(sr_g, xl + q), w);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) v[a].w[q >> 1] = w[a];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; q += 2) {
+        T x0v[Q], x1v[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          const float2 p = Cd::dec2(v[a].w[q >> 1]);
+          x0v[a] = p.x;
+          x1v[a] = p.y;
+        }
+        const float d0 = update(x0v, q);
+        const float d1 = update(x1v, q + 1);
+        F2 x[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) x[a] = F2(make_float2(x0v[a], x1v[a]));
+        uint32_t w[Q];
+        encode3_pair<Q, S>(x, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) v[a].w[q >> 1] = w[a];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      T x[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) x[a] = Cd::dec(v[a].get(q));
+      if constexpr (kAddShift) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) x[a] -= shift3(C, a);  // exact (Sterbenz)
+      }
+      update(x, q);
+      if constexpr (kAddShift) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) x[a] += shift3(C, a);
+      }
+#pragma unroll
+      for (int a = 0; a < Q; ++a) v[a].set(q, Cd::enc(x[a]));
+    }
+  }
+  if (bad_bits & valid_bits) unstable = 1;
+  if (east_edge) {
+#pragma unroll
+    for (int q = 0; q < V; ++q)
+      if (!((valid_bits >> q) & 1u)) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) v[a].set(q, E(0));
+      }
+  }
+  if (lane_on) {
+    const uint32_t off = (static_cast<uint32_t>(k) * ny + j) * static_cast<uint32_t>(pitch) + xl;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) v[a].store(static_cast<E *>(D.dst[a]) + off);
+  }
+}
+
+// The fused 3D sweep of one domain: a persistent grid whose warps each update one strip
+// (sweep3_strip) at a time.
+template <int Q, int S, int V, bool DEF, int P>
+__global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>::kMinBlocks)
+    sweep3_kernel(const __grid_constant__ Dom3 dom, long long n, int par) {
+  constexpr int kStrip = 32 * V;
+  const Dom3 &D = dom;  // kernel parameter: constants are read from the parameter bank
+  const int lane = threadIdx.x & 31;
+  const int strips = (D.nx + kStrip - 1) / kStrip;
+  const int items = D.ny * D.nz * strips;  // < 2^31: a direction holds < 2^31 elements
   int unstable = 0;
   // strips from the device counter (the last warp to finish resets it for the next
   // launch), or every (grid warps)-th strip
@@ -434,172 +608,7 @@ __global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>
       if (lane == 0) next = static_cast<int>(atomicAdd(&D.items[0], 1u));
     }
     const int row = item / strips;
-    const int x0 = (item - row * strips) * kStrip;
-    const int j = row % ny, k = row / ny;
-    const int xl = x0 + lane * V;
-    const bool lane_on = xl < nx;
-    const bool west_edge = x0 == 0, east_edge = x0 + kStrip >= nx;
-    const int col_l = west_edge ? (west_inlet ? 0 : nx - 1) : x0 - 1;
-    const int col_r = east_edge ? 0 : x0 + kStrip;
-    const int k_last = nx - 1 - xl;
-    const int xl_ld = min(xl, pitch - V);
-    Strip<S, V> v[Q];
-    E end_in[Q];
-    {
-      const RowOff3 R = row_off3(D, j, k);
-      for_dirs<Q, 0>([&](auto ac) {
-        constexpr int a = decltype(ac)::value;
-        const E *rp = src_row_ptr<Q, E, a>(D, R);
-        v[a].load(rp + xl_ld);
-        end_in[a] = E(0);
-        if constexpr (ex3<Q>(a) == 1) end_in[a] = __ldg(rp + col_l);
-        else if constexpr (ex3<Q>(a) == -1) end_in[a] = __ldg(rp + col_r);
-      });
-    }
-    uint8_t b[V];
-    {
-      const uint8_t *mrow = D.mask + (static_cast<size_t>(k) * ny + j) * pitch + xl_ld;
-#pragma unroll
-      for (int q = 0; q < V; ++q) b[q] = lane_on ? __ldg(mrow + q) : uint8_t(0);
-    }
-    // the +-1 x-shift of the pull
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int ex = ex3<Q>(a);
-      if (ex == 1) {
-        E in = shfl_up1<E>(v[a].last());
-        in = lane == 0 ? end_in[a] : in;
-        v[a].shift_up(in);
-      } else if (ex == -1) {
-        E keep = E(0);
-        if (east_edge) {
-#pragma unroll
-          for (int q = 0; q < V; ++q) keep = (q == k_last) ? v[a].get(q) : keep;
-        }
-        E in = shfl_down1<E>(v[a].first());
-        in = (lane == 31 && !east_edge) ? end_in[a] : in;
-        v[a].shift_down(in);
-        if (east_edge) {
-          const E fix = east_out ? keep : end_in[a];
-#pragma unroll
-          for (int q = 0; q < V; ++q)
-            if (q == k_last) v[a].set(q, fix);
-        }
-      }
-    }
-    bool any_lane = false;
-#pragma unroll
-    for (int q = 0; q < V; ++q) any_lane |= b[q] != 0;
-    const bool any_solid = __any_sync(0xffffffffu, any_lane);
-    const unsigned valid_bits =
-        east_edge ? (nx - xl >= V ? (1u << V) - 1u : (nx > xl ? (1u << (nx - xl)) - 1u : 0u)) : (1u << V) - 1u;
-    unsigned bad_bits = 0u;
-    auto update = [&](T (&x)[Q], int q) -> T {
-      if (q == 0 && west_edge && west_inlet && lane == 0) {
-#pragma unroll
-        for (int a = 1; a < Q; ++a)
-          if (ex3<Q>(a) == 1) x[a] = C.ghost[a];
-      }
-      Macro3<T> m;
-      if (any_solid) {
-        T uo[3] = {T(0), T(0), T(0)};
-        const bool solid = b[q] != 0;
-        if (solid) body_velocity3<DEF>(D, b[q], xl + q, j, k, uo);
-        m = macro3<Q, T, SHIFT, true>(x, C, solid, uo);
-        collide3<Q, T, SHIFT, true>(x, m, C);
-        if (solid) {
-          T *fv = static_cast<T *>(D.fvp) + 3 * ((static_cast<size_t>(k) * ny + j) * pitch + xl + q);
-          fv[0] = m.f[0] * kUnscale;
-          fv[1] = m.f[1] * kUnscale;
-          fv[2] = m.f[2] * kUnscale;
-        }
-      } else {
-        const T uo[3] = {T(0), T(0), T(0)};
-        m = macro3<Q, T, SHIFT, false>(x, C, false, uo);
-        collide3<Q, T, SHIFT, false>(x, m, C);
-      }
-      bad_bits |= (fabs(m.rho - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
-      return m.d;
-    };
-    if constexpr (sizeof(E) == 2) {
-      const uint32_t sr_g = sr_group_bits(sr_row_key(n, row), xl);
-      if (Sweep3Shape<S>::kPaired && !any_solid) {
-        const Const3<F2> CP = pair_const3(D.pc);
-#pragma unroll
-        for (int q = 0; q < V; q += 2) {
-          F2 x[Q];
-#pragma unroll
-          for (int a = 0; a < Q; ++a) x[a] = F2(Cd::dec2(v[a].w[q >> 1]));
-          if (q == 0 && west_edge && west_inlet) {
-            const bool g = lane == 0;
-#pragma unroll
-            for (int a = 1; a < Q; ++a)
-              if (ex3<Q>(a) == 1) x[a].v.x = g ? C.ghost[a] : x[a].v.x;
-          }
-          const F2 uo[3] = {F2(0.f), F2(0.f), F2(0.f)};
-          const Macro3<F2> m = macro3<Q, F2, SHIFT, false>(x, CP, false, uo);
-          collide3<Q, F2, SHIFT, false>(x, m, CP);
-          bad_bits |= (fabsf(m.rho.v.x - kRhoMid) < kRhoHalf ? 0u : 1u) << q;
-          bad_bits |= (fabsf(m.rho.v.y - kRhoMid) < kRhoHalf ? 0u : 1u) << (q + 1);
-          uint32_t w[Q];
-          encode3_pair<Q, S>(x, m.d, sr_pair_bits(sr_g, xl + q), w);
-#pragma unroll
-          for (int a = 0; a < Q; ++a) v[a].w[q >> 1] = w[a];
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < V; q += 2) {
-          T x0v[Q], x1v[Q];
-#pragma unroll
-          for (int a = 0; a < Q; ++a) {
-            const float2 p = Cd::dec2(v[a].w[q >> 1]);
-            x0v[a] = p.x;
-            x1v[a] = p.y;
-          }
-          const float d0 = update(x0v, q);
-          const float d1 = update(x1v, q + 1);
-          F2 x[Q];
-#pragma unroll
-          for (int a = 0; a < Q; ++a) x[a] = F2(make_float2(x0v[a], x1v[a]));
-          uint32_t w[Q];
-          encode3_pair<Q, S>(x, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + q), w);
-#pragma unroll
-          for (int a = 0; a < Q; ++a) v[a].w[q >> 1] = w[a];
-        }
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        T x[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) x[a] = Cd::dec(v[a].get(q));
-        if constexpr (kAddShift) {
-#pragma unroll
-          for (int a = 0; a < Q; ++a) x[a] -= shift3(C, a);  // exact (Sterbenz)
-        }
-        update(x, q);
-        if constexpr (kAddShift) {
-#pragma unroll
-          for (int a = 0; a < Q; ++a) x[a] += shift3(C, a);
-        }
-#pragma unroll
-        for (int a = 0; a < Q; ++a) v[a].set(q, Cd::enc(x[a]));
-      }
-    }
-    if (bad_bits & valid_bits) unstable = 1;
-    if (east_edge) {
-#pragma unroll
-      for (int q = 0; q < V; ++q)
-        if (!((valid_bits >> q) & 1u)) {
-#pragma unroll
-          for (int a = 0; a < Q; ++a) v[a].set(q, E(0));
-        }
-    }
-    if (lane_on) {
-      const uint32_t off = (static_cast<uint32_t>(k) * ny + j) * static_cast<uint32_t>(pitch) + xl;
-#pragma unroll
-      for (int a = 0; a < Q; ++a) v[a].store(static_cast<E *>(D.dst[a]) + off);
-    }
+    sweep3_strip<Q, S, V, DEF>(D, row, (item - row * strips) * kStrip, n, lane, unstable);
     item = kDyn ? __shfl_sync(0xffffffffu, next, 0) : next;
   }
   if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(D.status, 1);
@@ -612,6 +621,56 @@ __global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>
   }
 }
 
+// ---- batches of 3D domains (lbm3_batch_*) ----------------------------------------------
+
+constexpr int kGroup3 = 16;  // domains per batched launch (their parameters in the kernel's)
+
+// One step of up to kGroup3 domains in one launch. Each domain's parameters (for the
+// lattice it reads at this step) and step index travel in the kernel parameter bank, as
+// the single-domain sweep's do; domain d owns items base[d] .. base[d + 1] - 1, one strip
+// each, rows in order.
+struct Batch3Args {
+  Dom3 dom[kGroup3];
+  long long n[kGroup3];
+  int32_t base[kGroup3 + 1];
+  uint32_t *ctr;  // [2]: next item, finished warps (reset by the last)
+  int32_t ndom;
+};
+
+// The batched sweep: warps take strips of every listed domain from one device counter.
+// Fixed geometry only (no moving, coupled or pulsating bodies).
+template <int Q, int S, int V, int P>
+__global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>::kMinBlocks)
+    sweep3_batch_kernel(const __grid_constant__ Batch3Args args) {
+  constexpr int kStrip = 32 * V;
+  const int lane = threadIdx.x & 31;
+  const int total = args.base[args.ndom];
+  int item = 0;
+  if (lane == 0) item = static_cast<int>(atomicAdd(&args.ctr[0], 1u));
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item < total) {
+    int next = 0;
+    if (lane == 0) next = static_cast<int>(atomicAdd(&args.ctr[0], 1u));
+    int d = 0;  // the listed domain owning the item (uniform over the warp)
+    while (d + 1 < args.ndom && args.base[d + 1] <= item) ++d;
+    const Dom3 &D = args.dom[d];
+    const int strips = (D.nx + kStrip - 1) / kStrip;
+    const int local = item - args.base[d];
+    const int row = local / strips;
+    int unstable = 0;
+    sweep3_strip<Q, S, V, false>(D, row, (local - row * strips) * kStrip, args.n[d], lane, unstable);
+    if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(D.status, 1);
+    item = __shfl_sync(0xffffffffu, next, 0);
+  }
+  if (lane == 0) {
+    __threadfence();  // this warp's last fetch is ordered before its count
+    if (atomicAdd(&args.ctr[1], 1u) == gridDim.x * (blockDim.x >> 5) - 1u) {
+      args.ctr[0] = 0u;
+      args.ctr[1] = 0u;
+    }
+  }
+}
+
 // Launch the sweep of one storage (lbm3d_sweep_<storage>.cu): pipeline 0, 3 or 4 (3 and 4
 // for 16-bit storage only), grid blocks of Sweep3Shape<S, P>::kThreads threads.
 // sweep3_fits gives the resident blocks per SM of that shape (0: not compiled or cannot
@@ -619,7 +678,10 @@ __global__ void __launch_bounds__(Sweep3Shape<S, P>::kThreads, Sweep3Shape<S, P>
 #define LBM3_SWEEP_DECL(NAME)                                                                   \
   cudaError_t launch_sweep3_##NAME(int q, int pipe, bool deform, int grid, cudaStream_t st,     \
                                    const Dom3 &dom, long long n, int par);                      \
-  int sweep3_fits_##NAME(int q, int pipe);
+  int sweep3_fits_##NAME(int q, int pipe);                                                      \
+  cudaError_t launch_sweep3b_##NAME(int q, int pipe, int grid, cudaStream_t st,                 \
+                                    const Batch3Args &args);                                    \
+  int sweep3b_fits_##NAME(int q, int pipe);
 LBM3_SWEEP_DECL(f64)
 LBM3_SWEEP_DECL(f32)
 LBM3_SWEEP_DECL(f16s)
@@ -646,6 +708,28 @@ template <int S, int P> int sweep3_fits_sp(int q) {
   const cudaError_t e = q == 15
       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep3_kernel<15, S, Sh::kV, false, P>, Sh::kThreads, 0)
       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep3_kernel<19, S, Sh::kV, false, P>, Sh::kThreads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+// The batched launcher and its occupancy query (blocks per SM) for storage S, pipeline P.
+template <int S, int P>
+cudaError_t launch_sweep3b_sp(int q, int grid, cudaStream_t st, const Batch3Args &args) {
+  using Sh = Sweep3Shape<S, P>;
+  if (q == 15) sweep3_batch_kernel<15, S, Sh::kV, P><<<grid, Sh::kThreads, 0, st>>>(args);
+  else sweep3_batch_kernel<19, S, Sh::kV, P><<<grid, Sh::kThreads, 0, st>>>(args);
+  return cudaGetLastError();
+}
+
+template <int S, int P> int sweep3b_fits_sp(int q) {
+  using Sh = Sweep3Shape<S, P>;
+  int nb = 0;
+  const cudaError_t e = q == 15
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep3_batch_kernel<15, S, Sh::kV, P>, Sh::kThreads, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep3_batch_kernel<19, S, Sh::kV, P>, Sh::kThreads, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -1,5 +1,6 @@
-// The 3D sweep (lbm3d.cuh) instantiated for FP64 storage: D3Q19 and D3Q15, rigid and
-// pulsating bodies, one register budget (pipeline 0).
+// The 3D sweep (lbm3d.cuh) instantiated for FP64 storage: the single-domain sweep
+// (D3Q19 and D3Q15, rigid and pulsating bodies) and the batched sweep of fixed-geometry
+// domains, one register budget (pipeline 0).
 #include "lbm3d.cuh"
 
 namespace lbm {
@@ -12,6 +13,13 @@ cudaError_t launch_sweep3_f64(int q, int pipe, bool deform, int grid, cudaStream
 }
 
 int sweep3_fits_f64(int q, int pipe) { return pipe == 0 ? sweep3_fits_sp<LBM_F64, 0>(q) : 0; }
+
+cudaError_t launch_sweep3b_f64(int q, int pipe, int grid, cudaStream_t st, const Batch3Args &args) {
+  if (pipe != 0) return cudaErrorInvalidValue;
+  return launch_sweep3b_sp<LBM_F64, 0>(q, grid, st, args);
+}
+
+int sweep3b_fits_f64(int q, int pipe) { return pipe == 0 ? sweep3b_fits_sp<LBM_F64, 0>(q) : 0; }
 
 }  // namespace d3
 }  // namespace lbm

@@ -203,3 +203,33 @@ def test_3d_no_cpu_fallback(lib):
     st = L.lbm3_domain_create(C.byref(p), shapes, ns, bodies, nb, None, _native.ALLOC_FN(),
                               _native.FREE_FN(), None, C.byref(h))
     assert st == 3 and h.value is None
+
+
+@pytest.mark.parametrize("args", [
+    (0, 0, 2, 19),      # no slots
+    (5000, 0, 2, 19),   # too many slots
+    (4, 0, 9, 19),      # unknown storage
+    (4, 0, 2, 17),      # unknown lattice
+])
+def test_3d_batch_arguments_rejected_before_cuda(lib, args):
+    from paper_1901_08766_gb300 import _native
+    L = lib.load()
+    h = C.c_void_p()
+    st = L.lbm3_batch_create(*args, None, _native.ALLOC_FN(), _native.FREE_FN(), None, C.byref(h))
+    assert st == 1 and h.value is None
+    # NULL handles are rejected, destroy(NULL) is a no-op
+    n = C.c_int64()
+    assert L.lbm3_batch_run(None, 1, C.byref(n)) == 1
+    assert L.lbm3_batch_evict(None, 0) == 1
+    assert L.lbm3_batch_destroy(None) == 0
+
+
+def test_3d_batch_no_cpu_fallback(lib):
+    import torch
+    from paper_1901_08766_gb300 import _native
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = lib.load()
+    h = C.c_void_p()
+    st = L.lbm3_batch_create(4, 0, 2, 19, None, _native.ALLOC_FN(), _native.FREE_FN(), None, C.byref(h))
+    assert st == 3 and h.value is None
