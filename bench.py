@@ -999,6 +999,7 @@ def sphere3d(lbm, torch, np, only=None, lattice=19):
                      "peak_source": peak[1]})
     if only:
         return {"perf": perf, "case_perf": "sphere channel 384x128x128, D=32, Re=100"}
+    batched = batch3_perf(lbm, torch)
     cpu = [cpu_baseline3(q) for q in (19, 15)]
     acc = []
     spec = synth.sphere_channel(192, 64, 64, D=16.0, re=100.0, steps=4000)
@@ -1018,8 +1019,52 @@ def sphere3d(lbm, torch, np, only=None, lattice=19):
         for r in rows:
             r["cd_rel_vs_f64"] = (r["cd_last_1000"] - ref) / ref
         acc += rows
-    return {"perf": perf, "drag": acc, "cpu_baseline": cpu,
+    return {"perf": perf, "batched": batched, "drag": acc, "cpu_baseline": cpu,
             "case_perf": "sphere channel 384x128x128, D=32, Re=100", "case_drag": spec["name"]}
+
+
+def batch3_perf(lbm, torch, steps=60):
+    """Eight uneven sphere channels (nx 96..320, ny 48..64, nz 48, D = 12) stepped as one
+    3D batch against one domain at a time, µs per step of all eight (sweeps and force
+    reductions, CUDA events on one stream, after 5 warm-up steps)."""
+    import synth
+    st = torch.cuda.Stream()
+
+    def per_step(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            fn(5)
+            torch.cuda.synchronize()
+            e0.record(st)
+            fn(steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+        return 1000.0 * e0.elapsed_time(e1) / steps
+
+    rows = []
+    for storage, q in (("f16s", 19), ("f16s", 15), ("f32", 19)):
+        specs = [dict(synth.sphere_channel(96 + 32 * i, 48 + 8 * (i % 3), 48, D=12.0), lattice=q) for i in range(8)]
+        nodes = sum(s["nx"] * s["ny"] * s["nz"] for s in specs)
+        with torch.cuda.stream(st):
+            doms = [lbm.Domain3(s, storage=storage, force_capacity=4096, stream=st) for s in specs]
+
+        def alone(n):
+            for d in doms:
+                d.step(n)
+        us_alone = per_step(alone)
+        for d in doms:
+            d.close()
+        with torch.cuda.stream(st):
+            b = lbm.Batch3(storage, lattice=q, max_domains=len(specs), stream=st)
+            slots = [b.admit(s, nsteps=10 ** 6, force_capacity=4096) for s in specs]
+        us_batch = per_step(lambda n: b.run(n))
+        for k in slots:
+            b.poll(k)
+        b.close()
+        rows.append({"lattice": f"D3Q{q}", "storage": storage, "domains": len(specs), "nodes": nodes,
+                     "us_per_step_batched": us_batch, "us_per_step_one_at_a_time": us_alone,
+                     "glups_batched": nodes / us_batch / 1e3, "glups_one_at_a_time": nodes / us_alone / 1e3})
+    return rows
 
 
 def cpu_baseline3(q, seconds=8.0):
