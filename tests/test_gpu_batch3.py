@@ -178,3 +178,39 @@ def _bytes_args(spec, storage):
     from paper_1901_08766_gb300 import _native
     p = _native.params3_from_spec(spec, storage, 1, 16)
     return C.byref(p), len(spec["bodies"])
+
+
+def test_batch3_two_groups_and_a_domain_without_bodies(lbm):
+    # 19 domains: two launch groups per step (16 + 3, then fewer as domains finish); one
+    # domain has no bodies, one a body without solid nodes
+    q, storage = 15, "f16s"
+    specs = []
+    for i in range(17):
+        c = (10.5 + i % 5, 8.25, 6.5)
+        specs.append(synth.spec3(f"g{i}", 24 + 4 * (i % 6), 16 + (i % 3), 12 + (i % 4), 0.05,
+                                 [synth.sphere(1, c, 2.5 + 0.2 * (i % 3))], [synth.body3(c, 5.0)], 0, 0.02,
+                                 synth.channel_edges3(), u_in=(0.02, 0.0, 0.0), u0=(0.02, 0.0, 0.0), lattice=q))
+    specs.append(synth.spec3("nobody", 40, 12, 10, 0.05, [], [], 0, 0.02, synth.channel_edges3(),
+                             u_in=(0.02, 0.0, 0.0), u0=(0.02, 0.0, 0.0), lattice=q))
+    far = (200.0, 6.0, 5.0)  # a body whose sphere lies outside the grid: zero force entries
+    specs.append(synth.spec3("nosolid", 36, 12, 10, 0.05, [synth.sphere(1, far, 3.0)], [synth.body3(far, 6.0)],
+                             0, 0.02, synth.channel_edges3(), u_in=(0.02, 0.0, 0.0), u0=(0.02, 0.0, 0.0),
+                             lattice=q))
+    targets = [20 + 3 * (i % 7) for i in range(len(specs))]
+    raws = [_pops(sp, storage, 50 + i) for i, sp in enumerate(specs)]
+    b = lbm.Batch3(storage, lattice=q, max_domains=len(specs))
+    slots = [b.admit(sp, nsteps=n, force_capacity=64) for sp, n in zip(specs, targets)]
+    for k, raw in zip(slots, raws):
+        b.domain(k).set_populations(raw)
+    while b.run(10):
+        pass
+    got = []
+    for k in slots:
+        f, done = b.poll(k)
+        assert done
+        got.append((b.domain(k).get_populations().view(np.uint8).copy(), f))
+    b.close()
+    for sp, raw, n, (pops, f) in zip(specs, raws, targets, got):
+        ref_pops, ref_f = _alone(lbm, sp, storage, raw, n)
+        assert np.array_equal(pops, ref_pops), sp["name"]
+        assert np.array_equal(f, ref_f), sp["name"]
