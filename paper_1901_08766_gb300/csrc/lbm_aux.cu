@@ -184,15 +184,6 @@ __device__ __forceinline__ ShapeDev shape_at(const DomDev &D, const ShapeDev &s0
   return s;
 }
 
-// Largest distance of a shape's node from its reference point: the radius of a circle;
-// for a NACA section (reference at the quarter chord) 3/4 of the chord along it plus the
-// largest half thickness across it, 5 |t| c max(poly) < 5 |t| c (0.2969 + 0.2843) < 3 |t| c,
-// and never less than the chord.
-__host__ __device__ __forceinline__ double shape_extent(const ShapeDev &s) {
-  if (s.kind == LBM_SHAPE_CIRCLE) return s.radius;
-  return fmax(s.chord, 0.75 * s.chord + 3.0 * fabs(s.thickness) * s.chord);
-}
-
 __device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int x0, int j, int &lo, int &hi) {
   lo = 0;
   hi = nx - 1;
@@ -211,17 +202,24 @@ __device__ __forceinline__ void shape_cols(const ShapeDev &s, int nx, int x0, in
   hi = min(nx - 1, static_cast<int>(dhi));
 }
 
+// A shape placed for one row: its geometry, column interval, and the FP32 copies the
+// circle pre-test of inside_row uses (converted once per row, not per node: the
+// conversions and FP64 compares ran on the FP64 pipe, the move kernel's bottleneck).
 struct RowShape {
   ShapeDev s;
   int lo, hi;
+  float fcx, fcy, fr2;  // centre and squared radius in FP32
+  int fast;             // a circle within the pre-test's bounds
 };
 
 // The column interval of shape s0 at index n in row j from FP32 positions with a margin
 // of 2 cells: conservative (it contains every node within the shape's reach) while
 // positions stay below 10^6 cells and n below 2^24, where the FP32 position error is
 // below 0.15 cell. Rows far from every shape thereby cost no FP64 work.
-__device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &s0, long long n, int j,
+__device__ __forceinline__ void shape_cols_f32(const DomDev &D, int k, long long n, float fn, int j,
                                                int &lo, int &hi) {
+  const ShapeDev &s0 = D.shapes[k];
+  const float4 f = D.shapes_f[k];  // FP32 centre and extent (no FP64 conversions here)
   lo = 0;
   hi = D.nx - 1;
   if (s0.kind == LBM_SHAPE_ANNULUS_OUTSIDE) return;
@@ -235,23 +233,21 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
     // centre and (1 + |a|) times its size: cull about the centre with the reach grown by
     // both (no trigonometry here)
     const int b = s0.body - 1;
-    const float fn = float(n);
     cx = (float(D.centre0[2 * b]) - float(D.x0)) + float(D.bodies[5 * b + 2]) * fn;
     cy = float(D.centre0[2 * b + 1]) + float(D.bodies[5 * b + 3]) * fn;
     const float ox = float(s0.cx - D.centre0[2 * b]), oy = float(s0.cy - D.centre0[2 * b + 1]);
     const float grow = deforms(D, s0.body) ? fabsf(float(D.dpar[2 * b])) : 0.f;
-    turn = (1.0f + grow) * sqrtf(ox * ox + oy * oy) + grow * float(shape_extent(s0)) + 0.01f;
+    turn = (1.0f + grow) * sqrtf(ox * ox + oy * oy) + grow * f.z + 0.01f;
   } else {
     float vx = 0.f, vy = 0.f;
-    if (s0.body >= 1 && s0.body <= D.nbodies) {
-      vx = float(D.bodies[5 * (s0.body - 1) + 2]);
-      vy = float(D.bodies[5 * (s0.body - 1) + 3]);
+    if (s0.body >= 1 && s0.body <= D.nbodies) {  // the FP32 copy of the body table
+      vx = D.bodies_f[5 * (s0.body - 1) + 2];
+      vy = D.bodies_f[5 * (s0.body - 1) + 3];
     }
-    const float fn = float(n);
-    cx = (float(s0.cx) - float(D.x0)) + vx * fn;
-    cy = float(s0.cy) + vy * fn;
+    cx = (f.x - float(D.x0)) + vx * fn;
+    cy = f.y + vy * fn;
   }
-  const float reach = float(shape_extent(s0)) + 2.0f + turn;
+  const float reach = f.z + 2.0f + turn;
   if (!(fabsf(float(j) - cy) <= reach)) {
     lo = 1;
     hi = 0;
@@ -263,19 +259,28 @@ __device__ __forceinline__ void shape_cols_f32(const DomDev &D, const ShapeDev &
   hi = min(D.nx - 1, static_cast<int>(fhi));
 }
 
+// The FP32 copies of a row shape's geometry (after r.s is set).
+__device__ __forceinline__ void prep_row_shape(RowShape &r) {
+  const ShapeDev &s = r.s;
+  r.fast = s.kind == LBM_SHAPE_CIRCLE && fabs(s.cx) < 4096.0 && fabs(s.cy) < 4096.0 && s.radius < 100.0;
+  r.fcx = float(s.cx);
+  r.fcy = float(s.cy);
+  r.fr2 = float(s.radius) * float(s.radius);
+}
+
 // inside() with an FP32 pre-test for circles: a node whose FP32 squared distance is
 // farther than 0.5 from r^2 is decided there, the others take the exact FP64 predicate.
 // With centres below 4096 in magnitude (FP32 position error <= 1.2e-4) and radii below
 // 100 (|dx|, |dy| <= r + 2 in the column interval), the FP32 error of d^2 is below
 // 2 (|dx| + |dy|) 1.2e-4 + 3 d^2 2^-24 < 0.06, so the FP32 decision is the exact one.
-__device__ __forceinline__ bool inside_fast(const ShapeDev &s, int i, int j) {
-  if (s.kind == LBM_SHAPE_CIRCLE && fabs(s.cx) < 4096.0 && fabs(s.cy) < 4096.0 && s.radius < 100.0) {
-    const float dx = float(i) - float(s.cx), dy = float(j) - float(s.cy);
-    const float d2 = dx * dx + dy * dy, r2 = float(s.radius) * float(s.radius);
-    if (d2 < r2 - 0.5f) return true;
-    if (d2 > r2 + 0.5f) return false;
+__device__ __forceinline__ bool inside_row(const RowShape &r, int i, int j) {
+  if (r.fast) {
+    const float dx = float(i) - r.fcx, dy = float(j) - r.fcy;
+    const float d2 = dx * dx + dy * dy;
+    if (d2 < r.fr2 - 0.5f) return true;
+    if (d2 > r.fr2 + 0.5f) return false;
   }
-  return inside(s, double(i), double(j));
+  return inside(r.s, double(i), double(j));
 }
 
 // Body ids of row j over columns [c0, c1] at the geometry held in rs (warp-wide).
@@ -285,7 +290,7 @@ __device__ void write_ids(const DomDev &D, int j, int c0, int c1, int lane, cons
     uint8_t id = 0;
     if (i < D.nx)
       for (int k = 0; k < D.nshapes; ++k)
-        if (i >= rs[k].lo && i <= rs[k].hi && inside_fast(rs[k].s, i + D.x0, j))
+        if (i >= rs[k].lo && i <= rs[k].hi && inside_row(rs[k], i + D.x0, j))
           id = static_cast<uint8_t>(rs[k].s.body);
     row[i] = id;
   }
@@ -295,6 +300,7 @@ __device__ void write_ids(const DomDev &D, int j, int c0, int c1, int lane, cons
 __device__ void place_row(const DomDev &D, int j, long long n, int lane, RowShape *rs) {
   for (int k = lane; k < D.nshapes; k += 32) {
     rs[k].s = shape_at(D, D.shapes[k], n);
+    prep_row_shape(rs[k]);
     shape_cols(rs[k].s, D.nx, D.x0, j, rs[k].lo, rs[k].hi);
   }
   __syncwarp();
@@ -355,13 +361,14 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
       if (n < dy.step_end) {
         const bool fsi = D.fsi_on != 0;
+        const float fn0 = float(n), fn1 = float(n + 1);
         olo = D.nx; ohi = -1; nlo = D.nx; nhi = -1;
         for (int k = 0; k < D.nshapes; ++k) {
           int lo, hi;
-          shape_cols_f32(D, D.shapes[k], n, mr.j, lo, hi);
+          shape_cols_f32(D, k, n, fn0, mr.j, lo, hi);
           if (lo <= hi) { olo = min(olo, lo); ohi = max(ohi, hi); }
           if (fsi) continue;
-          shape_cols_f32(D, D.shapes[k], n + 1, mr.j, lo, hi);
+          shape_cols_f32(D, k, n + 1, fn1, mr.j, lo, hi);
           if (lo <= hi) { nlo = min(nlo, lo); nhi = max(nhi, hi); }
         }
         // row 0 also moves the body centres (domains without coupled bodies)
@@ -421,8 +428,11 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       const int c0 = min(jolo, jnlo), c1 = max(johi, jnhi);
       if (c0 <= c1) {
         for (int k = lane; k < D.nshapes; k += 32) {
-          shape_cols_f32(D, D.shapes[k], n + 1, j, rs[k].lo, rs[k].hi);
-          if (rs[k].lo <= rs[k].hi) rs[k].s = shape_at(D, D.shapes[k], n + 1, true);
+          shape_cols_f32(D, k, n + 1, float(n + 1), j, rs[k].lo, rs[k].hi);
+          if (rs[k].lo <= rs[k].hi) {
+            rs[k].s = shape_at(D, D.shapes[k], n + 1, true);
+            prep_row_shape(rs[k]);
+          }
         }
         __syncwarp();
         write_ids(D, j, c0, c1, lane, rs);
@@ -510,6 +520,7 @@ fsi_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Cou
       if (lo <= hi) { c0 = min(c0, lo); c1 = max(c1, hi); }
       rs[k].s = coupled(D, s0.body) ? shape_about(D, s0, cen[warp][s0.body - 1][0], cen[warp][s0.body - 1][1])
                                     : shape_at(D, s0, n + 1);
+      prep_row_shape(rs[k]);
       shape_cols(rs[k].s, D.nx, D.x0, j, rs[k].lo, rs[k].hi);
       if (rs[k].lo <= rs[k].hi) { c0 = min(c0, rs[k].lo); c1 = max(c1, rs[k].hi); }
     }

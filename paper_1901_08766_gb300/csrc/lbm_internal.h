@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cmath>
 
 #include <cuda_runtime.h>
 
@@ -60,6 +61,7 @@ struct DomDev {
   CellConst<double> cd;     // collision constants for FP64 compute
   // moving domains (prescribed translation; null / 0 otherwise)
   const ShapeDev *shapes;   // [nshapes] reference geometry (step index 0)
+  const float4 *shapes_f;   // [nshapes] FP32 centre x, y and extent (shape_extent) of each
   const double *centre0;    // [nbodies][2] reference centres
   double *rowsum;           // [ny][nbodies][3] per-row sums of -F_VP and the step they belong to
   int32_t nshapes, moving;
@@ -139,6 +141,15 @@ struct ShapeDev {
   int32_t kind, body;
   double cx, cy, radius, chord, thickness, ca, sa;  // ca, sa = cos/sin(aoa) from the host
 };
+
+// Largest distance of a shape's node from its reference point: the radius of a circle;
+// for a NACA section (reference at the quarter chord) 3/4 of the chord along it plus the
+// largest half thickness across it, 5 |t| c max(poly) < 5 |t| c (0.2969 + 0.2843) < 3 |t| c,
+// and never less than the chord.
+__host__ __device__ inline double shape_extent(const ShapeDev &s) {
+  if (s.kind == LBM_SHAPE_CIRCLE) return s.radius;
+  return fmax(s.chord, 0.75 * s.chord + 3.0 * fabs(s.thickness) * s.chord);
+}
 
 // One domain of a batched admission (lbm_batch_admit_many): where its mask, lattices and
 // solid-node list live, its geometry, and the position of its rows in the flat row list

@@ -122,7 +122,8 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   // moving domains: reference geometry, reference centres, per-row force sums
   L.shapes_off = L.centre0_off = L.rowsum_off = L.fsi_off = L.def_off = o;
   if (p.moving) {
-    o += align_up(sizeof(ShapeDev) * kMaxMovingShapes, 256);
+    // the shapes, then their FP32 centre and extent (the move kernel's culling)
+    o += align_up((sizeof(ShapeDev) + sizeof(float4)) * kMaxMovingShapes, 256);
     L.centre0_off = o;
     o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
     L.rowsum_off = o;
@@ -635,6 +636,8 @@ lbm_status prepare_slot(lbm_batch *b, const lbm_params *p, const lbm_geometry *g
   D.x0 = p->x_origin;
   D.nshapes = p->moving ? geom->nshapes : 0;
   D.shapes = p->moving ? reinterpret_cast<const ShapeDev *>(base + L.shapes_off) : nullptr;
+  D.shapes_f = p->moving ? reinterpret_cast<const float4 *>(base + L.shapes_off + sizeof(ShapeDev) * kMaxMovingShapes)
+                         : nullptr;
   D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
   D.rowsum = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
   D.fsi = p->moving ? reinterpret_cast<double *>(base + L.fsi_off) : nullptr;
@@ -758,6 +761,14 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     ShapeDev *dsh = p->moving ? const_cast<ShapeDev *>(D.shapes)
                               : reinterpret_cast<ShapeDev *>(static_cast<char *>(tmp) + counts_bytes + offs_bytes);
     ADM_CUDA(cudaMemcpyAsync(dsh, shapes.data(), sizeof(ShapeDev) * ns, cudaMemcpyHostToDevice, st));
+    std::vector<float4> shapes_f;
+    if (p->moving) {
+      for (const ShapeDev &d : shapes)
+        shapes_f.push_back(make_float4(static_cast<float>(d.cx), static_cast<float>(d.cy),
+                                       static_cast<float>(shape_extent(d)), 0.f));
+      ADM_CUDA(cudaMemcpyAsync(const_cast<float4 *>(D.shapes_f), shapes_f.data(), sizeof(float4) * ns,
+                               cudaMemcpyHostToDevice, st));
+    }
     // a moving domain is placed at its step index below, once its body table is resident
     if (!p->moving) ADM_CUDA(launch_rasterize(st, mask, p->nx, p->ny, s.pitch, dsh, ns, p->x_origin));
   }
