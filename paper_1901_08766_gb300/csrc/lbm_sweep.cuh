@@ -361,7 +361,7 @@ __device__ __forceinline__ void update_strip(Strip<S, V> (&v)[kQ], const uint32_
 #pragma unroll
         for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = enc.w[a];
       }
-    } else {
+    } else if constexpr (S == LBM_F16S) {
       // strips with solid nodes: out of line (solid_strip16)
       uint32_t wl[kQ * (V / 2)];
 #pragma unroll
@@ -374,6 +374,27 @@ __device__ __forceinline__ void update_strip(Strip<S, V> (&v)[kQ], const uint32_
       for (int a = 0; a < kQ; ++a)
 #pragma unroll
         for (int q = 0; q < V / 2; ++q) v[a].w[q] = wl[a * (V / 2) + q];
+    } else {
+      // BF16-shifted: inline (its force-free path spilled more with the call: 377 -> 383 us)
+#pragma unroll
+      for (int k = 0; k < V; k += 2) {
+        T x0[kQ], x1[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+          const float2 p = Cd::dec2(v[a].w[k >> 1]);
+          x0[a] = p.x;
+          x1[a] = p.y;
+        }
+        const float d0 = update(x0, k);
+        const float d1 = update(x1, k + 1);
+        F2 xp[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) xp[a] = F2(make_float2(x0[a], x1[a]));
+        uint32_t w[kQ];
+        encode_pair_mass_kept<S>(xp, F2(make_float2(d0, d1)), sr_pair_bits(sr_g, xl + k + D.x0), w);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) v[a].w[k >> 1] = w[a];
+      }
     }
   } else {
 #pragma unroll
