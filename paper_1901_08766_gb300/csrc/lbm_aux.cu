@@ -349,7 +349,9 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
   const int nrows = ctr->nmove;
   const long long run_base = ctr->run_base;
   const int stride = gridDim.x * kMoveWarps;
-  for (int base = blockIdx.x * kMoveWarps + warp; base < nrows; base += 32 * stride) {
+  // consecutive items (the consecutive rows a body crosses) go to warps of different
+  // blocks, so the busy rows spread over the SMs instead of filling one block's warps
+  for (int base = warp * static_cast<int>(gridDim.x) + blockIdx.x; base < nrows; base += 32 * stride) {
     // lane l: item base + l * stride
     const int ql = base + lane * stride;
     int olo = 1, ohi = 0, nlo = 1, nhi = 0;
@@ -473,7 +475,8 @@ fsi_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Cou
   RowShape *rs = shapes[warp];
   const int nrows = ctr->nmove;
   const long long run_base = ctr->run_base;
-  for (int q = blockIdx.x * kMoveWarps + warp; q < nrows; q += gridDim.x * kMoveWarps) {
+  // consecutive rows to warps of different blocks (as in move_kernel)
+  for (int q = warp * static_cast<int>(gridDim.x) + blockIdx.x; q < nrows; q += gridDim.x * kMoveWarps) {
     const MoveRow mr = rows[q];
     const DomDev &D = doms[mr.dom];
     if (!D.fsi_on) continue;
