@@ -340,6 +340,8 @@ lbm_status set_config(lbm_batch *b, int vec, int warps, int rows, int pipe) {
   if (pipe < 0 || pipe > 4)
     return fail(LBM_EINVAL, "pipeline must be 0 (direct), 1 (TMA-staged), 2 (register-prefetched), "
                             "3 or 4 (direct for 20 or 24 resident warps)");
+  if (vec == b->vec && warps == b->warps && rows == b->rows && pipe == b->pipe && b->grid_sweep > 0)
+    return LBM_OK;  // unchanged: the work lists and the captured graph stay valid
   const int occ = sweep_occupancy(b->storage, vec, pipe, warps);
   if (occ <= 0) return fail(LBM_ECUDA, "sweep kernel cannot run with %d warps per block", warps);
   b->vec = vec;
