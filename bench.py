@@ -505,8 +505,10 @@ def measure_e2e(lbm, torch, specs, args):
 
 
 def _e2e_job(lbm, torch, specs, args, stream):
+    import gc
     steps = args.steps
     marks = []
+    gc.collect()  # garbage of the earlier measurements collected before the clock starts
     with torch.cuda.stream(stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
