@@ -163,3 +163,55 @@ def test_full_size_batch_one_step_sampled_parity(lbm):
         f_gpu, _ = batch.poll(slots[d])
         assert np.allclose(f_gpu, f_ora, rtol=1e-4, atol=1e-5)
     batch.close()
+
+
+def test_randomised_membership_tiles_and_graphs_equal_alone(lbm):
+    # domains admitted and evicted at random chunk boundaries while the tile shape and
+    # register budget change (and sometimes are set to the current one again), graphs of
+    # 8 steps replayed: each domain's populations and force series equal its run alone
+    rng = np.random.default_rng(190108766)
+    base = [synth.parity_case(n) for n in ("channel_97x61", "periodic_97x61", "mixed_edges_61x47")]
+    tiles = [(8, 12, 4, 4), (8, 6, 4, 4), (8, 10, 2, 3), (4, 8, 1, 0), (8, 16, 4, 0), (8, 8, 2, 1)]
+    b = lbm.Batch("f16s", max_domains=5, graph_steps=8)
+    live, done, specs, raws, forces = {}, {}, {}, {}, {}
+    admitted = 0
+    tile = tiles[0]
+    b.set_tile(*tile)
+    for chunk in range(40):
+        if admitted < 9 and len(live) < 5 and rng.random() < 0.6:
+            sp = dict(base[admitted % 3], name=f"r{admitted}")
+            n = int(rng.integers(20, 90))
+            raw = codec.encode(synth.random_populations(300 + admitted, sp["nx"], sp["ny"], 0.05), "f16s")
+            k = b.admit(sp, nsteps=n)
+            b.set_populations(k, raw)
+            live[k] = admitted
+            specs[admitted], raws[admitted], forces[admitted] = (sp, n), raw, []
+            admitted += 1
+        if rng.random() < 0.3:
+            tile = tiles[int(rng.integers(len(tiles)))] if rng.random() < 0.7 else tile
+            b.set_tile(*tile)
+        b.run(int(rng.integers(3, 20)))
+        for k in list(live):
+            f, fin = b.poll(k)
+            forces[live[k]].append(f)
+            if fin:
+                done[live[k]] = b.get_populations(k).view(np.uint16).copy()
+                b.evict(k)
+                del live[k]
+    while b.run(50):
+        pass
+    for k in list(live):
+        f, fin = b.poll(k)
+        assert fin
+        forces[live[k]].append(f)
+        done[live[k]] = b.get_populations(k).view(np.uint16).copy()
+    b.close()
+    assert len(done) == admitted >= 5
+    for r, pops in done.items():
+        sp, n = specs[r]
+        d = lbm.Domain(sp, storage="f16s")
+        d.set_populations(raws[r])
+        f = d.run(n)
+        assert np.array_equal(d.get_populations().view(np.uint16), pops), sp["name"]
+        assert np.array_equal(np.concatenate(forces[r]), f), sp["name"]
+        d.close()
