@@ -397,7 +397,9 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
         // -F_VP of each body over the row's solid nodes (all inside the old interval),
         // with the step index as a tag: the force kernel adds only the entries of its
         // step, so rows (or bodies) without solid nodes here need no entry
-        const T *fv = static_cast<const T *>(D.fvp) + 2 * static_cast<size_t>(j) * D.pitch;
+        // the F_VP field the sweep of step n wrote (the parity of the lattice it read)
+        const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
+        const T *fv = static_cast<const T *>(D.fvp[par]) + 2 * static_cast<size_t>(j) * D.pitch;
         unsigned present = 0u;  // bit b: body b has a node in the interval
         for (int i = jolo + lane; i <= johi; i += 32) present |= 1u << (mrow[i] & 31);
         present = __reduce_or_sync(0xffffffffu, present) & ~1u;
@@ -901,10 +903,13 @@ cudaError_t launch_halo_pack(cudaStream_t st, const HaloPack &pack, int max_ny) 
 // the body's row-major node list in FP64, then a fixed shuffle + shared-memory tree,
 // so the sum order depends only on the node list, not on the tiling or the batch.
 
-constexpr int kForceThreads = 512;
+// Small blocks at no more than 32 registers: one fits on an SM beside the direct sweep's
+// two 384-thread blocks at 80 registers (61,440 of 65,536), so the reduction of step n
+// runs while the sweep of step n + 1 does.
+constexpr int kForceThreads = 128;
 
 template <int S>
-__global__ void __launch_bounds__(kForceThreads)
+__global__ void __launch_bounds__(kForceThreads, 16)
 forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, const Counters *ctr,
               int s) {
   using T = typename Codec<S>::T;
@@ -915,7 +920,9 @@ forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, con
     const ForceItem item = items[it];
     const DomDev &D = doms[item.dom];
     const DomDyn dy = dyn[item.dom];
-    const T *fv = static_cast<const T *>(D.fvp);
+    // the F_VP field the sweep of this step wrote (the parity of the lattice it read)
+    const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
+    const T *fv = static_cast<const T *>(D.fvp[par]);
     const int32_t *solid = D.solid;
     const int force_every = D.force_every;
     // the node indices do not depend on the step: their loads overlap the checks below

@@ -47,7 +47,9 @@ struct DomDev {
   float *bodies_f;         // the same table rounded to FP32 (FP32-compute storages)
   const int32_t *solid;    // solid nodes (j * pitch + i), grouped by body, row-major
   const int32_t *solid_off;// [nbodies + 1] offsets into solid
-  void *fvp;               // F_VP of solid nodes, [ny][pitch] pairs in compute precision
+  void *fvp[2];            // F_VP of solid nodes, [ny][pitch] pairs in compute precision, one
+                           // field per parity of the lattice the sweep read: a step's force
+                           // reduction reads one while the next step's sweep writes the other
   double *ring;            // force ring [cap][nbodies][2]
   int32_t *status;         // bit 0: unstable; bit 1: a bounded device-side wait ran out
   int32_t nx, ny, pitch;

@@ -104,8 +104,8 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   size_t o = 2 * L.lat_bytes;
   L.mask_off = o;
   o += align_up(static_cast<size_t>(p.ny) * pitch, 256);
-  L.fvp_off = o;
-  o += align_up(static_cast<size_t>(p.ny) * pitch * 2 * (p.storage == LBM_F64 ? 8 : 4), 256);
+  L.fvp_off = o;  // two F_VP fields (by lattice parity)
+  o += 2 * align_up(static_cast<size_t>(p.ny) * pitch * 2 * (p.storage == LBM_F64 ? 8 : 4), 256);
   L.bodies_off = o;
   o += align_up(sizeof(double) * 5 * std::max(1, nbodies), 256);
   L.bodies_f_off = o;
@@ -255,6 +255,12 @@ struct lbm_batch {
   DomDyn *d_dyn = nullptr;
   DomDyn *h_dyn = nullptr;  // pinned staging
   cudaEvent_t dyn_ev = nullptr;
+  // the force reduction of a fixed-geometry batch runs on a second stream beside the next
+  // step's sweep: ev_sweep orders it after its sweep, ev_force[s & 1] the sweep two steps
+  // later (which rewrites the F_VP field it reads) after it, ev_join the batch stream
+  // after the last of them
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_sweep = nullptr, ev_force[2] = {nullptr, nullptr}, ev_join = nullptr;
   TileDev *d_tiles = nullptr;
   int tiles_cap = 0;
   ForceItem *d_items = nullptr;
@@ -441,9 +447,26 @@ lbm_status rebuild_lists(lbm_batch *b) {
 // Step s of the current run: the sweep, then the force reduction over the F_VP field the
 // sweep wrote. The force kernel is launched even when no body records forces (it returns
 // at once), so that a captured graph stays valid when the batch membership changes.
+// Fixed-geometry batches fork the force reduction to the second stream: it reads the F_VP
+// field of step s while step s + 1's sweep writes the other one, so it runs beside that
+// sweep (its small blocks fit next to the sweep's). Moving and coupled domains keep one
+// stream: their per-step geometry and state updates depend on the forces.
+bool forks(const lbm_batch *b) { return b->nmove == 0 && !b->has_fsi; }
+
 lbm_status enqueue_step(lbm_batch *b, int s) {
+  const bool fork = forks(b);
+  // the sweep rewrites the F_VP field that step s - 2's force reduction read
+  if (fork && s >= 2) LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_force[s & 1], 0));
   LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, s));
   b->launches++;
+  if (fork) {
+    LBM_CUDA(cudaEventRecord(b->ev_sweep, b->st));
+    LBM_CUDA(cudaStreamWaitEvent(b->st2, b->ev_sweep, 0));
+    LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st2, b->d_doms, b->d_dyn, b->d_items, b->d_ctr, s));
+    LBM_CUDA(cudaEventRecord(b->ev_force[s & 1], b->st2));
+    b->launches++;
+    return LBM_OK;
+  }
   if (b->nmove > 0) {  // moving domains: row force sums, then the next step's geometry
     LBM_CUDA(launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
     b->launches++;
@@ -458,6 +481,14 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   return LBM_OK;
 }
 
+// The batch stream waits for the force reductions forked to the second stream.
+lbm_status join_side(lbm_batch *b) {
+  if (!forks(b)) return LBM_OK;
+  LBM_CUDA(cudaEventRecord(b->ev_join, b->st2));
+  LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_join, 0));
+  return LBM_OK;
+}
+
 lbm_status capture_graph(lbm_batch *b) {
   drop_graph(b);
   cudaGraph_t g = nullptr;
@@ -465,6 +496,7 @@ lbm_status capture_graph(lbm_batch *b) {
   const long long before = b->launches;
   lbm_status rc = LBM_OK;
   for (int s = 0; s < b->graph_steps && rc == LBM_OK; ++s) rc = enqueue_step(b, s);
+  if (rc == LBM_OK) rc = join_side(b);
   cudaError_t e = rc == LBM_OK ? launch_advance(b->st, b->d_ctr, b->graph_steps) : cudaSuccess;
   cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
   b->launches = before;  // capture only records; replays count
@@ -589,6 +621,10 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
     rc = enqueue_step(b, static_cast<int>(s - s0));
     if (rc != LBM_OK) return rc;
   }
+  if (s0 < steps) {
+    rc = join_side(b);
+    if (rc != LBM_OK) return rc;
+  }
   for (Slot &s : b->slots) {
     if (!s.used || s.done >= s.target) continue;
     const long long adv = std::min(steps, s.target - s.done);
@@ -631,7 +667,8 @@ lbm_status prepare_slot(lbm_batch *b, const lbm_params *p, const lbm_geometry *g
   D.bodies_f = bodf;
   int32_t *off = reinterpret_cast<int32_t *>(base + L.off_off);
   D.solid_off = off;
-  D.fvp = base + L.fvp_off;
+  D.fvp[0] = base + L.fvp_off;
+  D.fvp[1] = base + L.fvp_off + (L.bodies_off - L.fvp_off) / 2;
   D.ring = reinterpret_cast<double *>(base + L.ring_off);
   D.status = reinterpret_cast<int32_t *>(base + L.status_off);
   D.moving = p->moving;
@@ -837,7 +874,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
   ADM_CUDA(launch_init(p->storage, st, D.lat[0], p->nx, p->ny, s.pitch, p->rho0, p->u0_x, p->u0_y));
   ADM_CUDA(cudaMemsetAsync(D.lat[1], 0, L.lat_bytes, st));
   ADM_CUDA(cudaMemsetAsync(D.status, 0, sizeof(int32_t), st));
-  ADM_CUDA(cudaMemsetAsync(D.fvp, 0, L.bodies_off - L.fvp_off, st));
+  ADM_CUDA(cudaMemsetAsync(D.fvp[0], 0, L.bodies_off - L.fvp_off, st));
   if (p->force_every > 0)
     ADM_CUDA(cudaMemsetAsync(D.ring, 0, sizeof(double) * 2 * std::max(1, nbodies) * s.p.force_capacity, st));
   ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
@@ -997,7 +1034,7 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
     seg1.push_back(FillSeg{base + L.kappa_off, nullptr,
                            align_up(sizeof(double) * std::max(1, nbs[i]), 256) + sizeof(float) * std::max(1, nbs[i])});
     seg1.push_back(FillSeg{D.status, nullptr, sizeof(int32_t)});
-    seg1.push_back(FillSeg{D.fvp, nullptr, L.bodies_off - L.fvp_off});
+    seg1.push_back(FillSeg{D.fvp[0], nullptr, L.bodies_off - L.fvp_off});
     r0 += p.ny;
     c0 += static_cast<size_t>(nbs[i] + 1) * p.ny;
     s0 += geoms[i].nshapes;
@@ -1274,6 +1311,12 @@ void destroy(lbm_batch *b) {
   if (b->h_ctr) cudaFreeHost(b->h_ctr);
   if (b->h_poll) cudaFreeHost(b->h_poll);
   if (b->dyn_ev) cudaEventDestroy(b->dyn_ev);
+  if (b->st2) {
+    cudaStreamSynchronize(b->st2);
+    cudaStreamDestroy(b->st2);
+  }
+  for (cudaEvent_t e : {b->ev_sweep, b->ev_force[0], b->ev_force[1], b->ev_join})
+    if (e) cudaEventDestroy(e);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
   delete b;
 }
@@ -1319,6 +1362,15 @@ lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, 
     cudaGetLastError();
     destroy(b);
     return fail(LBM_ENOMEM, "pinned host allocation failed");
+  }
+  if (cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_sweep, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_force[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_force[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(b);
+    return fail(LBM_ECUDA, "stream or event creation failed");
   }
   cudaEventRecord(b->dyn_ev, b->st);
   cudaMemsetAsync(b->d_ctr, 0, sizeof(Counters), b->st);

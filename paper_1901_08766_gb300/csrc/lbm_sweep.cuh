@@ -206,23 +206,24 @@ template <int S, int V> struct RowData {
 // Phase 3 of a strip row, shared by the row pipelines: update the V pulled nodes of a
 // lane in place (inlet ghost, moments, penalization, collision, F_VP of solid nodes,
 // stability check, rounding to the storage type) and zero the padding beyond nx. mb: the
-// nodes' body ids, four per word. The caller stores v[].
+// nodes' body ids, four per word; fvp: the F_VP field of this step's parity. The caller
+// stores v[].
 // The update of a 16-bit strip that holds solid nodes, node by node in FP32 (moments,
 // penalization, collision, F_VP, stability bits as in update_strip), out of line: the
 // strips of the force-free path, nearly all of them, then run with the registers this
 // path would otherwise claim (the direct sweep at 24 resident warps: 168 B of spills
 // before, 72 B after; 376 -> 358 us on the 64-domain batch). w: the strip's words
-// [kQ][V / 2], updated in place; mb0, mb1: its mask bytes. Returns the nodes whose
-// density left (0.01, 100) as bits.
+// [kQ][V / 2], updated in place; mb0, mb1: its mask bytes; fvp: the F_VP field of this
+// step's parity. Returns the nodes whose density left (0.01, 100) as bits.
 template <int S, int V, bool DEF>
 __device__ __noinline__ unsigned solid_strip16(uint32_t *w, uint32_t mb0, uint32_t mb1, const DomDev &D,
-                                             const CellConst<float> &C, int lane, int xl, int j, bool west_first,
-                                             uint32_t sr_g) {
+                                             void *fvp, const CellConst<float> &C, int lane, int xl, int j,
+                                             bool west_first, uint32_t sr_g) {
   using Cd = Codec<S>;
   constexpr bool SHIFT = Cd::kShiftCompute;
   constexpr float kRhoMid = 50.005f * float(Cd::kScale), kRhoHalf = 49.995f * float(Cd::kScale);
   constexpr float kUnscale = 1.0f / float(Cd::kScale);
-  float *__restrict__ dfvp = static_cast<float *>(D.fvp);
+  float *__restrict__ dfvp = static_cast<float *>(fvp);
   unsigned bb = 0u;
 #pragma unroll
   for (int k = 0; k < V; k += 2) {
@@ -278,7 +279,7 @@ __device__ __forceinline__ void update_strip(Strip<S, V> (&v)[kQ], const uint32_
                                              const CellConst<F2> &CP, const int lane, const int xl,
                                              const int j, const long long n, const bool west_edge,
                                              const bool west_inlet, const bool east_edge,
-                                             const int nx, int &unstable) {
+                                             const int nx, void *fvp, int &unstable) {
   using Cd = Codec<S>;
   using E = typename Cd::E;
   using T = typename Cd::T;
@@ -287,7 +288,7 @@ __device__ __forceinline__ void update_strip(Strip<S, V> (&v)[kQ], const uint32_
   constexpr T kRhoMid = T(50.005) * T(Cd::kScale), kRhoHalf = T(49.995) * T(Cd::kScale);
   constexpr T kUnscale = T(1) / T(Cd::kScale);
   const int pitch = D.pitch;
-  T *__restrict__ dfvp = static_cast<T *>(D.fvp);
+  T *__restrict__ dfvp = static_cast<T *>(fvp);
   bool any_solid_lane = false;
 #pragma unroll
   for (int q = 0; q < (V + 3) / 4; ++q) any_solid_lane |= (mb[q] != 0u);
@@ -368,8 +369,8 @@ __device__ __forceinline__ void update_strip(Strip<S, V> (&v)[kQ], const uint32_
       for (int a = 0; a < kQ; ++a)
 #pragma unroll
         for (int q = 0; q < V / 2; ++q) wl[a * (V / 2) + q] = v[a].w[q];
-      bad_bits |= solid_strip16<S, V, DEF>(wl, mb[0], (V + 3) / 4 > 1 ? mb[(V + 3) / 4 - 1] : 0u, D, C, lane, xl, j,
-                                           west_edge && west_inlet, sr_g);
+      bad_bits |= solid_strip16<S, V, DEF>(wl, mb[0], (V + 3) / 4 > 1 ? mb[(V + 3) / 4 - 1] : 0u, D, fvp, C, lane,
+                                           xl, j, west_edge && west_inlet, sr_g);
 #pragma unroll
       for (int a = 0; a < kQ; ++a)
 #pragma unroll
@@ -632,7 +633,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &args, int s) {
         }
       }
       update_strip<S, V, DEF>(v, R.mb, D, C, CF, CP, lane, xl, j, n, west_edge, west_inlet,
-                              east_edge, nx, unstable);
+                              east_edge, nx, D.fvp[par], unstable);
       if (lane_on) {
 #pragma unroll
         for (int a = 0; a < kQ; ++a)

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(512) sweep_tma_kernel(SweepArgs args, int s) {
         m = node_macro<T, SHIFT, true>(x, C, solid, uox, uoy);
         collide<T, SHIFT, true>(x, m, C);
         if (solid) {
-          T *fv = static_cast<T *>(D.fvp) + 2 * (static_cast<size_t>(j) * pitch + xl + k);
+          T *fv = static_cast<T *>(D.fvp[par]) + 2 * (static_cast<size_t>(j) * pitch + xl + k);
           fv[0] = m.fx * (T(1) / T(Cd::kScale));  // unscaled (power of two: exact)
           fv[1] = m.fy * (T(1) / T(Cd::kScale));
         }
