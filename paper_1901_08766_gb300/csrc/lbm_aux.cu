@@ -418,7 +418,7 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
             fy += __shfl_down_sync(0xffffffffu, fy, off);
           }
           if (lane == 0) {
-            double *r = D.rowsum + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
+            double *r = D.rowsum[par] + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
             r[0] = fx;
             r[1] = fy;
             r[2] = static_cast<double>(n);
@@ -935,7 +935,7 @@ forces_kernel(const DomDev *doms, const DomDyn *dyn, const ForceItem *items, con
     if (item.rows) {
       // moving domain: the per-row sums of -F_VP, rows in order per thread
       for (int q = q0; q < item.end; q += blockDim.x) {
-        const double *r = D.rowsum + (static_cast<size_t>(q) * D.nbodies + (item.body - 1)) * 3;
+        const double *r = D.rowsum[par] + (static_cast<size_t>(q) * D.nbodies + (item.body - 1)) * 3;
         if (r[2] == static_cast<double>(n)) {  // written for this step
           fx += r[0];
           fy += r[1];

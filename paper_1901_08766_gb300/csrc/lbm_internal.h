@@ -65,7 +65,8 @@ struct DomDev {
   const ShapeDev *shapes;   // [nshapes] reference geometry (step index 0)
   const float4 *shapes_f;   // [nshapes] FP32 centre x, y and extent (shape_extent) of each
   const double *centre0;    // [nbodies][2] reference centres
-  double *rowsum;           // [ny][nbodies][3] per-row sums of -F_VP and the step they belong to
+  double *rowsum[2];        // [ny][nbodies][3] per-row sums of -F_VP and the step they belong to,
+                            // one table per lattice parity (as the F_VP fields)
   int32_t nshapes, moving;
   // slab decomposition: global column of local column 0, and the lattices of linked
   // neighbour domains ([0] west, [1] east; used where the edge is LBM_NEIGHBOR)

@@ -126,8 +126,8 @@ Layout layout_of(const lbm_params &p, int nbodies) {
     o += align_up((sizeof(ShapeDev) + sizeof(float4)) * kMaxMovingShapes, 256);
     L.centre0_off = o;
     o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
-    L.rowsum_off = o;
-    o += align_up(sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
+    L.rowsum_off = o;  // two tables (by lattice parity)
+    o += align_up(2 * sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p.ny), 256);
     // coupled bodies: state of two step parities [2][nbodies][6], parameters [nbodies][8]
     L.fsi_off = o;
     o += align_up(sizeof(double) * 20 * std::max(1, nbodies), 256);
@@ -447,11 +447,12 @@ lbm_status rebuild_lists(lbm_batch *b) {
 // Step s of the current run: the sweep, then the force reduction over the F_VP field the
 // sweep wrote. The force kernel is launched even when no body records forces (it returns
 // at once), so that a captured graph stays valid when the batch membership changes.
-// Fixed-geometry batches fork the force reduction to the second stream: it reads the F_VP
-// field of step s while step s + 1's sweep writes the other one, so it runs beside that
-// sweep (its small blocks fit next to the sweep's). Moving and coupled domains keep one
-// stream: their per-step geometry and state updates depend on the forces.
-bool forks(const lbm_batch *b) { return b->nmove == 0 && !b->has_fsi; }
+// Batches without coupled bodies fork the force reduction to the second stream: it reads
+// the F_VP field (and, for moving domains, the row sums) of step s's parity while step
+// s + 1's sweep and move kernel write the other ones, so it runs beside that sweep (its
+// small blocks fit next to the sweep's). Coupled bodies keep one stream: their next state
+// and geometry depend on the forces.
+bool forks(const lbm_batch *b) { return !b->has_fsi; }
 
 lbm_status enqueue_step(lbm_batch *b, int s) {
   const bool fork = forks(b);
@@ -460,6 +461,10 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, s));
   b->launches++;
   if (fork) {
+    if (b->nmove > 0) {  // moving domains: row force sums (by parity), then the next geometry
+      LBM_CUDA(launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
+      b->launches++;
+    }
     LBM_CUDA(cudaEventRecord(b->ev_sweep, b->st));
     LBM_CUDA(cudaStreamWaitEvent(b->st2, b->ev_sweep, 0));
     LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st2, b->d_doms, b->d_dyn, b->d_items, b->d_ctr, s));
@@ -678,7 +683,8 @@ lbm_status prepare_slot(lbm_batch *b, const lbm_params *p, const lbm_geometry *g
   D.shapes_f = p->moving ? reinterpret_cast<const float4 *>(base + L.shapes_off + sizeof(ShapeDev) * kMaxMovingShapes)
                          : nullptr;
   D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
-  D.rowsum = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
+  D.rowsum[0] = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
+  D.rowsum[1] = p->moving ? D.rowsum[0] + 3 * static_cast<size_t>(std::max(1, nbodies)) * p->ny : nullptr;
   D.fsi = p->moving ? reinterpret_cast<double *>(base + L.fsi_off) : nullptr;
   D.fsi_par = p->moving ? reinterpret_cast<const double *>(base + L.fsi_off) + 12 * std::max(1, nbodies) : nullptr;
   D.fsi_on = 0;
@@ -835,7 +841,7 @@ lbm_status admit(lbm_batch *b, const lbm_params *p, const uint8_t *mask_host,
     ADM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.centre0), hc0.data(), sizeof(double) * hc0.size(),
                              cudaMemcpyHostToDevice, st));
     // per-row force sums start untagged (all-ones bytes: a NaN tag equals no step)
-    ADM_CUDA(cudaMemsetAsync(D.rowsum, 0xff, sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
+    ADM_CUDA(cudaMemsetAsync(D.rowsum[0], 0xff, 2 * sizeof(double) * 3 * std::max(1, nbodies) * static_cast<size_t>(p->ny), st));
     ADM_CUDA(cudaMemsetAsync(D.fsi, 0, sizeof(double) * 20 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemsetAsync(const_cast<double *>(D.dpar), 0, sizeof(double) * 8 * std::max(1, nbodies), st));
     ADM_CUDA(cudaMemcpyAsync(b->d_doms + k, &D, sizeof(DomDev), cudaMemcpyHostToDevice, st));
