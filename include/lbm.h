@@ -235,7 +235,10 @@ LBM_API lbm_status lbm_domain_destroy(lbm_domain *d);
 
 /* A batch advances many domains of one storage type together: each time step is one
  * persistent launch over a tile work list covering every resident domain, plus one
- * force-reduction launch; steps are replayed from captured CUDA graphs.
+ * force-reduction launch; steps are replayed from captured CUDA graphs. Unless a domain
+ * has coupled bodies, the force reduction of a step runs on a second stream of the
+ * library's beside the next step's sweep; every call returns with that stream joined to
+ * cuda_stream, so work ordered after a call on cuda_stream sees its results.
  *  max_domains:      slot count (1..4096).
  *  hbm_budget_bytes: admission limit on the sum of lbm_domain_bytes (0: no limit).
  *  graph_steps:      steps per captured graph (0: no graphs, one launch per kernel).
