@@ -729,6 +729,8 @@ def experiment(args):
                     r[k + "_rel_vs_f64"] = (r[k] - ref[k]) / ref[k] if ref[k] else None
     elif args.experiment == "sphere3d":
         out.update(sphere3d(lbm, torch, np, [args.storage] if args.quick else None, args.lattice))
+    elif args.experiment == "batch3":
+        out["batched"] = batch3_perf(lbm, torch)
     elif args.experiment == "admission":
         # the end-to-end jobs of the batched workload alone (admission, steps, readback),
         # repeated, for the cost of each phase
@@ -1126,6 +1128,7 @@ def main():
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 15],
                     help="3D lattice of --experiment sphere3d --quick")
     ap.add_argument("--experiment", choices=["couette", "precision", "cylinder", "sphere3d", "served", "viv", "admission",
+                                             "batch3",
                                              "paper"],
                     default=None,
                     help="accuracy study instead of the benchmark")
