@@ -57,8 +57,9 @@ def test_domain_bytes(lib):
     pitch = 128  # 97 rounded up to 64
     lat16 = 9 * 61 * pitch * 2
     assert b16 >= 2 * lat16 + 61 * pitch + 8192 * 2 * 2 * 8
-    # populations 8 vs 2 bytes (x2 lattices), F_VP field 16 vs 8 bytes per node
-    assert b64 - b16 == pytest.approx(2 * 9 * 61 * pitch * 6 + 61 * pitch * 8, abs=1024)
+    # populations 8 vs 2 bytes (x2 lattices), F_VP fields (one per lattice parity) 16 vs
+    # 8 bytes per node
+    assert b64 - b16 == pytest.approx(2 * 9 * 61 * pitch * 6 + 2 * 61 * pitch * 8, abs=1024)
 
 
 BAD = [
