@@ -267,7 +267,10 @@ LBM_API lbm_status lbm_batch_admit(lbm_batch *b, const lbm_params *p, const uint
  * nbodies is 0). slots[i] receives domain i's slot. All or none: on any error nothing is
  * admitted and every allocation is given back. LBM_EBUSY when fewer than n slots are free
  * or the memory budget would be exceeded; LBM_EINVAL as lbm_batch_admit, with the
- * domain's index in the message. No counterpart in the paper (admission scheduling). */
+ * domain's index in the message. Memory: for n >= 2 the domains' blocks come from one
+ * allocation and their solid-node lists from another (two allocator calls in all); an
+ * evicted domain's share is returned, and leaves the memory budget, when the last domain
+ * of the group leaves. No counterpart in the paper (admission scheduling). */
 LBM_API lbm_status lbm_batch_admit_many(lbm_batch *b, int32_t n, const lbm_params *params,
                                         const lbm_geometry *geoms, const lbm_body *const *bodies,
                                         const int32_t *nbodies, const int64_t *nsteps, int32_t *slots);
@@ -279,19 +282,20 @@ LBM_API lbm_status lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t *steps
 
 /* Drain a slot's recorded forces (as lbm_forces); *done = 1 once the slot has run all
  * its steps and its forces are drained. Synchronises the stream. */
-/* lbm_batch_poll for n slots with one synchronisation (their entries and status words
- * are staged in pinned host memory by asynchronous copies): outs[i] receives up to
+LBM_API lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_entries,
+                          int64_t *written, int32_t *done);
+
+/* lbm_batch_poll for n slots with one synchronisation: their entries and status words
+ * reach pinned host memory by asynchronous copies (for n >= 4, one copy launch gathers
+ * them into device staging, read back by one transfer): outs[i] receives up to
  * max_entries[i] entries of slot slots[i], [entries][nbodies][2] FP64, written[i] their
  * number, done[i] as lbm_batch_poll, status[i] the slot's own state (LBM_OK, LBM_EUNSTABLE
  * or LBM_ETIMEOUT; a failed slot's entries are still drained). Returns LBM_EINVAL or
- * LBM_ENOTFOUND (nothing drained) for a bad argument, LBM_ENOMEM if the pinned staging
- * cannot grow, LBM_ECUDA if a copy fails. No counterpart in the paper (host I/O). */
+ * LBM_ENOTFOUND (nothing drained) for a bad argument, LBM_ENOMEM if the pinned or device
+ * staging cannot grow, LBM_ECUDA if a copy fails. No counterpart in the paper (host I/O). */
 LBM_API lbm_status lbm_batch_poll_many(lbm_batch *b, int32_t n, const int32_t *slots,
                                        double *const *outs, const int64_t *max_entries,
                                        int64_t *written, int32_t *done, int32_t *status);
-
-LBM_API lbm_status lbm_batch_poll(lbm_batch *b, int32_t slot, double *out, int64_t max_entries,
-                          int64_t *written, int32_t *done);
 
 /* Per-slot access, as the single-domain calls of the same name. Synchronise. */
 LBM_API lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, double *ux, double *uy);

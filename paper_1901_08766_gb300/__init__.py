@@ -503,25 +503,13 @@ class Batch:
         out = [None] * len(specs)
         if plain:
             n = len(plain)
-            P = (_native.Params * n)()
-            G = (_native.Geometry * n)()
-            BP = (C.POINTER(_native.Body) * n)()
-            NB = (C.c_int32 * n)()
-            NS = (C.c_int64 * n)()
-            keep = []
-            for q, k in enumerate(plain):
-                sp = specs[k]
-                P[q] = _native.params_from_spec(sp, self.storage, force_every, force_capacity)
-                g, shapes = _native.geometry_from_spec(sp)
-                bodies, nb = _native.bodies_from_spec(sp)
-                keep += [shapes, bodies]
-                G[q] = g
-                BP[q] = C.cast(bodies, C.POINTER(_native.Body))
-                NB[q] = nb
-                NS[q] = int(sp["steps"] if nsteps is None else
-                            (nsteps[k] if isinstance(nsteps, (list, tuple)) else nsteps))
+            group = [specs[k] for k in plain]
+            steps = [int(sp["steps"] if nsteps is None else
+                         (nsteps[k] if isinstance(nsteps, (list, tuple)) else nsteps))
+                     for k, sp in zip(plain, group)]
+            many = _native.ManyDomains(group, self.storage, force_every, force_capacity, steps)
             S = (C.c_int32 * n)()
-            check(load().lbm_batch_admit_many(self._h, n, P, G, BP, NB, NS, S), "lbm_batch_admit_many")
+            check(load().lbm_batch_admit_many(self._h, n, *many.args(), S), "lbm_batch_admit_many")
             for q, k in enumerate(plain):
                 sp = specs[k]
                 self._meta[S[q]] = (sp["nx"], sp["ny"], len(sp["bodies"]), force_capacity)

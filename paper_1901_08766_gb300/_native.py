@@ -270,6 +270,48 @@ def geometry_from_spec(spec):
     return g, arr
 
 
+class ManyDomains:
+    """The admission arguments of many domains, built in one pass into numpy arrays laid
+    out as the C structures (the same bytes as params_from_spec, geometry_from_spec and
+    bodies_from_spec per domain, without a ctypes object per field)."""
+
+    def __init__(self, specs, storage: str, force_every: int, force_capacity: int, nsteps):
+        pd, sd, bd = np.dtype(Params), np.dtype(Shape), np.dtype(Body)
+        gd = np.dtype({"names": ["shapes", "nshapes"], "formats": [np.uintp, np.int32],
+                       "offsets": [0, 8], "itemsize": C.sizeof(Geometry)})
+        st = STORAGE[storage]
+        self.params = np.array(
+            [(sp["nx"], sp["ny"], sp["nu"], 0.0, sp["magic_lambda"], sp["eta"], sp["rho0"],
+              sp["u_in"][0], sp["u_in"][1], sp["u0"][0], sp["u0"][1],
+              EDGE[sp["edges"]["west"]], EDGE[sp["edges"]["east"]], EDGE[sp["edges"]["south"]],
+              EDGE[sp["edges"]["north"]], st, force_every, force_capacity, moving_mode(sp),
+              int(sp.get("x_origin", 0))) for sp in specs], dtype=pd)
+        shapes = [(SHAPE[s["kind"]], s["body"], s["cx"], s["cy"], s.get("radius", 0.0),
+                   s.get("chord", 0.0), s.get("thickness", 0.0), s.get("aoa_rad", 0.0))
+                  for sp in specs for s in sp["shapes"]]
+        self.shapes = np.array(shapes or [(0, 0) + (0.0,) * 6], dtype=sd)
+        bodies = [(b["cx"], b["cy"], b["vx"], b["vy"], b["omega"], b["ref_length"])
+                  for sp in specs for b in sp["bodies"]]
+        self.bodies = np.array(bodies or [(0.0,) * 6], dtype=bd)
+        ns = np.array([len(sp["shapes"]) for sp in specs], dtype=np.int64)
+        self.nbodies = np.array([len(sp["bodies"]) for sp in specs], dtype=np.int32)
+        self.geometry = np.zeros(len(specs), dtype=gd)
+        self.geometry["shapes"] = self.shapes.ctypes.data + sd.itemsize * (np.cumsum(ns) - ns)
+        self.geometry["nshapes"] = ns
+        nb = self.nbodies.astype(np.int64)
+        self.body_ptrs = (self.bodies.ctypes.data + bd.itemsize * (np.cumsum(nb) - nb)).astype(np.uintp)
+        self.nsteps = np.array(nsteps, dtype=np.int64)
+
+    def args(self):
+        """(params, geometries, body pointers, body counts, step counts) as the pointers
+        lbm_batch_admit_many takes; valid while this object lives."""
+        return (self.params.ctypes.data_as(C.POINTER(Params)),
+                self.geometry.ctypes.data_as(C.POINTER(Geometry)),
+                self.body_ptrs.ctypes.data_as(C.POINTER(C.POINTER(Body))),
+                self.nbodies.ctypes.data_as(C.POINTER(_I32)),
+                self.nsteps.ctypes.data_as(C.POINTER(_I64)))
+
+
 def params3_from_spec(spec, storage: str, force_every: int = 1,
                       force_capacity: int = 8192) -> Params3:
     e = spec["edges"]

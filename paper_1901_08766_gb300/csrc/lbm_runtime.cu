@@ -184,7 +184,18 @@ struct Slot {
                                        // halo edge fed from a caller's buffer)
   void *halo_send[2] = {nullptr, nullptr};  // halo edges: where lbm_batch_pack_halos writes
   bool fsi = false;                    // some body responds to its force
+  int group = -1;  // >= 0: block and solid list are carved from the shared allocations of
+                   // a batched admission (lbm_batch::groups[group])
   DomDev dev{};
+};
+
+// The two allocations a batched admission takes for all of its domains (domain blocks,
+// solid lists), returned when the last of those domains leaves the batch; `bytes` is
+// what the domains count against the memory budget until then.
+struct Group {
+  void *block = nullptr, *solid = nullptr;
+  int members = 0;
+  size_t bytes = 0;
 };
 
 }  // namespace
@@ -284,6 +295,9 @@ struct lbm_batch {
   int inject = 0;  // SweepArgs::inject of later sweep launches (host failure injection)
   char *h_poll = nullptr;  // pinned staging of lbm_batch_poll_many (grows as needed)
   size_t h_poll_cap = 0;
+  char *d_poll = nullptr;  // device staging where lbm_batch_poll_many gathers (grows as needed)
+  size_t d_poll_cap = 0;
+  std::vector<Group> groups;  // shared allocations of batched admissions (free entries reused)
 };
 
 struct lbm_domain {
@@ -647,17 +661,18 @@ lbm_status read_status(lbm_batch *b, const Slot &s, int *st) {
 }
 
 // Host-side part of admitting a domain: the slot's parameters, its device block (one
-// allocation holding lattices, mask, F_VP field, body tables, force ring, status word)
-// and its device description with the collision constants. No GPU work is issued.
+// allocation holding lattices, mask, F_VP field, body tables, force ring, status word;
+// or, with `block` given, that part of a batched admission's shared allocation) and its
+// device description with the collision constants. No GPU work is issued.
 lbm_status prepare_slot(lbm_batch *b, const lbm_params *p, const lbm_geometry *geom, int nbodies,
-                        long long nsteps, const Layout &L, Slot &s) {
+                        long long nsteps, const Layout &L, Slot &s, void *block = nullptr) {
   s = Slot();
   s.p = *p;
   if (s.p.force_capacity == 0) s.p.force_capacity = 8192;
   s.nbodies = nbodies;
   s.pitch = pitch_of(p->nx);
   s.target = nsteps;
-  s.block = b->al.get(L.total);
+  s.block = block ? block : b->al.get(L.total);
   if (!s.block) return fail(LBM_ENOMEM, "device allocation of %zu bytes failed", L.total);
   s.bytes = L.total;
   char *base = static_cast<char *>(s.block);
@@ -940,17 +955,38 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
   cudaStream_t st = b->st;
   std::vector<Slot> S(n);
   void *tmp = nullptr;
+  // Two or more domains share one allocation for their blocks and one for their solid
+  // lists (two allocator calls instead of two per domain; the group's memory returns when
+  // its last domain leaves).
+  const bool grouped = n > 1;
+  void *gblock = nullptr, *gsolid = nullptr;
   auto release = [&](lbm_status r) {
     cudaStreamSynchronize(st);
-    for (Slot &x : S) {
-      b->al.put(x.block);
-      b->al.put(x.solid);
+    if (grouped) {
+      b->al.put(gblock);
+      b->al.put(gsolid);
+    } else {
+      for (Slot &x : S) {
+        b->al.put(x.block);
+        b->al.put(x.solid);
+      }
     }
     b->al.put(tmp);
     return r;
   };
+  std::vector<size_t> boff(n, 0);
+  if (grouped) {
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+      boff[i] = total;
+      total += align_up(Ls[i].total, 256);
+    }
+    gblock = b->al.get(total);
+    if (!gblock) return fail(LBM_ENOMEM, "device allocation of %zu bytes failed", total);
+  }
   for (int i = 0; i < n; ++i) {
-    lbm_status rc = prepare_slot(b, &ps[i], &geoms[i], nbs[i], nsteps[i], Ls[i], S[i]);
+    lbm_status rc = prepare_slot(b, &ps[i], &geoms[i], nbs[i], nsteps[i], Ls[i], S[i],
+                                 grouped ? static_cast<char *>(gblock) + boff[i] : nullptr);
     if (rc != LBM_OK) return release(rc);
   }
 
@@ -1096,14 +1132,30 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
       hso.insert(hso.end(), ho.begin(), ho.end());
       S[i].solid_off = ho;
       nsolid[i] = static_cast<size_t>(acc);
-      S[i].solid = b->al.get(sizeof(int32_t) * std::max<size_t>(1, nsolid[i]));
-      if (!S[i].solid) return release(fail(LBM_ENOMEM, "solid list allocation failed"));
-      S[i].dev.solid = static_cast<const int32_t *>(S[i].solid);
-      ad[i].solid = static_cast<int32_t *>(S[i].solid);
       ad[i].row_off = reinterpret_cast<const int32_t *>(t + o_ro) + oo;
       cc += static_cast<size_t>(nb + 1) * ny;
       oo += static_cast<size_t>(nb) * ny;
     }
+  }
+  if (grouped) {
+    std::vector<size_t> soff(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+      soff[i] = total;
+      total += align_up(sizeof(int32_t) * std::max<size_t>(1, nsolid[i]), 256);
+    }
+    gsolid = b->al.get(total);
+    if (!gsolid) return release(fail(LBM_ENOMEM, "solid list allocation failed"));
+    for (int i = 0; i < n; ++i) S[i].solid = static_cast<char *>(gsolid) + soff[i];
+  } else {
+    for (int i = 0; i < n; ++i) {
+      S[i].solid = b->al.get(sizeof(int32_t) * std::max<size_t>(1, nsolid[i]));
+      if (!S[i].solid) return release(fail(LBM_ENOMEM, "solid list allocation failed"));
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    S[i].dev.solid = static_cast<const int32_t *>(S[i].solid);
+    ad[i].solid = static_cast<int32_t *>(S[i].solid);
   }
   // second upload: row offsets, descriptors with the solid lists, per-domain solid
   // offsets and the domains' device descriptions, copied into place by one fill launch
@@ -1133,16 +1185,46 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
 #undef ADM_CUDA
   b->al.put(tmp);
   tmp = nullptr;
+  int g = -1;
+  if (grouped) {
+    for (size_t q = 0; q < b->groups.size() && g < 0; ++q)
+      if (b->groups[q].members == 0) g = static_cast<int>(q);
+    if (g < 0) {
+      g = static_cast<int>(b->groups.size());
+      b->groups.emplace_back();
+    }
+    b->groups[g] = Group{gblock, gsolid, n, 0};
+  }
   for (int i = 0; i < n; ++i) {
     Slot &x = S[i];
     x.used = true;
+    x.group = g;
     x.bytes = Ls[i].total + sizeof(int32_t) * std::max<size_t>(1, nsolid[i]);
     b->bytes_in_use += x.bytes;
+    if (g >= 0) b->groups[g].bytes += x.bytes;
     b->slots[ks[i]] = x;
     slots_out[i] = ks[i];
   }
   b->dirty = true;
   return LBM_OK;
+}
+
+// Return a slot's device memory: its own two allocations, or its share of a batched
+// admission's, which go back (and leave the memory budget) with the group's last domain.
+void release_memory(lbm_batch *b, Slot &s) {
+  if (s.group >= 0) {
+    Group &g = b->groups[s.group];
+    if (--g.members == 0) {
+      b->al.put(g.block);
+      b->al.put(g.solid);
+      b->bytes_in_use -= g.bytes;
+      g = Group();
+    }
+  } else {
+    b->al.put(s.block);
+    b->al.put(s.solid);
+    b->bytes_in_use -= s.bytes;
+  }
 }
 
 lbm_status check_slot(lbm_batch *b, int slot) {
@@ -1194,7 +1276,7 @@ lbm_status poll_many(lbm_batch *b, int n, const int32_t *slots, double *const *o
     return fail(LBM_EINVAL, "an argument array is NULL");
   std::vector<long long> cnt(n);
   std::vector<size_t> at(n);
-  size_t bytes = align_up(sizeof(int32_t) * n, 16);
+  size_t bytes = align_up(sizeof(int32_t) * n, 16), nspan = 0;
   for (int i = 0; i < n; ++i) {
     lbm_status rc = check_slot(b, slots[i]);
     if (rc != LBM_OK) return rc;
@@ -1203,12 +1285,25 @@ lbm_status poll_many(lbm_batch *b, int n, const int32_t *slots, double *const *o
     if (cnt[i] > 0 && !outs[i]) return fail(LBM_EINVAL, "outs[%d] is NULL", i);
     at[i] = bytes;
     bytes += sizeof(double) * 2 * static_cast<size_t>(s.nbodies) * static_cast<size_t>(std::max(0ll, cnt[i]));
+    // copy spans of this slot: its status word and the ring entries up to each wrap
+    nspan += 1;
+    if (s.nbodies > 0)
+      for (long long c = 0; c < cnt[i];) {
+        c += std::min(cnt[i] - c, static_cast<long long>(s.dev.force_cap) - (s.drained + c) % s.dev.force_cap);
+        nspan += 1;
+      }
   }
-  if (bytes > b->h_poll_cap) {
+  // From four slots on, the status words and ring entries are gathered into device
+  // staging by one copy launch and read back by one transfer (two copies per slot cost
+  // more host time); the copy descriptors follow the results in both staging buffers.
+  const bool gather = n >= 4;
+  const size_t seg_at = align_up(bytes, 16);
+  const size_t need = gather ? seg_at + sizeof(FillSeg) * nspan : bytes;
+  if (need > b->h_poll_cap) {
     if (b->h_poll) cudaFreeHost(b->h_poll);
     b->h_poll = nullptr;
     b->h_poll_cap = 0;
-    const size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
+    const size_t cap = std::max<size_t>(need * 2, 1 << 16);
     if (cudaMallocHost(&b->h_poll, cap) != cudaSuccess) {
       cudaGetLastError();
       b->h_poll = nullptr;
@@ -1216,20 +1311,44 @@ lbm_status poll_many(lbm_batch *b, int n, const int32_t *slots, double *const *o
     }
     b->h_poll_cap = cap;
   }
+  if (gather && need > b->d_poll_cap) {
+    b->al.put(b->d_poll);
+    b->d_poll_cap = 0;
+    const size_t cap = std::max<size_t>(need * 2, 1 << 16);
+    b->d_poll = static_cast<char *>(b->al.get(cap));
+    if (!b->d_poll) return fail(LBM_ENOMEM, "device staging of %zu bytes failed", cap);
+    b->d_poll_cap = cap;
+  }
   int32_t *st_words = reinterpret_cast<int32_t *>(b->h_poll);
+  FillSeg *segs = reinterpret_cast<FillSeg *>(b->h_poll + seg_at);
+  int nseg = 0;
+  // one span from the device to the results at offset `off`
+  auto take = [&](size_t off, const void *src, size_t len) -> cudaError_t {
+    if (gather) {
+      segs[nseg++] = FillSeg{b->d_poll + off, src, len};
+      return cudaSuccess;
+    }
+    return cudaMemcpyAsync(b->h_poll + off, src, len, cudaMemcpyDeviceToHost, b->st);
+  };
   for (int i = 0; i < n; ++i) {
     const Slot &s = b->slots[slots[i]];
-    LBM_CUDA(cudaMemcpyAsync(st_words + i, s.dev.status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->st));
+    LBM_CUDA(take(sizeof(int32_t) * i, s.dev.status, sizeof(int32_t)));
     const size_t per = 2 * static_cast<size_t>(s.nbodies);
     long long copied = 0;
     while (copied < cnt[i] && per > 0) {
       const long long e = s.drained + copied;
       const long long pos = e % s.dev.force_cap;
       const long long chunk = std::min(cnt[i] - copied, static_cast<long long>(s.dev.force_cap) - pos);
-      LBM_CUDA(cudaMemcpyAsync(b->h_poll + at[i] + sizeof(double) * copied * per, s.dev.ring + pos * per,
-                               sizeof(double) * per * chunk, cudaMemcpyDeviceToHost, b->st));
+      LBM_CUDA(take(at[i] + sizeof(double) * copied * per, s.dev.ring + pos * per, sizeof(double) * per * chunk));
       copied += chunk;
     }
+  }
+  if (gather) {
+    FillSeg *d_segs = reinterpret_cast<FillSeg *>(b->d_poll + seg_at);
+    LBM_CUDA(cudaMemcpyAsync(d_segs, segs, sizeof(FillSeg) * nseg, cudaMemcpyHostToDevice, b->st));
+    LBM_CUDA(launch_fill(b->st, d_segs, nseg));
+    b->launches++;
+    LBM_CUDA(cudaMemcpyAsync(b->h_poll, b->d_poll, bytes, cudaMemcpyDeviceToHost, b->st));
   }
   LBM_CUDA(cudaStreamSynchronize(b->st));
   for (int i = 0; i < n; ++i) {
@@ -1302,10 +1421,8 @@ void destroy(lbm_batch *b) {
   if (b->st) cudaStreamSynchronize(b->st);
   drop_graph(b);
   for (Slot &s : b->slots)
-    if (s.used) {
-      b->al.put(s.block);
-      b->al.put(s.solid);
-    }
+    if (s.used) release_memory(b, s);
+  b->al.put(b->d_poll);
   b->al.put(b->d_doms);
   b->al.put(b->d_dyn);
   b->al.put(b->d_tiles);
@@ -1843,9 +1960,7 @@ lbm_status lbm_batch_evict(lbm_batch *b, int32_t slot) {
     LBM_CUDA(cudaMemcpyAsync(b->d_doms + s.link_east, &P.dev, sizeof(DomDev), cudaMemcpyHostToDevice, b->st));
   }
   LBM_CUDA(cudaStreamSynchronize(b->st));
-  b->al.put(s.block);
-  b->al.put(s.solid);
-  b->bytes_in_use -= s.bytes;
+  release_memory(b, s);
   s = Slot();
   b->dirty = true;
   return LBM_OK;

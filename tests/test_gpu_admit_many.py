@@ -131,12 +131,15 @@ def test_admit_many_failures_admit_nothing(lbm):
     del k0
 
 
-def test_poll_many_equals_polls(lbm):
-    specs = synth.batched_domains(6)
+@pytest.mark.parametrize("n,cap", [(6, 32), (6, 7), (3, 7)])
+def test_poll_many_equals_polls(lbm, n, cap):
+    # from four slots on poll_many gathers every slot's status word and ring entries on the
+    # device and reads them back at once; with a ring of 7 entries the reads wrap around it
+    specs = synth.batched_domains(n)
     got, want = [], []
     for many in (True, False):
         b = lbm.Batch("f16s", max_domains=8, graph_steps=0)
-        slots = b.admit_many(specs, nsteps=[11 + k for k in range(len(specs))], force_capacity=32)
+        slots = b.admit_many(specs, nsteps=[11 + k for k in range(len(specs))], force_capacity=cap)
         for _ in range(3):
             b.run(5)
             out = b.poll_many(slots) if many else [b.poll(k) for k in slots]
@@ -145,7 +148,46 @@ def test_poll_many_equals_polls(lbm):
     for ga, wa in zip(got, want):
         for (fa, da), (fb, db) in zip(ga, wa):
             assert da == db and np.array_equal(fa, fb)
-    assert [d for _, d in got[-1]] == [True] * 5 + [False]  # nsteps 11..16 after 15 steps
+    # nsteps 11, 12, ... after 15 steps
+    assert [d for _, d in got[-1]] == [11 + k <= 15 for k in range(n)]
+    assert all(len(f) == 5 for f, _ in got[0])
+
+
+def test_batched_admission_memory_returns_with_its_last_domain(lbm):
+    # the domains of one batched admission share its allocations: their memory stays
+    # counted until the last of them leaves; the others step on unchanged meanwhile
+    specs = synth.batched_domains(4)
+    b = lbm.Batch("f16s", max_domains=8, graph_steps=0)
+    slots = b.admit_many(specs, nsteps=20, force_capacity=32)
+    held = b.info()["bytes_in_use"]
+    assert held >= sum(lbm.domain_bytes(sp, "f16s", force_capacity=32) for sp in specs)
+    b.run(4)
+    b.evict(slots[0])
+    b.evict(slots[2])
+    assert b.info()["bytes_in_use"] == held and b.info()["resident"] == 2
+    b.run(16)
+    got = [(b.get_populations(k), b.poll(k)[0]) for k in (slots[1], slots[3])]
+    # a domain admitted alone returns its memory at once
+    k = b.admit(specs[0], nsteps=5)
+    assert b.info()["bytes_in_use"] > held
+    b.evict(k)
+    assert b.info()["bytes_in_use"] == held
+    b.evict(slots[1])
+    assert b.info()["bytes_in_use"] == held
+    b.evict(slots[3])
+    assert b.info()["bytes_in_use"] == 0 and b.info()["resident"] == 0
+    # the freed group entry serves the next batched admission
+    again = b.admit_many(specs[:2], nsteps=3)
+    b.run(3)
+    assert all(d for _, d in b.poll_many(again))
+    b.close()
+    for (pa, fa), sp in zip(got, (specs[1], specs[3])):
+        ref = lbm.Batch("f16s", max_domains=1, graph_steps=0)
+        r = ref.admit(sp, nsteps=20, force_capacity=32)
+        ref.run(20)
+        assert np.array_equal(pa.view(np.uint16), ref.get_populations(r).view(np.uint16))
+        assert np.array_equal(fa, ref.poll(r)[0])
+        ref.close()
 
 
 @pytest.mark.parametrize("moving", [True, 2])
