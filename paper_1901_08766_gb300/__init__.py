@@ -568,20 +568,27 @@ class Batch:
         n = len(slots)
         if n == 0:
             return []
-        bufs = []
-        S = (C.c_int32 * n)(*slots)
-        O = (_native._DP * n)()
-        M = (C.c_int64 * n)()
-        for q, k in enumerate(slots):
-            nx, ny, nb, cap = self._meta[k]
-            buf = np.zeros((cap, max(nb, 1), 2))
-            bufs.append(buf)
-            O[q] = buf.ctypes.data_as(_native._DP)
-            M[q] = cap
-        W, D, ST = (C.c_int64 * n)(), (C.c_int32 * n)(), (C.c_int32 * n)()
-        check(load().lbm_batch_poll_many(self._h, n, S, O, M, W, D, ST), "lbm_batch_poll_many")
-        return [(bufs[q][: W[q], : self._meta[k][2]].copy(), bool(D[q]), int(ST[q]))
-                for q, k in enumerate(slots)]
+        meta = [self._meta[k] for k in slots]
+        # one host buffer for every slot's entries: slot q's [cap][max(nb, 1)][2] at off[q]
+        per = np.array([2 * max(m[2], 1) for m in meta], dtype=np.int64)
+        cap = np.array([m[3] for m in meta], dtype=np.int64)
+        off = np.cumsum(per * cap) - per * cap
+        buf = np.empty(int((per * cap).sum()))
+        ptrs = (buf.ctypes.data + 8 * off).astype(np.uintp)
+        S = np.array(slots, dtype=np.int32)
+        W, D, ST = np.zeros(n, np.int64), np.zeros(n, np.int32), np.zeros(n, np.int32)
+        _i32, _i64 = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+        check(load().lbm_batch_poll_many(self._h, n, S.ctypes.data_as(_i32),
+                                         ptrs.ctypes.data_as(C.POINTER(_native._DP)),
+                                         cap.ctypes.data_as(_i64), W.ctypes.data_as(_i64),
+                                         D.ctypes.data_as(_i32), ST.ctypes.data_as(_i32)),
+              "lbm_batch_poll_many")
+        out = []
+        for q, m in enumerate(meta):
+            w, o, nb = int(W[q]), int(off[q]), max(m[2], 1)
+            f = buf[o: o + w * 2 * nb].reshape(w, nb, 2)[:, : m[2]].copy()
+            out.append((f, bool(D[q]), int(ST[q])))
+        return out
 
     def moments(self, slot: int):
         nx, ny, nb, cap = self._meta[slot]

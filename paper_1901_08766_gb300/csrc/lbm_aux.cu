@@ -786,9 +786,10 @@ cudaError_t launch_admit_scatter(cudaStream_t st, const AdmitDev *ad, int n, int
 static_assert(kPitchAlign % 16 == 0, "16-byte row stores need pitches of 16 elements");
 
 // Block r: row r of every direction of lattice A set to f^eq(rho0, u0) as init_kernel
-// does, and the same rows of lattice B to zero, with 16-byte stores (a row starts on a
-// 16-byte boundary: lattices start on 256-byte boundaries and the pitch is a multiple of
-// 64 elements).
+// does, with 16-byte stores (a row starts on a 16-byte boundary: lattices start on
+// 256-byte boundaries and the pitch is a multiple of 64 elements). Of lattice B only the
+// words holding padding columns (x >= nx) are zeroed: the first sweep writes every node
+// of it before anything reads one, and the padding stays as every lattice keeps it.
 template <int S>
 __global__ void admit_init_kernel(const AdmitDev *ad, int n) {
   using Cd = Codec<S>;
@@ -821,7 +822,8 @@ __global__ void admit_init_kernel(const AdmitDev *ad, int n) {
 #pragma unroll
     for (int q = 0; q < kPer; ++q) u.e[q] = wd * kPer + q < A.nx ? val : E(0);
     reinterpret_cast<uint4 *>(static_cast<E *>(A.lat[0]) + off)[wd] = u.v;
-    reinterpret_cast<uint4 *>(static_cast<E *>(A.lat[1]) + off)[wd] = make_uint4(0u, 0u, 0u, 0u);
+    if ((wd + 1) * kPer > A.nx)
+      reinterpret_cast<uint4 *>(static_cast<E *>(A.lat[1]) + off)[wd] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 

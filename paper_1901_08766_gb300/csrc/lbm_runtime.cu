@@ -295,6 +295,9 @@ struct lbm_batch {
   int inject = 0;  // SweepArgs::inject of later sweep launches (host failure injection)
   char *h_poll = nullptr;  // pinned staging of lbm_batch_poll_many (grows as needed)
   size_t h_poll_cap = 0;
+  bool h_poll_own = false;  // h_poll is its own allocation (else a part of h_pin)
+  char *h_pin = nullptr;    // one pinned block: h_dyn, h_ctr and the first h_poll
+  void *d_base = nullptr;   // one device block: d_doms, d_dyn, d_ctr
   char *d_poll = nullptr;  // device staging where lbm_batch_poll_many gathers (grows as needed)
   size_t d_poll_cap = 0;
   std::vector<Group> groups;  // shared allocations of batched admissions (free entries reused)
@@ -1003,7 +1006,7 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
   }
   int nrings = 0;
   for (int i = 0; i < n; ++i) nrings += ps[i].force_every > 0 ? 1 : 0;
-  const int nseg1 = 5 * n + nrings, nseg2 = 2 * n;  // fills before and after the counts are known
+  const int nseg1 = 4 * n + nrings, nseg2 = 2 * n;  // fills before and after the counts are known
   const size_t o_ad = 0;
   const size_t o_cnt = align_up(o_ad + sizeof(AdmitDev) * n, 256);
   const size_t o_ro = align_up(o_cnt + sizeof(int32_t) * counts_n, 256);
@@ -1072,11 +1075,12 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
     char *base = static_cast<char *>(x.block);
     seg1.push_back(FillSeg{D.bodies, t + o_bd + sizeof(double) * bt0, sizeof(double) * bt});
     seg1.push_back(FillSeg{D.bodies_f, t + o_bf + sizeof(float) * bt0, sizeof(float) * bt});
-    // dilation rates (zero: no body pulsates), status word, F_VP field, force ring
+    // dilation rates (zero: no body pulsates), status word, force ring (the F_VP fields
+    // are not cleared: a sweep writes F_VP of every solid node before the force
+    // reduction of its step reads it, and nothing reads it elsewhere)
     seg1.push_back(FillSeg{base + L.kappa_off, nullptr,
                            align_up(sizeof(double) * std::max(1, nbs[i]), 256) + sizeof(float) * std::max(1, nbs[i])});
     seg1.push_back(FillSeg{D.status, nullptr, sizeof(int32_t)});
-    seg1.push_back(FillSeg{D.fvp[0], nullptr, L.bodies_off - L.fvp_off});
     r0 += p.ny;
     c0 += static_cast<size_t>(nbs[i] + 1) * p.ny;
     s0 += geoms[i].nshapes;
@@ -1300,7 +1304,7 @@ lbm_status poll_many(lbm_batch *b, int n, const int32_t *slots, double *const *o
   const size_t seg_at = align_up(bytes, 16);
   const size_t need = gather ? seg_at + sizeof(FillSeg) * nspan : bytes;
   if (need > b->h_poll_cap) {
-    if (b->h_poll) cudaFreeHost(b->h_poll);
+    if (b->h_poll && b->h_poll_own) cudaFreeHost(b->h_poll);
     b->h_poll = nullptr;
     b->h_poll_cap = 0;
     const size_t cap = std::max<size_t>(need * 2, 1 << 16);
@@ -1310,6 +1314,7 @@ lbm_status poll_many(lbm_batch *b, int n, const int32_t *slots, double *const *o
       return fail(LBM_ENOMEM, "pinned staging of %zu bytes failed", cap);
     }
     b->h_poll_cap = cap;
+    b->h_poll_own = true;
   }
   if (gather && need > b->d_poll_cap) {
     b->al.put(b->d_poll);
@@ -1423,16 +1428,13 @@ void destroy(lbm_batch *b) {
   for (Slot &s : b->slots)
     if (s.used) release_memory(b, s);
   b->al.put(b->d_poll);
-  b->al.put(b->d_doms);
-  b->al.put(b->d_dyn);
+  b->al.put(b->d_base);
   b->al.put(b->d_tiles);
   b->al.put(b->d_items);
   b->al.put(b->d_moves);
-  b->al.put(b->d_ctr);
   if (b->st) cudaStreamSynchronize(b->st);
-  if (b->h_dyn) cudaFreeHost(b->h_dyn);
-  if (b->h_ctr) cudaFreeHost(b->h_ctr);
-  if (b->h_poll) cudaFreeHost(b->h_poll);
+  if (b->h_pin) cudaFreeHost(b->h_pin);
+  if (b->h_poll && b->h_poll_own) cudaFreeHost(b->h_poll);
   if (b->dyn_ev) cudaEventDestroy(b->dyn_ev);
   if (b->st2) {
     cudaStreamSynchronize(b->st2);
@@ -1475,17 +1477,26 @@ lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, 
   b->al = Alloc{alloc, free_fn, ctx, b->st};
   b->grid_force = 2 * b->sm_count;
   b->slots.resize(max_domains);
-  b->d_doms = static_cast<DomDev *>(b->al.get(sizeof(DomDev) * max_domains));
-  b->d_dyn = static_cast<DomDyn *>(b->al.get(sizeof(DomDyn) * max_domains));
-  b->d_ctr = static_cast<Counters *>(b->al.get(sizeof(Counters)));
-  if (!b->d_doms || !b->d_dyn || !b->d_ctr) { destroy(b); return fail(LBM_ENOMEM, "device allocation failed"); }
-  if (cudaMallocHost(&b->h_dyn, sizeof(DomDyn) * max_domains) != cudaSuccess ||
-      cudaMallocHost(&b->h_ctr, sizeof(Counters)) != cudaSuccess ||
+  // domain descriptions, dynamic state and counters in one device allocation; their
+  // pinned staging and the first poll staging in one pinned block
+  const size_t doms_b = align_up(sizeof(DomDev) * max_domains, 256);
+  const size_t dyn_b = align_up(sizeof(DomDyn) * max_domains, 256);
+  b->d_base = b->al.get(doms_b + dyn_b + sizeof(Counters));
+  if (!b->d_base) { destroy(b); return fail(LBM_ENOMEM, "device allocation failed"); }
+  b->d_doms = static_cast<DomDev *>(b->d_base);
+  b->d_dyn = reinterpret_cast<DomDyn *>(static_cast<char *>(b->d_base) + doms_b);
+  b->d_ctr = reinterpret_cast<Counters *>(static_cast<char *>(b->d_base) + doms_b + dyn_b);
+  const size_t ctr_b = align_up(sizeof(Counters), 256), poll_b = size_t(1) << 16;
+  if (cudaMallocHost(&b->h_pin, dyn_b + ctr_b + poll_b) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->dyn_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     destroy(b);
     return fail(LBM_ENOMEM, "pinned host allocation failed");
   }
+  b->h_dyn = reinterpret_cast<DomDyn *>(b->h_pin);
+  b->h_ctr = reinterpret_cast<Counters *>(b->h_pin + dyn_b);
+  b->h_poll = b->h_pin + dyn_b + ctr_b;
+  b->h_poll_cap = poll_b;
   if (cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_sweep, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_force[0], cudaEventDisableTiming) != cudaSuccess ||
