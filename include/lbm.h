@@ -275,6 +275,13 @@ LBM_API lbm_status lbm_batch_admit_many(lbm_batch *b, int32_t n, const lbm_param
                                         const lbm_geometry *geoms, const lbm_body *const *bodies,
                                         const int32_t *nbodies, const int64_t *nsteps, int32_t *slots);
 
+/* Whether lbm_batch_admit_many takes two allocations for all of its domains (on = 1, the
+ * default: fewer allocator calls; a group's memory returns, and leaves the budget, when
+ * its last domain leaves) or two per domain (on = 0: each domain's memory returns at its
+ * eviction, as after lbm_batch_admit; for a server under a memory budget, whose requests
+ * end at different times). Applies to later admissions. No counterpart in the paper. */
+LBM_API lbm_status lbm_batch_set_grouped_admission(lbm_batch *b, int32_t on);
+
 /* Advance every resident, unfinished domain by up to max_steps steps; a domain stops
  * at its own nsteps. *steps_run = steps actually run (<= max_steps). Asynchronous.
  * Returns LBM_EBUSY (nothing run) if a domain's force ring cannot hold the entries. */

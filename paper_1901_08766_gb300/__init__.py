@@ -690,6 +690,12 @@ class Batch:
         from .tuning import cached_autotune
         return cached_autotune(cache, self.workload_key(), tune, self.set_tile, self.get_tile)
 
+    def set_grouped_admission(self, on: bool):
+        """admit_many with two allocations for all of its domains (True, the default; a
+        group's memory returns with its last domain) or two per domain (False)."""
+        check(load().lbm_batch_set_grouped_admission(self._h, int(bool(on))),
+              "lbm_batch_set_grouped_admission")
+
     def set_tile(self, vec: int, warps: int, rows: int, pipeline: int = 0):
         check(load().lbm_batch_set_tile(self._h, vec, warps, rows, pipeline), "lbm_batch_set_tile")
 

@@ -156,6 +156,7 @@ SIGNATURES = {
     "lbm_batch_capture": (C.c_int, [_VP]),
     "lbm_batch_autotune": (C.c_int, [_VP, _I32, _DP]),
     "lbm_batch_set_tile": (C.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    "lbm_batch_set_grouped_admission": (C.c_int, [_VP, _I32]),
     "lbm_batch_get_tile": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
                                      C.POINTER(_I32)]),
     "lbm_batch_info": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I64),

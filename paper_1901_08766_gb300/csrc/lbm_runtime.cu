@@ -301,6 +301,7 @@ struct lbm_batch {
   char *d_poll = nullptr;  // device staging where lbm_batch_poll_many gathers (grows as needed)
   size_t d_poll_cap = 0;
   std::vector<Group> groups;  // shared allocations of batched admissions (free entries reused)
+  bool group_admit = true;    // lbm_batch_admit_many takes shared allocations
 };
 
 struct lbm_domain {
@@ -961,7 +962,7 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
   // Two or more domains share one allocation for their blocks and one for their solid
   // lists (two allocator calls instead of two per domain; the group's memory returns when
   // its last domain leaves).
-  const bool grouped = n > 1;
+  const bool grouped = n > 1 && b->group_admit;
   void *gblock = nullptr, *gsolid = nullptr;
   auto release = [&](lbm_status r) {
     cudaStreamSynchronize(st);
@@ -2020,6 +2021,13 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps, double *best_us) {
   Range range("lbm_batch_autotune");
   if (!b) return fail(LBM_EINVAL, "batch is NULL");
   return autotune(b, reps, best_us);
+}
+
+lbm_status lbm_batch_set_grouped_admission(lbm_batch *b, int32_t on) {
+  if (!b) return fail(LBM_EINVAL, "batch is NULL");
+  if (on != 0 && on != 1) return fail(LBM_EINVAL, "on must be 0 or 1");
+  b->group_admit = on != 0;
+  return LBM_OK;
 }
 
 lbm_status lbm_batch_set_tile(lbm_batch *b, int32_t vec, int32_t warps, int32_t rows,

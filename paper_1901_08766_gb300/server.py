@@ -88,6 +88,10 @@ class Server:
         self.max_domains = max_domains
         self.storage = storage
         self.hbm_budget = hbm_budget
+        if hbm_budget > 0 and hasattr(backend, "set_grouped_admission"):
+            # requests admitted together end at different times: under a memory budget
+            # each one's memory must return at its own eviction
+            backend.set_grouped_admission(False)
         self.chunk_steps = int(chunk_steps)
         self.force_every = int(force_every)
         self.force_capacity = self.chunk_steps + 8  # force entries of one chunk per request

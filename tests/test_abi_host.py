@@ -234,3 +234,13 @@ def test_3d_batch_no_cpu_fallback(lib):
     h = C.c_void_p()
     st = L.lbm3_batch_create(4, 0, 2, 19, None, _native.ALLOC_FN(), _native.FREE_FN(), None, C.byref(h))
     assert st == 3 and h.value is None
+
+
+def test_batch_null_handles_rejected(lib):
+    # the 2D batch's setters and drains reject a NULL batch before touching CUDA
+    L = lib.load()
+    assert L.lbm_batch_set_grouped_admission(None, 1) == 1
+    assert L.lbm_batch_set_tile(None, 8, 12, 4, 4) == 1
+    n = C.c_int64()
+    assert L.lbm_batch_run(None, 1, C.byref(n)) == 1
+    assert L.lbm_batch_pack_halos(None) == 1

@@ -181,6 +181,17 @@ def test_batched_admission_memory_returns_with_its_last_domain(lbm):
     b.run(3)
     assert all(d for _, d in b.poll_many(again))
     b.close()
+    # with grouped admission off, each domain's memory returns at its eviction
+    c = lbm.Batch("f16s", max_domains=8, graph_steps=0)
+    c.set_grouped_admission(False)
+    ks = c.admit_many(specs, nsteps=5, force_capacity=32)
+    assert c.info()["bytes_in_use"] == held
+    c.evict(ks[0])
+    assert c.info()["bytes_in_use"] < held
+    for k in ks[1:]:
+        c.evict(k)
+    assert c.info()["bytes_in_use"] == 0
+    c.close()
     for (pa, fa), sp in zip(got, (specs[1], specs[3])):
         ref = lbm.Batch("f16s", max_domains=1, graph_steps=0)
         r = ref.admit(sp, nsteps=20, force_capacity=32)
