@@ -302,6 +302,7 @@ struct lbm_batch {
   size_t d_poll_cap = 0;
   std::vector<Group> groups;  // shared allocations of batched admissions (free entries reused)
   bool group_admit = true;    // lbm_batch_admit_many takes shared allocations
+  cudaEvent_t adm_ev = nullptr;  // lbm_batch_admit_many: the per-row counts are on the host
 };
 
 struct lbm_domain {
@@ -1107,12 +1108,14 @@ lbm_status admit_many(lbm_batch *b, int n, const lbm_params *ps, const lbm_geome
   AdmitDev *d_ad = reinterpret_cast<AdmitDev *>(t + o_ad);
   ADM_CUDA(launch_fill(st, d_fill1, static_cast<int>(seg1.size())));
   ADM_CUDA(launch_admit_raster_count(st, d_ad, n, static_cast<int>(rows)));
-  ADM_CUDA(launch_admit_init(b->storage, st, d_ad, n, static_cast<int>(rows)));
   // per-row counts and unknown body ids back to the host: the one synchronisation needed
+  // (on an event before the initial state, which runs while the host sizes the lists)
   std::vector<int32_t> hc(counts_n);
   ADM_CUDA(cudaMemcpyAsync(hc.data(), t + o_cnt, sizeof(int32_t) * counts_n, cudaMemcpyDeviceToHost, st));
   ADM_CUDA(cudaMemcpyAsync(ad.data(), d_ad, sizeof(AdmitDev) * n, cudaMemcpyDeviceToHost, st));
-  ADM_CUDA(cudaStreamSynchronize(st));
+  ADM_CUDA(cudaEventRecord(b->adm_ev, st));
+  ADM_CUDA(launch_admit_init(b->storage, st, d_ad, n, static_cast<int>(rows)));
+  ADM_CUDA(cudaEventSynchronize(b->adm_ev));
   for (int i = 0; i < n; ++i)
     if (ad[i].bad > 0)
       return release(fail(LBM_EINVAL, "domain %d: mask holds body id %d but only %d bodies were given", i, ad[i].bad, nbs[i]));
@@ -1441,7 +1444,7 @@ void destroy(lbm_batch *b) {
     cudaStreamSynchronize(b->st2);
     cudaStreamDestroy(b->st2);
   }
-  for (cudaEvent_t e : {b->ev_sweep, b->ev_force[0], b->ev_force[1], b->ev_join})
+  for (cudaEvent_t e : {b->ev_sweep, b->ev_force[0], b->ev_force[1], b->ev_join, b->adm_ev})
     if (e) cudaEventDestroy(e);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
   delete b;
@@ -1502,7 +1505,8 @@ lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, 
       cudaEventCreateWithFlags(&b->ev_sweep, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_force[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_force[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->adm_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     destroy(b);
     return fail(LBM_ECUDA, "stream or event creation failed");
