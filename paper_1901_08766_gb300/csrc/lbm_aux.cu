@@ -433,9 +433,13 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
       if (c0 <= c1) {
         for (int k = lane; k < D.nshapes; k += 32) {
           shape_cols_f32(D, k, n + 1, float(n + 1), j, rs[k].lo, rs[k].hi);
-          if (rs[k].lo <= rs[k].hi) {
-            rs[k].s = shape_at(D, D.shapes[k], n + 1, true);
-            prep_row_shape(rs[k]);
+          if (rs[k].lo <= rs[k].hi) {  // the shape at n + 1, placed once for all rows
+            const PlacedShape &t = D.placed[k];
+            rs[k].s = t.s;
+            rs[k].fcx = t.fcx;
+            rs[k].fcy = t.fcy;
+            rs[k].fr2 = t.fr2;
+            rs[k].fast = t.fast;
           }
         }
         __syncwarp();
@@ -540,6 +544,37 @@ fsi_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Cou
 cudaError_t launch_fsi(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
                        const MoveRow *rows, const Counters *ctr, int s) {
   fsi_kernel<<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, s);
+  return cudaGetLastError();
+}
+
+// Every shape of a moving domain at the index after step s (block: one domain, thread:
+// one shape), as each busy row of the move kernel placed it before: its FP64 position
+// and the FP32 copies of the pre-test, computed once per step instead of once per row
+// (that FP64 work ran on every busy row). Domains with coupled bodies are placed by
+// fsi_kernel after their force reduction.
+__global__ void __launch_bounds__(kMaxMovingShapes)
+shape_table_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr, int s) {
+  const MoveRow *movedoms = rows + ctr->nmove;
+  const int ndom = ctr->nmovedom;
+  for (int q = blockIdx.x; q < ndom; q += gridDim.x) {
+    const int d = movedoms[q].dom;
+    const DomDev &D = doms[d];
+    if (D.fsi_on != 0) continue;
+    const DomDyn dy = dyn[d];
+    const long long n = dy.step0 + ctr->run_base + s;  // as in move_kernel
+    if (n >= dy.step_end) continue;
+    for (int k = threadIdx.x; k < D.nshapes; k += blockDim.x) {
+      RowShape r;
+      r.s = shape_at(D, D.shapes[k], n + 1, true);
+      prep_row_shape(r);
+      D.placed[k] = PlacedShape{r.s, r.fcx, r.fcy, r.fr2, r.fast};
+    }
+  }
+}
+
+cudaError_t launch_shape_table(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                               const MoveRow *rows, const Counters *ctr, int s) {
+  shape_table_kernel<<<grid, kMaxMovingShapes, 0, st>>>(doms, dyn, rows, ctr, s);
   return cudaGetLastError();
 }
 

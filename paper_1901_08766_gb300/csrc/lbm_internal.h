@@ -39,6 +39,7 @@ template <typename T> struct CellConst {
 
 // Per-domain static description, resident in device memory (one per batch slot).
 struct ShapeDev;
+struct PlacedShape;
 
 struct DomDev {
   void *lat[2];            // lattice A/B: [9][ny][pitch] elements of the storage type
@@ -63,6 +64,8 @@ struct DomDev {
   CellConst<double> cd;     // collision constants for FP64 compute
   // moving domains (prescribed translation; null / 0 otherwise)
   const ShapeDev *shapes;   // [nshapes] reference geometry (step index 0)
+  PlacedShape *placed;      // [nshapes] moving domains: each shape at the next step index,
+                            // written once per step before the move kernel reads it
   const float4 *shapes_f;   // [nshapes] FP32 centre x, y and extent (shape_extent) of each
   const double *centre0;    // [nbodies][2] reference centres
   double *rowsum[2];        // [ny][nbodies][3] per-row sums of -F_VP and the step they belong to,
@@ -123,7 +126,7 @@ struct Counters {
   int32_t nforce;
   long long run_base;  // steps completed in the current run (advanced by the graphs)
   int32_t nmove;       // rows of moving domains
-  int32_t pad;
+  int32_t nmovedom;    // moving domains, listed after their rows
   // work items of the direct sweep, taken by warps in turn: the next item and the warps
   // that have run out; the last warp to run out resets both for the next launch
   int32_t item_next, item_done;
@@ -143,6 +146,13 @@ struct SweepArgs {
 struct ShapeDev {
   int32_t kind, body;
   double cx, cy, radius, chord, thickness, ca, sa;  // ca, sa = cos/sin(aoa) from the host
+};
+
+// A shape at one step index with the FP32 copies of the move kernel's circle pre-test.
+struct PlacedShape {
+  ShapeDev s;
+  float fcx, fcy, fr2;  // centre and squared radius in FP32
+  int32_t fast;         // a circle within the pre-test's bounds
 };
 
 // Largest distance of a shape's node from its reference point: the radius of a circle;
@@ -204,6 +214,11 @@ cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
 // then the mask and body centres of the next step index
 cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
                         const MoveRow *rows, const Counters *ctr, int s, int storage);
+// moving domains (rows: the move list, whose ctr->nmove rows are followed by one entry
+// per moving domain): every shape at the index after step s, for the move kernel of
+// step s; grid: blocks striding over the domains
+cudaError_t launch_shape_table(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                               const MoveRow *rows, const Counters *ctr, int s);
 // the mask and body centres of one moving domain at step index n
 cudaError_t launch_place(cudaStream_t st, const DomDev *dom_dev, int nx, int ny, int pitch, long long n);
 // coupled bodies: advance their state with the force of the step just reduced, then the

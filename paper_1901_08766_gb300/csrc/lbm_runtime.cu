@@ -122,8 +122,9 @@ Layout layout_of(const lbm_params &p, int nbodies) {
   // moving domains: reference geometry, reference centres, per-row force sums
   L.shapes_off = L.centre0_off = L.rowsum_off = L.fsi_off = L.def_off = o;
   if (p.moving) {
-    // the shapes, then their FP32 centre and extent (the move kernel's culling)
-    o += align_up((sizeof(ShapeDev) + sizeof(float4)) * kMaxMovingShapes, 256);
+    // the shapes, their FP32 centre and extent (the move kernel's culling), and the
+    // shapes placed at the next step index (written each step by the shape table kernel)
+    o += align_up((sizeof(ShapeDev) + sizeof(float4) + sizeof(PlacedShape)) * kMaxMovingShapes, 256);
     L.centre0_off = o;
     o += align_up(sizeof(double) * 2 * std::max(1, nbodies), 256);
     L.rowsum_off = o;  // two tables (by lattice parity)
@@ -279,6 +280,7 @@ struct lbm_batch {
   MoveRow *d_moves = nullptr;  // rows of moving domains (geometry update after each sweep)
   int moves_cap = 0;
   int nmove = 0;               // rows in the list; 0: no move kernel in the step
+  int nmovedom = 0;            // moving domains, listed after the rows (d_moves + nmove)
   bool has_fsi = false;        // some resident domain has coupled bodies: fsi kernel per step
   bool has_deform = false;     // some resident domain has pulsating bodies: the sweep with
                                // the dilation term of U_O
@@ -303,6 +305,9 @@ struct lbm_batch {
   std::vector<Group> groups;  // shared allocations of batched admissions (free entries reused)
   bool group_admit = true;    // lbm_batch_admit_many takes shared allocations
   cudaEvent_t adm_ev = nullptr;  // lbm_batch_admit_many: the per-row counts are on the host
+  // moving domains: the shape table of a step runs on st2 beside its sweep, after ev_pre
+  // (the previous step's move kernel); the move kernel waits for ev_tab
+  cudaEvent_t ev_pre = nullptr, ev_tab = nullptr;
 };
 
 struct lbm_domain {
@@ -405,6 +410,10 @@ lbm_status rebuild_lists(lbm_batch *b) {
     has_deform = has_deform || (s.used && s.dev.deform != 0u);
   }
   if ((b->nmove > 0) != !moves.empty() || has_fsi != b->has_fsi || has_deform != b->has_deform) drop_graph(b);
+  // after the rows: one entry per moving domain (the shape table kernel's blocks)
+  const int nrows_move = static_cast<int>(moves.size());
+  for (int k = 0; k < b->max_domains && nrows_move > 0; ++k)
+    if (b->slots[k].used && b->slots[k].p.moving) moves.push_back(MoveRow{k, -1});
   b->has_fsi = has_fsi;
   b->has_deform = has_deform;
   if (static_cast<int>(moves.size()) > b->moves_cap || (!moves.empty() && !b->d_moves)) {
@@ -416,7 +425,8 @@ lbm_status rebuild_lists(lbm_batch *b) {
     b->moves_cap = cap;
     drop_graph(b);
   }
-  b->nmove = static_cast<int>(moves.size());
+  b->nmove = nrows_move;
+  b->nmovedom = static_cast<int>(moves.size()) - nrows_move;
   if (!moves.empty())
     LBM_CUDA(cudaMemcpyAsync(b->d_moves, moves.data(), sizeof(MoveRow) * moves.size(),
                              cudaMemcpyHostToDevice, b->st));
@@ -452,7 +462,7 @@ lbm_status rebuild_lists(lbm_batch *b) {
   b->h_ctr->nforce = b->nitems;
   b->h_ctr->run_base = 0;
   b->h_ctr->nmove = b->nmove;
-  b->h_ctr->pad = 0;
+  b->h_ctr->nmovedom = b->nmovedom;
   b->h_ctr->item_next = 0;
   b->h_ctr->item_done = 0;
   LBM_CUDA(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, b->st));
@@ -475,12 +485,21 @@ bool forks(const lbm_batch *b) { return !b->has_fsi; }
 
 lbm_status enqueue_step(lbm_batch *b, int s) {
   const bool fork = forks(b);
+  if (fork && b->nmove > 0) {
+    // the moving shapes at the next index, on the second stream beside the sweep
+    LBM_CUDA(cudaEventRecord(b->ev_pre, b->st));
+    LBM_CUDA(cudaStreamWaitEvent(b->st2, b->ev_pre, 0));
+    LBM_CUDA(launch_shape_table(b->grid_force, b->st2, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s));
+    LBM_CUDA(cudaEventRecord(b->ev_tab, b->st2));
+    b->launches++;
+  }
   // the sweep rewrites the F_VP field that step s - 2's force reduction read
   if (fork && s >= 2) LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_force[s & 1], 0));
   LBM_CUDA(sweep_launch(b, b->grid_sweep, b->vec, b->pipe, b->warps, b->rows, s));
   b->launches++;
   if (fork) {
     if (b->nmove > 0) {  // moving domains: row force sums (by parity), then the next geometry
+      LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_tab, 0));
       LBM_CUDA(launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
       b->launches++;
     }
@@ -492,8 +511,9 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
     return LBM_OK;
   }
   if (b->nmove > 0) {  // moving domains: row force sums, then the next step's geometry
+    LBM_CUDA(launch_shape_table(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s));
     LBM_CUDA(launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
-    b->launches++;
+    b->launches += 2;
   }
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
                          b->d_ctr, s));
@@ -599,10 +619,12 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
         prc = fail(LBM_ECUDA, "sweep launch failed");
       cudaEventRecord(ev[3 * s + 1], b->st);
       if (b->nmove > 0) {
-        if (launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
+        if (launch_shape_table(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
+                               static_cast<int>(s)) != cudaSuccess ||
+            launch_move(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
                         static_cast<int>(s), b->storage) != cudaSuccess)
           prc = fail(LBM_ECUDA, "move launch failed");
-        b->launches++;
+        b->launches += 2;
       }
       if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
                         static_cast<int>(s)) != cudaSuccess)
@@ -702,6 +724,9 @@ lbm_status prepare_slot(lbm_batch *b, const lbm_params *p, const lbm_geometry *g
   D.shapes = p->moving ? reinterpret_cast<const ShapeDev *>(base + L.shapes_off) : nullptr;
   D.shapes_f = p->moving ? reinterpret_cast<const float4 *>(base + L.shapes_off + sizeof(ShapeDev) * kMaxMovingShapes)
                          : nullptr;
+  D.placed = p->moving ? reinterpret_cast<PlacedShape *>(base + L.shapes_off + (sizeof(ShapeDev) + sizeof(float4)) *
+                                                                                  kMaxMovingShapes)
+                       : nullptr;
   D.centre0 = p->moving ? reinterpret_cast<const double *>(base + L.centre0_off) : nullptr;
   D.rowsum[0] = p->moving ? reinterpret_cast<double *>(base + L.rowsum_off) : nullptr;
   D.rowsum[1] = p->moving ? D.rowsum[0] + 3 * static_cast<size_t>(std::max(1, nbodies)) * p->ny : nullptr;
@@ -1444,7 +1469,7 @@ void destroy(lbm_batch *b) {
     cudaStreamSynchronize(b->st2);
     cudaStreamDestroy(b->st2);
   }
-  for (cudaEvent_t e : {b->ev_sweep, b->ev_force[0], b->ev_force[1], b->ev_join, b->adm_ev})
+  for (cudaEvent_t e : {b->ev_sweep, b->ev_force[0], b->ev_force[1], b->ev_join, b->adm_ev, b->ev_pre, b->ev_tab})
     if (e) cudaEventDestroy(e);
   if (b->own_stream && b->st) cudaStreamDestroy(b->st);
   delete b;
@@ -1506,7 +1531,9 @@ lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, 
       cudaEventCreateWithFlags(&b->ev_force[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_force[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->adm_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->adm_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_pre, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_tab, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     destroy(b);
     return fail(LBM_ECUDA, "stream or event creation failed");
