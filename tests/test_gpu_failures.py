@@ -141,6 +141,44 @@ def test_guard_bands_untouched_on_ragged_sizes(lbm, storage):
     assert not a.violations, a.violations
 
 
+@pytest.mark.parametrize("grouped", [True, False])
+def test_batched_admission_refused_allocations_and_guard_bands(lbm, grouped):
+    # lbm_batch_admit_many with its shared allocations (grouped) or two per domain: every
+    # allocator request it makes refused in turn gives LBM_ENOMEM, admits nothing and
+    # keeps nothing; a successful admission steps with the guard bands intact
+    specs = [synth._spec("edge", nx, ny, 0.05, [synth._circle(1, nx / 3.0, ny / 2.0, max(1.0, min(nx, ny) / 4.0))],
+                         [synth._body(nx / 3.0, ny / 2.0, 2.0)], 0, 0.02,
+                         synth._edges("inlet", "outflow", "free_slip", "free_slip"), u_in=(0.02, 0.0))
+             for nx, ny in [(65, 7), (130, 5), (257, 9), (97, 61), (3, 3)]]
+    probe = GuardedAllocator()
+    b = lbm.Batch("f16s", max_domains=8, graph_steps=0, allocator=probe)
+    b.set_grouped_admission(grouped)
+    before = probe.requests
+    slots = b.admit_many(specs, nsteps=20)
+    n_admit = probe.requests - before
+    assert n_admit == (3 if grouped else 2 * len(specs) + 1)
+    for pipe in (0, 3, 4):
+        b.set_tile(8, 8 if pipe != 3 else 5, 2, pipe)
+        b.run(5)
+    b.poll_many(slots)
+    probe.check_all()
+    b.close()
+    assert not probe.live and not probe.violations, probe.violations
+    for k in range(n_admit):
+        a = GuardedAllocator(fail_at=before + k)
+        b = lbm.Batch("f16s", max_domains=8, graph_steps=0, allocator=a)
+        b.set_grouped_admission(grouped)
+        with pytest.raises(lbm.LbmError) as ei:
+            b.admit_many(specs, nsteps=20)
+        assert ei.value.status == LBM_ENOMEM, (k, ei.value)
+        info = b.info()
+        assert info["resident"] == 0 and info["bytes_in_use"] == 0
+        a.check_all()
+        b.close()
+        assert not a.live, f"refusing request {k} leaked {len(a.live)} blocks"
+        assert not a.violations
+
+
 def test_injected_unstable_slot_is_reported_alone(lbm):
     spec = _small_channel()
     b = lbm.Batch("f32", max_domains=2, graph_steps=0)
