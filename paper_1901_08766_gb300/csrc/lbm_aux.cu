@@ -335,29 +335,28 @@ __device__ void place_centres(const DomDev &D, long long n, int lane) {
   }
 }
 
-// Rows of moving domains, one work item per row. Most rows lie far from every shape: a
-// warp first culls 32 of its items at once (lane l takes the item l strides ahead, FP32
-// column intervals at n and n + 1), then does the exact work on the items a shape
-// reaches, with the whole warp, one after the other. Busy rows stay spread over the
-// warps as in a plain one-row-per-warp loop.
-template <typename T>
-__global__ void __launch_bounds__(kMoveWarps * 32, 2)
-move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr, int s) {
-  __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  RowShape *rs = shapes[warp];
+// Rows of moving domains, in two launches. The first culls every row (one thread per
+// row, FP32 column intervals at n and n + 1) and appends the rows a shape reaches at
+// either index, with their intervals, to a list; the second gives each listed row a
+// warp for the exact work: the row's -F_VP sums over the mask the sweep used, then its
+// mask at index n + 1. (One launch that culled 32 rows per warp and then walked its busy
+// rows one after another took as long as its longest walk.) The list's order does not
+// matter: each row writes only its own sums and mask row.
+__global__ void __launch_bounds__(256)
+move_cull_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr,
+                 BusyRow *busy, int s) {
+  Counters *c = const_cast<Counters *>(ctr);
+  const int lane = threadIdx.x & 31;
   const int nrows = ctr->nmove;
   const long long run_base = ctr->run_base;
-  const int stride = gridDim.x * kMoveWarps;
-  // consecutive items (the consecutive rows a body crosses) go to warps of different
-  // blocks, so the busy rows spread over the SMs instead of filling one block's warps
-  for (int base = warp * static_cast<int>(gridDim.x) + blockIdx.x; base < nrows; base += 32 * stride) {
-    // lane l: item base + l * stride
-    const int ql = base + lane * stride;
+  const int stride = gridDim.x * blockDim.x;
+  // warp-uniform bounds: every lane takes part in the ballot
+  for (int base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < nrows; base += stride) {
+    const int q = base + lane;
     int olo = 1, ohi = 0, nlo = 1, nhi = 0;
-    bool busy = false;
-    if (ql < nrows) {
-      const MoveRow mr = rows[ql];
+    bool is_busy = false;
+    if (q < nrows) {
+      const MoveRow mr = rows[q];
       const DomDev &D = doms[mr.dom];
       const DomDyn dy = dyn[mr.dom];
       const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
@@ -374,79 +373,106 @@ move_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Co
           if (lo <= hi) { nlo = min(nlo, lo); nhi = max(nhi, hi); }
         }
         // row 0 also moves the body centres (domains without coupled bodies)
-        busy = olo <= ohi || nlo <= nhi || (mr.j == 0 && !fsi);
+        is_busy = olo <= ohi || nlo <= nhi || (mr.j == 0 && !fsi);
       }
     }
-    unsigned work = __ballot_sync(0xffffffffu, busy);
-    while (work) {
-      const int l = __ffs(work) - 1;
-      work &= work - 1;
-      const int q = base + l * stride;
-      const int jolo = __shfl_sync(0xffffffffu, olo, l), johi = __shfl_sync(0xffffffffu, ohi, l);
-      const int jnlo = __shfl_sync(0xffffffffu, nlo, l), jnhi = __shfl_sync(0xffffffffu, nhi, l);
-      const MoveRow mr = rows[q];
-      const DomDev &D = doms[mr.dom];
-      const DomDyn dy = dyn[mr.dom];
-      const long long n = dy.step0 + run_base + s;
-      const int j = mr.j;
-      // (a domain with coupled bodies takes only the row sums here: its next geometry
-      // depends on the force, and fsi_kernel places it after the force reduction)
-      const bool fsi = D.fsi_on != 0;
-      const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
-      if (D.force_every > 0 && (n + 1) % D.force_every == 0 && jolo <= johi) {
-        // -F_VP of each body over the row's solid nodes (all inside the old interval),
-        // with the step index as a tag: the force kernel adds only the entries of its
-        // step, so rows (or bodies) without solid nodes here need no entry
-        // the F_VP field the sweep of step n wrote (the parity of the lattice it read)
-        const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
-        const T *fv = static_cast<const T *>(D.fvp[par]) + 2 * static_cast<size_t>(j) * D.pitch;
-        unsigned present = 0u;  // bit b: body b has a node in the interval
-        for (int i = jolo + lane; i <= johi; i += 32) present |= 1u << (mrow[i] & 31);
-        present = __reduce_or_sync(0xffffffffu, present) & ~1u;
-        while (present) {
-          const int body = __ffs(present) - 1;
-          present &= present - 1;
-          double fx = 0.0, fy = 0.0;
-          for (int i = jolo + lane; i <= johi; i += 32)
-            if (mrow[i] == body) {
-              fx -= double(fv[2 * i]);
-              fy -= double(fv[2 * i + 1]);
-            }
+    const unsigned m = __ballot_sync(0xffffffffu, is_busy);
+    if (m != 0u) {
+      int at = 0;
+      if (lane == 0) at = atomicAdd(&c->nbusy, __popc(m));
+      at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & ((1u << lane) - 1u));
+      if (is_busy) busy[at] = BusyRow{q, olo, ohi, nlo, nhi};
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMoveWarps * 32, 3)
+move_rows_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr,
+                 const BusyRow *busy, int s) {
+  __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
+  Counters *c = const_cast<Counters *>(ctr);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RowShape *rs = shapes[warp];
+  const int nbusy = ctr->nbusy;
+  const long long run_base = ctr->run_base;
+  // consecutive list entries (the consecutive rows a body crosses) go to warps of
+  // different blocks, so the busy rows spread over the SMs
+  for (int w = warp * static_cast<int>(gridDim.x) + blockIdx.x; w < nbusy; w += gridDim.x * kMoveWarps) {
+    const BusyRow br = busy[w];
+    const int jolo = br.olo, johi = br.ohi, jnlo = br.nlo, jnhi = br.nhi;
+    const MoveRow mr = rows[br.q];
+    const DomDev &D = doms[mr.dom];
+    const DomDyn dy = dyn[mr.dom];
+    const long long n = dy.step0 + run_base + s;
+    const int j = mr.j;
+    // (a domain with coupled bodies takes only the row sums here: its next geometry
+    // depends on the force, and fsi_kernel places it after the force reduction)
+    const bool fsi = D.fsi_on != 0;
+    const uint8_t *mrow = D.mask + static_cast<size_t>(j) * D.pitch;
+    if (D.force_every > 0 && (n + 1) % D.force_every == 0 && jolo <= johi) {
+      // -F_VP of each body over the row's solid nodes (all inside the old interval),
+      // with the step index as a tag: the force kernel adds only the entries of its
+      // step, so rows (or bodies) without solid nodes here need no entry
+      // the F_VP field the sweep of step n wrote (the parity of the lattice it read)
+      const int par = (dy.parity + static_cast<int>((run_base + s) & 1)) & 1;
+      const T *fv = static_cast<const T *>(D.fvp[par]) + 2 * static_cast<size_t>(j) * D.pitch;
+      unsigned present = 0u;  // bit b: body b has a node in the interval
+      for (int i = jolo + lane; i <= johi; i += 32) present |= 1u << (mrow[i] & 31);
+      present = __reduce_or_sync(0xffffffffu, present) & ~1u;
+      while (present) {
+        const int body = __ffs(present) - 1;
+        present &= present - 1;
+        double fx = 0.0, fy = 0.0;
+        for (int i = jolo + lane; i <= johi; i += 32)
+          if (mrow[i] == body) {
+            fx -= double(fv[2 * i]);
+            fy -= double(fv[2 * i + 1]);
+          }
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            fx += __shfl_down_sync(0xffffffffu, fx, off);
-            fy += __shfl_down_sync(0xffffffffu, fy, off);
-          }
-          if (lane == 0) {
-            double *r = D.rowsum[par] + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
-            r[0] = fx;
-            r[1] = fy;
-            r[2] = static_cast<double>(n);
-          }
+        for (int off = 16; off > 0; off >>= 1) {
+          fx += __shfl_down_sync(0xffffffffu, fx, off);
+          fy += __shfl_down_sync(0xffffffffu, fy, off);
+        }
+        if (lane == 0) {
+          double *r = D.rowsum[par] + (static_cast<size_t>(j) * D.nbodies + (body - 1)) * 3;
+          r[0] = fx;
+          r[1] = fy;
+          r[2] = static_cast<double>(n);
+        }
+      }
+    }
+    __syncwarp();
+    if (fsi) continue;
+    // the mask changes only where a shape reaches at either index: the shapes at
+    // n + 1 with their column intervals in this row, then their ids over the union
+    const int c0 = min(jolo, jnlo), c1 = max(johi, jnhi);
+    if (c0 <= c1) {
+      for (int k = lane; k < D.nshapes; k += 32) {
+        shape_cols_f32(D, k, n + 1, float(n + 1), j, rs[k].lo, rs[k].hi);
+        if (rs[k].lo <= rs[k].hi) {  // the shape at n + 1, placed once for all rows
+          const PlacedShape &t = D.placed[k];
+          rs[k].s = t.s;
+          rs[k].fcx = t.fcx;
+          rs[k].fcy = t.fcy;
+          rs[k].fr2 = t.fr2;
+          rs[k].fast = t.fast;
         }
       }
       __syncwarp();
-      if (fsi) continue;
-      // the mask changes only where a shape reaches at either index: the shapes at
-      // n + 1 with their column intervals in this row, then their ids over the union
-      const int c0 = min(jolo, jnlo), c1 = max(johi, jnhi);
-      if (c0 <= c1) {
-        for (int k = lane; k < D.nshapes; k += 32) {
-          shape_cols_f32(D, k, n + 1, float(n + 1), j, rs[k].lo, rs[k].hi);
-          if (rs[k].lo <= rs[k].hi) {  // the shape at n + 1, placed once for all rows
-            const PlacedShape &t = D.placed[k];
-            rs[k].s = t.s;
-            rs[k].fcx = t.fcx;
-            rs[k].fcy = t.fcy;
-            rs[k].fr2 = t.fr2;
-            rs[k].fast = t.fast;
-          }
-        }
-        __syncwarp();
-        write_ids(D, j, c0, c1, lane, rs);
-      }
-      __syncwarp();
-      if (j == 0) place_centres(D, n + 1, lane);
+      write_ids(D, j, c0, c1, lane, rs);
+    }
+    __syncwarp();
+    if (j == 0) place_centres(D, n + 1, lane);
+  }
+  // the last block to finish empties the list for the next step (every block read its
+  // length before finishing)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&c->busy_done, 1) == static_cast<int>(gridDim.x) - 1) {
+      c->nbusy = 0;
+      c->busy_done = 0;
     }
   }
 }
@@ -481,7 +507,7 @@ fsi_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Cou
   RowShape *rs = shapes[warp];
   const int nrows = ctr->nmove;
   const long long run_base = ctr->run_base;
-  // consecutive rows to warps of different blocks (as in move_kernel)
+  // consecutive rows to warps of different blocks (as in move_rows_kernel)
   for (int q = warp * static_cast<int>(gridDim.x) + blockIdx.x; q < nrows; q += gridDim.x * kMoveWarps) {
     const MoveRow mr = rows[q];
     const DomDev &D = doms[mr.dom];
@@ -561,7 +587,7 @@ shape_table_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, c
     const DomDev &D = doms[d];
     if (D.fsi_on != 0) continue;
     const DomDyn dy = dyn[d];
-    const long long n = dy.step0 + ctr->run_base + s;  // as in move_kernel
+    const long long n = dy.step0 + ctr->run_base + s;  // as in the move kernels
     if (n >= dy.step_end) continue;
     for (int k = threadIdx.x; k < D.nshapes; k += blockDim.x) {
       RowShape r;
@@ -579,11 +605,12 @@ cudaError_t launch_shape_table(int grid, cudaStream_t st, const DomDev *doms, co
 }
 
 cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
-                        const MoveRow *rows, const Counters *ctr, int s, int storage) {
+                        const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s, int storage) {
+  move_cull_kernel<<<grid, 256, 0, st>>>(doms, dyn, rows, ctr, busy, s);
   if (storage == LBM_F64)
-    move_kernel<double><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, s);
+    move_rows_kernel<double><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, busy, s);
   else
-    move_kernel<float><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, s);
+    move_rows_kernel<float><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, busy, s);
   return cudaGetLastError();
 }
 

@@ -120,6 +120,13 @@ struct MoveRow {
   int32_t dom, j;
 };
 
+// A row of a moving domain that a shape reaches at index n or n + 1 (the move kernels'
+// list): its index in the move rows and its column intervals at n and at n + 1 (lo > hi:
+// none).
+struct BusyRow {
+  int32_t q, olo, ohi, nlo, nhi;
+};
+
 // Device-side counters of a batch.
 struct Counters {
   int32_t ntiles;
@@ -130,6 +137,9 @@ struct Counters {
   // work items of the direct sweep, taken by warps in turn: the next item and the warps
   // that have run out; the last warp to run out resets both for the next launch
   int32_t item_next, item_done;
+  // the move kernels' list of busy rows: its length, and the blocks of the second launch
+  // that have finished (the last one empties the list)
+  int32_t nbusy, busy_done;
 };
 
 struct SweepArgs {
@@ -211,9 +221,10 @@ void fill_cell_const(DomDev &d, int storage);
 void set_last_error(const char *msg);
 cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
 // moving domains: after the sweep of a step, per-row -F_VP sums over the mask it used,
-// then the mask and body centres of the next step index
+// then the mask and body centres of the next step index (two launches: the rows a shape
+// reaches are listed in busy, then each gets a warp)
 cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
-                        const MoveRow *rows, const Counters *ctr, int s, int storage);
+                        const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s, int storage);
 // moving domains (rows: the move list, whose ctr->nmove rows are followed by one entry
 // per moving domain): every shape at the index after step s, for the move kernel of
 // step s; grid: blocks striding over the domains

@@ -278,6 +278,7 @@ struct lbm_batch {
   ForceItem *d_items = nullptr;
   int items_cap = 0;
   MoveRow *d_moves = nullptr;  // rows of moving domains (geometry update after each sweep)
+  BusyRow *d_busy = nullptr;   // the move kernels' list of busy rows (as many entries as d_moves)
   int moves_cap = 0;
   int nmove = 0;               // rows in the list; 0: no move kernel in the step
   int nmovedom = 0;            // moving domains, listed after the rows (d_moves + nmove)
@@ -424,8 +425,10 @@ lbm_status rebuild_lists(lbm_batch *b) {
     const int cap = std::max<int>(static_cast<int>(moves.size()) * 2, 1024);
     LBM_CUDA(cudaStreamSynchronize(b->st));
     b->al.put(b->d_moves);
+    b->al.put(b->d_busy);
     b->d_moves = static_cast<MoveRow *>(b->al.get(sizeof(MoveRow) * cap));
-    if (!b->d_moves) { b->moves_cap = 0; return fail(LBM_ENOMEM, "move list allocation failed"); }
+    b->d_busy = static_cast<BusyRow *>(b->al.get(sizeof(BusyRow) * cap));
+    if (!b->d_moves || !b->d_busy) { b->moves_cap = 0; return fail(LBM_ENOMEM, "move list allocation failed"); }
     b->moves_cap = cap;
     drop_graph(b);
   }
@@ -469,6 +472,8 @@ lbm_status rebuild_lists(lbm_batch *b) {
   b->h_ctr->nmovedom = b->nmovedom;
   b->h_ctr->item_next = 0;
   b->h_ctr->item_done = 0;
+  b->h_ctr->nbusy = 0;
+  b->h_ctr->busy_done = 0;
   LBM_CUDA(cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, b->st));
   LBM_CUDA(cudaStreamSynchronize(b->st));
   b->dirty = false;
@@ -504,8 +509,8 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   if (fork) {
     if (b->nmove > 0) {  // moving domains: row force sums (by parity), then the next geometry
       LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_tab, 0));
-      LBM_CUDA(launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
-      b->launches++;
+      LBM_CUDA(launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s, b->storage));
+      b->launches += 2;
     }
     LBM_CUDA(cudaEventRecord(b->ev_sweep, b->st));
     LBM_CUDA(cudaStreamWaitEvent(b->st2, b->ev_sweep, 0));
@@ -516,8 +521,8 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   }
   if (b->nmove > 0) {  // moving domains: row force sums, then the next step's geometry
     LBM_CUDA(launch_shape_table(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s));
-    LBM_CUDA(launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s, b->storage));
-    b->launches += 2;
+    LBM_CUDA(launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s, b->storage));
+    b->launches += 3;
   }
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
                          b->d_ctr, s));
@@ -625,10 +630,10 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
       if (b->nmove > 0) {
         if (launch_shape_table(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
                                static_cast<int>(s)) != cudaSuccess ||
-            launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
+            launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy,
                         static_cast<int>(s), b->storage) != cudaSuccess)
           prc = fail(LBM_ECUDA, "move launch failed");
-        b->launches += 2;
+        b->launches += 3;
       }
       if (launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items, b->d_ctr,
                         static_cast<int>(s)) != cudaSuccess)
@@ -662,7 +667,8 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
     const long long reps = steps / b->graph_steps;
     for (long long r = 0; r < reps; ++r) {
       LBM_CUDA(cudaGraphLaunch(b->graph, b->st));
-      b->launches += (2 + (b->nmove > 0 ? 1 : 0) + (b->has_fsi ? 1 : 0)) * static_cast<long long>(b->graph_steps) + 1;
+      // per step: sweep, forces; moving domains: shape table, cull, rows; coupled: fsi
+      b->launches += (2 + (b->nmove > 0 ? 3 : 0) + (b->has_fsi ? 1 : 0)) * static_cast<long long>(b->graph_steps) + 1;
     }
     s0 = reps * b->graph_steps;
   }
@@ -1465,6 +1471,7 @@ void destroy(lbm_batch *b) {
   b->al.put(b->d_tiles);
   b->al.put(b->d_items);
   b->al.put(b->d_moves);
+  b->al.put(b->d_busy);
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->h_pin) cudaFreeHost(b->h_pin);
   if (b->h_poll && b->h_poll_own) cudaFreeHost(b->h_poll);
