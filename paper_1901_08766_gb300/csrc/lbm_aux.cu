@@ -341,8 +341,11 @@ __device__ void place_centres(const DomDev &D, long long n, int lane) {
 // warp for the exact work: the row's -F_VP sums over the mask the sweep used, then its
 // mask at index n + 1. (One launch that culled 32 rows per warp and then walked its busy
 // rows one after another took as long as its longest walk.) The list's order does not
-// matter: each row writes only its own sums and mask row.
-__global__ void __launch_bounds__(256)
+// matter: each row writes only its own sums and mask row. The culling reads only the
+// shapes, so it runs beside the sweep, in 64-thread blocks (at most 64 registers: the
+// room one block has on an SM next to the sweep's two).
+constexpr int kCullThreads = 64;
+__global__ void __launch_bounds__(kCullThreads)
 move_cull_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr,
                  BusyRow *busy, int s) {
   Counters *c = const_cast<Counters *>(ctr);
@@ -604,9 +607,14 @@ cudaError_t launch_shape_table(int grid, cudaStream_t st, const DomDev *doms, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
-                        const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s, int storage) {
-  move_cull_kernel<<<grid, 256, 0, st>>>(doms, dyn, rows, ctr, busy, s);
+cudaError_t launch_move_cull(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                             const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s) {
+  move_cull_kernel<<<grid, kCullThreads, 0, st>>>(doms, dyn, rows, ctr, busy, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move_rows(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                             const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s, int storage) {
   if (storage == LBM_F64)
     move_rows_kernel<double><<<grid, kMoveWarps * 32, 0, st>>>(doms, dyn, rows, ctr, busy, s);
   else

@@ -220,11 +220,14 @@ void fill_cell_const(DomDev &d, int storage);
 // the message lbm_last_error returns (shared by the 2D and 3D entry points)
 void set_last_error(const char *msg);
 cudaError_t launch_advance(cudaStream_t st, Counters *ctr, int k);
-// moving domains: after the sweep of a step, per-row -F_VP sums over the mask it used,
-// then the mask and body centres of the next step index (two launches: the rows a shape
-// reaches are listed in busy, then each gets a warp)
-cudaError_t launch_move(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
-                        const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s, int storage);
+// moving domains, step s: the rows a shape reaches at its index n or n + 1 listed in busy
+// (needs only the shapes, so it may run beside the sweep) ...
+cudaError_t launch_move_cull(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                             const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s);
+// ... then, after the sweep, a warp per listed row: its -F_VP sums over the mask the
+// sweep used, then its mask at n + 1, and the body centres of n + 1
+cudaError_t launch_move_rows(int grid, cudaStream_t st, const DomDev *doms, const DomDyn *dyn,
+                             const MoveRow *rows, const Counters *ctr, BusyRow *busy, int s, int storage);
 // moving domains (rows: the move list, whose ctr->nmove rows are followed by one entry
 // per moving domain): every shape at the index after step s, for the move kernel of
 // step s; grid: blocks striding over the domains

@@ -495,12 +495,14 @@ bool forks(const lbm_batch *b) { return !b->has_fsi; }
 lbm_status enqueue_step(lbm_batch *b, int s) {
   const bool fork = forks(b);
   if (fork && b->nmove > 0) {
-    // the moving shapes at the next index, on the second stream beside the sweep
+    // the moving shapes at the next index and the list of rows they reach, on the second
+    // stream beside the sweep (neither reads what the sweep writes)
     LBM_CUDA(cudaEventRecord(b->ev_pre, b->st));
     LBM_CUDA(cudaStreamWaitEvent(b->st2, b->ev_pre, 0));
     LBM_CUDA(launch_shape_table(b->grid_force, b->st2, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s));
+    LBM_CUDA(launch_move_cull(b->grid_force, b->st2, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s));
     LBM_CUDA(cudaEventRecord(b->ev_tab, b->st2));
-    b->launches++;
+    b->launches += 2;
   }
   // the sweep rewrites the F_VP field that step s - 2's force reduction read
   if (fork && s >= 2) LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_force[s & 1], 0));
@@ -509,8 +511,8 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   if (fork) {
     if (b->nmove > 0) {  // moving domains: row force sums (by parity), then the next geometry
       LBM_CUDA(cudaStreamWaitEvent(b->st, b->ev_tab, 0));
-      LBM_CUDA(launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s, b->storage));
-      b->launches += 2;
+      LBM_CUDA(launch_move_rows(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s, b->storage));
+      b->launches++;
     }
     LBM_CUDA(cudaEventRecord(b->ev_sweep, b->st));
     LBM_CUDA(cudaStreamWaitEvent(b->st2, b->ev_sweep, 0));
@@ -521,7 +523,8 @@ lbm_status enqueue_step(lbm_batch *b, int s) {
   }
   if (b->nmove > 0) {  // moving domains: row force sums, then the next step's geometry
     LBM_CUDA(launch_shape_table(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, s));
-    LBM_CUDA(launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s, b->storage));
+    LBM_CUDA(launch_move_cull(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s));
+    LBM_CUDA(launch_move_rows(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy, s, b->storage));
     b->launches += 3;
   }
   LBM_CUDA(launch_forces(b->storage, b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_items,
@@ -630,8 +633,10 @@ lbm_status run(lbm_batch *b, long long max_steps, long long *steps_run, Profile 
       if (b->nmove > 0) {
         if (launch_shape_table(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr,
                                static_cast<int>(s)) != cudaSuccess ||
-            launch_move(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy,
-                        static_cast<int>(s), b->storage) != cudaSuccess)
+            launch_move_cull(b->grid_force, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy,
+                             static_cast<int>(s)) != cudaSuccess ||
+            launch_move_rows(b->grid_move, b->st, b->d_doms, b->d_dyn, b->d_moves, b->d_ctr, b->d_busy,
+                             static_cast<int>(s), b->storage) != cudaSuccess)
           prc = fail(LBM_ECUDA, "move launch failed");
         b->launches += 3;
       }
