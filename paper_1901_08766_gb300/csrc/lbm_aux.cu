@@ -358,8 +358,9 @@ move_cull_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, con
     const int q = base + lane;
     int olo = 1, ohi = 0, nlo = 1, nhi = 0;
     bool is_busy = false;
+    MoveRow mr{0, 0};
     if (q < nrows) {
-      const MoveRow mr = rows[q];
+      mr = rows[q];
       const DomDev &D = doms[mr.dom];
       const DomDyn dy = dyn[mr.dom];
       const long long n = dy.step0 + run_base + s;  // the sweep just computed step n + 1
@@ -384,13 +385,13 @@ move_cull_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, con
       int at = 0;
       if (lane == 0) at = atomicAdd(&c->nbusy, __popc(m));
       at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & ((1u << lane) - 1u));
-      if (is_busy) busy[at] = BusyRow{q, olo, ohi, nlo, nhi};
+      if (is_busy) busy[at] = BusyRow{mr.dom, mr.j, olo, ohi, nlo, nhi};
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMoveWarps * 32, 3)
+__global__ void __launch_bounds__(kMoveWarps * 32, 4)
 move_rows_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, const Counters *ctr,
                  const BusyRow *busy, int s) {
   __shared__ RowShape shapes[kMoveWarps][kMaxMovingShapes];
@@ -404,11 +405,10 @@ move_rows_kernel(const DomDev *doms, const DomDyn *dyn, const MoveRow *rows, con
   for (int w = warp * static_cast<int>(gridDim.x) + blockIdx.x; w < nbusy; w += gridDim.x * kMoveWarps) {
     const BusyRow br = busy[w];
     const int jolo = br.olo, johi = br.ohi, jnlo = br.nlo, jnhi = br.nhi;
-    const MoveRow mr = rows[br.q];
-    const DomDev &D = doms[mr.dom];
-    const DomDyn dy = dyn[mr.dom];
+    const DomDev &D = doms[br.dom];
+    const DomDyn dy = dyn[br.dom];
     const long long n = dy.step0 + run_base + s;
-    const int j = mr.j;
+    const int j = br.j;
     // (a domain with coupled bodies takes only the row sums here: its next geometry
     // depends on the force, and fsi_kernel places it after the force reduction)
     const bool fsi = D.fsi_on != 0;

@@ -121,10 +121,9 @@ struct MoveRow {
 };
 
 // A row of a moving domain that a shape reaches at index n or n + 1 (the move kernels'
-// list): its index in the move rows and its column intervals at n and at n + 1 (lo > hi:
-// none).
+// list): its domain and row, and its column intervals at n and at n + 1 (lo > hi: none).
 struct BusyRow {
-  int32_t q, olo, ohi, nlo, nhi;
+  int32_t dom, j, olo, ohi, nlo, nhi;
 };
 
 // Device-side counters of a batch.

@@ -289,9 +289,10 @@ struct lbm_batch {
   Counters *h_ctr = nullptr;  // pinned staging for tile/item counts
   int vec = 0, warps = 0, rows = 0, pipe = 0;
   int grid_sweep = 0, grid_force = 0;
-  // the move kernel: three of its 256-thread blocks (77 registers) fit on an SM; warps
-  // walk their busy rows one after another, so more warps shorten the longest walk
-  // (all-moving 64-domain batch: 400.5 -> 392.3 us per step against two blocks per SM)
+  // the move kernels' per-row pass: four of its 256-thread blocks (64 registers, 44 KB
+  // of shared memory) fit on an SM; each listed row gets a warp, so more warps leave
+  // fewer rows to one warp (a move kernel that walked its rows itself: 400.5 -> 392.3 us
+  // per step of the all-moving 64-domain batch at three blocks per SM against two)
   int grid_move = 0;
   int ntiles = 0, nitems = 0;
   bool dirty = true;
@@ -1521,7 +1522,7 @@ lbm_status create(int max_domains, size_t budget, int storage, int graph_steps, 
   }
   b->al = Alloc{alloc, free_fn, ctx, b->st};
   b->grid_force = 2 * b->sm_count;
-  b->grid_move = 3 * b->sm_count;
+  b->grid_move = 4 * b->sm_count;
   b->slots.resize(max_domains);
   // domain descriptions, dynamic state and counters in one device allocation; their
   // pinned staging and the first poll staging in one pinned block
