@@ -22,3 +22,13 @@ def lbm():
     import paper_1901_08766_gb300 as pkg
     pkg.load()
     return pkg
+
+
+@pytest.fixture(scope="session")
+def built_library():
+    """The compiled library, built here if needed (nvcc only; no GPU): host tests whose
+    code path asks the library for sizes (lbm_domain_bytes) load it without a device."""
+    import paper_1901_08766_gb300 as pkg
+    pkg.build()
+    pkg.load()
+    return pkg

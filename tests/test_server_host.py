@@ -10,6 +10,12 @@ from paper_1901_08766_gb300 import tuning
 from paper_1901_08766_gb300._native import LBM_EBUSY, LBM_EINVAL, LBM_EUNSTABLE, LbmError
 
 
+@pytest.fixture(autouse=True)
+def _library(built_library):
+    # the server sizes requests under a memory budget with lbm_domain_bytes
+    return built_library
+
+
 class FakeBatch:
     """Mimics lbm.Batch: a slot runs until its own step target; each step records a force
     that depends only on (request name, step), like the real library's results."""
@@ -227,6 +233,23 @@ def test_group_admission_is_fifo_and_used():
     res = [f.result() for f in futs]
     assert all(r.status == "ok" for r in res) and [r.steps for r in res] == [20 + i for i in range(6)]
     assert [r.admitted for r in res] == sorted(r.admitted for r in res)
+
+
+class FakeBatchGrouping(FakeBatchMany):
+    """FakeBatchMany that records the grouped-admission setting it is given."""
+
+    def set_grouped_admission(self, on):
+        self.grouped = bool(on)
+
+
+@pytest.mark.parametrize("budget,grouped", [(0, None), (1 << 30, False)])
+def test_server_under_a_budget_admits_groups_per_domain(budget, grouped):
+    # requests admitted together end at different times: under a memory budget the
+    # server turns grouped admission off, so each request's memory returns at its own
+    # eviction; without a budget the batch keeps its default
+    fb = FakeBatchGrouping(budget_cells=10 ** 9, clock=Clock())
+    srvmod.Server(backend=fb, hbm_budget=budget, chunk_steps=16, clock=fb.clock)
+    assert getattr(fb, "grouped", None) is grouped
 
 
 def test_server_retunes_per_workload_class_and_persists(tmp_path):
